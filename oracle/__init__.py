@@ -1,0 +1,166 @@
+"""CPU oracle of the multi-resolution sampling renderer and fusion network.
+
+TEST INFRASTRUCTURE ONLY: the slow, obviously-correct reference the CUDA
+library is checked against.  It shares no code with the CUDA path; only
+`tests/`, `__graft_entry__.smoke()` and `bench.py`'s CPU-baseline leg may
+import it.  The product path never routes through it.
+
+* `render`, `lbvh`, `cast`, `philox*`: ctypes wrappers over `orc_pt.c`, a plain
+  C path tracer compiled with -ffp-contract=off (see that file's header).
+* `cnn`: the fusion network forward/backward, loss and Adam in float64 numpy.
+* `metrics`: linear->sRGB (Eq. cvt_color), RelMSE and PSNR (Sec. 5), average
+  spp (Sec. 5.1), box downsampling and the fallback gate.
+
+Functions whose results are not fixed by a closed form or library routine are
+still pinned by tests: see each module's header.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liborc.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile orc_pt.c into oracle/_build/liborc.so (gcc, -ffp-contract=off)."""
+    src = os.path.join(_HERE, "orc_pt.c")
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(src):
+        return _SO
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = _SO + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+           "-shared", "-fPIC", "-o", tmp, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_SO)
+            P = ctypes.c_void_p
+            i32, u32, u64 = ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64
+            L.orc_philox4x32_10.argtypes = [P, P, P]
+            L.orc_philox_uniforms.argtypes = [u32, u32, u32, u64, P]
+            L.orc_sincos2pi.argtypes = [P, i32, P, P]
+            L.orc_morton.argtypes = [P, i32, P]
+            L.orc_lbvh.argtypes = [P, i32, P, P, P, P, P]
+            L.orc_lbvh.restype = i32
+            L.orc_cast.argtypes = [P, i32, P, P, i32, i32, P, P]
+            L.orc_cast.restype = i32
+            L.orc_render.argtypes = [P, i32, P, P, P, P, i32, P, P, i32, i32, i32, i32, i32,
+                                     u64, i32, i32, i32, P, P, P, P, P, P]
+            L.orc_render.restype = i32
+            L.orc_num_threads.restype = i32
+            _lib = L
+    return _lib
+
+
+def _p(a):
+    return ctypes.c_void_p(a.ctypes.data) if a is not None else None
+
+
+def philox4x32_10(ctr, key):
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib().orc_philox4x32_10(_p(c), _p(k), _p(out))
+    return out
+
+
+def philox_uniforms(pixel: int, sample: int, bounce: int, seed: int):
+    """The 8 uniforms of one (pixel, sample, bounce): dims 0..7."""
+    out = np.zeros(8, dtype=np.float32)
+    lib().orc_philox_uniforms(pixel, sample, bounce, seed, _p(out))
+    return out
+
+
+def sincos2pi(u):
+    u = np.ascontiguousarray(u, dtype=np.float32)
+    c = np.zeros_like(u)
+    s = np.zeros_like(u)
+    lib().orc_sincos2pi(_p(u), u.size, _p(c), _p(s))
+    return c, s
+
+
+def morton(V):
+    V = np.ascontiguousarray(V, dtype=np.float32)
+    out = np.zeros(len(V), dtype=np.uint32)
+    lib().orc_morton(_p(V), len(V), _p(out))
+    return out
+
+
+def lbvh(V):
+    """Returns dict(morton, order, left, right, box) of the binary radix tree."""
+    V = np.ascontiguousarray(V, dtype=np.float32)
+    n = len(V)
+    r = {
+        "morton": np.zeros(n, np.uint32),
+        "order": np.zeros(n, np.int32),
+        "left": np.zeros(max(n - 1, 0), np.int32),
+        "right": np.zeros(max(n - 1, 0), np.int32),
+        "box": np.zeros((max(2 * n - 1, 0), 6), np.float32),
+    }
+    if n:
+        rc = lib().orc_lbvh(_p(V), n, _p(r["morton"]), _p(r["order"]),
+                            _p(r["left"]) if n > 1 else None,
+                            _p(r["right"]) if n > 1 else None, _p(r["box"]))
+        assert rc == 0
+    return r
+
+
+def cast(V, orig, dirs, brute: bool = False):
+    """Closest hit per ray through the LBVH (or by brute force)."""
+    V = np.ascontiguousarray(V, dtype=np.float32)
+    o = np.ascontiguousarray(orig, dtype=np.float32)
+    d = np.ascontiguousarray(dirs, dtype=np.float32)
+    prim = np.zeros(len(o), np.int32)
+    t = np.zeros(len(o), np.float32)
+    rc = lib().orc_cast(_p(V), len(V), _p(o), _p(d), len(o), int(brute), _p(prim), _p(t))
+    assert rc == 0
+    return prim, t
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())
+
+
+def render(scene, W, H, spp, max_depth, rr_start=None, seed=0, rows=None, threads=0):
+    """Path-trace the scene; returns dict(radiance[H,W,3], albedo, normal,
+    depth[H,W], counts[max_depth+1], shadow_counts[max_depth+1]).
+
+    rr_start=None disables Russian roulette.  rows=(r0, r1) renders only those
+    image rows (the result then has r1-r0 rows) -- used for bounded samples."""
+    if rr_start is None:
+        rr_start = 1 << 30
+    r0, r1 = (0, H) if rows is None else rows
+    h = r1 - r0
+    out = {
+        "radiance": np.zeros((h, W, 3), np.float32),
+        "albedo": np.zeros((h, W, 3), np.float32),
+        "normal": np.zeros((h, W, 3), np.float32),
+        "depth": np.zeros((h, W), np.float32),
+        "counts": np.zeros(max_depth + 1, np.uint64),
+        "shadow_counts": np.zeros(max_depth + 1, np.uint64),
+    }
+    s = scene
+    rc = lib().orc_render(_p(s["V"]), len(s["V"]), _p(s["tri_mat"]), _p(s["tri_light"]),
+                          _p(s["mats"]), _p(s["lights"]), len(s["lights"]), _p(s["env"]),
+                          _p(s["cam"]), W, H, spp, max_depth, rr_start, seed, r0, r1, threads,
+                          _p(out["radiance"]), _p(out["albedo"]), _p(out["normal"]),
+                          _p(out["depth"]), _p(out["counts"]), _p(out["shadow_counts"]))
+    if rc != 0:
+        raise ValueError(f"orc_render failed ({rc})")
+    return out

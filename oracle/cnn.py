@@ -1,0 +1,190 @@
+"""Float64 oracle of the fusion network (forward, backward, loss, Adam).
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
+
+The network fuses a low-resolution/high-spp render (LRHS) with a
+high-resolution/low-spp render (HRLS) and its auxiliary layers into the
+high-resolution image I_SR (problem statement of Sec. 4).  Its architecture
+is the all-high-resolution variant: bilinear x s upsampling of LRHS,
+concatenation with HRLS RGB, albedo and normal (12 channels), a 3x3 conv to
+64 channels + ReLU, 8 residual blocks x + conv(relu(conv(x))), and a 3x3 conv
+to 3 channels added to the upsampled LRHS.  All kernels are 3x3 with 64
+feature channels (Sec. 4, "Implement details").
+
+Parameter layout (flat float array, NPARAMS values): for each of the 18 convs
+in forward order, the weight in [Cout][3][3][Cin] order followed by the bias
+[Cout].
+
+Pins (tests/test_oracle_cnn.py): convolution equals brute-force loops on tiny
+inputs; bilinear upsampling equals torch's interpolate (align_corners=False);
+zero weights give out == up(LRHS) exactly; identity-kernel convs reproduce
+their input; gradients equal central finite differences.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+C_IN = 12
+C_F = 64
+N_BLOCKS = 8
+LAYERS = [(C_IN, C_F)] + [(C_F, C_F)] * (2 * N_BLOCKS) + [(C_F, 3)]
+
+
+def layer_offsets():
+    """[(w_off, b_off, cin, cout)] into the flat parameter array."""
+    offs, o = [], 0
+    for cin, cout in LAYERS:
+        offs.append((o, o + cout * 9 * cin, cin, cout))
+        o += cout * 9 * cin + cout
+    return offs
+
+
+NPARAMS = sum(co * 9 * ci + co for ci, co in LAYERS)
+
+
+def unpack(params):
+    p = np.asarray(params, dtype=np.float64)
+    out = []
+    for wo, bo, ci, co in layer_offsets():
+        out.append((p[wo:bo].reshape(co, 3, 3, ci), p[bo:bo + co]))
+    return out
+
+
+def pack(layers):
+    return np.concatenate([np.concatenate([w.ravel(), b.ravel()]) for w, b in layers])
+
+
+def conv3x3(x, w, b):
+    """NHWC 3x3 convolution, zero padding 1: out[n,y,x,o] = b[o] +
+    sum_{dy,dx,c} in[n, y+dy-1, x+dx-1, c] * w[o, dy, dx, c]."""
+    x = np.asarray(x, dtype=np.float64)
+    N, H, W, _ = x.shape
+    xp = np.pad(x, ((0, 0), (1, 1), (1, 1), (0, 0)))
+    out = np.broadcast_to(b, (N, H, W, w.shape[0])).copy()
+    for dy in range(3):
+        for dx in range(3):
+            out += xp[:, dy:dy + H, dx:dx + W, :] @ w[:, dy, dx, :].T
+    return out
+
+
+def conv3x3_backward(x, w, dout):
+    """Gradients of conv3x3 w.r.t. input, weight and bias."""
+    x = np.asarray(x, dtype=np.float64)
+    N, H, W, _ = x.shape
+    xp = np.pad(x, ((0, 0), (1, 1), (1, 1), (0, 0)))
+    dxp = np.zeros_like(xp)
+    dw = np.zeros_like(w)
+    for dy in range(3):
+        for dx in range(3):
+            win = xp[:, dy:dy + H, dx:dx + W, :]
+            dw[:, dy, dx, :] = np.einsum("nyxo,nyxc->oc", dout, win)
+            dxp[:, dy:dy + H, dx:dx + W, :] += dout @ w[:, dy, dx, :]
+    return dxp[:, 1:-1, 1:-1, :], dw, dout.sum(axis=(0, 1, 2))
+
+
+def _src_index(dst, s, n_in):
+    src = (dst + 0.5) / s - 0.5
+    src = np.maximum(src, 0.0)
+    i0 = np.floor(src).astype(np.int64)
+    i0 = np.minimum(i0, n_in - 1)
+    i1 = np.minimum(i0 + 1, n_in - 1)
+    return i0, i1, src - i0
+
+
+def bilinear_up(x, s):
+    """Bilinear x s upsampling with half-pixel centres, clamped at the edges:
+    src = max(0, (dst + 0.5) / s - 0.5) (align_corners=False semantics)."""
+    x = np.asarray(x, dtype=np.float64)
+    N, h, w, C = x.shape
+    y0, y1, ly = _src_index(np.arange(h * s), s, h)
+    x0, x1, lx = _src_index(np.arange(w * s), s, w)
+    ly = ly[None, :, None, None]
+    lx = lx[None, None, :, None]
+    top = x[:, y0][:, :, x0] * (1 - lx) + x[:, y0][:, :, x1] * lx
+    bot = x[:, y1][:, :, x0] * (1 - lx) + x[:, y1][:, :, x1] * lx
+    return top * (1 - ly) + bot * ly
+
+
+def fusion_input(lrhs, hrls, albedo, normal, s):
+    up = bilinear_up(lrhs, s)
+    return np.concatenate([up, hrls, albedo, normal], axis=-1).astype(np.float64), up
+
+
+def forward(params, lrhs, hrls, albedo, normal, s, keep=False):
+    """I_SR for batched NHWC inputs (LRHS [N,h,w,3]; the rest [N,s*h,s*w,3])."""
+    L = unpack(params)
+    x0, up = fusion_input(lrhs, hrls, albedo, normal, s)
+    acts = {"x0": x0}
+    a = conv3x3(x0, *L[0])
+    acts["pre0"] = a
+    h = np.maximum(a, 0.0)
+    acts["h0"] = h
+    for k in range(N_BLOCKS):
+        a1 = conv3x3(h, *L[1 + 2 * k])
+        r = np.maximum(a1, 0.0)
+        h = h + conv3x3(r, *L[2 + 2 * k])
+        acts[f"a{k}"] = a1
+        acts[f"r{k}"] = r
+        acts[f"h{k + 1}"] = h
+    y = conv3x3(h, *L[-1]) + up
+    return (y, acts) if keep else y
+
+
+def l1log_loss(pred, target):
+    """mean |log1p(max(pred,0)) - log1p(target)| and its gradient w.r.t. pred
+    (subgradient 0 where the difference is 0 or pred < 0)."""
+    pred = np.asarray(pred, dtype=np.float64)
+    target = np.asarray(target, dtype=np.float64)
+    pc = np.maximum(pred, 0.0)
+    d = np.log1p(pc) - np.log1p(target)
+    n = pred.size
+    loss = np.abs(d).sum() / n
+    g = np.sign(d) / (1.0 + pc) / n
+    g = np.where(pred > 0.0, g, 0.0)
+    return loss, g
+
+
+def backward(params, acts, dy):
+    """Gradient of the loss w.r.t. the flat params, given dL/dI_SR."""
+    L = unpack(params)
+    grads = [None] * len(L)
+    h = acts[f"h{N_BLOCKS}"]
+    dh, dw, db = conv3x3_backward(h, L[-1][0], dy)
+    grads[-1] = (dw, db)
+    for k in reversed(range(N_BLOCKS)):
+        r = acts[f"r{k}"]
+        dr, dw2, db2 = conv3x3_backward(r, L[2 + 2 * k][0], dh)
+        grads[2 + 2 * k] = (dw2, db2)
+        da = dr * (acts[f"a{k}"] > 0.0)
+        hin = acts[f"h{k}"]
+        dhin, dw1, db1 = conv3x3_backward(hin, L[1 + 2 * k][0], da)
+        grads[1 + 2 * k] = (dw1, db1)
+        dh = dh + dhin
+    da0 = dh * (acts["pre0"] > 0.0)
+    _, dw0, db0 = conv3x3_backward(acts["x0"], L[0][0], da0)
+    grads[0] = (dw0, db0)
+    return pack(grads)
+
+
+def loss_and_grad(params, lrhs, hrls, albedo, normal, target, s):
+    y, acts = forward(params, lrhs, hrls, albedo, normal, s, keep=True)
+    loss, dy = l1log_loss(y, target)
+    return loss, backward(params, acts, dy)
+
+
+def adam(params, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One bias-corrected Adam update (Kingma & Ba 2015); step counts from 1."""
+    m = beta1 * m + (1 - beta1) * grad
+    v = beta2 * v + (1 - beta2) * grad * grad
+    mh = m / (1 - beta1 ** step)
+    vh = v / (1 - beta2 ** step)
+    return params - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+def kaiming(seed: int):
+    """Kaiming-normal weights (std sqrt(2 / (9 Cin))), zero biases."""
+    rng = np.random.default_rng(np.random.SeedSequence([0x6B61696D, int(seed)]))
+    layers = []
+    for ci, co in LAYERS:
+        layers.append((rng.normal(0, np.sqrt(2.0 / (9 * ci)), (co, 3, 3, ci)), np.zeros(co)))
+    return pack(layers)

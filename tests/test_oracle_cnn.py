@@ -1,0 +1,138 @@
+"""Oracle pins for the fusion network: convolution by brute force, bilinear
+upsampling by torch, special cases, finite-difference gradients, Adam."""
+import numpy as np
+import pytest
+
+from oracle import cnn
+
+
+def test_param_count():
+    assert cnn.NPARAMS == 12 * 9 * 64 + 64 + 16 * (64 * 9 * 64 + 64) + 64 * 9 * 3 + 3
+    offs = cnn.layer_offsets()
+    assert len(offs) == 18 and offs[-1][1] + 3 == cnn.NPARAMS
+
+
+def test_conv_equals_brute_force_loops():
+    rng = np.random.default_rng(0)
+    x = rng.normal(size=(2, 5, 4, 3))
+    w = rng.normal(size=(2, 3, 3, 3))
+    b = rng.normal(size=2)
+    got = cnn.conv3x3(x, w, b)
+    N, H, W, C = x.shape
+    want = np.zeros((N, H, W, 2))
+    for n in range(N):
+        for y in range(H):
+            for xx in range(W):
+                for o in range(2):
+                    acc = b[o]
+                    for dy in range(3):
+                        for dx in range(3):
+                            yy, xs = y + dy - 1, xx + dx - 1
+                            if 0 <= yy < H and 0 <= xs < W:
+                                for c in range(C):
+                                    acc += x[n, yy, xs, c] * w[o, dy, dx, c]
+                    want[n, y, xx, o] = acc
+    assert np.allclose(got, want, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("s", [2, 4])
+def test_bilinear_matches_torch(s):
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(s)
+    x = rng.uniform(0, 3, (2, 5, 7, 3))
+    got = cnn.bilinear_up(x, s)
+    t = torch.nn.functional.interpolate(torch.from_numpy(x).permute(0, 3, 1, 2), scale_factor=s,
+                                        mode="bilinear", align_corners=False)
+    assert np.allclose(got, t.permute(0, 2, 3, 1).numpy(), rtol=0, atol=1e-12)
+
+
+def _inputs(rng, N=1, h=4, w=4, s=2):
+    lr = rng.uniform(0, 2, (N, h, w, 3))
+    hr = rng.uniform(0, 2, (N, h * s, w * s, 3))
+    alb = rng.uniform(0, 1, (N, h * s, w * s, 3))
+    nrm = rng.uniform(-1, 1, (N, h * s, w * s, 3))
+    return lr, hr, alb, nrm
+
+
+def test_zero_weights_give_upsampled_lrhs():
+    rng = np.random.default_rng(1)
+    lr, hr, alb, nrm = _inputs(rng)
+    y = cnn.forward(np.zeros(cnn.NPARAMS), lr, hr, alb, nrm, 2)
+    assert np.array_equal(y, cnn.bilinear_up(lr, 2))
+
+
+def test_identity_kernel_reproduces_input():
+    rng = np.random.default_rng(2)
+    x = rng.normal(size=(1, 6, 5, 4))
+    w = np.zeros((4, 3, 3, 4))
+    for c in range(4):
+        w[c, 1, 1, c] = 1.0
+    assert np.array_equal(cnn.conv3x3(x, w, np.zeros(4)), x)
+
+
+def test_residual_structure_with_identity_layers():
+    # conv_in = identity on the first 12 channels, every block's second conv 0,
+    # conv_out reads back channels 3..5 (HRLS): y = up(LRHS) + relu(HRLS) = up + HRLS
+    rng = np.random.default_rng(3)
+    lr, hr, alb, nrm = _inputs(rng)
+    L = [(np.zeros((co, 3, 3, ci)), np.zeros(co)) for ci, co in cnn.LAYERS]
+    for c in range(12):
+        L[0][0][c, 1, 1, c] = 1.0
+    for k in range(3):
+        L[-1][0][k, 1, 1, 3 + k] = 1.0
+    y = cnn.forward(cnn.pack(L), lr, hr, alb, nrm, 2)
+    assert np.allclose(y, cnn.bilinear_up(lr, 2) + hr, rtol=0, atol=1e-14)
+
+
+def test_loss_gradient_matches_finite_differences():
+    rng = np.random.default_rng(4)
+    pred = rng.uniform(-0.5, 3, (1, 3, 3, 3))
+    tgt = rng.uniform(0, 3, (1, 3, 3, 3))
+    _, g = cnn.l1log_loss(pred, tgt)
+    h = 1e-7
+    for idx in np.ndindex(pred.shape):
+        if abs(pred[idx]) < 1e-3:
+            continue
+        p1, p0 = pred.copy(), pred.copy()
+        p1[idx] += h
+        p0[idx] -= h
+        fd = (cnn.l1log_loss(p1, tgt)[0] - cnn.l1log_loss(p0, tgt)[0]) / (2 * h)
+        assert abs(fd - g[idx]) < 1e-7
+
+
+def test_network_gradient_matches_finite_differences():
+    rng = np.random.default_rng(5)
+    lr, hr, alb, nrm = _inputs(rng, N=1, h=4, w=4, s=2)
+    tgt = rng.uniform(0, 2, hr.shape)
+    params = cnn.kaiming(0) * 0.5 + rng.normal(0, 0.01, cnn.NPARAMS)
+    loss, g = cnn.loss_and_grad(params, lr, hr, alb, nrm, tgt, 2)
+    h = 1e-6
+    offs = cnn.layer_offsets()
+    picks = []
+    for li in (0, 1, 2, 9, 16, 17):
+        wo, bo, ci, co = offs[li]
+        picks += list(rng.integers(wo, bo, 4)) + [bo]
+    for i in picks:
+        p1, p0 = params.copy(), params.copy()
+        p1[i] += h
+        p0[i] -= h
+        fd = (cnn.loss_and_grad(p1, lr, hr, alb, nrm, tgt, 2)[0]
+              - cnn.loss_and_grad(p0, lr, hr, alb, nrm, tgt, 2)[0]) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1e-3, abs(g[i])) + 1e-9, (i, fd, g[i])
+
+
+def test_adam_first_step_closed_form():
+    # with zero moments, step 1 moves every parameter by lr * g / (|g| + eps)
+    rng = np.random.default_rng(6)
+    p = rng.normal(size=100)
+    g = rng.normal(size=100)
+    p1, m, v = cnn.adam(p, g, np.zeros(100), np.zeros(100), 1, 1e-3)
+    assert np.allclose(p1, p - 1e-3 * g / (np.abs(g) + 1e-8), rtol=0, atol=1e-15)
+    assert np.allclose(m, 0.1 * g) and np.allclose(v, 0.001 * g * g)
+
+
+def test_kaiming_statistics():
+    p = cnn.unpack(cnn.kaiming(0))
+    w = p[1][0]
+    assert abs(w.std() - np.sqrt(2 / 576)) < 0.01 * np.sqrt(2 / 576) * 5
+    assert all((b == 0).all() for _, b in p)

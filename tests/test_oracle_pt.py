@@ -1,0 +1,114 @@
+"""Oracle pins for the path tracer: closed forms of light transport,
+unbiasedness, error decay, and the structure of the estimator."""
+import numpy as np
+import pytest
+
+from synth import scenes
+
+
+@pytest.mark.parametrize("D", [1, 2, 3, 6])
+def test_white_furnace_closed_form(orc, D):
+    # inside a closed emissive Lambertian sphere every path returns
+    # Le * sum_{k=0..D} rho^k exactly (cosine sampling: f cos / pdf = rho)
+    Le, rho = 1.5, 0.6
+    r = orc.render(scenes.furnace_sphere(Le, rho), 12, 10, 3, D, seed=11)
+    want = Le * sum(rho**k for k in range(D + 1))
+    assert np.allclose(r["radiance"], want, rtol=2e-6, atol=0)
+    assert (r["counts"] == 12 * 10 * 3).all()
+    assert (r["shadow_counts"] == 0).all()     # no lights to sample
+
+
+def test_white_furnace_with_roulette_is_unbiased(orc):
+    Le, rho, D = 1.0, 0.7, 8
+    r = orc.render(scenes.furnace_sphere(Le, rho), 32, 32, 32, D, rr_start=1, seed=5)
+    want = Le * sum(rho**k for k in range(D + 1))
+    x = r["radiance"].reshape(-1, 3)[:, 0].astype(np.float64)
+    sem = x.std(ddof=1) / np.sqrt(len(x))
+    assert abs(x.mean() - want) < 4 * sem
+    assert sem > 0   # roulette does add variance
+    c = r["counts"].astype(np.int64)
+    assert (np.diff(c) <= 0).all() and c[-1] < c[1]
+
+
+@pytest.mark.parametrize("D", [1, 2, 5])
+def test_diffuse_plane_under_uniform_sky(orc, D):
+    # NEE of the sky and BSDF sampling have equal (cosine) pdfs, so both MIS
+    # weights are 1/2 and every path returns rho * L_sky
+    rho, Lsky = 0.6, 2.0
+    r = orc.render(scenes.sky_plane(rho, Lsky), 16, 16, 4, D, seed=2)
+    assert np.allclose(r["radiance"], rho * Lsky, rtol=2e-6, atol=0)
+    assert np.allclose(r["albedo"], rho) and np.allclose(r["normal"], [0, 1, 0])
+
+
+def test_depth_zero_is_emission_only(orc):
+    r = orc.render(scenes.cornell_box(sphere_subdiv=1), 16, 16, 4, 0, seed=0)
+    rad = r["radiance"]
+    # each sample returns 0 or Le = 15 (light seen directly): pixel = 15 k / 4
+    assert set(np.unique(rad)) <= {15.0 * k / 4 for k in range(5)} and (rad == 15.0).any()
+
+
+def test_error_decays_as_inverse_sqrt_spp(orc):
+    # furnace with Russian roulette: unbiased, finite variance, exact reference
+    Le, rho, D = 1.0, 0.7, 8
+    sc = scenes.furnace_sphere(Le, rho)
+    ref = Le * sum(rho**k for k in range(D + 1))
+    spps = [4, 16, 64, 256]
+    rmse = []
+    for spp in spps:
+        errs = [np.mean((orc.render(sc, 16, 16, spp, D, rr_start=1, seed=s)["radiance"] - ref) ** 2)
+                for s in range(3)]
+        rmse.append(np.sqrt(np.mean(errs)))
+    slope = np.polyfit(np.log(spps), np.log(rmse), 1)[0]
+    assert -0.55 < slope < -0.45, (slope, rmse)
+
+
+def test_low_res_render_is_box_average_of_high_res(orc):
+    # an LR pixel jitters over its whole footprint, so in expectation it is the
+    # mean of the s x s HR pixels it covers (same camera frustum)
+    sc = scenes.cornell_box(sphere_subdiv=2)
+    lr = orc.render(sc, 8, 8, 2048, 3, seed=3)["radiance"].astype(np.float64)
+    hr = orc.render(sc, 16, 16, 512, 3, seed=4)["radiance"].astype(np.float64)
+    hr_down = hr.reshape(8, 2, 8, 2, 3).mean(axis=(1, 3))
+    rel = np.abs(lr - hr_down).mean() / np.abs(hr_down).mean()
+    assert rel < 0.05, rel
+
+
+def test_aux_buffers_on_axis_aligned_walls(orc):
+    sc = scenes.cornell_box(sphere_subdiv=1)
+    W = H = 32
+    r = orc.render(sc, W, H, 4, 2, seed=0)
+    # centre pixel sees the back wall (z = -1): white albedo, normal +z
+    c = r["albedo"][H // 2, W // 2]
+    assert np.array_equal(c, np.float32([0.75, 0.75, 0.75]))
+    assert np.array_equal(r["normal"][H // 2, W // 2], np.float32([0, 0, 1]))
+    d = r["depth"][H // 2, W // 2]
+    assert 4.39 < d < 4.45     # eye at z = 3.4, wall at z = -1, near-axial ray
+    # bottom-centre pixel sees the floor: normal +y
+    assert np.array_equal(r["normal"][H - 1, W // 2], np.float32([0, 1, 0]))
+
+
+def test_rows_and_threads_do_not_change_results(orc):
+    sc = scenes.cornell_box(sphere_subdiv=1)
+    full = orc.render(sc, 16, 16, 4, 3, seed=9, threads=4)
+    one = orc.render(sc, 16, 16, 4, 3, seed=9, threads=1)
+    part = orc.render(sc, 16, 16, 4, 3, seed=9, rows=(5, 9), threads=2)
+    assert np.array_equal(full["radiance"], one["radiance"])
+    assert np.array_equal(full["radiance"][5:9], part["radiance"])
+    assert np.array_equal(full["counts"], one["counts"])
+
+
+def test_seed_changes_estimate(orc):
+    sc = scenes.cornell_box(sphere_subdiv=1)
+    a = orc.render(sc, 8, 8, 2, 3, seed=1)["radiance"]
+    b = orc.render(sc, 8, 8, 2, 3, seed=2)["radiance"]
+    assert not np.array_equal(a, b)
+
+
+def test_procedural_scene_size_and_value_range(orc):
+    sc = scenes.procedural(0)
+    assert len(sc["V"]) == 200962 + 6
+    assert len(sc["lights"]) == 3
+    r = orc.render(sc, 32, 32, 4, 4, rr_start=3, seed=0)
+    rad = r["radiance"]
+    assert np.isfinite(rad).all() and (rad >= 0).all()
+    assert (rad <= 10).mean() > 0.95    # linear HDR mostly in [0, 10] (Sec. 3.2)
