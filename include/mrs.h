@@ -1,0 +1,143 @@
+/*
+ * mrs.h -- C ABI of the multi-resolution sampling renderer for GB300 (sm_103a).
+ *
+ * The method (Hou et al., "Fast Monte Carlo Rendering via Multi-Resolution
+ * Sampling", Sec. 1 and Sec. 4) renders the same view twice -- a
+ * low-resolution image at a high sample count (LRHS) and a high-resolution
+ * image at a low sample count (HRLS, with albedo / normal / depth layers,
+ * Sec. 3.2 and Sec. 4) -- and fuses them with a convolutional network into the
+ * high-resolution estimate I_SR (problem statement of Sec. 4).
+ *
+ * Conventions for every entry point:
+ *  - Image pointers are DEVICE pointers owned by the caller, float32, NHWC,
+ *    C-contiguous ([N][H][W][C]; N = 1 where no batch argument exists).
+ *  - Scene and parameter arrays passed by HOST pointer are copied in before
+ *    the call returns; the caller may free them afterwards.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *    enqueued asynchronously unless the entry point says it synchronises.
+ *  - Arguments are validated before anything is launched; on an invalid
+ *    argument the call returns MRS_ERR_ARG and has no effect.  CUDA errors are
+ *    mapped to MRS_ERR_CUDA (the CUDA error string is kept for
+ *    mrs_last_error()).  No entry point aborts the process.
+ *  - Handles (mrs_scene, mrs_net) own all device memory they allocate; it is
+ *    released by the matching mrs_*_free call.  A handle may be used from one
+ *    stream at a time.
+ *  - There is no CPU fallback: without a CUDA device every call that computes
+ *    returns MRS_ERR_CUDA.
+ */
+#ifndef MRS_H
+#define MRS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t mrs_status;
+#define MRS_OK 0
+#define MRS_ERR_ARG (-1)       /* invalid argument (null pointer, size, range) */
+#define MRS_ERR_OOM (-2)       /* device allocation failed */
+#define MRS_ERR_CUDA (-3)      /* a CUDA runtime/driver call failed */
+#define MRS_ERR_TIMEOUT (-4)   /* a bounded device-side wait gave up */
+#define MRS_ERR_CAPACITY (-5)  /* a size exceeds a documented capacity */
+#define MRS_ERR_STATE (-6)     /* handle used in the wrong state */
+
+typedef struct mrs_scene_s* mrs_scene;
+typedef struct mrs_net_s* mrs_net;
+
+/* Human-readable name of a status code (static string). */
+const char* mrs_status_string(mrs_status s);
+/* Last error detail recorded by this thread (static per-thread buffer). */
+const char* mrs_last_error(void);
+
+/* ------------------------------------------------------------------------
+ * Scene + LBVH.  The renderer that produces LRHS and HRLS (Sec. 1, Sec. 3.2)
+ * needs a ray-casting structure; the paper renders with Blender Cycles and
+ * does not specify one, so this library builds a linear BVH on the GPU:
+ * 30-bit Morton codes of triangle centroids (10 bits per axis, x highest) in
+ * the centroid bounding box, a stable radix sort of (code, triangle index),
+ * the binary radix tree of Karras (HPG 2012) over the 64-bit keys
+ * code << 32 | index, and a bottom-up refit of the boxes.
+ *
+ * V          host, float [n_tris][3][3]   triangle vertices
+ * tri_mat    host, int32 [n_tris]         material index (0 <= m < n_mats)
+ * tri_light  host, int32 [n_tris]         light index (0 <= l < n_lights) or -1
+ * mats       host, float [n_mats][8]      type (0 Lambert, 1 GGX), albedo rgb,
+ *                                         GGX alpha, emitted radiance rgb
+ *                                         (one-sided, along cross(v1-v0, v2-v0))
+ * lights     host, float [n_lights][12]   quad lights p0, e1, e2, Le (may be
+ *                                         NULL when n_lights == 0)
+ * env        host, float [3]              constant environment radiance
+ * cam        host, float [12]             eye, forward, right*tan(fov/2)*aspect,
+ *                                         up*tan(fov/2)
+ * n_tris may be 0 (every ray misses).  The LBVH is built on `stream` before
+ * the call returns (the call synchronises `stream`).
+ * ------------------------------------------------------------------------ */
+mrs_status mrs_build_scene(const float* V, int32_t n_tris, const int32_t* tri_mat,
+                           const int32_t* tri_light, const float* mats, int32_t n_mats,
+                           const float* lights, int32_t n_lights, const float* env,
+                           const float* cam, void* stream, mrs_scene* out);
+
+/* Re-run the GPU LBVH build (Morton codes, sort, radix tree, refit) over the
+ * scene's resident triangles, asynchronously on `stream`. */
+mrs_status mrs_scene_rebuild(mrs_scene scene, void* stream);
+
+mrs_status mrs_free_scene(mrs_scene scene);
+
+/* Copy the LBVH to caller DEVICE buffers (any may be NULL):
+ * morton [n] (input order), order [n] (sorted position -> triangle index),
+ * left/right [n-1] (child id: < n-1 internal node, >= n-1 leaf n-1+position),
+ * box [(2n-1)][6] (lo xyz, hi xyz; internal nodes first, then leaves). */
+mrs_status mrs_scene_export_bvh(mrs_scene scene, uint32_t* morton, int32_t* order,
+                                int32_t* left, int32_t* right, float* box, void* stream);
+
+/* Closest hit of n_rays rays through the LBVH: orig/dir device float [n][3];
+ * prim device int32 [n] (triangle index, -1 on miss), t device float [n]
+ * (-1 on miss).  Ties in t go to the smaller triangle index. */
+mrs_status mrs_cast(mrs_scene scene, const float* orig, const float* dir, int32_t n_rays,
+                    int32_t* prim, float* t, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Monte Carlo path tracing (Sec. 1: the LRHS and HRLS renders; Sec. 3.2:
+ * auxiliary render layers).  Unidirectional path tracing with next-event
+ * estimation to the quad lights and the environment, power-heuristic MIS,
+ * Lambert and GGX (visible-normal sampling, Smith height-correlated masking)
+ * materials, Russian roulette from bounce rr_start on (p = min(0.95, max
+ * throughput channel)).  max_depth is the number of scattering events
+ * (0 = emission only).  Random numbers: Philox4x32-10 with counter
+ * (pixel, sample, bounce, group) and key (seed lo, seed hi); group 0 gives
+ * BSDF u1, u2, light u, v; group 1 light pick, roulette, pixel jitter x, y.
+ *
+ * Per pixel, the per-sample radiance is summed in sample order with Kahan
+ * compensation in float32 and divided by spp.  Aux layers are the first-hit
+ * albedo, the normal facing the camera, and the hit distance (0 on a miss),
+ * averaged over samples.  An image at 1/s resolution through the same camera
+ * covers the same frustum: each of its pixels jitters over its whole
+ * footprint (the LRHS render).
+ *
+ * radiance device float [H][W][3] (required); albedo, normal [H][W][3] and
+ * depth [H][W] device (may be NULL); counts / shadow_counts device uint64
+ * [max_depth+1] (may be NULL): extension / shadow rays cast at each bounce.
+ * rr_start < 0 disables Russian roulette.  Limits: W, H in [1, 16384],
+ * spp in [1, 65536], max_depth in [0, 32].  Allocates its path-state arena
+ * inside the scene handle on first use (grown on demand).
+ * ------------------------------------------------------------------------ */
+mrs_status mrs_render(mrs_scene scene, int32_t W, int32_t H, int32_t spp, int32_t max_depth,
+                      int32_t rr_start, uint64_t seed, float* radiance, float* albedo,
+                      float* normal, float* depth, uint64_t* counts, uint64_t* shadow_counts,
+                      void* stream);
+
+/* Paths per wave for subsequent mrs_render calls on this scene (rounded to
+ * whole samples of the image; default 16M paths).  For tests and tuning. */
+mrs_status mrs_scene_set_wave(mrs_scene scene, int64_t max_paths_per_wave);
+
+/* The 8 Philox uniforms of each (pixel, sample, bounce) triple given in
+ * `triples` (device uint32 [n][3]) for key = seed: out device float [n][8]. */
+mrs_status mrs_philox_uniforms(const uint32_t* triples, int32_t n, uint64_t seed, float* out,
+                               void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MRS_H */

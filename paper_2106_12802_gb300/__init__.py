@@ -1,0 +1,8 @@
+"""GB300-native multi-resolution sampling renderer (Hou et al., arXiv 2106.12802).
+
+The compute path is libmrs.so (hand-written CUDA for sm_103a) behind the C ABI
+in include/mrs.h; this package is a thin binding over it.  PyTorch is used for
+device memory and streams only.
+"""
+from ._lib import MrsError, library_path, load  # noqa: F401
+from .render import Scene, philox_uniforms, render  # noqa: F401

@@ -1,0 +1,74 @@
+"""ctypes loader for libmrs.so and the C-ABI signatures of include/mrs.h.
+
+Argument marshalling only.  If the library is missing or fails to load, every
+call raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+P = ctypes.c_void_p
+I32 = ctypes.c_int32
+I64 = ctypes.c_int64
+U64 = ctypes.c_uint64
+F32 = ctypes.c_float
+F64 = ctypes.c_double
+
+# name -> argtypes (restype is always int32 mrs_status unless listed in _RES)
+SIGS = {
+    "mrs_build_scene": [P, I32, P, P, P, I32, P, I32, P, P, P, P],
+    "mrs_scene_rebuild": [P, P],
+    "mrs_free_scene": [P],
+    "mrs_scene_export_bvh": [P, P, P, P, P, P, P],
+    "mrs_cast": [P, P, P, I32, P, P, P],
+    "mrs_render": [P, I32, I32, I32, I32, I32, U64, P, P, P, P, P, P, P],
+    "mrs_scene_set_wave": [P, I64],
+    "mrs_philox_uniforms": [P, I32, U64, P, P],
+    "mrs_status_string": [I32],
+    "mrs_last_error": [],
+}
+_RES = {"mrs_status_string": ctypes.c_char_p, "mrs_last_error": ctypes.c_char_p}
+
+
+class MrsError(RuntimeError):
+    def __init__(self, fn, status, detail):
+        super().__init__(f"{fn} failed: status {status}: {detail}")
+        self.status = status
+
+
+def library_path() -> str:
+    return _build.SO
+
+
+def load(build_if_missing: bool = True):
+    """Load libmrs.so (building it first if it is missing and nvcc exists)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_build.SO):
+                if not build_if_missing:
+                    raise RuntimeError(f"CUDA library not built: {_build.SO}")
+                _build.build()
+            L = ctypes.CDLL(_build.SO)
+            for name, args in SIGS.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = _RES.get(name, I32)
+            _lib = L
+    return _lib
+
+
+def call(name, *args):
+    L = load()
+    st = getattr(L, name)(*args)
+    if st != 0:
+        detail = (L.mrs_last_error() or b"").decode(errors="replace")
+        raise MrsError(name, st, detail)
+    return st

@@ -1,0 +1,460 @@
+// LBVH construction on the GPU: centroid bounds, 30-bit Morton codes, a
+// stable LSD radix sort of (code, triangle index), the binary radix tree of
+// Karras (HPG 2012) and a bottom-up box refit that also writes the traversal
+// node layout (both child boxes + child ids in one 64-byte node).
+//
+// Compiled with --fmad=false: the Morton quantisation must round exactly like
+// the oracle's ((v0 + v1) + v2) * (1/3), (c - lo) * (1024 / extent).
+#include <stdarg.h>
+#include <string.h>
+
+#include "common.cuh"
+
+namespace mrs {
+
+static thread_local char g_err[512];
+void set_error(const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+const char* last_error() { return g_err; }
+
+namespace {
+
+constexpr int kBlock = 256;
+constexpr int kSortItems = 8;                 // keys per thread per sort tile
+constexpr int kTile = kBlock * kSortItems;    // 2048 keys per tile
+
+__device__ __forceinline__ float centroid(const float* V, int i, int a)
+{
+    const float* p = V + (size_t)i * 9;
+    return ((p[a] + p[3 + a]) + p[6 + a]) * 0.333333343267f;
+}
+
+// per-block min/max of centroids -> part[block][6]
+__global__ void k_bounds_partial(const float* __restrict__ V, int n, float* __restrict__ part)
+{
+    __shared__ float s[6][kBlock];
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock)
+        for (int a = 0; a < 3; ++a) {
+            float c = centroid(V, i, a);
+            lo[a] = fminf(lo[a], c);
+            hi[a] = fmaxf(hi[a], c);
+        }
+    for (int a = 0; a < 3; ++a) { s[a][threadIdx.x] = lo[a]; s[3 + a][threadIdx.x] = hi[a]; }
+    __syncthreads();
+    for (int w = kBlock / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int a = 0; a < 3; ++a) {
+                s[a][threadIdx.x] = fminf(s[a][threadIdx.x], s[a][threadIdx.x + w]);
+                s[3 + a][threadIdx.x] = fmaxf(s[3 + a][threadIdx.x], s[3 + a][threadIdx.x + w]);
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x < 6) part[blockIdx.x * 6 + threadIdx.x] = s[threadIdx.x][0];
+}
+
+// reduce the partials (one block) and emit Morton codes (grid-stride)
+__global__ void k_morton(const float* __restrict__ V, int n, const float* __restrict__ part,
+                         int nparts, uint32_t* __restrict__ codes, uint32_t* __restrict__ keys,
+                         int* __restrict__ vals)
+{
+    __shared__ float lo[3], sc[3];
+    if (threadIdx.x < 3) {
+        float l = INFINITY, h = -INFINITY;
+        for (int b = 0; b < nparts; ++b) {
+            l = fminf(l, part[b * 6 + threadIdx.x]);
+            h = fmaxf(h, part[b * 6 + 3 + threadIdx.x]);
+        }
+        float ext = h - l;
+        lo[threadIdx.x] = l;
+        sc[threadIdx.x] = ext > 0.0f ? 1024.0f / ext : 0.0f;
+    }
+    __syncthreads();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        uint32_t q[3];
+        for (int a = 0; a < 3; ++a) {
+            float f = (centroid(V, i, a) - lo[a]) * sc[a];
+            if (!(f > 0.0f)) f = 0.0f;
+            uint32_t u = (uint32_t)f;
+            q[a] = u > 1023u ? 1023u : u;
+        }
+        uint32_t code = 0;
+        for (int b = 0; b < 10; ++b)
+            code |= (((q[0] >> b) & 1u) << (3 * b + 2)) | (((q[1] >> b) & 1u) << (3 * b + 1)) |
+                    (((q[2] >> b) & 1u) << (3 * b));
+        codes[i] = code;
+        keys[i] = code;
+        vals[i] = i;
+    }
+}
+
+// ---- stable LSD radix sort, 8-bit digits ---------------------------------
+__global__ void k_sort_hist(const uint32_t* __restrict__ keys, int n, int shift,
+                            uint32_t* __restrict__ counts, int ntiles)
+{
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    int base = blockIdx.x * kTile;
+    for (int k = 0; k < kSortItems; ++k) {
+        int i = base + k * kBlock + threadIdx.x;
+        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    counts[threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+// exclusive scan of counts[0..m) in place, one block of 1024 threads
+__global__ void k_sort_scan(uint32_t* __restrict__ counts, int m)
+{
+    __shared__ uint32_t s[1024];
+    __shared__ uint32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < m; base += 1024) {
+        int i = base + threadIdx.x;
+        uint32_t v = i < m ? counts[i] : 0u;
+        s[threadIdx.x] = v;
+        __syncthreads();
+        for (int off = 1; off < 1024; off <<= 1) {
+            uint32_t t = threadIdx.x >= off ? s[threadIdx.x - off] : 0u;
+            __syncthreads();
+            s[threadIdx.x] += t;
+            __syncthreads();
+        }
+        if (i < m) counts[i] = carry + s[threadIdx.x] - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += s[1023];
+        __syncthreads();
+    }
+}
+
+// scatter: rank of each key among equal digits = tile offset + keys before it
+// in the tile (round-major, then warp, then lane order == index order)
+__global__ void k_sort_scatter(const uint32_t* __restrict__ kin, const int* __restrict__ vin,
+                               uint32_t* __restrict__ kout, int* __restrict__ vout, int n,
+                               int shift, const uint32_t* __restrict__ offs, int ntiles)
+{
+    __shared__ uint32_t run[256];
+    __shared__ uint32_t wc[kBlock / 32][256];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    run[threadIdx.x] = offs[threadIdx.x * ntiles + blockIdx.x];
+    int base = blockIdx.x * kTile;
+    for (int k = 0; k < kSortItems; ++k) {
+        for (int w = 0; w < kBlock / 32; ++w) wc[w][threadIdx.x] = 0;
+        __syncthreads();
+        int i = base + k * kBlock + threadIdx.x;
+        bool valid = i < n;
+        uint32_t key = valid ? kin[i] : 0u;
+        uint32_t digit = valid ? ((key >> shift) & 255u) : 256u;
+        unsigned peers = __match_any_sync(0xffffffffu, digit);
+        unsigned lt = (1u << lane) - 1u;
+        uint32_t lrank = __popc(peers & lt);
+        if (valid && lrank == 0) wc[warp][digit] = __popc(peers);
+        __syncthreads();
+        // per digit: exclusive prefix over warps; advance the running offset
+        {
+            uint32_t acc = 0;
+            for (int w = 0; w < kBlock / 32; ++w) {
+                uint32_t c = wc[w][threadIdx.x];
+                wc[w][threadIdx.x] = acc;
+                acc += c;
+            }
+            wc[0][threadIdx.x] += 0;   // keep layout; prefix stored in wc
+            __syncthreads();
+            if (valid) {
+                uint32_t pos = run[digit] + wc[warp][digit] + lrank;
+                kout[pos] = key;
+                vout[pos] = vin[i];
+            }
+            __syncthreads();
+            run[threadIdx.x] += acc;
+        }
+        __syncthreads();
+    }
+}
+
+// ---- Karras radix tree ------------------------------------------------------
+__device__ __forceinline__ int delta(const uint32_t* code, const int* order, int n, int i, int j)
+{
+    if (j < 0 || j > n - 1) return -1;
+    uint64_t a = ((uint64_t)code[i] << 32) | (uint32_t)order[i];
+    uint64_t b = ((uint64_t)code[j] << 32) | (uint32_t)order[j];
+    return __clzll(a ^ b);
+}
+
+__global__ void k_karras(const uint32_t* __restrict__ code, const int* __restrict__ order, int n,
+                         int* __restrict__ left, int* __restrict__ right, int* __restrict__ parent)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    int d = (delta(code, order, n, i, i + 1) - delta(code, order, n, i, i - 1)) > 0 ? 1 : -1;
+    int dmin = delta(code, order, n, i, i - d);
+    int lmax = 2;
+    while (delta(code, order, n, i, i + lmax * d) > dmin) lmax <<= 1;
+    int l = 0;
+    for (int t = lmax >> 1; t >= 1; t >>= 1)
+        if (delta(code, order, n, i, i + (l + t) * d) > dmin) l += t;
+    int j = i + l * d;
+    int dnode = delta(code, order, n, i, j);
+    int s = 0, div = 2, t;
+    do {
+        t = (l + div - 1) / div;
+        if (delta(code, order, n, i, i + (s + t) * d) > dnode) s += t;
+        div <<= 1;
+    } while (t > 1);
+    int gamma = i + s * d + (d < 0 ? -1 : 0);
+    int L = (min(i, j) == gamma) ? (n - 1) + gamma : gamma;
+    int R = (max(i, j) == gamma + 1) ? (n - 1) + gamma + 1 : gamma + 1;
+    left[i] = L;
+    right[i] = R;
+    parent[L] = i;
+    parent[R] = i;
+    if (i == 0) parent[0] = -1;
+}
+
+// leaves: sorted triangle records, material/light, leaf boxes
+__global__ void k_leaves(const float* __restrict__ V, const int* __restrict__ tri_mat,
+                         const int* __restrict__ tri_light, const int* __restrict__ order, int n,
+                         float4* __restrict__ tris, int2* __restrict__ tri_ml,
+                         float* __restrict__ box, int* __restrict__ visit)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n - 1) visit[k] = 0;
+    if (k >= n) return;
+    int prim = order[k];
+    const float* p = V + (size_t)prim * 9;
+    float v0x = p[0], v0y = p[1], v0z = p[2];
+    tris[3 * k + 0] = make_float4(v0x, v0y, v0z, __int_as_float(prim));
+    tris[3 * k + 1] = make_float4(p[3] - v0x, p[4] - v0y, p[5] - v0z, 0.0f);
+    tris[3 * k + 2] = make_float4(p[6] - v0x, p[7] - v0y, p[8] - v0z, 0.0f);
+    tri_ml[k] = make_int2(tri_mat[prim], tri_light[prim]);
+    float* b = box + (size_t)(n - 1 + k) * 6;
+    for (int a = 0; a < 3; ++a) {
+        b[a] = fminf(fminf(p[a], p[3 + a]), p[6 + a]);
+        b[3 + a] = fmaxf(fmaxf(p[a], p[3 + a]), p[6 + a]);
+    }
+}
+
+// bottom-up refit: the second child to arrive at a parent computes its box
+// and writes the 64-byte traversal node (both child boxes + child ids)
+__global__ void k_refit(int n, const int* __restrict__ left, const int* __restrict__ right,
+                        const int* __restrict__ parent, float* box, int* visit,
+                        float4* __restrict__ nodes)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int node = parent[(n - 1) + k];
+    while (node >= 0) {
+        __threadfence();
+        if (atomicAdd(&visit[node], 1) == 0) return;   // first arrival: the sibling finishes
+        __threadfence();
+        int l = left[node], r = right[node];
+        const volatile float* bl = box + (size_t)l * 6;
+        const volatile float* br = box + (size_t)r * 6;
+        float L[6], R[6];
+        for (int a = 0; a < 6; ++a) { L[a] = bl[a]; R[a] = br[a]; }
+        float* b = box + (size_t)node * 6;
+        for (int a = 0; a < 3; ++a) {
+            b[a] = fminf(L[a], R[a]);
+            b[3 + a] = fmaxf(L[3 + a], R[3 + a]);
+        }
+        nodes[4 * node + 0] = make_float4(L[0], L[1], L[2], L[3]);
+        nodes[4 * node + 1] = make_float4(L[4], L[5], R[0], R[1]);
+        nodes[4 * node + 2] = make_float4(R[2], R[3], R[4], R[5]);
+        nodes[4 * node + 3] = make_float4(__int_as_float(l), __int_as_float(r), 0.0f, 0.0f);
+        node = parent[node];
+    }
+}
+
+inline int blocks_for(int64_t n, int per) { return (int)((n + per - 1) / per); }
+
+mrs_status build_lbvh(mrs_scene_s* S, cudaStream_t st)
+{
+    int n = S->n;
+    if (n <= 0) return MRS_OK;
+    int nparts = 2 * sm_count();
+    int ntiles = blocks_for(n, kTile);
+    size_t need = sizeof(float) * 6 * nparts + sizeof(uint32_t) * 256 * (size_t)ntiles +
+                  (sizeof(uint32_t) + sizeof(int)) * 2 * (size_t)n + 256;
+    mrs_status s = S->sort_tmp.ensure(need);
+    if (s != MRS_OK) return s;
+    char* p = S->sort_tmp.as<char>();
+    float* part = (float*)p; p += sizeof(float) * 6 * nparts;
+    uint32_t* counts = (uint32_t*)p; p += sizeof(uint32_t) * 256 * (size_t)ntiles;
+    uint32_t* ka = (uint32_t*)p; p += sizeof(uint32_t) * (size_t)n;
+    uint32_t* kb = (uint32_t*)p; p += sizeof(uint32_t) * (size_t)n;
+    int* va = (int*)p; p += sizeof(int) * (size_t)n;
+    int* vb = (int*)p;
+
+    k_bounds_partial<<<nparts, kBlock, 0, st>>>(S->V, n, part);
+    k_morton<<<min(blocks_for(n, kBlock), 8 * sm_count()), kBlock, 0, st>>>(S->V, n, part, nparts,
+                                                                        S->morton, ka, va);
+    // 30-bit codes: digits at bits 0, 8, 16, 24 (4 passes, ends back in ka/va)
+    for (int pass = 0; pass < 4; ++pass) {
+        int shift = pass * 8;
+        uint32_t* kin = (pass & 1) ? kb : ka;
+        uint32_t* kout = (pass & 1) ? ka : kb;
+        int* vin = (pass & 1) ? vb : va;
+        int* vout = (pass & 1) ? va : vb;
+        k_sort_hist<<<ntiles, kBlock, 0, st>>>(kin, n, shift, counts, ntiles);
+        k_sort_scan<<<1, 1024, 0, st>>>(counts, 256 * ntiles);
+        k_sort_scatter<<<ntiles, kBlock, 0, st>>>(kin, vin, kout, vout, n, shift, counts, ntiles);
+    }
+    MRS_CHECK(cudaMemcpyAsync(S->skeys, ka, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st));
+    MRS_CHECK(cudaMemcpyAsync(S->order, va, sizeof(int) * n, cudaMemcpyDeviceToDevice, st));
+    if (n > 1)
+        k_karras<<<blocks_for(n - 1, kBlock), kBlock, 0, st>>>(S->skeys, S->order, n, S->left,
+                                                              S->right, S->parent);
+    k_leaves<<<blocks_for(n, kBlock), kBlock, 0, st>>>(S->V, S->tri_mat, S->tri_light, S->order,
+                                                       n, S->tris, S->tri_ml, S->box, S->visit);
+    if (n > 1)
+        k_refit<<<blocks_for(n, kBlock), kBlock, 0, st>>>(n, S->left, S->right, S->parent, S->box,
+                                                          S->visit, S->nodes);
+    return cuda_status(cudaGetLastError(), "lbvh launch");
+}
+
+void free_scene(mrs_scene_s* S)
+{
+    void* ptrs[] = {S->V, S->tri_mat, S->tri_light, S->mats, S->lights, S->morton, S->skeys,
+                    S->order, S->left, S->right, S->parent, S->visit, S->box, S->nodes,
+                    S->tris, S->tri_ml};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    S->sort_tmp.release();
+    S->arena.release();
+    delete S;
+}
+
+template <class T> mrs_status dalloc(T** p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cuda_status(cudaMalloc((void**)p, sizeof(T) * count), "cudaMalloc");
+}
+
+}  // namespace
+}  // namespace mrs
+
+using namespace mrs;
+
+extern "C" const char* mrs_last_error(void) { return mrs::last_error(); }
+
+extern "C" const char* mrs_status_string(mrs_status s)
+{
+    switch (s) {
+    case MRS_OK: return "ok";
+    case MRS_ERR_ARG: return "invalid argument";
+    case MRS_ERR_OOM: return "out of device memory";
+    case MRS_ERR_CUDA: return "CUDA error";
+    case MRS_ERR_TIMEOUT: return "device wait timed out";
+    case MRS_ERR_CAPACITY: return "capacity exceeded";
+    case MRS_ERR_STATE: return "invalid handle state";
+    default: return "unknown status";
+    }
+}
+
+extern "C" mrs_status mrs_build_scene(const float* V, int32_t n, const int32_t* tri_mat,
+                                      const int32_t* tri_light, const float* mats,
+                                      int32_t n_mats, const float* lights, int32_t n_lights,
+                                      const float* env, const float* cam, void* stream,
+                                      mrs_scene* out)
+{
+    MRS_ARG(out != nullptr, "out is NULL");
+    *out = nullptr;
+    MRS_ARG(n >= 0 && n <= (1 << 28), "n_tris out of range [0, 2^28]");
+    MRS_ARG(n == 0 || (V && tri_mat && tri_light), "triangle arrays are NULL");
+    MRS_ARG(n_mats >= 0 && (n_mats == 0 || mats), "mats");
+    MRS_ARG(n_lights >= 0 && (n_lights == 0 || lights), "lights");
+    MRS_ARG(env && cam, "env/cam NULL");
+    for (int i = 0; i < n; ++i) {
+        MRS_ARG(tri_mat[i] >= 0 && tri_mat[i] < n_mats, "tri_mat index out of range");
+        MRS_ARG(tri_light[i] >= -1 && tri_light[i] < n_lights, "tri_light index out of range");
+    }
+    for (int m = 0; m < n_mats; ++m) {
+        float t = mats[m * 8];
+        MRS_ARG(t == 0.0f || t == 1.0f, "material type must be 0 or 1");
+        MRS_ARG(t == 0.0f || mats[m * 8 + 4] > 0.0f, "GGX alpha must be > 0");
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    mrs_scene_s* S = new mrs_scene_s();
+    S->n = n; S->n_mats = n_mats; S->n_lights = n_lights;
+    memcpy(S->env, env, sizeof(S->env));
+    memcpy(S->cam, cam, sizeof(S->cam));
+    mrs_status s = MRS_OK;
+#define TRY(x) do { if (s == MRS_OK) s = (x); } while (0)
+    TRY(dalloc(&S->V, (size_t)n * 9));
+    TRY(dalloc(&S->tri_mat, n));
+    TRY(dalloc(&S->tri_light, n));
+    TRY(dalloc(&S->mats, (size_t)n_mats * 8));
+    TRY(dalloc(&S->lights, (size_t)n_lights * 12));
+    TRY(dalloc(&S->morton, n));
+    TRY(dalloc(&S->skeys, n));
+    TRY(dalloc(&S->order, n));
+    TRY(dalloc(&S->left, n > 1 ? n - 1 : 1));
+    TRY(dalloc(&S->right, n > 1 ? n - 1 : 1));
+    TRY(dalloc(&S->parent, n > 0 ? 2 * (size_t)n - 1 : 1));
+    TRY(dalloc(&S->visit, n > 1 ? n - 1 : 1));
+    TRY(dalloc(&S->box, n > 0 ? (2 * (size_t)n - 1) * 6 : 6));
+    TRY(dalloc(&S->nodes, n > 1 ? 4 * (size_t)(n - 1) : 4));
+    TRY(dalloc(&S->tris, 3 * (size_t)(n > 0 ? n : 1)));
+    TRY(dalloc(&S->tri_ml, n > 0 ? n : 1));
+    if (n > 0) {
+        TRY(cuda_status(cudaMemcpyAsync(S->V, V, sizeof(float) * 9 * (size_t)n, cudaMemcpyHostToDevice, st), "copy V"));
+        TRY(cuda_status(cudaMemcpyAsync(S->tri_mat, tri_mat, sizeof(int) * n, cudaMemcpyHostToDevice, st), "copy tri_mat"));
+        TRY(cuda_status(cudaMemcpyAsync(S->tri_light, tri_light, sizeof(int) * n, cudaMemcpyHostToDevice, st), "copy tri_light"));
+    }
+    if (n_mats > 0)
+        TRY(cuda_status(cudaMemcpyAsync(S->mats, mats, sizeof(float) * 8 * n_mats, cudaMemcpyHostToDevice, st), "copy mats"));
+    if (n_lights > 0)
+        TRY(cuda_status(cudaMemcpyAsync(S->lights, lights, sizeof(float) * 12 * n_lights, cudaMemcpyHostToDevice, st), "copy lights"));
+    TRY(build_lbvh(S, st));
+    TRY(cuda_status(cudaStreamSynchronize(st), "build_scene sync"));
+#undef TRY
+    if (s != MRS_OK) { free_scene(S); return s; }
+    *out = S;
+    return MRS_OK;
+}
+
+extern "C" mrs_status mrs_scene_rebuild(mrs_scene S, void* stream)
+{
+    MRS_ARG(S != nullptr, "scene is NULL");
+    return build_lbvh(S, (cudaStream_t)stream);
+}
+
+extern "C" mrs_status mrs_free_scene(mrs_scene S)
+{
+    if (!S) return MRS_OK;
+    cudaDeviceSynchronize();
+    free_scene(S);
+    return MRS_OK;
+}
+
+extern "C" mrs_status mrs_scene_export_bvh(mrs_scene S, uint32_t* morton, int32_t* order,
+                                           int32_t* left, int32_t* right, float* box,
+                                           void* stream)
+{
+    MRS_ARG(S != nullptr, "scene is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    int n = S->n;
+    if (n == 0) return MRS_OK;
+    if (morton) MRS_CHECK(cudaMemcpyAsync(morton, S->morton, 4 * (size_t)n, cudaMemcpyDeviceToDevice, st));
+    if (order) MRS_CHECK(cudaMemcpyAsync(order, S->order, 4 * (size_t)n, cudaMemcpyDeviceToDevice, st));
+    if (n > 1 && left) MRS_CHECK(cudaMemcpyAsync(left, S->left, 4 * (size_t)(n - 1), cudaMemcpyDeviceToDevice, st));
+    if (n > 1 && right) MRS_CHECK(cudaMemcpyAsync(right, S->right, 4 * (size_t)(n - 1), cudaMemcpyDeviceToDevice, st));
+    if (box) MRS_CHECK(cudaMemcpyAsync(box, S->box, 24 * (2 * (size_t)n - 1), cudaMemcpyDeviceToDevice, st));
+    return MRS_OK;
+}
+
+extern "C" mrs_status mrs_scene_set_wave(mrs_scene S, int64_t max_paths)
+{
+    MRS_ARG(S != nullptr, "scene is NULL");
+    MRS_ARG(max_paths >= 1 && max_paths <= (int64_t(1) << 30), "wave size out of range [1, 2^30]");
+    S->wave_paths = max_paths;
+    return MRS_OK;
+}

@@ -1,0 +1,118 @@
+// Shared helpers of the CUDA library: status mapping, error detail, the
+// scene handle layout, and the float3 algebra used by the renderer kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include "../../include/mrs.h"
+
+namespace mrs {
+
+void set_error(const char* fmt, ...);
+
+inline mrs_status cuda_status(cudaError_t e, const char* what)
+{
+    if (e == cudaSuccess) return MRS_OK;
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? MRS_ERR_OOM : MRS_ERR_CUDA;
+}
+
+#define MRS_CHECK(call)                                                     \
+    do {                                                                    \
+        mrs_status _s = ::mrs::cuda_status((call), #call);                  \
+        if (_s != MRS_OK) return _s;                                        \
+    } while (0)
+
+#define MRS_ARG(cond, msg)                                                  \
+    do {                                                                    \
+        if (!(cond)) {                                                      \
+            ::mrs::set_error("invalid argument: %s", msg);                  \
+            return MRS_ERR_ARG;                                             \
+        }                                                                   \
+    } while (0)
+
+// Device buffer that grows on demand (never shrinks until freed).
+struct Buf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    mrs_status ensure(size_t need)
+    {
+        if (need <= bytes) return MRS_OK;
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+        if (need == 0) return MRS_OK;
+        cudaError_t e = cudaMalloc(&p, need);
+        if (e != cudaSuccess) { p = nullptr; return cuda_status(e, "cudaMalloc"); }
+        bytes = need;
+        return MRS_OK;
+    }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+inline int sm_count()
+{
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+}  // namespace mrs
+
+// Scene handle: triangle soup, materials, lights, camera and the LBVH, all
+// resident on the device, plus the render arena.
+struct mrs_scene_s {
+    int n = 0, n_mats = 0, n_lights = 0;
+    float env[3] = {0, 0, 0};
+    float cam[12] = {0};
+    // inputs (input order)
+    float* V = nullptr;          // [n][9]
+    int* tri_mat = nullptr;      // [n]
+    int* tri_light = nullptr;    // [n]
+    float* mats = nullptr;       // [n_mats][8]
+    float* lights = nullptr;     // [n_lights][12]
+    // LBVH
+    uint32_t* morton = nullptr;  // [n] input order
+    uint32_t* skeys = nullptr;   // [n] sorted codes
+    int* order = nullptr;        // [n] sorted position -> triangle
+    int* left = nullptr;         // [n-1]
+    int* right = nullptr;        // [n-1]
+    int* parent = nullptr;       // [2n-1]
+    int* visit = nullptr;        // [n-1]
+    float* box = nullptr;        // [2n-1][6]
+    float4* nodes = nullptr;     // [n-1][4]: child boxes + child ids
+    float4* tris = nullptr;      // [n][3]: (v0, prim bits), (e1, 0), (e2, 0) in sorted order
+    int2* tri_ml = nullptr;      // [n]: material, light in sorted order
+    mrs::Buf sort_tmp;           // radix-sort scratch
+    mrs::Buf arena;              // render path state
+    int64_t wave_paths = int64_t(1) << 24;
+};
+
+// Layout of the render arena for a wave of P paths (floats unless noted).
+namespace mrs {
+struct PathSoA {
+    float *ox, *oy, *oz, *dx, *dy, *dz;   // ray
+    float *bx, *by, *bz;                  // throughput
+    float *Lx, *Ly, *Lz;                  // path radiance
+    float *pdf_b, *pdf_e;                 // MIS pdfs of the last BSDF sample
+    float* hit_t;
+    int* hit_id;                          // sorted leaf position or -1
+    float *sdx, *sdy, *sdz, *stmax;       // shadow ray direction and extent
+    float *scx, *scy, *scz;               // unoccluded shadow contribution
+    float *ax, *ay, *az, *nx, *ny, *nz, *dep;   // first-hit aux
+    int *q0, *q1, *qs;                    // queues (cur / next / shadow)
+};
+}  // namespace mrs

@@ -1,0 +1,716 @@
+// Wavefront Monte Carlo path tracer: produces the LRHS / HRLS radiance and
+// the albedo / normal / depth render layers of the multi-resolution sampling
+// method (Sec. 1, Sec. 3.2-3.3).  Per wave of paths:
+//   raygen -> for each bounce: traverse (closest hit) -> shade (emission, NEE
+//   shadow-ray setup, BSDF sampling, roulette, warp-ballot compaction) ->
+//   traverse_shadow (any hit, adds the unoccluded NEE term) -> accumulate
+//   (per-pixel Kahan sums in sample order).
+//
+// Compiled with --fmad=false and IEEE div/sqrt: every float operation is a
+// single correctly rounded binary32 operation in the order written, which is
+// what makes the per-bounce ray counts and the radiance reproducible
+// bit-for-bit by an independent CPU implementation of the same estimator.
+#include "common.cuh"
+
+namespace mrs {
+namespace {
+
+constexpr float PI_F = 3.14159265358979323846f;
+constexpr float INV_PI_F = 0.318309886183790671538f;
+constexpr float RAY_EPS = 1e-4f;
+constexpr float SHADOW_FRAC = 0.999f;
+constexpr float T_INF = 1e30f;
+constexpr int kThreads = 256;
+constexpr int kStack = 64;   // LBVH depth <= 62 (one key bit per level)
+
+// ---- Philox4x32-10 (Salmon et al., SC'11) ----------------------------------
+__device__ __forceinline__ uint4 philox(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) { k.x += 0x9E3779B9u; k.y += 0xBB67AE85u; }
+        uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+__device__ __forceinline__ float u01(uint32_t x) { return (float)(x >> 8) * (1.0f / 16777216.0f); }
+__device__ __forceinline__ float4 draws(uint32_t pixel, uint32_t sample, uint32_t bounce,
+                                        uint32_t group, uint2 key)
+{
+    uint4 o = philox(make_uint4(pixel, sample, bounce, group), key);
+    return make_float4(u01(o.x), u01(o.y), u01(o.z), u01(o.w));
+}
+
+// ---- float3 algebra, left-to-right evaluation -------------------------------
+struct V3 { float x, y, z; };
+__device__ __forceinline__ V3 mk(float x, float y, float z) { return {x, y, z}; }
+__device__ __forceinline__ V3 operator+(V3 a, V3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ V3 operator-(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ V3 operator*(V3 a, float s) { return {a.x * s, a.y * s, a.z * s}; }
+__device__ __forceinline__ float dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ V3 cross(V3 a, V3 b)
+{
+    return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+__device__ __forceinline__ V3 normalize(V3 a) { float inv = 1.0f / sqrtf(dot(a, a)); return a * inv; }
+__device__ __forceinline__ V3 madd(V3 a, V3 b, float s)
+{
+    return {a.x + b.x * s, a.y + b.y * s, a.z + b.z * s};
+}
+__device__ __forceinline__ float maxc(V3 a) { return fmaxf(fmaxf(a.x, a.y), a.z); }
+
+// cos / sin of 2 pi u: quadrant from 4u, Taylor polynomials (Horner) on
+// [0, pi/2) truncated after x^14 / x^13
+__device__ __forceinline__ void sincos2pi(float u, float& c, float& s)
+{
+    float t = u * 4.0f;
+    int q = (int)t;
+    if (q > 3) q = 3;
+    float f = t - (float)q;
+    float x = f * 1.57079632679489661923f;
+    float x2 = x * x;
+    float sp = (float)(1.0 / 6227020800.0);
+    sp = (float)(-1.0 / 39916800.0) + x2 * sp;
+    sp = (float)(1.0 / 362880.0) + x2 * sp;
+    sp = (float)(-1.0 / 5040.0) + x2 * sp;
+    sp = (float)(1.0 / 120.0) + x2 * sp;
+    sp = (float)(-1.0 / 6.0) + x2 * sp;
+    sp = 1.0f + x2 * sp;
+    float sn = x * sp;
+    float cp = (float)(-1.0 / 87178291200.0);
+    cp = (float)(1.0 / 479001600.0) + x2 * cp;
+    cp = (float)(-1.0 / 3628800.0) + x2 * cp;
+    cp = (float)(1.0 / 40320.0) + x2 * cp;
+    cp = (float)(-1.0 / 720.0) + x2 * cp;
+    cp = (float)(1.0 / 24.0) + x2 * cp;
+    cp = -0.5f + x2 * cp;
+    float cs = 1.0f + x2 * cp;
+    if (q == 0) { c = cs; s = sn; }
+    else if (q == 1) { c = -sn; s = cs; }
+    else if (q == 2) { c = -cs; s = -sn; }
+    else { c = sn; s = -cs; }
+}
+
+// ---- scene access -----------------------------------------------------------
+struct SceneView {
+    int n, n_lights;
+    const float4* __restrict__ nodes;
+    const float4* __restrict__ tris;
+    const int2* __restrict__ tri_ml;
+    const float* __restrict__ mats;
+    const float* __restrict__ lights;
+};
+
+// Moller-Trumbore against a sorted triangle record; t in (0, tmax) or -1
+__device__ __forceinline__ float intersect(V3 o, V3 d, const float4* tri, float tmax, int& prim)
+{
+    float4 a = __ldg(tri), b = __ldg(tri + 1), c = __ldg(tri + 2);
+    prim = __float_as_int(a.w);
+    V3 v0 = mk(a.x, a.y, a.z), e1 = mk(b.x, b.y, b.z), e2 = mk(c.x, c.y, c.z);
+    V3 p = cross(d, e2);
+    float det = dot(e1, p);
+    if (det == 0.0f) return -1.0f;
+    float inv = 1.0f / det;
+    V3 s = o - v0;
+    float u = dot(s, p) * inv;
+    if (u < 0.0f || u > 1.0f) return -1.0f;
+    V3 q = cross(s, e1);
+    float v = dot(d, q) * inv;
+    if (v < 0.0f || u + v > 1.0f) return -1.0f;
+    float t = dot(e2, q) * inv;
+    if (!(t > 0.0f) || !(t < tmax)) return -1.0f;
+    return t;
+}
+
+// conservative slab test; returns entry distance or +inf on a miss
+__device__ __forceinline__ float slab(float lx, float ly, float lz, float hx, float hy, float hz,
+                                      V3 o, V3 inv, float tmax)
+{
+    float t0x = (lx - o.x) * inv.x, t1x = (hx - o.x) * inv.x;
+    float t0y = (ly - o.y) * inv.y, t1y = (hy - o.y) * inv.y;
+    float t0z = (lz - o.z) * inv.z, t1z = (hz - o.z) * inv.z;
+    float tn = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fmaxf(fminf(t0z, t1z), 0.0f));
+    float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fminf(fmaxf(t0z, t1z), tmax));
+    return tn <= tf * 1.0000005f ? tn : INFINITY;
+}
+
+// closest hit (ties to the smaller triangle index) or any hit below tmax
+template <bool kAny>
+__device__ int traverse(const SceneView& S, V3 o, V3 d, float tmax, float& t_out)
+{
+    const int n = S.n;
+    int best = -1, best_prim = 0x7fffffff;
+    float bt = tmax;
+    if (n == 0) return -1;
+    if (n == 1) {
+        int prim;
+        float t = intersect(o, d, S.tris, tmax, prim);
+        if (t > 0.0f) { t_out = t; return 0; }
+        return -1;
+    }
+    V3 inv = mk(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
+    int stack[kStack];
+    int sp = 0;
+    int node = 0;
+    while (true) {
+        if (node < n - 1) {
+            const float4* nd = S.nodes + 4 * node;
+            float4 a = __ldg(nd), b = __ldg(nd + 1), c = __ldg(nd + 2), e = __ldg(nd + 3);
+            float t0 = slab(a.x, a.y, a.z, a.w, b.x, b.y, o, inv, bt);
+            float t1 = slab(b.z, b.w, c.x, c.y, c.z, c.w, o, inv, bt);
+            int c0 = __float_as_int(e.x), c1 = __float_as_int(e.y);
+            bool h0 = t0 != INFINITY, h1 = t1 != INFINITY;
+            if (h0 && h1) {
+                int nearc = t0 <= t1 ? c0 : c1, farc = t0 <= t1 ? c1 : c0;
+                if (sp < kStack) stack[sp++] = farc;
+                node = nearc;
+                continue;
+            }
+            if (h0) { node = c0; continue; }
+            if (h1) { node = c1; continue; }
+        } else {
+            int k = node - (n - 1), prim;
+            float t = intersect(o, d, S.tris + 3 * k, kAny ? tmax : T_INF, prim);
+            if (t > 0.0f) {
+                if (kAny) { t_out = t; return k; }
+                if (t < bt || (t == bt && prim < best_prim)) { bt = t; best = k; best_prim = prim; }
+            }
+        }
+        if (sp == 0) break;
+        node = stack[--sp];
+    }
+    if (best >= 0) t_out = bt;
+    return best;
+}
+
+// ---- materials --------------------------------------------------------------
+struct Mat { int type; V3 albedo; float alpha; V3 Le; };
+__device__ __forceinline__ Mat material(const float* mats, int m)
+{
+    const float* p = mats + 8 * m;
+    Mat r;
+    r.type = (int)__ldg(p);
+    r.albedo = mk(__ldg(p + 1), __ldg(p + 2), __ldg(p + 3));
+    r.alpha = __ldg(p + 4);
+    r.Le = mk(__ldg(p + 5), __ldg(p + 6), __ldg(p + 7));
+    return r;
+}
+
+__device__ __forceinline__ void basis(V3 n, V3& t, V3& b)
+{
+    float sign = copysignf(1.0f, n.z);
+    float a = -1.0f / (sign + n.z);
+    float bb = n.x * n.y * a;
+    t = mk(1.0f + sign * n.x * n.x * a, sign * bb, -sign * n.x);
+    b = mk(bb, sign + n.y * n.y * a, -n.y);
+}
+__device__ __forceinline__ V3 to_local(V3 w, V3 t, V3 b, V3 n) { return mk(dot(w, t), dot(w, b), dot(w, n)); }
+__device__ __forceinline__ V3 to_world(V3 w, V3 t, V3 b, V3 n)
+{
+    return mk(t.x * w.x + b.x * w.y + n.x * w.z, t.y * w.x + b.y * w.y + n.y * w.z,
+              t.z * w.x + b.z * w.y + n.z * w.z);
+}
+__device__ __forceinline__ V3 cosine_sample(float u1, float u2)
+{
+    float r = sqrtf(u1), c, s;
+    sincos2pi(u2, c, s);
+    return mk(r * c, r * s, sqrtf(fmaxf(0.0f, 1.0f - u1)));
+}
+__device__ __forceinline__ float ggx_lambda(V3 w, float a2)
+{
+    float tan2 = (w.x * w.x + w.y * w.y) / (w.z * w.z);
+    return (sqrtf(1.0f + a2 * tan2) - 1.0f) * 0.5f;
+}
+__device__ __forceinline__ float ggx_D(float hz, float a2)
+{
+    float den = hz * hz * (a2 - 1.0f) + 1.0f;
+    return a2 / (PI_F * den * den);
+}
+__device__ __forceinline__ V3 schlick(V3 F0, float cosh)
+{
+    float m = fmaxf(0.0f, 1.0f - cosh);
+    float m2 = m * m;
+    float m5 = m2 * m2 * m;
+    return mk(F0.x + (1.0f - F0.x) * m5, F0.y + (1.0f - F0.y) * m5, F0.z + (1.0f - F0.z) * m5);
+}
+__device__ V3 bsdf_eval(const Mat& m, V3 wo, V3 wi, float& pdf)
+{
+    if (m.type == 0) {
+        pdf = wi.z * INV_PI_F;
+        return m.albedo * INV_PI_F;
+    }
+    float a2 = m.alpha * m.alpha;
+    V3 h = normalize(wo + wi);
+    float D = ggx_D(h.z, a2);
+    float lo = ggx_lambda(wo, a2), li = ggx_lambda(wi, a2);
+    float G1 = 1.0f / (1.0f + lo);
+    float G2 = 1.0f / ((1.0f + lo) + li);
+    V3 F = schlick(m.albedo, dot(wo, h));
+    float k = (D * G2) / ((4.0f * wo.z) * wi.z);
+    pdf = (G1 * D) / (4.0f * wo.z);
+    return F * k;
+}
+__device__ bool bsdf_sample(const Mat& m, V3 wo, float u1, float u2, V3& wi, V3& weight, float& pdf)
+{
+    if (m.type == 0) {
+        wi = cosine_sample(u1, u2);
+        if (!(wi.z > 0.0f)) return false;
+        pdf = wi.z * INV_PI_F;
+        weight = m.albedo;
+        return true;
+    }
+    float al = m.alpha, a2 = al * al;
+    V3 Vh = normalize(mk(al * wo.x, al * wo.y, wo.z));
+    float lensq = Vh.x * Vh.x + Vh.y * Vh.y;
+    V3 T1 = mk(1.0f, 0.0f, 0.0f);
+    if (lensq > 0.0f) { float il = 1.0f / sqrtf(lensq); T1 = mk(-Vh.y * il, Vh.x * il, 0.0f); }
+    V3 T2 = cross(Vh, T1);
+    float r = sqrtf(u1), c, s;
+    sincos2pi(u2, c, s);
+    float t1 = r * c, t2 = r * s;
+    float sv = 0.5f * (1.0f + Vh.z);
+    t2 = (1.0f - sv) * sqrtf(1.0f - t1 * t1) + sv * t2;
+    float q = sqrtf(fmaxf(0.0f, 1.0f - t1 * t1 - t2 * t2));
+    V3 Nh = mk(T1.x * t1 + T2.x * t2 + Vh.x * q, T1.y * t1 + T2.y * t2 + Vh.y * q,
+               T1.z * t1 + T2.z * t2 + Vh.z * q);
+    V3 h = normalize(mk(al * Nh.x, al * Nh.y, fmaxf(0.0f, Nh.z)));
+    float k = 2.0f * dot(wo, h);
+    wi = mk(k * h.x - wo.x, k * h.y - wo.y, k * h.z - wo.z);
+    if (!(wi.z > 0.0f)) return false;
+    float lo = ggx_lambda(wo, a2), li = ggx_lambda(wi, a2);
+    float g = (1.0f + lo) / ((1.0f + lo) + li);
+    V3 F = schlick(m.albedo, dot(wo, h));
+    weight = F * g;
+    float D = ggx_D(h.z, a2);
+    pdf = ((1.0f / (1.0f + lo)) * D) / (4.0f * wo.z);
+    return true;
+}
+
+// ---- wave kernels -----------------------------------------------------------
+struct WaveParams {
+    SceneView S;
+    PathSoA P;
+    float env[3];
+    float cam[12];
+    int W, H, max_depth, rr_start;
+    int64_t wh;          // pixels
+    int s0;              // first sample index of the wave
+    int n_paths;         // paths in the wave (= k * wh)
+    uint2 key;
+    uint32_t* cnt;       // [max_depth + 2] extension rays per bounce
+    uint32_t* scnt;      // [max_depth + 1] shadow rays per bounce
+};
+
+__global__ void __launch_bounds__(kThreads) k_raygen(WaveParams w)
+{
+    PathSoA& P = w.P;
+    if (blockIdx.x == 0 && threadIdx.x == 0) w.cnt[0] = (uint32_t)w.n_paths;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < w.n_paths; p += gridDim.x * blockDim.x) {
+        int pix = (int)(p % w.wh);
+        int sample = w.s0 + (int)(p / w.wh);
+        int px = pix % w.W, py = pix / w.W;
+        float4 g1 = draws((uint32_t)pix, (uint32_t)sample, 0u, 1u, w.key);
+        const float* cam = w.cam;
+        float sx = ((float)px + g1.z) / (float)w.W;
+        float sy = ((float)py + g1.w) / (float)w.H;
+        float a = 2.0f * sx - 1.0f, bq = 1.0f - 2.0f * sy;
+        V3 d = normalize(mk(cam[3] + cam[6] * a + cam[9] * bq, cam[4] + cam[7] * a + cam[10] * bq,
+                            cam[5] + cam[8] * a + cam[11] * bq));
+        P.ox[p] = cam[0]; P.oy[p] = cam[1]; P.oz[p] = cam[2];
+        P.dx[p] = d.x; P.dy[p] = d.y; P.dz[p] = d.z;
+        P.bx[p] = 1.0f; P.by[p] = 1.0f; P.bz[p] = 1.0f;
+        P.Lx[p] = 0.0f; P.Ly[p] = 0.0f; P.Lz[p] = 0.0f;
+        P.pdf_b[p] = 0.0f; P.pdf_e[p] = 0.0f;
+        P.ax[p] = 0.0f; P.ay[p] = 0.0f; P.az[p] = 0.0f;
+        P.nx[p] = 0.0f; P.ny[p] = 0.0f; P.nz[p] = 0.0f; P.dep[p] = 0.0f;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_trace(WaveParams w, int b)
+{
+    PathSoA& P = w.P;
+    const int count = (int)*(volatile uint32_t*)&w.cnt[b];
+    const int* q = (b & 1) ? P.q1 : P.q0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        int p = b == 0 ? i : q[i];
+        V3 o = mk(P.ox[p], P.oy[p], P.oz[p]), d = mk(P.dx[p], P.dy[p], P.dz[p]);
+        float t = -1.0f;
+        int k = traverse<false>(w.S, o, d, T_INF, t);
+        P.hit_t[p] = t;
+        P.hit_id[p] = k;
+    }
+}
+
+// warp-aggregated append: returns this lane's slot (valid only where flag)
+__device__ __forceinline__ int warp_append(bool flag, uint32_t* counter)
+{
+    unsigned m = __ballot_sync(0xffffffffu, flag);
+    if (!m) return -1;
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(m) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(counter, (uint32_t)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    return (int)(base + __popc(m & ((1u << lane) - 1u)));
+}
+
+__global__ void __launch_bounds__(kThreads) k_shade(WaveParams w, int b)
+{
+    PathSoA& P = w.P;
+    const SceneView& S = w.S;
+    const int count = (int)*(volatile uint32_t*)&w.cnt[b];
+    const int* q = (b & 1) ? P.q1 : P.q0;
+    int* qn = (b & 1) ? P.q0 : P.q1;
+    const V3 env = mk(w.env[0], w.env[1], w.env[2]);
+    const bool env_on = env.x > 0.0f || env.y > 0.0f || env.z > 0.0f;
+    const int n_choices = S.n_lights + (env_on ? 1 : 0);
+    const float pick = n_choices > 0 ? 1.0f / (float)n_choices : 0.0f;
+    const int stride = gridDim.x * blockDim.x;
+    const int end = (count + 31) & ~31;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < end; i += stride) {
+        bool cont = false, shadow = false;
+        int p = 0;
+        if (i < count) {
+            p = b == 0 ? i : q[i];
+            V3 o = mk(P.ox[p], P.oy[p], P.oz[p]), d = mk(P.dx[p], P.dy[p], P.dz[p]);
+            V3 beta = mk(P.bx[p], P.by[p], P.bz[p]);
+            V3 L = mk(P.Lx[p], P.Ly[p], P.Lz[p]);
+            float pdf_b = P.pdf_b[p], pdf_e = P.pdf_e[p];
+            int k = P.hit_id[p];
+            float t = P.hit_t[p];
+            do {
+                if (k < 0) {
+                    if (env_on) {
+                        float wgt = 1.0f;
+                        if (b > 0 && pdf_e > 0.0f)
+                            wgt = (pdf_b * pdf_b) / (pdf_b * pdf_b + pdf_e * pdf_e);
+                        L = mk(L.x + beta.x * env.x * wgt, L.y + beta.y * env.y * wgt,
+                               L.z + beta.z * env.z * wgt);
+                    }
+                    break;
+                }
+                const float4* tr = S.tris + 3 * k;
+                float4 ta = __ldg(tr), tb = __ldg(tr + 1), tc = __ldg(tr + 2);
+                int2 ml = __ldg(S.tri_ml + k);
+                V3 p3 = madd(o, d, t);
+                V3 ng = normalize(cross(mk(tb.x, tb.y, tb.z), mk(tc.x, tc.y, tc.z)));
+                float cos_o = dot(d, ng);
+                V3 ns = cos_o > 0.0f ? ng * -1.0f : ng;
+                Mat m = material(S.mats, ml.x);
+                if (b == 0) {
+                    P.ax[p] = m.albedo.x; P.ay[p] = m.albedo.y; P.az[p] = m.albedo.z;
+                    P.nx[p] = ns.x; P.ny[p] = ns.y; P.nz[p] = ns.z; P.dep[p] = t;
+                }
+                if ((m.Le.x > 0.0f || m.Le.y > 0.0f || m.Le.z > 0.0f) && cos_o < 0.0f) {
+                    float wgt = 1.0f;
+                    int li = ml.y;
+                    if (b > 0 && li >= 0) {
+                        const float* lq = S.lights + 12 * li;
+                        V3 ln = cross(mk(__ldg(lq + 3), __ldg(lq + 4), __ldg(lq + 5)),
+                                      mk(__ldg(lq + 6), __ldg(lq + 7), __ldg(lq + 8)));
+                        float area = sqrtf(dot(ln, ln));
+                        float pl = pick * (t * t) / (-cos_o * area);
+                        wgt = (pdf_b * pdf_b) / (pdf_b * pdf_b + pl * pl);
+                    }
+                    L = mk(L.x + beta.x * m.Le.x * wgt, L.y + beta.y * m.Le.y * wgt,
+                           L.z + beta.z * m.Le.z * wgt);
+                }
+                if (b == w.max_depth) break;
+                if (!(m.albedo.x > 0.0f || m.albedo.y > 0.0f || m.albedo.z > 0.0f)) break;
+
+                int pix = (int)(p % w.wh);
+                uint32_t sample = (uint32_t)(w.s0 + (int)(p / w.wh));
+                float4 g0 = draws((uint32_t)pix, sample, (uint32_t)b, 0u, w.key);
+                float4 g1 = draws((uint32_t)pix, sample, (uint32_t)b, 1u, w.key);
+                V3 T, B;
+                basis(ns, T, B);
+                V3 wo = to_local(d * -1.0f, T, B, ns);
+                V3 org = madd(p3, ns, RAY_EPS);
+                P.ox[p] = org.x; P.oy[p] = org.y; P.oz[p] = org.z;
+
+                if (n_choices > 0) {
+                    int kl = (int)(g1.x * (float)n_choices);
+                    if (kl > n_choices - 1) kl = n_choices - 1;
+                    if (kl < S.n_lights) {
+                        const float* lq = S.lights + 12 * kl;
+                        V3 p0 = mk(__ldg(lq), __ldg(lq + 1), __ldg(lq + 2));
+                        V3 e1 = mk(__ldg(lq + 3), __ldg(lq + 4), __ldg(lq + 5));
+                        V3 e2 = mk(__ldg(lq + 6), __ldg(lq + 7), __ldg(lq + 8));
+                        V3 Le = mk(__ldg(lq + 9), __ldg(lq + 10), __ldg(lq + 11));
+                        V3 x = madd(madd(p0, e1, g0.z), e2, g0.w);
+                        V3 ln = cross(e1, e2);
+                        float area = sqrtf(dot(ln, ln));
+                        V3 nl = ln * (1.0f / area);
+                        V3 dl = x - org;
+                        float d2 = dot(dl, dl);
+                        float dist = sqrtf(d2);
+                        V3 wi = dl * (1.0f / dist);
+                        float cos_l = -dot(wi, nl), cos_s = dot(wi, ns);
+                        if (cos_l > 0.0f && cos_s > 0.0f) {
+                            float pb;
+                            V3 f = bsdf_eval(m, wo, to_local(wi, T, B, ns), pb);
+                            float pl = pick * d2 / (cos_l * area);
+                            float wgt = (pl * pl) / (pl * pl + pb * pb);
+                            float sc = (cos_s / pl) * wgt;
+                            P.scx[p] = beta.x * f.x * Le.x * sc;
+                            P.scy[p] = beta.y * f.y * Le.y * sc;
+                            P.scz[p] = beta.z * f.z * Le.z * sc;
+                            P.sdx[p] = wi.x; P.sdy[p] = wi.y; P.sdz[p] = wi.z;
+                            P.stmax[p] = dist * SHADOW_FRAC;
+                            shadow = true;
+                        }
+                    } else {
+                        V3 wl = cosine_sample(g0.z, g0.w);
+                        if (wl.z > 0.0f) {
+                            V3 wi = normalize(to_world(wl, T, B, ns));
+                            float pb;
+                            V3 f = bsdf_eval(m, wo, wl, pb);
+                            float pe = pick * wl.z * INV_PI_F;
+                            float wgt = (pe * pe) / (pe * pe + pb * pb);
+                            float sc = (wl.z / pe) * wgt;
+                            P.scx[p] = beta.x * f.x * env.x * sc;
+                            P.scy[p] = beta.y * f.y * env.y * sc;
+                            P.scz[p] = beta.z * f.z * env.z * sc;
+                            P.sdx[p] = wi.x; P.sdy[p] = wi.y; P.sdz[p] = wi.z;
+                            P.stmax[p] = T_INF;
+                            shadow = true;
+                        }
+                    }
+                }
+
+                V3 wl, wt;
+                float pb;
+                if (!bsdf_sample(m, wo, g0.x, g0.y, wl, wt, pb)) break;
+                beta = mk(beta.x * wt.x, beta.y * wt.y, beta.z * wt.z);
+                pdf_b = pb;
+                pdf_e = env_on ? pick * wl.z * INV_PI_F : 0.0f;
+                if (!(maxc(beta) > 0.0f)) break;
+                if (b >= w.rr_start) {
+                    float qq = fminf(0.95f, maxc(beta));
+                    if (g1.y >= qq) break;
+                    beta = mk(beta.x / qq, beta.y / qq, beta.z / qq);
+                }
+                V3 nd = normalize(to_world(wl, T, B, ns));
+                P.dx[p] = nd.x; P.dy[p] = nd.y; P.dz[p] = nd.z;
+                P.bx[p] = beta.x; P.by[p] = beta.y; P.bz[p] = beta.z;
+                P.pdf_b[p] = pdf_b; P.pdf_e[p] = pdf_e;
+                cont = true;
+            } while (0);
+            P.Lx[p] = L.x; P.Ly[p] = L.y; P.Lz[p] = L.z;
+        }
+        int slot = warp_append(cont, &w.cnt[b + 1]);
+        if (cont) qn[slot] = p;
+        int sslot = warp_append(shadow, &w.scnt[b]);
+        if (shadow) P.qs[sslot] = p;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_shadow(WaveParams w, int b)
+{
+    PathSoA& P = w.P;
+    const int count = (int)*(volatile uint32_t*)&w.scnt[b];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        int p = P.qs[i];
+        V3 o = mk(P.ox[p], P.oy[p], P.oz[p]), d = mk(P.sdx[p], P.sdy[p], P.sdz[p]);
+        float t;
+        if (traverse<true>(w.S, o, d, P.stmax[p], t) < 0) {
+            P.Lx[p] = P.Lx[p] + P.scx[p];
+            P.Ly[p] = P.Ly[p] + P.scy[p];
+            P.Lz[p] = P.Lz[p] + P.scz[p];
+        }
+    }
+}
+
+// per pixel: add this wave's samples in sample order (Kahan for radiance)
+__global__ void __launch_bounds__(kThreads) k_accumulate(WaveParams w, float* acc, int k)
+{
+    PathSoA& P = w.P;
+    int64_t wh = w.wh;
+    for (int64_t pix = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; pix < wh;
+         pix += (int64_t)gridDim.x * blockDim.x) {
+        float* a = acc + 13 * pix;
+        float s0 = a[0], s1 = a[1], s2 = a[2], c0 = a[3], c1 = a[4], c2 = a[5];
+        float ax = a[6], ay = a[7], az = a[8], nx = a[9], ny = a[10], nz = a[11], ds = a[12];
+        for (int s = 0; s < k; ++s) {
+            int64_t p = s * wh + pix;
+            float y, t;
+            y = P.Lx[p] - c0; t = s0 + y; c0 = (t - s0) - y; s0 = t;
+            y = P.Ly[p] - c1; t = s1 + y; c1 = (t - s1) - y; s1 = t;
+            y = P.Lz[p] - c2; t = s2 + y; c2 = (t - s2) - y; s2 = t;
+            ax = ax + P.ax[p]; ay = ay + P.ay[p]; az = az + P.az[p];
+            nx = nx + P.nx[p]; ny = ny + P.ny[p]; nz = nz + P.nz[p];
+            ds = ds + P.dep[p];
+        }
+        a[0] = s0; a[1] = s1; a[2] = s2; a[3] = c0; a[4] = c1; a[5] = c2;
+        a[6] = ax; a[7] = ay; a[8] = az; a[9] = nx; a[10] = ny; a[11] = nz; a[12] = ds;
+    }
+}
+
+__global__ void k_counts(const uint32_t* cnt, const uint32_t* scnt, int nb, uint64_t* counts,
+                         uint64_t* shadow_counts)
+{
+    int b = threadIdx.x;
+    if (b >= nb) return;
+    if (counts) counts[b] += cnt[b];
+    if (shadow_counts) shadow_counts[b] += scnt[b];
+}
+
+__global__ void k_resolve(const float* __restrict__ acc, int64_t wh, int spp, float* radiance,
+                          float* albedo, float* normal, float* depth)
+{
+    float fs = (float)spp;
+    for (int64_t pix = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; pix < wh;
+         pix += (int64_t)gridDim.x * blockDim.x) {
+        const float* a = acc + 13 * pix;
+        radiance[3 * pix] = a[0] / fs; radiance[3 * pix + 1] = a[1] / fs; radiance[3 * pix + 2] = a[2] / fs;
+        if (albedo) { albedo[3 * pix] = a[6] / fs; albedo[3 * pix + 1] = a[7] / fs; albedo[3 * pix + 2] = a[8] / fs; }
+        if (normal) { normal[3 * pix] = a[9] / fs; normal[3 * pix + 1] = a[10] / fs; normal[3 * pix + 2] = a[11] / fs; }
+        if (depth) depth[pix] = a[12] / fs;
+    }
+}
+
+__global__ void k_cast(SceneView S, const float* orig, const float* dir, int n, int* prim, float* tout)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        V3 o = mk(orig[3 * i], orig[3 * i + 1], orig[3 * i + 2]);
+        V3 d = mk(dir[3 * i], dir[3 * i + 1], dir[3 * i + 2]);
+        float t = -1.0f;
+        int k = traverse<false>(S, o, d, T_INF, t);
+        if (k >= 0) {
+            prim[i] = __float_as_int(__ldg(S.tris + 3 * k).w);
+            tout[i] = t;
+        } else {
+            prim[i] = -1;
+            tout[i] = -1.0f;
+        }
+    }
+}
+
+__global__ void k_philox(const uint32_t* triples, int n, uint2 key, float* out)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (uint32_t g = 0; g < 2; ++g) {
+        float4 u = draws(triples[3 * i], triples[3 * i + 1], triples[3 * i + 2], g, key);
+        out[8 * i + 4 * g] = u.x; out[8 * i + 4 * g + 1] = u.y;
+        out[8 * i + 4 * g + 2] = u.z; out[8 * i + 4 * g + 3] = u.w;
+    }
+}
+
+SceneView view(const mrs_scene_s* S)
+{
+    return SceneView{S->n, S->n_lights, S->nodes, S->tris, S->tri_ml, S->mats, S->lights};
+}
+
+inline int grid_for(int64_t n)
+{
+    int64_t g = (n + kThreads - 1) / kThreads;
+    int64_t cap = (int64_t)sm_count() * 8;
+    if (g > cap) g = cap;
+    return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+}  // namespace mrs
+
+using namespace mrs;
+
+extern "C" mrs_status mrs_render(mrs_scene S, int32_t W, int32_t H, int32_t spp, int32_t max_depth,
+                                 int32_t rr_start, uint64_t seed, float* radiance, float* albedo,
+                                 float* normal, float* depth, uint64_t* counts,
+                                 uint64_t* shadow_counts, void* stream)
+{
+    MRS_ARG(S != nullptr, "scene is NULL");
+    MRS_ARG(W >= 1 && W <= 16384 && H >= 1 && H <= 16384, "W, H must be in [1, 16384]");
+    MRS_ARG(spp >= 1 && spp <= 65536, "spp must be in [1, 65536]");
+    MRS_ARG(max_depth >= 0 && max_depth <= 32, "max_depth must be in [0, 32]");
+    MRS_ARG(radiance != nullptr, "radiance is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t wh = (int64_t)W * H;
+    int64_t k = S->wave_paths / wh;
+    if (k < 1) k = 1;
+    if (k > spp) k = spp;
+    MRS_ARG(k * wh <= (int64_t(1) << 31) - 1, "wave too large");
+    const int64_t P = k * wh;
+    const int nb = max_depth + 1;
+    // arena: 30 float/int arrays of P + accum 13 * wh + counters
+    const int kArrays = 33;
+    size_t arr = ((size_t)P * 4 + 255) & ~(size_t)255;
+    size_t need = arr * kArrays + (size_t)wh * 13 * 4 + 256 + 4 * 2 * 64;
+    mrs_status s = S->arena.ensure(need);
+    if (s != MRS_OK) return s;
+    char* base = S->arena.as<char>();
+    float* f[kArrays];
+    for (int i = 0; i < kArrays; ++i) f[i] = (float*)(base + arr * i);
+    PathSoA soa;
+    float** fields[] = {&soa.ox, &soa.oy, &soa.oz, &soa.dx, &soa.dy, &soa.dz, &soa.bx, &soa.by,
+                        &soa.bz, &soa.Lx, &soa.Ly, &soa.Lz, &soa.pdf_b, &soa.pdf_e, &soa.hit_t,
+                        &soa.sdx, &soa.sdy, &soa.sdz, &soa.stmax, &soa.scx, &soa.scy, &soa.scz,
+                        &soa.ax, &soa.ay, &soa.az, &soa.nx, &soa.ny, &soa.nz, &soa.dep};
+    int fi = 0;
+    for (float** fp : fields) *fp = f[fi++];
+    soa.hit_id = (int*)f[fi++];
+    soa.q0 = (int*)f[fi++];
+    soa.q1 = (int*)f[fi++];
+    soa.qs = (int*)f[fi++];
+    float* acc = (float*)(base + arr * kArrays);
+    uint32_t* cnt = (uint32_t*)(base + arr * kArrays + (size_t)wh * 13 * 4 + 256);
+    uint32_t* scnt = cnt + 64;
+
+    WaveParams w;
+    w.S = view(S);
+    w.P = soa;
+    memcpy(w.env, S->env, sizeof(w.env));
+    memcpy(w.cam, S->cam, sizeof(w.cam));
+    w.W = W; w.H = H; w.max_depth = max_depth;
+    w.rr_start = rr_start < 0 ? 0x7fffffff : rr_start;
+    w.wh = wh;
+    w.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    w.cnt = cnt;
+    w.scnt = scnt;
+
+    MRS_CHECK(cudaMemsetAsync(acc, 0, (size_t)wh * 13 * 4, st));
+    if (counts) MRS_CHECK(cudaMemsetAsync(counts, 0, sizeof(uint64_t) * nb, st));
+    if (shadow_counts) MRS_CHECK(cudaMemsetAsync(shadow_counts, 0, sizeof(uint64_t) * nb, st));
+    for (int s0 = 0; s0 < spp; s0 += (int)k) {
+        int kk = (int)((spp - s0) < k ? (spp - s0) : k);
+        w.s0 = s0;
+        w.n_paths = (int)(kk * wh);
+        MRS_CHECK(cudaMemsetAsync(cnt, 0, 4 * 2 * 64, st));
+        int g = grid_for(w.n_paths);
+        k_raygen<<<g, kThreads, 0, st>>>(w);
+        for (int b = 0; b <= max_depth; ++b) {
+            k_trace<<<g, kThreads, 0, st>>>(w, b);
+            k_shade<<<g, kThreads, 0, st>>>(w, b);
+            k_shadow<<<g, kThreads, 0, st>>>(w, b);
+        }
+        k_accumulate<<<grid_for(wh), kThreads, 0, st>>>(w, acc, kk);
+        if (counts || shadow_counts) k_counts<<<1, 64, 0, st>>>(cnt, scnt, nb, counts, shadow_counts);
+    }
+    k_resolve<<<grid_for(wh), kThreads, 0, st>>>(acc, wh, spp, radiance, albedo, normal, depth);
+    return cuda_status(cudaGetLastError(), "render launch");
+}
+
+extern "C" mrs_status mrs_cast(mrs_scene S, const float* orig, const float* dir, int32_t n,
+                               int32_t* prim, float* t, void* stream)
+{
+    MRS_ARG(S != nullptr, "scene is NULL");
+    MRS_ARG(n >= 0, "n_rays < 0");
+    if (n == 0) return MRS_OK;
+    MRS_ARG(orig && dir && prim && t, "NULL buffer");
+    k_cast<<<grid_for(n), kThreads, 0, (cudaStream_t)stream>>>(view(S), orig, dir, n, prim, t);
+    return cuda_status(cudaGetLastError(), "cast launch");
+}
+
+extern "C" mrs_status mrs_philox_uniforms(const uint32_t* triples, int32_t n, uint64_t seed,
+                                          float* out, void* stream)
+{
+    MRS_ARG(n >= 0, "n < 0");
+    if (n == 0) return MRS_OK;
+    MRS_ARG(triples && out, "NULL buffer");
+    k_philox<<<(n + kThreads - 1) / kThreads, kThreads, 0, (cudaStream_t)stream>>>(
+        triples, n, make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)), out);
+    return cuda_status(cudaGetLastError(), "philox launch");
+}

@@ -1,0 +1,125 @@
+"""Python binding of the scene / LBVH / path-tracing entry points.
+
+Marshalling only: every computation runs in libmrs.so's kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from ._lib import call, load
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _hptr(a):
+    return ctypes.c_void_p(a.ctypes.data) if a is not None and a.size else None
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(t, dtype):
+    assert t.is_cuda and t.dtype == dtype and t.is_contiguous(), (t.device, t.dtype)
+    return t
+
+
+class Scene:
+    """Device-resident scene + LBVH (mrs_build_scene).  `desc` is the dict of
+    arrays produced by the seeded scene generators."""
+
+    def __init__(self, desc, stream=None):
+        load()
+        self.desc = desc
+        self.n = int(len(desc["V"]))
+        V = np.ascontiguousarray(desc["V"], np.float32)
+        tm = np.ascontiguousarray(desc["tri_mat"], np.int32)
+        tl = np.ascontiguousarray(desc["tri_light"], np.int32)
+        mats = np.ascontiguousarray(desc["mats"], np.float32)
+        lights = np.ascontiguousarray(desc["lights"], np.float32)
+        env = np.ascontiguousarray(desc["env"], np.float32)
+        cam = np.ascontiguousarray(desc["cam"], np.float32)
+        h = ctypes.c_void_p()
+        call("mrs_build_scene", _hptr(V), self.n, _hptr(tm), _hptr(tl), _hptr(mats), len(mats),
+             _hptr(lights), len(lights), _hptr(env), _hptr(cam), _stream(stream), ctypes.byref(h))
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            call("mrs_free_scene", self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def rebuild(self, stream=None):
+        call("mrs_scene_rebuild", self.handle, _stream(stream))
+
+    def set_wave(self, paths: int):
+        call("mrs_scene_set_wave", self.handle, int(paths))
+
+    def export_bvh(self, stream=None):
+        n = self.n
+        dev = torch.device("cuda")
+        out = {
+            "morton": torch.zeros(n, dtype=torch.int32, device=dev),
+            "order": torch.zeros(n, dtype=torch.int32, device=dev),
+            "left": torch.zeros(max(n - 1, 1), dtype=torch.int32, device=dev),
+            "right": torch.zeros(max(n - 1, 1), dtype=torch.int32, device=dev),
+            "box": torch.zeros((max(2 * n - 1, 1), 6), dtype=torch.float32, device=dev),
+        }
+        call("mrs_scene_export_bvh", self.handle, _ptr(out["morton"]), _ptr(out["order"]),
+             _ptr(out["left"]), _ptr(out["right"]), _ptr(out["box"]), _stream(stream))
+        torch.cuda.synchronize()
+        r = {k: v.cpu().numpy() for k, v in out.items()}
+        r["morton"] = r["morton"].view(np.uint32)
+        r["left"] = r["left"][: max(n - 1, 0)]
+        r["right"] = r["right"][: max(n - 1, 0)]
+        r["box"] = r["box"][: max(2 * n - 1, 0)]
+        return r
+
+    def cast(self, orig, dirs, stream=None):
+        o = _dev(orig, torch.float32)
+        d = _dev(dirs, torch.float32)
+        n = o.shape[0]
+        prim = torch.empty(n, dtype=torch.int32, device=o.device)
+        t = torch.empty(n, dtype=torch.float32, device=o.device)
+        call("mrs_cast", self.handle, _ptr(o), _ptr(d), n, _ptr(prim), _ptr(t), _stream(stream))
+        return prim, t
+
+
+def render(scene: Scene, W, H, spp, max_depth, rr_start=None, seed=0, aux=True, counts=True,
+           out=None, stream=None):
+    """mrs_render into device tensors; returns dict of (device) tensors."""
+    dev = torch.device("cuda")
+    if out is None:
+        out = {"radiance": torch.empty((H, W, 3), dtype=torch.float32, device=dev)}
+        if aux:
+            out["albedo"] = torch.empty((H, W, 3), dtype=torch.float32, device=dev)
+            out["normal"] = torch.empty((H, W, 3), dtype=torch.float32, device=dev)
+            out["depth"] = torch.empty((H, W), dtype=torch.float32, device=dev)
+        if counts:
+            out["counts"] = torch.zeros(max_depth + 1, dtype=torch.int64, device=dev)
+            out["shadow_counts"] = torch.zeros(max_depth + 1, dtype=torch.int64, device=dev)
+    call("mrs_render", scene.handle, W, H, spp, max_depth, -1 if rr_start is None else rr_start,
+         int(seed) & 0xFFFFFFFFFFFFFFFF, _ptr(out["radiance"]), _ptr(out.get("albedo")),
+         _ptr(out.get("normal")), _ptr(out.get("depth")), _ptr(out.get("counts")),
+         _ptr(out.get("shadow_counts")), _stream(stream))
+    return out
+
+
+def philox_uniforms(triples, seed, stream=None):
+    tr = _dev(triples, torch.int32)
+    n = tr.shape[0]
+    out = torch.empty((n, 8), dtype=torch.float32, device=tr.device)
+    call("mrs_philox_uniforms", _ptr(tr), n, int(seed), _ptr(out), _stream(stream))
+    return out

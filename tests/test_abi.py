@@ -1,0 +1,64 @@
+"""CPU checks of the C-ABI library: it builds, loads, exports every entry point
+declared in include/*.h, and rejects invalid arguments before touching CUDA."""
+import ctypes
+import glob
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"\b(mrs_[a-z0-9_]+)\s*\(", src))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2106_12802_gb300 import _lib
+    return _lib.load()
+
+
+def test_header_declares_entry_points():
+    names = declared_symbols()
+    for want in ("mrs_build_scene", "mrs_render", "mrs_free_scene", "mrs_status_string"):
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2106_12802_gb300 import _lib
+    out = subprocess.run(["nm", "-D", "--defined-only", _lib.library_path()],
+                         capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\b(mrs_[a-z0-9_]+)\b", out))
+    missing = declared_symbols() - exported
+    assert not missing, missing
+    for name in declared_symbols():
+        assert hasattr(lib, name)
+
+
+def test_binding_signatures_cover_header():
+    from paper_2106_12802_gb300 import _lib
+    assert declared_symbols() <= set(_lib.SIGS)
+
+
+def test_invalid_arguments_rejected_without_cuda(lib):
+    assert lib.mrs_status_string(0) == b"ok"
+    assert lib.mrs_status_string(-1) == b"invalid argument"
+    # NULL scene handle
+    assert lib.mrs_render(None, 8, 8, 1, 1, -1, 0, None, None, None, None, None, None, None) == -1
+    assert b"scene" in lib.mrs_last_error()
+    assert lib.mrs_scene_rebuild(None, None) == -1
+    # NULL out pointer, negative sizes
+    assert lib.mrs_build_scene(None, 0, None, None, None, 0, None, 0, None, None, None, None) == -1
+    h = ctypes.c_void_p()
+    assert lib.mrs_build_scene(None, -5, None, None, None, 0, None, 0, None, None, None,
+                               ctypes.byref(h)) == -1
+    assert lib.mrs_philox_uniforms(None, -1, 0, None, None) == -1
+    assert lib.mrs_free_scene(None) == 0
