@@ -137,6 +137,71 @@ mrs_status mrs_scene_set_wave(mrs_scene scene, int64_t max_paths_per_wave);
 mrs_status mrs_philox_uniforms(const uint32_t* triples, int32_t n, uint64_t seed, float* out,
                                void* stream);
 
+
+/* ------------------------------------------------------------------------
+ * Fusion network (Sec. 4: I_SR is estimated from I_LRHS and I_HRLS + layers).
+ * Architecture (all-high-resolution variant): bilinear x s upsampling of LRHS
+ * (half-pixel centres, edge clamp), concatenation with HRLS RGB, albedo and
+ * normal (12 channels), conv3x3 12->64 + ReLU, 8 residual blocks
+ * h + conv3x3(relu(conv3x3(h))), conv3x3 64->3, plus the upsampled LRHS.
+ * All kernels 3x3 with zero padding; 64 feature channels (Sec. 4,
+ * "Implement details").
+ *
+ * Parameters: MRS_NET_NPARAMS float32 values; for each of the 18 convs in
+ * forward order, weight [Cout][3][3][Cin] then bias [Cout].
+ * ------------------------------------------------------------------------ */
+#define MRS_NET_NPARAMS 599555
+#define MRS_PREC_FP32 0   /* FP32 SIMT convolutions (reference precision) */
+#define MRS_PREC_BF16 1   /* BF16 operands on tcgen05 tensor cores, FP32 accumulate */
+#define MRS_PREC_FP8 2    /* FP8-E4M3 operands, per-output-channel weight scales */
+
+/* params: HOST float [n_params] (must equal MRS_NET_NPARAMS), copied in as the
+ * FP32 master weights; Adam moments start at zero. */
+mrs_status mrs_net_create(const float* params, int32_t n_params, mrs_net* out);
+mrs_status mrs_net_free(mrs_net net);
+/* Replace / read the FP32 master weights (HOST float [MRS_NET_NPARAMS]);
+ * set also resets the Adam state.  Both synchronise the device. */
+mrs_status mrs_net_set_params(mrs_net net, const float* params);
+mrs_status mrs_net_get_params(mrs_net net, float* params);
+
+/* I_SR = net(LRHS, HRLS, albedo, normal).  lrhs device [N][h][w][3]; hrls,
+ * albedo, normal device [N][H][W][3] with H = scale*h, W = scale*w;
+ * out device [N][H][W][3].  scale in {1, 2, 4, 8}; precision one of
+ * MRS_PREC_*.  Activation workspace lives in the net handle (grown on
+ * demand).  Limits: N*H*W <= 2^27 pixels. */
+mrs_status mrs_fuse(mrs_net net, const float* lrhs, const float* hrls, const float* albedo,
+                    const float* normal, int32_t N, int32_t H, int32_t W, int32_t scale,
+                    int32_t precision, float* out, void* stream);
+
+/* Image error metrics of x against ref (device float, n values each, both in
+ * scene-linear space), reduced in float64 on the GPU (Sec. 5):
+ * out[0] = PSNR of the sRGB images (Eq. cvt_color, peak 1; +inf if equal),
+ * out[1] = RelMSE with lambda1, lambda2, out[2] = MSE (linear).
+ * out is a HOST double[3]; the call synchronises `stream`. */
+mrs_status mrs_image_metrics(const float* x, const float* ref, int64_t n, double lambda1,
+                             double lambda2, double* out, void* stream);
+
+/* Fallback gate of the hybrid renderer: D = RelMSE(box_s(fused), LRHS)
+ * (lambda1 = 0.5, lambda2 = 0.01), box_s = mean over s x s blocks.  If
+ * D > tau, out = plain (the plain high-resolution render), else out = fused.
+ * fused, plain, out device [N][H][W][3]; lrhs device [N][h][w][3]; plain may
+ * equal NULL only if the caller accepts out = fused regardless (then
+ * *used_plain reports the decision without copying).  used_plain and D are
+ * HOST pointers (may be NULL); the call synchronises `stream`. */
+mrs_status mrs_gate(const float* fused, const float* lrhs, const float* plain, int32_t N,
+                    int32_t H, int32_t W, int32_t scale, double tau, float* out,
+                    int32_t* used_plain, double* D, void* stream);
+
+/* One 3x3 convolution with zero padding (a single layer of the network, for
+ * testing and tuning): x device float [N][H][W][cin], w HOST float
+ * [cout][3][3][cin], b HOST float [cout], out device float [N][H][W][cout];
+ * relu != 0 applies max(0, .).  precision MRS_PREC_FP32 computes in FP32;
+ * MRS_PREC_BF16 / MRS_PREC_FP8 round x and w to the operand type and
+ * accumulate in FP32 on the tensor cores (cin <= 64, cout <= 64). */
+mrs_status mrs_conv3x3(const float* x, int32_t N, int32_t H, int32_t W, int32_t cin,
+                       int32_t cout, const float* w, const float* b, int32_t relu,
+                       int32_t precision, float* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

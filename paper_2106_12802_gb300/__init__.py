@@ -6,3 +6,4 @@ device memory and streams only.
 """
 from ._lib import MrsError, library_path, load  # noqa: F401
 from .render import Scene, philox_uniforms, render  # noqa: F401
+from .fusion import NPARAMS, Net, conv3x3, gate, image_metrics  # noqa: F401

@@ -31,6 +31,14 @@ SIGS = {
     "mrs_render": [P, I32, I32, I32, I32, I32, U64, P, P, P, P, P, P, P],
     "mrs_scene_set_wave": [P, I64],
     "mrs_philox_uniforms": [P, I32, U64, P, P],
+    "mrs_net_create": [P, I32, P],
+    "mrs_net_free": [P],
+    "mrs_net_set_params": [P, P],
+    "mrs_net_get_params": [P, P],
+    "mrs_fuse": [P, P, P, P, P, I32, I32, I32, I32, I32, P, P],
+    "mrs_image_metrics": [P, P, I64, F64, F64, P, P],
+    "mrs_gate": [P, P, P, I32, I32, I32, I32, F64, P, P, P, P],
+    "mrs_conv3x3": [P, I32, I32, I32, I32, I32, P, P, I32, I32, P, P],
     "mrs_status_string": [I32],
     "mrs_last_error": [],
 }

@@ -1,0 +1,453 @@
+// 3x3 convolution as an implicit GEMM on the 5th-generation tensor cores
+// (tcgen05.mma, accumulators in TMEM, operands staged by TMA).
+//
+// GEMM view of one layer: M = output pixels, N = output channels (64, or 16
+// for the 3-channel head padded to 16), K = 9 taps x 64 input channels.  A CTA
+// tile is 128 consecutive pixels of one image row; for tap (dy, dx) its A
+// operand is the 128 x 64 input block at (row y+dy-1, column x0+dx-1), loaded
+// by one TMA box whose out-of-range part is zero-filled (this is the zero
+// padding).  Each activation row (64 channels) is 128 bytes (bf16) or 64 bytes
+// (fp8), stored with the matching TMA swizzle so the smem descriptors can
+// address it directly.  All 9 taps of the layer's weights stay resident in
+// shared memory for the whole persistent CTA.
+//
+// Warp roles (192 threads, one CTA per SM):
+//   warp 0: TMA producer (weights once, then 9 A boxes per tile, S-stage ring)
+//   warp 1: TMEM allocator and MMA issuer (one thread)
+//   warps 2-5: epilogue (tcgen05.ld of the 128 x N fp32 accumulator, bias,
+//              ReLU / residual / bilinear skip, vectorised stores)
+// The TMEM accumulator is double-buffered so the epilogue of tile i overlaps
+// the MMAs of tile i+1.  Every wait is bounded: on timeout the kernel sets
+// *err and all roles unwind, TMEM is freed, and the host reports
+// MRS_ERR_TIMEOUT.
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
+#include "conv_tc.cuh"
+
+namespace mrs {
+namespace {
+
+constexpr int kTileM = 128;
+constexpr int kThreads = 192;
+constexpr long long kTimeoutCycles = 4000000000LL;   // ~2 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait; false if this or another role gave up
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*(volatile int*)err) return false;
+        if (clock64() - t0 > kTimeoutCycles) {
+            atomicExch(err, 1);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1,
+                                            int c2, int c3, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1,
+                                            uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// tcgen05 shared-memory matrix descriptor, K-major, swizzled rows of
+// `row_bytes` (128 -> SWIZZLE_128B, 64 -> SWIZZLE_64B), 8-row groups.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, int row_bytes)
+{
+    uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);
+    d |= (uint64_t)1 << 16;                                  // LBO (unused when swizzled)
+    d |= (uint64_t)((8 * row_bytes) >> 4) << 32;              // SBO: next 8-row group
+    d |= (uint64_t)1 << 46;                                  // descriptor version
+    d |= (uint64_t)(row_bytes == 128 ? 2 : 4) << 61;         // swizzle mode
+    return d;
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                        uint32_t accum)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accum));
+}
+__device__ __forceinline__ void mma_f8(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                       uint32_t accum)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accum));
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// bilinear x s upsampling of LRHS at HR pixel (x, y): half-pixel centres,
+// clamped at the borders
+__device__ __forceinline__ void bilinear(const float* __restrict__ lr, int h, int w, int s, int x,
+                                         int y, float out[3])
+{
+    float inv = 1.0f / (float)s;
+    float sy = fmaxf(((float)y + 0.5f) * inv - 0.5f, 0.0f);
+    float sx = fmaxf(((float)x + 0.5f) * inv - 0.5f, 0.0f);
+    int y0 = min((int)sy, h - 1), x0 = min((int)sx, w - 1);
+    int y1 = min(y0 + 1, h - 1), x1 = min(x0 + 1, w - 1);
+    float ly = sy - (float)y0, lx = sx - (float)x0;
+    const float* a = lr + ((size_t)y0 * w + x0) * 3;
+    const float* b = lr + ((size_t)y0 * w + x1) * 3;
+    const float* c = lr + ((size_t)y1 * w + x0) * 3;
+    const float* d = lr + ((size_t)y1 * w + x1) * 3;
+    for (int k = 0; k < 3; ++k) {
+        float top = __ldg(a + k) * (1.0f - lx) + __ldg(b + k) * lx;
+        float bot = __ldg(c + k) * (1.0f - lx) + __ldg(d + k) * lx;
+        out[k] = top * (1.0f - ly) + bot * ly;
+    }
+}
+
+template <int NOUT, int OPER>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_conv_tc(const __grid_constant__ CUtensorMap tmap_x, const __grid_constant__ CUtensorMap tmap_w,
+              TcConvArgs a, int stages)
+{
+    constexpr int ROWB = OPER == TC_BF16 ? 128 : 64;          // bytes per activation row
+    constexpr int ABYTES = kTileM * ROWB;                    // one A stage
+    constexpr int WBYTES = 9 * NOUT * ROWB;                  // all taps of the weights
+    constexpr int KSTEPS = OPER == TC_BF16 ? 4 : 2;          // MMAs per tap (K = 16 / 32 per MMA)
+    constexpr uint32_t IDESC =
+        (1u << 4) | ((OPER == TC_BF16 ? 1u : 0u) << 7) | ((OPER == TC_BF16 ? 1u : 0u) << 10) |
+        ((uint32_t)(NOUT >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
+    constexpr uint32_t kTmemCols = 128;
+
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* sW = smem;
+    uint8_t* sA = smem + ((WBYTES + 1023) & ~1023);
+    uint64_t* bars = (uint64_t*)(sA + stages * ABYTES);
+    uint64_t* full = bars;
+    uint64_t* empty = bars + stages;
+    uint64_t* wbar = bars + 2 * stages;
+    uint64_t* tfull = wbar + 1;
+    uint64_t* tempty = tfull + 2;
+    uint32_t* tslot = (uint32_t*)(tempty + 2);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int XB = (a.W + kTileM - 1) / kTileM;
+    const int ntiles = a.N * a.H * XB;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < stages; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
+        mbar_init(wbar, 1);
+        for (int i = 0; i < 2; ++i) { mbar_init(&tfull[i], 1); mbar_init(&tempty[i], 4); }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tslot)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *(volatile uint32_t*)tslot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            mbar_expect_tx(wbar, WBYTES);
+            for (int t = 0; t < 9; ++t) tma_load_2d(sW + t * NOUT * ROWB, &tmap_w, 0, t * NOUT, wbar);
+            uint32_t it = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+                int xb = tile % XB, rest = tile / XB, y = rest % a.H, n = rest / a.H;
+                for (int t = 0; t < 9; ++t, ++it) {
+                    int s = it % stages;
+                    uint32_t ph = (it / stages) & 1;
+                    if (!mbar_wait(&empty[s], ph ^ 1, a.err)) { ok = false; break; }
+                    mbar_expect_tx(&full[s], ABYTES);
+                    tma_load_4d(sA + s * ABYTES, &tmap_x, 0, xb * kTileM + (t % 3) - 1,
+                                y + (t / 3) - 1, n, &full[s]);
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            bool ok = mbar_wait(wbar, 0, a.err);
+            uint32_t it = 0, lt = 0;
+            const uint32_t wbase = smem_u32(sW), abase = smem_u32(sA);
+            for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x, ++lt) {
+                uint32_t acc = lt & 1, use = lt >> 1;
+                if (!mbar_wait(&tempty[acc], (use & 1) ^ 1, a.err)) { ok = false; break; }
+                tc_fence_after();
+                uint32_t d = tmem + acc * 64;
+                for (int t = 0; t < 9; ++t, ++it) {
+                    int s = it % stages;
+                    uint32_t ph = (it / stages) & 1;
+                    if (!mbar_wait(&full[s], ph, a.err)) { ok = false; break; }
+                    tc_fence_after();
+#pragma unroll
+                    for (int k = 0; k < KSTEPS; ++k) {
+                        uint64_t ad = sdesc(abase + s * ABYTES + k * 32, ROWB);
+                        uint64_t bd = sdesc(wbase + t * NOUT * ROWB + k * 32, ROWB);
+                        if (OPER == TC_BF16) mma_f16(d, ad, bd, IDESC, (t | k) != 0);
+                        else mma_f8(d, ad, bd, IDESC, (t | k) != 0);
+                    }
+                    mma_commit(&empty[s]);
+                }
+                if (!ok) break;
+                mma_commit(&tfull[acc]);
+            }
+        }
+    } else {
+        // epilogue: warp w reads TMEM lanes 32 * (w % 4) .. + 31
+        const int q = warp & 3;
+        const int m = q * 32 + lane;
+        uint32_t lt = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
+            uint32_t acc = lt & 1, use = lt >> 1;
+            bool ok = mbar_wait(&tfull[acc], use & 1, a.err);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            tc_fence_after();
+            float v[NOUT];
+            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + acc * 64;
+#pragma unroll
+            for (int c = 0; c < NOUT; c += 16) {
+                uint32_t r[16];
+                tmem_ld16(taddr + c, r);
+                tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < 16; ++j) v[c + j] = __uint_as_float(r[j]);
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[acc]);
+
+            int xb = tile % XB, rest = tile / XB, y = rest % a.H, n = rest / a.H;
+            int x = xb * kTileM + m;
+            if (x >= a.W) continue;
+            size_t p = ((size_t)n * a.H + y) * a.W + x;
+            if (OPER == TC_FP8) {
+                // dequantise: acc * wscale[c] * xscale
+#pragma unroll
+                for (int c = 0; c < NOUT; ++c) v[c] = v[c] * (__ldg(a.wscale + c) * a.xscale);
+            }
+            if (a.mode == TC_RELU_BF16 || a.mode == TC_RESID_BF16) {
+                float o[64];
+#pragma unroll
+                for (int c = 0; c < 64; ++c) o[c] = v[c < NOUT ? c : 0] + __ldg(a.bias + c);
+                if (a.mode == TC_RELU_BF16) {
+#pragma unroll
+                    for (int c = 0; c < 64; ++c) o[c] = fmaxf(o[c], 0.0f);
+                } else {
+                    const uint4* rp = (const uint4*)((const __nv_bfloat16*)a.res + p * 64);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        uint4 u = rp[j];
+                        const __nv_bfloat162* h2 = (const __nv_bfloat162*)&u;
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            float2 f = __bfloat1622float2(h2[e]);
+                            o[8 * j + 2 * e] = f.x + o[8 * j + 2 * e];
+                            o[8 * j + 2 * e + 1] = f.y + o[8 * j + 2 * e + 1];
+                        }
+                    }
+                }
+                uint4* op = (uint4*)((__nv_bfloat16*)a.out + p * 64);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    uint4 u;
+                    __nv_bfloat162* h2 = (__nv_bfloat162*)&u;
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        h2[e] = __floats2bfloat162_rn(o[8 * j + 2 * e], o[8 * j + 2 * e + 1]);
+                    op[j] = u;
+                }
+                if (a.out_fp8) {
+                    uint4* fp = (uint4*)((uint8_t*)a.out_fp8 + p * 64);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        uint4 u;
+                        uint8_t* b8 = (uint8_t*)&u;
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) {
+                            float f = o[16 * j + e] * a.out_fp8_inv_scale;
+                            b8[e] = (uint8_t)__nv_cvt_float_to_fp8(f, __NV_SATFINITE, __NV_E4M3);
+                        }
+                        fp[j] = u;
+                    }
+                }
+            } else if (a.mode == TC_FINAL_F32) {
+                float up[3];
+                bilinear(a.lrhs + (size_t)n * (a.H / a.scale) * (a.W / a.scale) * 3,
+                         a.H / a.scale, a.W / a.scale, a.scale, x, y, up);
+                float* op = (float*)a.out + p * 3;
+                for (int c = 0; c < 3; ++c) op[c] = (v[c] + __ldg(a.bias + c)) + up[c];
+            } else {
+                float* op = (float*)a.out + p * a.cout;
+#pragma unroll
+                for (int c = 0; c < NOUT; ++c) {
+                    if (c < a.cout) {
+                        float o = v[c] + __ldg(a.bias + c);
+                        op[c] = a.relu ? fmaxf(o, 0.0f) : o;
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kTmemCols));
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void* p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+template <int NOUT, int OPER> size_t smem_bytes(int stages)
+{
+    constexpr int ROWB = OPER == TC_BF16 ? 128 : 64;
+    return 1024 + ((9 * NOUT * ROWB + 1023) & ~1023) + (size_t)stages * kTileM * ROWB + 8 * (2 * stages + 5) + 16;
+}
+
+template <int NOUT, int OPER>
+mrs_status launch(const TcConvArgs& a, cudaStream_t st)
+{
+    constexpr int ROWB = OPER == TC_BF16 ? 128 : 64;
+    int stages = OPER == TC_BF16 ? (NOUT == 64 ? 8 : 10) : 12;
+    size_t smem = smem_bytes<NOUT, OPER>(stages);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_conv_tc<NOUT, OPER>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_status(e, "conv smem attribute");
+        attr = true;
+    }
+    (void)ROWB;
+    int ntiles = a.N * a.H * ((a.W + kTileM - 1) / kTileM);
+    int grid = ntiles < sm_count() ? ntiles : sm_count();
+    if (grid < 1) return MRS_OK;
+    k_conv_tc<NOUT, OPER><<<grid, kThreads, smem, st>>>(*a.tmap_x, *a.tmap_w, a, stages);
+    return cuda_status(cudaGetLastError(), "conv launch");
+}
+
+}  // namespace
+
+mrs_status tc_make_act_map(CUtensorMap* m, const void* ptr, int N, int H, int W, int operand)
+{
+    auto fn = encode_fn();
+    if (!fn) { set_error("cuTensorMapEncodeTiled unavailable"); return MRS_ERR_CUDA; }
+    int rowb = operand == TC_BF16 ? 128 : 64;
+    cuuint64_t dims[4] = {64, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)N};
+    cuuint64_t strides[3] = {(cuuint64_t)rowb, (cuuint64_t)rowb * W, (cuuint64_t)rowb * W * H};
+    cuuint32_t box[4] = {64, (cuuint32_t)kTileM, 1, 1};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    CUresult r = fn(m, operand == TC_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8,
+                    4, const_cast<void*>(ptr), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    operand == TC_BF16 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) { set_error("cuTensorMapEncodeTiled(act) failed: %d", (int)r); return MRS_ERR_CUDA; }
+    return MRS_OK;
+}
+
+mrs_status tc_make_w_map(CUtensorMap* m, const void* ptr, int rows, int nout, int operand)
+{
+    auto fn = encode_fn();
+    if (!fn) { set_error("cuTensorMapEncodeTiled unavailable"); return MRS_ERR_CUDA; }
+    int rowb = operand == TC_BF16 ? 128 : 64;
+    cuuint64_t dims[2] = {64, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)rowb};
+    cuuint32_t box[2] = {64, (cuuint32_t)nout};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = fn(m, operand == TC_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8,
+                    2, const_cast<void*>(ptr), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    operand == TC_BF16 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) { set_error("cuTensorMapEncodeTiled(w) failed: %d", (int)r); return MRS_ERR_CUDA; }
+    return MRS_OK;
+}
+
+mrs_status tc_conv3x3(const TcConvArgs& a, cudaStream_t st)
+{
+    if (a.nout == 64) return a.operand == TC_BF16 ? launch<64, TC_BF16>(a, st) : launch<64, TC_FP8>(a, st);
+    if (a.nout == 16) return a.operand == TC_BF16 ? launch<16, TC_BF16>(a, st) : launch<16, TC_FP8>(a, st);
+    set_error("tc_conv3x3: nout must be 64 or 16");
+    return MRS_ERR_ARG;
+}
+
+}  // namespace mrs

@@ -1,0 +1,52 @@
+// Tensor-core 3x3 convolution (implicit GEMM on tcgen05) used by the fusion
+// network: internal interface between conv_tc.cu and fuse.cu.
+#pragma once
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace mrs {
+
+// Epilogue modes of the tensor-core convolution
+enum TcMode : int {
+    TC_RELU_BF16 = 0,   // out_bf16[p][64] = relu(acc + b)
+    TC_RESID_BF16 = 1,  // out_bf16[p][64] = res[p] + (acc + b)   (res may alias out)
+    TC_FINAL_F32 = 2,   // out_f32[p][3]  = (acc + b) + bilinear_up(lrhs)[p]
+    TC_PLAIN_F32 = 3,   // out_f32[p][cout] = acc + b, optional relu
+};
+
+enum TcOperand : int { TC_BF16 = 0, TC_FP8 = 1 };
+
+struct TcConvArgs {
+    const CUtensorMap* tmap_x;   // activations [N][H][W][64] (bf16) or [..][64] (fp8)
+    const CUtensorMap* tmap_w;   // packed weights [9 * nout][64]
+    const float* bias;           // [nout] (padded)
+    const float* wscale;         // fp8 only: per-output-channel dequant scale (may be NULL)
+    float xscale;                // fp8 only: activation dequant scale
+    const void* res;             // TC_RESID_BF16 residual (bf16 [p][64])
+    void* out;                   // output
+    const float* lrhs;           // TC_FINAL_F32: [N][h][w][3]
+    int N, H, W, scale;
+    int nout;                    // 64 or 16 (MMA N)
+    int cout;                    // valid output channels (TC_PLAIN_F32 / TC_FINAL_F32)
+    int relu;                    // TC_PLAIN_F32
+    int mode;
+    int operand;                 // TC_BF16 / TC_FP8
+    int* err;                    // device error word (timeouts)
+    // TC_RELU_BF16 / TC_RESID_BF16 with fp8 operands: also emit the fp8 copy
+    void* out_fp8;
+    float out_fp8_inv_scale;
+};
+
+// Encode a tiled tensor map for a [N][H][W][C] activation tensor whose rows
+// are `row_bytes` (= 128) bytes: box = 128 pixels of one image row.
+mrs_status tc_make_act_map(CUtensorMap* m, const void* ptr, int N, int H, int W, int operand);
+// Tensor map for packed weights [rows][64 (bf16) | 64 (fp8)].
+mrs_status tc_make_w_map(CUtensorMap* m, const void* ptr, int rows, int nout, int operand);
+
+mrs_status tc_conv3x3(const TcConvArgs& a, cudaStream_t st);
+
+}  // namespace mrs

@@ -1,0 +1,762 @@
+// Fusion network of the multi-resolution sampling method (Sec. 4): I_SR from
+// the LRHS render and the HRLS render + albedo / normal layers, plus the image
+// metrics of Sec. 5 (sRGB PSNR via Eq. cvt_color, RelMSE) and the fallback gate
+// of the hybrid renderer.
+//
+// Precisions: FP32 (SIMT direct convolution; reference precision), BF16
+// (tcgen05 implicit GEMM, conv_tc.cu) and FP8-E4M3 (tcgen05 kind::f8f6f4 with
+// per-output-channel weight scales and calibrated per-layer activation scales).
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <math.h>
+#include <string.h>
+
+#include <mutex>
+#include <vector>
+
+#include "conv_tc.cuh"
+
+namespace mrs {
+namespace {
+
+constexpr int kLayers = 18;
+constexpr int kFeat = 64;
+
+struct LayerShape { int cin, cout; size_t woff, boff; };
+
+const std::vector<LayerShape>& shapes()
+{
+    static std::vector<LayerShape> v;
+    if (v.empty()) {
+        size_t o = 0;
+        for (int l = 0; l < kLayers; ++l) {
+            int cin = l == 0 ? 12 : kFeat, cout = l == kLayers - 1 ? 3 : kFeat;
+            v.push_back({cin, cout, o, o + (size_t)cout * 9 * cin});
+            o += (size_t)cout * 9 * cin + cout;
+        }
+    }
+    return v;
+}
+constexpr size_t kParams = 599555;
+
+inline int nout_of(int l) { return l == kLayers - 1 ? 16 : 64; }
+
+// ---- input assembly ---------------------------------------------------------
+__device__ __forceinline__ void up_pixel(const float* __restrict__ lr, int h, int w, int s, int x,
+                                         int y, float o[3])
+{
+    float inv = 1.0f / (float)s;
+    float sy = fmaxf(((float)y + 0.5f) * inv - 0.5f, 0.0f);
+    float sx = fmaxf(((float)x + 0.5f) * inv - 0.5f, 0.0f);
+    int y0 = min((int)sy, h - 1), x0 = min((int)sx, w - 1);
+    int y1 = min(y0 + 1, h - 1), x1 = min(x0 + 1, w - 1);
+    float ly = sy - (float)y0, lx = sx - (float)x0;
+    const float* a = lr + ((size_t)y0 * w + x0) * 3;
+    const float* b = lr + ((size_t)y0 * w + x1) * 3;
+    const float* c = lr + ((size_t)y1 * w + x0) * 3;
+    const float* d = lr + ((size_t)y1 * w + x1) * 3;
+    for (int k = 0; k < 3; ++k) {
+        float top = __ldg(a + k) * (1.0f - lx) + __ldg(b + k) * lx;
+        float bot = __ldg(c + k) * (1.0f - lx) + __ldg(d + k) * lx;
+        o[k] = top * (1.0f - ly) + bot * ly;
+    }
+}
+
+// 12 fusion-input channels of pixel p: up(LRHS), HRLS, albedo, normal
+__device__ __forceinline__ void input12(const float* lrhs, const float* hrls, const float* alb,
+                                        const float* nrm, int H, int W, int s, size_t p, float v[12])
+{
+    int x = (int)(p % W);
+    size_t r = p / W;
+    int y = (int)(r % H), n = (int)(r / H);
+    int h = H / s, w = W / s;
+    up_pixel(lrhs + (size_t)n * h * w * 3, h, w, s, x, y, v);
+    for (int k = 0; k < 3; ++k) {
+        v[3 + k] = __ldg(hrls + 3 * p + k);
+        v[6 + k] = __ldg(alb + 3 * p + k);
+        v[9 + k] = __ldg(nrm + 3 * p + k);
+    }
+}
+
+__global__ void k_input_f32(const float* lrhs, const float* hrls, const float* alb,
+                            const float* nrm, int H, int W, int s, size_t P, float* x0)
+{
+    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < P;
+         p += (size_t)gridDim.x * blockDim.x) {
+        float v[12];
+        input12(lrhs, hrls, alb, nrm, H, W, s, p, v);
+        for (int k = 0; k < 12; ++k) x0[12 * p + k] = v[k];
+    }
+}
+
+// bf16 [P][64] (channels 12..63 zero) or fp8 [P][64] scaled by inv_scale
+__global__ void k_input_q(const float* lrhs, const float* hrls, const float* alb,
+                          const float* nrm, int H, int W, int s, size_t P, void* x0, int fp8,
+                          float inv_scale)
+{
+    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < P;
+         p += (size_t)gridDim.x * blockDim.x) {
+        float v[12];
+        input12(lrhs, hrls, alb, nrm, H, W, s, p, v);
+        if (!fp8) {
+            uint4* o = (uint4*)((__nv_bfloat16*)x0 + p * 64);
+            uint4 u[2];
+            __nv_bfloat162* h2 = (__nv_bfloat162*)u;
+            for (int e = 0; e < 8; ++e)
+                h2[e] = __floats2bfloat162_rn(2 * e < 12 ? v[2 * e] : 0.0f,
+                                              2 * e + 1 < 12 ? v[2 * e + 1] : 0.0f);
+            o[0] = u[0];
+            o[1] = u[1];
+            uint4 z = make_uint4(0, 0, 0, 0);
+            for (int j = 2; j < 8; ++j) o[j] = z;
+        } else {
+            uint4* o = (uint4*)((uint8_t*)x0 + p * 64);
+            uint4 u;
+            uint8_t* b8 = (uint8_t*)&u;
+            for (int e = 0; e < 16; ++e)
+                b8[e] = e < 12 ? (uint8_t)__nv_cvt_float_to_fp8(v[e] * inv_scale, __NV_SATFINITE, __NV_E4M3) : 0;
+            o[0] = u;
+            uint4 z = make_uint4(0, 0, 0, 0);
+            for (int j = 1; j < 4; ++j) o[j] = z;
+        }
+    }
+}
+
+// ---- FP32 SIMT direct convolution -------------------------------------------
+// block = 16 x 8 output pixels, 16 output channels (grid.z over channel groups);
+// input channels staged through shared memory 4 at a time with a 1-pixel halo
+constexpr int kTX = 16, kTY = 8, kCT = 16, kCC = 4;
+enum SimtMode { SIMT_PLAIN = 0, SIMT_RESID = 1, SIMT_FINAL = 2 };
+
+__global__ void __launch_bounds__(kTX * kTY)
+    k_conv_simt(const float* __restrict__ x, int cin, const float* __restrict__ w,
+                const float* __restrict__ b, int cout, int mode, int relu,
+                const float* __restrict__ res, float* __restrict__ out,
+                const float* __restrict__ lrhs, int H, int W, int s)
+{
+    __shared__ float sin_[kTY + 2][kTX + 2][kCC];
+    __shared__ __align__(16) float sw[9][kCC][kCT];
+    const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
+    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
+    const int n = blockIdx.z / ((cout + kCT - 1) / kCT);
+    const int o0 = (blockIdx.z % ((cout + kCT - 1) / kCT)) * kCT;
+    const float* xin = x + (size_t)n * H * W * cin;
+    float acc[kCT];
+#pragma unroll
+    for (int o = 0; o < kCT; ++o) acc[o] = 0.0f;
+    for (int c0 = 0; c0 < cin; c0 += kCC) {
+        for (int i = threadIdx.x; i < (kTY + 2) * (kTX + 2) * kCC; i += kTX * kTY) {
+            int c = i % kCC, px = (i / kCC) % (kTX + 2), py = i / (kCC * (kTX + 2));
+            int gx = x0 + px - 1, gy = y0 + py - 1;
+            float v = 0.0f;
+            if (gx >= 0 && gx < W && gy >= 0 && gy < H && c0 + c < cin)
+                v = __ldg(xin + ((size_t)gy * W + gx) * cin + c0 + c);
+            sin_[py][px][c] = v;
+        }
+        for (int i = threadIdx.x; i < 9 * kCC * kCT; i += kTX * kTY) {
+            int o = i % kCT, c = (i / kCT) % kCC, t = i / (kCT * kCC);
+            float v = 0.0f;
+            if (o0 + o < cout && c0 + c < cin) v = __ldg(w + ((size_t)(o0 + o) * 9 + t) * cin + c0 + c);
+            sw[t][c][o] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+#pragma unroll
+            for (int c = 0; c < kCC; ++c) {
+                float v = sin_[ty + t / 3][tx + t % 3][c];
+                const float4* w4 = (const float4*)sw[t][c];
+#pragma unroll
+                for (int o4 = 0; o4 < kCT / 4; ++o4) {
+                    float4 ww = w4[o4];
+                    acc[4 * o4] += v * ww.x;
+                    acc[4 * o4 + 1] += v * ww.y;
+                    acc[4 * o4 + 2] += v * ww.z;
+                    acc[4 * o4 + 3] += v * ww.w;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    int gx = x0 + tx, gy = y0 + ty;
+    if (gx >= W || gy >= H) return;
+    size_t p = ((size_t)n * H + gy) * W + gx;
+    if (mode == SIMT_FINAL) {
+        float up[3];
+        int h = H / s, wl = W / s;
+        up_pixel(lrhs + (size_t)n * h * wl * 3, h, wl, s, gx, gy, up);
+        for (int o = 0; o < kCT; ++o)
+            if (o0 + o < 3) out[p * 3 + o0 + o] = (acc[o] + __ldg(b + o0 + o)) + up[o0 + o];
+        return;
+    }
+#pragma unroll
+    for (int o = 0; o < kCT; ++o) {
+        if (o0 + o >= cout) break;
+        float v = acc[o] + __ldg(b + o0 + o);
+        if (mode == SIMT_RESID) v = res[p * cout + o0 + o] + v;
+        else if (relu) v = fmaxf(v, 0.0f);
+        out[p * cout + o0 + o] = v;
+    }
+}
+
+mrs_status conv_simt(const float* x, int cin, const float* w, const float* b, int cout, int mode,
+                     int relu, const float* res, float* out, const float* lrhs, int N, int H,
+                     int W, int s, cudaStream_t st)
+{
+    dim3 grid((W + kTX - 1) / kTX, (H + kTY - 1) / kTY, N * ((cout + kCT - 1) / kCT));
+    k_conv_simt<<<grid, kTX * kTY, 0, st>>>(x, cin, w, b, cout, mode, relu, res, out, lrhs, H, W, s);
+    return cuda_status(cudaGetLastError(), "conv_simt launch");
+}
+
+// ---- weight packing ---------------------------------------------------------
+// packed[tap][o][c] (o < nout, c < 64), zero padded; layer l at l * 9*64*64
+__global__ void k_pack_bf16(const float* __restrict__ master, size_t woff, size_t boff, int cin,
+                            int cout, int nout, __nv_bfloat16* __restrict__ wp, float* __restrict__ bp)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < 64) bp[i] = i < cout ? master[boff + i] : 0.0f;
+    if (i >= 9 * nout * 64) return;
+    int c = i % 64, o = (i / 64) % nout, t = i / (64 * nout);
+    float v = (o < cout && c < cin) ? master[woff + ((size_t)o * 9 + t) * cin + c] : 0.0f;
+    wp[i] = __float2bfloat16_rn(v);
+}
+
+// fp8: per-output-channel scale = amax / 448 over that channel's weights
+__global__ void k_pack_fp8(const float* __restrict__ master, size_t woff, size_t boff, int cin,
+                           int cout, int nout, uint8_t* __restrict__ wp, float* __restrict__ bp,
+                           float* __restrict__ wscale)
+{
+    __shared__ float amax[64];
+    int tid = threadIdx.x;
+    if (tid < 64) {
+        float m = 0.0f;
+        if (tid < cout)
+            for (int k = 0; k < 9 * cin; ++k) m = fmaxf(m, fabsf(master[woff + (size_t)tid * 9 * cin + k]));
+        amax[tid] = m > 0.0f ? m / 448.0f : 1.0f;
+        wscale[tid] = amax[tid];
+        bp[tid] = tid < cout ? master[boff + tid] : 0.0f;
+    }
+    __syncthreads();
+    for (int i = tid; i < 9 * nout * 64; i += blockDim.x) {
+        int c = i % 64, o = (i / 64) % nout, t = i / (64 * nout);
+        float v = (o < cout && c < cin) ? master[woff + ((size_t)o * 9 + t) * cin + c] / amax[o] : 0.0f;
+        wp[i] = (uint8_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+    }
+}
+
+// amax of a bf16 [P][64] tensor (for fp8 activation calibration)
+__global__ void k_amax_bf16(const __nv_bfloat16* __restrict__ x, size_t n, float* out)
+{
+    float m = 0.0f;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(__bfloat162float(x[i])));
+    for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax((int*)out, __float_as_int(m));
+}
+
+// ---- metrics ----------------------------------------------------------------
+__device__ __forceinline__ double srgb(double l)
+{
+    if (l <= 0.0) return 0.0;
+    if (l <= 0.0031308) return 12.92 * l;
+    if (l < 1.0) return 1.055 * pow(l, 1.0 / 2.4) - 0.055;
+    return 1.0;
+}
+
+constexpr int kRedBlocks = 1024;
+
+__global__ void k_metrics_partial(const float* __restrict__ x, const float* __restrict__ ref,
+                                  int64_t n, double l1, double l2, double* part)
+{
+    __shared__ double s[3][256];
+    double a = 0, b = 0, c = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double xv = x[i], rv = ref[i];
+        double d = srgb(xv) - srgb(rv);
+        a += d * d;
+        double e = xv - rv;
+        b += l1 * e * e / (rv * rv + l2);
+        c += e * e;
+    }
+    s[0][threadIdx.x] = a; s[1][threadIdx.x] = b; s[2][threadIdx.x] = c;
+    __syncthreads();
+    for (int w = 128; w; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int k = 0; k < 3; ++k) s[k][threadIdx.x] += s[k][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 3) part[blockIdx.x * 3 + threadIdx.x] = s[threadIdx.x][0];
+}
+
+__global__ void k_reduce_parts(const double* part, int nparts, int k, double* out)
+{
+    if (threadIdx.x < k) {
+        double acc = 0;
+        for (int i = 0; i < nparts; ++i) acc += part[i * k + threadIdx.x];
+        out[threadIdx.x] = acc;
+    }
+}
+
+// per LR pixel: RelMSE terms of box_s(fused) vs LRHS
+__global__ void k_gate_partial(const float* __restrict__ fused, const float* __restrict__ lrhs,
+                               int N, int H, int W, int s, double* part)
+{
+    __shared__ double sh[256];
+    int h = H / s, w = W / s;
+    int64_t nlr = (int64_t)N * h * w;
+    double acc = 0;
+    double inv = 1.0 / ((double)s * s);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nlr;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int xl = (int)(i % w);
+        int64_t r = i / w;
+        int yl = (int)(r % h), n = (int)(r / h);
+        for (int c = 0; c < 3; ++c) {
+            double m = 0;
+            for (int dy = 0; dy < s; ++dy)
+                for (int dx = 0; dx < s; ++dx)
+                    m += fused[(((int64_t)n * H + yl * s + dy) * W + xl * s + dx) * 3 + c];
+            m *= inv;
+            double ref = lrhs[i * 3 + c];
+            double e = m - ref;
+            acc += 0.5 * e * e / (ref * ref + 0.01);
+        }
+    }
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int k = 128; k; k >>= 1) {
+        if (threadIdx.x < k) sh[threadIdx.x] += sh[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void k_to_operand(const float* x, size_t P, int cin, void* o, int fp8, float inv)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < P * 64;
+         i += (size_t)gridDim.x * blockDim.x) {
+        size_t p = i / 64;
+        int c = (int)(i % 64);
+        float v = c < cin ? x[p * cin + c] : 0.0f;
+        if (fp8) ((uint8_t*)o)[i] = (uint8_t)__nv_cvt_float_to_fp8(v * inv, __NV_SATFINITE, __NV_E4M3);
+        else ((__nv_bfloat16*)o)[i] = __float2bfloat16_rn(v);
+    }
+}
+
+__global__ void k_amax_f32(const float* __restrict__ x, size_t n, float* out)
+{
+    float m = 0.0f;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(x[i]));
+    for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax((int*)out, __float_as_int(m));
+}
+
+struct Scratch {
+    std::mutex mu;
+    Buf b;
+};
+Scratch& scratch()
+{
+    static Scratch s;
+    return s;
+}
+
+}  // namespace
+}  // namespace mrs
+
+using namespace mrs;
+
+struct mrs_net_s {
+    float* master = nullptr;       // [kParams]
+    float* adam_m = nullptr;
+    float* adam_v = nullptr;
+    float* grad = nullptr;
+    int64_t step = 0;
+    __nv_bfloat16* wbf = nullptr;  // [18][9][64][64]
+    uint8_t* wf8 = nullptr;        // [18][9][64][64]
+    float* bias = nullptr;         // [18][64]
+    float* bias8 = nullptr;        // [18][64]
+    float* wscale = nullptr;       // [18][64]
+    bool bf_valid = false, f8_valid = false;
+    float xscale[kLayers];         // fp8 activation scales (calibrated)
+    bool xscale_valid = false;
+    CUtensorMap wmap_bf[kLayers], wmap_f8[kLayers];
+    Buf act;                       // activation workspace
+    Buf aux;                       // small device scratch
+    int* err = nullptr;            // device error word
+};
+
+namespace mrs {
+namespace {
+
+mrs_status pack_bf16(mrs_net_s* net, cudaStream_t st)
+{
+    if (net->bf_valid) return MRS_OK;
+    const auto& L = shapes();
+    for (int l = 0; l < kLayers; ++l) {
+        int nout = nout_of(l);
+        k_pack_bf16<<<(9 * nout * 64 + 255) / 256, 256, 0, st>>>(
+            net->master, L[l].woff, L[l].boff, L[l].cin, L[l].cout, nout,
+            net->wbf + (size_t)l * 9 * 64 * 64, net->bias + l * 64);
+        mrs_status s = tc_make_w_map(&net->wmap_bf[l], net->wbf + (size_t)l * 9 * 64 * 64, 9 * nout, nout, TC_BF16);
+        if (s != MRS_OK) return s;
+    }
+    net->bf_valid = true;
+    return cuda_status(cudaGetLastError(), "pack bf16");
+}
+
+mrs_status pack_fp8(mrs_net_s* net, cudaStream_t st)
+{
+    if (net->f8_valid) return MRS_OK;
+    const auto& L = shapes();
+    for (int l = 0; l < kLayers; ++l) {
+        int nout = nout_of(l);
+        k_pack_fp8<<<1, 256, 0, st>>>(net->master, L[l].woff, L[l].boff, L[l].cin, L[l].cout, nout,
+                                      net->wf8 + (size_t)l * 9 * 64 * 64, net->bias8 + l * 64,
+                                      net->wscale + l * 64);
+        mrs_status s = tc_make_w_map(&net->wmap_f8[l], net->wf8 + (size_t)l * 9 * 64 * 64, 9 * nout, nout, TC_FP8);
+        if (s != MRS_OK) return s;
+    }
+    net->f8_valid = true;
+    return cuda_status(cudaGetLastError(), "pack fp8");
+}
+
+mrs_status fuse_f32(mrs_net_s* net, const float* lrhs, const float* hrls, const float* alb,
+                    const float* nrm, int N, int H, int W, int s, float* out, cudaStream_t st)
+{
+    size_t P = (size_t)N * H * W;
+    mrs_status rc = net->act.ensure(P * (12 + 64 + 64) * 4);
+    if (rc != MRS_OK) return rc;
+    float* x0 = net->act.as<float>();
+    float* h = x0 + P * 12;
+    float* r = h + P * 64;
+    const auto& L = shapes();
+    k_input_f32<<<(int)((P + 255) / 256 < 65535 ? (P + 255) / 256 : 65535), 256, 0, st>>>(
+        lrhs, hrls, alb, nrm, H, W, s, P, x0);
+    rc = conv_simt(x0, 12, net->master + L[0].woff, net->master + L[0].boff, 64, SIMT_PLAIN, 1,
+                   nullptr, h, nullptr, N, H, W, s, st);
+    for (int k = 0; k < 8 && rc == MRS_OK; ++k) {
+        const LayerShape& a = L[1 + 2 * k];
+        const LayerShape& b = L[2 + 2 * k];
+        rc = conv_simt(h, 64, net->master + a.woff, net->master + a.boff, 64, SIMT_PLAIN, 1,
+                       nullptr, r, nullptr, N, H, W, s, st);
+        if (rc == MRS_OK)
+            rc = conv_simt(r, 64, net->master + b.woff, net->master + b.boff, 64, SIMT_RESID, 0, h,
+                           h, nullptr, N, H, W, s, st);
+    }
+    if (rc == MRS_OK)
+        rc = conv_simt(h, 64, net->master + L[17].woff, net->master + L[17].boff, 3, SIMT_FINAL, 0,
+                       nullptr, out, lrhs, N, H, W, s, st);
+    return rc;
+}
+
+mrs_status calibrate_fp8(mrs_net_s* net, const float* lrhs, const float* hrls, const float* alb,
+                         const float* nrm, int N, int H, int W, int s, cudaStream_t st);
+
+mrs_status fuse_tc(mrs_net_s* net, const float* lrhs, const float* hrls, const float* alb,
+                   const float* nrm, int N, int H, int W, int s, int prec, float* out,
+                   cudaStream_t st, bool calib = false)
+{
+    size_t P = (size_t)N * H * W;
+    const bool f8 = prec == MRS_PREC_FP8 && !calib;
+    mrs_status rc = pack_bf16(net, st);
+    if (rc != MRS_OK) return rc;
+    if (f8) {
+        if ((rc = pack_fp8(net, st)) != MRS_OK) return rc;
+        if (!net->xscale_valid &&
+            (rc = calibrate_fp8(net, lrhs, hrls, alb, nrm, N, H, W, s, st)) != MRS_OK)
+            return rc;
+    }
+    // workspace: x0, h, r in bf16 (128 B/px each); fp8 adds x0, h, r copies (64 B/px)
+    size_t need = P * 128 * 3 + (f8 ? P * 64 * 3 : 0) + 1024;
+    if ((rc = net->act.ensure(need)) != MRS_OK) return rc;
+    uint8_t* base = net->act.as<uint8_t>();
+    void* x0 = base;
+    void* h = base + P * 128;
+    void* r = base + P * 256;
+    uint8_t* x08 = base + P * 384;
+    uint8_t* h8 = x08 + P * 64;
+    uint8_t* r8 = h8 + P * 64;
+    int g = (int)((P + 255) / 256 < 65535 ? (P + 255) / 256 : 65535);
+    k_input_q<<<g, 256, 0, st>>>(lrhs, hrls, alb, nrm, H, W, s, P, f8 ? (void*)x08 : x0, f8 ? 1 : 0,
+                                 f8 ? 1.0f / net->xscale[0] : 1.0f);
+    if ((rc = cuda_status(cudaGetLastError(), "input")) != MRS_OK) return rc;
+    CUtensorMap mx, mh, mr;
+    int oper = f8 ? TC_FP8 : TC_BF16;
+    if ((rc = tc_make_act_map(&mx, f8 ? (void*)x08 : x0, N, H, W, oper)) != MRS_OK) return rc;
+    if ((rc = tc_make_act_map(&mh, f8 ? (void*)h8 : h, N, H, W, oper)) != MRS_OK) return rc;
+    if ((rc = tc_make_act_map(&mr, f8 ? (void*)r8 : r, N, H, W, oper)) != MRS_OK) return rc;
+    TcConvArgs a;
+    memset(&a, 0, sizeof(a));
+    a.N = N; a.H = H; a.W = W; a.scale = s;
+    a.operand = oper;
+    a.err = net->err;
+    const int nl = calib ? kLayers - 1 : kLayers;
+    for (int l = 0; l < nl && rc == MRS_OK; ++l) {
+        a.tmap_w = f8 ? &net->wmap_f8[l] : &net->wmap_bf[l];
+        a.bias = (f8 ? net->bias8 : net->bias) + l * 64;
+        a.wscale = f8 ? net->wscale + l * 64 : nullptr;
+        a.xscale = f8 ? net->xscale[l] : 1.0f;
+        a.nout = nout_of(l);
+        a.out_fp8 = nullptr;
+        if (l == 0) {
+            a.tmap_x = &mx; a.mode = TC_RELU_BF16; a.out = h; a.res = nullptr;
+            if (f8) { a.out_fp8 = h8; a.out_fp8_inv_scale = 1.0f / net->xscale[1]; }
+        } else if (l == kLayers - 1) {
+            a.tmap_x = &mh; a.mode = TC_FINAL_F32; a.out = out; a.lrhs = lrhs; a.cout = 3;
+        } else if (l % 2 == 1) {
+            a.tmap_x = &mh; a.mode = TC_RELU_BF16; a.out = r; a.res = nullptr;
+            if (f8) { a.out_fp8 = r8; a.out_fp8_inv_scale = 1.0f / net->xscale[l + 1]; }
+        } else {
+            a.tmap_x = &mr; a.mode = TC_RESID_BF16; a.out = h; a.res = h;
+            if (f8) { a.out_fp8 = h8; a.out_fp8_inv_scale = 1.0f / net->xscale[l + 1]; }
+        }
+        rc = tc_conv3x3(a, st);
+        if (calib && rc == MRS_OK && l < kLayers - 1) {
+            // amax of the input of layer l + 1 (h after conv_in / blocks, r after conv1)
+            const void* nxt = (l % 2 == 1) ? r : h;
+            float* am = net->aux.as<float>() + l + 1;
+            k_amax_bf16<<<512, 256, 0, st>>>((const __nv_bfloat16*)nxt, P * 64, am);
+            rc = cuda_status(cudaGetLastError(), "amax");
+        }
+    }
+    return rc;
+}
+
+// per-layer activation scales from one BF16 pass over the first input:
+// xscale[l] = amax(input of layer l) / 448
+mrs_status calibrate_fp8(mrs_net_s* net, const float* lrhs, const float* hrls, const float* alb,
+                         const float* nrm, int N, int H, int W, int s, cudaStream_t st)
+{
+    mrs_status rc = net->aux.ensure(4096);
+    if (rc != MRS_OK) return rc;
+    MRS_CHECK(cudaMemsetAsync(net->aux.p, 0, 4096, st));
+    size_t P = (size_t)N * H * W;
+    // layer 0 input amax: from the 12 input channels (computed in fp32 via the fp32 input kernel)
+    rc = fuse_tc(net, lrhs, hrls, alb, nrm, N, H, W, s, MRS_PREC_BF16, nullptr, st, true);
+    (void)P;
+    if (rc != MRS_OK) return rc;
+    // layer 0 input: amax of the bf16 fusion input x0
+    k_amax_bf16<<<512, 256, 0, st>>>(net->act.as<__nv_bfloat16>(), P * 64, net->aux.as<float>());
+    float am[kLayers];
+    MRS_CHECK(cudaMemcpyAsync(am, net->aux.p, sizeof(am), cudaMemcpyDeviceToHost, st));
+    MRS_CHECK(cudaStreamSynchronize(st));
+    for (int l = 0; l < kLayers; ++l) net->xscale[l] = am[l] > 0.0f ? am[l] / 448.0f : 1.0f;
+    net->xscale_valid = true;
+    return MRS_OK;
+}
+
+}  // namespace
+}  // namespace mrs
+
+extern "C" mrs_status mrs_net_create(const float* params, int32_t n_params, mrs_net* out)
+{
+    MRS_ARG(out != nullptr, "out is NULL");
+    *out = nullptr;
+    MRS_ARG(params != nullptr, "params is NULL");
+    MRS_ARG(n_params == (int32_t)kParams, "n_params must equal MRS_NET_NPARAMS");
+    mrs_net_s* net = new mrs_net_s();
+    mrs_status s = MRS_OK;
+    auto alloc = [&](void** p, size_t bytes) {
+        if (s == MRS_OK) s = cuda_status(cudaMalloc(p, bytes), "cudaMalloc(net)");
+    };
+    alloc((void**)&net->master, kParams * 4);
+    alloc((void**)&net->adam_m, kParams * 4);
+    alloc((void**)&net->adam_v, kParams * 4);
+    alloc((void**)&net->grad, kParams * 4);
+    alloc((void**)&net->wbf, (size_t)kLayers * 9 * 64 * 64 * 2);
+    alloc((void**)&net->wf8, (size_t)kLayers * 9 * 64 * 64);
+    alloc((void**)&net->bias, kLayers * 64 * 4);
+    alloc((void**)&net->bias8, kLayers * 64 * 4);
+    alloc((void**)&net->wscale, kLayers * 64 * 4);
+    alloc((void**)&net->err, 4);
+    if (s == MRS_OK) s = mrs_net_set_params(net, params);
+    if (s != MRS_OK) { mrs_net_free(net); return s; }
+    *out = net;
+    return MRS_OK;
+}
+
+extern "C" mrs_status mrs_net_free(mrs_net net)
+{
+    if (!net) return MRS_OK;
+    cudaDeviceSynchronize();
+    void* ptrs[] = {net->master, net->adam_m, net->adam_v, net->grad, net->wbf, net->wf8,
+                    net->bias, net->bias8, net->wscale, net->err};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    net->act.release();
+    net->aux.release();
+    delete net;
+    return MRS_OK;
+}
+
+extern "C" mrs_status mrs_net_set_params(mrs_net net, const float* params)
+{
+    MRS_ARG(net && params, "NULL argument");
+    MRS_CHECK(cudaMemcpy(net->master, params, kParams * 4, cudaMemcpyHostToDevice));
+    MRS_CHECK(cudaMemset(net->adam_m, 0, kParams * 4));
+    MRS_CHECK(cudaMemset(net->adam_v, 0, kParams * 4));
+    MRS_CHECK(cudaMemset(net->err, 0, 4));
+    net->step = 0;
+    net->bf_valid = net->f8_valid = net->xscale_valid = false;
+    return MRS_OK;
+}
+
+extern "C" mrs_status mrs_net_get_params(mrs_net net, float* params)
+{
+    MRS_ARG(net && params, "NULL argument");
+    MRS_CHECK(cudaMemcpy(params, net->master, kParams * 4, cudaMemcpyDeviceToHost));
+    return MRS_OK;
+}
+
+extern "C" mrs_status mrs_fuse(mrs_net net, const float* lrhs, const float* hrls,
+                               const float* albedo, const float* normal, int32_t N, int32_t H,
+                               int32_t W, int32_t scale, int32_t precision, float* out, void* stream)
+{
+    MRS_ARG(net != nullptr, "net is NULL");
+    MRS_ARG(lrhs && hrls && albedo && normal && out, "NULL image pointer");
+    MRS_ARG(scale == 1 || scale == 2 || scale == 4 || scale == 8, "scale must be 1, 2, 4 or 8");
+    MRS_ARG(N >= 1 && H >= 1 && W >= 1, "N, H, W must be >= 1");
+    MRS_ARG(H % scale == 0 && W % scale == 0, "H and W must be multiples of scale");
+    MRS_ARG((int64_t)N * H * W <= (int64_t(1) << 27), "N*H*W exceeds 2^27 pixels");
+    MRS_ARG(precision >= MRS_PREC_FP32 && precision <= MRS_PREC_FP8, "precision");
+    cudaStream_t st = (cudaStream_t)stream;
+    mrs_status rc;
+    if (precision == MRS_PREC_FP32)
+        rc = fuse_f32(net, lrhs, hrls, albedo, normal, N, H, W, scale, out, st);
+    else
+        rc = fuse_tc(net, lrhs, hrls, albedo, normal, N, H, W, scale, precision, out, st);
+    return rc;
+}
+
+extern "C" mrs_status mrs_image_metrics(const float* x, const float* ref, int64_t n, double l1,
+                                        double l2, double* out, void* stream)
+{
+    MRS_ARG(x && ref && out, "NULL pointer");
+    MRS_ARG(n >= 1, "n must be >= 1");
+    cudaStream_t st = (cudaStream_t)stream;
+    Scratch& S = scratch();
+    std::lock_guard<std::mutex> g(S.mu);
+    mrs_status rc = S.b.ensure(sizeof(double) * (kRedBlocks * 3 + 8));
+    if (rc != MRS_OK) return rc;
+    double* part = S.b.as<double>();
+    double* res = part + kRedBlocks * 3;
+    k_metrics_partial<<<kRedBlocks, 256, 0, st>>>(x, ref, n, l1, l2, part);
+    k_reduce_parts<<<1, 32, 0, st>>>(part, kRedBlocks, 3, res);
+    double h[3];
+    MRS_CHECK(cudaMemcpyAsync(h, res, sizeof(h), cudaMemcpyDeviceToHost, st));
+    MRS_CHECK(cudaStreamSynchronize(st));
+    double mse_s = h[0] / (double)n;
+    out[0] = mse_s == 0.0 ? INFINITY : 10.0 * log10(1.0 / mse_s);
+    out[1] = h[1] / (double)n;
+    out[2] = h[2] / (double)n;
+    return MRS_OK;
+}
+
+extern "C" mrs_status mrs_gate(const float* fused, const float* lrhs, const float* plain,
+                               int32_t N, int32_t H, int32_t W, int32_t scale, double tau,
+                               float* out, int32_t* used_plain, double* D, void* stream)
+{
+    MRS_ARG(fused && lrhs, "NULL pointer");
+    MRS_ARG(scale >= 1 && N >= 1 && H >= scale && W >= scale && H % scale == 0 && W % scale == 0,
+            "bad sizes");
+    cudaStream_t st = (cudaStream_t)stream;
+    Scratch& S = scratch();
+    std::lock_guard<std::mutex> g(S.mu);
+    mrs_status rc = S.b.ensure(sizeof(double) * (kRedBlocks + 8));
+    if (rc != MRS_OK) return rc;
+    double* part = S.b.as<double>();
+    double* res = part + kRedBlocks;
+    k_gate_partial<<<kRedBlocks, 256, 0, st>>>(fused, lrhs, N, H, W, scale, part);
+    k_reduce_parts<<<1, 32, 0, st>>>(part, kRedBlocks, 1, res);
+    double d;
+    MRS_CHECK(cudaMemcpyAsync(&d, res, sizeof(d), cudaMemcpyDeviceToHost, st));
+    MRS_CHECK(cudaStreamSynchronize(st));
+    d /= (double)N * (H / scale) * (W / scale) * 3;
+    bool use_plain = d > tau;
+    if (D) *D = d;
+    if (used_plain) *used_plain = use_plain ? 1 : 0;
+    size_t bytes = (size_t)N * H * W * 3 * 4;
+    if (out) {
+        const float* src = (use_plain && plain) ? plain : fused;
+        if (src != out) MRS_CHECK(cudaMemcpyAsync(out, src, bytes, cudaMemcpyDeviceToDevice, st));
+    }
+    return MRS_OK;
+}
+
+extern "C" mrs_status mrs_conv3x3(const float* x, int32_t N, int32_t H, int32_t W, int32_t cin,
+                                  int32_t cout, const float* w, const float* b, int32_t relu,
+                                  int32_t precision, float* out, void* stream)
+{
+    MRS_ARG(x && w && b && out, "NULL pointer");
+    MRS_ARG(N >= 1 && H >= 1 && W >= 1 && cin >= 1 && cout >= 1, "sizes must be >= 1");
+    MRS_ARG(precision == MRS_PREC_FP32 || (cin <= 64 && cout <= 64), "tensor-core conv needs cin, cout <= 64");
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t P = (size_t)N * H * W;
+    Scratch& S = scratch();
+    std::lock_guard<std::mutex> g(S.mu);
+    size_t wbytes = (size_t)cout * 9 * cin * 4;
+    size_t need = wbytes + cout * 4 + 9 * 64 * 64 * 2 + 64 * 4 * 2 + 1024 +
+                  (precision == MRS_PREC_FP32 ? 0 : P * 128) + 16;
+    mrs_status rc = S.b.ensure(need);
+    if (rc != MRS_OK) return rc;
+    uint8_t* base = S.b.as<uint8_t>();
+    float* dw = (float*)base;
+    float* db = dw + (size_t)cout * 9 * cin;
+    uint8_t* q = (uint8_t*)(((uintptr_t)(db + cout) + 255) & ~(uintptr_t)255);
+    MRS_CHECK(cudaMemcpyAsync(dw, w, wbytes, cudaMemcpyHostToDevice, st));
+    MRS_CHECK(cudaMemcpyAsync(db, b, cout * 4, cudaMemcpyHostToDevice, st));
+    if (precision == MRS_PREC_FP32) {
+        rc = conv_simt(x, cin, dw, db, cout, SIMT_PLAIN, relu, nullptr, out, nullptr, N, H, W, 1, st);
+        if (rc == MRS_OK) rc = cuda_status(cudaStreamSynchronize(st), "conv3x3 sync");
+        return rc;
+    }
+    // tensor cores: pack weights and input into the operand format
+    int nout = cout > 16 ? 64 : 16;
+    int oper = precision == MRS_PREC_BF16 ? TC_BF16 : TC_FP8;
+    void* wp = q;
+    float* bp = (float*)(q + 9 * 64 * 64 * 2);
+    float* ws = bp + 64;
+    float* amax_slot = ws + 64;   // one float, then the operand buffer (1024-aligned)
+    void* xq = (void*)(((uintptr_t)(amax_slot + 4) + 1023) & ~(uintptr_t)1023);
+    static int* err = nullptr;
+    if (!err) { MRS_CHECK(cudaMalloc(&err, 4)); MRS_CHECK(cudaMemset(err, 0, 4)); }
+    float xscale = 1.0f;
+    if (oper == TC_BF16) {
+        k_pack_bf16<<<(9 * nout * 64 + 255) / 256, 256, 0, st>>>(dw, 0, (size_t)cout * 9 * cin, cin, cout, nout,
+                                                                 (__nv_bfloat16*)wp, bp);
+    } else {
+        k_pack_fp8<<<1, 256, 0, st>>>(dw, 0, (size_t)cout * 9 * cin, cin, cout, nout, (uint8_t*)wp, bp, ws);
+    }
+    // input conversion: x fp32 [P][cin] -> [P][64] operand rows (fp8: per-tensor
+    // scale amax / 448, computed on the device)
+    if (oper == TC_FP8) {
+        float* amax = amax_slot;
+        MRS_CHECK(cudaMemsetAsync(amax, 0, 4, st));
+        k_amax_f32<<<512, 256, 0, st>>>(x, P * cin, amax);
+        float hm = 0;
+        MRS_CHECK(cudaMemcpyAsync(&hm, amax, 4, cudaMemcpyDeviceToHost, st));
+        MRS_CHECK(cudaStreamSynchronize(st));
+        xscale = hm > 0 ? hm / 448.0f : 1.0f;
+    }
+    k_to_operand<<<1024, 256, 0, st>>>(x, P, cin, xq, oper == TC_FP8, 1.0f / xscale);
+    CUtensorMap mx, mw;
+    if ((rc = tc_make_act_map(&mx, xq, N, H, W, oper)) != MRS_OK) return rc;
+    if ((rc = tc_make_w_map(&mw, wp, 9 * nout, nout, oper)) != MRS_OK) return rc;
+    TcConvArgs a;
+    memset(&a, 0, sizeof(a));
+    a.tmap_x = &mx; a.tmap_w = &mw; a.bias = bp; a.wscale = ws; a.xscale = xscale;
+    a.out = out; a.N = N; a.H = H; a.W = W; a.scale = 1; a.nout = nout; a.cout = cout;
+    a.relu = relu; a.mode = TC_PLAIN_F32; a.operand = oper; a.err = err;
+    rc = tc_conv3x3(a, st);
+    if (rc == MRS_OK) rc = cuda_status(cudaStreamSynchronize(st), "conv3x3 sync");
+    int herr = 0;
+    if (rc == MRS_OK) {
+        MRS_CHECK(cudaMemcpy(&herr, err, 4, cudaMemcpyDeviceToHost));
+        if (herr) { cudaMemset(err, 0, 4); set_error("tensor-core conv wait timed out"); return MRS_ERR_TIMEOUT; }
+    }
+    return rc;
+}
+

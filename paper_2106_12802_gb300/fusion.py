@@ -1,0 +1,99 @@
+"""Python binding of the fusion-network, metric and gate entry points.
+
+Marshalling only: every computation runs in libmrs.so's kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from ._lib import call, load
+from .render import _dev, _ptr, _stream
+
+NPARAMS = 599555
+PREC = {"fp32": 0, "bf16": 1, "fp8": 2}
+
+
+def _prec(p):
+    return PREC[p] if isinstance(p, str) else int(p)
+
+
+class Net:
+    """Fusion network handle (FP32 master weights + packed BF16/FP8 copies +
+    Adam state) created from a flat float32 parameter array."""
+
+    def __init__(self, params):
+        load()
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        assert p.size == NPARAMS, p.size
+        h = ctypes.c_void_p()
+        call("mrs_net_create", ctypes.c_void_p(p.ctypes.data), NPARAMS, ctypes.byref(h))
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            call("mrs_net_free", self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        assert p.size == NPARAMS
+        call("mrs_net_set_params", self.handle, ctypes.c_void_p(p.ctypes.data))
+
+    def get_params(self):
+        out = np.zeros(NPARAMS, np.float32)
+        call("mrs_net_get_params", self.handle, ctypes.c_void_p(out.ctypes.data))
+        return out
+
+    def fuse(self, lrhs, hrls, albedo, normal, scale, precision="bf16", out=None, stream=None):
+        """lrhs [N,h,w,3], others [N,H,W,3] float32 CUDA tensors -> [N,H,W,3]."""
+        for t in (lrhs, hrls, albedo, normal):
+            _dev(t, torch.float32)
+        N, H, W, _ = hrls.shape
+        if out is None:
+            out = torch.empty((N, H, W, 3), dtype=torch.float32, device=hrls.device)
+        call("mrs_fuse", self.handle, _ptr(lrhs), _ptr(hrls), _ptr(albedo), _ptr(normal), N, H, W,
+             scale, _prec(precision), _ptr(out), _stream(stream))
+        return out
+
+
+def conv3x3(x, w, b, relu=False, precision="fp32", stream=None):
+    """One 3x3 conv layer: x [N,H,W,cin] CUDA float32, w [cout,3,3,cin], b [cout] numpy."""
+    _dev(x, torch.float32)
+    N, H, W, cin = x.shape
+    w = np.ascontiguousarray(w, np.float32)
+    b = np.ascontiguousarray(b, np.float32)
+    cout = w.shape[0]
+    out = torch.empty((N, H, W, cout), dtype=torch.float32, device=x.device)
+    call("mrs_conv3x3", _ptr(x), N, H, W, cin, cout, ctypes.c_void_p(w.ctypes.data),
+         ctypes.c_void_p(b.ctypes.data), int(relu), _prec(precision), _ptr(out), _stream(stream))
+    return out
+
+
+def image_metrics(x, ref, lam1=0.5, lam2=0.01, stream=None):
+    """(sRGB PSNR, RelMSE, linear MSE) reduced in float64 on the GPU."""
+    _dev(x, torch.float32)
+    _dev(ref, torch.float32)
+    out = (ctypes.c_double * 3)()
+    call("mrs_image_metrics", _ptr(x), _ptr(ref), x.numel(), lam1, lam2, out, _stream(stream))
+    return float(out[0]), float(out[1]), float(out[2])
+
+
+def gate(fused, lrhs, plain, scale, tau=0.01, out=None, stream=None):
+    """Fallback gate: returns (out, used_plain, D)."""
+    N, H, W, _ = fused.shape
+    if out is None:
+        out = torch.empty_like(fused)
+    used = ctypes.c_int32()
+    D = ctypes.c_double()
+    call("mrs_gate", _ptr(fused), _ptr(lrhs), _ptr(plain), N, H, W, scale, float(tau), _ptr(out),
+         ctypes.byref(used), ctypes.byref(D), _stream(stream))
+    return out, bool(used.value), float(D.value)
