@@ -1,0 +1,396 @@
+#!/usr/bin/env python
+"""Benchmark of the multi-resolution sampling hot path on GB300.
+
+One step = one hybrid frame of the 200k-triangle procedural scene:
+  LBVH rebuild -> LRHS render 256x256 @ 64 spp -> HRLS render 1024x1024 @ 4 spp
+  (+ albedo / normal / depth) -> x4 fusion CNN in BF16 on tcgen05 -> fallback
+  gate (box-downsampled fused vs LRHS, RelMSE threshold 0.01).
+Max depth 8 with Russian roulette from bounce 3 for both renders.
+
+Prints one JSON line.  `value` is device-timed ms per frame (inputs resident in
+HBM, L2 flushed between steps); `e2e` times the same frame through the public
+API with the geometry uploaded from pinned host memory and the fused image read
+back every step.  `--impl reference` times the CPU oracle on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ms/frame at equal PSNR, hybrid vs plain HR path trace; Msamples/s; conv TFLOP/s"
+WORKLOAD = {
+    "workload": "hybrid frame: procedural 200,968-triangle scene (seed 0); LRHS 256x256 @ 64 spp + "
+                "HRLS 1024x1024 @ 4 spp (albedo/normal/depth), max depth 8, roulette from bounce 3; "
+                "x4 fusion CNN (12->64, 8 residual blocks, 64->3) in BF16 on tcgen05; fallback gate",
+    "scene_seed": 0, "lrhs": [256, 256, 64], "hrls": [1024, 1024, 4], "scale": 4,
+    "max_depth": 8, "rr_start": 3, "precision": "bf16", "net_init": "kaiming-normal seed 0",
+    "l2": "flushed between steps (512 MiB write)",
+}
+LR, HR, S = 256, 1024, 4
+SPP_LR, SPP_HR, DEPTH, RR = 64, 4, 8, 3
+CONV_FLOP_PER_PX = 2 * 9 * (12 * 64 + 16 * 64 * 64 + 64 * 3)      # 1,196,928
+# FP32 operations per traversal step, counted from the kernel source
+# (pt.cu: slab() on both children of a node; intersect() per triangle)
+OPS_PER_NODE_VISIT = 52
+OPS_PER_TRI_TEST = 50
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        d["source"] = "measured"
+        return d
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0, "source": "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return None
+        mhz = [float(r[1]) for r in self.rows if len(r) > 2 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 2 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if len(r) > 5 + i and r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(mhz)) if mhz else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def _traffic(kernel, src):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if the
+    kernel source is unchanged since the capture (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f).get(kernel)
+    if not d:
+        return None
+    with open(os.path.join(ROOT, "paper_2106_12802_gb300", "csrc", src), "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    return d["dram_bytes_per_launch"] if d.get("src_sha256_16") == sha else None
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle (bounded samples of the same frame)
+# ----------------------------------------------------------------------------
+def oracle_frame_sample(desc, params, lr_rows=2, hr_rows=4, cnn_rows=4, seed=0):
+    """Times the oracle on a bounded sample of the hybrid frame and scales each
+    part to a whole frame.  Returns (ms_per_frame, detail)."""
+    import oracle
+    from oracle import cnn
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.lbvh(desc["V"])
+    t_build = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.render(desc, LR, LR, SPP_LR, DEPTH, RR, seed, rows=(LR // 2, LR // 2 + lr_rows))
+    t_lr = max(time.perf_counter() - t0 - t_build, 1e-9)
+    t0 = time.perf_counter()
+    oracle.render(desc, HR, HR, SPP_HR, DEPTH, RR, seed + 1, rows=(HR // 2, HR // 2 + hr_rows))
+    t_hr = max(time.perf_counter() - t0 - t_build, 1e-9)
+    rng = np.random.default_rng(0)
+    halo = 18                      # receptive field of the 18 stacked 3x3 convs
+    rows = cnn_rows + 2 * halo
+    lr = rng.uniform(0, 2, (1, (rows + S - 1) // S, HR // S, 3))
+    hr = rng.uniform(0, 2, (1, lr.shape[1] * S, HR, 3))
+    t0 = time.perf_counter()
+    cnn.forward(params, lr, hr, hr, hr, S)
+    t_cnn = time.perf_counter() - t0
+    ms = 1e3 * (2 * t_build + t_lr * LR / lr_rows + t_hr * HR / hr_rows + t_cnn * HR / hr.shape[1])
+    detail = (f"LBVH build x2; LRHS rows {lr_rows}/{LR} and HRLS rows {hr_rows}/{HR} rendered "
+              f"(scaled by rows); FP64 CNN on a {hr.shape[1]}x{HR} strip (scaled by rows)")
+    return ms, detail
+
+
+def cpu_cores():
+    import oracle
+    try:
+        import threadpoolctl
+        blas = max([i.get("num_threads", 1) for i in threadpoolctl.threadpool_info()] or [1])
+    except Exception:
+        blas = os.cpu_count() or 1
+    return max(oracle.num_threads(), blas)
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import oracle
+    from oracle import cnn
+    from synth import scenes
+    desc = scenes.procedural(0)
+    params = cnn.kaiming(0)
+    oracle.build()
+    for _ in range(args.warmup):
+        oracle_frame_sample(desc, params, 1, 1, 1)
+    times = []
+    t_all = time.perf_counter()
+    for k in range(args.steps):
+        ms, detail = oracle_frame_sample(desc, params, 1, 2, 2, seed=k)
+        times.append(ms)
+    wall = time.perf_counter() - t_all
+    value = float(np.mean(times))
+    cores = cpu_cores()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "ms/frame",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": value,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64",
+        "data": "synthetic", "config": WORKLOAD,
+        "cpu_baseline": {"value": value, "unit": "ms/frame", "cores": cores, "kind": "oracle",
+                         "sample": detail + f"; {args.steps} samples, {wall:.1f} s wall"},
+        "e2e": {"value": value, "unit": "ms/frame", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+def run_gpu(args, rank, world):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2106_12802_gb300 as mrs
+    from oracle import cnn
+    from synth import scenes
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    mrs.load()
+    stream = torch.cuda.current_stream()
+    desc = scenes.procedural(0)
+    scene = mrs.Scene(desc)
+    params = cnn.kaiming(0).astype(np.float32)
+    net = mrs.Net(params)
+
+    lrhs = torch.empty((1, LR, LR, 3), device=dev)
+    hrls = torch.empty((1, HR, HR, 3), device=dev)
+    alb = torch.empty((1, HR, HR, 3), device=dev)
+    nrm = torch.empty((1, HR, HR, 3), device=dev)
+    dep = torch.empty((1, HR, HR), device=dev)
+    fused = torch.empty((1, HR, HR, 3), device=dev)
+    out = torch.empty((1, HR, HR, 3), device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    gate_info = {}
+
+    def frame(seed):
+        scene.rebuild()
+        mrs.render(scene, LR, LR, SPP_LR, DEPTH, RR, seed, out={"radiance": lrhs[0]})
+        mrs.render(scene, HR, HR, SPP_HR, DEPTH, RR, seed + 1,
+                   out={"radiance": hrls[0], "albedo": alb[0], "normal": nrm[0], "depth": dep[0]})
+        net.fuse(lrhs, hrls, alb, nrm, S, precision="bf16", out=fused)
+        _, used, D = mrs.gate(fused, lrhs, None, S, 0.01, out=out)
+        gate_info.update(used_plain=used, D=D)
+
+    for k in range(args.warmup):
+        frame(1000 + k)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+
+    # ---- timed region: device-resident inputs, L2 flushed between steps -----
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    mrs.profile_read()
+    mrs.profile_enable(True)
+    launches0 = mrs.kernel_launches()
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            frame(k)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    launches = (mrs.kernel_launches() - launches0) // max(args.steps, 1)
+    mrs.profile_enable(False)
+    prof = mrs.profile_read()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_local = float(np.sum(step_ms))
+    if world > 1:
+        t = torch.tensor([t_local], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_local = float(t.item())
+        dist.barrier()
+    ms_frame = t_local / (args.steps * world)
+
+    # ---- end to end through the public API with host buffers -----------------
+    Vh = torch.from_numpy(np.ascontiguousarray(desc["V"], np.float32)).pin_memory()
+    out_h = torch.empty((1, HR, HR, 3), dtype=torch.float32).pin_memory()
+
+    def frame_e2e(seed):
+        scene.update_vertices(Vh)
+        mrs.render(scene, LR, LR, SPP_LR, DEPTH, RR, seed, out={"radiance": lrhs[0]})
+        mrs.render(scene, HR, HR, SPP_HR, DEPTH, RR, seed + 1,
+                   out={"radiance": hrls[0], "albedo": alb[0], "normal": nrm[0], "depth": dep[0]})
+        net.fuse(lrhs, hrls, alb, nrm, S, precision="bf16", out=fused)
+        mrs.gate(fused, lrhs, None, S, 0.01, out=out)
+        out_h.copy_(out, non_blocking=True)
+        torch.cuda.synchronize()
+
+    frame_e2e(0)
+    e2e_steps = max(3, min(args.steps, 10))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        frame_e2e(k)
+    e2e_ms = 1e3 * (time.perf_counter() - t0) / e2e_steps
+    h2d = Vh.numel() * 4
+    d2h = out_h.numel() * 4
+
+    # ---- context measurements (outside the timed region) --------------------
+    extra = {}
+    if rank == 0 and not args.quick:
+        stats_lr = mrs.render_stats(scene, LR, LR, SPP_LR, DEPTH, RR, 0)
+        stats_hr = mrs.render_stats(scene, HR, HR, SPP_HR, DEPTH, RR, 1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        plain = mrs.render(scene, HR, HR, 64, DEPTH, RR, 7)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        plain = mrs.render(scene, HR, HR, 64, DEPTH, RR, 8, out=plain)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pms = e0.elapsed_time(e1)
+        rays = int(plain["counts"].sum().item() + plain["shadow_counts"].sum().item())
+        extra["plain_path_trace_1024_64spp"] = {
+            "ms": pms, "msamples_per_s": HR * HR * 64 / pms / 1e3, "mrays_per_s": rays / pms / 1e3}
+    else:
+        stats_lr = stats_hr = None
+
+    peaks = _peaks()
+    conv_ms = prof["conv_tc"][0] / args.steps
+    conv_flop = CONV_FLOP_PER_PX * HR * HR
+    family_ms = {k: v[0] / args.steps for k, v in prof.items() if v[1]}
+    dom = max(family_ms, key=family_ms.get)
+    roofline = None
+    if dom == "conv_tc":
+        peak = peaks["bf16_tflops_sustained"]
+        ach = conv_flop / (conv_ms * 1e-3) / 1e12
+        roofline = {"kernel": "k_conv_tc (tcgen05 implicit-GEMM 3x3 conv)", "bound": "tensor",
+                    "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                    "traffic": _traffic("k_conv_tc", "conv_tc.cu"),
+                    "peak_source": peaks["source"] + " bf16 sustained"}
+    elif dom in ("trace", "shadow") and stats_lr:
+        key = "" if dom == "trace" else "shadow_"
+        ops = OPS_PER_NODE_VISIT * (stats_lr[key + "visits"] + stats_hr[key + "visits"]) + \
+            OPS_PER_TRI_TEST * (stats_lr[key + "tests"] + stats_hr[key + "tests"])
+        kms = family_ms[dom]
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak = sms * 128 * peaks["sm_max_mhz"] * 1e6 / 1e12
+        ach = ops / (kms * 1e-3) / 1e12
+        roofline = {"kernel": f"k_{dom} (BVH traversal)", "bound": "alu", "achieved": ach,
+                    "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                    "traffic": _traffic(f"k_{dom}", "pt.cu"),
+                    "peak_source": f"{sms} SMs x 128 FP32 lanes x {peaks['sm_max_mhz']} MHz "
+                                   "(non-FMA ops; the kernel is built with --fmad=false)",
+                    "ops_per_frame": ops,
+                    "node_visits_per_frame": stats_lr[key + "visits"] + stats_hr[key + "visits"],
+                    "tri_tests_per_frame": stats_lr[key + "tests"] + stats_hr[key + "tests"]}
+
+    if rank == 0:
+        cpu = None
+        if not args.quick and not args.no_cpu_baseline:
+            cms, detail = oracle_frame_sample(desc, cnn.kaiming(0), 2, 4, 4)
+            cpu = {"value": cms, "unit": "ms/frame", "cores": cpu_cores(), "kind": "oracle",
+                   "sample": detail}
+        line = {
+            "metric": METRIC, "value": ms_frame, "unit": "ms/frame", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_local / args.steps,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+            "data": "synthetic", "config": WORKLOAD,
+            "parallelism": "replicas" if world > 1 else "single-gpu",
+            "e2e": {"value": e2e_ms, "unit": "ms/frame", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "roofline": roofline, "cpu_baseline": cpu, "clocks": clk.summary(),
+            "gpu_launches": int(launches),
+            "stage_ms_per_frame": {k: round(v, 4) for k, v in family_ms.items()},
+            "conv_tflops": conv_flop / (conv_ms * 1e-3) / 1e12 if conv_ms else None,
+            "gate": gate_info, **extra,
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mrs", choices=["mrs", "reference"])
+    ap.add_argument("--quick", action="store_true", help="skip context measurements")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "gloo" if args.impl == "reference" else "nccl"
+        if backend == "nccl":
+            import torch
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group(backend)
+    if args.impl == "reference":
+        rc = run_reference(args, rank, world)
+    else:
+        rc = run_gpu(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

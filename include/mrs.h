@@ -50,6 +50,9 @@ typedef struct mrs_net_s* mrs_net;
 const char* mrs_status_string(mrs_status s);
 /* Last error detail recorded by this thread (static per-thread buffer). */
 const char* mrs_last_error(void);
+/* Number of CUDA kernels this library has launched in this process so far
+ * (instrumentation for benchmarks; no paper counterpart). */
+uint64_t mrs_kernel_launches(void);
 
 /* ------------------------------------------------------------------------
  * Scene + LBVH.  The renderer that produces LRHS and HRLS (Sec. 1, Sec. 3.2)
@@ -82,6 +85,12 @@ mrs_status mrs_build_scene(const float* V, int32_t n_tris, const int32_t* tri_ma
 /* Re-run the GPU LBVH build (Morton codes, sort, radix tree, refit) over the
  * scene's resident triangles, asynchronously on `stream`. */
 mrs_status mrs_scene_rebuild(mrs_scene scene, void* stream);
+
+/* Replace the triangle vertices (HOST float [n][3][3], n equal to the scene's
+ * triangle count; materials and lights unchanged) and rebuild the LBVH, both
+ * asynchronously on `stream` (an animated scene's per-frame update).  The
+ * host buffer must stay valid until the stream reaches this point. */
+mrs_status mrs_scene_update_vertices(mrs_scene scene, const float* V, int32_t n, void* stream);
 
 mrs_status mrs_free_scene(mrs_scene scene);
 
@@ -127,6 +136,24 @@ mrs_status mrs_render(mrs_scene scene, int32_t W, int32_t H, int32_t spp, int32_
                       int32_t rr_start, uint64_t seed, float* radiance, float* albedo,
                       float* normal, float* depth, uint64_t* counts, uint64_t* shadow_counts,
                       void* stream);
+
+/* The same render with instrumented traversal: stats device uint64[4] receives
+ * BVH node visits and triangle tests of the closest-hit traversals, then of
+ * the shadow (any-hit) traversals.  The radiance equals mrs_render's.  For
+ * measuring algorithmic work (roofline accounting); no paper counterpart. */
+mrs_status mrs_render_stats(mrs_scene scene, int32_t W, int32_t H, int32_t spp, int32_t max_depth,
+                            int32_t rr_start, uint64_t seed, float* radiance, uint64_t* stats,
+                            void* stream);
+
+/* Per-kernel CUDA-event timing: when enabled, the library records an event
+ * pair on the launching stream around each launch of the kernels below, and
+ * mrs_profile_read (which synchronises on those events) returns and clears
+ * the total milliseconds and launch count of one kernel family:
+ * 0 closest-hit traversal, 1 shade, 2 shadow traversal, 3 ray generation,
+ * 4 accumulation, 5 LBVH build (whole), 6 tensor-core conv, 7 SIMT conv,
+ * 8 fusion input, 9 metrics, 10 training kernels.  Instrumentation only. */
+mrs_status mrs_profile_enable(int32_t on);
+mrs_status mrs_profile_read(int32_t kernel, double* total_ms, int64_t* launches);
 
 /* Paths per wave for subsequent mrs_render calls on this scene (rounded to
  * whole samples of the image; default 16M paths).  For tests and tuning. */

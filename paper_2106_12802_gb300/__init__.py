@@ -4,6 +4,7 @@ The compute path is libmrs.so (hand-written CUDA for sm_103a) behind the C ABI
 in include/mrs.h; this package is a thin binding over it.  PyTorch is used for
 device memory and streams only.
 """
-from ._lib import MrsError, library_path, load  # noqa: F401
-from .render import Scene, philox_uniforms, render  # noqa: F401
+from ._lib import MrsError, kernel_launches, library_path, load  # noqa: F401
+from .render import (PROFILE_KERNELS, Scene, philox_uniforms, profile_enable,  # noqa: F401
+                     profile_read, render, render_stats)
 from .fusion import NPARAMS, Net, conv3x3, gate, image_metrics  # noqa: F401

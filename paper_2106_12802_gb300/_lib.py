@@ -25,11 +25,15 @@ F64 = ctypes.c_double
 SIGS = {
     "mrs_build_scene": [P, I32, P, P, P, I32, P, I32, P, P, P, P],
     "mrs_scene_rebuild": [P, P],
+    "mrs_scene_update_vertices": [P, P, I32, P],
     "mrs_free_scene": [P],
     "mrs_scene_export_bvh": [P, P, P, P, P, P, P],
     "mrs_cast": [P, P, P, I32, P, P, P],
     "mrs_render": [P, I32, I32, I32, I32, I32, U64, P, P, P, P, P, P, P],
     "mrs_scene_set_wave": [P, I64],
+    "mrs_render_stats": [P, I32, I32, I32, I32, I32, U64, P, P, P],
+    "mrs_profile_enable": [I32],
+    "mrs_profile_read": [I32, P, P],
     "mrs_philox_uniforms": [P, I32, U64, P, P],
     "mrs_net_create": [P, I32, P],
     "mrs_net_free": [P],
@@ -41,8 +45,14 @@ SIGS = {
     "mrs_conv3x3": [P, I32, I32, I32, I32, I32, P, P, I32, I32, P, P],
     "mrs_status_string": [I32],
     "mrs_last_error": [],
+    "mrs_kernel_launches": [],
 }
-_RES = {"mrs_status_string": ctypes.c_char_p, "mrs_last_error": ctypes.c_char_p}
+_RES = {"mrs_status_string": ctypes.c_char_p, "mrs_last_error": ctypes.c_char_p,
+        "mrs_kernel_launches": ctypes.c_uint64}
+
+
+def kernel_launches() -> int:
+    return int(load().mrs_kernel_launches())
 
 
 class MrsError(RuntimeError):

@@ -8,6 +8,9 @@
 #include <stdarg.h>
 #include <string.h>
 
+#include <mutex>
+#include <vector>
+
 #include "common.cuh"
 
 namespace mrs {
@@ -21,6 +24,40 @@ void set_error(const char* fmt, ...)
     va_end(ap);
 }
 const char* last_error() { return g_err; }
+
+std::atomic<unsigned long long>& launch_counter()
+{
+    static std::atomic<unsigned long long> c{0};
+    return c;
+}
+
+namespace {
+struct Prof {
+    std::mutex mu;
+    bool on = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[PK_COUNT];
+};
+Prof& prof()
+{
+    static Prof p;
+    return p;
+}
+}  // namespace
+
+bool prof_on() { return prof().on; }
+cudaEvent_t prof_record(cudaStream_t st)
+{
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    cudaEventRecord(e, st);
+    return e;
+}
+void prof_push(int k, cudaEvent_t a, cudaEvent_t b)
+{
+    if (!b) { cudaEventDestroy(a); return; }
+    std::lock_guard<std::mutex> g(prof().mu);
+    prof().ev[k].push_back({a, b});
+}
 
 namespace {
 
@@ -292,9 +329,12 @@ mrs_status build_lbvh(mrs_scene_s* S, cudaStream_t st)
     int* va = (int*)p; p += sizeof(int) * (size_t)n;
     int* vb = (int*)p;
 
+    cudaEvent_t lbvh_a = prof_on() ? prof_record(st) : nullptr;
     k_bounds_partial<<<nparts, kBlock, 0, st>>>(S->V, n, part);
+    MRS_LAUNCHED(1);
     k_morton<<<min(blocks_for(n, kBlock), 8 * sm_count()), kBlock, 0, st>>>(S->V, n, part, nparts,
                                                                         S->morton, ka, va);
+    MRS_LAUNCHED(1);
     // 30-bit codes: digits at bits 0, 8, 16, 24 (4 passes, ends back in ka/va)
     for (int pass = 0; pass < 4; ++pass) {
         int shift = pass * 8;
@@ -303,19 +343,28 @@ mrs_status build_lbvh(mrs_scene_s* S, cudaStream_t st)
         int* vin = (pass & 1) ? vb : va;
         int* vout = (pass & 1) ? va : vb;
         k_sort_hist<<<ntiles, kBlock, 0, st>>>(kin, n, shift, counts, ntiles);
+        MRS_LAUNCHED(1);
         k_sort_scan<<<1, 1024, 0, st>>>(counts, 256 * ntiles);
+        MRS_LAUNCHED(1);
         k_sort_scatter<<<ntiles, kBlock, 0, st>>>(kin, vin, kout, vout, n, shift, counts, ntiles);
+        MRS_LAUNCHED(1);
     }
     MRS_CHECK(cudaMemcpyAsync(S->skeys, ka, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st));
     MRS_CHECK(cudaMemcpyAsync(S->order, va, sizeof(int) * n, cudaMemcpyDeviceToDevice, st));
-    if (n > 1)
+    if (n > 1) {
         k_karras<<<blocks_for(n - 1, kBlock), kBlock, 0, st>>>(S->skeys, S->order, n, S->left,
                                                               S->right, S->parent);
+        MRS_LAUNCHED(1);
+    }
     k_leaves<<<blocks_for(n, kBlock), kBlock, 0, st>>>(S->V, S->tri_mat, S->tri_light, S->order,
                                                        n, S->tris, S->tri_ml, S->box, S->visit);
-    if (n > 1)
+    MRS_LAUNCHED(1);
+    if (n > 1) {
         k_refit<<<blocks_for(n, kBlock), kBlock, 0, st>>>(n, S->left, S->right, S->parent, S->box,
                                                           S->visit, S->nodes);
+        MRS_LAUNCHED(1);
+    }
+    if (lbvh_a) prof_push(PK_LBVH, lbvh_a, prof_record(st));
     return cuda_status(cudaGetLastError(), "lbvh launch");
 }
 
@@ -344,6 +393,35 @@ template <class T> mrs_status dalloc(T** p, size_t count)
 using namespace mrs;
 
 extern "C" const char* mrs_last_error(void) { return mrs::last_error(); }
+
+extern "C" uint64_t mrs_kernel_launches(void) { return mrs::launch_counter().load(); }
+
+extern "C" mrs_status mrs_profile_enable(int32_t on)
+{
+    mrs::prof().on = on != 0;
+    return MRS_OK;
+}
+
+extern "C" mrs_status mrs_profile_read(int32_t kernel, double* total_ms, int64_t* launches)
+{
+    MRS_ARG(kernel >= 0 && kernel < mrs::PK_COUNT, "kernel id out of range");
+    MRS_ARG(total_ms && launches, "NULL output");
+    std::lock_guard<std::mutex> g(mrs::prof().mu);
+    auto& v = mrs::prof().ev[kernel];
+    double tot = 0;
+    for (auto& pr : v) {
+        MRS_CHECK(cudaEventSynchronize(pr.second));
+        float ms = 0;
+        MRS_CHECK(cudaEventElapsedTime(&ms, pr.first, pr.second));
+        tot += ms;
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
+    *total_ms = tot;
+    *launches = (int64_t)v.size();
+    v.clear();
+    return MRS_OK;
+}
 
 extern "C" const char* mrs_status_string(mrs_status s)
 {
@@ -425,6 +503,18 @@ extern "C" mrs_status mrs_scene_rebuild(mrs_scene S, void* stream)
 {
     MRS_ARG(S != nullptr, "scene is NULL");
     return build_lbvh(S, (cudaStream_t)stream);
+}
+
+extern "C" mrs_status mrs_scene_update_vertices(mrs_scene S, const float* V, int32_t n,
+                                                void* stream)
+{
+    MRS_ARG(S != nullptr, "scene is NULL");
+    MRS_ARG(n == S->n, "n must equal the scene's triangle count");
+    MRS_ARG(n == 0 || V != nullptr, "V is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n > 0)
+        MRS_CHECK(cudaMemcpyAsync(S->V, V, sizeof(float) * 9 * (size_t)n, cudaMemcpyHostToDevice, st));
+    return build_lbvh(S, st);
 }
 
 extern "C" mrs_status mrs_free_scene(mrs_scene S)

@@ -8,9 +8,31 @@
 
 #include "../../include/mrs.h"
 
+#include <atomic>
+
 namespace mrs {
 
 void set_error(const char* fmt, ...);
+
+// number of kernels this library has launched (process-wide)
+std::atomic<unsigned long long>& launch_counter();
+#define MRS_LAUNCHED(n) (::mrs::launch_counter().fetch_add((n), std::memory_order_relaxed))
+
+// Optional per-kernel CUDA-event timing (off unless mrs_profile_enable(1)):
+// events are recorded on the launching stream around each timed launch.
+enum ProfKernel {
+    PK_TRACE = 0, PK_SHADE, PK_SHADOW, PK_RAYGEN, PK_ACCUM, PK_LBVH, PK_CONV_TC, PK_CONV_SIMT,
+    PK_INPUT, PK_METRICS, PK_TRAIN, PK_COUNT
+};
+bool prof_on();
+cudaEvent_t prof_record(cudaStream_t st);
+void prof_push(int kernel, cudaEvent_t a, cudaEvent_t b);
+#define MRS_TIMED(kid, st, ...)                                             \
+    do {                                                                    \
+        cudaEvent_t _mrs_a = ::mrs::prof_on() ? ::mrs::prof_record(st) : nullptr; \
+        __VA_ARGS__;                                                        \
+        if (_mrs_a) ::mrs::prof_push((kid), _mrs_a, ::mrs::prof_record(st)); \
+    } while (0)
 
 inline mrs_status cuda_status(cudaError_t e, const char* what)
 {

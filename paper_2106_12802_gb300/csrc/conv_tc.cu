@@ -402,7 +402,8 @@ mrs_status launch(const TcConvArgs& a, cudaStream_t st)
     int ntiles = a.N * a.H * ((a.W + kTileM - 1) / kTileM);
     int grid = ntiles < sm_count() ? ntiles : sm_count();
     if (grid < 1) return MRS_OK;
-    k_conv_tc<NOUT, OPER><<<grid, kThreads, smem, st>>>(*a.tmap_x, *a.tmap_w, a, stages);
+    MRS_TIMED(PK_CONV_TC, st, (k_conv_tc<NOUT, OPER><<<grid, kThreads, smem, st>>>(*a.tmap_x, *a.tmap_w, a, stages)));
+    MRS_LAUNCHED(1);
     return cuda_status(cudaGetLastError(), "conv launch");
 }
 

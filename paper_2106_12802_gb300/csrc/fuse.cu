@@ -204,7 +204,8 @@ mrs_status conv_simt(const float* x, int cin, const float* w, const float* b, in
                      int W, int s, cudaStream_t st)
 {
     dim3 grid((W + kTX - 1) / kTX, (H + kTY - 1) / kTY, N * ((cout + kCT - 1) / kCT));
-    k_conv_simt<<<grid, kTX * kTY, 0, st>>>(x, cin, w, b, cout, mode, relu, res, out, lrhs, H, W, s);
+    MRS_TIMED(PK_CONV_SIMT, st, k_conv_simt<<<grid, kTX * kTY, 0, st>>>(x, cin, w, b, cout, mode, relu, res, out, lrhs, H, W, s));
+    MRS_LAUNCHED(1);
     return cuda_status(cudaGetLastError(), "conv_simt launch");
 }
 
@@ -400,6 +401,7 @@ mrs_status pack_bf16(mrs_net_s* net, cudaStream_t st)
         k_pack_bf16<<<(9 * nout * 64 + 255) / 256, 256, 0, st>>>(
             net->master, L[l].woff, L[l].boff, L[l].cin, L[l].cout, nout,
             net->wbf + (size_t)l * 9 * 64 * 64, net->bias + l * 64);
+        MRS_LAUNCHED(1);
         mrs_status s = tc_make_w_map(&net->wmap_bf[l], net->wbf + (size_t)l * 9 * 64 * 64, 9 * nout, nout, TC_BF16);
         if (s != MRS_OK) return s;
     }
@@ -416,6 +418,7 @@ mrs_status pack_fp8(mrs_net_s* net, cudaStream_t st)
         k_pack_fp8<<<1, 256, 0, st>>>(net->master, L[l].woff, L[l].boff, L[l].cin, L[l].cout, nout,
                                       net->wf8 + (size_t)l * 9 * 64 * 64, net->bias8 + l * 64,
                                       net->wscale + l * 64);
+        MRS_LAUNCHED(1);
         mrs_status s = tc_make_w_map(&net->wmap_f8[l], net->wf8 + (size_t)l * 9 * 64 * 64, 9 * nout, nout, TC_FP8);
         if (s != MRS_OK) return s;
     }
@@ -435,6 +438,7 @@ mrs_status fuse_f32(mrs_net_s* net, const float* lrhs, const float* hrls, const 
     const auto& L = shapes();
     k_input_f32<<<(int)((P + 255) / 256 < 65535 ? (P + 255) / 256 : 65535), 256, 0, st>>>(
         lrhs, hrls, alb, nrm, H, W, s, P, x0);
+    MRS_LAUNCHED(1);
     rc = conv_simt(x0, 12, net->master + L[0].woff, net->master + L[0].boff, 64, SIMT_PLAIN, 1,
                    nullptr, h, nullptr, N, H, W, s, st);
     for (int k = 0; k < 8 && rc == MRS_OK; ++k) {
@@ -482,6 +486,7 @@ mrs_status fuse_tc(mrs_net_s* net, const float* lrhs, const float* hrls, const f
     int g = (int)((P + 255) / 256 < 65535 ? (P + 255) / 256 : 65535);
     k_input_q<<<g, 256, 0, st>>>(lrhs, hrls, alb, nrm, H, W, s, P, f8 ? (void*)x08 : x0, f8 ? 1 : 0,
                                  f8 ? 1.0f / net->xscale[0] : 1.0f);
+    MRS_LAUNCHED(1);
     if ((rc = cuda_status(cudaGetLastError(), "input")) != MRS_OK) return rc;
     CUtensorMap mx, mh, mr;
     int oper = f8 ? TC_FP8 : TC_BF16;
@@ -519,6 +524,7 @@ mrs_status fuse_tc(mrs_net_s* net, const float* lrhs, const float* hrls, const f
             const void* nxt = (l % 2 == 1) ? r : h;
             float* am = net->aux.as<float>() + l + 1;
             k_amax_bf16<<<512, 256, 0, st>>>((const __nv_bfloat16*)nxt, P * 64, am);
+            MRS_LAUNCHED(1);
             rc = cuda_status(cudaGetLastError(), "amax");
         }
     }
@@ -540,6 +546,7 @@ mrs_status calibrate_fp8(mrs_net_s* net, const float* lrhs, const float* hrls, c
     if (rc != MRS_OK) return rc;
     // layer 0 input: amax of the bf16 fusion input x0
     k_amax_bf16<<<512, 256, 0, st>>>(net->act.as<__nv_bfloat16>(), P * 64, net->aux.as<float>());
+    MRS_LAUNCHED(1);
     float am[kLayers];
     MRS_CHECK(cudaMemcpyAsync(am, net->aux.p, sizeof(am), cudaMemcpyDeviceToHost, st));
     MRS_CHECK(cudaStreamSynchronize(st));
@@ -644,7 +651,9 @@ extern "C" mrs_status mrs_image_metrics(const float* x, const float* ref, int64_
     double* part = S.b.as<double>();
     double* res = part + kRedBlocks * 3;
     k_metrics_partial<<<kRedBlocks, 256, 0, st>>>(x, ref, n, l1, l2, part);
+    MRS_LAUNCHED(1);
     k_reduce_parts<<<1, 32, 0, st>>>(part, kRedBlocks, 3, res);
+    MRS_LAUNCHED(1);
     double h[3];
     MRS_CHECK(cudaMemcpyAsync(h, res, sizeof(h), cudaMemcpyDeviceToHost, st));
     MRS_CHECK(cudaStreamSynchronize(st));
@@ -670,7 +679,9 @@ extern "C" mrs_status mrs_gate(const float* fused, const float* lrhs, const floa
     double* part = S.b.as<double>();
     double* res = part + kRedBlocks;
     k_gate_partial<<<kRedBlocks, 256, 0, st>>>(fused, lrhs, N, H, W, scale, part);
+    MRS_LAUNCHED(1);
     k_reduce_parts<<<1, 32, 0, st>>>(part, kRedBlocks, 1, res);
+    MRS_LAUNCHED(1);
     double d;
     MRS_CHECK(cudaMemcpyAsync(&d, res, sizeof(d), cudaMemcpyDeviceToHost, st));
     MRS_CHECK(cudaStreamSynchronize(st));
@@ -727,8 +738,10 @@ extern "C" mrs_status mrs_conv3x3(const float* x, int32_t N, int32_t H, int32_t 
     if (oper == TC_BF16) {
         k_pack_bf16<<<(9 * nout * 64 + 255) / 256, 256, 0, st>>>(dw, 0, (size_t)cout * 9 * cin, cin, cout, nout,
                                                                  (__nv_bfloat16*)wp, bp);
+        MRS_LAUNCHED(1);
     } else {
         k_pack_fp8<<<1, 256, 0, st>>>(dw, 0, (size_t)cout * 9 * cin, cin, cout, nout, (uint8_t*)wp, bp, ws);
+        MRS_LAUNCHED(1);
     }
     // input conversion: x fp32 [P][cin] -> [P][64] operand rows (fp8: per-tensor
     // scale amax / 448, computed on the device)
@@ -736,12 +749,14 @@ extern "C" mrs_status mrs_conv3x3(const float* x, int32_t N, int32_t H, int32_t 
         float* amax = amax_slot;
         MRS_CHECK(cudaMemsetAsync(amax, 0, 4, st));
         k_amax_f32<<<512, 256, 0, st>>>(x, P * cin, amax);
+        MRS_LAUNCHED(1);
         float hm = 0;
         MRS_CHECK(cudaMemcpyAsync(&hm, amax, 4, cudaMemcpyDeviceToHost, st));
         MRS_CHECK(cudaStreamSynchronize(st));
         xscale = hm > 0 ? hm / 448.0f : 1.0f;
     }
     k_to_operand<<<1024, 256, 0, st>>>(x, P, cin, xq, oper == TC_FP8, 1.0f / xscale);
+    MRS_LAUNCHED(1);
     CUtensorMap mx, mw;
     if ((rc = tc_make_act_map(&mx, xq, N, H, W, oper)) != MRS_OK) return rc;
     if ((rc = tc_make_w_map(&mw, wp, 9 * nout, nout, oper)) != MRS_OK) return rc;

@@ -137,8 +137,9 @@ __device__ __forceinline__ float slab(float lx, float ly, float lz, float hx, fl
 }
 
 // closest hit (ties to the smaller triangle index) or any hit below tmax
-template <bool kAny>
-__device__ int traverse(const SceneView& S, V3 o, V3 d, float tmax, float& t_out)
+template <bool kAny, bool kCount = false>
+__device__ int traverse(const SceneView& S, V3 o, V3 d, float tmax, float& t_out,
+                        unsigned long long* nvisit = nullptr, unsigned long long* ntest = nullptr)
 {
     const int n = S.n;
     int best = -1, best_prim = 0x7fffffff;
@@ -156,6 +157,7 @@ __device__ int traverse(const SceneView& S, V3 o, V3 d, float tmax, float& t_out
     int node = 0;
     while (true) {
         if (node < n - 1) {
+            if (kCount) ++*nvisit;
             const float4* nd = S.nodes + 4 * node;
             float4 a = __ldg(nd), b = __ldg(nd + 1), c = __ldg(nd + 2), e = __ldg(nd + 3);
             float t0 = slab(a.x, a.y, a.z, a.w, b.x, b.y, o, inv, bt);
@@ -172,6 +174,7 @@ __device__ int traverse(const SceneView& S, V3 o, V3 d, float tmax, float& t_out
             if (h1) { node = c1; continue; }
         } else {
             int k = node - (n - 1), prim;
+            if (kCount) ++*ntest;
             float t = intersect(o, d, S.tris + 3 * k, kAny ? tmax : T_INF, prim);
             if (t > 0.0f) {
                 if (kAny) { t_out = t; return k; }
@@ -301,6 +304,7 @@ struct WaveParams {
     uint2 key;
     uint32_t* cnt;       // [max_depth + 2] extension rays per bounce
     uint32_t* scnt;      // [max_depth + 1] shadow rays per bounce
+    unsigned long long* stats;   // counting variant: node visits / triangle tests (closest, shadow)
 };
 
 __global__ void __launch_bounds__(kThreads) k_raygen(WaveParams w)
@@ -328,8 +332,10 @@ __global__ void __launch_bounds__(kThreads) k_raygen(WaveParams w)
     }
 }
 
+template <bool kCount>
 __global__ void __launch_bounds__(kThreads) k_trace(WaveParams w, int b)
 {
+    unsigned long long nv = 0, nt = 0;
     PathSoA& P = w.P;
     const int count = (int)*(volatile uint32_t*)&w.cnt[b];
     const int* q = (b & 1) ? P.q1 : P.q0;
@@ -337,10 +343,11 @@ __global__ void __launch_bounds__(kThreads) k_trace(WaveParams w, int b)
         int p = b == 0 ? i : q[i];
         V3 o = mk(P.ox[p], P.oy[p], P.oz[p]), d = mk(P.dx[p], P.dy[p], P.dz[p]);
         float t = -1.0f;
-        int k = traverse<false>(w.S, o, d, T_INF, t);
+        int k = traverse<false, kCount>(w.S, o, d, T_INF, t, &nv, &nt);
         P.hit_t[p] = t;
         P.hit_id[p] = k;
     }
+    if (kCount) { atomicAdd(&w.stats[0], nv); atomicAdd(&w.stats[1], nt); }
 }
 
 // warp-aggregated append: returns this lane's slot (valid only where flag)
@@ -507,20 +514,23 @@ __global__ void __launch_bounds__(kThreads) k_shade(WaveParams w, int b)
     }
 }
 
+template <bool kCount>
 __global__ void __launch_bounds__(kThreads) k_shadow(WaveParams w, int b)
 {
+    unsigned long long nv = 0, nt = 0;
     PathSoA& P = w.P;
     const int count = (int)*(volatile uint32_t*)&w.scnt[b];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
         int p = P.qs[i];
         V3 o = mk(P.ox[p], P.oy[p], P.oz[p]), d = mk(P.sdx[p], P.sdy[p], P.sdz[p]);
         float t;
-        if (traverse<true>(w.S, o, d, P.stmax[p], t) < 0) {
+        if (traverse<true, kCount>(w.S, o, d, P.stmax[p], t, &nv, &nt) < 0) {
             P.Lx[p] = P.Lx[p] + P.scx[p];
             P.Ly[p] = P.Ly[p] + P.scy[p];
             P.Lz[p] = P.Lz[p] + P.scz[p];
         }
     }
+    if (kCount) { atomicAdd(&w.stats[2], nv); atomicAdd(&w.stats[3], nt); }
 }
 
 // per pixel: add this wave's samples in sample order (Kahan for radiance)
@@ -617,10 +627,10 @@ inline int grid_for(int64_t n)
 
 using namespace mrs;
 
-extern "C" mrs_status mrs_render(mrs_scene S, int32_t W, int32_t H, int32_t spp, int32_t max_depth,
-                                 int32_t rr_start, uint64_t seed, float* radiance, float* albedo,
-                                 float* normal, float* depth, uint64_t* counts,
-                                 uint64_t* shadow_counts, void* stream)
+static mrs_status render_impl(mrs_scene S, int32_t W, int32_t H, int32_t spp, int32_t max_depth,
+                              int32_t rr_start, uint64_t seed, float* radiance, float* albedo,
+                              float* normal, float* depth, uint64_t* counts,
+                              uint64_t* shadow_counts, unsigned long long* stats, void* stream)
 {
     MRS_ARG(S != nullptr, "scene is NULL");
     MRS_ARG(W >= 1 && W <= 16384 && H >= 1 && H <= 16384, "W, H must be in [1, 16384]");
@@ -670,6 +680,7 @@ extern "C" mrs_status mrs_render(mrs_scene S, int32_t W, int32_t H, int32_t spp,
     w.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
     w.cnt = cnt;
     w.scnt = scnt;
+    w.stats = stats;
 
     MRS_CHECK(cudaMemsetAsync(acc, 0, (size_t)wh * 13 * 4, st));
     if (counts) MRS_CHECK(cudaMemsetAsync(counts, 0, sizeof(uint64_t) * nb, st));
@@ -680,17 +691,47 @@ extern "C" mrs_status mrs_render(mrs_scene S, int32_t W, int32_t H, int32_t spp,
         w.n_paths = (int)(kk * wh);
         MRS_CHECK(cudaMemsetAsync(cnt, 0, 4 * 2 * 64, st));
         int g = grid_for(w.n_paths);
-        k_raygen<<<g, kThreads, 0, st>>>(w);
+        MRS_TIMED(PK_RAYGEN, st, k_raygen<<<g, kThreads, 0, st>>>(w));
+        MRS_LAUNCHED(1);
         for (int b = 0; b <= max_depth; ++b) {
-            k_trace<<<g, kThreads, 0, st>>>(w, b);
-            k_shade<<<g, kThreads, 0, st>>>(w, b);
-            k_shadow<<<g, kThreads, 0, st>>>(w, b);
+            if (stats) MRS_TIMED(PK_TRACE, st, k_trace<true><<<g, kThreads, 0, st>>>(w, b));
+            else MRS_TIMED(PK_TRACE, st, k_trace<false><<<g, kThreads, 0, st>>>(w, b));
+            MRS_LAUNCHED(1);
+            MRS_TIMED(PK_SHADE, st, k_shade<<<g, kThreads, 0, st>>>(w, b));
+            MRS_LAUNCHED(1);
+            if (stats) MRS_TIMED(PK_SHADOW, st, k_shadow<true><<<g, kThreads, 0, st>>>(w, b));
+            else MRS_TIMED(PK_SHADOW, st, k_shadow<false><<<g, kThreads, 0, st>>>(w, b));
+            MRS_LAUNCHED(1);
         }
-        k_accumulate<<<grid_for(wh), kThreads, 0, st>>>(w, acc, kk);
-        if (counts || shadow_counts) k_counts<<<1, 64, 0, st>>>(cnt, scnt, nb, counts, shadow_counts);
+        MRS_TIMED(PK_ACCUM, st, k_accumulate<<<grid_for(wh), kThreads, 0, st>>>(w, acc, kk));
+        MRS_LAUNCHED(1);
+        if (counts || shadow_counts) {
+            k_counts<<<1, 64, 0, st>>>(cnt, scnt, nb, counts, shadow_counts);
+            MRS_LAUNCHED(1);
+        }
     }
     k_resolve<<<grid_for(wh), kThreads, 0, st>>>(acc, wh, spp, radiance, albedo, normal, depth);
+    MRS_LAUNCHED(1);
     return cuda_status(cudaGetLastError(), "render launch");
+}
+
+extern "C" mrs_status mrs_render(mrs_scene S, int32_t W, int32_t H, int32_t spp, int32_t max_depth,
+                                 int32_t rr_start, uint64_t seed, float* radiance, float* albedo,
+                                 float* normal, float* depth, uint64_t* counts,
+                                 uint64_t* shadow_counts, void* stream)
+{
+    return render_impl(S, W, H, spp, max_depth, rr_start, seed, radiance, albedo, normal, depth,
+                       counts, shadow_counts, nullptr, stream);
+}
+
+extern "C" mrs_status mrs_render_stats(mrs_scene S, int32_t W, int32_t H, int32_t spp,
+                                       int32_t max_depth, int32_t rr_start, uint64_t seed,
+                                       float* radiance, uint64_t* stats, void* stream)
+{
+    MRS_ARG(stats != nullptr, "stats is NULL");
+    MRS_CHECK(cudaMemsetAsync(stats, 0, 4 * sizeof(uint64_t), (cudaStream_t)stream));
+    return render_impl(S, W, H, spp, max_depth, rr_start, seed, radiance, nullptr, nullptr, nullptr,
+                       nullptr, nullptr, (unsigned long long*)stats, stream);
 }
 
 extern "C" mrs_status mrs_cast(mrs_scene S, const float* orig, const float* dir, int32_t n,
@@ -701,6 +742,7 @@ extern "C" mrs_status mrs_cast(mrs_scene S, const float* orig, const float* dir,
     if (n == 0) return MRS_OK;
     MRS_ARG(orig && dir && prim && t, "NULL buffer");
     k_cast<<<grid_for(n), kThreads, 0, (cudaStream_t)stream>>>(view(S), orig, dir, n, prim, t);
+    MRS_LAUNCHED(1);
     return cuda_status(cudaGetLastError(), "cast launch");
 }
 
@@ -712,5 +754,6 @@ extern "C" mrs_status mrs_philox_uniforms(const uint32_t* triples, int32_t n, ui
     MRS_ARG(triples && out, "NULL buffer");
     k_philox<<<(n + kThreads - 1) / kThreads, kThreads, 0, (cudaStream_t)stream>>>(
         triples, n, make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)), out);
+    MRS_LAUNCHED(1);
     return cuda_status(cudaGetLastError(), "philox launch");
 }

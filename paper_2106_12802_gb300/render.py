@@ -64,6 +64,17 @@ class Scene:
     def rebuild(self, stream=None):
         call("mrs_scene_rebuild", self.handle, _stream(stream))
 
+    def update_vertices(self, V, stream=None):
+        """Upload new vertices (pinned or pageable host float32 [n,3,3] array or
+        CPU tensor) and rebuild the LBVH."""
+        if isinstance(V, torch.Tensor):
+            assert V.device.type == "cpu" and V.dtype == torch.float32 and V.is_contiguous()
+            ptr = ctypes.c_void_p(V.data_ptr())
+        else:
+            V = np.ascontiguousarray(V, np.float32)
+            ptr = ctypes.c_void_p(V.ctypes.data)
+        call("mrs_scene_update_vertices", self.handle, ptr, self.n, _stream(stream))
+
     def set_wave(self, paths: int):
         call("mrs_scene_set_wave", self.handle, int(paths))
 
@@ -114,6 +125,36 @@ def render(scene: Scene, W, H, spp, max_depth, rr_start=None, seed=0, aux=True, 
          int(seed) & 0xFFFFFFFFFFFFFFFF, _ptr(out["radiance"]), _ptr(out.get("albedo")),
          _ptr(out.get("normal")), _ptr(out.get("depth")), _ptr(out.get("counts")),
          _ptr(out.get("shadow_counts")), _stream(stream))
+    return out
+
+
+def render_stats(scene: Scene, W, H, spp, max_depth, rr_start=None, seed=0, stream=None):
+    """Node visits / triangle tests of the closest-hit and shadow traversals."""
+    dev = torch.device("cuda")
+    rad = torch.empty((H, W, 3), dtype=torch.float32, device=dev)
+    st = torch.zeros(4, dtype=torch.int64, device=dev)
+    call("mrs_render_stats", scene.handle, W, H, spp, max_depth, -1 if rr_start is None else rr_start,
+         int(seed), _ptr(rad), _ptr(st), _stream(stream))
+    v = st.cpu().tolist()
+    return {"visits": v[0], "tests": v[1], "shadow_visits": v[2], "shadow_tests": v[3]}
+
+
+PROFILE_KERNELS = ["trace", "shade", "shadow", "raygen", "accumulate", "lbvh", "conv_tc",
+                   "conv_simt", "input", "metrics", "train"]
+
+
+def profile_enable(on=True):
+    call("mrs_profile_enable", int(bool(on)))
+
+
+def profile_read():
+    """{kernel family: (total ms, launches)} since the last read (synchronises)."""
+    out = {}
+    for i, name in enumerate(PROFILE_KERNELS):
+        ms = ctypes.c_double()
+        n = ctypes.c_int64()
+        call("mrs_profile_read", i, ctypes.byref(ms), ctypes.byref(n))
+        out[name] = (float(ms.value), int(n.value))
     return out
 
 
