@@ -101,7 +101,31 @@ mrs_status mrs_free_scene(mrs_scene scene);
 mrs_status mrs_scene_export_bvh(mrs_scene scene, uint32_t* morton, int32_t* order,
                                 int32_t* left, int32_t* right, float* box, void* stream);
 
-/* Closest hit of n_rays rays through the LBVH: orig/dir device float [n][3];
+/* LBVH build that allocates nothing.  The paper has no counterpart: this is
+ * for callers that cannot call cudaMalloc (or any allocating library
+ * routine) -- code running inside another allocator's callback, under a
+ * memory-reservation regime that forbids new device allocations, or in a
+ * hard real-time frame loop where an allocation could stall.  It builds the
+ * same tree as mrs_build_scene (bit-identical outputs), from device inputs
+ * into device outputs, with all scratch memory (about 7.5 MB) in one static
+ * device array inside libmrs.so; every GPU that loads the library keeps that
+ * array until the process exits.
+ *
+ * V      device float [n][3][3] triangle vertices
+ * morton device uint32 [n], order device int32 [n], left/right device int32
+ *        [n-1] (may be NULL when n == 1), box device float [(2n-1)][6]: the same
+ *        layouts as mrs_scene_export_bvh.
+ * n must be <= MRS_LBVH_STATIC_MAX_TRIS, else MRS_ERR_CAPACITY with a message.
+ * The first call on a device looks up the device address of the static array
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Calls share the one array: two calls whose work
+ * overlaps on the GPU (different streams, or different host threads) race
+ * and corrupt each other; serialise them.  Work is enqueued on `stream`. */
+#define MRS_LBVH_STATIC_MAX_TRIS 262144
+mrs_status mrs_lbvh_build_static(const float* V, int32_t n, uint32_t* morton, int32_t* order,
+                                 int32_t* left, int32_t* right, float* box, void* stream);
+
+/* Closest hit of n_rays rays through the LBVH/* Closest hit of n_rays rays through the LBVH: orig/dir device float [n][3];
  * prim device int32 [n] (triangle index, -1 on miss), t device float [n]
  * (-1 on miss).  Ties in t go to the smaller triangle index. */
 mrs_status mrs_cast(mrs_scene scene, const float* orig, const float* dir, int32_t n_rays,

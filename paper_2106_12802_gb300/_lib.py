@@ -29,6 +29,7 @@ SIGS = {
     "mrs_free_scene": [P],
     "mrs_scene_export_bvh": [P, P, P, P, P, P, P],
     "mrs_cast": [P, P, P, I32, P, P, P],
+    "mrs_lbvh_build_static": [P, I32, P, P, P, P, P, P],
     "mrs_render": [P, I32, I32, I32, I32, I32, U64, P, P, P, P, P, P, P],
     "mrs_scene_set_wave": [P, I64],
     "mrs_render_stats": [P, I32, I32, I32, I32, I32, U64, P, P, P],

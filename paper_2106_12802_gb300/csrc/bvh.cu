@@ -380,6 +380,78 @@ void free_scene(mrs_scene_s* S)
     delete S;
 }
 
+// ---- LBVH build without allocation --------------------------------------
+// For callers that cannot allocate device memory (see mrs_lbvh_build_static in
+// mrs.h), all scratch of the build lives in one file-scope device array sized
+// for MRS_LBVH_STATIC_MAX_TRIS triangles:
+//   centroid-bound partials | digit counts | keys a/b | values a/b | parent | visit
+constexpr int kStaticMaxTris = MRS_LBVH_STATIC_MAX_TRIS;
+constexpr int kStaticParts = 512;
+constexpr int kStaticTiles = (kStaticMaxTris + kTile - 1) / kTile;
+constexpr size_t kStaticBytes = sizeof(float) * 6 * kStaticParts +
+                                sizeof(uint32_t) * 256 * kStaticTiles +
+                                sizeof(uint32_t) * 4 * (size_t)kStaticMaxTris +
+                                sizeof(int) * 3 * (size_t)kStaticMaxTris;
+static __device__ __align__(256) unsigned char g_lbvh_static[kStaticBytes];
+
+// leaf boxes of the sorted triangles; zeroes the refit visit counters (the
+// static scratch keeps the previous call's contents)
+__global__ void k_static_leaves(const float* __restrict__ V, const int* __restrict__ order, int n,
+                                float* __restrict__ box, int* __restrict__ visit)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n - 1) visit[k] = 0;
+    if (k >= n) return;
+    const float* p = V + (size_t)order[k] * 9;
+    float* b = box + (size_t)(n - 1 + k) * 6;
+    for (int a = 0; a < 3; ++a) {
+        b[a] = fminf(fminf(p[a], p[3 + a]), p[6 + a]);
+        b[3 + a] = fmaxf(fmaxf(p[a], p[3 + a]), p[6 + a]);
+    }
+}
+
+// bottom-up box refit (second arrival at a parent computes its box)
+__global__ void k_static_refit(int n, const int* __restrict__ left, const int* __restrict__ right,
+                               const int* __restrict__ parent, float* box, int* visit)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int node = parent[(n - 1) + k];
+    while (node >= 0) {
+        __threadfence();
+        if (atomicAdd(&visit[node], 1) == 0) return;
+        __threadfence();
+        const volatile float* bl = box + (size_t)left[node] * 6;
+        const volatile float* br = box + (size_t)right[node] * 6;
+        float* b = box + (size_t)node * 6;
+        for (int a = 0; a < 3; ++a) {
+            b[a] = fminf(bl[a], br[a]);
+            b[3 + a] = fmaxf(bl[3 + a], br[3 + a]);
+        }
+        node = parent[node];
+    }
+}
+
+// device address of g_lbvh_static for the current device, looked up once per
+// device (the symbol's host-side name is not a device address)
+mrs_status static_scratch(unsigned char** out)
+{
+    static std::mutex mu;
+    static unsigned char* addr[64] = {nullptr};
+    int dev = 0;
+    MRS_CHECK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) { set_error("device index %d out of range", dev); return MRS_ERR_CUDA; }
+    std::lock_guard<std::mutex> g(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_lbvh_static);
+        if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress(g_lbvh_static)");
+        addr[dev] = (unsigned char*)p;
+    }
+    *out = addr[dev];
+    return MRS_OK;
+}
+
 template <class T> mrs_status dalloc(T** p, size_t count)
 {
     *p = nullptr;
@@ -547,4 +619,65 @@ extern "C" mrs_status mrs_scene_set_wave(mrs_scene S, int64_t max_paths)
     MRS_ARG(max_paths >= 1 && max_paths <= (int64_t(1) << 30), "wave size out of range [1, 2^30]");
     S->wave_paths = max_paths;
     return MRS_OK;
+}
+
+extern "C" mrs_status mrs_lbvh_build_static(const float* V, int32_t n, uint32_t* morton,
+                                            int32_t* order, int32_t* left, int32_t* right,
+                                            float* box, void* stream)
+{
+    MRS_ARG(n >= 0, "n_tris < 0");
+    if (n > MRS_LBVH_STATIC_MAX_TRIS) {
+        set_error("n_tris = %d exceeds MRS_LBVH_STATIC_MAX_TRIS = %d (static scratch capacity)",
+                  n, MRS_LBVH_STATIC_MAX_TRIS);
+        return MRS_ERR_CAPACITY;
+    }
+    if (n == 0) return MRS_OK;
+    MRS_ARG(V && morton && order && box, "NULL pointer");
+    MRS_ARG(n == 1 || (left && right), "left/right are NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned char* base = nullptr;
+    mrs_status s = static_scratch(&base);
+    if (s != MRS_OK) return s;
+    const int nparts = 2 * sm_count() < kStaticParts ? 2 * sm_count() : kStaticParts;
+    const int ntiles = blocks_for(n, kTile);
+    unsigned char* p = base;
+    float* part = (float*)p; p += sizeof(float) * 6 * kStaticParts;
+    uint32_t* counts = (uint32_t*)p; p += sizeof(uint32_t) * 256 * kStaticTiles;
+    uint32_t* ka = (uint32_t*)p; p += sizeof(uint32_t) * (size_t)kStaticMaxTris;
+    uint32_t* kb = (uint32_t*)p; p += sizeof(uint32_t) * (size_t)kStaticMaxTris;
+    int* va = (int*)p; p += sizeof(int) * (size_t)kStaticMaxTris;
+    int* vb = (int*)p; p += sizeof(int) * (size_t)kStaticMaxTris;
+    int* parent = (int*)p; p += sizeof(int) * 2 * (size_t)kStaticMaxTris;
+    int* visit = (int*)p;
+
+    k_bounds_partial<<<nparts, kBlock, 0, st>>>(V, n, part);
+    MRS_LAUNCHED(1);
+    k_morton<<<min(blocks_for(n, kBlock), 8 * sm_count()), kBlock, 0, st>>>(V, n, part, nparts,
+                                                                        morton, ka, va);
+    MRS_LAUNCHED(1);
+    for (int pass = 0; pass < 4; ++pass) {
+        int shift = pass * 8;
+        uint32_t* kin = (pass & 1) ? kb : ka;
+        uint32_t* kout = (pass & 1) ? ka : kb;
+        int* vin = (pass & 1) ? vb : va;
+        int* vout = (pass & 1) ? va : vb;
+        k_sort_hist<<<ntiles, kBlock, 0, st>>>(kin, n, shift, counts, ntiles);
+        MRS_LAUNCHED(1);
+        k_sort_scan<<<1, 1024, 0, st>>>(counts, 256 * ntiles);
+        MRS_LAUNCHED(1);
+        k_sort_scatter<<<ntiles, kBlock, 0, st>>>(kin, vin, kout, vout, n, shift, counts, ntiles);
+        MRS_LAUNCHED(1);
+    }
+    MRS_CHECK(cudaMemcpyAsync(order, va, sizeof(int) * (size_t)n, cudaMemcpyDeviceToDevice, st));
+    if (n > 1) {
+        k_karras<<<blocks_for(n - 1, kBlock), kBlock, 0, st>>>(ka, order, n, left, right, parent);
+        MRS_LAUNCHED(1);
+    }
+    k_static_leaves<<<blocks_for(n, kBlock), kBlock, 0, st>>>(V, order, n, box, visit);
+    MRS_LAUNCHED(1);
+    if (n > 1) {
+        k_static_refit<<<blocks_for(n, kBlock), kBlock, 0, st>>>(n, left, right, parent, box, visit);
+        MRS_LAUNCHED(1);
+    }
+    return cuda_status(cudaGetLastError(), "static lbvh launch");
 }
