@@ -224,7 +224,34 @@ mrs_status mrs_fuse(mrs_net net, const float* lrhs, const float* hrls, const flo
                     const float* normal, int32_t N, int32_t H, int32_t W, int32_t scale,
                     int32_t precision, float* out, void* stream);
 
-/* Image error metrics of x against ref (device float, n values each, both in
+/* One training step of the fusion network (learned part of the method; the
+ * paper trains with a robust loss and SGD, Sec. 4 "Loss function" and
+ * "Implement details" -- this library uses L1 on log(1 + radiance) with Adam):
+ * forward with every activation kept, loss mean |slog(y) - slog(target)|
+ * with slog(x) = sign(x) log1p(|x|) (log(1 + radiance) for x >= 0) over
+ * N*H*W*3 values (reduced in float64), full backward
+ * (transposed convolutions with flipped taps, ReLU masks, dW / db
+ * reductions), and one bias-corrected Adam update (beta1 0.9, beta2 0.999,
+ * eps 1e-8) of the FP32 master weights.  LRHS, HRLS and the target are
+ * clipped at 100 first (firefly clipping of the training data, Sec. 3.2).
+ * Image arguments as in mrs_fuse plus target device [N][H][W][3];
+ * precision must be MRS_PREC_FP32.  loss_out (HOST, may be NULL) receives
+ * the loss before the update; when non-NULL the call synchronises `stream`.
+ * Limit: N*H*W <= 2^22 pixels. */
+mrs_status mrs_train_step(mrs_net net, const float* lrhs, const float* hrls, const float* albedo,
+                          const float* normal, const float* target, int32_t N, int32_t H,
+                          int32_t W, int32_t scale, float lr, int32_t precision, double* loss_out,
+                          void* stream);
+/* Gradient of the last mrs_train_step (HOST float [MRS_NET_NPARAMS]; synchronises). */
+mrs_status mrs_net_get_grads(mrs_net net, float* grads);
+/* Checkpoint / resume: FP32 master weights, Adam moments (HOST float
+ * [MRS_NET_NPARAMS] each) and the Adam step count.  Both synchronise. */
+mrs_status mrs_net_get_state(mrs_net net, float* params, float* adam_m, float* adam_v,
+                             int64_t* step);
+mrs_status mrs_net_set_state(mrs_net net, const float* params, const float* adam_m,
+                             const float* adam_v, int64_t step);
+
+/* Image error metrics of x against ref/* Image error metrics of x against ref (device float, n values each, both in
  * scene-linear space), reduced in float64 on the GPU (Sec. 5):
  * out[0] = PSNR of the sRGB images (Eq. cvt_color, peak 1; +inf if equal),
  * out[1] = RelMSE with lambda1, lambda2, out[2] = MSE (linear).

@@ -130,17 +130,21 @@ def forward(params, lrhs, hrls, albedo, normal, s, keep=False):
     return (y, acts) if keep else y
 
 
+def slog(x):
+    """sign(x) * log1p(|x|): log(1 + radiance) extended oddly to negative values."""
+    return np.sign(x) * np.log1p(np.abs(x))
+
+
 def l1log_loss(pred, target):
-    """mean |log1p(max(pred,0)) - log1p(target)| and its gradient w.r.t. pred
-    (subgradient 0 where the difference is 0 or pred < 0)."""
+    """mean |slog(pred) - slog(target)| and its gradient w.r.t. pred,
+    sign(d) / (1 + |pred|) / n (subgradient 0 where d = 0).  For non-negative
+    values slog is log(1 + x), the L1-on-log(1+radiance) loss."""
     pred = np.asarray(pred, dtype=np.float64)
     target = np.asarray(target, dtype=np.float64)
-    pc = np.maximum(pred, 0.0)
-    d = np.log1p(pc) - np.log1p(target)
+    d = slog(pred) - slog(target)
     n = pred.size
     loss = np.abs(d).sum() / n
-    g = np.sign(d) / (1.0 + pc) / n
-    g = np.where(pred > 0.0, g, 0.0)
+    g = np.sign(d) / (1.0 + np.abs(pred)) / n
     return loss, g
 
 
@@ -179,6 +183,19 @@ def adam(params, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
     mh = m / (1 - beta1 ** step)
     vh = v / (1 - beta2 ** step)
     return params - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+def train_step(params, m, v, step, lr, lrhs, hrls, albedo, normal, target, s, clip=100.0):
+    """One training step as the method's learned part runs it: radiance inputs
+    and target clipped at `clip` (firefly clipping, Sec. 3.2), L1-log loss,
+    backward, bias-corrected Adam at step `step` (counting from 1).
+    Returns (new params, m, v, loss, grad)."""
+    lr_c = np.minimum(np.asarray(lrhs, np.float64), clip)
+    hr_c = np.minimum(np.asarray(hrls, np.float64), clip)
+    tg_c = np.minimum(np.asarray(target, np.float64), clip)
+    loss, grad = loss_and_grad(params, lr_c, hr_c, albedo, normal, tg_c, s)
+    p1, m1, v1 = adam(params, grad, m, v, step, lr)
+    return p1, m1, v1, loss, grad
 
 
 def kaiming(seed: int):

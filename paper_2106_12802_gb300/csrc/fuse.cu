@@ -78,13 +78,18 @@ __device__ __forceinline__ void input12(const float* lrhs, const float* hrls, co
     }
 }
 
+// clip > 0: radiance inputs (LRHS, HRLS) clipped at `clip` before use (the
+// training data's firefly clipping, Sec. 3.2)
 __global__ void k_input_f32(const float* lrhs, const float* hrls, const float* alb,
-                            const float* nrm, int H, int W, int s, size_t P, float* x0)
+                            const float* nrm, int H, int W, int s, size_t P, float* x0,
+                            float clip = 0.0f)
 {
     for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < P;
          p += (size_t)gridDim.x * blockDim.x) {
         float v[12];
         input12(lrhs, hrls, alb, nrm, H, W, s, p, v);
+        if (clip > 0.0f)
+            for (int k = 0; k < 6; ++k) v[k] = fminf(v[k], clip);
         for (int k = 0; k < 12; ++k) x0[12 * p + k] = v[k];
     }
 }
@@ -126,7 +131,7 @@ __global__ void k_input_q(const float* lrhs, const float* hrls, const float* alb
 // block = 16 x 8 output pixels, 16 output channels (grid.z over channel groups);
 // input channels staged through shared memory 4 at a time with a 1-pixel halo
 constexpr int kTX = 16, kTY = 8, kCT = 16, kCC = 4;
-enum SimtMode { SIMT_PLAIN = 0, SIMT_RESID = 1, SIMT_FINAL = 2 };
+enum SimtMode { SIMT_PLAIN = 0, SIMT_RESID = 1, SIMT_FINAL = 2, SIMT_MASK = 3 };
 
 __global__ void __launch_bounds__(kTX * kTY)
     k_conv_simt(const float* __restrict__ x, int cin, const float* __restrict__ w,
@@ -194,6 +199,7 @@ __global__ void __launch_bounds__(kTX * kTY)
         if (o0 + o >= cout) break;
         float v = acc[o] + __ldg(b + o0 + o);
         if (mode == SIMT_RESID) v = res[p * cout + o0 + o] + v;
+        else if (mode == SIMT_MASK) v = res[p * cout + o0 + o] > 0.0f ? v : 0.0f;
         else if (relu) v = fmaxf(v, 0.0f);
         out[p * cout + o0 + o] = v;
     }
@@ -354,6 +360,149 @@ __global__ void k_amax_f32(const float* __restrict__ x, size_t n, float* out)
     if ((threadIdx.x & 31) == 0) atomicMax((int*)out, __float_as_int(m));
 }
 
+// ---- training kernels (FP32) -----------------------------------------------
+// transposed-conv weights: wt[c][t][o] = w[o][8 - t][c]  (flipped taps)
+__global__ void k_wtrans(const float* __restrict__ w, int cin, int cout, float* __restrict__ wt)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= cin * 9 * cout) return;
+    int o = i % cout, t = (i / cout) % 9, c = i / (cout * 9);
+    wt[i] = w[((size_t)o * 9 + (8 - t)) * cin + c];
+}
+
+// dW[o][t][c] = sum_p dy[p][o] * x[p shifted by tap t][c] (zero padded), db[o] = sum_p dy[p][o]
+// grid (G, 9): block (g, t) reduces pixel tiles g, g+G, ... for tap t into part[g][t][o][c]
+constexpr int kDwTile = 64;
+__global__ void __launch_bounds__(256)
+    k_dw_partial(const float* __restrict__ x, int cin, const float* __restrict__ dy, int cout,
+                 int N, int H, int W, float* __restrict__ part, float* __restrict__ dbpart)
+{
+    __shared__ __align__(16) float sdy[kDwTile][64];
+    __shared__ __align__(16) float sx[kDwTile][64];
+    const int t = blockIdx.y, g = blockIdx.x, G = gridDim.x;
+    const int dyo = t / 3 - 1, dxo = t % 3 - 1;
+    const int og = threadIdx.x / 16, cg = threadIdx.x % 16;
+    const size_t P = (size_t)N * H * W;
+    const size_t ntiles = (P + kDwTile - 1) / kDwTile;
+    float acc[4][4] = {{0}};
+    float dbacc[4] = {0, 0, 0, 0};
+    for (size_t tile = g; tile < ntiles; tile += G) {
+        size_t p0 = tile * kDwTile;
+        for (int i = threadIdx.x; i < kDwTile * 64; i += 256) {
+            int px = i / 64, ch = i % 64;
+            size_t p = p0 + px;
+            float vd = 0.0f, vx = 0.0f;
+            if (p < P) {
+                if (ch < cout) vd = dy[p * cout + ch];
+                int xx = (int)(p % W), yy = (int)((p / W) % H);
+                size_t n = p / ((size_t)W * H);
+                int sx_ = xx + dxo, sy_ = yy + dyo;
+                if (ch < cin && sx_ >= 0 && sx_ < W && sy_ >= 0 && sy_ < H)
+                    vx = x[((n * H + sy_) * W + sx_) * cin + ch];
+            }
+            sdy[px][ch] = vd;
+            sx[px][ch] = vx;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int px = 0; px < kDwTile; ++px) {
+            float4 a = *(const float4*)&sdy[px][og * 4];
+            float4 b = *(const float4*)&sx[px][cg * 4];
+            float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += av[i] * bv[j];
+            if (t == 0 && cg == 0)
+                for (int i = 0; i < 4; ++i) dbacc[i] += av[i];
+        }
+        __syncthreads();
+    }
+    float* out = part + ((size_t)g * 9 + t) * cout * cin;
+    for (int i = 0; i < 4; ++i) {
+        int o = og * 4 + i;
+        if (o >= cout) continue;
+        for (int j = 0; j < 4; ++j) {
+            int c = cg * 4 + j;
+            if (c < cin) out[(size_t)o * cin + c] = acc[i][j];
+        }
+        if (t == 0 && cg == 0) dbpart[(size_t)g * cout + o] = dbacc[i];
+    }
+}
+
+// grad[o][t][c] (params layout) = sum_g part[g][t][o][c]; grad_b[o] = sum_g dbpart[g][o]
+__global__ void k_dw_reduce(const float* __restrict__ part, const float* __restrict__ dbpart,
+                            int G, int cin, int cout, float* __restrict__ gw, float* __restrict__ gb)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int nw = cout * 9 * cin;
+    if (i < nw) {
+        int c = i % cin, t = (i / cin) % 9, o = i / (cin * 9);
+        float acc = 0.0f;
+        for (int g = 0; g < G; ++g) acc += part[(((size_t)g * 9 + t) * cout + o) * cin + c];
+        gw[i] = acc;
+    } else if (i < nw + cout) {
+        int o = i - nw;
+        float acc = 0.0f;
+        for (int g = 0; g < G; ++g) acc += dbpart[(size_t)g * cout + o];
+        gb[o] = acc;
+    }
+}
+
+// L1 loss on slog(x) = sign(x) log1p(|x|) (= log(1 + x) for x >= 0):
+// d = slog(y) - slog(min(t, clip)); dy = sign(d) / (1 + |y|) / n; loss
+// partials reduced in float64
+__device__ __forceinline__ double slog(double x) { return x < 0.0 ? -log1p(-x) : log1p(x); }
+
+__global__ void k_loss_l1log(const float* __restrict__ y, const float* __restrict__ tgt, size_t n,
+                             float clip, float* __restrict__ dy, double* __restrict__ part)
+{
+    __shared__ double sh[256];
+    double acc = 0.0;
+    const float inv_n = 1.0f / (float)n;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        float yp = y[i];
+        float tv = clip > 0.0f ? fminf(tgt[i], clip) : tgt[i];
+        double d = slog((double)yp) - slog((double)tv);
+        acc += fabs(d);
+        float g = 0.0f;
+        if (d != 0.0) g = (d > 0.0 ? 1.0f : -1.0f) / (1.0f + fabsf(yp)) * inv_n;
+        dy[i] = g;
+    }
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void k_mask_inplace(float* __restrict__ d, const float* __restrict__ act, size_t n)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        if (!(act[i] > 0.0f)) d[i] = 0.0f;
+}
+
+// bias-corrected Adam (Kingma & Ba): bc1 = 1 - beta1^t, bc2 = 1 - beta2^t
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, size_t n, float lr, float b1, float b2, float eps,
+                       float bc1, float bc2)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        float gi = g[i];
+        float mi = b1 * m[i] + (1.0f - b1) * gi;
+        float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        float mh = mi / bc1, vh = vi / bc2;
+        p[i] = p[i] - lr * mh / (sqrtf(vh) + eps);
+    }
+}
+
 struct Scratch {
     std::mutex mu;
     Buf b;
@@ -386,6 +535,8 @@ struct mrs_net_s {
     CUtensorMap wmap_bf[kLayers], wmap_f8[kLayers];
     Buf act;                       // activation workspace
     Buf aux;                       // small device scratch
+    Buf tact;                      // training activations
+    Buf ttmp;                      // training scratch (transposed weights, dW partials, loss)
     int* err = nullptr;            // device error word
 };
 
@@ -775,3 +926,184 @@ extern "C" mrs_status mrs_conv3x3(const float* x, int32_t N, int32_t H, int32_t 
     return rc;
 }
 
+
+namespace mrs {
+namespace {
+
+constexpr int kDwSplits = 64;
+constexpr float kClip = 100.0f;
+
+__global__ void k_clip_copy(const float* __restrict__ x, size_t n, float clip, float* __restrict__ y)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        y[i] = fminf(x[i], clip);
+}
+
+inline int grid1d(size_t n) { size_t g = (n + 255) / 256; return (int)(g < 4096 ? (g ? g : 1) : 4096); }
+
+// dW / db of layer l from its input x [P][cin] and output gradient dy [P][cout]
+mrs_status layer_dw(mrs_net_s* net, int l, const float* x, const float* dy, int N, int H, int W,
+                    float* part, float* dbpart, cudaStream_t st)
+{
+    const LayerShape& L = shapes()[l];
+    dim3 grid(kDwSplits, 9);
+    MRS_TIMED(PK_TRAIN, st, k_dw_partial<<<grid, 256, 0, st>>>(x, L.cin, dy, L.cout, N, H, W, part, dbpart));
+    MRS_LAUNCHED(1);
+    int nw = L.cout * 9 * L.cin + L.cout;
+    MRS_TIMED(PK_TRAIN, st, k_dw_reduce<<<(nw + 255) / 256, 256, 0, st>>>(part, dbpart, kDwSplits, L.cin, L.cout,
+                                                         net->grad + L.woff, net->grad + L.boff));
+    MRS_LAUNCHED(1);
+    return cuda_status(cudaGetLastError(), "dw");
+}
+
+// transposed conv of layer l: dx [P][cin] = conv(dy [P][cout], flipped w^T), epilogue `mode`
+mrs_status layer_dx(mrs_net_s* net, int l, const float* dy, float* wt, const float* zero,
+                    int mode, const float* res, float* dx, int N, int H, int W, cudaStream_t st)
+{
+    const LayerShape& L = shapes()[l];
+    int n = L.cin * 9 * L.cout;
+    k_wtrans<<<(n + 255) / 256, 256, 0, st>>>(net->master + L.woff, L.cin, L.cout, wt);
+    MRS_LAUNCHED(1);
+    return conv_simt(dy, L.cout, wt, zero, L.cin, mode, 0, res, dx, nullptr, N, H, W, 1, st);
+}
+
+mrs_status train_step_f32(mrs_net_s* net, const float* lrhs, const float* hrls, const float* alb,
+                          const float* nrm, const float* target, int N, int H, int W, int s,
+                          float lr, double* loss_out, cudaStream_t st)
+{
+    const size_t P = (size_t)N * H * W;
+    const size_t F = P * 64;
+    const size_t nlr = (size_t)N * (H / s) * (W / s) * 3;
+    // activations: x0 | h0..h8 | r0..r7 | y | dy | dh | da | lrhs_clipped
+    size_t need = (P * 12 + 9 * F + 8 * F + 2 * P * 3 + 2 * F + nlr) * 4;
+    mrs_status rc = net->tact.ensure(need);
+    if (rc != MRS_OK) return rc;
+    size_t tneed = (64 * 9 * 64 + 64) * 4 + ((size_t)kDwSplits * 9 * 64 * 64 + kDwSplits * 64) * 4 +
+                   (kRedBlocks + 8) * 8;
+    if ((rc = net->ttmp.ensure(tneed)) != MRS_OK) return rc;
+    float* x0 = net->tact.as<float>();
+    float* hs = x0 + P * 12;
+    float* rs = hs + 9 * F;
+    float* y = rs + 8 * F;
+    float* dy = y + P * 3;
+    float* dh = dy + P * 3;
+    float* da = dh + F;
+    float* lrc = da + F;
+    float* wt = net->ttmp.as<float>();
+    float* zero = wt + 64 * 9 * 64;
+    float* part = zero + 64;
+    float* dbpart = part + (size_t)kDwSplits * 9 * 64 * 64;
+    double* lparts = (double*)(dbpart + kDwSplits * 64);
+    double* lres = lparts + kRedBlocks;
+    MRS_CHECK(cudaMemsetAsync(zero, 0, 64 * 4, st));
+    const auto& L = shapes();
+    const float* M = net->master;
+
+    // forward, keeping every activation the backward needs
+    k_clip_copy<<<grid1d(nlr), 256, 0, st>>>(lrhs, nlr, kClip, lrc);
+    MRS_LAUNCHED(1);
+    k_input_f32<<<grid1d(P), 256, 0, st>>>(lrc, hrls, alb, nrm, H, W, s, P, x0, kClip);
+    MRS_LAUNCHED(1);
+    rc = conv_simt(x0, 12, M + L[0].woff, M + L[0].boff, 64, SIMT_PLAIN, 1, nullptr, hs, nullptr, N, H, W, s, st);
+    for (int k = 0; k < 8 && rc == MRS_OK; ++k) {
+        const LayerShape& a = L[1 + 2 * k];
+        const LayerShape& b = L[2 + 2 * k];
+        rc = conv_simt(hs + k * F, 64, M + a.woff, M + a.boff, 64, SIMT_PLAIN, 1, nullptr, rs + k * F,
+                       nullptr, N, H, W, s, st);
+        if (rc == MRS_OK)
+            rc = conv_simt(rs + k * F, 64, M + b.woff, M + b.boff, 64, SIMT_RESID, 0, hs + k * F,
+                           hs + (k + 1) * F, nullptr, N, H, W, s, st);
+    }
+    if (rc == MRS_OK)
+        rc = conv_simt(hs + 8 * F, 64, M + L[17].woff, M + L[17].boff, 3, SIMT_FINAL, 0, nullptr, y, lrc,
+                       N, H, W, s, st);
+    if (rc != MRS_OK) return rc;
+
+    // loss (float64 reduction) and dL/dy
+    MRS_TIMED(PK_TRAIN, st, k_loss_l1log<<<kRedBlocks, 256, 0, st>>>(y, target, P * 3, kClip, dy, lparts));
+    MRS_LAUNCHED(1);
+    k_reduce_parts<<<1, 32, 0, st>>>(lparts, kRedBlocks, 1, lres);
+    MRS_LAUNCHED(1);
+
+    // backward
+    if ((rc = layer_dw(net, 17, hs + 8 * F, dy, N, H, W, part, dbpart, st)) != MRS_OK) return rc;
+    if ((rc = layer_dx(net, 17, dy, wt, zero, SIMT_PLAIN, nullptr, dh, N, H, W, st)) != MRS_OK) return rc;
+    for (int k = 7; k >= 0; --k) {
+        int l2 = 2 + 2 * k, l1 = 1 + 2 * k;
+        if ((rc = layer_dw(net, l2, rs + k * F, dh, N, H, W, part, dbpart, st)) != MRS_OK) return rc;
+        if ((rc = layer_dx(net, l2, dh, wt, zero, SIMT_MASK, rs + k * F, da, N, H, W, st)) != MRS_OK) return rc;
+        if ((rc = layer_dw(net, l1, hs + k * F, da, N, H, W, part, dbpart, st)) != MRS_OK) return rc;
+        if ((rc = layer_dx(net, l1, da, wt, zero, SIMT_RESID, dh, dh, N, H, W, st)) != MRS_OK) return rc;
+    }
+    k_mask_inplace<<<grid1d(F), 256, 0, st>>>(dh, hs, F);
+    MRS_LAUNCHED(1);
+    if ((rc = layer_dw(net, 0, x0, dh, N, H, W, part, dbpart, st)) != MRS_OK) return rc;
+
+    // Adam on the FP32 master weights
+    net->step += 1;
+    const double b1 = 0.9, b2 = 0.999;
+    float bc1 = (float)(1.0 - pow(b1, (double)net->step));
+    float bc2 = (float)(1.0 - pow(b2, (double)net->step));
+    MRS_TIMED(PK_TRAIN, st, k_adam<<<grid1d(kParams), 256, 0, st>>>(net->master, net->grad, net->adam_m, net->adam_v,
+                                                        kParams, lr, (float)b1, (float)b2, 1e-8f, bc1, bc2));
+    MRS_LAUNCHED(1);
+    net->bf_valid = net->f8_valid = net->xscale_valid = false;
+    if (loss_out) {
+        double h = 0;
+        MRS_CHECK(cudaMemcpyAsync(&h, lres, sizeof(double), cudaMemcpyDeviceToHost, st));
+        MRS_CHECK(cudaStreamSynchronize(st));
+        *loss_out = h / (double)(P * 3);
+    }
+    return cuda_status(cudaGetLastError(), "train step");
+}
+
+}  // namespace
+}  // namespace mrs
+
+extern "C" mrs_status mrs_train_step(mrs_net net, const float* lrhs, const float* hrls,
+                                     const float* albedo, const float* normal, const float* target,
+                                     int32_t N, int32_t H, int32_t W, int32_t scale, float lr,
+                                     int32_t precision, double* loss_out, void* stream)
+{
+    MRS_ARG(net != nullptr, "net is NULL");
+    MRS_ARG(lrhs && hrls && albedo && normal && target, "NULL image pointer");
+    MRS_ARG(scale == 1 || scale == 2 || scale == 4 || scale == 8, "scale must be 1, 2, 4 or 8");
+    MRS_ARG(N >= 1 && H >= 1 && W >= 1 && H % scale == 0 && W % scale == 0, "bad sizes");
+    MRS_ARG((int64_t)N * H * W <= (int64_t(1) << 22), "training batch exceeds 2^22 pixels");
+    MRS_ARG(lr >= 0.0f, "lr < 0");
+    MRS_ARG(precision == MRS_PREC_FP32, "training precision must be MRS_PREC_FP32");
+    return train_step_f32(net, lrhs, hrls, albedo, normal, target, N, H, W, scale, lr, loss_out,
+                          (cudaStream_t)stream);
+}
+
+extern "C" mrs_status mrs_net_get_grads(mrs_net net, float* grads)
+{
+    MRS_ARG(net && grads, "NULL argument");
+    MRS_CHECK(cudaMemcpy(grads, net->grad, kParams * 4, cudaMemcpyDeviceToHost));
+    return MRS_OK;
+}
+
+extern "C" mrs_status mrs_net_get_state(mrs_net net, float* params, float* adam_m, float* adam_v,
+                                        int64_t* step)
+{
+    MRS_ARG(net && params && adam_m && adam_v && step, "NULL argument");
+    MRS_CHECK(cudaMemcpy(params, net->master, kParams * 4, cudaMemcpyDeviceToHost));
+    MRS_CHECK(cudaMemcpy(adam_m, net->adam_m, kParams * 4, cudaMemcpyDeviceToHost));
+    MRS_CHECK(cudaMemcpy(adam_v, net->adam_v, kParams * 4, cudaMemcpyDeviceToHost));
+    *step = net->step;
+    return MRS_OK;
+}
+
+extern "C" mrs_status mrs_net_set_state(mrs_net net, const float* params, const float* adam_m,
+                                        const float* adam_v, int64_t step)
+{
+    MRS_ARG(net && params && adam_m && adam_v, "NULL argument");
+    MRS_ARG(step >= 0, "step < 0");
+    MRS_CHECK(cudaMemcpy(net->master, params, kParams * 4, cudaMemcpyHostToDevice));
+    MRS_CHECK(cudaMemcpy(net->adam_m, adam_m, kParams * 4, cudaMemcpyHostToDevice));
+    MRS_CHECK(cudaMemcpy(net->adam_v, adam_v, kParams * 4, cudaMemcpyHostToDevice));
+    net->step = step;
+    net->bf_valid = net->f8_valid = net->xscale_valid = false;
+    return MRS_OK;
+}

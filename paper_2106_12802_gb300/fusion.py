@@ -65,6 +65,71 @@ class Net:
         return out
 
 
+def _np_ptr(a):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def train_step(net, lrhs, hrls, albedo, normal, target, scale, lr=1e-4, precision="fp32",
+               sync_loss=True, stream=None):
+    """One Adam step on a batch (CUDA float32 NHWC tensors); returns the loss
+    (float) or None when sync_loss is False (no host synchronisation)."""
+    for t in (lrhs, hrls, albedo, normal, target):
+        _dev(t, torch.float32)
+    N, H, W, _ = hrls.shape
+    loss = ctypes.c_double()
+    call("mrs_train_step", net.handle, _ptr(lrhs), _ptr(hrls), _ptr(albedo), _ptr(normal),
+         _ptr(target), N, H, W, scale, float(lr), _prec(precision),
+         ctypes.byref(loss) if sync_loss else None, _stream(stream))
+    return float(loss.value) if sync_loss else None
+
+
+def get_grads(net):
+    out = np.zeros(NPARAMS, np.float32)
+    call("mrs_net_get_grads", net.handle, _np_ptr(out))
+    return out
+
+
+def get_state(net):
+    p, m, v = (np.zeros(NPARAMS, np.float32) for _ in range(3))
+    step = ctypes.c_int64()
+    call("mrs_net_get_state", net.handle, _np_ptr(p), _np_ptr(m), _np_ptr(v), ctypes.byref(step))
+    return {"params": p, "adam_m": m, "adam_v": v, "step": int(step.value)}
+
+
+def set_state(net, st):
+    p, m, v = (np.ascontiguousarray(st[k], np.float32) for k in ("params", "adam_m", "adam_v"))
+    call("mrs_net_set_state", net.handle, _np_ptr(p), _np_ptr(m), _np_ptr(v), int(st["step"]))
+
+
+CKPT_MAGIC = b"MRSNET01"
+
+
+def save_checkpoint(net, path, seed=0):
+    """Flat little-endian file: magic, nparams (int64), step (int64), data seed
+    (uint64), then params, Adam m, Adam v as float32."""
+    st = get_state(net)
+    with open(path, "wb") as f:
+        f.write(CKPT_MAGIC)
+        f.write(np.array([NPARAMS, st["step"]], dtype="<i8").tobytes())
+        f.write(np.array([seed], dtype="<u8").tobytes())
+        for k in ("params", "adam_m", "adam_v"):
+            f.write(st[k].astype("<f4").tobytes())
+
+
+def load_checkpoint(net, path):
+    """Restores a save_checkpoint file into `net`; returns the stored data seed."""
+    with open(path, "rb") as f:
+        if f.read(8) != CKPT_MAGIC:
+            raise ValueError("not an mrs checkpoint")
+        n, step = np.frombuffer(f.read(16), dtype="<i8")
+        if n != NPARAMS:
+            raise ValueError(f"checkpoint has {n} parameters, expected {NPARAMS}")
+        seed = int(np.frombuffer(f.read(8), dtype="<u8")[0])
+        arrs = [np.frombuffer(f.read(4 * NPARAMS), dtype="<f4").astype(np.float32) for _ in range(3)]
+    set_state(net, {"params": arrs[0], "adam_m": arrs[1], "adam_v": arrs[2], "step": int(step)})
+    return seed
+
+
 def conv3x3(x, w, b, relu=False, precision="fp32", stream=None):
     """One 3x3 conv layer: x [N,H,W,cin] CUDA float32, w [cout,3,3,cin], b [cout] numpy."""
     _dev(x, torch.float32)

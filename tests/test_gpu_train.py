@@ -1,0 +1,97 @@
+"""GPU training step (forward with kept activations, L1-log loss, backward,
+Adam) against the float64 oracle, through the C ABI.
+
+Tolerances: the GPU step runs in FP32 (SIMT convolutions), the oracle in
+float64; per layer the gradient must agree to 1e-4 in relative L2 norm, the
+loss to 1e-6 relative, and the Adam update to 1% of lr where the oracle
+gradient is not tiny (the first Adam step is lr * g / (|g| + eps): where
+|g| ~ eps its direction is ill-conditioned)."""
+import numpy as np
+import pytest
+
+from oracle import cnn
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mrs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2106_12802_gb300 as m
+    m.load()
+    return m
+
+
+def _batch(seed, N, h, w, s):
+    rng = np.random.default_rng(seed)
+    lr = rng.gamma(2.0, 0.5, (N, h, w, 3)).astype(np.float32)
+    hr = rng.gamma(1.0, 1.0, (N, h * s, w * s, 3)).astype(np.float32)
+    hr[0, 0, 0, 0] = 250.0            # a firefly above the clip level
+    alb = rng.uniform(0, 1, (N, h * s, w * s, 3)).astype(np.float32)
+    nrm = rng.uniform(-1, 1, (N, h * s, w * s, 3)).astype(np.float32)
+    tgt = rng.gamma(2.0, 0.5, (N, h * s, w * s, 3)).astype(np.float32)
+    return lr, hr, alb, nrm, tgt
+
+
+def _params(seed):
+    layers = cnn.unpack(cnn.kaiming(seed))
+    out = []
+    for i, (w, b) in enumerate(layers):
+        if 1 <= i <= 16 and i % 2 == 0:
+            w = w * 0.25
+        out.append((w, b + 0.02))
+    return cnn.pack(out).astype(np.float32)
+
+
+def _cuda(*a):
+    return [torch.from_numpy(np.ascontiguousarray(t)).cuda() for t in a]
+
+
+@pytest.mark.parametrize("N,h,w,s", [(2, 4, 6, 4), (1, 8, 8, 2)])
+def test_train_step_gradients_and_update_match_oracle(mrs, N, h, w, s):
+    lr, hr, alb, nrm, tgt = _batch(1, N, h, w, s)
+    p = _params(0)
+    net = mrs.Net(p)
+    loss = mrs.train_step(net, *_cuda(lr, hr, alb, nrm, tgt), s, lr=1e-3)
+    g = mrs.get_grads(net)
+    p1 = net.get_params()
+    z = np.zeros(mrs.NPARAMS)
+    rp, _, _, rloss, rg = cnn.train_step(p.astype(np.float64), z, z, 1, 1e-3, lr, hr, alb, nrm, tgt, s)
+    assert abs(loss - rloss) <= 1e-6 * rloss
+    for li, (wo, bo, ci, co) in enumerate(cnn.layer_offsets()):
+        for a, b in ((wo, bo), (bo, bo + co)):
+            ref = rg[a:b]
+            err = np.linalg.norm(g[a:b] - ref) / max(np.linalg.norm(ref), 1e-30)
+            assert err < 1e-4, (li, a, err)
+    ok = np.abs(rg) > 1e-6
+    assert np.abs((p1 - p) - (rp - p))[ok].max() <= 0.01 * 1e-3
+
+
+def test_training_reduces_loss_on_a_fixed_batch(mrs):
+    lr, hr, alb, nrm, tgt = _batch(2, 2, 8, 8, 4)
+    net = mrs.Net(_params(1))
+    t = _cuda(lr, hr, alb, nrm, tgt)
+    losses = [mrs.train_step(net, *t, 4, lr=1e-3) for _ in range(40)]
+    assert losses[-1] < 0.7 * losses[0], losses[::5]
+
+
+def test_checkpoint_resume_is_bit_identical(mrs, tmp_path):
+    lr, hr, alb, nrm, tgt = _batch(3, 1, 4, 4, 4)
+    t = _cuda(lr, hr, alb, nrm, tgt)
+    a = mrs.Net(_params(2))
+    for _ in range(2):
+        mrs.train_step(a, *t, 4, lr=1e-3)
+    path = str(tmp_path / "ck.bin")
+    mrs.save_checkpoint(a, path, seed=5)
+    for _ in range(3):
+        mrs.train_step(a, *t, 4, lr=1e-3)
+    b = mrs.Net(np.zeros(mrs.NPARAMS, np.float32))
+    assert mrs.load_checkpoint(b, path) == 5
+    for _ in range(3):
+        mrs.train_step(b, *t, 4, lr=1e-3)
+    sa, sb = mrs.get_state(a), mrs.get_state(b)
+    assert sa["step"] == sb["step"] == 5
+    for k in ("params", "adam_m", "adam_v"):
+        assert np.array_equal(sa[k], sb[k]), k

@@ -136,3 +136,34 @@ def test_kaiming_statistics():
     w = p[1][0]
     assert abs(w.std() - np.sqrt(2 / 576)) < 0.01 * np.sqrt(2 / 576) * 5
     assert all((b == 0).all() for _, b in p)
+
+
+def test_train_step_clips_inputs_and_target():
+    # with everything below the clip level, the clipped step equals the plain one;
+    # scaling the inputs far above it leaves the clipped step unchanged
+    rng = np.random.default_rng(7)
+    lr, hr, alb, nrm = _inputs(rng, N=1, h=2, w=2, s=2)
+    tgt = rng.uniform(0, 2, hr.shape)
+    p = cnn.kaiming(1) * 0.3
+    z = np.zeros_like(p)
+    a = cnn.train_step(p, z, z, 1, 1e-3, lr, hr, alb, nrm, tgt, 2)
+    loss, grad = cnn.loss_and_grad(p, lr, hr, alb, nrm, tgt, 2)
+    assert a[3] == loss and np.array_equal(a[4], grad)
+    big = cnn.train_step(p, z, z, 1, 1e-3, lr + 500, hr + 500, alb, nrm, tgt + 500, 2)
+    ref = cnn.loss_and_grad(p, np.full_like(lr, 100.0), np.full_like(hr, 100.0), alb, nrm,
+                            np.full_like(tgt, 100.0), 2)
+    assert big[3] == ref[0] and np.array_equal(big[4], ref[1])
+
+
+def test_slog_loss_extends_log1p():
+    # for non-negative values the loss is L1 on log(1 + x); slog is odd and monotone
+    rng = np.random.default_rng(8)
+    a = rng.uniform(0, 5, 50)
+    b = rng.uniform(0, 5, 50)
+    loss, _ = cnn.l1log_loss(a, b)
+    assert abs(loss - np.mean(np.abs(np.log1p(a) - np.log1p(b)))) < 1e-15
+    x = np.linspace(-5, 5, 1001)
+    assert np.array_equal(cnn.slog(-x), -cnn.slog(x)) and (np.diff(cnn.slog(x)) > 0).all()
+    # negative predictions keep a gradient pointing back up
+    _, g = cnn.l1log_loss(np.array([-0.5]), np.array([1.0]))
+    assert g[0] < 0 and abs(g[0] + 1 / 1.5) < 1e-15
