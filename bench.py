@@ -58,7 +58,7 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks / throttle reasons sampled every 100 ms."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -72,7 +72,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -196,6 +196,82 @@ def run_reference(args, rank, world):
 
 
 # ----------------------------------------------------------------------------
+# equal-PSNR comparison: hybrid frame vs plain high-resolution path tracing
+# ----------------------------------------------------------------------------
+def equal_psnr(mrs, scene, s, ref_spp=4096, train_scenes=8, train_steps=1500):
+    """Trains the fusion network on held-out procedural scenes (seeds 1..),
+    renders a ref_spp reference of the bench scene, scores the hybrid frame
+    (BF16 fusion) and finds the plain HR spp that reaches the same sRGB PSNR
+    (bisection on spp); returns both times (CUDA events, same renderer)."""
+    import torch
+
+    from paper_2106_12802_gb300 import trainer
+    from synth import scenes
+    t0 = time.perf_counter()
+    data = trainer.make_dataset(range(1, 1 + train_scenes), size=HR, s=s, spp_lr=SPP_LR,
+                                spp_hr=SPP_HR, spp_tgt=256, depth=DEPTH, rr=RR,
+                                scene_fn=scenes.procedural)
+    net = mrs.Net(trainer.init_params(0))
+    trainer.train(net, data, train_steps, batch=8, crop=96, s=s, lr=1e-3, seed=0)
+    del data
+    t_train = time.perf_counter() - t0
+    ref = mrs.render(scene, HR, HR, ref_spp, DEPTH, RR, 99991, aux=False, counts=False)["radiance"]
+    ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        ev[0].record()
+        r = fn()
+        ev[1].record()
+        torch.cuda.synchronize()
+        return r, ev[0].elapsed_time(ev[1])
+
+    def hybrid():
+        lr = mrs.render(scene, LR, LR, SPP_LR, DEPTH, RR, 5, aux=False, counts=False)["radiance"]
+        hr = mrs.render(scene, HR, HR, SPP_HR, DEPTH, RR, 6, aux=True, counts=False)
+        out = net.fuse(lr[None], hr["radiance"][None], hr["albedo"][None], hr["normal"][None], s,
+                       precision="bf16")
+        return out[0]
+
+    fused, t_h = timed(hybrid)
+    p_h = mrs.image_metrics(fused.contiguous(), ref)[0]
+    cache = {}
+
+    def plain_psnr(n):
+        if n not in cache:
+            img = mrs.render(scene, HR, HR, n, DEPTH, RR, 7, aux=False, counts=False)["radiance"]
+            cache[n] = mrs.image_metrics(img, ref)[0]
+        return cache[n]
+
+    lo, hi = 1, 1
+    while plain_psnr(hi) < p_h and hi < ref_spp // 4:
+        lo, hi = hi, hi * 2
+    while hi - lo > 1 and plain_psnr(hi) >= p_h:
+        mid = (lo + hi) // 2
+        if plain_psnr(mid) >= p_h:
+            hi = mid
+        else:
+            lo = mid
+    n_eq = hi
+    _, t_p = timed(lambda: mrs.render(scene, HR, HR, n_eq, DEPTH, RR, 7, aux=False, counts=False))
+    # the method without the network: upsampled LRHS (zero-weight network)
+    lr = mrs.render(scene, LR, LR, SPP_LR, DEPTH, RR, 5, aux=False, counts=False)["radiance"]
+    hr = mrs.render(scene, HR, HR, SPP_HR, DEPTH, RR, 6, aux=True, counts=False)
+    up = mrs.Net(np.zeros(mrs.NPARAMS, np.float32)).fuse(
+        lr[None], hr["radiance"][None], hr["albedo"][None], hr["normal"][None], s, precision="fp32")
+    p_lr_up = mrs.image_metrics(up[0].contiguous(), ref)[0]
+    p_hrls = mrs.image_metrics(hr["radiance"], ref)[0]
+    return {"reference_spp": ref_spp, "hybrid_psnr_db": p_h, "hybrid_ms": t_h,
+            "upsampled_lrhs_psnr_db": p_lr_up, "hrls_psnr_db": p_hrls, "plain_spp_at_equal_psnr": n_eq,
+            "plain_psnr_db": plain_psnr(n_eq), "plain_ms": t_p, "speedup_plain_over_hybrid": t_p / t_h,
+            "spp_avg_hybrid": SPP_LR / (s * s) + SPP_HR,
+            "training": f"{train_scenes} procedural scenes (seeds 1..{train_scenes}) at {HR}^2, "
+                        f"targets 256 spp, {train_steps} Adam steps, batch 8 x 96^2, lr 1e-3, "
+                        f"{t_train:.1f} s"}
+
+
+# ----------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------
 def run_gpu(args, rank, world):
@@ -293,6 +369,8 @@ def run_gpu(args, rank, world):
 
     # ---- context measurements (outside the timed region) --------------------
     extra = {}
+    if rank == 0 and not args.quick and not args.no_equal_psnr:
+        extra["equal_psnr"] = equal_psnr(mrs, scene, S)
     if rank == 0 and not args.quick:
         stats_lr = mrs.render_stats(scene, LR, LR, SPP_LR, DEPTH, RR, 0)
         stats_hr = mrs.render_stats(scene, HR, HR, SPP_HR, DEPTH, RR, 1)
@@ -367,11 +445,12 @@ def run_gpu(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mrs", choices=["mrs", "reference"])
     ap.add_argument("--quick", action="store_true", help="skip context measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-equal-psnr", action="store_true")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -1,0 +1,109 @@
+"""Training-data generation, training loop and evaluation of the fusion network.
+
+The learned part of the method (Sec. 4): the network is trained on
+(LRHS, HRLS + albedo / normal, high-spp target) triples that this renderer
+produces from seeded procedural scenes, and judged against the high-spp
+render.  All rendering, convolution, loss, optimiser and metric arithmetic
+runs in libmrs.so; this module only orchestrates calls and slices crops.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import fusion
+from .fusion import NPARAMS
+from .render import Scene, render as render_image
+
+LAYERS = [(12, 64)] + [(64, 64)] * 16 + [(64, 3)]
+
+
+def init_params(seed: int, resid_gain: float = 0.1) -> np.ndarray:
+    """Kaiming-normal weights (std sqrt(2 / (9 Cin))) with the second conv of
+    every residual block scaled by `resid_gain` and the 3-channel head set to
+    zero, so that an untrained network outputs the upsampled LRHS exactly and
+    training starts from the method-without-network baseline."""
+    rng = np.random.default_rng(np.random.SeedSequence([0x696E6974, int(seed)]))
+    parts = []
+    for i, (ci, co) in enumerate(LAYERS):
+        w = rng.normal(0.0, np.sqrt(2.0 / (9 * ci)), (co, 3, 3, ci))
+        if 1 <= i <= 16 and i % 2 == 0:
+            w *= resid_gain
+        if i == len(LAYERS) - 1:
+            w[:] = 0.0
+        parts += [w.ravel(), np.zeros(co)]
+    p = np.concatenate(parts).astype(np.float32)
+    assert p.size == NPARAMS
+    return p
+
+
+def render_example(scene, size, s, spp_lr, spp_hr, spp_tgt, depth, rr, seed):
+    """One training triple: LRHS [1,size/s,size/s,3], HRLS + albedo + normal
+    [1,size,size,3], target [1,size,size,3] (independent seeds per render)."""
+    lr = render_image(scene, size // s, size // s, spp_lr, depth, rr, 3 * seed + 0, aux=False,
+                       counts=False)["radiance"]
+    hr = render_image(scene, size, size, spp_hr, depth, rr, 3 * seed + 1, aux=True, counts=False)
+    tg = render_image(scene, size, size, spp_tgt, depth, rr, 3 * seed + 2, aux=False,
+                       counts=False)["radiance"]
+    return {"lrhs": lr[None], "hrls": hr["radiance"][None], "albedo": hr["albedo"][None],
+            "normal": hr["normal"][None], "target": tg[None]}
+
+
+def make_dataset(scene_seeds, size=256, s=4, spp_lr=64, spp_hr=4, spp_tgt=256, depth=8, rr=3,
+                 scene_fn=None):
+    """Render one example per procedural scene seed; tensors stay on the GPU."""
+    from synth import scenes
+    scene_fn = scene_fn or (lambda sd: scenes.procedural(sd, n_spheres=24, n_large=8))
+    data = []
+    for sd in scene_seeds:
+        sc = Scene(scene_fn(sd))
+        data.append(render_example(sc, size, s, spp_lr, spp_hr, spp_tgt, depth, rr, sd))
+        sc.close()
+    torch.cuda.synchronize()
+    return data
+
+
+def random_batch(data, batch, crop, s, rng):
+    """`batch` random crops (crop x crop HR, aligned to the scale) from `data`."""
+    keys = ("lrhs", "hrls", "albedo", "normal", "target")
+    out = {k: [] for k in keys}
+    for _ in range(batch):
+        ex = data[int(rng.integers(len(data)))]
+        H = ex["hrls"].shape[1]
+        y = int(rng.integers(0, (H - crop) // s + 1)) * s
+        x = int(rng.integers(0, (H - crop) // s + 1)) * s
+        out["lrhs"].append(ex["lrhs"][:, y // s:(y + crop) // s, x // s:(x + crop) // s])
+        for k in keys[1:]:
+            out[k].append(ex[k][:, y:y + crop, x:x + crop])
+    return {k: torch.cat(v).contiguous() for k, v in out.items()}
+
+
+def train(net, data, steps, batch=16, crop=128, s=4, lr=1e-4, seed=0, log_every=0):
+    rng = np.random.default_rng(seed)
+    losses = []
+    for i in range(steps):
+        b = random_batch(data, batch, crop, s, rng)
+        sync = bool(log_every) and (i % log_every == 0 or i == steps - 1)
+        loss = fusion.train_step(net, b["lrhs"], b["hrls"], b["albedo"], b["normal"], b["target"],
+                                 s, lr=lr, sync_loss=sync)
+        if sync:
+            losses.append((i, loss))
+    torch.cuda.synchronize()
+    return losses
+
+
+def evaluate(net, data, s=4, precision="fp32"):
+    """Mean sRGB PSNR / RelMSE against the target of: the fused image, the
+    method without the network (upsampled LRHS, via a zero-weight network)
+    and the HRLS input."""
+    zero = fusion.Net(np.zeros(NPARAMS, np.float32))
+    acc = {"fused": [], "upsampled_lrhs": [], "hrls": []}
+    for ex in data:
+        fused = net.fuse(ex["lrhs"], ex["hrls"], ex["albedo"], ex["normal"], s, precision=precision)
+        up = zero.fuse(ex["lrhs"], ex["hrls"], ex["albedo"], ex["normal"], s, precision="fp32")
+        for k, img in (("fused", fused), ("upsampled_lrhs", up), ("hrls", ex["hrls"])):
+            psnr, rel, _ = fusion.image_metrics(img, ex["target"])
+            acc[k].append((psnr, rel))
+    zero.close()
+    return {k: {"psnr": float(np.mean([a for a, _ in v])), "relmse": float(np.mean([b for _, b in v]))}
+            for k, v in acc.items()}
