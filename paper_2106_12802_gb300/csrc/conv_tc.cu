@@ -3,23 +3,30 @@
 //
 // GEMM view of one layer: M = output pixels, N = output channels (64, or 16
 // for the 3-channel head padded to 16), K = 9 taps x 64 input channels.  A CTA
-// tile is 128 consecutive pixels of one image row; for tap (dy, dx) its A
-// operand is the 128 x 64 input block at (row y+dy-1, column x0+dx-1), loaded
-// by one TMA box whose out-of-range part is zero-filled (this is the zero
-// padding).  Each activation row (64 channels) is 128 bytes (bf16) or 64 bytes
-// (fp8), stored with the matching TMA swizzle so the smem descriptors can
-// address it directly.  All 9 taps of the layer's weights stay resident in
-// shared memory for the whole persistent CTA.
+// tile is 128 consecutive pixels of one image row.  Each activation row (64
+// channels) is 128 bytes (bf16) or 64 bytes (fp8), stored with the matching
+// TMA swizzle so the smem descriptors address it directly.
+//   bf16: per kernel row dy one TMA box of 130 pixels (columns x0-1 .. x0+128
+//         of input row y+dy-1) feeds the three taps dx = 0, 1, 2 through
+//         descriptors whose start is shifted by dx rows (3 boxes per tile);
+//   fp8:  one 128-pixel box per tap (9 per tile; a 64-byte row shift is not
+//         expressible within the 64B swizzle pattern).
+// Out-of-range parts of a box are zero-filled: this is the zero padding.  All
+// 9 taps of the layer's weights stay resident in shared memory for the whole
+// persistent CTA.
 //
-// Warp roles (192 threads, one CTA per SM):
-//   warp 0: TMA producer (weights once, then 9 A boxes per tile, S-stage ring)
+// Warp roles (320 threads, one CTA per SM):
+//   warp 0: TMA producer (weights once, then A boxes through an S-stage ring,
+//           and each tile's residual into one of two staging slots)
 //   warp 1: TMEM allocator and MMA issuer (one thread)
-//   warps 2-5: epilogue (tcgen05.ld of the 128 x N fp32 accumulator, bias,
-//              ReLU / residual / bilinear skip, vectorised stores)
+//   warps 2-9: epilogue; warp w reads TMEM lanes 32 (w % 4) .. + 31 and 32 of
+//           the 64 output channels: bias, ReLU / residual / bilinear skip,
+//           BF16 results written into the staging slot (swizzled) and sent out
+//           by one TMA store per tile
 // The TMEM accumulator is double-buffered so the epilogue of tile i overlaps
-// the MMAs of tile i+1.  Every wait is bounded: on timeout the kernel sets
-// *err and all roles unwind, TMEM is freed, and the host reports
-// MRS_ERR_TIMEOUT.
+// the MMAs of tile i+1.  Every wait is bounded (no hardware barrier inside the
+// role loops): on timeout the kernel sets *err, all roles unwind, TMEM is
+// freed, and the host reports MRS_ERR_TIMEOUT.
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
@@ -29,7 +36,9 @@ namespace mrs {
 namespace {
 
 constexpr int kTileM = 128;
-constexpr int kThreads = 192;
+constexpr int kEpiWarps = 8;
+constexpr int kEpiThreads = 32 * kEpiWarps;
+constexpr int kThreads = 64 + kEpiThreads;   // TMA warp, MMA warp, epilogue warps
 constexpr long long kTimeoutCycles = 4000000000LL;   // ~2 s at 2 GHz
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
@@ -168,15 +177,37 @@ __device__ __forceinline__ void bilinear(const float* __restrict__ lr, int h, in
     }
 }
 
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap* map, const void* src, int c0,
+                                             int c1, int c2, int c3)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%2, %3, %4, %5}], [%1];" ::"l"(
+            (uint64_t)map),
+        "r"(smem_u32(src)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+        : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// byte offset of 16-byte chunk j of row m in a SWIZZLE_128B tile
+__device__ __forceinline__ uint32_t sw128(int m, int j) { return m * 128 + ((j ^ (m & 7)) << 4); }
+
 template <int NOUT, int OPER>
 __global__ void __launch_bounds__(kThreads, 1)
     k_conv_tc(const __grid_constant__ CUtensorMap tmap_x, const __grid_constant__ CUtensorMap tmap_w,
-              TcConvArgs a, int stages)
+              const __grid_constant__ CUtensorMap tmap_res,
+              const __grid_constant__ CUtensorMap tmap_out, TcConvArgs a, int stages)
 {
+    constexpr bool HALO = OPER == TC_BF16;                   // 3 halo boxes per tile (else 9)
     constexpr int ROWB = OPER == TC_BF16 ? 128 : 64;          // bytes per activation row
-    constexpr int ABYTES = kTileM * ROWB;                    // one A stage
-    constexpr int WBYTES = 9 * NOUT * ROWB;                  // all taps of the weights
-    constexpr int KSTEPS = OPER == TC_BF16 ? 4 : 2;          // MMAs per tap (K = 16 / 32 per MMA)
+    constexpr int BOXPX = HALO ? kHaloBox : kTileM;
+    constexpr int ABYTES = ((BOXPX * ROWB + 1023) / 1024) * 1024;   // one A stage
+    constexpr int LOADS = HALO ? 3 : 9;                       // A boxes per tile
+    constexpr int WBYTES = 9 * NOUT * ROWB;                   // all taps of the weights
+    constexpr int KSTEPS = OPER == TC_BF16 ? 4 : 2;           // MMAs per tap (K = 16 / 32 per MMA)
+    constexpr int SBYTES = kTileM * 128;                      // residual / output staging slot
     constexpr uint32_t IDESC =
         (1u << 4) | ((OPER == TC_BF16 ? 1u : 0u) << 7) | ((OPER == TC_BF16 ? 1u : 0u) << 10) |
         ((uint32_t)(NOUT >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
@@ -186,25 +217,38 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* sW = smem;
     uint8_t* sA = smem + ((WBYTES + 1023) & ~1023);
-    uint64_t* bars = (uint64_t*)(sA + stages * ABYTES);
+    uint8_t* sS = sA + stages * ABYTES;                       // 2 staging slots
+    float* sBias = (float*)(sS + 2 * SBYTES);                 // 64 floats
+    uint64_t* bars = (uint64_t*)(sBias + 64);
     uint64_t* full = bars;
     uint64_t* empty = bars + stages;
     uint64_t* wbar = bars + 2 * stages;
     uint64_t* tfull = wbar + 1;
     uint64_t* tempty = tfull + 2;
-    uint32_t* tslot = (uint32_t*)(tempty + 2);
+    uint64_t* rfull = tempty + 2;
+    uint64_t* rempty = rfull + 2;
+    uint64_t* edone = rempty + 2;                             // epilogue warps done with a slot
+    uint32_t* tslot = (uint32_t*)(edone + 2);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int XB = (a.W + kTileM - 1) / kTileM;
     const int ntiles = a.N * a.H * XB;
+    const bool bf_out = a.mode == TC_RELU_BF16 || a.mode == TC_RESID_BF16;
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < stages; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
         mbar_init(wbar, 1);
-        for (int i = 0; i < 2; ++i) { mbar_init(&tfull[i], 1); mbar_init(&tempty[i], 4); }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&tfull[i], 1);
+            mbar_init(&tempty[i], kEpiWarps);
+            mbar_init(&rfull[i], 1);
+            mbar_init(&rempty[i], 1);
+            mbar_init(&edone[i], kEpiWarps);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
+    if (threadIdx.x < 64) sBias[threadIdx.x] = threadIdx.x < NOUT ? a.bias[threadIdx.x] : 0.0f;
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(tslot)),
@@ -219,17 +263,28 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) {
             mbar_expect_tx(wbar, WBYTES);
             for (int t = 0; t < 9; ++t) tma_load_2d(sW + t * NOUT * ROWB, &tmap_w, 0, t * NOUT, wbar);
-            uint32_t it = 0;
+            uint32_t it = 0, j = 0;
             bool ok = true;
-            for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+            for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x, ++j) {
                 int xb = tile % XB, rest = tile / XB, y = rest % a.H, n = rest / a.H;
-                for (int t = 0; t < 9; ++t, ++it) {
+                for (int l = 0; l < LOADS; ++l, ++it) {
                     int s = it % stages;
                     uint32_t ph = (it / stages) & 1;
                     if (!mbar_wait(&empty[s], ph ^ 1, a.err)) { ok = false; break; }
-                    mbar_expect_tx(&full[s], ABYTES);
-                    tma_load_4d(sA + s * ABYTES, &tmap_x, 0, xb * kTileM + (t % 3) - 1,
-                                y + (t / 3) - 1, n, &full[s]);
+                    mbar_expect_tx(&full[s], BOXPX * ROWB);
+                    int dy = HALO ? l : l / 3, dx = HALO ? 0 : l % 3;
+                    tma_load_4d(sA + s * ABYTES, &tmap_x, 0, xb * kTileM + dx - 1, y + dy - 1, n,
+                                &full[s]);
+                }
+                if (!ok) break;
+                // residual tile (or just the slot hand-over) for the epilogue
+                uint32_t slot = j & 1, use = j >> 1;
+                if (!mbar_wait(&rempty[slot], (use & 1) ^ 1, a.err)) break;
+                if (a.mode == TC_RESID_BF16) {
+                    mbar_expect_tx(&rfull[slot], SBYTES);
+                    tma_load_4d(sS + slot * SBYTES, &tmap_res, 0, xb * kTileM, y, n, &rfull[slot]);
+                } else {
+                    mbar_arrive(&rfull[slot]);
                 }
             }
         }
@@ -243,17 +298,24 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (!mbar_wait(&tempty[acc], (use & 1) ^ 1, a.err)) { ok = false; break; }
                 tc_fence_after();
                 uint32_t d = tmem + acc * 64;
-                for (int t = 0; t < 9; ++t, ++it) {
+                for (int l = 0; l < LOADS; ++l, ++it) {
                     int s = it % stages;
                     uint32_t ph = (it / stages) & 1;
                     if (!mbar_wait(&full[s], ph, a.err)) { ok = false; break; }
                     tc_fence_after();
+                    for (int dxi = 0; dxi < (HALO ? 3 : 1); ++dxi) {
+                        int t = HALO ? l * 3 + dxi : l;
+                        uint32_t astart = abase + s * ABYTES + dxi * ROWB;
 #pragma unroll
-                    for (int k = 0; k < KSTEPS; ++k) {
-                        uint64_t ad = sdesc(abase + s * ABYTES + k * 32, ROWB);
-                        uint64_t bd = sdesc(wbase + t * NOUT * ROWB + k * 32, ROWB);
-                        if (OPER == TC_BF16) mma_f16(d, ad, bd, IDESC, (t | k) != 0);
-                        else mma_f8(d, ad, bd, IDESC, (t | k) != 0);
+                        for (int k = 0; k < KSTEPS; ++k) {
+                            // a row-shifted start (dx rows into the halo box) needs
+                            // no base offset: the 128B swizzle is a function of the
+                            // absolute shared-memory address, as TMA wrote it
+                            uint64_t ad = sdesc(astart + k * 32, ROWB);
+                            uint64_t bd = sdesc(wbase + t * NOUT * ROWB + k * 32, ROWB);
+                            if (OPER == TC_BF16) mma_f16(d, ad, bd, IDESC, (t | k) != 0);
+                            else mma_f8(d, ad, bd, IDESC, (t | k) != 0);
+                        }
                     }
                     mma_commit(&empty[s]);
                 }
@@ -262,100 +324,129 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         }
     } else {
-        // epilogue: warp w reads TMEM lanes 32 * (w % 4) .. + 31
-        const int q = warp & 3;
+        // epilogue: 8 warps; warp w reads TMEM lanes 32 * (w % 4) .. + 31 and
+        // output channels [32 h, 32 h + 32) with h = (w - 2) / 4
+        const int q = warp & 3, half = (warp - 2) >> 2;
         const int m = q * 32 + lane;
+        const int cbase = 32 * half;
+        const bool load_half = cbase < NOUT;
         uint32_t lt = 0;
+        bool ok = true;
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
-            uint32_t acc = lt & 1, use = lt >> 1;
-            bool ok = mbar_wait(&tfull[acc], use & 1, a.err);
+            uint32_t acc = lt & 1, use = lt >> 1, slot = lt & 1;
+            ok = mbar_wait(&tfull[acc], use & 1, a.err);
             if (!__all_sync(0xffffffffu, ok)) break;
             tc_fence_after();
-            float v[NOUT];
-            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + acc * 64;
+            float v[32];
+            if (load_half) {
+                const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + acc * 64 + cbase;
 #pragma unroll
-            for (int c = 0; c < NOUT; c += 16) {
-                uint32_t r[16];
-                tmem_ld16(taddr + c, r);
-                tmem_wait_ld();
+                for (int c = 0; c < 32; c += 16) {
+                    if (cbase + c < NOUT) {
+                        uint32_t r[16];
+                        tmem_ld16(taddr + c, r);
+                        tmem_wait_ld();
 #pragma unroll
-                for (int j = 0; j < 16; ++j) v[c + j] = __uint_as_float(r[j]);
+                        for (int j = 0; j < 16; ++j) v[c + j] = __uint_as_float(r[j]);
+                    }
+                }
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[acc]);
+            ok = mbar_wait(&rfull[slot], use & 1, a.err);
+            if (!__all_sync(0xffffffffu, ok)) break;
 
             int xb = tile % XB, rest = tile / XB, y = rest % a.H, n = rest / a.H;
             int x = xb * kTileM + m;
-            if (x >= a.W) continue;
             size_t p = ((size_t)n * a.H + y) * a.W + x;
-            if (OPER == TC_FP8) {
-                // dequantise: acc * wscale[c] * xscale
+            if (OPER == TC_FP8 && load_half) {
 #pragma unroll
-                for (int c = 0; c < NOUT; ++c) v[c] = v[c] * (__ldg(a.wscale + c) * a.xscale);
+                for (int c = 0; c < 32; ++c)
+                    v[c] = v[c] * (__ldg(a.wscale + (cbase + c < NOUT ? cbase + c : 0)) * a.xscale);
             }
-            if (a.mode == TC_RELU_BF16 || a.mode == TC_RESID_BF16) {
-                float o[64];
+            uint8_t* srow = sS + slot * SBYTES;
+            if (bf_out) {
+                float o[32];
 #pragma unroll
-                for (int c = 0; c < 64; ++c) o[c] = v[c < NOUT ? c : 0] + __ldg(a.bias + c);
+                for (int c = 0; c < 32; ++c) o[c] = v[c] + sBias[cbase + c];
                 if (a.mode == TC_RELU_BF16) {
 #pragma unroll
-                    for (int c = 0; c < 64; ++c) o[c] = fmaxf(o[c], 0.0f);
+                    for (int c = 0; c < 32; ++c) o[c] = fmaxf(o[c], 0.0f);
                 } else {
-                    const uint4* rp = (const uint4*)((const __nv_bfloat16*)a.res + p * 64);
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        uint4 u = rp[j];
+                    for (int jj = 0; jj < 4; ++jj) {
+                        uint4 u = *(const uint4*)(srow + sw128(m, 4 * half + jj));
                         const __nv_bfloat162* h2 = (const __nv_bfloat162*)&u;
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
                             float2 f = __bfloat1622float2(h2[e]);
-                            o[8 * j + 2 * e] = f.x + o[8 * j + 2 * e];
-                            o[8 * j + 2 * e + 1] = f.y + o[8 * j + 2 * e + 1];
+                            o[8 * jj + 2 * e] = f.x + o[8 * jj + 2 * e];
+                            o[8 * jj + 2 * e + 1] = f.y + o[8 * jj + 2 * e + 1];
                         }
                     }
                 }
-                uint4* op = (uint4*)((__nv_bfloat16*)a.out + p * 64);
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
+                for (int jj = 0; jj < 4; ++jj) {
                     uint4 u;
                     __nv_bfloat162* h2 = (__nv_bfloat162*)&u;
 #pragma unroll
                     for (int e = 0; e < 4; ++e)
-                        h2[e] = __floats2bfloat162_rn(o[8 * j + 2 * e], o[8 * j + 2 * e + 1]);
-                    op[j] = u;
+                        h2[e] = __floats2bfloat162_rn(o[8 * jj + 2 * e], o[8 * jj + 2 * e + 1]);
+                    *(uint4*)(srow + sw128(m, 4 * half + jj)) = u;
                 }
-                if (a.out_fp8) {
-                    uint4* fp = (uint4*)((uint8_t*)a.out_fp8 + p * 64);
+                if (a.out_fp8 && x < a.W) {
+                    uint4* fp = (uint4*)((uint8_t*)a.out_fp8 + p * 64 + cbase);
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
+                    for (int jj = 0; jj < 2; ++jj) {
                         uint4 u;
                         uint8_t* b8 = (uint8_t*)&u;
 #pragma unroll
-                        for (int e = 0; e < 16; ++e) {
-                            float f = o[16 * j + e] * a.out_fp8_inv_scale;
-                            b8[e] = (uint8_t)__nv_cvt_float_to_fp8(f, __NV_SATFINITE, __NV_E4M3);
-                        }
-                        fp[j] = u;
+                        for (int e = 0; e < 16; ++e)
+                            b8[e] = (uint8_t)__nv_cvt_float_to_fp8(o[16 * jj + e] * a.out_fp8_inv_scale,
+                                                                   __NV_SATFINITE, __NV_E4M3);
+                        fp[jj] = u;
                     }
                 }
-            } else if (a.mode == TC_FINAL_F32) {
-                float up[3];
-                bilinear(a.lrhs + (size_t)n * (a.H / a.scale) * (a.W / a.scale) * 3,
-                         a.H / a.scale, a.W / a.scale, a.scale, x, y, up);
-                float* op = (float*)a.out + p * 3;
-                for (int c = 0; c < 3; ++c) op[c] = (v[c] + __ldg(a.bias + c)) + up[c];
-            } else {
-                float* op = (float*)a.out + p * a.cout;
+                fence_async_smem();
+            } else if (x < a.W && load_half) {
+                if (a.mode == TC_FINAL_F32) {
+                    if (half == 0) {
+                        float up[3];
+                        bilinear(a.lrhs + (size_t)n * (a.H / a.scale) * (a.W / a.scale) * 3,
+                                 a.H / a.scale, a.W / a.scale, a.scale, x, y, up);
+                        float* op = (float*)a.out + p * 3;
+                        for (int c = 0; c < 3; ++c) op[c] = (v[c] + sBias[c]) + up[c];
+                    }
+                } else {
+                    float* op = (float*)a.out + p * a.cout;
 #pragma unroll
-                for (int c = 0; c < NOUT; ++c) {
-                    if (c < a.cout) {
-                        float o = v[c] + __ldg(a.bias + c);
-                        op[c] = a.relu ? fmaxf(o, 0.0f) : o;
+                    for (int c = 0; c < 32; ++c) {
+                        if (cbase + c < a.cout && cbase + c < NOUT) {
+                            float o = v[c] + sBias[cbase + c];
+                            op[cbase + c] = a.relu ? fmaxf(o, 0.0f) : o;
+                        }
                     }
                 }
             }
+            // hand the slot to the storing thread (bounded wait; no hardware barrier)
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&edone[slot]);
+            bool st_ok = true;
+            if (warp == 2 && lane == 0) {
+                st_ok = mbar_wait(&edone[slot], use & 1, a.err);
+                if (st_ok && bf_out) {
+                    tma_store_4d(&tmap_out, srow, 0, xb * kTileM, y, n);
+                    bulk_commit();
+                    bulk_wait_read1();                 // the previous tile's store has read its slot
+                    if (lt > 0) mbar_arrive(&rempty[(lt - 1) & 1]);
+                } else if (st_ok) {
+                    mbar_arrive(&rempty[slot]);
+                }
+            }
+            if (warp == 2 && !__all_sync(0xffffffffu, st_ok)) break;
         }
+        if (warp == 2 && lane == 0) bulk_wait_all();
     }
     __syncthreads();
     if (warp == 1) {
@@ -382,14 +473,18 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 template <int NOUT, int OPER> size_t smem_bytes(int stages)
 {
     constexpr int ROWB = OPER == TC_BF16 ? 128 : 64;
-    return 1024 + ((9 * NOUT * ROWB + 1023) & ~1023) + (size_t)stages * kTileM * ROWB + 8 * (2 * stages + 5) + 16;
+    constexpr int BOXPX = OPER == TC_BF16 ? kHaloBox : kTileM;
+    constexpr int ABYTES = ((BOXPX * ROWB + 1023) / 1024) * 1024;
+    return 1024 + ((9 * NOUT * ROWB + 1023) & ~1023) + (size_t)stages * ABYTES +
+           2 * kTileM * 128 + 64 * 4 + 8 * (2 * stages + 11) + 16;
 }
 
 template <int NOUT, int OPER>
 mrs_status launch(const TcConvArgs& a, cudaStream_t st)
 {
-    constexpr int ROWB = OPER == TC_BF16 ? 128 : 64;
-    int stages = OPER == TC_BF16 ? (NOUT == 64 ? 8 : 10) : 12;
+    // A-operand ring: as many stages as fit next to the weights and staging
+    int stages = 2;
+    while (smem_bytes<NOUT, OPER>(stages + 1) <= 227 * 1024 && stages < 16) ++stages;
     size_t smem = smem_bytes<NOUT, OPER>(stages);
     static bool attr = false;
     if (!attr) {
@@ -398,25 +493,27 @@ mrs_status launch(const TcConvArgs& a, cudaStream_t st)
         if (e != cudaSuccess) return cuda_status(e, "conv smem attribute");
         attr = true;
     }
-    (void)ROWB;
     int ntiles = a.N * a.H * ((a.W + kTileM - 1) / kTileM);
     int grid = ntiles < sm_count() ? ntiles : sm_count();
     if (grid < 1) return MRS_OK;
-    MRS_TIMED(PK_CONV_TC, st, (k_conv_tc<NOUT, OPER><<<grid, kThreads, smem, st>>>(*a.tmap_x, *a.tmap_w, a, stages)));
+    const CUtensorMap* res = a.tmap_res ? a.tmap_res : a.tmap_x;
+    const CUtensorMap* out = a.tmap_out ? a.tmap_out : a.tmap_x;
+    MRS_TIMED(PK_CONV_TC, st, (k_conv_tc<NOUT, OPER><<<grid, kThreads, smem, st>>>(*a.tmap_x, *a.tmap_w, *res, *out, a, stages)));
     MRS_LAUNCHED(1);
     return cuda_status(cudaGetLastError(), "conv launch");
 }
 
 }  // namespace
 
-mrs_status tc_make_act_map(CUtensorMap* m, const void* ptr, int N, int H, int W, int operand)
+mrs_status tc_make_act_map(CUtensorMap* m, const void* ptr, int N, int H, int W, int operand,
+                           int box_px)
 {
     auto fn = encode_fn();
     if (!fn) { set_error("cuTensorMapEncodeTiled unavailable"); return MRS_ERR_CUDA; }
     int rowb = operand == TC_BF16 ? 128 : 64;
     cuuint64_t dims[4] = {64, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)N};
     cuuint64_t strides[3] = {(cuuint64_t)rowb, (cuuint64_t)rowb * W, (cuuint64_t)rowb * W * H};
-    cuuint32_t box[4] = {64, (cuuint32_t)kTileM, 1, 1};
+    cuuint32_t box[4] = {64, (cuuint32_t)box_px, 1, 1};
     cuuint32_t es[4] = {1, 1, 1, 1};
     CUresult r = fn(m, operand == TC_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8,
                     4, const_cast<void*>(ptr), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,

@@ -21,7 +21,9 @@ enum TcMode : int {
 enum TcOperand : int { TC_BF16 = 0, TC_FP8 = 1 };
 
 struct TcConvArgs {
-    const CUtensorMap* tmap_x;   // activations [N][H][W][64] (bf16) or [..][64] (fp8)
+    const CUtensorMap* tmap_x;   // A operand [N][H][W][64] (bf16, 130-pixel halo boxes) or (fp8, 128)
+    const CUtensorMap* tmap_res; // TC_RESID_BF16 residual (bf16, 128-pixel boxes)
+    const CUtensorMap* tmap_out; // TC_RELU_BF16 / TC_RESID_BF16 output (bf16, 128-pixel boxes)
     const CUtensorMap* tmap_w;   // packed weights [9 * nout][64]
     const float* bias;           // [nout] (padded)
     const float* wscale;         // fp8 only: per-output-channel dequant scale (may be NULL)
@@ -41,9 +43,13 @@ struct TcConvArgs {
     float out_fp8_inv_scale;
 };
 
-// Encode a tiled tensor map for a [N][H][W][C] activation tensor whose rows
-// are `row_bytes` (= 128) bytes: box = 128 pixels of one image row.
-mrs_status tc_make_act_map(CUtensorMap* m, const void* ptr, int N, int H, int W, int operand);
+// Box width (pixels) of A-operand maps: one 128-pixel tile plus a 1-pixel halo
+// on each side (bf16); fp8 A operands and all residual / output maps use 128.
+constexpr int kHaloBox = 130;
+// Encode a tiled tensor map for a [N][H][W][64] activation tensor (rows of 128
+// bytes in bf16, 64 in fp8): box = box_px pixels of one image row.
+mrs_status tc_make_act_map(CUtensorMap* m, const void* ptr, int N, int H, int W, int operand,
+                           int box_px = 128);
 // Tensor map for packed weights [rows][64 (bf16) | 64 (fp8)].
 mrs_status tc_make_w_map(CUtensorMap* m, const void* ptr, int rows, int nout, int operand);
 

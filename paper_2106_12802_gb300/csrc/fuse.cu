@@ -639,11 +639,16 @@ mrs_status fuse_tc(mrs_net_s* net, const float* lrhs, const float* hrls, const f
                                  f8 ? 1.0f / net->xscale[0] : 1.0f);
     MRS_LAUNCHED(1);
     if ((rc = cuda_status(cudaGetLastError(), "input")) != MRS_OK) return rc;
-    CUtensorMap mx, mh, mr;
+    // A-operand maps (bf16: 130-pixel halo boxes; fp8: 128) and the bf16
+    // residual / output maps (128-pixel boxes)
+    CUtensorMap mx, mh, mr, oh, orr;
     int oper = f8 ? TC_FP8 : TC_BF16;
-    if ((rc = tc_make_act_map(&mx, f8 ? (void*)x08 : x0, N, H, W, oper)) != MRS_OK) return rc;
-    if ((rc = tc_make_act_map(&mh, f8 ? (void*)h8 : h, N, H, W, oper)) != MRS_OK) return rc;
-    if ((rc = tc_make_act_map(&mr, f8 ? (void*)r8 : r, N, H, W, oper)) != MRS_OK) return rc;
+    int abox = f8 ? 128 : kHaloBox;
+    if ((rc = tc_make_act_map(&mx, f8 ? (void*)x08 : x0, N, H, W, oper, abox)) != MRS_OK) return rc;
+    if ((rc = tc_make_act_map(&mh, f8 ? (void*)h8 : h, N, H, W, oper, abox)) != MRS_OK) return rc;
+    if ((rc = tc_make_act_map(&mr, f8 ? (void*)r8 : r, N, H, W, oper, abox)) != MRS_OK) return rc;
+    if ((rc = tc_make_act_map(&oh, h, N, H, W, TC_BF16, 128)) != MRS_OK) return rc;
+    if ((rc = tc_make_act_map(&orr, r, N, H, W, TC_BF16, 128)) != MRS_OK) return rc;
     TcConvArgs a;
     memset(&a, 0, sizeof(a));
     a.N = N; a.H = H; a.W = W; a.scale = s;
@@ -657,16 +662,19 @@ mrs_status fuse_tc(mrs_net_s* net, const float* lrhs, const float* hrls, const f
         a.xscale = f8 ? net->xscale[l] : 1.0f;
         a.nout = nout_of(l);
         a.out_fp8 = nullptr;
+        a.tmap_res = nullptr;
+        a.tmap_out = nullptr;
         if (l == 0) {
-            a.tmap_x = &mx; a.mode = TC_RELU_BF16; a.out = h; a.res = nullptr;
+            a.tmap_x = &mx; a.mode = TC_RELU_BF16; a.out = h; a.res = nullptr; a.tmap_out = &oh;
             if (f8) { a.out_fp8 = h8; a.out_fp8_inv_scale = 1.0f / net->xscale[1]; }
         } else if (l == kLayers - 1) {
             a.tmap_x = &mh; a.mode = TC_FINAL_F32; a.out = out; a.lrhs = lrhs; a.cout = 3;
         } else if (l % 2 == 1) {
-            a.tmap_x = &mh; a.mode = TC_RELU_BF16; a.out = r; a.res = nullptr;
+            a.tmap_x = &mh; a.mode = TC_RELU_BF16; a.out = r; a.res = nullptr; a.tmap_out = &orr;
             if (f8) { a.out_fp8 = r8; a.out_fp8_inv_scale = 1.0f / net->xscale[l + 1]; }
         } else {
             a.tmap_x = &mr; a.mode = TC_RESID_BF16; a.out = h; a.res = h;
+            a.tmap_res = &oh; a.tmap_out = &oh;
             if (f8) { a.out_fp8 = h8; a.out_fp8_inv_scale = 1.0f / net->xscale[l + 1]; }
         }
         rc = tc_conv3x3(a, st);
@@ -909,7 +917,7 @@ extern "C" mrs_status mrs_conv3x3(const float* x, int32_t N, int32_t H, int32_t 
     k_to_operand<<<1024, 256, 0, st>>>(x, P, cin, xq, oper == TC_FP8, 1.0f / xscale);
     MRS_LAUNCHED(1);
     CUtensorMap mx, mw;
-    if ((rc = tc_make_act_map(&mx, xq, N, H, W, oper)) != MRS_OK) return rc;
+    if ((rc = tc_make_act_map(&mx, xq, N, H, W, oper, oper == TC_BF16 ? kHaloBox : 128)) != MRS_OK) return rc;
     if ((rc = tc_make_w_map(&mw, wp, 9 * nout, nout, oper)) != MRS_OK) return rc;
     TcConvArgs a;
     memset(&a, 0, sizeof(a));
