@@ -15,9 +15,10 @@
 // 9 taps of the layer's weights stay resident in shared memory for the whole
 // persistent CTA.
 //
-// Warp roles (320 threads, one CTA per SM):
-//   warp 0: TMA producer (weights once, then A boxes through an S-stage ring,
-//           and each tile's residual into one of two staging slots)
+// Warp roles (384 threads, one CTA per SM):
+//   warp 0: TMA producer (weights once, then A boxes through an S-stage ring)
+//   warp 10: residual prefetch into one of three staging slots
+//   warp 11: output TMA stores from the staging slots
 //   warp 1: TMEM allocator and MMA issuer (one thread)
 //   warps 2-9: epilogue; warp w reads TMEM lanes 32 (w % 4) .. + 31 and 32 of
 //           the 64 output channels: bias, ReLU / residual / bilinear skip,
@@ -35,10 +36,15 @@
 namespace mrs {
 namespace {
 
-constexpr int kTileM = 128;
+constexpr int kTileM = 128;          // MMA M: pixels x0-1 .. x0+126 of one image row
+constexpr int kQuarter = 30;         // output pixels per 32-lane TMEM quarter
+constexpr int kTileOut = 4 * kQuarter;   // output pixels per tile
 constexpr int kEpiWarps = 8;
 constexpr int kEpiThreads = 32 * kEpiWarps;
-constexpr int kThreads = 64 + kEpiThreads;   // TMA warp, MMA warp, epilogue warps
+constexpr int kResWarp = 2 + kEpiWarps;        // residual-prefetch warp
+constexpr int kStoreWarp = kResWarp + 1;       // output-store warp
+constexpr int kThreads = 32 * (kStoreWarp + 1);  // A-TMA, MMA, epilogue, residual, store warps
+constexpr int kSlots = 3;                      // residual / output staging slots
 constexpr long long kTimeoutCycles = 4000000000LL;   // ~2 s at 2 GHz
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
@@ -71,19 +77,46 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
         : "memory");
     return ok != 0;
 }
-// bounded wait; false if this or another role gave up
+// as above, but the thread may be suspended (up to `ns` nanoseconds) until the
+// phase completes instead of spinning in a loop that takes issue slots from
+// the working warps
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t parity, uint32_t ns)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(ns)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait; false if this or another role gave up.  Each poll lets the
+// hardware suspend the thread (1 ms limit) until the phase completes; the
+// error word and the clock are consulted between polls
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err)
 {
     if (mbar_try_wait(bar, parity)) return true;
     long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity)) {
+    for (;;) {
+        if (mbar_try_wait_sleep(bar, parity, 1000000u)) return true;
         if (*(volatile int*)err) return false;
         if (clock64() - t0 > kTimeoutCycles) {
             atomicExch(err, 1);
             return false;
         }
     }
-    return true;
+}
+
+// warp-wide wait: lane 0 polls, then every lane observes the completed phase
+// once (acquiring the data the phase guards)
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t* bar, uint32_t parity, int* err)
+{
+    bool ok = true;
+    if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, err);
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (ok) (void)mbar_try_wait(bar, parity);
+    return ok;
 }
 
 __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1,
@@ -187,9 +220,21 @@ __device__ __forceinline__ void tma_store_4d(const CUtensorMap* map, const void*
         : "memory");
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// job -> (column block, image, rows [y0, y1)): a job is `rows_per_job`
+// consecutive output rows of one 128-pixel column strip of one image
+__device__ __forceinline__ void job_rows(int job, int XB, int segs, int rows_per_job, int H,
+                                         int& xb, int& n, int& y0, int& y1)
+{
+    int seg = job % segs, rest = job / segs;
+    xb = rest % XB;
+    n = rest / XB;
+    y0 = seg * rows_per_job;
+    y1 = min(H, y0 + rows_per_job);
+}
 
 // byte offset of 16-byte chunk j of row m in a SWIZZLE_128B tile
 __device__ __forceinline__ uint32_t sw128(int m, int j) { return m * 128 + ((j ^ (m & 7)) << 4); }
@@ -200,25 +245,25 @@ __global__ void __launch_bounds__(kThreads, 1)
               const __grid_constant__ CUtensorMap tmap_res,
               const __grid_constant__ CUtensorMap tmap_out, TcConvArgs a, int stages)
 {
-    constexpr bool HALO = OPER == TC_BF16;                   // 3 halo boxes per tile (else 9)
     constexpr int ROWB = OPER == TC_BF16 ? 128 : 64;          // bytes per activation row
-    constexpr int BOXPX = HALO ? kHaloBox : kTileM;
-    constexpr int ABYTES = ((BOXPX * ROWB + 1023) / 1024) * 1024;   // one A stage
-    constexpr int LOADS = HALO ? 3 : 9;                       // A boxes per tile
+    constexpr int ABYTES = kTileM * ROWB;                     // one input row of the ring
+    constexpr int NF = 3 * NOUT;                              // MMA N: (dx, cout) columns
     constexpr int WBYTES = 9 * NOUT * ROWB;                   // all taps of the weights
-    constexpr int KSTEPS = OPER == TC_BF16 ? 4 : 2;           // MMAs per tap (K = 16 / 32 per MMA)
+    constexpr int KSTEPS = OPER == TC_BF16 ? 4 : 2;           // MMAs per kernel row (K 16 / 32)
     constexpr int SBYTES = kTileM * 128;                      // residual / output staging slot
+    constexpr int ACCSTRIDE = 256;                            // TMEM columns per accumulator
+    constexpr int CHUNKS = NOUT == 64 ? 2 : 1;                // 16-channel chunks per warp
     constexpr uint32_t IDESC =
         (1u << 4) | ((OPER == TC_BF16 ? 1u : 0u) << 7) | ((OPER == TC_BF16 ? 1u : 0u) << 10) |
-        ((uint32_t)(NOUT >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
-    constexpr uint32_t kTmemCols = 128;
+        ((uint32_t)(NF >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
+    constexpr uint32_t kTmemCols = 512;
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* sW = smem;
     uint8_t* sA = smem + ((WBYTES + 1023) & ~1023);
-    uint8_t* sS = sA + stages * ABYTES;                       // 2 staging slots
-    float* sBias = (float*)(sS + 2 * SBYTES);                 // 64 floats
+    uint8_t* sS = sA + stages * ABYTES;                       // kSlots staging slots
+    float* sBias = (float*)(sS + kSlots * SBYTES);            // 64 floats
     uint64_t* bars = (uint64_t*)(sBias + 64);
     uint64_t* full = bars;
     uint64_t* empty = bars + stages;
@@ -226,13 +271,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t* tfull = wbar + 1;
     uint64_t* tempty = tfull + 2;
     uint64_t* rfull = tempty + 2;
-    uint64_t* rempty = rfull + 2;
-    uint64_t* edone = rempty + 2;                             // epilogue warps done with a slot
-    uint32_t* tslot = (uint32_t*)(edone + 2);
+    uint64_t* rempty = rfull + kSlots;
+    uint64_t* edone = rempty + kSlots;                        // epilogue warps done with a slot
+    uint32_t* tslot = (uint32_t*)(edone + kSlots);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int XB = (a.W + kTileM - 1) / kTileM;
-    const int ntiles = a.N * a.H * XB;
+    const int XB = (a.W + kTileOut - 1) / kTileOut;
+    const int njobs = a.N * XB * a.segs;
     const bool bf_out = a.mode == TC_RELU_BF16 || a.mode == TC_RESID_BF16;
 
     if (threadIdx.x == 0) {
@@ -241,6 +286,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int i = 0; i < 2; ++i) {
             mbar_init(&tfull[i], 1);
             mbar_init(&tempty[i], kEpiWarps);
+        }
+        for (int i = 0; i < kSlots; ++i) {
             mbar_init(&rfull[i], 1);
             mbar_init(&rempty[i], 1);
             mbar_init(&edone[i], kEpiWarps);
@@ -260,193 +307,225 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t tmem = *(volatile uint32_t*)tslot;
 
     if (warp == 0) {
+        // A producer: input rows y0-1 .. y1 of the job's strip, 128 pixels from
+        // x0-1, each loaded once into the ring
         if (lane == 0) {
             mbar_expect_tx(wbar, WBYTES);
             for (int t = 0; t < 9; ++t) tma_load_2d(sW + t * NOUT * ROWB, &tmap_w, 0, t * NOUT, wbar);
-            uint32_t it = 0, j = 0;
+            uint32_t it = 0;
             bool ok = true;
-            for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x, ++j) {
-                int xb = tile % XB, rest = tile / XB, y = rest % a.H, n = rest / a.H;
-                for (int l = 0; l < LOADS; ++l, ++it) {
+            for (int job = blockIdx.x; ok && job < njobs; job += gridDim.x) {
+                int xb, n, y0, y1;
+                job_rows(job, XB, a.segs, a.rows_per_job, a.H, xb, n, y0, y1);
+                for (int r = y0 - 1; r <= y1; ++r, ++it) {
                     int s = it % stages;
-                    uint32_t ph = (it / stages) & 1;
-                    if (!mbar_wait(&empty[s], ph ^ 1, a.err)) { ok = false; break; }
-                    mbar_expect_tx(&full[s], BOXPX * ROWB);
-                    int dy = HALO ? l : l / 3, dx = HALO ? 0 : l % 3;
-                    tma_load_4d(sA + s * ABYTES, &tmap_x, 0, xb * kTileM + dx - 1, y + dy - 1, n,
-                                &full[s]);
-                }
-                if (!ok) break;
-                // residual tile (or just the slot hand-over) for the epilogue
-                uint32_t slot = j & 1, use = j >> 1;
-                if (!mbar_wait(&rempty[slot], (use & 1) ^ 1, a.err)) break;
-                if (a.mode == TC_RESID_BF16) {
-                    mbar_expect_tx(&rfull[slot], SBYTES);
-                    tma_load_4d(sS + slot * SBYTES, &tmap_res, 0, xb * kTileM, y, n, &rfull[slot]);
-                } else {
-                    mbar_arrive(&rfull[slot]);
+                    if (!mbar_wait(&empty[s], ((it / stages) & 1) ^ 1, a.err)) { ok = false; break; }
+                    mbar_expect_tx(&full[s], ABYTES);
+                    // MMA rows 32q .. 32q+31 <- pixels x0-1+30q .. x0+30+30q
+                    for (int q = 0; q < 4; ++q)
+                        tma_load_4d(sA + s * ABYTES + q * 32 * ROWB, &tmap_x, 0,
+                                    xb * kTileOut - 1 + q * kQuarter, r, n, &full[s]);
                 }
             }
         }
+    } else if (warp == kResWarp) {
+        // residual tiles (or just the slot hand-over) for the epilogue, kSlots ahead
+        if (lane == 0) {
+            uint32_t j = 0;
+            bool ok = true;
+            for (int job = blockIdx.x; ok && job < njobs; job += gridDim.x) {
+                int xb, n, y0, y1;
+                job_rows(job, XB, a.segs, a.rows_per_job, a.H, xb, n, y0, y1);
+                for (int y = y0; y < y1; ++y, ++j) {
+                    uint32_t slot = j % kSlots, use = j / kSlots;
+                    if (!mbar_wait(&rempty[slot], (use & 1) ^ 1, a.err)) { ok = false; break; }
+                    if (a.mode == TC_RESID_BF16) {
+                        mbar_expect_tx(&rfull[slot], kTileOut * 128);
+                        tma_load_4d(sS + slot * SBYTES, &tmap_res, 0, xb * kTileOut, y, n, &rfull[slot]);
+                    } else {
+                        mbar_arrive(&rfull[slot]);
+                    }
+                }
+            }
+        }
+    } else if (warp == kStoreWarp) {
+        // output stores: one TMA store per finished staging slot, then the slot
+        // is handed back to the residual warp once the store has read it
+        if (lane == 0) {
+            uint32_t j = 0;
+            bool ok = true;
+            for (int job = blockIdx.x; ok && job < njobs; job += gridDim.x) {
+                int xb, n, y0, y1;
+                job_rows(job, XB, a.segs, a.rows_per_job, a.H, xb, n, y0, y1);
+                for (int y = y0; y < y1; ++y, ++j) {
+                    uint32_t slot = j % kSlots, use = j / kSlots;
+                    if (!mbar_wait(&edone[slot], use & 1, a.err)) { ok = false; break; }
+                    if (bf_out) {
+                        tma_store_4d(&tmap_out, sS + slot * SBYTES, 0, xb * kTileOut, y, n);
+                        bulk_commit();
+                        bulk_wait_read0();
+                    }
+                    mbar_arrive(&rempty[slot]);
+                }
+            }
+            bulk_wait_all();
+        }
     } else if (warp == 1) {
+        // MMA issuer: per output row, for each kernel row dy one A row of the
+        // ring against the (dx, cout) x cin weight block of that dy
         if (lane == 0) {
             bool ok = mbar_wait(wbar, 0, a.err);
             uint32_t it = 0, lt = 0;
             const uint32_t wbase = smem_u32(sW), abase = smem_u32(sA);
-            for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x, ++lt) {
-                uint32_t acc = lt & 1, use = lt >> 1;
-                if (!mbar_wait(&tempty[acc], (use & 1) ^ 1, a.err)) { ok = false; break; }
-                tc_fence_after();
-                uint32_t d = tmem + acc * 64;
-                for (int l = 0; l < LOADS; ++l, ++it) {
-                    int s = it % stages;
-                    uint32_t ph = (it / stages) & 1;
-                    if (!mbar_wait(&full[s], ph, a.err)) { ok = false; break; }
+            for (int job = blockIdx.x; ok && job < njobs; job += gridDim.x) {
+                int xb, n, y0, y1;
+                job_rows(job, XB, a.segs, a.rows_per_job, a.H, xb, n, y0, y1);
+                const uint32_t base = it;
+                for (int y = y0; ok && y < y1; ++y, ++lt) {
+                    uint32_t acc = lt & 1, use = lt >> 1;
+                    if (!mbar_wait(&tempty[acc], (use & 1) ^ 1, a.err)) { ok = false; break; }
                     tc_fence_after();
-                    for (int dxi = 0; dxi < (HALO ? 3 : 1); ++dxi) {
-                        int t = HALO ? l * 3 + dxi : l;
-                        uint32_t astart = abase + s * ABYTES + dxi * ROWB;
+                    const uint32_t d = tmem + acc * ACCSTRIDE;
+                    for (int dy = 0; dy < 3; ++dy) {
+                        uint32_t pos = base + (y - y0) + dy;        // ring position of row y-1+dy
+                        int s = pos % stages;
+                        if (!mbar_wait(&full[s], (pos / stages) & 1, a.err)) { ok = false; break; }
+                        tc_fence_after();
 #pragma unroll
                         for (int k = 0; k < KSTEPS; ++k) {
-                            // a row-shifted start (dx rows into the halo box) needs
-                            // no base offset: the 128B swizzle is a function of the
-                            // absolute shared-memory address, as TMA wrote it
-                            uint64_t ad = sdesc(astart + k * 32, ROWB);
-                            uint64_t bd = sdesc(wbase + t * NOUT * ROWB + k * 32, ROWB);
-                            if (OPER == TC_BF16) mma_f16(d, ad, bd, IDESC, (t | k) != 0);
-                            else mma_f8(d, ad, bd, IDESC, (t | k) != 0);
+                            uint64_t ad = sdesc(abase + s * ABYTES + k * 32, ROWB);
+                            uint64_t bd = sdesc(wbase + dy * NF * ROWB + k * 32, ROWB);
+                            if (OPER == TC_BF16) mma_f16(d, ad, bd, IDESC, (dy | k) != 0);
+                            else mma_f8(d, ad, bd, IDESC, (dy | k) != 0);
                         }
                     }
-                    mma_commit(&empty[s]);
+                    if (!ok) break;
+                    mma_commit(&empty[(base + (y - y0)) % stages]);   // row y-1 is done
+                    mma_commit(&tfull[acc]);
                 }
-                if (!ok) break;
-                mma_commit(&tfull[acc]);
+                if (ok) {
+                    uint32_t rows = (uint32_t)(y1 - y0);
+                    mma_commit(&empty[(base + rows) % stages]);
+                    mma_commit(&empty[(base + rows + 1) % stages]);
+                    it = base + rows + 2;
+                }
             }
         }
     } else {
-        // epilogue: 8 warps; warp w reads TMEM lanes 32 * (w % 4) .. + 31 and
-        // output channels [32 h, 32 h + 32) with h = (w - 2) / 4
+        // epilogue: 8 warps; warp w reads TMEM lanes 32 q .. 32 q + 31 (q = w % 4,
+        // pixels x0-1+30q+lane) and output channels [32 h, 32 h + 32),
+        // h = (w - 2) / 4.  Lane k < 30 produces output pixel x0 + 30q + k:
+        // out[c] = D[k][dx0][c] + D[k+1][dx1][c] + D[k+2][dx2][c], the two
+        // neighbours by warp shuffles within the quarter.
         const int q = warp & 3, half = (warp - 2) >> 2;
-        const int m = q * 32 + lane;
-        const int cbase = 32 * half;
-        const bool load_half = cbase < NOUT;
+        const int j = q * kQuarter + lane;                     // output pixel in the tile
+        const bool active = half * 32 < NOUT;
         uint32_t lt = 0;
-        bool ok = true;
-        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
-            uint32_t acc = lt & 1, use = lt >> 1, slot = lt & 1;
-            ok = mbar_wait(&tfull[acc], use & 1, a.err);
-            if (!__all_sync(0xffffffffu, ok)) break;
+        bool stop = false;
+        for (int job = blockIdx.x; !stop && job < njobs; job += gridDim.x) {
+          int xb, n, y0, y1;
+          job_rows(job, XB, a.segs, a.rows_per_job, a.H, xb, n, y0, y1);
+          for (int y = y0; y < y1; ++y, ++lt) {
+            uint32_t acc = lt & 1, use = lt >> 1;
+            uint32_t slot = lt % kSlots, suse = lt / kSlots;
+            if (!mbar_wait_warp(&tfull[acc], use & 1, a.err)) { stop = true; break; }
             tc_fence_after();
-            float v[32];
-            if (load_half) {
-                const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + acc * 64 + cbase;
-#pragma unroll
-                for (int c = 0; c < 32; c += 16) {
-                    if (cbase + c < NOUT) {
-                        uint32_t r[16];
-                        tmem_ld16(taddr + c, r);
-                        tmem_wait_ld();
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) v[c + j] = __uint_as_float(r[j]);
-                    }
-                }
-            }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&tempty[acc]);
-            ok = mbar_wait(&rfull[slot], use & 1, a.err);
-            if (!__all_sync(0xffffffffu, ok)) break;
-
-            int xb = tile % XB, rest = tile / XB, y = rest % a.H, n = rest / a.H;
-            int x = xb * kTileM + m;
-            size_t p = ((size_t)n * a.H + y) * a.W + x;
-            if (OPER == TC_FP8 && load_half) {
-#pragma unroll
-                for (int c = 0; c < 32; ++c)
-                    v[c] = v[c] * (__ldg(a.wscale + (cbase + c < NOUT ? cbase + c : 0)) * a.xscale);
-            }
+            if (!mbar_wait_warp(&rfull[slot], suse & 1, a.err)) { stop = true; break; }
+            const int x = xb * kTileOut + j;
+            const bool valid = lane < kQuarter && x < a.W;
+            const size_t p = ((size_t)n * a.H + y) * a.W + (valid ? x : 0);
             uint8_t* srow = sS + slot * SBYTES;
-            if (bf_out) {
-                float o[32];
+            for (int cc = 0; cc < CHUNKS && active; ++cc) {
+                const int c0 = half * 32 + cc * 16;
+                const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + acc * ACCSTRIDE + c0;
+                uint32_t r0[16], r1[16], r2[16];
+                tmem_ld16(taddr, r0);
+                tmem_ld16(taddr + NOUT, r1);
+                tmem_ld16(taddr + 2 * NOUT, r2);
+                tmem_wait_ld();
+                float v[16];
 #pragma unroll
-                for (int c = 0; c < 32; ++c) o[c] = v[c] + sBias[cbase + c];
-                if (a.mode == TC_RELU_BF16) {
+                for (int e = 0; e < 16; ++e) {
+                    float s1 = __shfl_down_sync(0xffffffffu, __uint_as_float(r1[e]), 1);
+                    float s2 = __shfl_down_sync(0xffffffffu, __uint_as_float(r2[e]), 2);
+                    v[e] = __uint_as_float(r0[e]) + s1 + s2;
+                }
+                if (OPER == TC_FP8) {
 #pragma unroll
-                    for (int c = 0; c < 32; ++c) o[c] = fmaxf(o[c], 0.0f);
-                } else {
+                    for (int e = 0; e < 16; ++e)
+                        v[e] = v[e] * (__ldg(a.wscale + (c0 + e < NOUT ? c0 + e : 0)) * a.xscale);
+                }
+                if (bf_out && lane < kQuarter) {
+                    float o[16];
 #pragma unroll
-                    for (int jj = 0; jj < 4; ++jj) {
-                        uint4 u = *(const uint4*)(srow + sw128(m, 4 * half + jj));
-                        const __nv_bfloat162* h2 = (const __nv_bfloat162*)&u;
+                    for (int e = 0; e < 16; ++e) o[e] = v[e] + sBias[c0 + e];
+                    if (a.mode == TC_RELU_BF16) {
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            float2 f = __bfloat1622float2(h2[e]);
-                            o[8 * jj + 2 * e] = f.x + o[8 * jj + 2 * e];
-                            o[8 * jj + 2 * e + 1] = f.y + o[8 * jj + 2 * e + 1];
+                        for (int e = 0; e < 16; ++e) o[e] = fmaxf(o[e], 0.0f);
+                    } else {
+#pragma unroll
+                        for (int jj = 0; jj < 2; ++jj) {
+                            uint4 u = *(const uint4*)(srow + sw128(j, c0 / 8 + jj));
+                            const __nv_bfloat162* h2 = (const __nv_bfloat162*)&u;
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                float2 f = __bfloat1622float2(h2[e]);
+                                o[8 * jj + 2 * e] = f.x + o[8 * jj + 2 * e];
+                                o[8 * jj + 2 * e + 1] = f.y + o[8 * jj + 2 * e + 1];
+                            }
                         }
                     }
-                }
-#pragma unroll
-                for (int jj = 0; jj < 4; ++jj) {
-                    uint4 u;
-                    __nv_bfloat162* h2 = (__nv_bfloat162*)&u;
-#pragma unroll
-                    for (int e = 0; e < 4; ++e)
-                        h2[e] = __floats2bfloat162_rn(o[8 * jj + 2 * e], o[8 * jj + 2 * e + 1]);
-                    *(uint4*)(srow + sw128(m, 4 * half + jj)) = u;
-                }
-                if (a.out_fp8 && x < a.W) {
-                    uint4* fp = (uint4*)((uint8_t*)a.out_fp8 + p * 64 + cbase);
 #pragma unroll
                     for (int jj = 0; jj < 2; ++jj) {
+                        uint4 u;
+                        __nv_bfloat162* h2 = (__nv_bfloat162*)&u;
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            h2[e] = __floats2bfloat162_rn(o[8 * jj + 2 * e], o[8 * jj + 2 * e + 1]);
+                        *(uint4*)(srow + sw128(j, c0 / 8 + jj)) = u;
+                    }
+                    if (a.out_fp8 && valid) {
                         uint4 u;
                         uint8_t* b8 = (uint8_t*)&u;
 #pragma unroll
                         for (int e = 0; e < 16; ++e)
-                            b8[e] = (uint8_t)__nv_cvt_float_to_fp8(o[16 * jj + e] * a.out_fp8_inv_scale,
+                            b8[e] = (uint8_t)__nv_cvt_float_to_fp8(o[e] * a.out_fp8_inv_scale,
                                                                    __NV_SATFINITE, __NV_E4M3);
-                        fp[jj] = u;
+                        *(uint4*)((uint8_t*)a.out_fp8 + p * 64 + c0) = u;
                     }
-                }
-                fence_async_smem();
-            } else if (x < a.W && load_half) {
-                if (a.mode == TC_FINAL_F32) {
-                    if (half == 0) {
-                        float up[3];
-                        bilinear(a.lrhs + (size_t)n * (a.H / a.scale) * (a.W / a.scale) * 3,
-                                 a.H / a.scale, a.W / a.scale, a.scale, x, y, up);
-                        float* op = (float*)a.out + p * 3;
-                        for (int c = 0; c < 3; ++c) op[c] = (v[c] + sBias[c]) + up[c];
-                    }
-                } else {
-                    float* op = (float*)a.out + p * a.cout;
+                } else if (valid) {
+                    if (a.mode == TC_FINAL_F32) {
+                        if (c0 == 0) {
+                            float up[3];
+                            bilinear(a.lrhs + (size_t)n * (a.H / a.scale) * (a.W / a.scale) * 3,
+                                     a.H / a.scale, a.W / a.scale, a.scale, x, y, up);
+                            float* op = (float*)a.out + p * 3;
+                            for (int c = 0; c < 3; ++c) op[c] = (v[c] + sBias[c]) + up[c];
+                        }
+                    } else {
+                        float* op = (float*)a.out + p * a.cout;
 #pragma unroll
-                    for (int c = 0; c < 32; ++c) {
-                        if (cbase + c < a.cout && cbase + c < NOUT) {
-                            float o = v[c] + sBias[cbase + c];
-                            op[cbase + c] = a.relu ? fmaxf(o, 0.0f) : o;
+                        for (int e = 0; e < 16; ++e) {
+                            if (c0 + e < a.cout) {
+                                float o = v[e] + sBias[c0 + e];
+                                op[c0 + e] = a.relu ? fmaxf(o, 0.0f) : o;
+                            }
                         }
                     }
                 }
             }
-            // hand the slot to the storing thread (bounded wait; no hardware barrier)
+            if (stop) break;
+            // TMEM of this accumulator is free again; the staging slot goes to
+            // the store warp
+            tc_fence_before();
+            if (bf_out) fence_async_smem();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&edone[slot]);
-            bool st_ok = true;
-            if (warp == 2 && lane == 0) {
-                st_ok = mbar_wait(&edone[slot], use & 1, a.err);
-                if (st_ok && bf_out) {
-                    tma_store_4d(&tmap_out, srow, 0, xb * kTileM, y, n);
-                    bulk_commit();
-                    bulk_wait_read1();                 // the previous tile's store has read its slot
-                    if (lt > 0) mbar_arrive(&rempty[(lt - 1) & 1]);
-                } else if (st_ok) {
-                    mbar_arrive(&rempty[slot]);
-                }
+            if (lane == 0) {
+                mbar_arrive(&tempty[acc]);
+                mbar_arrive(&edone[slot]);
             }
-            if (warp == 2 && !__all_sync(0xffffffffu, st_ok)) break;
+          }
         }
-        if (warp == 2 && lane == 0) bulk_wait_all();
     }
     __syncthreads();
     if (warp == 1) {
@@ -473,18 +552,16 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 template <int NOUT, int OPER> size_t smem_bytes(int stages)
 {
     constexpr int ROWB = OPER == TC_BF16 ? 128 : 64;
-    constexpr int BOXPX = OPER == TC_BF16 ? kHaloBox : kTileM;
-    constexpr int ABYTES = ((BOXPX * ROWB + 1023) / 1024) * 1024;
-    return 1024 + ((9 * NOUT * ROWB + 1023) & ~1023) + (size_t)stages * ABYTES +
-           2 * kTileM * 128 + 64 * 4 + 8 * (2 * stages + 11) + 16;
+    return 1024 + ((9 * NOUT * ROWB + 1023) & ~1023) + (size_t)stages * kTileM * ROWB +
+           (size_t)kSlots * kTileM * 128 + 64 * 4 + 8 * (2 * stages + 5 + 3 * kSlots) + 16;
 }
 
 template <int NOUT, int OPER>
 mrs_status launch(const TcConvArgs& a, cudaStream_t st)
 {
-    // A-operand ring: as many stages as fit next to the weights and staging
-    int stages = 2;
-    while (smem_bytes<NOUT, OPER>(stages + 1) <= 227 * 1024 && stages < 16) ++stages;
+    // input-row ring: as many rows as fit next to the weights and staging
+    int stages = 4;
+    while (smem_bytes<NOUT, OPER>(stages + 1) <= 227 * 1024 && stages < 12) ++stages;
     size_t smem = smem_bytes<NOUT, OPER>(stages);
     static bool attr = false;
     if (!attr) {
@@ -493,12 +570,22 @@ mrs_status launch(const TcConvArgs& a, cudaStream_t st)
         if (e != cudaSuccess) return cuda_status(e, "conv smem attribute");
         attr = true;
     }
-    int ntiles = a.N * a.H * ((a.W + kTileM - 1) / kTileM);
-    int grid = ntiles < sm_count() ? ntiles : sm_count();
+    // jobs: each column strip of each image is cut into `segs` runs of rows so
+    // that there are at most as many jobs as SMs (whole strips when the image
+    // set already has more strips than SMs)
+    TcConvArgs b = a;
+    int strips = a.N * ((a.W + kTileOut - 1) / kTileOut);
+    int segs = sm_count() / strips;
+    if (segs < 1) segs = 1;
+    if (segs > a.H) segs = a.H;
+    b.rows_per_job = (a.H + segs - 1) / segs;
+    b.segs = (a.H + b.rows_per_job - 1) / b.rows_per_job;
+    int njobs = strips * b.segs;
+    int grid = njobs < sm_count() ? njobs : sm_count();
     if (grid < 1) return MRS_OK;
     const CUtensorMap* res = a.tmap_res ? a.tmap_res : a.tmap_x;
     const CUtensorMap* out = a.tmap_out ? a.tmap_out : a.tmap_x;
-    MRS_TIMED(PK_CONV_TC, st, (k_conv_tc<NOUT, OPER><<<grid, kThreads, smem, st>>>(*a.tmap_x, *a.tmap_w, *res, *out, a, stages)));
+    MRS_TIMED(PK_CONV_TC, st, (k_conv_tc<NOUT, OPER><<<grid, kThreads, smem, st>>>(*a.tmap_x, *a.tmap_w, *res, *out, b, stages)));
     MRS_LAUNCHED(1);
     return cuda_status(cudaGetLastError(), "conv launch");
 }

@@ -21,9 +21,9 @@ enum TcMode : int {
 enum TcOperand : int { TC_BF16 = 0, TC_FP8 = 1 };
 
 struct TcConvArgs {
-    const CUtensorMap* tmap_x;   // A operand [N][H][W][64] (bf16, 130-pixel halo boxes) or (fp8, 128)
-    const CUtensorMap* tmap_res; // TC_RESID_BF16 residual (bf16, 128-pixel boxes)
-    const CUtensorMap* tmap_out; // TC_RELU_BF16 / TC_RESID_BF16 output (bf16, 128-pixel boxes)
+    const CUtensorMap* tmap_x;   // A operand [N][H][W][64] (bf16 or fp8, kABox-pixel boxes)
+    const CUtensorMap* tmap_res; // TC_RESID_BF16 residual (bf16, kOutBox-pixel boxes)
+    const CUtensorMap* tmap_out; // TC_RELU_BF16 / TC_RESID_BF16 output (bf16, kOutBox-pixel boxes)
     const CUtensorMap* tmap_w;   // packed weights [9 * nout][64]
     const float* bias;           // [nout] (padded)
     const float* wscale;         // fp8 only: per-output-channel dequant scale (may be NULL)
@@ -38,14 +38,17 @@ struct TcConvArgs {
     int mode;
     int operand;                 // TC_BF16 / TC_FP8
     int* err;                    // device error word (timeouts)
+    int segs, rows_per_job;      // row runs per column strip (set by the launcher)
     // TC_RELU_BF16 / TC_RESID_BF16 with fp8 operands: also emit the fp8 copy
     void* out_fp8;
     float out_fp8_inv_scale;
 };
 
-// Box width (pixels) of A-operand maps: one 128-pixel tile plus a 1-pixel halo
-// on each side (bf16); fp8 A operands and all residual / output maps use 128.
-constexpr int kHaloBox = 130;
+// Box widths (pixels): A operands are loaded as four 32-pixel boxes per input
+// row (each covering one TMEM lane quarter: 30 output pixels plus one halo
+// pixel on each side); residual and output maps move a tile's 120 pixels.
+constexpr int kABox = 32;
+constexpr int kOutBox = 120;
 // Encode a tiled tensor map for a [N][H][W][64] activation tensor (rows of 128
 // bytes in bf16, 64 in fp8): box = box_px pixels of one image row.
 mrs_status tc_make_act_map(CUtensorMap* m, const void* ptr, int N, int H, int W, int operand,

@@ -643,12 +643,11 @@ mrs_status fuse_tc(mrs_net_s* net, const float* lrhs, const float* hrls, const f
     // residual / output maps (128-pixel boxes)
     CUtensorMap mx, mh, mr, oh, orr;
     int oper = f8 ? TC_FP8 : TC_BF16;
-    int abox = f8 ? 128 : kHaloBox;
-    if ((rc = tc_make_act_map(&mx, f8 ? (void*)x08 : x0, N, H, W, oper, abox)) != MRS_OK) return rc;
-    if ((rc = tc_make_act_map(&mh, f8 ? (void*)h8 : h, N, H, W, oper, abox)) != MRS_OK) return rc;
-    if ((rc = tc_make_act_map(&mr, f8 ? (void*)r8 : r, N, H, W, oper, abox)) != MRS_OK) return rc;
-    if ((rc = tc_make_act_map(&oh, h, N, H, W, TC_BF16, 128)) != MRS_OK) return rc;
-    if ((rc = tc_make_act_map(&orr, r, N, H, W, TC_BF16, 128)) != MRS_OK) return rc;
+    if ((rc = tc_make_act_map(&mx, f8 ? (void*)x08 : x0, N, H, W, oper, kABox)) != MRS_OK) return rc;
+    if ((rc = tc_make_act_map(&mh, f8 ? (void*)h8 : h, N, H, W, oper, kABox)) != MRS_OK) return rc;
+    if ((rc = tc_make_act_map(&mr, f8 ? (void*)r8 : r, N, H, W, oper, kABox)) != MRS_OK) return rc;
+    if ((rc = tc_make_act_map(&oh, h, N, H, W, TC_BF16, kOutBox)) != MRS_OK) return rc;
+    if ((rc = tc_make_act_map(&orr, r, N, H, W, TC_BF16, kOutBox)) != MRS_OK) return rc;
     TcConvArgs a;
     memset(&a, 0, sizeof(a));
     a.N = N; a.H = H; a.W = W; a.scale = s;
@@ -917,7 +916,7 @@ extern "C" mrs_status mrs_conv3x3(const float* x, int32_t N, int32_t H, int32_t 
     k_to_operand<<<1024, 256, 0, st>>>(x, P, cin, xq, oper == TC_FP8, 1.0f / xscale);
     MRS_LAUNCHED(1);
     CUtensorMap mx, mw;
-    if ((rc = tc_make_act_map(&mx, xq, N, H, W, oper, oper == TC_BF16 ? kHaloBox : 128)) != MRS_OK) return rc;
+    if ((rc = tc_make_act_map(&mx, xq, N, H, W, oper, kABox)) != MRS_OK) return rc;
     if ((rc = tc_make_w_map(&mw, wp, 9 * nout, nout, oper)) != MRS_OK) return rc;
     TcConvArgs a;
     memset(&a, 0, sizeof(a));
