@@ -71,14 +71,16 @@ __device__ __forceinline__ float centroid(const float* V, int i, int a)
     return ((p[a] + p[3 + a]) + p[6 + a]) * 0.333333343267f;
 }
 
-// per-block min/max of centroids -> part[block][6]
-__global__ void k_bounds_partial(const float* __restrict__ V, int n, float* __restrict__ part)
+// per-block min/max of centroids -> part[block][6]; over triangles idx[0..n)
+// (or 0..n-1 when idx is NULL)
+__global__ void k_bounds_partial(const float* __restrict__ V, int n, float* __restrict__ part,
+                                 const int* __restrict__ idx = nullptr)
 {
     __shared__ float s[6][kBlock];
     float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock)
+    for (int k = blockIdx.x * kBlock + threadIdx.x; k < n; k += gridDim.x * kBlock)
         for (int a = 0; a < 3; ++a) {
-            float c = centroid(V, i, a);
+            float c = centroid(V, idx ? idx[k] : k, a);
             lo[a] = fminf(lo[a], c);
             hi[a] = fmaxf(hi[a], c);
         }
@@ -95,10 +97,12 @@ __global__ void k_bounds_partial(const float* __restrict__ V, int n, float* __re
     if (threadIdx.x < 6) part[blockIdx.x * 6 + threadIdx.x] = s[threadIdx.x][0];
 }
 
-// reduce the partials (one block) and emit Morton codes (grid-stride)
+// reduce the partials (one block) and emit Morton codes (grid-stride) of
+// triangles idx[0..n) (or 0..n-1): keys[k], vals[k] = triangle; codes[triangle]
+// too when codes is not NULL
 __global__ void k_morton(const float* __restrict__ V, int n, const float* __restrict__ part,
                          int nparts, uint32_t* __restrict__ codes, uint32_t* __restrict__ keys,
-                         int* __restrict__ vals)
+                         int* __restrict__ vals, const int* __restrict__ idx = nullptr)
 {
     __shared__ float lo[3], sc[3];
     if (threadIdx.x < 3) {
@@ -112,7 +116,8 @@ __global__ void k_morton(const float* __restrict__ V, int n, const float* __rest
         sc[threadIdx.x] = ext > 0.0f ? 1024.0f / ext : 0.0f;
     }
     __syncthreads();
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int i = idx ? idx[k] : k;
         uint32_t q[3];
         for (int a = 0; a < 3; ++a) {
             float f = (centroid(V, i, a) - lo[a]) * sc[a];
@@ -124,9 +129,9 @@ __global__ void k_morton(const float* __restrict__ V, int n, const float* __rest
         for (int b = 0; b < 10; ++b)
             code |= (((q[0] >> b) & 1u) << (3 * b + 2)) | (((q[1] >> b) & 1u) << (3 * b + 1)) |
                     (((q[2] >> b) & 1u) << (3 * b));
-        codes[i] = code;
-        keys[i] = code;
-        vals[i] = i;
+        if (codes) codes[i] = code;
+        keys[k] = code;
+        vals[k] = i;
     }
 }
 
@@ -278,6 +283,24 @@ __global__ void k_leaves(const float* __restrict__ V, const int* __restrict__ tr
     }
 }
 
+// records of the exhaustively tested (large) triangles at positions ns..n-1
+__global__ void k_big_leaves(const float* __restrict__ V, const int* __restrict__ tri_mat,
+                             const int* __restrict__ tri_light, const int* __restrict__ big_idx,
+                             int ns, int nb, int* __restrict__ order, float4* __restrict__ tris,
+                             int2* __restrict__ tri_ml)
+{
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    int prim = big_idx[b], k = ns + b;
+    const float* p = V + (size_t)prim * 9;
+    float v0x = p[0], v0y = p[1], v0z = p[2];
+    order[k] = prim;
+    tris[3 * k + 0] = make_float4(v0x, v0y, v0z, __int_as_float(prim));
+    tris[3 * k + 1] = make_float4(p[3] - v0x, p[4] - v0y, p[5] - v0z, 0.0f);
+    tris[3 * k + 2] = make_float4(p[6] - v0x, p[7] - v0y, p[8] - v0z, 0.0f);
+    tri_ml[k] = make_int2(tri_mat[prim], tri_light[prim]);
+}
+
 // bottom-up refit: the second child to arrive at a parent computes its box
 // and writes the 64-byte traversal node (both child boxes + child ids)
 __global__ void k_refit(int n, const int* __restrict__ left, const int* __restrict__ right,
@@ -311,71 +334,132 @@ __global__ void k_refit(int n, const int* __restrict__ left, const int* __restri
 
 inline int blocks_for(int64_t n, int per) { return (int)((n + per - 1) / per); }
 
+// The traversal structure: an LBVH over the scene's compact triangles (ns of
+// them, S->small_idx) plus the large triangles (S->big_idx) that every ray
+// tests exhaustively first -- large triangles (a ground plane, walls) would
+// otherwise inflate the boxes of the tree's upper levels.  The closest hit is
+// the same either way (smallest t, ties to the smaller triangle index).
 mrs_status build_lbvh(mrs_scene_s* S, cudaStream_t st)
 {
-    int n = S->n;
+    const int n = S->n, ns = S->ns, nb = n - ns;
     if (n <= 0) return MRS_OK;
     int nparts = 2 * sm_count();
-    int ntiles = blocks_for(n, kTile);
+    int ntiles = blocks_for(ns > 0 ? ns : 1, kTile);
     size_t need = sizeof(float) * 6 * nparts + sizeof(uint32_t) * 256 * (size_t)ntiles +
-                  (sizeof(uint32_t) + sizeof(int)) * 2 * (size_t)n + 256;
+                  (sizeof(uint32_t) + sizeof(int)) * 2 * (size_t)(ns > 0 ? ns : 1) + 256;
     mrs_status s = S->sort_tmp.ensure(need);
     if (s != MRS_OK) return s;
     char* p = S->sort_tmp.as<char>();
     float* part = (float*)p; p += sizeof(float) * 6 * nparts;
     uint32_t* counts = (uint32_t*)p; p += sizeof(uint32_t) * 256 * (size_t)ntiles;
-    uint32_t* ka = (uint32_t*)p; p += sizeof(uint32_t) * (size_t)n;
-    uint32_t* kb = (uint32_t*)p; p += sizeof(uint32_t) * (size_t)n;
-    int* va = (int*)p; p += sizeof(int) * (size_t)n;
+    uint32_t* ka = (uint32_t*)p; p += sizeof(uint32_t) * (size_t)ns;
+    uint32_t* kb = (uint32_t*)p; p += sizeof(uint32_t) * (size_t)ns;
+    int* va = (int*)p; p += sizeof(int) * (size_t)ns;
     int* vb = (int*)p;
 
     cudaEvent_t lbvh_a = prof_on() ? prof_record(st) : nullptr;
-    k_bounds_partial<<<nparts, kBlock, 0, st>>>(S->V, n, part);
-    MRS_LAUNCHED(1);
-    k_morton<<<min(blocks_for(n, kBlock), 8 * sm_count()), kBlock, 0, st>>>(S->V, n, part, nparts,
-                                                                        S->morton, ka, va);
-    MRS_LAUNCHED(1);
-    // 30-bit codes: digits at bits 0, 8, 16, 24 (4 passes, ends back in ka/va)
-    for (int pass = 0; pass < 4; ++pass) {
-        int shift = pass * 8;
-        uint32_t* kin = (pass & 1) ? kb : ka;
-        uint32_t* kout = (pass & 1) ? ka : kb;
-        int* vin = (pass & 1) ? vb : va;
-        int* vout = (pass & 1) ? va : vb;
-        k_sort_hist<<<ntiles, kBlock, 0, st>>>(kin, n, shift, counts, ntiles);
+    if (ns > 0) {
+        k_bounds_partial<<<nparts, kBlock, 0, st>>>(S->V, ns, part, S->small_idx);
         MRS_LAUNCHED(1);
-        k_sort_scan<<<1, 1024, 0, st>>>(counts, 256 * ntiles);
+        k_morton<<<min(blocks_for(ns, kBlock), 8 * sm_count()), kBlock, 0, st>>>(
+            S->V, ns, part, nparts, nullptr, ka, va, S->small_idx);
         MRS_LAUNCHED(1);
-        k_sort_scatter<<<ntiles, kBlock, 0, st>>>(kin, vin, kout, vout, n, shift, counts, ntiles);
+        // 30-bit codes: digits at bits 0, 8, 16, 24 (4 passes, ends back in ka/va)
+        for (int pass = 0; pass < 4; ++pass) {
+            int shift = pass * 8;
+            uint32_t* kin = (pass & 1) ? kb : ka;
+            uint32_t* kout = (pass & 1) ? ka : kb;
+            int* vin = (pass & 1) ? vb : va;
+            int* vout = (pass & 1) ? va : vb;
+            k_sort_hist<<<ntiles, kBlock, 0, st>>>(kin, ns, shift, counts, ntiles);
+            MRS_LAUNCHED(1);
+            k_sort_scan<<<1, 1024, 0, st>>>(counts, 256 * ntiles);
+            MRS_LAUNCHED(1);
+            k_sort_scatter<<<ntiles, kBlock, 0, st>>>(kin, vin, kout, vout, ns, shift, counts, ntiles);
+            MRS_LAUNCHED(1);
+        }
+        MRS_CHECK(cudaMemcpyAsync(S->skeys, ka, sizeof(uint32_t) * ns, cudaMemcpyDeviceToDevice, st));
+        MRS_CHECK(cudaMemcpyAsync(S->order, va, sizeof(int) * ns, cudaMemcpyDeviceToDevice, st));
+        if (ns > 1) {
+            k_karras<<<blocks_for(ns - 1, kBlock), kBlock, 0, st>>>(S->skeys, S->order, ns, S->left,
+                                                                   S->right, S->parent);
+            MRS_LAUNCHED(1);
+        }
+        k_leaves<<<blocks_for(ns, kBlock), kBlock, 0, st>>>(S->V, S->tri_mat, S->tri_light, S->order,
+                                                            ns, S->tris, S->tri_ml, S->box, S->visit);
         MRS_LAUNCHED(1);
+        if (ns > 1) {
+            k_refit<<<blocks_for(ns, kBlock), kBlock, 0, st>>>(ns, S->left, S->right, S->parent,
+                                                               S->box, S->visit, S->nodes);
+            MRS_LAUNCHED(1);
+        }
     }
-    MRS_CHECK(cudaMemcpyAsync(S->skeys, ka, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st));
-    MRS_CHECK(cudaMemcpyAsync(S->order, va, sizeof(int) * n, cudaMemcpyDeviceToDevice, st));
-    if (n > 1) {
-        k_karras<<<blocks_for(n - 1, kBlock), kBlock, 0, st>>>(S->skeys, S->order, n, S->left,
-                                                              S->right, S->parent);
-        MRS_LAUNCHED(1);
-    }
-    k_leaves<<<blocks_for(n, kBlock), kBlock, 0, st>>>(S->V, S->tri_mat, S->tri_light, S->order,
-                                                       n, S->tris, S->tri_ml, S->box, S->visit);
-    MRS_LAUNCHED(1);
-    if (n > 1) {
-        k_refit<<<blocks_for(n, kBlock), kBlock, 0, st>>>(n, S->left, S->right, S->parent, S->box,
-                                                          S->visit, S->nodes);
+    if (nb > 0) {
+        k_big_leaves<<<blocks_for(nb, kBlock), kBlock, 0, st>>>(S->V, S->tri_mat, S->tri_light,
+                                                                S->big_idx, ns, nb, S->order,
+                                                                S->tris, S->tri_ml);
         MRS_LAUNCHED(1);
     }
     if (lbvh_a) prof_push(PK_LBVH, lbvh_a, prof_record(st));
     return cuda_status(cudaGetLastError(), "lbvh launch");
 }
 
+// Large triangles: AABB extent >= 1/4 of the centroid bounds' largest extent,
+// at most kMaxBig of them (else none); computed on the host from the vertices.
+constexpr int kMaxBig = 64;
+void classify(const float* V, int n, std::vector<int>& small, std::vector<int>& big)
+{
+    small.clear();
+    big.clear();
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int i = 0; i < n; ++i)
+        for (int a = 0; a < 3; ++a) {
+            const float* p = V + (size_t)i * 9;
+            float c = ((p[a] + p[3 + a]) + p[6 + a]) * (1.0f / 3.0f);
+            lo[a] = fminf(lo[a], c);
+            hi[a] = fmaxf(hi[a], c);
+        }
+    float L = 0.0f;
+    for (int a = 0; a < 3; ++a) L = fmaxf(L, hi[a] - lo[a]);
+    for (int i = 0; i < n; ++i) {
+        const float* p = V + (size_t)i * 9;
+        float e = 0.0f;
+        for (int a = 0; a < 3; ++a)
+            e = fmaxf(e, fmaxf(fmaxf(p[a], p[3 + a]), p[6 + a]) - fminf(fminf(p[a], p[3 + a]), p[6 + a]));
+        (L > 0.0f && e >= 0.25f * L ? big : small).push_back(i);
+    }
+    if ((int)big.size() > kMaxBig) {
+        small.resize(n);
+        for (int i = 0; i < n; ++i) small[i] = i;
+        big.clear();
+    }
+}
+
+mrs_status upload_classes(mrs_scene_s* S, const float* V, cudaStream_t st)
+{
+    std::vector<int> small, big;
+    classify(V, S->n, small, big);
+    S->ns = (int)small.size();
+    if (!small.empty())
+        MRS_CHECK(cudaMemcpyAsync(S->small_idx, small.data(), sizeof(int) * small.size(),
+                                  cudaMemcpyHostToDevice, st));
+    if (!big.empty())
+        MRS_CHECK(cudaMemcpyAsync(S->big_idx, big.data(), sizeof(int) * big.size(),
+                                  cudaMemcpyHostToDevice, st));
+    // the vectors must outlive the copies
+    MRS_CHECK(cudaStreamSynchronize(st));
+    return MRS_OK;
+}
+
 void free_scene(mrs_scene_s* S)
 {
     void* ptrs[] = {S->V, S->tri_mat, S->tri_light, S->mats, S->lights, S->morton, S->skeys,
                     S->order, S->left, S->right, S->parent, S->visit, S->box, S->nodes,
-                    S->tris, S->tri_ml};
+                    S->tris, S->tri_ml, S->small_idx, S->big_idx};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     S->sort_tmp.release();
+    S->export_tmp.release();
     S->arena.release();
     delete S;
 }
@@ -554,6 +638,8 @@ extern "C" mrs_status mrs_build_scene(const float* V, int32_t n, const int32_t* 
     TRY(dalloc(&S->nodes, n > 1 ? 4 * (size_t)(n - 1) : 4));
     TRY(dalloc(&S->tris, 3 * (size_t)(n > 0 ? n : 1)));
     TRY(dalloc(&S->tri_ml, n > 0 ? n : 1));
+    TRY(dalloc(&S->small_idx, n > 0 ? n : 1));
+    TRY(dalloc(&S->big_idx, kMaxBig));
     if (n > 0) {
         TRY(cuda_status(cudaMemcpyAsync(S->V, V, sizeof(float) * 9 * (size_t)n, cudaMemcpyHostToDevice, st), "copy V"));
         TRY(cuda_status(cudaMemcpyAsync(S->tri_mat, tri_mat, sizeof(int) * n, cudaMemcpyHostToDevice, st), "copy tri_mat"));
@@ -563,6 +649,7 @@ extern "C" mrs_status mrs_build_scene(const float* V, int32_t n, const int32_t* 
         TRY(cuda_status(cudaMemcpyAsync(S->mats, mats, sizeof(float) * 8 * n_mats, cudaMemcpyHostToDevice, st), "copy mats"));
     if (n_lights > 0)
         TRY(cuda_status(cudaMemcpyAsync(S->lights, lights, sizeof(float) * 12 * n_lights, cudaMemcpyHostToDevice, st), "copy lights"));
+    if (n > 0) TRY(upload_classes(S, V, st));
     TRY(build_lbvh(S, st));
     TRY(cuda_status(cudaStreamSynchronize(st), "build_scene sync"));
 #undef TRY
@@ -584,8 +671,11 @@ extern "C" mrs_status mrs_scene_update_vertices(mrs_scene S, const float* V, int
     MRS_ARG(n == S->n, "n must equal the scene's triangle count");
     MRS_ARG(n == 0 || V != nullptr, "V is NULL");
     cudaStream_t st = (cudaStream_t)stream;
-    if (n > 0)
+    if (n > 0) {
         MRS_CHECK(cudaMemcpyAsync(S->V, V, sizeof(float) * 9 * (size_t)n, cudaMemcpyHostToDevice, st));
+        mrs_status s = upload_classes(S, V, st);
+        if (s != MRS_OK) return s;
+    }
     return build_lbvh(S, st);
 }
 
@@ -603,13 +693,65 @@ extern "C" mrs_status mrs_scene_export_bvh(mrs_scene S, uint32_t* morton, int32_
 {
     MRS_ARG(S != nullptr, "scene is NULL");
     cudaStream_t st = (cudaStream_t)stream;
-    int n = S->n;
+    const int n = S->n;
     if (n == 0) return MRS_OK;
-    if (morton) MRS_CHECK(cudaMemcpyAsync(morton, S->morton, 4 * (size_t)n, cudaMemcpyDeviceToDevice, st));
-    if (order) MRS_CHECK(cudaMemcpyAsync(order, S->order, 4 * (size_t)n, cudaMemcpyDeviceToDevice, st));
-    if (n > 1 && left) MRS_CHECK(cudaMemcpyAsync(left, S->left, 4 * (size_t)(n - 1), cudaMemcpyDeviceToDevice, st));
-    if (n > 1 && right) MRS_CHECK(cudaMemcpyAsync(right, S->right, 4 * (size_t)(n - 1), cudaMemcpyDeviceToDevice, st));
-    if (box) MRS_CHECK(cudaMemcpyAsync(box, S->box, 24 * (2 * (size_t)n - 1), cudaMemcpyDeviceToDevice, st));
+    // the LBVH over all n triangles, built by the same kernels
+    const int nparts = 2 * sm_count();
+    const int ntiles = blocks_for(n, kTile);
+    size_t need = sizeof(float) * 6 * nparts + sizeof(uint32_t) * 256 * (size_t)ntiles +
+                  sizeof(uint32_t) * 5 * (size_t)n + sizeof(int) * 7 * (size_t)n +
+                  sizeof(float) * 6 * (2 * (size_t)n) + 1024;
+    mrs_status rc = S->export_tmp.ensure(need);
+    if (rc != MRS_OK) return rc;
+    char* p = S->export_tmp.as<char>();
+    float* part = (float*)p; p += sizeof(float) * 6 * nparts;
+    uint32_t* counts = (uint32_t*)p; p += sizeof(uint32_t) * 256 * (size_t)ntiles;
+    uint32_t* codes = (uint32_t*)p; p += sizeof(uint32_t) * (size_t)n;
+    uint32_t* ka = (uint32_t*)p; p += sizeof(uint32_t) * (size_t)n;
+    uint32_t* kb = (uint32_t*)p; p += sizeof(uint32_t) * (size_t)n;
+    int* va = (int*)p; p += sizeof(int) * (size_t)n;
+    int* vb = (int*)p; p += sizeof(int) * (size_t)n;
+    int* ord = (int*)p; p += sizeof(int) * (size_t)n;
+    int* lft = (int*)p; p += sizeof(int) * (size_t)n;
+    int* rgt = (int*)p; p += sizeof(int) * (size_t)n;
+    int* par = (int*)p; p += sizeof(int) * 2 * (size_t)n;
+    int* vis = (int*)p; p += sizeof(int) * (size_t)n;
+    float* bx = (float*)p;
+    k_bounds_partial<<<nparts, kBlock, 0, st>>>(S->V, n, part);
+    MRS_LAUNCHED(1);
+    k_morton<<<min(blocks_for(n, kBlock), 8 * sm_count()), kBlock, 0, st>>>(S->V, n, part, nparts,
+                                                                        codes, ka, va);
+    MRS_LAUNCHED(1);
+    for (int pass = 0; pass < 4; ++pass) {
+        int shift = pass * 8;
+        uint32_t* kin = (pass & 1) ? kb : ka;
+        uint32_t* kout = (pass & 1) ? ka : kb;
+        int* vin = (pass & 1) ? vb : va;
+        int* vout = (pass & 1) ? va : vb;
+        k_sort_hist<<<ntiles, kBlock, 0, st>>>(kin, n, shift, counts, ntiles);
+        MRS_LAUNCHED(1);
+        k_sort_scan<<<1, 1024, 0, st>>>(counts, 256 * ntiles);
+        MRS_LAUNCHED(1);
+        k_sort_scatter<<<ntiles, kBlock, 0, st>>>(kin, vin, kout, vout, n, shift, counts, ntiles);
+        MRS_LAUNCHED(1);
+    }
+    MRS_CHECK(cudaMemcpyAsync(ord, va, sizeof(int) * (size_t)n, cudaMemcpyDeviceToDevice, st));
+    if (n > 1) {
+        k_karras<<<blocks_for(n - 1, kBlock), kBlock, 0, st>>>(ka, ord, n, lft, rgt, par);
+        MRS_LAUNCHED(1);
+    }
+    k_static_leaves<<<blocks_for(n, kBlock), kBlock, 0, st>>>(S->V, ord, n, bx, vis);
+    MRS_LAUNCHED(1);
+    if (n > 1) {
+        k_static_refit<<<blocks_for(n, kBlock), kBlock, 0, st>>>(n, lft, rgt, par, bx, vis);
+        MRS_LAUNCHED(1);
+    }
+    MRS_CHECK(cudaGetLastError());
+    if (morton) MRS_CHECK(cudaMemcpyAsync(morton, codes, 4 * (size_t)n, cudaMemcpyDeviceToDevice, st));
+    if (order) MRS_CHECK(cudaMemcpyAsync(order, ord, 4 * (size_t)n, cudaMemcpyDeviceToDevice, st));
+    if (n > 1 && left) MRS_CHECK(cudaMemcpyAsync(left, lft, 4 * (size_t)(n - 1), cudaMemcpyDeviceToDevice, st));
+    if (n > 1 && right) MRS_CHECK(cudaMemcpyAsync(right, rgt, 4 * (size_t)(n - 1), cudaMemcpyDeviceToDevice, st));
+    if (box) MRS_CHECK(cudaMemcpyAsync(box, bx, 24 * (2 * (size_t)n - 1), cudaMemcpyDeviceToDevice, st));
     return MRS_OK;
 }
 

@@ -109,7 +109,10 @@ struct mrs_scene_s {
     // LBVH
     uint32_t* morton = nullptr;  // [n] input order
     uint32_t* skeys = nullptr;   // [n] sorted codes
-    int* order = nullptr;        // [n] sorted position -> triangle
+    int* order = nullptr;        // [n] position -> triangle: BVH leaves 0..ns-1, large ns..n-1
+    int ns = 0;                  // triangles in the LBVH (the rest are tested exhaustively)
+    int* small_idx = nullptr;    // [ns] triangles of the LBVH, in input order
+    int* big_idx = nullptr;      // [n - ns] large triangles, in input order
     int* left = nullptr;         // [n-1]
     int* right = nullptr;        // [n-1]
     int* parent = nullptr;       // [2n-1]
@@ -119,6 +122,7 @@ struct mrs_scene_s {
     float4* tris = nullptr;      // [n][3]: (v0, prim bits), (e1, 0), (e2, 0) in sorted order
     int2* tri_ml = nullptr;      // [n]: material, light in sorted order
     mrs::Buf sort_tmp;           // radix-sort scratch
+    mrs::Buf export_tmp;         // full-scene LBVH built on export
     mrs::Buf arena;              // render path state
     int64_t wave_paths = int64_t(1) << 24;
 };

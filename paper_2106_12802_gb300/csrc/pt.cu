@@ -95,7 +95,7 @@ __device__ __forceinline__ void sincos2pi(float u, float& c, float& s)
 
 // ---- scene access -----------------------------------------------------------
 struct SceneView {
-    int n, n_lights;
+    int n, ns, n_lights;   // triangles; of them in the LBVH (positions 0..ns-1); lights
     const float4* __restrict__ nodes;
     const float4* __restrict__ tris;
     const int2* __restrict__ tri_ml;
@@ -141,15 +141,34 @@ template <bool kAny, bool kCount = false>
 __device__ int traverse(const SceneView& S, V3 o, V3 d, float tmax, float& t_out,
                         unsigned long long* nvisit = nullptr, unsigned long long* ntest = nullptr)
 {
-    const int n = S.n;
+    const int n = S.ns;
     int best = -1, best_prim = 0x7fffffff;
     float bt = tmax;
-    if (n == 0) return -1;
+    // large triangles (positions ns .. S.n-1) first: a hit there bounds the
+    // tree traversal below
+    for (int k = n; k < S.n; ++k) {
+        int prim;
+        if (kCount) ++*ntest;
+        float t = intersect(o, d, S.tris + 3 * k, kAny ? tmax : T_INF, prim);
+        if (t > 0.0f) {
+            if (kAny) { t_out = t; return k; }
+            if (t < bt || (t == bt && prim < best_prim)) { bt = t; best = k; best_prim = prim; }
+        }
+    }
+    if (n == 0) {
+        if (best >= 0) t_out = bt;
+        return best;
+    }
     if (n == 1) {
         int prim;
-        float t = intersect(o, d, S.tris, tmax, prim);
-        if (t > 0.0f) { t_out = t; return 0; }
-        return -1;
+        if (kCount) ++*ntest;
+        float t = intersect(o, d, S.tris, kAny ? tmax : T_INF, prim);
+        if (t > 0.0f) {
+            if (kAny) { t_out = t; return 0; }
+            if (t < bt || (t == bt && prim < best_prim)) { bt = t; best = 0; best_prim = prim; }
+        }
+        if (best >= 0) t_out = bt;
+        return best;
     }
     V3 inv = mk(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
     int stack[kStack];
@@ -333,7 +352,7 @@ __global__ void __launch_bounds__(kThreads) k_raygen(WaveParams w)
 }
 
 template <bool kCount>
-__global__ void __launch_bounds__(kThreads) k_trace(WaveParams w, int b)
+__global__ void __launch_bounds__(kThreads, 8) k_trace(WaveParams w, int b)
 {
     unsigned long long nv = 0, nt = 0;
     PathSoA& P = w.P;
@@ -515,7 +534,7 @@ __global__ void __launch_bounds__(kThreads) k_shade(WaveParams w, int b)
 }
 
 template <bool kCount>
-__global__ void __launch_bounds__(kThreads) k_shadow(WaveParams w, int b)
+__global__ void __launch_bounds__(kThreads, 8) k_shadow(WaveParams w, int b)
 {
     unsigned long long nv = 0, nt = 0;
     PathSoA& P = w.P;
@@ -611,7 +630,7 @@ __global__ void k_philox(const uint32_t* triples, int n, uint2 key, float* out)
 
 SceneView view(const mrs_scene_s* S)
 {
-    return SceneView{S->n, S->n_lights, S->nodes, S->tris, S->tri_ml, S->mats, S->lights};
+    return SceneView{S->n, S->ns, S->n_lights, S->nodes, S->tris, S->tri_ml, S->mats, S->lights};
 }
 
 inline int grid_for(int64_t n)
