@@ -262,6 +262,7 @@ def equal_psnr(mrs, scene, s, ref_spp=4096, train_scenes=8, train_steps=1500):
         lr[None], hr["radiance"][None], hr["albedo"][None], hr["normal"][None], s, precision="fp32")
     p_lr_up = mrs.image_metrics(up[0].contiguous(), ref)[0]
     p_hrls = mrs.image_metrics(hr["radiance"], ref)[0]
+    equal_psnr.trained_params = net.get_params()
     return {"reference_spp": ref_spp, "hybrid_psnr_db": p_h, "hybrid_ms": t_h,
             "upsampled_lrhs_psnr_db": p_lr_up, "hrls_psnr_db": p_hrls, "plain_spp_at_equal_psnr": n_eq,
             "plain_psnr_db": plain_psnr(n_eq), "plain_ms": t_p, "speedup_plain_over_hybrid": t_p / t_h,
@@ -269,6 +270,106 @@ def equal_psnr(mrs, scene, s, ref_spp=4096, train_scenes=8, train_steps=1500):
             "training": f"{train_scenes} procedural scenes (seeds 1..{train_scenes}) at {HR}^2, "
                         f"targets 256 spp, {train_steps} Adam steps, batch 8 x 96^2, lr 1e-3, "
                         f"{t_train:.1f} s"}
+
+
+# ----------------------------------------------------------------------------
+# batched serving: many frames of uneven size, scale and spp in one CUDA graph
+# ----------------------------------------------------------------------------
+def batched_serving(mrs, params, n_jobs=32, n_scenes=4, psnr_jobs=4, seed=5):
+    """32 hybrid frames (HR in {512, 1024, 2048}^2, scale in {2, 4}, HRLS spp in
+    {1, 2, 4, 8}, LRHS 64 spp) over a pool of procedural scenes, each frame =
+    LRHS + HRLS renders, fusion and the device-side gate, all captured in one
+    CUDA graph per fusion precision.  Render wave sizes are autotuned per
+    shape.  PSNR against 4096-spp references is reported for the first
+    `psnr_jobs` frames that are at most 1024^2."""
+    import torch
+
+    from paper_2106_12802_gb300 import autotune
+    from synth import scenes
+    rng = np.random.default_rng(seed)
+    pool = [mrs.Scene(scenes.procedural(100 + k)) for k in range(n_scenes)]
+    jobs = []
+    for j in range(n_jobs):
+        jobs.append({"scene": int(rng.integers(n_scenes)), "hr": int(rng.choice([512, 1024, 2048])),
+                     "s": int(rng.choice([2, 4])), "spp_h": int(rng.choice([1, 2, 4, 8])),
+                     "seed": 1000 + j})
+    net = mrs.Net(params)
+    dev = torch.device("cuda")
+    bufs, waves = [], {}
+    for jb in jobs:
+        H, s = jb["hr"], jb["s"]
+        bufs.append({"lr": torch.empty((1, H // s, H // s, 3), device=dev),
+                     "hr": torch.empty((1, H, H, 3), device=dev),
+                     "alb": torch.empty((1, H, H, 3), device=dev),
+                     "nrm": torch.empty((1, H, H, 3), device=dev),
+                     "dep": torch.empty((1, H, H), device=dev),
+                     "fused": torch.empty((1, H, H, 3), device=dev),
+                     "out": torch.empty((1, H, H, 3), device=dev),
+                     "used": torch.zeros(2, dtype=torch.int32, device=dev),
+                     "D": torch.zeros(1, dtype=torch.float64, device=dev)})
+    # autotune the wave per render shape (outside the graph)
+    for jb in jobs:
+        sc = pool[jb["scene"]]
+        for (W, spp) in ((jb["hr"] // jb["s"], SPP_LR), (jb["hr"], jb["spp_h"])):
+            if (W, spp) not in waves:
+                waves[(W, spp)] = autotune.tune_wave(sc, W, W, spp, DEPTH, RR, cache=None, reps=1)[0]
+
+    def batch(prec):
+        for jb, b in zip(jobs, bufs):
+            sc = pool[jb["scene"]]
+            H, s = jb["hr"], jb["s"]
+            sc.set_wave(waves[(H // s, SPP_LR)])
+            mrs.render(sc, H // s, H // s, SPP_LR, DEPTH, RR, jb["seed"], out={"radiance": b["lr"][0]})
+            sc.set_wave(waves[(H, jb["spp_h"])])
+            mrs.render(sc, H, H, jb["spp_h"], DEPTH, RR, jb["seed"] + 7,
+                       out={"radiance": b["hr"][0], "albedo": b["alb"][0], "normal": b["nrm"][0],
+                            "depth": b["dep"][0]})
+            net.fuse(b["lr"], b["hr"], b["alb"], b["nrm"], s, precision=prec, out=b["fused"])
+            mrs.gate_async(b["fused"], b["lr"], None, s, 0.01, out=b["out"], used=b["used"], D=b["D"])
+
+    result = {"jobs": n_jobs, "distinct_scenes": n_scenes,
+              "hr_mix": {str(r): sum(1 for jb in jobs if jb["hr"] == r) for r in (512, 1024, 2048)},
+              "paths_per_batch": int(sum((jb["hr"] // jb["s"]) ** 2 * SPP_LR + jb["hr"] ** 2 * jb["spp_h"]
+                                         for jb in jobs))}
+    refs = {}
+    for prec in ("bf16", "fp8"):
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            batch(prec)                      # warm-up: sizes buffers, packs / calibrates weights
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            batch(prec)
+        g.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 3
+        e0.record()
+        for _ in range(reps):
+            g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        ps = []
+        for jb, b in zip(jobs, bufs):
+            if len(ps) >= psnr_jobs:
+                break
+            if jb["hr"] > 1024:
+                continue
+            key = id(b)
+            if key not in refs:
+                refs[key] = mrs.render(pool[jb["scene"]], jb["hr"], jb["hr"], 4096, DEPTH, RR,
+                                       99991, aux=False, counts=False)["radiance"]
+            ps.append(mrs.image_metrics(b["fused"][0].contiguous(), refs[key])[0])
+        result[prec] = {"ms_per_batch": ms, "frames_per_s": n_jobs / ms * 1e3,
+                        "mean_psnr_db_vs_4096spp": float(np.mean(ps)) if ps else None,
+                        "psnr_frames": len(ps)}
+        del g
+    for sc in pool:
+        sc.close()
+    return result
 
 
 # ----------------------------------------------------------------------------
@@ -371,6 +472,9 @@ def run_gpu(args, rank, world):
     extra = {}
     if rank == 0 and not args.quick and not args.no_equal_psnr:
         extra["equal_psnr"] = equal_psnr(mrs, scene, S)
+    if rank == 0 and not args.quick and not args.no_batched:
+        p = getattr(equal_psnr, "trained_params", None)
+        extra["batched_serving"] = batched_serving(mrs, p if p is not None else params)
     if rank == 0 and not args.quick:
         stats_lr = mrs.render_stats(scene, LR, LR, SPP_LR, DEPTH, RR, 0)
         stats_hr = mrs.render_stats(scene, HR, HR, SPP_HR, DEPTH, RR, 1)
@@ -451,6 +555,7 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip context measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-equal-psnr", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

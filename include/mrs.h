@@ -179,6 +179,14 @@ mrs_status mrs_render_stats(mrs_scene scene, int32_t W, int32_t H, int32_t spp, 
 mrs_status mrs_profile_enable(int32_t on);
 mrs_status mrs_profile_read(int32_t kernel, double* total_ms, int64_t* launches);
 
+/* Failure-detection self-test (no paper counterpart): launches a kernel whose
+ * bounded device-side wait (the kind every tensor-core kernel uses on its
+ * mbarriers) waits for an event that never happens.  The wait must give up
+ * after limit_us microseconds (1 .. 100000), raise the kernel's error word
+ * and return; the call then returns MRS_ERR_TIMEOUT and the CUDA context
+ * stays usable.  Synchronises `stream`. */
+mrs_status mrs_selftest_wait_timeout(int32_t limit_us, void* stream);
+
 /* Paths per wave for subsequent mrs_render calls on this scene (rounded to
  * whole samples of the image; default 16M paths).  For tests and tuning. */
 mrs_status mrs_scene_set_wave(mrs_scene scene, int64_t max_paths_per_wave);
@@ -269,6 +277,17 @@ mrs_status mrs_image_metrics(const float* x, const float* ref, int64_t n, double
 mrs_status mrs_gate(const float* fused, const float* lrhs, const float* plain, int32_t N,
                     int32_t H, int32_t W, int32_t scale, double tau, float* out,
                     int32_t* used_plain, double* D, void* stream);
+
+/* The same gate without any host synchronisation (capturable in a CUDA
+ * graph): the decision stays on the device.  used_plain is a DEVICE int32[2]:
+ * [0] = 1 if D > tau, [1] = 1 if `out` received the plain render (plain given
+ * and D > tau); D (DEVICE double, may be NULL) receives D.  out receives
+ * plain or fused accordingly (out may alias fused).  The first call allocates
+ * a small reduction buffer (make it before any stream capture); concurrent
+ * calls from several threads are serialised. */
+mrs_status mrs_gate_async(const float* fused, const float* lrhs, const float* plain, int32_t N,
+                          int32_t H, int32_t W, int32_t scale, double tau, float* out,
+                          int32_t* used_plain, double* D, void* stream);
 
 /* One 3x3 convolution with zero padding (a single layer of the network, for
  * testing and tuning): x device float [N][H][W][cin], w HOST float

@@ -94,18 +94,23 @@ __device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t pari
 // bounded wait; false if this or another role gave up.  Each poll lets the
 // hardware suspend the thread (1 ms limit) until the phase completes; the
 // error word and the clock are consulted between polls
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err)
+__device__ __forceinline__ bool mbar_wait_limit(uint64_t* bar, uint32_t parity, int* err,
+                                                long long limit_cycles, uint32_t sleep_ns)
 {
     if (mbar_try_wait(bar, parity)) return true;
     long long t0 = clock64();
     for (;;) {
-        if (mbar_try_wait_sleep(bar, parity, 1000000u)) return true;
+        if (mbar_try_wait_sleep(bar, parity, sleep_ns)) return true;
         if (*(volatile int*)err) return false;
-        if (clock64() - t0 > kTimeoutCycles) {
+        if (clock64() - t0 > limit_cycles) {
             atomicExch(err, 1);
             return false;
         }
     }
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err)
+{
+    return mbar_wait_limit(bar, parity, err, kTimeoutCycles, 1000000u);
 }
 
 // warp-wide wait: lane 0 polls, then every lane observes the completed phase
@@ -624,6 +629,40 @@ mrs_status tc_make_w_map(CUtensorMap* m, const void* ptr, int rows, int nout, in
                     operand == TC_BF16 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) { set_error("cuTensorMapEncodeTiled(w) failed: %d", (int)r); return MRS_ERR_CUDA; }
+    return MRS_OK;
+}
+
+namespace {
+// waits on an mbarrier that nothing completes; the bounded wait must give up,
+// raise the error word and return (exercises the kernels' timeout path)
+__global__ void k_wait_selftest(int* err, long long limit_cycles, int* gave_up)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        bool ok = mbar_wait_limit(&bar, 0, err, limit_cycles, 1000u);
+        *gave_up = ok ? 0 : 1;
+    }
+}
+}  // namespace
+
+mrs_status tc_wait_selftest(long long limit_cycles, int* gave_up, cudaStream_t st)
+{
+    int* d = nullptr;
+    MRS_CHECK(cudaMalloc(&d, 2 * sizeof(int)));
+    MRS_CHECK(cudaMemsetAsync(d, 0, 2 * sizeof(int), st));
+    k_wait_selftest<<<1, 32, 0, st>>>(d, limit_cycles, d + 1);
+    MRS_LAUNCHED(1);
+    int h[2] = {0, 0};
+    mrs_status rc = cuda_status(cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, st), "selftest copy");
+    if (rc == MRS_OK) rc = cuda_status(cudaStreamSynchronize(st), "selftest sync");
+    cudaFree(d);
+    if (rc != MRS_OK) return rc;
+    *gave_up = h[1] && h[0];
     return MRS_OK;
 }
 

@@ -58,4 +58,8 @@ mrs_status tc_make_w_map(CUtensorMap* m, const void* ptr, int rows, int nout, in
 
 mrs_status tc_conv3x3(const TcConvArgs& a, cudaStream_t st);
 
+// Launches a kernel whose bounded mbarrier wait can never complete; *gave_up
+// = 1 if the wait gave up after limit_cycles and raised the error word.
+mrs_status tc_wait_selftest(long long limit_cycles, int* gave_up, cudaStream_t st);
+
 }  // namespace mrs

@@ -503,6 +503,31 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float
     }
 }
 
+// gate decision on the device: D = sum / count; use_plain = D > tau
+__global__ void k_gate_decide(const double* part, int nparts, double count, double tau,
+                              int use_plain_avail, int* used_plain, double* D)
+{
+    if (threadIdx.x == 0) {
+        double acc = 0;
+        for (int i = 0; i < nparts; ++i) acc += part[i];
+        double d = acc / count;
+        if (D) *D = d;
+        int u = d > tau ? 1 : 0;
+        used_plain[0] = u;
+        used_plain[1] = u && use_plain_avail;     // whether `out` takes the plain render
+    }
+}
+
+// out = plain if the gate chose it (and a plain render was given), else fused
+__global__ void k_gate_select(const float* __restrict__ fused, const float* __restrict__ plain,
+                              size_t n, const int* __restrict__ choice, float* __restrict__ out)
+{
+    const float* src = choice[1] != 0 ? plain : fused;
+    if (src == out) return;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = src[i];
+}
+
 struct Scratch {
     std::mutex mu;
     Buf b;
@@ -1113,4 +1138,46 @@ extern "C" mrs_status mrs_net_set_state(mrs_net net, const float* params, const 
     net->step = step;
     net->bf_valid = net->f8_valid = net->xscale_valid = false;
     return MRS_OK;
+}
+
+extern "C" mrs_status mrs_selftest_wait_timeout(int32_t limit_us, void* stream)
+{
+    MRS_ARG(limit_us >= 1 && limit_us <= 100000, "limit_us must be in [1, 100000]");
+    int clk_khz = 0, dev = 0;
+    MRS_CHECK(cudaGetDevice(&dev));
+    MRS_CHECK(cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, dev));
+    long long cycles = (long long)limit_us * (clk_khz > 0 ? clk_khz : 2000000) / 1000;
+    int gave_up = 0;
+    mrs_status rc = tc_wait_selftest(cycles, &gave_up, (cudaStream_t)stream);
+    if (rc != MRS_OK) return rc;
+    if (gave_up) {
+        set_error("device wait gave up after %d us (self-test)", limit_us);
+        return MRS_ERR_TIMEOUT;
+    }
+    return MRS_OK;
+}
+
+extern "C" mrs_status mrs_gate_async(const float* fused, const float* lrhs, const float* plain,
+                                     int32_t N, int32_t H, int32_t W, int32_t scale, double tau,
+                                     float* out, int32_t* used_plain, double* D, void* stream)
+{
+    MRS_ARG(fused && lrhs && out && used_plain, "NULL pointer");
+    MRS_ARG(scale >= 1 && N >= 1 && H >= scale && W >= scale && H % scale == 0 && W % scale == 0,
+            "bad sizes");
+    cudaStream_t st = (cudaStream_t)stream;
+    static std::mutex mu;
+    static Buf parts;
+    std::lock_guard<std::mutex> g(mu);
+    mrs_status rc = parts.ensure(sizeof(double) * kRedBlocks);
+    if (rc != MRS_OK) return rc;
+    k_gate_partial<<<kRedBlocks, 256, 0, st>>>(fused, lrhs, N, H, W, scale, parts.as<double>());
+    MRS_LAUNCHED(1);
+    k_gate_decide<<<1, 32, 0, st>>>(parts.as<double>(), kRedBlocks,
+                                    (double)N * (H / scale) * (W / scale) * 3, tau,
+                                    plain ? 1 : 0, used_plain, D);
+    MRS_LAUNCHED(1);
+    size_t n = (size_t)N * H * W * 3;
+    k_gate_select<<<1024, 256, 0, st>>>(fused, plain ? plain : fused, n, used_plain, out);
+    MRS_LAUNCHED(1);
+    return cuda_status(cudaGetLastError(), "gate_async launch");
 }

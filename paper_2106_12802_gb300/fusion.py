@@ -152,6 +152,21 @@ def image_metrics(x, ref, lam1=0.5, lam2=0.01, stream=None):
     return float(out[0]), float(out[1]), float(out[2])
 
 
+def gate_async(fused, lrhs, plain, scale, tau=0.01, out=None, used=None, D=None, stream=None):
+    """Device-side fallback gate (no host sync; capturable).  Returns (out,
+    used[int32 x2 device], D[float64 device])."""
+    N, H, W, _ = fused.shape
+    if out is None:
+        out = torch.empty_like(fused)
+    if used is None:
+        used = torch.zeros(2, dtype=torch.int32, device=fused.device)
+    if D is None:
+        D = torch.zeros(1, dtype=torch.float64, device=fused.device)
+    call("mrs_gate_async", _ptr(fused), _ptr(lrhs), _ptr(plain), N, H, W, scale, float(tau),
+         _ptr(out), _ptr(used), _ptr(D), _stream(stream))
+    return out, used, D
+
+
 def gate(fused, lrhs, plain, scale, tau=0.01, out=None, stream=None):
     """Fallback gate: returns (out, used_plain, D)."""
     N, H, W, _ = fused.shape
