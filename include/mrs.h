@@ -45,6 +45,7 @@ typedef int32_t mrs_status;
 
 typedef struct mrs_scene_s* mrs_scene;
 typedef struct mrs_net_s* mrs_net;
+typedef struct mrs_ctx_s* mrs_ctx;
 
 /* Human-readable name of a status code (static string). */
 const char* mrs_status_string(mrs_status s);
@@ -186,6 +187,21 @@ mrs_status mrs_profile_read(int32_t kernel, double* total_ms, int64_t* launches)
  * and return; the call then returns MRS_ERR_TIMEOUT and the CUDA context
  * stays usable.  Synchronises `stream`. */
 mrs_status mrs_selftest_wait_timeout(int32_t limit_us, void* stream);
+
+/* Render contexts.  mrs_render keeps its path state in the scene handle, so
+ * renders of one scene are serialised; a context owns its own path-state
+ * arena, so renders of the same scene through different contexts may run
+ * concurrently on different streams (e.g. the LRHS and HRLS renders of a
+ * frame, whose low-occupancy last bounces then overlap).  mrs_render_ctx takes
+ * the arguments of mrs_render; the arena is allocated on first use and grown
+ * on demand (make the first call before any stream capture). */
+mrs_status mrs_ctx_create(mrs_ctx* out);
+mrs_status mrs_ctx_free(mrs_ctx ctx);
+mrs_status mrs_ctx_set_wave(mrs_ctx ctx, int64_t max_paths_per_wave);
+mrs_status mrs_render_ctx(mrs_ctx ctx, mrs_scene scene, int32_t W, int32_t H, int32_t spp,
+                          int32_t max_depth, int32_t rr_start, uint64_t seed, float* radiance,
+                          float* albedo, float* normal, float* depth, uint64_t* counts,
+                          uint64_t* shadow_counts, void* stream);
 
 /* Paths per wave for subsequent mrs_render calls on this scene (rounded to
  * whole samples of the image; default 16M paths).  For tests and tuning. */

@@ -127,6 +127,13 @@ struct mrs_scene_s {
     int64_t wave_paths = int64_t(1) << 24;
 };
 
+// Render context: a path-state arena of its own, so that several renders of
+// the same scene can run concurrently on different streams.
+struct mrs_ctx_s {
+    mrs::Buf arena;
+    int64_t wave_paths = int64_t(1) << 24;
+};
+
 // Layout of the render arena for a wave of P paths (floats unless noted).
 namespace mrs {
 struct PathSoA {

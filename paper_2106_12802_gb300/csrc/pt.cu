@@ -646,10 +646,11 @@ inline int grid_for(int64_t n)
 
 using namespace mrs;
 
-static mrs_status render_impl(mrs_scene S, int32_t W, int32_t H, int32_t spp, int32_t max_depth,
-                              int32_t rr_start, uint64_t seed, float* radiance, float* albedo,
-                              float* normal, float* depth, uint64_t* counts,
-                              uint64_t* shadow_counts, unsigned long long* stats, void* stream)
+static mrs_status render_impl(mrs_scene S, Buf& arena, int64_t wave_paths, int32_t W, int32_t H,
+                              int32_t spp, int32_t max_depth, int32_t rr_start, uint64_t seed,
+                              float* radiance, float* albedo, float* normal, float* depth,
+                              uint64_t* counts, uint64_t* shadow_counts,
+                              unsigned long long* stats, void* stream)
 {
     MRS_ARG(S != nullptr, "scene is NULL");
     MRS_ARG(W >= 1 && W <= 16384 && H >= 1 && H <= 16384, "W, H must be in [1, 16384]");
@@ -658,7 +659,7 @@ static mrs_status render_impl(mrs_scene S, int32_t W, int32_t H, int32_t spp, in
     MRS_ARG(radiance != nullptr, "radiance is NULL");
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t wh = (int64_t)W * H;
-    int64_t k = S->wave_paths / wh;
+    int64_t k = wave_paths / wh;
     if (k < 1) k = 1;
     if (k > spp) k = spp;
     MRS_ARG(k * wh <= (int64_t(1) << 31) - 1, "wave too large");
@@ -668,9 +669,9 @@ static mrs_status render_impl(mrs_scene S, int32_t W, int32_t H, int32_t spp, in
     const int kArrays = 33;
     size_t arr = ((size_t)P * 4 + 255) & ~(size_t)255;
     size_t need = arr * kArrays + (size_t)wh * 13 * 4 + 256 + 4 * 2 * 64;
-    mrs_status s = S->arena.ensure(need);
+    mrs_status s = arena.ensure(need);
     if (s != MRS_OK) return s;
-    char* base = S->arena.as<char>();
+    char* base = arena.as<char>();
     float* f[kArrays];
     for (int i = 0; i < kArrays; ++i) f[i] = (float*)(base + arr * i);
     PathSoA soa;
@@ -739,18 +740,55 @@ extern "C" mrs_status mrs_render(mrs_scene S, int32_t W, int32_t H, int32_t spp,
                                  float* normal, float* depth, uint64_t* counts,
                                  uint64_t* shadow_counts, void* stream)
 {
-    return render_impl(S, W, H, spp, max_depth, rr_start, seed, radiance, albedo, normal, depth,
-                       counts, shadow_counts, nullptr, stream);
+    MRS_ARG(S != nullptr, "scene is NULL");
+    return render_impl(S, S->arena, S->wave_paths, W, H, spp, max_depth, rr_start, seed, radiance,
+                       albedo, normal, depth, counts, shadow_counts, nullptr, stream);
+}
+
+extern "C" mrs_status mrs_ctx_create(mrs_ctx* out)
+{
+    MRS_ARG(out != nullptr, "out is NULL");
+    *out = new mrs_ctx_s();
+    return MRS_OK;
+}
+
+extern "C" mrs_status mrs_ctx_free(mrs_ctx ctx)
+{
+    if (!ctx) return MRS_OK;
+    cudaDeviceSynchronize();
+    ctx->arena.release();
+    delete ctx;
+    return MRS_OK;
+}
+
+extern "C" mrs_status mrs_ctx_set_wave(mrs_ctx ctx, int64_t max_paths)
+{
+    MRS_ARG(ctx != nullptr, "ctx is NULL");
+    MRS_ARG(max_paths >= 1 && max_paths <= (int64_t(1) << 30), "wave size out of range [1, 2^30]");
+    ctx->wave_paths = max_paths;
+    return MRS_OK;
+}
+
+extern "C" mrs_status mrs_render_ctx(mrs_ctx ctx, mrs_scene S, int32_t W, int32_t H, int32_t spp,
+                                     int32_t max_depth, int32_t rr_start, uint64_t seed,
+                                     float* radiance, float* albedo, float* normal, float* depth,
+                                     uint64_t* counts, uint64_t* shadow_counts, void* stream)
+{
+    MRS_ARG(ctx != nullptr, "ctx is NULL");
+    MRS_ARG(S != nullptr, "scene is NULL");
+    return render_impl(S, ctx->arena, ctx->wave_paths, W, H, spp, max_depth, rr_start, seed,
+                       radiance, albedo, normal, depth, counts, shadow_counts, nullptr, stream);
 }
 
 extern "C" mrs_status mrs_render_stats(mrs_scene S, int32_t W, int32_t H, int32_t spp,
                                        int32_t max_depth, int32_t rr_start, uint64_t seed,
                                        float* radiance, uint64_t* stats, void* stream)
 {
+    MRS_ARG(S != nullptr, "scene is NULL");
     MRS_ARG(stats != nullptr, "stats is NULL");
     MRS_CHECK(cudaMemsetAsync(stats, 0, 4 * sizeof(uint64_t), (cudaStream_t)stream));
-    return render_impl(S, W, H, spp, max_depth, rr_start, seed, radiance, nullptr, nullptr, nullptr,
-                       nullptr, nullptr, (unsigned long long*)stats, stream);
+    return render_impl(S, S->arena, S->wave_paths, W, H, spp, max_depth, rr_start, seed, radiance,
+                       nullptr, nullptr, nullptr, nullptr, nullptr, (unsigned long long*)stats, stream);
 }
 
 extern "C" mrs_status mrs_cast(mrs_scene S, const float* orig, const float* dir, int32_t n,

@@ -108,9 +108,35 @@ class Scene:
         return prim, t
 
 
+class RenderContext:
+    """A path-state arena of its own (mrs_ctx): renders of one scene through
+    different contexts may run concurrently on different streams."""
+
+    def __init__(self):
+        load()
+        h = ctypes.c_void_p()
+        call("mrs_ctx_create", ctypes.byref(h))
+        self.handle = h
+
+    def set_wave(self, paths: int):
+        call("mrs_ctx_set_wave", self.handle, int(paths))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            call("mrs_ctx_free", self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def render(scene: Scene, W, H, spp, max_depth, rr_start=None, seed=0, aux=True, counts=True,
-           out=None, stream=None):
-    """mrs_render into device tensors; returns dict of (device) tensors."""
+           out=None, stream=None, ctx: RenderContext | None = None):
+    """mrs_render (or mrs_render_ctx when ctx is given) into device tensors;
+    returns dict of (device) tensors."""
     dev = torch.device("cuda")
     if out is None:
         out = {"radiance": torch.empty((H, W, 3), dtype=torch.float32, device=dev)}
@@ -121,10 +147,14 @@ def render(scene: Scene, W, H, spp, max_depth, rr_start=None, seed=0, aux=True, 
         if counts:
             out["counts"] = torch.zeros(max_depth + 1, dtype=torch.int64, device=dev)
             out["shadow_counts"] = torch.zeros(max_depth + 1, dtype=torch.int64, device=dev)
-    call("mrs_render", scene.handle, W, H, spp, max_depth, -1 if rr_start is None else rr_start,
-         int(seed) & 0xFFFFFFFFFFFFFFFF, _ptr(out["radiance"]), _ptr(out.get("albedo")),
-         _ptr(out.get("normal")), _ptr(out.get("depth")), _ptr(out.get("counts")),
-         _ptr(out.get("shadow_counts")), _stream(stream))
+    args = (W, H, spp, max_depth, -1 if rr_start is None else rr_start,
+            int(seed) & 0xFFFFFFFFFFFFFFFF, _ptr(out["radiance"]), _ptr(out.get("albedo")),
+            _ptr(out.get("normal")), _ptr(out.get("depth")), _ptr(out.get("counts")),
+            _ptr(out.get("shadow_counts")), _stream(stream))
+    if ctx is None:
+        call("mrs_render", scene.handle, *args)
+    else:
+        call("mrs_render_ctx", ctx.handle, scene.handle, *args)
     return out
 
 
