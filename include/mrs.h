@@ -258,8 +258,11 @@ mrs_status mrs_fuse(mrs_net net, const float* lrhs, const float* hrls, const flo
  * reductions), and one bias-corrected Adam update (beta1 0.9, beta2 0.999,
  * eps 1e-8) of the FP32 master weights.  LRHS, HRLS and the target are
  * clipped at 100 first (firefly clipping of the training data, Sec. 3.2).
- * Image arguments as in mrs_fuse plus target device [N][H][W][3];
- * precision must be MRS_PREC_FP32.  loss_out (HOST, may be NULL) receives
+ * Image arguments as in mrs_fuse plus target device [N][H][W][3].
+ * precision MRS_PREC_FP32: every convolution in FP32 (SIMT);
+ * MRS_PREC_BF16: forward and transposed convolutions on the tensor cores
+ * with BF16 activations and activation gradients, FP32 accumulation, FP32
+ * dW / db reductions and FP32 master weights.  loss_out (HOST, may be NULL) receives
  * the loss before the update; when non-NULL the call synchronises `stream`.
  * Limit: N*H*W <= 2^22 pixels. */
 mrs_status mrs_train_step(mrs_net net, const float* lrhs, const float* hrls, const float* albedo,

@@ -283,7 +283,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int XB = (a.W + kTileOut - 1) / kTileOut;
     const int njobs = a.N * XB * a.segs;
-    const bool bf_out = a.mode == TC_RELU_BF16 || a.mode == TC_RESID_BF16;
+    const bool bf_out = a.mode == TC_RELU_BF16 || a.mode == TC_RESID_BF16 ||
+                        a.mode == TC_LIN_BF16 || a.mode == TC_MASK_BF16;
+    const bool loads_res = a.mode == TC_RESID_BF16 || a.mode == TC_MASK_BF16;
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < stages; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
@@ -344,7 +346,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int y = y0; y < y1; ++y, ++j) {
                     uint32_t slot = j % kSlots, use = j / kSlots;
                     if (!mbar_wait(&rempty[slot], (use & 1) ^ 1, a.err)) { ok = false; break; }
-                    if (a.mode == TC_RESID_BF16) {
+                    if (loads_res) {
                         mbar_expect_tx(&rfull[slot], kTileOut * 128);
                         tma_load_4d(sS + slot * SBYTES, &tmap_res, 0, xb * kTileOut, y, n, &rfull[slot]);
                     } else {
@@ -467,7 +469,19 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (a.mode == TC_RELU_BF16) {
 #pragma unroll
                         for (int e = 0; e < 16; ++e) o[e] = fmaxf(o[e], 0.0f);
-                    } else {
+                    } else if (a.mode == TC_MASK_BF16) {
+#pragma unroll
+                        for (int jj = 0; jj < 2; ++jj) {
+                            uint4 u = *(const uint4*)(srow + sw128(j, c0 / 8 + jj));
+                            const __nv_bfloat162* h2 = (const __nv_bfloat162*)&u;
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                float2 f = __bfloat1622float2(h2[e]);
+                                if (!(f.x > 0.0f)) o[8 * jj + 2 * e] = 0.0f;
+                                if (!(f.y > 0.0f)) o[8 * jj + 2 * e + 1] = 0.0f;
+                            }
+                        }
+                    } else if (a.mode == TC_RESID_BF16) {
 #pragma unroll
                         for (int jj = 0; jj < 2; ++jj) {
                             uint4 u = *(const uint4*)(srow + sw128(j, c0 / 8 + jj));

@@ -16,6 +16,8 @@ enum TcMode : int {
     TC_RESID_BF16 = 1,  // out_bf16[p][64] = res[p] + (acc + b)   (res may alias out)
     TC_FINAL_F32 = 2,   // out_f32[p][3]  = (acc + b) + bilinear_up(lrhs)[p]
     TC_PLAIN_F32 = 3,   // out_f32[p][cout] = acc + b, optional relu
+    TC_LIN_BF16 = 4,    // out_bf16[p][64] = acc + b
+    TC_MASK_BF16 = 5,   // out_bf16[p][64] = mask[p] > 0 ? acc + b : 0   (mask via tmap_res)
 };
 
 enum TcOperand : int { TC_BF16 = 0, TC_FP8 = 1 };

@@ -373,9 +373,14 @@ __global__ void k_wtrans(const float* __restrict__ w, int cin, int cout, float* 
 // dW[o][t][c] = sum_p dy[p][o] * x[p shifted by tap t][c] (zero padded), db[o] = sum_p dy[p][o]
 // grid (G, 9): block (g, t) reduces pixel tiles g, g+G, ... for tap t into part[g][t][o][c]
 constexpr int kDwTile = 64;
+__device__ __forceinline__ float ldf(const float* p) { return *p; }
+__device__ __forceinline__ float ldf(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+
+// x [P][xs] (first cin channels used), dy [P][ys] (first cout used); fp32 or bf16
+template <typename TX, typename TY>
 __global__ void __launch_bounds__(256)
-    k_dw_partial(const float* __restrict__ x, int cin, const float* __restrict__ dy, int cout,
-                 int N, int H, int W, float* __restrict__ part, float* __restrict__ dbpart)
+    k_dw_partial(const TX* __restrict__ x, int cin, int xs, const TY* __restrict__ dy, int cout,
+                 int ys, int N, int H, int W, float* __restrict__ part, float* __restrict__ dbpart)
 {
     __shared__ __align__(16) float sdy[kDwTile][64];
     __shared__ __align__(16) float sx[kDwTile][64];
@@ -393,12 +398,12 @@ __global__ void __launch_bounds__(256)
             size_t p = p0 + px;
             float vd = 0.0f, vx = 0.0f;
             if (p < P) {
-                if (ch < cout) vd = dy[p * cout + ch];
+                if (ch < cout) vd = ldf(dy + p * ys + ch);
                 int xx = (int)(p % W), yy = (int)((p / W) % H);
                 size_t n = p / ((size_t)W * H);
                 int sx_ = xx + dxo, sy_ = yy + dyo;
                 if (ch < cin && sx_ >= 0 && sx_ < W && sy_ >= 0 && sy_ < H)
-                    vx = x[((n * H + sy_) * W + sx_) * cin + ch];
+                    vx = ldf(x + ((n * H + sy_) * W + sx_) * xs + ch);
             }
             sdy[px][ch] = vd;
             sx[px][ch] = vx;
@@ -528,6 +533,26 @@ __global__ void k_gate_select(const float* __restrict__ fused, const float* __re
         out[i] = src[i];
 }
 
+// transposed, tap-flipped weights of layer (cin, cout) packed as the
+// tensor-core operand of dX = conv(dY): wp[t][c][o] = w[o][8 - t][c]
+// (rows c < cin of nout, columns o < cout of 64, zero padded)
+__global__ void k_pack_bf16_T(const float* __restrict__ master, size_t woff, int cin, int cout,
+                              int nout, __nv_bfloat16* __restrict__ wp)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 9 * nout * 64) return;
+    int o = i % 64, c = (i / 64) % nout, t = i / (64 * nout);
+    float v = (c < cin && o < cout) ? master[woff + ((size_t)o * 9 + (8 - t)) * cin + c] : 0.0f;
+    wp[i] = __float2bfloat16_rn(v);
+}
+
+// d[i] = act[i] > 0 ? d[i] : 0 over bf16 tensors
+__global__ void k_mask_bf16(__nv_bfloat16* __restrict__ d, const __nv_bfloat16* __restrict__ act, size_t n)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        if (!(__bfloat162float(act[i]) > 0.0f)) d[i] = __float2bfloat16_rn(0.0f);
+}
+
 struct Scratch {
     std::mutex mu;
     Buf b;
@@ -557,7 +582,9 @@ struct mrs_net_s {
     bool bf_valid = false, f8_valid = false;
     float xscale[kLayers];         // fp8 activation scales (calibrated)
     bool xscale_valid = false;
-    CUtensorMap wmap_bf[kLayers], wmap_f8[kLayers];
+    CUtensorMap wmap_bf[kLayers], wmap_f8[kLayers], wmap_bfT[kLayers];
+    __nv_bfloat16* wbfT = nullptr; // [18][9][64][64] transposed, tap-flipped (backward)
+    bool bfT_valid = false;
     Buf act;                       // activation workspace
     Buf aux;                       // small device scratch
     Buf tact;                      // training activations
@@ -757,6 +784,7 @@ extern "C" mrs_status mrs_net_create(const float* params, int32_t n_params, mrs_
     alloc((void**)&net->adam_v, kParams * 4);
     alloc((void**)&net->grad, kParams * 4);
     alloc((void**)&net->wbf, (size_t)kLayers * 9 * 64 * 64 * 2);
+    alloc((void**)&net->wbfT, (size_t)kLayers * 9 * 64 * 64 * 2);
     alloc((void**)&net->wf8, (size_t)kLayers * 9 * 64 * 64);
     alloc((void**)&net->bias, kLayers * 64 * 4);
     alloc((void**)&net->bias8, kLayers * 64 * 4);
@@ -772,7 +800,7 @@ extern "C" mrs_status mrs_net_free(mrs_net net)
 {
     if (!net) return MRS_OK;
     cudaDeviceSynchronize();
-    void* ptrs[] = {net->master, net->adam_m, net->adam_v, net->grad, net->wbf, net->wf8,
+    void* ptrs[] = {net->master, net->adam_m, net->adam_v, net->grad, net->wbf, net->wbfT, net->wf8,
                     net->bias, net->bias8, net->wscale, net->err};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -790,7 +818,7 @@ extern "C" mrs_status mrs_net_set_params(mrs_net net, const float* params)
     MRS_CHECK(cudaMemset(net->adam_v, 0, kParams * 4));
     MRS_CHECK(cudaMemset(net->err, 0, 4));
     net->step = 0;
-    net->bf_valid = net->f8_valid = net->xscale_valid = false;
+    net->bf_valid = net->f8_valid = net->xscale_valid = net->bfT_valid = false;
     return MRS_OK;
 }
 
@@ -980,7 +1008,7 @@ mrs_status layer_dw(mrs_net_s* net, int l, const float* x, const float* dy, int 
 {
     const LayerShape& L = shapes()[l];
     dim3 grid(kDwSplits, 9);
-    MRS_TIMED(PK_TRAIN, st, k_dw_partial<<<grid, 256, 0, st>>>(x, L.cin, dy, L.cout, N, H, W, part, dbpart));
+    MRS_TIMED(PK_TRAIN, st, (k_dw_partial<float, float><<<grid, 256, 0, st>>>(x, L.cin, L.cin, dy, L.cout, L.cout, N, H, W, part, dbpart)));
     MRS_LAUNCHED(1);
     int nw = L.cout * 9 * L.cin + L.cout;
     MRS_TIMED(PK_TRAIN, st, k_dw_reduce<<<(nw + 255) / 256, 256, 0, st>>>(part, dbpart, kDwSplits, L.cin, L.cout,
@@ -1080,7 +1108,7 @@ mrs_status train_step_f32(mrs_net_s* net, const float* lrhs, const float* hrls, 
     MRS_TIMED(PK_TRAIN, st, k_adam<<<grid1d(kParams), 256, 0, st>>>(net->master, net->grad, net->adam_m, net->adam_v,
                                                         kParams, lr, (float)b1, (float)b2, 1e-8f, bc1, bc2));
     MRS_LAUNCHED(1);
-    net->bf_valid = net->f8_valid = net->xscale_valid = false;
+    net->bf_valid = net->f8_valid = net->xscale_valid = net->bfT_valid = false;
     if (loss_out) {
         double h = 0;
         MRS_CHECK(cudaMemcpyAsync(&h, lres, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -1088,6 +1116,156 @@ mrs_status train_step_f32(mrs_net_s* net, const float* lrhs, const float* hrls, 
         *loss_out = h / (double)(P * 3);
     }
     return cuda_status(cudaGetLastError(), "train step");
+}
+
+mrs_status pack_bf16_T(mrs_net_s* net, cudaStream_t st)
+{
+    if (net->bfT_valid) return MRS_OK;
+    const auto& L = shapes();
+    for (int l = 1; l < kLayers; ++l) {
+        __nv_bfloat16* wp = net->wbfT + (size_t)l * 9 * 64 * 64;
+        k_pack_bf16_T<<<(9 * 64 * 64 + 255) / 256, 256, 0, st>>>(net->master, L[l].woff, L[l].cin,
+                                                                 L[l].cout, 64, wp);
+        MRS_LAUNCHED(1);
+        mrs_status rc = tc_make_w_map(&net->wmap_bfT[l], wp, 9 * 64, 64, TC_BF16);
+        if (rc != MRS_OK) return rc;
+    }
+    net->bfT_valid = true;
+    return cuda_status(cudaGetLastError(), "pack bf16 T");
+}
+
+// BF16 training step: forward and transposed convolutions on the tensor-core
+// kernel with BF16 activations / activation gradients, FP32 accumulation,
+// FP32 dW / db reductions and FP32 master weights + Adam
+mrs_status train_step_bf16(mrs_net_s* net, const float* lrhs, const float* hrls, const float* alb,
+                           const float* nrm, const float* target, int N, int H, int W, int s,
+                           float lr, double* loss_out, cudaStream_t st)
+{
+    const size_t P = (size_t)N * H * W;
+    const size_t F = P * 64;                       // bf16 elements of one [P][64] tensor
+    const size_t nlr = (size_t)N * (H / s) * (W / s) * 3;
+    size_t need = (size_t)(1 + 9 + 8 + 3) * F * 2 + (2 * P * 3 + nlr + P * 3) * 4 + 4096;
+    mrs_status rc = net->tact.ensure(need);
+    if (rc != MRS_OK) return rc;
+    size_t tneed = (64 * 9 * 64 + 64) * 4 + ((size_t)kDwSplits * 9 * 64 * 64 + kDwSplits * 64) * 4 +
+                   (kRedBlocks + 8) * 8;
+    if ((rc = net->ttmp.ensure(tneed)) != MRS_OK) return rc;
+    if ((rc = pack_bf16(net, st)) != MRS_OK) return rc;
+    if ((rc = pack_bf16_T(net, st)) != MRS_OK) return rc;
+    __nv_bfloat16* x0 = net->tact.as<__nv_bfloat16>();
+    __nv_bfloat16* hs = x0 + F;
+    __nv_bfloat16* rs = hs + 9 * F;
+    __nv_bfloat16* dyb = rs + 8 * F;
+    __nv_bfloat16* dh = dyb + F;
+    __nv_bfloat16* da = dh + F;
+    float* y = (float*)(da + F);
+    float* dy = y + P * 3;
+    float* lrc = dy + P * 3;
+    float* hrc = lrc + nlr;
+    float* zero = net->ttmp.as<float>() + 64 * 9 * 64;
+    float* part = zero + 64;
+    float* dbpart = part + (size_t)kDwSplits * 9 * 64 * 64;
+    double* lparts = (double*)(dbpart + kDwSplits * 64);
+    double* lres = lparts + kRedBlocks;
+    MRS_CHECK(cudaMemsetAsync(zero, 0, 64 * 4, st));
+    const auto& L = shapes();
+
+    // tensor maps: A operands (32-pixel boxes) and residual / output (120-pixel)
+    auto amap = [&](CUtensorMap* m, const void* ptr) { return tc_make_act_map(m, ptr, N, H, W, TC_BF16, kABox); };
+    auto omap = [&](CUtensorMap* m, const void* ptr) { return tc_make_act_map(m, ptr, N, H, W, TC_BF16, kOutBox); };
+    std::vector<CUtensorMap> hA(9), hO(9), rA(8), rO(8);
+    CUtensorMap x0A, dybA, dhA, dhO, daA, daO;
+    for (int k = 0; k < 9 && rc == MRS_OK; ++k) {
+        if ((rc = amap(&hA[k], hs + k * F)) == MRS_OK) rc = omap(&hO[k], hs + k * F);
+        if (k < 8 && rc == MRS_OK) { if ((rc = amap(&rA[k], rs + k * F)) == MRS_OK) rc = omap(&rO[k], rs + k * F); }
+    }
+    if (rc == MRS_OK) rc = amap(&x0A, x0);
+    if (rc == MRS_OK) rc = amap(&dybA, dyb);
+    if (rc == MRS_OK) rc = amap(&dhA, dh);
+    if (rc == MRS_OK) rc = omap(&dhO, dh);
+    if (rc == MRS_OK) rc = amap(&daA, da);
+    if (rc == MRS_OK) rc = omap(&daO, da);
+    if (rc != MRS_OK) return rc;
+    TcConvArgs a;
+    memset(&a, 0, sizeof(a));
+    a.N = N; a.H = H; a.W = W; a.scale = s; a.operand = TC_BF16; a.err = net->err; a.nout = 64;
+    auto conv = [&](const CUtensorMap* A, const CUtensorMap* Wm, const float* bias, int mode,
+                    const CUtensorMap* res, const CUtensorMap* out, int nout) {
+        a.tmap_x = A; a.tmap_w = Wm; a.bias = bias; a.mode = mode; a.tmap_res = res;
+        a.tmap_out = out; a.nout = nout;
+        return tc_conv3x3(a, st);
+    };
+
+    // forward
+    k_clip_copy<<<grid1d(nlr), 256, 0, st>>>(lrhs, nlr, kClip, lrc);
+    MRS_LAUNCHED(1);
+    k_clip_copy<<<grid1d(P * 3), 256, 0, st>>>(hrls, P * 3, kClip, hrc);
+    MRS_LAUNCHED(1);
+    k_input_q<<<grid1d(P), 256, 0, st>>>(lrc, hrc, alb, nrm, H, W, s, P, x0, 0, 1.0f);
+    MRS_LAUNCHED(1);
+    rc = conv(&x0A, &net->wmap_bf[0], net->bias, TC_RELU_BF16, nullptr, &hO[0], 64);
+    for (int k = 0; k < 8 && rc == MRS_OK; ++k) {
+        rc = conv(&hA[k], &net->wmap_bf[1 + 2 * k], net->bias + (1 + 2 * k) * 64, TC_RELU_BF16,
+                  nullptr, &rO[k], 64);
+        if (rc == MRS_OK)
+            rc = conv(&rA[k], &net->wmap_bf[2 + 2 * k], net->bias + (2 + 2 * k) * 64, TC_RESID_BF16,
+                      &hO[k], &hO[k + 1], 64);
+    }
+    if (rc == MRS_OK) {
+        a.out = y; a.lrhs = lrc; a.cout = 3;
+        rc = conv(&hA[8], &net->wmap_bf[17], net->bias + 17 * 64, TC_FINAL_F32, nullptr, nullptr, 16);
+    }
+    if (rc != MRS_OK) return rc;
+
+    // loss
+    MRS_TIMED(PK_TRAIN, st, k_loss_l1log<<<kRedBlocks, 256, 0, st>>>(y, target, P * 3, kClip, dy, lparts));
+    MRS_LAUNCHED(1);
+    k_reduce_parts<<<1, 32, 0, st>>>(lparts, kRedBlocks, 1, lres);
+    MRS_LAUNCHED(1);
+
+    // backward
+    dim3 dwg(kDwSplits, 9);
+    auto dw = [&](int l, auto xptr, int xs, auto dyptr, int ys) {
+        const LayerShape& S_ = L[l];
+        MRS_TIMED(PK_TRAIN, st, (k_dw_partial<<<dwg, 256, 0, st>>>(xptr, S_.cin, xs, dyptr, S_.cout, ys, N, H, W, part, dbpart)));
+        MRS_LAUNCHED(1);
+        int nw = S_.cout * 9 * S_.cin + S_.cout;
+        k_dw_reduce<<<(nw + 255) / 256, 256, 0, st>>>(part, dbpart, kDwSplits, S_.cin, S_.cout,
+                                                       net->grad + S_.woff, net->grad + S_.boff);
+        MRS_LAUNCHED(1);
+        return cuda_status(cudaGetLastError(), "dw");
+    };
+    if ((rc = dw(17, (const __nv_bfloat16*)(hs + 8 * F), 64, (const float*)dy, 3)) != MRS_OK) return rc;
+    k_to_operand<<<1024, 256, 0, st>>>(dy, P, 3, dyb, 0, 1.0f);
+    MRS_LAUNCHED(1);
+    if ((rc = conv(&dybA, &net->wmap_bfT[17], zero, TC_LIN_BF16, nullptr, &dhO, 64)) != MRS_OK) return rc;
+    for (int k = 7; k >= 0; --k) {
+        int l2 = 2 + 2 * k, l1 = 1 + 2 * k;
+        if ((rc = dw(l2, (const __nv_bfloat16*)(rs + k * F), 64, (const __nv_bfloat16*)dh, 64)) != MRS_OK) return rc;
+        if ((rc = conv(&dhA, &net->wmap_bfT[l2], zero, TC_MASK_BF16, &rO[k], &daO, 64)) != MRS_OK) return rc;
+        if ((rc = dw(l1, (const __nv_bfloat16*)(hs + k * F), 64, (const __nv_bfloat16*)da, 64)) != MRS_OK) return rc;
+        if ((rc = conv(&daA, &net->wmap_bfT[l1], zero, TC_RESID_BF16, &dhO, &dhO, 64)) != MRS_OK) return rc;
+    }
+    k_mask_bf16<<<grid1d(F), 256, 0, st>>>(dh, hs, F);
+    MRS_LAUNCHED(1);
+    if ((rc = dw(0, (const __nv_bfloat16*)x0, 64, (const __nv_bfloat16*)dh, 64)) != MRS_OK) return rc;
+
+    // Adam on the FP32 master weights
+    net->step += 1;
+    const double b1 = 0.9, b2 = 0.999;
+    float bc1 = (float)(1.0 - pow(b1, (double)net->step));
+    float bc2 = (float)(1.0 - pow(b2, (double)net->step));
+    MRS_TIMED(PK_TRAIN, st, k_adam<<<grid1d(kParams), 256, 0, st>>>(net->master, net->grad, net->adam_m, net->adam_v,
+                                                        kParams, lr, (float)b1, (float)b2, 1e-8f, bc1, bc2));
+    MRS_LAUNCHED(1);
+    net->bf_valid = net->f8_valid = net->xscale_valid = net->bfT_valid = false;
+    if (loss_out) {
+        double h = 0;
+        MRS_CHECK(cudaMemcpyAsync(&h, lres, sizeof(double), cudaMemcpyDeviceToHost, st));
+        MRS_CHECK(cudaStreamSynchronize(st));
+        *loss_out = h / (double)(P * 3);
+    }
+    return cuda_status(cudaGetLastError(), "train step bf16");
 }
 
 }  // namespace
@@ -1104,7 +1282,11 @@ extern "C" mrs_status mrs_train_step(mrs_net net, const float* lrhs, const float
     MRS_ARG(N >= 1 && H >= 1 && W >= 1 && H % scale == 0 && W % scale == 0, "bad sizes");
     MRS_ARG((int64_t)N * H * W <= (int64_t(1) << 22), "training batch exceeds 2^22 pixels");
     MRS_ARG(lr >= 0.0f, "lr < 0");
-    MRS_ARG(precision == MRS_PREC_FP32, "training precision must be MRS_PREC_FP32");
+    MRS_ARG(precision == MRS_PREC_FP32 || precision == MRS_PREC_BF16,
+            "training precision must be MRS_PREC_FP32 or MRS_PREC_BF16");
+    if (precision == MRS_PREC_BF16)
+        return train_step_bf16(net, lrhs, hrls, albedo, normal, target, N, H, W, scale, lr, loss_out,
+                               (cudaStream_t)stream);
     return train_step_f32(net, lrhs, hrls, albedo, normal, target, N, H, W, scale, lr, loss_out,
                           (cudaStream_t)stream);
 }
@@ -1136,7 +1318,7 @@ extern "C" mrs_status mrs_net_set_state(mrs_net net, const float* params, const 
     MRS_CHECK(cudaMemcpy(net->adam_m, adam_m, kParams * 4, cudaMemcpyHostToDevice));
     MRS_CHECK(cudaMemcpy(net->adam_v, adam_v, kParams * 4, cudaMemcpyHostToDevice));
     net->step = step;
-    net->bf_valid = net->f8_valid = net->xscale_valid = false;
+    net->bf_valid = net->f8_valid = net->xscale_valid = net->bfT_valid = false;
     return MRS_OK;
 }
 

@@ -95,3 +95,30 @@ def test_checkpoint_resume_is_bit_identical(mrs, tmp_path):
     assert sa["step"] == sb["step"] == 5
     for k in ("params", "adam_m", "adam_v"):
         assert np.array_equal(sa[k], sb[k]), k
+
+
+def test_bf16_train_step_gradients_close_to_oracle(mrs):
+    # BF16 activations / activation gradients with FP32 accumulation: every
+    # layer's gradient stays within a few per cent of the float64 gradient
+    lr, hr, alb, nrm, tgt = _batch(4, 2, 8, 16, 4)
+    p = _params(3)
+    net = mrs.Net(p)
+    loss = mrs.train_step(net, *_cuda(lr, hr, alb, nrm, tgt), 4, lr=1e-3, precision="bf16")
+    g = mrs.get_grads(net)
+    z = np.zeros(mrs.NPARAMS)
+    _, _, _, rloss, rg = cnn.train_step(p.astype(np.float64), z, z, 1, 1e-3, lr, hr, alb, nrm, tgt, 4)
+    assert abs(loss - rloss) <= 2e-2 * rloss
+    for li, (wo, bo, ci, co) in enumerate(cnn.layer_offsets()):
+        ref = rg[wo:bo]
+        got = g[wo:bo].astype(np.float64)
+        cos = got @ ref / (np.linalg.norm(got) * np.linalg.norm(ref) + 1e-30)
+        rel = np.linalg.norm(got - ref) / (np.linalg.norm(ref) + 1e-30)
+        assert cos > 0.995 and rel < 0.1, (li, cos, rel)
+
+
+def test_bf16_training_reduces_loss(mrs):
+    lr, hr, alb, nrm, tgt = _batch(5, 2, 8, 8, 4)
+    net = mrs.Net(_params(4))
+    t = _cuda(lr, hr, alb, nrm, tgt)
+    losses = [mrs.train_step(net, *t, 4, lr=1e-3, precision="bf16") for _ in range(40)]
+    assert losses[-1] < 0.7 * losses[0], losses[::5]
