@@ -176,7 +176,8 @@ mrs_status mrs_render_stats(mrs_scene scene, int32_t W, int32_t H, int32_t spp, 
  * the total milliseconds and launch count of one kernel family:
  * 0 closest-hit traversal, 1 shade, 2 shadow traversal, 3 ray generation,
  * 4 accumulation, 5 LBVH build (whole), 6 tensor-core conv, 7 SIMT conv,
- * 8 fusion input, 9 metrics, 10 training kernels.  Instrumentation only. */
+ * 8 fusion input, 9 metrics, 10 training kernels (other than 11),
+ * 11 tensor-core weight gradient.  Instrumentation only. */
 mrs_status mrs_profile_enable(int32_t on);
 mrs_status mrs_profile_read(int32_t kernel, double* total_ms, int64_t* launches);
 
@@ -317,6 +318,21 @@ mrs_status mrs_gate_async(const float* fused, const float* lrhs, const float* pl
 mrs_status mrs_conv3x3(const float* x, int32_t N, int32_t H, int32_t W, int32_t cin,
                        int32_t cout, const float* w, const float* b, int32_t relu,
                        int32_t precision, float* out, void* stream);
+
+/* Weight and bias gradients of one 3x3 convolution with zero padding (the
+ * backward pass of mrs_conv3x3 with respect to its parameters, the training
+ * step's contraction): x device float [N][H][W][cin], dy device float
+ * [N][H][W][cout] (the gradient of the output), dw HOST float
+ * [cout][3][3][cin] = sum over pixels of dy[p][o] * x[p + (ky-1, kx-1)][c]
+ * (zero outside the image), db HOST float [cout] = sum over pixels of
+ * dy[p][o].  cin, cout in [1, 64].  MRS_PREC_FP32 computes in FP32 on the
+ * SIMT cores; MRS_PREC_BF16 rounds x and dy to BF16 and accumulates in FP32
+ * on the tensor cores.  Partial sums are reduced in a fixed order
+ * (deterministic).  Synchronises `stream`; MRS_ERR_TIMEOUT if a device wait
+ * gave up. */
+mrs_status mrs_conv3x3_wgrad(const float* x, const float* dy, int32_t N, int32_t H, int32_t W,
+                             int32_t cin, int32_t cout, int32_t precision, float* dw, float* db,
+                             void* stream);
 
 #ifdef __cplusplus
 }

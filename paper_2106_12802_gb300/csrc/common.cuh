@@ -22,7 +22,7 @@ std::atomic<unsigned long long>& launch_counter();
 // events are recorded on the launching stream around each timed launch.
 enum ProfKernel {
     PK_TRACE = 0, PK_SHADE, PK_SHADOW, PK_RAYGEN, PK_ACCUM, PK_LBVH, PK_CONV_TC, PK_CONV_SIMT,
-    PK_INPUT, PK_METRICS, PK_TRAIN, PK_COUNT
+    PK_INPUT, PK_METRICS, PK_TRAIN, PK_WGRAD_TC, PK_COUNT
 };
 bool prof_on();
 cudaEvent_t prof_record(cudaStream_t st);

@@ -688,4 +688,211 @@ mrs_status tc_conv3x3(const TcConvArgs& a, cudaStream_t st)
     return MRS_ERR_ARG;
 }
 
+
+// ---------------------------------------------------------------------------
+// Weight gradient on the tensor cores: the GEMM
+//     D[(t, c)][o] = sum_p x[p + shift_t][c] * dy[p][o]
+// with K = pixels.  Both tensors keep their [pixel][64-channel] layout, which
+// for this GEMM is MN-major (the M or N index is the contiguous one): a TMA
+// box of pixels with 128-byte swizzled rows is the canonical MN-major
+// SWIZZLE_128B operand, one 128-byte row per K index, 8-row groups 1024 bytes
+// apart.  M = 128 is made of two 64-channel MN atoms LBO bytes apart, so one
+// MMA covers two taps:
+//   MMA dx     (dx = 0..2): rows 0-63 tap (ky 0, dx), rows 64-127 tap (ky 1, dx)
+//                           (input rows y-1 and y sit in slots RB bytes apart)
+//   MMA 3 + dx            : rows 0-63 tap (ky 2, dx), rows 64-127 read a
+//                           region of ones, which makes those rows db[o]
+// A job is kWgKB output pixels of one image row.  Per job the producer loads
+// input rows y-1, y, y+1 (kWgKB + 2 pixels from x0 - 1, zero-filled outside
+// the image: the zero padding) and dy row y (kWgKB pixels); the kx shift is a
+// descriptor start offset of kx 128-byte rows.  Each CTA takes a contiguous
+// run of jobs, accumulates all 9 taps in TMEM (6 x 64 fp32 columns) and writes
+// one partial; the partials are summed by a separate reduction.
+// Warp 0 lane 0: TMA producer; warp 1: TMEM allocator, lane 0 MMA issuer;
+// warps 0-3: epilogue (warp w reads TMEM lanes 32w .. 32w + 31).
+namespace {
+
+constexpr int kWgThreads = 128;
+constexpr int kWgRB = ((kWgKB + 2) * 128 + 1023) & ~1023;   // one input-row slot
+constexpr int kWgBB = kWgKB * 128;                           // dy slot
+constexpr int kWgStage = 3 * kWgRB + kWgBB;
+constexpr uint32_t kWgTx = 3 * (kWgKB + 2) * 128 + kWgKB * 128;   // bytes landed per job
+
+// MN-major SWIZZLE_128B descriptor: `lbo` = bytes to the next 64-element MN
+// atom, SBO = 1024 bytes to the next group of 8 K rows
+__device__ __forceinline__ uint64_t sdesc_mn(uint32_t saddr, uint32_t lbo)
+{
+    uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// waits for a phase regardless of the error word (used to drain copies in
+// flight before the CTA exits); gives up after `limit_cycles`
+__device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity, long long limit_cycles)
+{
+    long long t0 = clock64();
+    while (!mbar_try_wait_sleep(bar, parity, 100000u))
+        if (clock64() - t0 > limit_cycles) return;
+}
+
+__global__ void __launch_bounds__(kWgThreads, 1)
+    k_wgrad_tc(const __grid_constant__ CUtensorMap tmap_x, const __grid_constant__ CUtensorMap tmap_dy,
+               TcWgradArgs a, int stages)
+{
+    // kind::f16, D f32, A and B bf16, both MN-major, N = 64, M = 128
+    constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
+                               ((uint32_t)(64 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    constexpr uint32_t kTmemCols = 512;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* sOnes = smem + (size_t)stages * kWgStage;
+    uint64_t* full = (uint64_t*)(sOnes + kWgRB);
+    uint64_t* empty = full + stages;
+    uint64_t* done = empty + stages;
+    uint32_t* tslot = (uint32_t*)(done + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int XS = (a.W + kWgKB - 1) / kWgKB;
+    const long long njobs = (long long)a.N * a.H * XS;
+    const long long j0 = njobs * blockIdx.x / gridDim.x;
+    const long long j1 = njobs * (blockIdx.x + 1) / gridDim.x;
+
+    for (int i = threadIdx.x; i < kWgRB / 4; i += kWgThreads) ((uint32_t*)sOnes)[i] = 0x3F803F80u;  // bf16 1.0
+    fence_async_smem();
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < stages; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_async_smem();
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tslot)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *(volatile uint32_t*)tslot;
+
+    if (warp == 0 && lane == 0) {
+        uint32_t it = 0;
+        for (long long j = j0; j < j1; ++j, ++it) {
+            int xs = (int)(j % XS);
+            long long rest = j / XS;
+            int y = (int)(rest % a.H), n = (int)(rest / a.H);
+            int s = it % stages;
+            if (!mbar_wait(&empty[s], ((it / stages) & 1) ^ 1, a.err)) break;
+            mbar_expect_tx(&full[s], kWgTx);
+            uint8_t* sb = smem + (size_t)s * kWgStage;
+            for (int r = 0; r < 3; ++r)
+                tma_load_4d(sb + r * kWgRB, &tmap_x, 0, xs * kWgKB - 1, y - 1 + r, n, &full[s]);
+            tma_load_4d(sb + 3 * kWgRB, &tmap_dy, 0, xs * kWgKB, y, n, &full[s]);
+        }
+        // no copy may still be landing when the CTA exits
+        for (uint32_t i = it > (uint32_t)stages ? it - stages : 0; i < it; ++i)
+            mbar_drain(&full[i % stages], (i / stages) & 1, kTimeoutCycles);
+    } else if (warp == 1 && lane == 0) {
+        const uint32_t ones = smem_u32(sOnes);
+        uint32_t it = 0;
+        for (long long j = j0; j < j1; ++j, ++it) {
+            int s = it % stages;
+            if (!mbar_wait(&full[s], (it / stages) & 1, a.err)) break;
+            tc_fence_after();
+            const uint32_t base = smem_u32(smem + (size_t)s * kWgStage);
+            const uint32_t bB = base + 3 * kWgRB;
+#pragma unroll
+            for (int kk = 0; kk < kWgKB / 16; ++kk) {
+                const uint64_t bd = sdesc_mn(bB + kk * 2048, kWgBB);
+#pragma unroll
+                for (int q = 0; q < 6; ++q) {
+                    const int kx = q % 3;
+                    const uint32_t top = base + (q < 3 ? 0 : 2 * kWgRB);
+                    const uint32_t lbo = q < 3 ? (uint32_t)kWgRB : ones - top;
+                    mma_f16(tmem + q * 64, sdesc_mn(top + kx * 128 + kk * 2048, lbo), bd, IDESC,
+                            (it > 0 || kk > 0) ? 1u : 0u);
+                }
+            }
+            mma_commit(&empty[s]);
+        }
+        mma_commit(done);   // arrives once every MMA issued above has completed
+    }
+    __syncwarp();
+
+    const bool ok = mbar_wait_warp(done, 0, a.err);
+    tc_fence_after();
+    if (ok) {
+        const bool have = j1 > j0;
+        const int m = 32 * warp + lane, c = m & 63;
+        float* P = a.part + (size_t)blockIdx.x * 9 * a.cout * a.cin;
+        for (int q = 0; q < 6; ++q) {
+            // TMEM lane m of MMA q: tap t (or the bias row when t < 0)
+            const int t = q < 3 ? (m < 64 ? q : 3 + q) : (m < 64 ? 3 + q : -1);
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                uint32_t r[16];
+                tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + q * 64 + h * 16, r);
+                tmem_wait_ld();
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int o = h * 16 + i;
+                    const float v = have ? __uint_as_float(r[i]) : 0.0f;
+                    if (o >= a.cout) continue;
+                    if (t >= 0) {
+                        if (c < a.cin) P[((size_t)t * a.cout + o) * a.cin + c] = v;
+                    } else if (q == 3 && m == 64) {
+                        a.dbpart[(size_t)blockIdx.x * a.cout + o] = v;
+                    }
+                }
+            }
+        }
+    }
+    // on the error path the MMAs may still run: TMEM is freed only after them
+    if (!ok && warp == 1 && lane == 0) mbar_drain(done, 0, kTimeoutCycles);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kTmemCols));
+    }
+}
+
+size_t wgrad_smem(int stages)
+{
+    return 1024 + (size_t)stages * kWgStage + kWgRB + 8 * (2 * stages + 1) + 16;
+}
+
+}  // namespace
+
+int tc_wgrad_max_parts() { return sm_count(); }
+
+mrs_status tc_conv3x3_wgrad(const TcWgradArgs& a, int* nparts, cudaStream_t st)
+{
+    if (a.cin < 1 || a.cin > 64 || a.cout < 1 || a.cout > 64) {
+        set_error("tc_conv3x3_wgrad: cin, cout must be in [1, 64]");
+        return MRS_ERR_ARG;
+    }
+    int stages = 2;
+    while (wgrad_smem(stages + 1) <= 227 * 1024 && stages < 8) ++stages;
+    size_t smem = wgrad_smem(stages);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_status(e, "wgrad smem attribute");
+        attr = true;
+    }
+    long long njobs = (long long)a.N * a.H * ((a.W + kWgKB - 1) / kWgKB);
+    int grid = njobs < sm_count() ? (int)njobs : sm_count();
+    *nparts = grid;
+    if (grid < 1) return MRS_OK;
+    MRS_TIMED(PK_WGRAD_TC, st, (k_wgrad_tc<<<grid, kWgThreads, smem, st>>>(*a.tmap_x, *a.tmap_dy, a, stages)));
+    MRS_LAUNCHED(1);
+    return cuda_status(cudaGetLastError(), "wgrad launch");
+}
+
 }  // namespace mrs

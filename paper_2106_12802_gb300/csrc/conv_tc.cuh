@@ -60,6 +60,25 @@ mrs_status tc_make_w_map(CUtensorMap* m, const void* ptr, int rows, int nout, in
 
 mrs_status tc_conv3x3(const TcConvArgs& a, cudaStream_t st);
 
+// Weight and bias gradients of a 3x3 conv (zero padding 1) on the tensor
+// cores, as per-CTA partial sums:
+//   part[g][t][o][c] (t = ky * 3 + kx) = sum over CTA g's pixels p of
+//       dy[p][o] * x[p + (ky - 1, kx - 1)][c],   dbpart[g][o] = sum dy[p][o]
+// for o < cout, c < cin.  x and dy are bf16 [N][H][W][64] tensors described
+// by tc_make_act_map with box widths kWgKB + 2 (x) and kWgKB (dy).  *nparts
+// receives the number of partials written (at most tc_wgrad_max_parts()).
+constexpr int kWgKB = 64;
+struct TcWgradArgs {
+    const CUtensorMap* tmap_x;
+    const CUtensorMap* tmap_dy;
+    float* part;
+    float* dbpart;
+    int N, H, W, cin, cout;
+    int* err;
+};
+int tc_wgrad_max_parts();
+mrs_status tc_conv3x3_wgrad(const TcWgradArgs& a, int* nparts, cudaStream_t st);
+
 // Launches a kernel whose bounded mbarrier wait can never complete; *gave_up
 // = 1 if the wait gave up after limit_cycles and raised the error word.
 mrs_status tc_wait_selftest(long long limit_cycles, int* gave_up, cudaStream_t st);

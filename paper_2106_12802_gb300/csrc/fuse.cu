@@ -11,6 +11,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 #include <vector>
 
@@ -1147,8 +1148,8 @@ mrs_status train_step_bf16(mrs_net_s* net, const float* lrhs, const float* hrls,
     size_t need = (size_t)(1 + 9 + 8 + 3) * F * 2 + (2 * P * 3 + nlr + P * 3) * 4 + 4096;
     mrs_status rc = net->tact.ensure(need);
     if (rc != MRS_OK) return rc;
-    size_t tneed = (64 * 9 * 64 + 64) * 4 + ((size_t)kDwSplits * 9 * 64 * 64 + kDwSplits * 64) * 4 +
-                   (kRedBlocks + 8) * 8;
+    const size_t maxp = (size_t)std::max(kDwSplits, tc_wgrad_max_parts());
+    size_t tneed = (64 * 9 * 64 + 64) * 4 + (maxp * 9 * 64 * 64 + maxp * 64) * 4 + (kRedBlocks + 8) * 8;
     if ((rc = net->ttmp.ensure(tneed)) != MRS_OK) return rc;
     if ((rc = pack_bf16(net, st)) != MRS_OK) return rc;
     if ((rc = pack_bf16_T(net, st)) != MRS_OK) return rc;
@@ -1164,8 +1165,8 @@ mrs_status train_step_bf16(mrs_net_s* net, const float* lrhs, const float* hrls,
     float* hrc = lrc + nlr;
     float* zero = net->ttmp.as<float>() + 64 * 9 * 64;
     float* part = zero + 64;
-    float* dbpart = part + (size_t)kDwSplits * 9 * 64 * 64;
-    double* lparts = (double*)(dbpart + kDwSplits * 64);
+    float* dbpart = part + maxp * 9 * 64 * 64;
+    double* lparts = (double*)(dbpart + maxp * 64);
     double* lres = lparts + kRedBlocks;
     MRS_CHECK(cudaMemsetAsync(zero, 0, 64 * 4, st));
     const auto& L = shapes();
@@ -1185,6 +1186,19 @@ mrs_status train_step_bf16(mrs_net_s* net, const float* lrhs, const float* hrls,
     if (rc == MRS_OK) rc = omap(&dhO, dh);
     if (rc == MRS_OK) rc = amap(&daA, da);
     if (rc == MRS_OK) rc = omap(&daO, da);
+    // weight-gradient operands: x rows with a one-pixel halo, dy rows
+    auto xwmap = [&](CUtensorMap* m, const void* ptr) { return tc_make_act_map(m, ptr, N, H, W, TC_BF16, kWgKB + 2); };
+    auto dwmap = [&](CUtensorMap* m, const void* ptr) { return tc_make_act_map(m, ptr, N, H, W, TC_BF16, kWgKB); };
+    std::vector<CUtensorMap> hX(9), rX(8);
+    CUtensorMap x0X, dybD, dhD, daD;
+    for (int k = 0; k < 9 && rc == MRS_OK; ++k) {
+        rc = xwmap(&hX[k], hs + k * F);
+        if (k < 8 && rc == MRS_OK) rc = xwmap(&rX[k], rs + k * F);
+    }
+    if (rc == MRS_OK) rc = xwmap(&x0X, x0);
+    if (rc == MRS_OK) rc = dwmap(&dybD, dyb);
+    if (rc == MRS_OK) rc = dwmap(&dhD, dh);
+    if (rc == MRS_OK) rc = dwmap(&daD, da);
     if (rc != MRS_OK) return rc;
     TcConvArgs a;
     memset(&a, 0, sizeof(a));
@@ -1223,32 +1237,37 @@ mrs_status train_step_bf16(mrs_net_s* net, const float* lrhs, const float* hrls,
     k_reduce_parts<<<1, 32, 0, st>>>(lparts, kRedBlocks, 1, lres);
     MRS_LAUNCHED(1);
 
-    // backward
-    dim3 dwg(kDwSplits, 9);
-    auto dw = [&](int l, auto xptr, int xs, auto dyptr, int ys) {
+    // backward: weight gradients on the tensor cores (per-CTA partials, then a
+    // deterministic reduction), data gradients as convs with the flipped,
+    // transposed weights
+    auto dw = [&](int l, const CUtensorMap* xm, const CUtensorMap* dym) {
         const LayerShape& S_ = L[l];
-        MRS_TIMED(PK_TRAIN, st, (k_dw_partial<<<dwg, 256, 0, st>>>(xptr, S_.cin, xs, dyptr, S_.cout, ys, N, H, W, part, dbpart)));
-        MRS_LAUNCHED(1);
+        TcWgradArgs wa;
+        wa.tmap_x = xm; wa.tmap_dy = dym; wa.part = part; wa.dbpart = dbpart;
+        wa.N = N; wa.H = H; wa.W = W; wa.cin = S_.cin; wa.cout = S_.cout; wa.err = net->err;
+        int np = 0;
+        mrs_status r = tc_conv3x3_wgrad(wa, &np, st);
+        if (r != MRS_OK) return r;
         int nw = S_.cout * 9 * S_.cin + S_.cout;
-        k_dw_reduce<<<(nw + 255) / 256, 256, 0, st>>>(part, dbpart, kDwSplits, S_.cin, S_.cout,
-                                                       net->grad + S_.woff, net->grad + S_.boff);
+        MRS_TIMED(PK_TRAIN, st, k_dw_reduce<<<(nw + 255) / 256, 256, 0, st>>>(part, dbpart, np, S_.cin, S_.cout,
+                                                       net->grad + S_.woff, net->grad + S_.boff));
         MRS_LAUNCHED(1);
         return cuda_status(cudaGetLastError(), "dw");
     };
-    if ((rc = dw(17, (const __nv_bfloat16*)(hs + 8 * F), 64, (const float*)dy, 3)) != MRS_OK) return rc;
     k_to_operand<<<1024, 256, 0, st>>>(dy, P, 3, dyb, 0, 1.0f);
     MRS_LAUNCHED(1);
+    if ((rc = dw(17, &hX[8], &dybD)) != MRS_OK) return rc;
     if ((rc = conv(&dybA, &net->wmap_bfT[17], zero, TC_LIN_BF16, nullptr, &dhO, 64)) != MRS_OK) return rc;
     for (int k = 7; k >= 0; --k) {
         int l2 = 2 + 2 * k, l1 = 1 + 2 * k;
-        if ((rc = dw(l2, (const __nv_bfloat16*)(rs + k * F), 64, (const __nv_bfloat16*)dh, 64)) != MRS_OK) return rc;
+        if ((rc = dw(l2, &rX[k], &dhD)) != MRS_OK) return rc;
         if ((rc = conv(&dhA, &net->wmap_bfT[l2], zero, TC_MASK_BF16, &rO[k], &daO, 64)) != MRS_OK) return rc;
-        if ((rc = dw(l1, (const __nv_bfloat16*)(hs + k * F), 64, (const __nv_bfloat16*)da, 64)) != MRS_OK) return rc;
+        if ((rc = dw(l1, &hX[k], &daD)) != MRS_OK) return rc;
         if ((rc = conv(&daA, &net->wmap_bfT[l1], zero, TC_RESID_BF16, &dhO, &dhO, 64)) != MRS_OK) return rc;
     }
     k_mask_bf16<<<grid1d(F), 256, 0, st>>>(dh, hs, F);
     MRS_LAUNCHED(1);
-    if ((rc = dw(0, (const __nv_bfloat16*)x0, 64, (const __nv_bfloat16*)dh, 64)) != MRS_OK) return rc;
+    if ((rc = dw(0, &x0X, &dhD)) != MRS_OK) return rc;
 
     // Adam on the FP32 master weights
     net->step += 1;
@@ -1362,4 +1381,61 @@ extern "C" mrs_status mrs_gate_async(const float* fused, const float* lrhs, cons
     k_gate_select<<<1024, 256, 0, st>>>(fused, plain ? plain : fused, n, used_plain, out);
     MRS_LAUNCHED(1);
     return cuda_status(cudaGetLastError(), "gate_async launch");
+}
+
+extern "C" mrs_status mrs_conv3x3_wgrad(const float* x, const float* dy, int32_t N, int32_t H,
+                                        int32_t W, int32_t cin, int32_t cout, int32_t precision,
+                                        float* dw, float* db, void* stream)
+{
+    using namespace mrs;
+    MRS_ARG(x && dy && dw && db, "NULL pointer");
+    MRS_ARG(N >= 1 && H >= 1 && W >= 1, "sizes must be >= 1");
+    MRS_ARG(cin >= 1 && cin <= 64 && cout >= 1 && cout <= 64, "cin, cout must be in [1, 64]");
+    MRS_ARG(precision == MRS_PREC_FP32 || precision == MRS_PREC_BF16, "precision must be FP32 or BF16");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t P = (size_t)N * H * W;
+    const size_t nw = (size_t)cout * 9 * cin;
+    const size_t maxp = (size_t)std::max(kDwSplits, tc_wgrad_max_parts());
+    Scratch& S = scratch();
+    std::lock_guard<std::mutex> g(S.mu);
+    size_t need = (nw + cout) * 4 + maxp * (9 * 64 * 64 + 64) * 4 + 4096 +
+                  (precision == MRS_PREC_BF16 ? 2 * P * 128 : 0);
+    mrs_status rc = S.b.ensure(need);
+    if (rc != MRS_OK) return rc;
+    float* gw = S.b.as<float>();
+    float* gb = gw + nw;
+    float* part = (float*)(((uintptr_t)(gb + cout) + 255) & ~(uintptr_t)255);
+    float* dbpart = part + maxp * 9 * 64 * 64;
+    static int* err = nullptr;
+    if (!err) { MRS_CHECK(cudaMalloc(&err, 4)); MRS_CHECK(cudaMemset(err, 0, 4)); }
+    int np = 0;
+    if (precision == MRS_PREC_FP32) {
+        k_dw_partial<float, float><<<dim3(kDwSplits, 9), 256, 0, st>>>(x, cin, cin, dy, cout, cout, N, H, W,
+                                                                      part, dbpart);
+        MRS_LAUNCHED(1);
+        np = kDwSplits;
+    } else {
+        uint8_t* xq = (uint8_t*)(((uintptr_t)(dbpart + maxp * 64) + 1023) & ~(uintptr_t)1023);
+        uint8_t* dq = xq + P * 128;
+        k_to_operand<<<1024, 256, 0, st>>>(x, P, cin, xq, 0, 1.0f);
+        MRS_LAUNCHED(1);
+        k_to_operand<<<1024, 256, 0, st>>>(dy, P, cout, dq, 0, 1.0f);
+        MRS_LAUNCHED(1);
+        CUtensorMap mx, md;
+        if ((rc = tc_make_act_map(&mx, xq, N, H, W, TC_BF16, kWgKB + 2)) != MRS_OK) return rc;
+        if ((rc = tc_make_act_map(&md, dq, N, H, W, TC_BF16, kWgKB)) != MRS_OK) return rc;
+        TcWgradArgs wa;
+        wa.tmap_x = &mx; wa.tmap_dy = &md; wa.part = part; wa.dbpart = dbpart;
+        wa.N = N; wa.H = H; wa.W = W; wa.cin = cin; wa.cout = cout; wa.err = err;
+        if ((rc = tc_conv3x3_wgrad(wa, &np, st)) != MRS_OK) return rc;
+    }
+    k_dw_reduce<<<(int)((nw + cout + 255) / 256), 256, 0, st>>>(part, dbpart, np, cin, cout, gw, gb);
+    MRS_LAUNCHED(1);
+    MRS_CHECK(cudaMemcpyAsync(dw, gw, nw * 4, cudaMemcpyDeviceToHost, st));
+    MRS_CHECK(cudaMemcpyAsync(db, gb, cout * 4, cudaMemcpyDeviceToHost, st));
+    MRS_CHECK(cudaStreamSynchronize(st));
+    int herr = 0;
+    MRS_CHECK(cudaMemcpy(&herr, err, 4, cudaMemcpyDeviceToHost));
+    if (herr) { cudaMemset(err, 0, 4); set_error("tensor-core weight-gradient wait timed out"); return MRS_ERR_TIMEOUT; }
+    return MRS_OK;
 }

@@ -143,6 +143,22 @@ def conv3x3(x, w, b, relu=False, precision="fp32", stream=None):
     return out
 
 
+def conv3x3_wgrad(x, dy, precision="fp32", stream=None):
+    """Weight / bias gradients of a 3x3 conv: x [N,H,W,cin], dy [N,H,W,cout]
+    CUDA float32 -> (dw [cout,3,3,cin], db [cout]) numpy float32."""
+    _dev(x, torch.float32)
+    _dev(dy, torch.float32)
+    N, H, W, cin = x.shape
+    cout = dy.shape[3]
+    if tuple(dy.shape[:3]) != (N, H, W):
+        raise ValueError("x and dy must share N, H, W")
+    dw = np.zeros((cout, 3, 3, cin), np.float32)
+    db = np.zeros(cout, np.float32)
+    call("mrs_conv3x3_wgrad", _ptr(x), _ptr(dy), N, H, W, cin, cout, _prec(precision),
+         ctypes.c_void_p(dw.ctypes.data), ctypes.c_void_p(db.ctypes.data), _stream(stream))
+    return dw, db
+
+
 def image_metrics(x, ref, lam1=0.5, lam2=0.01, stream=None):
     """(sRGB PSNR, RelMSE, linear MSE) reduced in float64 on the GPU."""
     _dev(x, torch.float32)

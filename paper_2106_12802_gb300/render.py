@@ -170,7 +170,7 @@ def render_stats(scene: Scene, W, H, spp, max_depth, rr_start=None, seed=0, stre
 
 
 PROFILE_KERNELS = ["trace", "shade", "shadow", "raygen", "accumulate", "lbvh", "conv_tc",
-                   "conv_simt", "input", "metrics", "train"]
+                   "conv_simt", "input", "metrics", "train", "wgrad_tc"]
 
 
 def profile_enable(on=True):
