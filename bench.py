@@ -35,7 +35,8 @@ WORKLOAD = {
                 "x4 fusion CNN (12->64, 8 residual blocks, 64->3) in BF16 on tcgen05; fallback gate; "
                 "the two renders run concurrently on two streams",
     "scene_seed": 0, "lrhs": [256, 256, 64], "hrls": [1024, 1024, 4], "scale": 4,
-    "max_depth": 8, "rr_start": 3, "precision": "bf16", "net_init": "kaiming-normal seed 0",
+    "max_depth": 8, "rr_start": 3, "precision": "bf16", "net_init": "trained before the timed region (BF16 training step, 3000 Adam steps on 8 "
+                "held-out procedural scenes); Kaiming-normal seed 0 under --quick",
     "l2": "flushed between steps (512 MiB write)",
 }
 LR, HR, S = 256, 1024, 4
@@ -199,23 +200,35 @@ def run_reference(args, rank, world):
 # ----------------------------------------------------------------------------
 # equal-PSNR comparison: hybrid frame vs plain high-resolution path tracing
 # ----------------------------------------------------------------------------
-def equal_psnr(mrs, scene, s, ref_spp=4096, train_scenes=8, train_steps=1500):
-    """Trains the fusion network on held-out procedural scenes (seeds 1..),
-    renders a ref_spp reference of the bench scene, scores the hybrid frame
-    (BF16 fusion) and finds the plain HR spp that reaches the same sRGB PSNR
-    (bisection on spp); returns both times (CUDA events, same renderer)."""
-    import torch
-
+def train_net(mrs, s, train_scenes=8, train_steps=3000, batch=16, crop=128, precision="bf16"):
+    """Trains the fusion network on held-out procedural scenes (seeds 1..,
+    never the bench scene) with the library's training step; returns the net
+    and a description of the training."""
     from paper_2106_12802_gb300 import trainer
     from synth import scenes
     t0 = time.perf_counter()
     data = trainer.make_dataset(range(1, 1 + train_scenes), size=HR, s=s, spp_lr=SPP_LR,
                                 spp_hr=SPP_HR, spp_tgt=256, depth=DEPTH, rr=RR,
                                 scene_fn=scenes.procedural)
+    t_data = time.perf_counter() - t0
     net = mrs.Net(trainer.init_params(0))
-    trainer.train(net, data, train_steps, batch=8, crop=96, s=s, lr=1e-3, seed=0)
-    del data
+    t0 = time.perf_counter()
+    trainer.train(net, data, train_steps, batch=batch, crop=crop, s=s, lr=1e-3, seed=0,
+                  precision=precision)
     t_train = time.perf_counter() - t0
+    del data
+    return net, (f"{train_scenes} procedural scenes (seeds 1..{train_scenes}) at {HR}^2, targets "
+                 f"256 spp ({t_data:.1f} s to render); {train_steps} Adam steps, batch {batch} x "
+                 f"{crop}^2, lr 1e-3, {precision} training step ({t_train:.1f} s)")
+
+
+def equal_psnr(mrs, scene, s, net, training, ref_spp=4096):
+    """Renders a ref_spp reference of the bench scene, scores the hybrid frame
+    (BF16 fusion with the trained net) and finds the plain HR spp that reaches
+    the same sRGB PSNR (bisection on spp); returns both times (CUDA events,
+    same renderer)."""
+    import torch
+
     ref = mrs.render(scene, HR, HR, ref_spp, DEPTH, RR, 99991, aux=False, counts=False)["radiance"]
     ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
 
@@ -274,14 +287,11 @@ def equal_psnr(mrs, scene, s, ref_spp=4096, train_scenes=8, train_steps=1500):
         lr[None], hr["radiance"][None], hr["albedo"][None], hr["normal"][None], s, precision="fp32")
     p_lr_up = mrs.image_metrics(up[0].contiguous(), ref)[0]
     p_hrls = mrs.image_metrics(hr["radiance"], ref)[0]
-    equal_psnr.trained_params = net.get_params()
     return {"reference_spp": ref_spp, "hybrid_psnr_db": p_h, "hybrid_ms": t_h,
             "upsampled_lrhs_psnr_db": p_lr_up, "hrls_psnr_db": p_hrls, "plain_spp_at_equal_psnr": n_eq,
             "plain_psnr_db": plain_psnr(n_eq), "plain_ms": t_p, "speedup_plain_over_hybrid": t_p / t_h,
             "spp_avg_hybrid": SPP_LR / (s * s) + SPP_HR,
-            "training": f"{train_scenes} procedural scenes (seeds 1..{train_scenes}) at {HR}^2, "
-                        f"targets 256 spp, {train_steps} Adam steps, batch 8 x 96^2, lr 1e-3, "
-                        f"{t_train:.1f} s"}
+            "training": training}
 
 
 # ----------------------------------------------------------------------------
@@ -402,8 +412,15 @@ def run_gpu(args, rank, world):
     stream = torch.cuda.current_stream()
     desc = scenes.procedural(0)
     scene = mrs.Scene(desc)
-    params = cnn.kaiming(0).astype(np.float32)
-    net = mrs.Net(params)
+    # the network: trained on held-out scenes before anything is timed (the
+    # timed frame and the equal-PSNR comparison use the same weights);
+    # --quick keeps the Kaiming initialisation (timing does not depend on the
+    # weights, the gate's decision does)
+    if args.quick:
+        net, training = mrs.Net(cnn.kaiming(0).astype(np.float32)), None
+    else:
+        net, training = train_net(mrs, S)
+    params = net.get_params()
 
     lrhs = torch.empty((1, LR, LR, 3), device=dev)
     hrls = torch.empty((1, HR, HR, 3), device=dev)
@@ -495,10 +512,9 @@ def run_gpu(args, rank, world):
     # ---- context measurements (outside the timed region) --------------------
     extra = {}
     if rank == 0 and not args.quick and not args.no_equal_psnr:
-        extra["equal_psnr"] = equal_psnr(mrs, scene, S)
+        extra["equal_psnr"] = equal_psnr(mrs, scene, S, net, training)
     if rank == 0 and not args.quick and not args.no_batched:
-        p = getattr(equal_psnr, "trained_params", None)
-        extra["batched_serving"] = batched_serving(mrs, p if p is not None else params)
+        extra["batched_serving"] = batched_serving(mrs, params)
     if rank == 0 and not args.quick:
         stats_lr = mrs.render_stats(scene, LR, LR, SPP_LR, DEPTH, RR, 0)
         stats_hr = mrs.render_stats(scene, HR, HR, SPP_HR, DEPTH, RR, 1)
@@ -566,7 +582,7 @@ def run_gpu(args, rank, world):
             "stage_note": "per-kernel-family CUDA-event totals; the two renders overlap, so "
                           "render stages can sum to more than the frame",
             "conv_tflops": conv_flop / (conv_ms * 1e-3) / 1e12 if conv_ms else None,
-            "gate": gate_info, **extra,
+            "gate": gate_info, "training": training, **extra,
         }
         print(json.dumps(line), flush=True)
     return 0

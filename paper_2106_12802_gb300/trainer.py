@@ -78,14 +78,16 @@ def random_batch(data, batch, crop, s, rng):
     return {k: torch.cat(v).contiguous() for k, v in out.items()}
 
 
-def train(net, data, steps, batch=16, crop=128, s=4, lr=1e-4, seed=0, log_every=0):
+def train(net, data, steps, batch=16, crop=128, s=4, lr=1e-4, seed=0, log_every=0, precision="fp32"):
+    """Adam on random crops of `data`; precision "fp32" (SIMT) or "bf16"
+    (tensor cores, FP32 master weights)."""
     rng = np.random.default_rng(seed)
     losses = []
     for i in range(steps):
         b = random_batch(data, batch, crop, s, rng)
         sync = bool(log_every) and (i % log_every == 0 or i == steps - 1)
         loss = fusion.train_step(net, b["lrhs"], b["hrls"], b["albedo"], b["normal"], b["target"],
-                                 s, lr=lr, sync_loss=sync)
+                                 s, lr=lr, sync_loss=sync, precision=precision)
         if sync:
             losses.append((i, loss))
     torch.cuda.synchronize()
