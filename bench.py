@@ -42,6 +42,11 @@ WORKLOAD = {
 LR, HR, S = 256, 1024, 4
 SPP_LR, SPP_HR, DEPTH, RR = 64, 4, 8, 3
 CONV_FLOP_PER_PX = 2 * 9 * (12 * 64 + 16 * 64 * 64 + 64 * 3)      # 1,196,928
+# algorithmic HBM bytes per HR pixel of the 18 BF16 conv layers: input layer
+# reads 12 channels (24 B) and writes 128 B; each residual block reads h,
+# writes r, reads r and h, writes h (5 x 128 B); the head reads 128 B and
+# writes 3 FP32 (12 B)
+CONV_BYTES_PER_PX = (24 + 128) + 8 * 5 * 128 + (128 + 12)           # 5,412
 # FP32 operations per traversal step, counted from the kernel source
 # (pt.cu: slab() on both children of a node; intersect() per triangle)
 OPS_PER_NODE_VISIT = 52
@@ -536,15 +541,27 @@ def run_gpu(args, rank, world):
     conv_ms = prof["conv_tc"][0] / args.steps
     conv_flop = CONV_FLOP_PER_PX * HR * HR
     family_ms = {k: v[0] / args.steps for k, v in prof.items() if v[1]}
+    # the conv stack against both of its rooflines: arithmetic intensity
+    # 1,196,928 / 5,412 = 221 FLOP/B is below the measured ridge (about 256),
+    # so HBM is the binding one
+    conv_roof = None
+    if conv_ms:
+        c_tf = conv_flop / (conv_ms * 1e-3) / 1e12
+        c_gbs = CONV_BYTES_PER_PX * HR * HR / (conv_ms * 1e-3) / 1e9
+        conv_roof = {"tflops": c_tf, "tensor_frac": c_tf / peaks["bf16_tflops_sustained"],
+                     "hbm_gbs": c_gbs, "hbm_frac": c_gbs / peaks["hbm_gbs"],
+                     "flop_per_byte": CONV_FLOP_PER_PX / CONV_BYTES_PER_PX,
+                     "ridge_flop_per_byte": peaks["bf16_tflops_sustained"] * 1e3 / peaks["hbm_gbs"],
+                     "bound": "hbm" if CONV_FLOP_PER_PX / CONV_BYTES_PER_PX <
+                     peaks["bf16_tflops_sustained"] * 1e3 / peaks["hbm_gbs"] else "tensor"}
     dom = max(family_ms, key=family_ms.get)
     roofline = None
     if dom == "conv_tc":
-        peak = peaks["bf16_tflops_sustained"]
-        ach = conv_flop / (conv_ms * 1e-3) / 1e12
-        roofline = {"kernel": "k_conv_tc (tcgen05 implicit-GEMM 3x3 conv)", "bound": "tensor",
-                    "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                    "traffic": _traffic("k_conv_tc", "conv_tc.cu"),
-                    "peak_source": peaks["source"] + " bf16 sustained"}
+        ach = CONV_BYTES_PER_PX * HR * HR / (conv_ms * 1e-3) / 1e9
+        roofline = {"kernel": "k_conv_tc (tcgen05 implicit-GEMM 3x3 conv)", "bound": "hbm",
+                    "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": ach / peaks["hbm_gbs"], "traffic": _traffic("k_conv_tc", "conv_tc.cu"),
+                    "peak_source": peaks["source"] + " HBM copy"}
     elif dom in ("trace", "shadow") and stats_lr:
         key = "" if dom == "trace" else "shadow_"
         ops = OPS_PER_NODE_VISIT * (stats_lr[key + "visits"] + stats_hr[key + "visits"]) + \
@@ -582,6 +599,7 @@ def run_gpu(args, rank, world):
             "stage_note": "per-kernel-family CUDA-event totals; the two renders overlap, so "
                           "render stages can sum to more than the frame",
             "conv_tflops": conv_flop / (conv_ms * 1e-3) / 1e12 if conv_ms else None,
+            "conv_roofline": conv_roof,
             "gate": gate_info, "training": training, **extra,
         }
         print(json.dumps(line), flush=True)

@@ -148,6 +148,33 @@ def l1log_loss(pred, target):
     return loss, g
 
 
+def robust_loss(pred, target, beta=0.1):
+    """The robust loss l_r of the method's training (Sec. 3, "Loss function"):
+    mean over all pixel-channel values of |e| / (beta + |e|), e = pred - target,
+    and its gradient w.r.t. pred, sign(e) * beta / (beta + |e|)^2 / n
+    (subgradient 0 where e = 0).  Close to |e| / beta for small errors and
+    always below 1 for large ones."""
+    pred = np.asarray(pred, dtype=np.float64)
+    target = np.asarray(target, dtype=np.float64)
+    e = pred - target
+    a = np.abs(e)
+    n = pred.size
+    loss = (a / (beta + a)).sum() / n
+    g = np.sign(e) * beta / (beta + a) ** 2 / n
+    return loss, g
+
+
+LOSSES = {"l1log": 0, "robust": 1}
+
+
+def loss_fn(pred, target, loss="l1log", beta=0.1):
+    if loss == "l1log":
+        return l1log_loss(pred, target)
+    if loss == "robust":
+        return robust_loss(pred, target, beta)
+    raise ValueError(f"unknown loss {loss!r}")
+
+
 def backward(params, acts, dy):
     """Gradient of the loss w.r.t. the flat params, given dL/dI_SR."""
     L = unpack(params)
@@ -170,10 +197,10 @@ def backward(params, acts, dy):
     return pack(grads)
 
 
-def loss_and_grad(params, lrhs, hrls, albedo, normal, target, s):
+def loss_and_grad(params, lrhs, hrls, albedo, normal, target, s, loss="l1log", beta=0.1):
     y, acts = forward(params, lrhs, hrls, albedo, normal, s, keep=True)
-    loss, dy = l1log_loss(y, target)
-    return loss, backward(params, acts, dy)
+    value, dy = loss_fn(y, target, loss, beta)
+    return value, backward(params, acts, dy)
 
 
 def adam(params, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
@@ -185,17 +212,19 @@ def adam(params, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
     return params - lr * mh / (np.sqrt(vh) + eps), m, v
 
 
-def train_step(params, m, v, step, lr, lrhs, hrls, albedo, normal, target, s, clip=100.0):
+def train_step(params, m, v, step, lr, lrhs, hrls, albedo, normal, target, s, clip=100.0,
+               loss="l1log", beta=0.1):
     """One training step as the method's learned part runs it: radiance inputs
-    and target clipped at `clip` (firefly clipping, Sec. 3.2), L1-log loss,
-    backward, bias-corrected Adam at step `step` (counting from 1).
+    and target clipped at `clip` (firefly clipping, Sec. 3.2), the loss
+    ("l1log", or "robust" = l_r with factor `beta`, Sec. 3), backward,
+    bias-corrected Adam at step `step` (counting from 1).
     Returns (new params, m, v, loss, grad)."""
     lr_c = np.minimum(np.asarray(lrhs, np.float64), clip)
     hr_c = np.minimum(np.asarray(hrls, np.float64), clip)
     tg_c = np.minimum(np.asarray(target, np.float64), clip)
-    loss, grad = loss_and_grad(params, lr_c, hr_c, albedo, normal, tg_c, s)
+    value, grad = loss_and_grad(params, lr_c, hr_c, albedo, normal, tg_c, s, loss, beta)
     p1, m1, v1 = adam(params, grad, m, v, step, lr)
-    return p1, m1, v1, loss, grad
+    return p1, m1, v1, value, grad
 
 
 def kaiming(seed: int):

@@ -167,3 +167,58 @@ def test_slog_loss_extends_log1p():
     # negative predictions keep a gradient pointing back up
     _, g = cnn.l1log_loss(np.array([-0.5]), np.array([1.0]))
     assert g[0] < 0 and abs(g[0] + 1 / 1.5) < 1e-15
+
+
+def test_robust_loss_closed_forms():
+    # a constant error e on every value gives exactly e / (beta + e), whatever
+    # the size: 1/2 at e = beta, 3/4 at e = 3 beta
+    tgt = np.random.default_rng(10).uniform(0, 4, (2, 5, 7, 3))
+    for e, want in ((0.1, 0.5), (0.3, 0.75), (-0.1, 0.5)):
+        loss, _ = cnn.robust_loss(tgt + e, tgt, beta=0.1)
+        assert abs(loss - want) < 1e-12, (e, loss)
+    # bounded by 1 for huge errors, ~|e| / beta for tiny ones, 0 at e = 0
+    loss, _ = cnn.robust_loss(tgt + 1e6, tgt, beta=0.1)
+    assert 0.9999 < loss < 1.0
+    loss, g = cnn.robust_loss(tgt + 1e-7, tgt, beta=0.1)
+    assert abs(loss - 1e-6) < 1e-11
+    loss, g = cnn.robust_loss(tgt, tgt, beta=0.1)
+    assert loss == 0.0 and not g.any()
+    # symmetric: the gradient flips sign with the error
+    _, gp = cnn.robust_loss(tgt + 0.2, tgt)
+    _, gm = cnn.robust_loss(tgt - 0.2, tgt)
+    assert np.allclose(gp, -gm, rtol=0, atol=1e-15) and (gp > 0).all()
+
+
+def test_robust_loss_gradient_matches_finite_differences():
+    rng = np.random.default_rng(11)
+    pred = rng.uniform(-0.5, 3, (1, 3, 3, 3))
+    tgt = rng.uniform(0, 3, (1, 3, 3, 3))
+    _, g = cnn.robust_loss(pred, tgt, beta=0.1)
+    h = 1e-7
+    for idx in np.ndindex(pred.shape):
+        if abs(pred[idx] - tgt[idx]) < 1e-3:
+            continue
+        p1, p0 = pred.copy(), pred.copy()
+        p1[idx] += h
+        p0[idx] -= h
+        fd = (cnn.robust_loss(p1, tgt)[0] - cnn.robust_loss(p0, tgt)[0]) / (2 * h)
+        assert abs(fd - g[idx]) < 1e-7 * max(1.0, abs(g[idx]))
+
+
+def test_network_gradient_robust_loss_matches_finite_differences():
+    rng = np.random.default_rng(12)
+    lr, hr, alb, nrm = _inputs(rng, N=1, h=4, w=4, s=2)
+    tgt = rng.uniform(0, 2, hr.shape)
+    params = cnn.kaiming(1) * 0.5 + rng.normal(0, 0.01, cnn.NPARAMS)
+    _, g = cnn.loss_and_grad(params, lr, hr, alb, nrm, tgt, 2, loss="robust", beta=0.1)
+    h = 1e-6
+    offs = cnn.layer_offsets()
+    for li in (0, 5, 17):
+        wo, bo, _, _ = offs[li]
+        for i in list(rng.integers(wo, bo, 3)) + [bo]:
+            p1, p0 = params.copy(), params.copy()
+            p1[i] += h
+            p0[i] -= h
+            fd = (cnn.loss_and_grad(p1, lr, hr, alb, nrm, tgt, 2, loss="robust")[0]
+                  - cnn.loss_and_grad(p0, lr, hr, alb, nrm, tgt, 2, loss="robust")[0]) / (2 * h)
+            assert abs(fd - g[i]) <= 1e-6 * max(1e-3, abs(g[i])) + 1e-9, (i, fd, g[i])
