@@ -35,8 +35,9 @@ WORKLOAD = {
                 "x4 fusion CNN (12->64, 8 residual blocks, 64->3) in BF16 on tcgen05; fallback gate; "
                 "the two renders run concurrently on two streams",
     "scene_seed": 0, "lrhs": [256, 256, 64], "hrls": [1024, 1024, 4], "scale": 4,
-    "max_depth": 8, "rr_start": 3, "precision": "bf16", "net_init": "trained before the timed region (BF16 training step, 3000 Adam steps on 8 "
-                "held-out procedural scenes); Kaiming-normal seed 0 under --quick",
+    "max_depth": 8, "rr_start": 3, "precision": "bf16", "net_init": "trained before the timed region (BF16 training step, robust loss l_r with "
+                "beta 0.1, 3000 Adam steps on 8 held-out procedural scenes); Kaiming-normal seed 0 "
+                "under --quick",
     "l2": "flushed between steps (512 MiB write)",
 }
 LR, HR, S = 256, 1024, 4
@@ -205,7 +206,8 @@ def run_reference(args, rank, world):
 # ----------------------------------------------------------------------------
 # equal-PSNR comparison: hybrid frame vs plain high-resolution path tracing
 # ----------------------------------------------------------------------------
-def train_net(mrs, s, train_scenes=8, train_steps=3000, batch=16, crop=128, precision="bf16"):
+def train_net(mrs, s, train_scenes=8, train_steps=3000, batch=16, crop=128, precision="bf16",
+              loss="robust", beta=0.1):
     """Trains the fusion network on held-out procedural scenes (seeds 1..,
     never the bench scene) with the library's training step; returns the net
     and a description of the training."""
@@ -219,12 +221,13 @@ def train_net(mrs, s, train_scenes=8, train_steps=3000, batch=16, crop=128, prec
     net = mrs.Net(trainer.init_params(0))
     t0 = time.perf_counter()
     trainer.train(net, data, train_steps, batch=batch, crop=crop, s=s, lr=1e-3, seed=0,
-                  precision=precision)
+                  precision=precision, loss=loss, beta=beta)
     t_train = time.perf_counter() - t0
     del data
     return net, (f"{train_scenes} procedural scenes (seeds 1..{train_scenes}) at {HR}^2, targets "
                  f"256 spp ({t_data:.1f} s to render); {train_steps} Adam steps, batch {batch} x "
-                 f"{crop}^2, lr 1e-3, {precision} training step ({t_train:.1f} s)")
+                 f"{crop}^2, lr 1e-3, {loss} loss" + (f" (beta {beta})" if loss == "robust" else "") +
+                 f", {precision} training step ({t_train:.1f} s)")
 
 
 def equal_psnr(mrs, scene, s, net, training, ref_spp=4096):

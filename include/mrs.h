@@ -252,18 +252,19 @@ mrs_status mrs_fuse(mrs_net net, const float* lrhs, const float* hrls, const flo
 /* One training step of the fusion network (learned part of the method; the
  * paper trains with a robust loss and SGD, Sec. 4 "Loss function" and
  * "Implement details" -- this library uses L1 on log(1 + radiance) with Adam):
- * forward with every activation kept, loss mean |slog(y) - slog(target)|
- * with slog(x) = sign(x) log1p(|x|) (log(1 + radiance) for x >= 0) over
- * N*H*W*3 values (reduced in float64), full backward
+ * forward with every activation kept, the net's loss (mrs_net_set_loss;
+ * default mean |slog(y) - slog(target)| with slog(x) = sign(x) log1p(|x|),
+ * log(1 + radiance) for x >= 0) over N*H*W*3 values (reduced in float64),
+ * full backward
  * (transposed convolutions with flipped taps, ReLU masks, dW / db
  * reductions), and one bias-corrected Adam update (beta1 0.9, beta2 0.999,
  * eps 1e-8) of the FP32 master weights.  LRHS, HRLS and the target are
  * clipped at 100 first (firefly clipping of the training data, Sec. 3.2).
  * Image arguments as in mrs_fuse plus target device [N][H][W][3].
  * precision MRS_PREC_FP32: every convolution in FP32 (SIMT);
- * MRS_PREC_BF16: forward and transposed convolutions on the tensor cores
- * with BF16 activations and activation gradients, FP32 accumulation, FP32
- * dW / db reductions and FP32 master weights.  loss_out (HOST, may be NULL) receives
+ * MRS_PREC_BF16: forward, transposed and weight-gradient convolutions on
+ * the tensor cores with BF16 activations and activation gradients, FP32
+ * accumulation, FP32 dW / db reductions and FP32 master weights.  loss_out (HOST, may be NULL) receives
  * the loss before the update; when non-NULL the call synchronises `stream`.
  * Limit: N*H*W <= 2^22 pixels. */
 mrs_status mrs_train_step(mrs_net net, const float* lrhs, const float* hrls, const float* albedo,
@@ -279,7 +280,7 @@ mrs_status mrs_net_get_state(mrs_net net, float* params, float* adam_m, float* a
 mrs_status mrs_net_set_state(mrs_net net, const float* params, const float* adam_m,
                              const float* adam_v, int64_t step);
 
-/* Image error metrics of x against ref/* Image error metrics of x against ref (device float, n values each, both in
+/* Image error metrics of x against ref (device float, n values each, both in
  * scene-linear space), reduced in float64 on the GPU (Sec. 5):
  * out[0] = PSNR of the sRGB images (Eq. cvt_color, peak 1; +inf if equal),
  * out[1] = RelMSE with lambda1, lambda2, out[2] = MSE (linear).
@@ -318,6 +319,19 @@ mrs_status mrs_gate_async(const float* fused, const float* lrhs, const float* pl
 mrs_status mrs_conv3x3(const float* x, int32_t N, int32_t H, int32_t W, int32_t cin,
                        int32_t cout, const float* w, const float* b, int32_t relu,
                        int32_t precision, float* out, void* stream);
+
+/* Training loss of mrs_train_step (a property of the net, default
+ * MRS_LOSS_L1LOG):
+ *   MRS_LOSS_L1LOG  mean |slog(y) - slog(t)|, slog(x) = sign(x) log(1 + |x|)
+ *                   (L1 on log(1 + radiance), extended oddly below 0)
+ *   MRS_LOSS_ROBUST the robust loss l_r of Sec. 3 ("Loss function"): mean over
+ *                   pixel-channel values of |y - t| / (beta + |y - t|); the
+ *                   paper uses beta = 0.1
+ * with t the target clipped at 100 in both cases.  beta must be positive and
+ * finite (ignored by MRS_LOSS_L1LOG).  Host-side setting, no device work. */
+#define MRS_LOSS_L1LOG 0
+#define MRS_LOSS_ROBUST 1
+mrs_status mrs_net_set_loss(mrs_net net, int32_t loss, float beta);
 
 /* Weight and bias gradients of one 3x3 convolution with zero padding (the
  * backward pass of mrs_conv3x3 with respect to its parameters, the training

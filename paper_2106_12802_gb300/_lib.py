@@ -54,6 +54,7 @@ SIGS = {
     "mrs_gate_async": [P, P, P, I32, I32, I32, I32, F64, P, P, P, P],
     "mrs_conv3x3": [P, I32, I32, I32, I32, I32, P, P, I32, I32, P, P],
     "mrs_conv3x3_wgrad": [P, P, I32, I32, I32, I32, I32, I32, P, P, P],
+    "mrs_net_set_loss": [P, I32, F32],
     "mrs_selftest_wait_timeout": [I32, P],
     "mrs_status_string": [I32],
     "mrs_last_error": [],

@@ -15,12 +15,12 @@
 // 9 taps of the layer's weights stay resident in shared memory for the whole
 // persistent CTA.
 //
-// Warp roles (384 threads, one CTA per SM):
+// Warp roles (640 threads, one CTA per SM):
 //   warp 0: TMA producer (weights once, then A boxes through an S-stage ring)
-//   warp 10: residual prefetch into one of three staging slots
-//   warp 11: output TMA stores from the staging slots
+//   warp 18: residual prefetch into one of three staging slots
+//   warp 19: output TMA stores from the staging slots
 //   warp 1: TMEM allocator and MMA issuer (one thread)
-//   warps 2-9: epilogue; warp w reads TMEM lanes 32 (w % 4) .. + 31 and 32 of
+//   warps 2-17: epilogue; warp w reads TMEM lanes 32 (w % 4) .. + 31 and 16 of
 //           the 64 output channels: bias, ReLU / residual / bilinear skip,
 //           BF16 results written into the staging slot (swizzled) and sent out
 //           by one TMA store per tile
@@ -39,7 +39,9 @@ namespace {
 constexpr int kTileM = 128;          // MMA M: pixels x0-1 .. x0+126 of one image row
 constexpr int kQuarter = 30;         // output pixels per 32-lane TMEM quarter
 constexpr int kTileOut = 4 * kQuarter;   // output pixels per tile
-constexpr int kEpiWarps = 8;
+constexpr int kEpiWarps = 16;                  // 4 per TMEM lane quarter
+constexpr int kEpiGroups = kEpiWarps / 4;      // channel groups per quarter
+constexpr int kEpiCh = 64 / kEpiGroups;        // output channels per epilogue warp
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kResWarp = 2 + kEpiWarps;        // residual-prefetch warp
 constexpr int kStoreWarp = kResWarp + 1;       // output-store warp
@@ -257,7 +259,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     constexpr int KSTEPS = OPER == TC_BF16 ? 4 : 2;           // MMAs per kernel row (K 16 / 32)
     constexpr int SBYTES = kTileM * 128;                      // residual / output staging slot
     constexpr int ACCSTRIDE = 256;                            // TMEM columns per accumulator
-    constexpr int CHUNKS = NOUT == 64 ? 2 : 1;                // 16-channel chunks per warp
+    constexpr int CHUNKS = NOUT == 64 ? kEpiCh / 16 : 1;      // 16-channel chunks per warp
     constexpr uint32_t IDESC =
         (1u << 4) | ((OPER == TC_BF16 ? 1u : 0u) << 7) | ((OPER == TC_BF16 ? 1u : 0u) << 10) |
         ((uint32_t)(NF >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
@@ -419,14 +421,15 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         }
     } else {
-        // epilogue: 8 warps; warp w reads TMEM lanes 32 q .. 32 q + 31 (q = w % 4,
-        // pixels x0-1+30q+lane) and output channels [32 h, 32 h + 32),
-        // h = (w - 2) / 4.  Lane k < 30 produces output pixel x0 + 30q + k:
+        // epilogue: kEpiWarps warps; warp w reads TMEM lanes 32 q .. 32 q + 31
+        // (q = w % 4, pixels x0-1+30q+lane) and output channels
+        // [kEpiCh h, kEpiCh (h + 1)), h = (w - 2) / 4.  Lane k < 30 produces
+        // output pixel x0 + 30q + k:
         // out[c] = D[k][dx0][c] + D[k+1][dx1][c] + D[k+2][dx2][c], the two
         // neighbours by warp shuffles within the quarter.
         const int q = warp & 3, half = (warp - 2) >> 2;
         const int j = q * kQuarter + lane;                     // output pixel in the tile
-        const bool active = half * 32 < NOUT;
+        const bool active = half * kEpiCh < NOUT;
         uint32_t lt = 0;
         bool stop = false;
         for (int job = blockIdx.x; !stop && job < njobs; job += gridDim.x) {
@@ -443,7 +446,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const size_t p = ((size_t)n * a.H + y) * a.W + (valid ? x : 0);
             uint8_t* srow = sS + slot * SBYTES;
             for (int cc = 0; cc < CHUNKS && active; ++cc) {
-                const int c0 = half * 32 + cc * 16;
+                const int c0 = half * kEpiCh + cc * 16;
                 const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + acc * ACCSTRIDE + c0;
                 uint32_t r0[16], r1[16], r2[16];
                 tmem_ld16(taddr, r0);

@@ -455,25 +455,35 @@ __global__ void k_dw_reduce(const float* __restrict__ part, const float* __restr
     }
 }
 
-// L1 loss on slog(x) = sign(x) log1p(|x|) (= log(1 + x) for x >= 0):
-// d = slog(y) - slog(min(t, clip)); dy = sign(d) / (1 + |y|) / n; loss
-// partials reduced in float64
+// Training losses, reduced in float64 per block; dy receives dL/dy.
+//   MRS_LOSS_L1LOG: L1 on slog(x) = sign(x) log1p(|x|) (= log(1 + x) for
+//     x >= 0): d = slog(y) - slog(min(t, clip)); dy = sign(d) / (1 + |y|) / n
+//   MRS_LOSS_ROBUST: the robust loss l_r of Sec. 3, e = y - min(t, clip),
+//     |e| / (beta + |e|) per value; dy = sign(e) beta / (beta + |e|)^2 / n
 __device__ __forceinline__ double slog(double x) { return x < 0.0 ? -log1p(-x) : log1p(x); }
 
-__global__ void k_loss_l1log(const float* __restrict__ y, const float* __restrict__ tgt, size_t n,
-                             float clip, float* __restrict__ dy, double* __restrict__ part)
+__global__ void k_loss(const float* __restrict__ y, const float* __restrict__ tgt, size_t n,
+                       float clip, int kind, float beta, float* __restrict__ dy,
+                       double* __restrict__ part)
 {
     __shared__ double sh[256];
     double acc = 0.0;
     const float inv_n = 1.0f / (float)n;
+    const double b = (double)beta, dinv_n = 1.0 / (double)n;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
          i += (size_t)gridDim.x * blockDim.x) {
         float yp = y[i];
         float tv = clip > 0.0f ? fminf(tgt[i], clip) : tgt[i];
-        double d = slog((double)yp) - slog((double)tv);
-        acc += fabs(d);
         float g = 0.0f;
-        if (d != 0.0) g = (d > 0.0 ? 1.0f : -1.0f) / (1.0f + fabsf(yp)) * inv_n;
+        if (kind == MRS_LOSS_ROBUST) {
+            double e = (double)yp - (double)tv, a = fabs(e);
+            acc += a / (b + a);
+            if (e != 0.0) g = (float)((e > 0.0 ? b : -b) / ((b + a) * (b + a)) * dinv_n);
+        } else {
+            double d = slog((double)yp) - slog((double)tv);
+            acc += fabs(d);
+            if (d != 0.0) g = (d > 0.0 ? 1.0f : -1.0f) / (1.0f + fabsf(yp)) * inv_n;
+        }
         dy[i] = g;
     }
     sh[threadIdx.x] = acc;
@@ -591,6 +601,8 @@ struct mrs_net_s {
     Buf tact;                      // training activations
     Buf ttmp;                      // training scratch (transposed weights, dW partials, loss)
     int* err = nullptr;            // device error word
+    int loss_kind = MRS_LOSS_L1LOG;
+    float loss_beta = 0.1f;
 };
 
 namespace mrs {
@@ -1082,7 +1094,8 @@ mrs_status train_step_f32(mrs_net_s* net, const float* lrhs, const float* hrls, 
     if (rc != MRS_OK) return rc;
 
     // loss (float64 reduction) and dL/dy
-    MRS_TIMED(PK_TRAIN, st, k_loss_l1log<<<kRedBlocks, 256, 0, st>>>(y, target, P * 3, kClip, dy, lparts));
+    MRS_TIMED(PK_TRAIN, st, k_loss<<<kRedBlocks, 256, 0, st>>>(y, target, P * 3, kClip, net->loss_kind,
+                                                               net->loss_beta, dy, lparts));
     MRS_LAUNCHED(1);
     k_reduce_parts<<<1, 32, 0, st>>>(lparts, kRedBlocks, 1, lres);
     MRS_LAUNCHED(1);
@@ -1232,7 +1245,8 @@ mrs_status train_step_bf16(mrs_net_s* net, const float* lrhs, const float* hrls,
     if (rc != MRS_OK) return rc;
 
     // loss
-    MRS_TIMED(PK_TRAIN, st, k_loss_l1log<<<kRedBlocks, 256, 0, st>>>(y, target, P * 3, kClip, dy, lparts));
+    MRS_TIMED(PK_TRAIN, st, k_loss<<<kRedBlocks, 256, 0, st>>>(y, target, P * 3, kClip, net->loss_kind,
+                                                               net->loss_beta, dy, lparts));
     MRS_LAUNCHED(1);
     k_reduce_parts<<<1, 32, 0, st>>>(lparts, kRedBlocks, 1, lres);
     MRS_LAUNCHED(1);
@@ -1437,5 +1451,15 @@ extern "C" mrs_status mrs_conv3x3_wgrad(const float* x, const float* dy, int32_t
     int herr = 0;
     MRS_CHECK(cudaMemcpy(&herr, err, 4, cudaMemcpyDeviceToHost));
     if (herr) { cudaMemset(err, 0, 4); set_error("tensor-core weight-gradient wait timed out"); return MRS_ERR_TIMEOUT; }
+    return MRS_OK;
+}
+
+extern "C" mrs_status mrs_net_set_loss(mrs_net net, int32_t loss, float beta)
+{
+    MRS_ARG(net != nullptr, "net is NULL");
+    MRS_ARG(loss == MRS_LOSS_L1LOG || loss == MRS_LOSS_ROBUST, "unknown loss");
+    MRS_ARG(beta > 0.0f && beta < 1e30f, "beta must be positive and finite");
+    net->loss_kind = loss;
+    net->loss_beta = beta;
     return MRS_OK;
 }

@@ -16,6 +16,9 @@ NPARAMS = 599555
 PREC = {"fp32": 0, "bf16": 1, "fp8": 2}
 
 
+LOSSES = {"l1log": 0, "robust": 1}
+
+
 def _prec(p):
     return PREC[p] if isinstance(p, str) else int(p)
 
@@ -31,6 +34,12 @@ class Net:
         h = ctypes.c_void_p()
         call("mrs_net_create", ctypes.c_void_p(p.ctypes.data), NPARAMS, ctypes.byref(h))
         self.handle = h
+
+    def set_loss(self, loss="l1log", beta=0.1):
+        """Training loss of train_step: "l1log" (L1 on log(1 + x)) or "robust"
+        (the paper's l_r with factor beta)."""
+        call("mrs_net_set_loss", self.handle, LOSSES[loss] if isinstance(loss, str) else int(loss),
+             float(beta))
 
     def close(self):
         if getattr(self, "handle", None):
@@ -70,11 +79,14 @@ def _np_ptr(a):
 
 
 def train_step(net, lrhs, hrls, albedo, normal, target, scale, lr=1e-4, precision="fp32",
-               sync_loss=True, stream=None):
+               sync_loss=True, stream=None, loss=None, beta=0.1):
     """One Adam step on a batch (CUDA float32 NHWC tensors); returns the loss
-    (float) or None when sync_loss is False (no host synchronisation)."""
+    (float) or None when sync_loss is False (no host synchronisation).
+    `loss` ("l1log" / "robust"), when given, first sets the net's loss."""
     for t in (lrhs, hrls, albedo, normal, target):
         _dev(t, torch.float32)
+    if loss is not None:
+        net.set_loss(loss, beta)
     N, H, W, _ = hrls.shape
     loss = ctypes.c_double()
     call("mrs_train_step", net.handle, _ptr(lrhs), _ptr(hrls), _ptr(albedo), _ptr(normal),

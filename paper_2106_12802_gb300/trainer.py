@@ -49,15 +49,45 @@ def render_example(scene, size, s, spp_lr, spp_hr, spp_tgt, depth, rr, seed):
             "normal": hr["normal"][None], "target": tg[None]}
 
 
+# spp sets of the method's training (Sec. 4, implementation details): each
+# training example draws its HRLS spp and its LRHS spp from these, with the
+# HRLS spp below the LRHS spp
+SPP_HRLS_SET = (1, 2, 3, 4, 5, 6, 7, 8, 12, 16, 32)
+SPP_LRHS_SET = (2, 3, 4, 5, 6, 7, 8, 12, 16, 32, 64, 128, 250, 1000, 4000)
+
+
+def random_spp_pair(rng, spp_tgt):
+    """(spp_lr, spp_hr) drawn uniformly from the two sets with spp_hr <
+    spp_lr; LRHS values at or above the target's spp are left out (a noisier
+    target than the input would make no sense)."""
+    lr_set = [v for v in SPP_LRHS_SET if v < spp_tgt]
+    hr_set = [v for v in SPP_HRLS_SET if v < max(lr_set)]
+    if not lr_set or not hr_set:
+        raise ValueError(f"spp_tgt={spp_tgt} leaves no valid (LRHS, HRLS) spp pair")
+    while True:
+        hr = int(hr_set[int(rng.integers(len(hr_set)))])
+        lr = int(lr_set[int(rng.integers(len(lr_set)))])
+        if hr < lr:
+            return lr, hr
+
+
 def make_dataset(scene_seeds, size=256, s=4, spp_lr=64, spp_hr=4, spp_tgt=256, depth=8, rr=3,
-                 scene_fn=None):
-    """Render one example per procedural scene seed; tensors stay on the GPU."""
+                 scene_fn=None, spp_random=False, examples_per_scene=1, seed=0):
+    """Render `examples_per_scene` examples per procedural scene seed (render
+    seeds differ per example); with spp_random each example draws its (LRHS,
+    HRLS) spp with random_spp_pair, else uses (spp_lr, spp_hr).  Tensors stay
+    on the GPU; each example records its spp under "spp"."""
     from synth import scenes
     scene_fn = scene_fn or (lambda sd: scenes.procedural(sd, n_spheres=24, n_large=8))
+    rng = np.random.default_rng(np.random.SeedSequence([0x737070, int(seed)]))
     data = []
     for sd in scene_seeds:
         sc = Scene(scene_fn(sd))
-        data.append(render_example(sc, size, s, spp_lr, spp_hr, spp_tgt, depth, rr, sd))
+        for e in range(examples_per_scene):
+            a, b = random_spp_pair(rng, spp_tgt) if spp_random else (spp_lr, spp_hr)
+            ex = render_example(sc, size, s, a, b, spp_tgt, depth, rr, sd + 100003 * e)
+            ex["spp"] = (a, b)
+            data.append(ex)
         sc.close()
     torch.cuda.synchronize()
     return data
@@ -78,10 +108,14 @@ def random_batch(data, batch, crop, s, rng):
     return {k: torch.cat(v).contiguous() for k, v in out.items()}
 
 
-def train(net, data, steps, batch=16, crop=128, s=4, lr=1e-4, seed=0, log_every=0, precision="fp32"):
+def train(net, data, steps, batch=16, crop=128, s=4, lr=1e-4, seed=0, log_every=0, precision="fp32",
+          loss=None, beta=0.1):
     """Adam on random crops of `data`; precision "fp32" (SIMT) or "bf16"
-    (tensor cores, FP32 master weights)."""
+    (tensor cores, FP32 master weights); `loss` ("l1log" / "robust"), when
+    given, sets the net's training loss first."""
     rng = np.random.default_rng(seed)
+    if loss is not None:
+        net.set_loss(loss, beta)
     losses = []
     for i in range(steps):
         b = random_batch(data, batch, crop, s, rng)

@@ -122,3 +122,61 @@ def test_bf16_training_reduces_loss(mrs):
     t = _cuda(lr, hr, alb, nrm, tgt)
     losses = [mrs.train_step(net, *t, 4, lr=1e-3, precision="bf16") for _ in range(40)]
     assert losses[-1] < 0.7 * losses[0], losses[::5]
+
+
+@pytest.mark.parametrize("N,h,w,s", [(2, 4, 6, 4), (1, 8, 8, 2)])
+def test_robust_loss_train_step_matches_oracle(mrs, N, h, w, s):
+    # the paper's l_r (beta = 0.1) through the FP32 step: loss, every layer's
+    # gradient and the Adam update against the float64 oracle
+    lr, hr, alb, nrm, tgt = _batch(6, N, h, w, s)
+    p = _params(5)
+    net = mrs.Net(p)
+    loss = mrs.train_step(net, *_cuda(lr, hr, alb, nrm, tgt), s, lr=1e-3, loss="robust", beta=0.1)
+    g = mrs.get_grads(net)
+    p1 = net.get_params()
+    z = np.zeros(mrs.NPARAMS)
+    rp, _, _, rloss, rg = cnn.train_step(p.astype(np.float64), z, z, 1, 1e-3, lr, hr, alb, nrm, tgt, s,
+                                         loss="robust", beta=0.1)
+    assert abs(loss - rloss) <= 1e-6 * rloss
+    for li, (wo, bo, ci, co) in enumerate(cnn.layer_offsets()):
+        for a, b in ((wo, bo), (bo, bo + co)):
+            ref = rg[a:b]
+            err = np.linalg.norm(g[a:b] - ref) / max(np.linalg.norm(ref), 1e-30)
+            assert err < 1e-4, (li, a, err)
+    ok = np.abs(rg) > 1e-6
+    assert np.abs((p1 - p) - (rp - p))[ok].max() <= 0.01 * 1e-3
+
+
+def test_robust_loss_bf16_and_loss_switch(mrs):
+    # l_r weights an error by beta / (beta + |e|)^2, so a forward rounding
+    # error de changes the gradient of that value by 2 de / (beta + |e|)
+    # relative (and near e = 0 BF16 rounding decides its sign).  The target
+    # keeps every |e| in [1, 3], where BF16 forward rounding (de ~ 1e-2) moves
+    # dy by ~2%, so that the comparison measures the kernels rather than the
+    # loss's own sensitivity
+    lr, hr, alb, nrm, _ = _batch(7, 2, 8, 8, 4)
+    p = _params(6)
+    y = cnn.forward(p.astype(np.float64), np.minimum(lr, 100.0), np.minimum(hr, 100.0), alb, nrm, 4)
+    rng = np.random.default_rng(8)
+    tgt = (y + rng.choice([-1.0, 1.0], y.shape) * rng.uniform(1.0, 3.0, y.shape)).astype(np.float32)
+    net = mrs.Net(p)
+    t = _cuda(lr, hr, alb, nrm, tgt)
+    loss = mrs.train_step(net, *t, 4, lr=1e-3, precision="bf16", loss="robust", beta=0.1)
+    g = mrs.get_grads(net)
+    z = np.zeros(mrs.NPARAMS)
+    _, _, _, rloss, rg = cnn.train_step(p.astype(np.float64), z, z, 1, 1e-3, lr, hr, alb, nrm, tgt, 4,
+                                        loss="robust", beta=0.1)
+    assert abs(loss - rloss) <= 2e-2 * rloss
+    for li, (wo, bo, _, _) in enumerate(cnn.layer_offsets()):
+        ref, got = rg[wo:bo], g[wo:bo].astype(np.float64)
+        cos = got @ ref / (np.linalg.norm(got) * np.linalg.norm(ref) + 1e-30)
+        assert cos > 0.99, (li, cos)
+    # switching back to the default loss reproduces the oracle's L1-log loss
+    net2 = mrs.Net(p)
+    net2.set_loss("robust", 0.5)
+    net2.set_loss("l1log")
+    l2 = mrs.train_step(net2, *t, 4, lr=1e-3)
+    r2 = cnn.train_step(p.astype(np.float64), z, z, 1, 1e-3, lr, hr, alb, nrm, tgt, 4)[3]
+    assert abs(l2 - r2) <= 1e-6 * r2
+    with pytest.raises(Exception):
+        net2.set_loss("robust", 0.0)
