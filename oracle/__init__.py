@@ -61,7 +61,7 @@ def lib():
             L.orc_cast.argtypes = [P, i32, P, P, i32, i32, P, P]
             L.orc_cast.restype = i32
             L.orc_render.argtypes = [P, i32, P, P, P, P, i32, P, P, i32, i32, i32, i32, i32,
-                                     u64, i32, i32, i32, P, P, P, P, P, P]
+                                     i32, u64, i32, i32, i32, P, P, P, P, P, P]
             L.orc_render.restype = i32
             L.orc_num_threads.restype = i32
             _lib = L
@@ -137,12 +137,14 @@ def num_threads() -> int:
     return int(lib().orc_num_threads())
 
 
-def render(scene, W, H, spp, max_depth, rr_start=None, seed=0, rows=None, threads=0):
+def render(scene, W, H, spp, max_depth, rr_start=None, seed=0, rows=None, threads=0, grid=1):
     """Path-trace the scene; returns dict(radiance[H,W,3], albedo, normal,
     depth[H,W], counts[max_depth+1], shadow_counts[max_depth+1]).
 
     rr_start=None disables Russian roulette.  rows=(r0, r1) renders only those
-    image rows (the result then has r1-r0 rows) -- used for bounded samples."""
+    image rows (the result then has r1-r0 rows) -- used for bounded samples.
+    grid=g > 1 samples each pixel only inside the centre sub-pixel of its g x g
+    block (nearest-neighbour downsampling of a g-times finer render)."""
     if rr_start is None:
         rr_start = 1 << 30
     r0, r1 = (0, H) if rows is None else rows
@@ -158,7 +160,7 @@ def render(scene, W, H, spp, max_depth, rr_start=None, seed=0, rows=None, thread
     s = scene
     rc = lib().orc_render(_p(s["V"]), len(s["V"]), _p(s["tri_mat"]), _p(s["tri_light"]),
                           _p(s["mats"]), _p(s["lights"]), len(s["lights"]), _p(s["env"]),
-                          _p(s["cam"]), W, H, spp, max_depth, rr_start, seed, r0, r1, threads,
+                          _p(s["cam"]), W, H, spp, max_depth, rr_start, grid, seed, r0, r1, threads,
                           _p(out["radiance"]), _p(out["albedo"]), _p(out["normal"]),
                           _p(out["depth"]), _p(out["counts"]), _p(out["shadow_counts"]))
     if rc != 0:

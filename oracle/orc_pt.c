@@ -589,6 +589,7 @@ static int bsdf_sample(const mat_t* m, v3 wo, float u1, float u2, v3* wi, v3* we
 /* ------------------------------------------------------------------------ */
 typedef struct {
     int W, H, spp, max_depth, rr_start;
+    int grid;   /* camera sampling grid: 1 = whole pixel footprint */
     uint32_t key[2];
 } rparams_t;
 
@@ -602,8 +603,15 @@ static v3 trace_path(const scene_t* S, const rparams_t* P, int px, int py, int s
     const float* cam = S->cam;
     v3 eye = mk(cam[0], cam[1], cam[2]), fwd = mk(cam[3], cam[4], cam[5]);
     v3 rgt = mk(cam[6], cam[7], cam[8]), up = mk(cam[9], cam[10], cam[11]);
-    float sx = ((float)px + g1[2]) / (float)P->W;
-    float sy = ((float)py + g1[3]) / (float)P->H;
+    /* grid g > 1: the pixel stands for a g x g block of a g-times finer image
+       and its samples cover only that block's sub-pixel (g*px + g/2,
+       g*py + g/2): nearest-neighbour downsampling of the finer image, the
+       low-resolution renders of Sec. 3, "Low Resolution Image Generation"
+       (rays of the low-resolution image on a sparse grid).  g = 1
+       is the ordinary box footprint of the pixel. */
+    const int g = P->grid;
+    float sx = ((float)(px * g + g / 2) + g1[2]) / (float)(P->W * g);
+    float sy = ((float)(py * g + g / 2) + g1[3]) / (float)(P->H * g);
     float a = 2.0f * sx - 1.0f, bq = 1.0f - 2.0f * sy;
     v3 o = eye;
     v3 d = normalize(mk(fwd.x + rgt.x * a + up.x * bq, fwd.y + rgt.y * a + up.y * bq,
@@ -733,11 +741,12 @@ static v3 trace_path(const scene_t* S, const rparams_t* P, int px, int py, int s
 int orc_render(const float* V, int n, const int32_t* tri_mat, const int32_t* tri_light,
                const float* mats, const float* lights, int n_lights, const float* env,
                const float* cam, int W, int H, int spp, int max_depth, int rr_start,
-               uint64_t seed, int row0, int row1, int threads,
+               int grid, uint64_t seed, int row0, int row1, int threads,
                float* radiance, float* albedo, float* normal, float* depth,
                uint64_t* counts, uint64_t* shadow_counts)
 {
     if (W <= 0 || H <= 0 || spp <= 0 || max_depth < 0 || max_depth > 62) return -1;
+    if (grid < 1 || grid > 64) return -1;
     if (row1 <= 0 || row1 > H) row1 = H;
     if (row0 < 0) row0 = 0;
     scene_t S;
@@ -745,7 +754,7 @@ int orc_render(const float* V, int n, const int32_t* tri_mat, const int32_t* tri
         scene_free(&S);
         return -2;
     }
-    rparams_t P = {W, H, spp, max_depth, rr_start, {(uint32_t)seed, (uint32_t)(seed >> 32)}};
+    rparams_t P = {W, H, spp, max_depth, rr_start, grid, {(uint32_t)seed, (uint32_t)(seed >> 32)}};
     int nb = max_depth + 1;
     uint64_t tot[64] = {0}, stot[64] = {0};
 #ifdef _OPENMP

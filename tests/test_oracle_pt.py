@@ -73,6 +73,30 @@ def test_low_res_render_is_box_average_of_high_res(orc):
     assert rel < 0.05, rel
 
 
+def test_sparse_grid_render_is_nearest_neighbour_of_high_res(orc):
+    # grid=2: an LR pixel samples only the centre sub-pixel (2i+1, 2j+1) of its
+    # 2 x 2 block, so in expectation it equals that HR pixel (nearest-neighbour
+    # downsampling, the paper's LR images); the other sub-pixels and the box
+    # average are far off on this scene's edges, so a wrong offset fails
+    sc = scenes.cornell_box(sphere_subdiv=2)
+    lr = orc.render(sc, 8, 8, 2048, 3, seed=3, grid=2)["radiance"].astype(np.float64)
+    hr = orc.render(sc, 16, 16, 512, 3, seed=4)["radiance"].astype(np.float64)
+
+    def rel(ref):
+        return np.abs(lr - ref).mean() / np.abs(ref).mean()
+    good = rel(hr[1::2, 1::2])
+    assert good < 0.05, good
+    for oy, ox in ((0, 0), (0, 1), (1, 0)):
+        assert rel(hr[oy::2, ox::2]) > 4 * good, (oy, ox)
+    assert rel(hr.reshape(8, 2, 8, 2, 3).mean(axis=(1, 3))) > 4 * good
+    # grid=1 is the ordinary render, bit for bit
+    a = orc.render(sc, 8, 8, 4, 3, seed=9)
+    b = orc.render(sc, 8, 8, 4, 3, seed=9, grid=1)
+    assert all(np.array_equal(a[k], b[k]) for k in a)
+    with pytest.raises(ValueError):
+        orc.render(sc, 8, 8, 4, 3, grid=0)
+
+
 def test_aux_buffers_on_axis_aligned_walls(orc):
     sc = scenes.cornell_box(sphere_subdiv=1)
     W = H = 32
