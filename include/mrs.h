@@ -204,6 +204,20 @@ mrs_status mrs_render_ctx(mrs_ctx ctx, mrs_scene scene, int32_t W, int32_t H, in
                           float* albedo, float* normal, float* depth, uint64_t* counts,
                           uint64_t* shadow_counts, void* stream);
 
+/* Render on a sparse camera-sampling grid (the paper's low-resolution images,
+ * Sec. 3 "Low Resolution Image Generation": nearest-neighbour downsampling
+ * of a `grid`-times finer render, i.e. rays on a sparse grid): pixel (x, y)
+ * of the W x H image draws all its samples inside the single sub-pixel
+ * (grid*x + grid/2, grid*y + grid/2) of the (grid*W) x (grid*H) image, instead
+ * of over its whole footprint.  grid = 1 is exactly mrs_render.  ctx may be
+ * NULL (the scene's own path state, as mrs_render) or a render context (as
+ * mrs_render_ctx).  grid in [1, 64], W*grid and H*grid <= 65536; other
+ * arguments as in mrs_render. */
+mrs_status mrs_render_grid(mrs_ctx ctx, mrs_scene scene, int32_t W, int32_t H, int32_t spp,
+                           int32_t max_depth, int32_t rr_start, uint64_t seed, int32_t grid,
+                           float* radiance, float* albedo, float* normal, float* depth,
+                           uint64_t* counts, uint64_t* shadow_counts, void* stream);
+
 /* Paths per wave for subsequent mrs_render calls on this scene (rounded to
  * whole samples of the image; default 16M paths).  For tests and tuning. */
 mrs_status mrs_scene_set_wave(mrs_scene scene, int64_t max_paths_per_wave);

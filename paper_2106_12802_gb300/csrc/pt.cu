@@ -317,6 +317,7 @@ struct WaveParams {
     float env[3];
     float cam[12];
     int W, H, max_depth, rr_start;
+    int grid;            // camera sampling grid (1 = whole pixel footprint)
     int64_t wh;          // pixels
     int s0;              // first sample index of the wave
     int n_paths;         // paths in the wave (= k * wh)
@@ -336,8 +337,13 @@ __global__ void __launch_bounds__(kThreads) k_raygen(WaveParams w)
         int px = pix % w.W, py = pix / w.W;
         float4 g1 = draws((uint32_t)pix, (uint32_t)sample, 0u, 1u, w.key);
         const float* cam = w.cam;
-        float sx = ((float)px + g1.z) / (float)w.W;
-        float sy = ((float)py + g1.w) / (float)w.H;
+        // grid g > 1: only the centre sub-pixel (g px + g/2, g py + g/2) of the
+        // pixel's g x g block is sampled (nearest-neighbour downsampling of a
+        // g-times finer image: the low-resolution renders of Sec. 3); g = 1 is
+        // the whole pixel footprint, the same operations as without a grid
+        const int g = w.grid;
+        float sx = ((float)(px * g + g / 2) + g1.z) / (float)(w.W * g);
+        float sy = ((float)(py * g + g / 2) + g1.w) / (float)(w.H * g);
         float a = 2.0f * sx - 1.0f, bq = 1.0f - 2.0f * sy;
         V3 d = normalize(mk(cam[3] + cam[6] * a + cam[9] * bq, cam[4] + cam[7] * a + cam[10] * bq,
                             cam[5] + cam[8] * a + cam[11] * bq));
@@ -648,6 +654,7 @@ using namespace mrs;
 
 static mrs_status render_impl(mrs_scene S, Buf& arena, int64_t wave_paths, int32_t W, int32_t H,
                               int32_t spp, int32_t max_depth, int32_t rr_start, uint64_t seed,
+                              int32_t grid,
                               float* radiance, float* albedo, float* normal, float* depth,
                               uint64_t* counts, uint64_t* shadow_counts,
                               unsigned long long* stats, void* stream)
@@ -657,6 +664,8 @@ static mrs_status render_impl(mrs_scene S, Buf& arena, int64_t wave_paths, int32
     MRS_ARG(spp >= 1 && spp <= 65536, "spp must be in [1, 65536]");
     MRS_ARG(max_depth >= 0 && max_depth <= 32, "max_depth must be in [0, 32]");
     MRS_ARG(radiance != nullptr, "radiance is NULL");
+    MRS_ARG(grid >= 1 && grid <= 64, "grid must be in [1, 64]");
+    MRS_ARG((int64_t)W * grid <= 65536 && (int64_t)H * grid <= 65536, "W * grid, H * grid must be <= 65536");
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t wh = (int64_t)W * H;
     int64_t k = wave_paths / wh;
@@ -695,6 +704,7 @@ static mrs_status render_impl(mrs_scene S, Buf& arena, int64_t wave_paths, int32
     memcpy(w.env, S->env, sizeof(w.env));
     memcpy(w.cam, S->cam, sizeof(w.cam));
     w.W = W; w.H = H; w.max_depth = max_depth;
+    w.grid = grid;
     w.rr_start = rr_start < 0 ? 0x7fffffff : rr_start;
     w.wh = wh;
     w.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
@@ -741,7 +751,7 @@ extern "C" mrs_status mrs_render(mrs_scene S, int32_t W, int32_t H, int32_t spp,
                                  uint64_t* shadow_counts, void* stream)
 {
     MRS_ARG(S != nullptr, "scene is NULL");
-    return render_impl(S, S->arena, S->wave_paths, W, H, spp, max_depth, rr_start, seed, radiance,
+    return render_impl(S, S->arena, S->wave_paths, W, H, spp, max_depth, rr_start, seed, 1, radiance,
                        albedo, normal, depth, counts, shadow_counts, nullptr, stream);
 }
 
@@ -776,8 +786,21 @@ extern "C" mrs_status mrs_render_ctx(mrs_ctx ctx, mrs_scene S, int32_t W, int32_
 {
     MRS_ARG(ctx != nullptr, "ctx is NULL");
     MRS_ARG(S != nullptr, "scene is NULL");
-    return render_impl(S, ctx->arena, ctx->wave_paths, W, H, spp, max_depth, rr_start, seed,
+    return render_impl(S, ctx->arena, ctx->wave_paths, W, H, spp, max_depth, rr_start, seed, 1,
                        radiance, albedo, normal, depth, counts, shadow_counts, nullptr, stream);
+}
+
+extern "C" mrs_status mrs_render_grid(mrs_ctx ctx, mrs_scene S, int32_t W, int32_t H, int32_t spp,
+                                      int32_t max_depth, int32_t rr_start, uint64_t seed,
+                                      int32_t grid, float* radiance, float* albedo, float* normal,
+                                      float* depth, uint64_t* counts, uint64_t* shadow_counts,
+                                      void* stream)
+{
+    MRS_ARG(S != nullptr, "scene is NULL");
+    Buf& arena = ctx ? ctx->arena : S->arena;
+    int64_t wave = ctx ? ctx->wave_paths : S->wave_paths;
+    return render_impl(S, arena, wave, W, H, spp, max_depth, rr_start, seed, grid, radiance, albedo,
+                       normal, depth, counts, shadow_counts, nullptr, stream);
 }
 
 extern "C" mrs_status mrs_render_stats(mrs_scene S, int32_t W, int32_t H, int32_t spp,
@@ -787,7 +810,7 @@ extern "C" mrs_status mrs_render_stats(mrs_scene S, int32_t W, int32_t H, int32_
     MRS_ARG(S != nullptr, "scene is NULL");
     MRS_ARG(stats != nullptr, "stats is NULL");
     MRS_CHECK(cudaMemsetAsync(stats, 0, 4 * sizeof(uint64_t), (cudaStream_t)stream));
-    return render_impl(S, S->arena, S->wave_paths, W, H, spp, max_depth, rr_start, seed, radiance,
+    return render_impl(S, S->arena, S->wave_paths, W, H, spp, max_depth, rr_start, seed, 1, radiance,
                        nullptr, nullptr, nullptr, nullptr, nullptr, (unsigned long long*)stats, stream);
 }
 

@@ -134,9 +134,11 @@ class RenderContext:
 
 
 def render(scene: Scene, W, H, spp, max_depth, rr_start=None, seed=0, aux=True, counts=True,
-           out=None, stream=None, ctx: RenderContext | None = None):
+           out=None, stream=None, ctx: RenderContext | None = None, grid=1):
     """mrs_render (or mrs_render_ctx when ctx is given) into device tensors;
-    returns dict of (device) tensors."""
+    returns dict of (device) tensors.  grid > 1 renders on the sparse
+    camera-sampling grid (mrs_render_grid): each pixel samples only the centre
+    sub-pixel of its grid x grid block, the paper's nearest-neighbour LR."""
     dev = torch.device("cuda")
     if out is None:
         out = {"radiance": torch.empty((H, W, 3), dtype=torch.float32, device=dev)}
@@ -147,11 +149,15 @@ def render(scene: Scene, W, H, spp, max_depth, rr_start=None, seed=0, aux=True, 
         if counts:
             out["counts"] = torch.zeros(max_depth + 1, dtype=torch.int64, device=dev)
             out["shadow_counts"] = torch.zeros(max_depth + 1, dtype=torch.int64, device=dev)
-    args = (W, H, spp, max_depth, -1 if rr_start is None else rr_start,
-            int(seed) & 0xFFFFFFFFFFFFFFFF, _ptr(out["radiance"]), _ptr(out.get("albedo")),
-            _ptr(out.get("normal")), _ptr(out.get("depth")), _ptr(out.get("counts")),
-            _ptr(out.get("shadow_counts")), _stream(stream))
-    if ctx is None:
+    bufs = (_ptr(out["radiance"]), _ptr(out.get("albedo")), _ptr(out.get("normal")),
+            _ptr(out.get("depth")), _ptr(out.get("counts")), _ptr(out.get("shadow_counts")),
+            _stream(stream))
+    head = (W, H, spp, max_depth, -1 if rr_start is None else rr_start, int(seed) & 0xFFFFFFFFFFFFFFFF)
+    args = head + bufs
+    if grid != 1:
+        call("mrs_render_grid", ctx.handle if ctx is not None else None, scene.handle, *head,
+             int(grid), *bufs)
+    elif ctx is None:
         call("mrs_render", scene.handle, *args)
     else:
         call("mrs_render_ctx", ctx.handle, scene.handle, *args)

@@ -37,11 +37,13 @@ def init_params(seed: int, resid_gain: float = 0.1) -> np.ndarray:
     return p
 
 
-def render_example(scene, size, s, spp_lr, spp_hr, spp_tgt, depth, rr, seed):
+def render_example(scene, size, s, spp_lr, spp_hr, spp_tgt, depth, rr, seed, lr_grid=1):
     """One training triple: LRHS [1,size/s,size/s,3], HRLS + albedo + normal
-    [1,size,size,3], target [1,size,size,3] (independent seeds per render)."""
+    [1,size,size,3], target [1,size,size,3] (independent seeds per render).
+    lr_grid = s renders the LRHS on the sparse grid (nearest-neighbour LR, the
+    paper's low-resolution images); 1 jitters over the whole LR pixel."""
     lr = render_image(scene, size // s, size // s, spp_lr, depth, rr, 3 * seed + 0, aux=False,
-                       counts=False)["radiance"]
+                       counts=False, grid=lr_grid)["radiance"]
     hr = render_image(scene, size, size, spp_hr, depth, rr, 3 * seed + 1, aux=True, counts=False)
     tg = render_image(scene, size, size, spp_tgt, depth, rr, 3 * seed + 2, aux=False,
                        counts=False)["radiance"]
@@ -72,7 +74,7 @@ def random_spp_pair(rng, spp_tgt):
 
 
 def make_dataset(scene_seeds, size=256, s=4, spp_lr=64, spp_hr=4, spp_tgt=256, depth=8, rr=3,
-                 scene_fn=None, spp_random=False, examples_per_scene=1, seed=0):
+                 scene_fn=None, spp_random=False, examples_per_scene=1, seed=0, lr_grid=1):
     """Render `examples_per_scene` examples per procedural scene seed (render
     seeds differ per example); with spp_random each example draws its (LRHS,
     HRLS) spp with random_spp_pair, else uses (spp_lr, spp_hr).  Tensors stay
@@ -85,7 +87,7 @@ def make_dataset(scene_seeds, size=256, s=4, spp_lr=64, spp_hr=4, spp_tgt=256, d
         sc = Scene(scene_fn(sd))
         for e in range(examples_per_scene):
             a, b = random_spp_pair(rng, spp_tgt) if spp_random else (spp_lr, spp_hr)
-            ex = render_example(sc, size, s, a, b, spp_tgt, depth, rr, sd + 100003 * e)
+            ex = render_example(sc, size, s, a, b, spp_tgt, depth, rr, sd + 100003 * e, lr_grid)
             ex["spp"] = (a, b)
             data.append(ex)
         sc.close()

@@ -84,14 +84,14 @@ def test_cast_equals_brute_force(mrs, orc, seed, n):
     assert np.array_equal(t.cpu().numpy(), tb)
 
 
-def _compare_render(mrs, orc, desc, W, H, spp, D, rr=None, seed=0, wave=None):
+def _compare_render(mrs, orc, desc, W, H, spp, D, rr=None, seed=0, wave=None, grid=1, ctx=None):
     sc = mrs.Scene(desc)
     if wave:
         sc.set_wave(wave)
-    g = mrs.render(sc, W, H, spp, D, rr_start=rr, seed=seed)
+    g = mrs.render(sc, W, H, spp, D, rr_start=rr, seed=seed, grid=grid, ctx=ctx)
     torch.cuda.synchronize()
     g = {k: v.cpu().numpy() for k, v in g.items()}
-    r = orc.render(desc, W, H, spp, D, rr_start=rr, seed=seed)
+    r = orc.render(desc, W, H, spp, D, rr_start=rr, seed=seed, grid=grid)
     assert np.array_equal(g["counts"].astype(np.uint64), r["counts"])
     assert np.array_equal(g["shadow_counts"].astype(np.uint64), r["shadow_counts"])
     assert_radiance_parity(g["radiance"], r["radiance"])
@@ -135,6 +135,24 @@ def test_render_degenerate_scenes(mrs, orc):
     _compare_render(mrs, orc, one, 9, 7, 3, 2)
     # 1 x 1 image, depth 0
     _compare_render(mrs, orc, scenes.cornell_box(sphere_subdiv=1), 1, 1, 3, 0)
+
+
+def test_render_sparse_grid_matches_oracle(mrs, orc):
+    # nearest-neighbour LR sampling (each pixel samples only the centre
+    # sub-pixel of its grid x grid block): bit-exact counts, aux and radiance
+    # parity as for the ordinary render; odd grid, ragged waves, a context
+    g4, _ = _compare_render(mrs, orc, scenes.cornell_box(sphere_subdiv=2), 32, 32, 16, 4, grid=4)
+    _compare_render(mrs, orc, scenes.procedural(0), 40, 24, 4, 8, rr=3, seed=2, grid=4)
+    _compare_render(mrs, orc, scenes.cornell_box(sphere_subdiv=2), 21, 13, 5, 3, seed=4, grid=3,
+                    wave=21 * 13 * 2)
+    ctx = mrs.RenderContext()
+    gc, _ = _compare_render(mrs, orc, scenes.cornell_box(sphere_subdiv=2), 32, 32, 16, 4, grid=4,
+                            ctx=ctx)
+    assert all(np.array_equal(g4[k], gc[k]) for k in g4)
+    sc = mrs.Scene(scenes.cornell_box(sphere_subdiv=1))
+    for bad in (0, 65):
+        with pytest.raises(Exception):
+            mrs.render(sc, 8, 8, 1, 2, grid=bad)
 
 
 def test_render_full_size_sampled_rows(mrs, orc):
