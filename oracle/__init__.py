@@ -61,7 +61,7 @@ def lib():
             L.orc_cast.argtypes = [P, i32, P, P, i32, i32, P, P]
             L.orc_cast.restype = i32
             L.orc_render.argtypes = [P, i32, P, P, P, P, i32, P, P, i32, i32, i32, i32, i32,
-                                     i32, u64, i32, i32, i32, P, P, P, P, P, P]
+                                     i32, u64, i32, i32, i32, P, P, P, P, P, P, P, P, P]
             L.orc_render.restype = i32
             L.orc_num_threads.restype = i32
             _lib = L
@@ -144,7 +144,10 @@ def render(scene, W, H, spp, max_depth, rr_start=None, seed=0, rows=None, thread
     rr_start=None disables Russian roulette.  rows=(r0, r1) renders only those
     image rows (the result then has r1-r0 rows) -- used for bounded samples.
     grid=g > 1 samples each pixel only inside the centre sub-pixel of its g x g
-    block (nearest-neighbour downsampling of a g-times finer render)."""
+    block (nearest-neighbour downsampling of a g-times finer render).
+    Also returns the extra layers diffuse, specular and variance [H,W,3]:
+    the radiance of the samples whose first hit is Lambertian / GGX, and the
+    per-channel sample variance of the pixel mean."""
     if rr_start is None:
         rr_start = 1 << 30
     r0, r1 = (0, H) if rows is None else rows
@@ -154,6 +157,9 @@ def render(scene, W, H, spp, max_depth, rr_start=None, seed=0, rows=None, thread
         "albedo": np.zeros((h, W, 3), np.float32),
         "normal": np.zeros((h, W, 3), np.float32),
         "depth": np.zeros((h, W), np.float32),
+        "diffuse": np.zeros((h, W, 3), np.float32),
+        "specular": np.zeros((h, W, 3), np.float32),
+        "variance": np.zeros((h, W, 3), np.float32),
         "counts": np.zeros(max_depth + 1, np.uint64),
         "shadow_counts": np.zeros(max_depth + 1, np.uint64),
     }
@@ -162,7 +168,8 @@ def render(scene, W, H, spp, max_depth, rr_start=None, seed=0, rows=None, thread
                           _p(s["mats"]), _p(s["lights"]), len(s["lights"]), _p(s["env"]),
                           _p(s["cam"]), W, H, spp, max_depth, rr_start, grid, seed, r0, r1, threads,
                           _p(out["radiance"]), _p(out["albedo"]), _p(out["normal"]),
-                          _p(out["depth"]), _p(out["counts"]), _p(out["shadow_counts"]))
+                          _p(out["depth"]), _p(out["diffuse"]), _p(out["specular"]),
+                          _p(out["variance"]), _p(out["counts"]), _p(out["shadow_counts"]))
     if rc != 0:
         raise ValueError(f"orc_render failed ({rc})")
     return out

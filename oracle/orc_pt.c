@@ -593,9 +593,11 @@ typedef struct {
     uint32_t key[2];
 } rparams_t;
 
-/* one path; returns radiance, writes first-hit aux, counts rays per bounce */
+/* one path; returns radiance, writes first-hit aux (albedo, shading normal,
+   depth, lobe = 1 Lambertian / 2 GGX / 0 no hit), counts rays per bounce */
 static v3 trace_path(const scene_t* S, const rparams_t* P, int px, int py, int sample,
-                     v3* alb, v3* nrm, float* depth, uint64_t* counts, uint64_t* shadow_counts)
+                     v3* alb, v3* nrm, float* depth, int* lobe, uint64_t* counts,
+                     uint64_t* shadow_counts)
 {
     uint32_t pixel = (uint32_t)(py * P->W + px);
     float g1[4];
@@ -621,7 +623,7 @@ static v3 trace_path(const scene_t* S, const rparams_t* P, int px, int py, int s
     int env_on = S->env.x > 0.0f || S->env.y > 0.0f || S->env.z > 0.0f;
     int n_choices = S->n_lights + (env_on ? 1 : 0);
     float pick = n_choices > 0 ? 1.0f / (float)n_choices : 0.0f;
-    *alb = mk(0, 0, 0); *nrm = mk(0, 0, 0); *depth = 0.0f;
+    *alb = mk(0, 0, 0); *nrm = mk(0, 0, 0); *depth = 0.0f; *lobe = 0;
 
     for (int b = 0; b <= P->max_depth; ++b) {
         counts[b] += 1;
@@ -642,7 +644,7 @@ static v3 trace_path(const scene_t* S, const rparams_t* P, int px, int py, int s
         float cos_o = dot(d, ng);
         v3 ns = cos_o > 0.0f ? scl(ng, -1.0f) : ng;
         mat_t m = material(S, prim);
-        if (b == 0) { *alb = m.albedo; *nrm = ns; *depth = t; }
+        if (b == 0) { *alb = m.albedo; *nrm = ns; *depth = t; *lobe = m.type == 0 ? 1 : 2; }
         if ((m.Le.x > 0.0f || m.Le.y > 0.0f || m.Le.z > 0.0f) && cos_o < 0.0f) {
             float w = 1.0f;
             int li = S->tri_light[prim];
@@ -743,6 +745,7 @@ int orc_render(const float* V, int n, const int32_t* tri_mat, const int32_t* tri
                const float* cam, int W, int H, int spp, int max_depth, int rr_start,
                int grid, uint64_t seed, int row0, int row1, int threads,
                float* radiance, float* albedo, float* normal, float* depth,
+               float* diffuse, float* specular, float* variance,
                uint64_t* counts, uint64_t* shadow_counts)
 {
     if (W <= 0 || H <= 0 || spp <= 0 || max_depth < 0 || max_depth > 62) return -1;
@@ -770,11 +773,20 @@ int orc_render(const float* V, int n, const int32_t* tri_mat, const int32_t* tri
             for (int px = 0; px < W; ++px) {
                 float s0 = 0, s1 = 0, s2 = 0, c0 = 0, c1 = 0, c2 = 0;
                 v3 as = mk(0, 0, 0), ns = mk(0, 0, 0);
+                v3 dsum = mk(0, 0, 0), ssum = mk(0, 0, 0), q = mk(0, 0, 0);
                 float ds = 0;
                 for (int s = 0; s < spp; ++s) {
                     v3 a, nn;
                     float dd;
-                    v3 Ls = trace_path(&S, &P, px, py, s, &a, &nn, &dd, cnt, scnt);
+                    int lobe;
+                    v3 Ls = trace_path(&S, &P, px, py, s, &a, &nn, &dd, &lobe, cnt, scnt);
+                    /* extra layers (Sec. 4: diffuse, specular, variance) in
+                       sample order: the sample's radiance goes to the layer of
+                       its first hit's lobe; q sums squares for the variance */
+                    v3 zero = mk(0, 0, 0);
+                    dsum = add(dsum, lobe == 1 ? Ls : zero);
+                    ssum = add(ssum, lobe == 2 ? Ls : zero);
+                    q = add(q, mul(Ls, Ls));
                     /* Kahan: y = x - c; t = s + y; c = (t - s) - y; s = t */
                     float y, t;
                     y = Ls.x - c0; t = s0 + y; c0 = (t - s0) - y; s0 = t;
@@ -790,6 +802,22 @@ int orc_render(const float* V, int n, const int32_t* tri_mat, const int32_t* tri
                 if (albedo) { albedo[3 * i] = as.x / fs; albedo[3 * i + 1] = as.y / fs; albedo[3 * i + 2] = as.z / fs; }
                 if (normal) { normal[3 * i] = ns.x / fs; normal[3 * i + 1] = ns.y / fs; normal[3 * i + 2] = ns.z / fs; }
                 if (depth) depth[i] = ds / fs;
+                if (diffuse) { diffuse[3 * i] = dsum.x / fs; diffuse[3 * i + 1] = dsum.y / fs; diffuse[3 * i + 2] = dsum.z / fs; }
+                if (specular) { specular[3 * i] = ssum.x / fs; specular[3 * i + 1] = ssum.y / fs; specular[3 * i + 2] = ssum.z / fs; }
+                if (variance) {
+                    /* sample variance of the pixel mean, per channel:
+                       (sum L^2 - (sum L)^2 / N) / (N (N - 1)), 0 for N = 1,
+                       floored at 0 (rounding) */
+                    float m[3] = {s0, s1, s2}, qq[3] = {q.x, q.y, q.z};
+                    for (int c = 0; c < 3; ++c) {
+                        float v = 0.0f;
+                        if (spp > 1) {
+                            v = (qq[c] - m[c] * m[c] / fs) / (fs * (fs - 1.0f));
+                            if (!(v > 0.0f)) v = 0.0f;
+                        }
+                        variance[3 * i + c] = v;
+                    }
+                }
             }
         }
 #pragma omp critical

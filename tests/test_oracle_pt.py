@@ -136,3 +136,46 @@ def test_procedural_scene_size_and_value_range(orc):
     rad = r["radiance"]
     assert np.isfinite(rad).all() and (rad >= 0).all()
     assert (rad <= 10).mean() > 0.95    # linear HDR mostly in [0, 10] (Sec. 3.2)
+
+
+def test_extra_layers_decompose_radiance(orc):
+    # every sample's radiance goes to the layer of its first hit's lobe; the
+    # Cornell box is closed and black outside (every sample hits), with
+    # Lambertian walls and one GGX sphere
+    r = orc.render(scenes.cornell_box(sphere_subdiv=2), 16, 16, 8, 4, seed=1)
+    assert (r["specular"] > 0).any() and (r["diffuse"] > 0).any()
+    assert np.allclose(r["diffuse"] + r["specular"], r["radiance"], rtol=1e-5, atol=1e-7)
+    # a pixel's layers are either all-diffuse or contain the sphere's samples
+    only_d = ~r["specular"].any(axis=2)
+    assert np.allclose(r["diffuse"][only_d], r["radiance"][only_d], rtol=1e-5, atol=1e-7)
+    # the procedural scene mixes Lambertian and GGX spheres under an environment
+    # seen directly by some samples: the two layers never exceed the radiance
+    p = orc.render(scenes.procedural(0), 24, 24, 4, 4, rr_start=3, seed=2)
+    assert (p["specular"] > 0).any() and (p["diffuse"] > 0).any()
+    assert (p["diffuse"] + p["specular"] <= p["radiance"] * (1 + 1e-5) + 1e-6).all()
+
+
+def test_extra_layers_closed_forms(orc):
+    # diffuse plane under a uniform sky, cosine-sampled, one scattering event:
+    # every sample is rho * L_sky, so diffuse = 1.2 and the variance is 0
+    r = orc.render(scenes.sky_plane(0.6, 2.0), 16, 16, 8, 2, seed=3)
+    assert np.allclose(r["diffuse"], 1.2, rtol=2e-6) and not r["specular"].any()
+    assert (r["variance"] <= 1e-10).all()
+    # white furnace without roulette: zero-variance estimator too
+    f = orc.render(scenes.furnace_sphere(1.5, 0.6), 8, 8, 16, 5, seed=4)
+    assert (f["variance"] <= 1e-6 * f["radiance"] ** 2).all()
+    # one sample per pixel has no sample variance
+    assert not orc.render(scenes.cornell_box(sphere_subdiv=1), 8, 8, 1, 3)["variance"].any()
+
+
+def test_variance_layer_matches_spread_of_independent_renders(orc):
+    # the layer estimates the variance of the pixel mean: its average over
+    # pixels matches the variance of the pixel values across independent
+    # renders (different seeds) at the same spp
+    sc = scenes.cornell_box(sphere_subdiv=2)
+    runs = [orc.render(sc, 8, 8, 16, 3, seed=100 + k) for k in range(96)]
+    rad = np.stack([r["radiance"] for r in runs]).astype(np.float64)
+    emp = rad.var(axis=0, ddof=1)
+    est = np.stack([r["variance"] for r in runs]).astype(np.float64).mean(axis=0)
+    ratio = est.sum() / emp.sum()
+    assert 0.85 < ratio < 1.15, ratio
