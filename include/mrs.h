@@ -218,6 +218,33 @@ mrs_status mrs_render_grid(mrs_ctx ctx, mrs_scene scene, int32_t W, int32_t H, i
                            float* radiance, float* albedo, float* normal, float* depth,
                            uint64_t* counts, uint64_t* shadow_counts, void* stream);
 
+/* Every output of a render, including the extra HRLS layers of Sec. 4
+ * (device pointers, all [H][W][3] float except depth [H][W] and the
+ * uint64[max_depth + 1] ray counts; only radiance is required, NULL skips a
+ * layer):
+ *   diffuse / specular: mean over samples of the radiance of the samples whose
+ *     first hit is Lambertian / GGX (samples that see the environment
+ *     directly count in neither: radiance = diffuse + specular + that part);
+ *   variance: per channel, the sample variance of the pixel mean,
+ *     (sum L^2 - (sum L)^2 / N) / (N (N - 1)) with the compensated sum of L,
+ *     0 when N = 1, floored at 0. */
+typedef struct {
+    float* radiance;
+    float* albedo;
+    float* normal;
+    float* depth;
+    float* diffuse;
+    float* specular;
+    float* variance;
+    uint64_t* counts;
+    uint64_t* shadow_counts;
+} mrs_render_out;
+/* mrs_render_grid with all outputs; the extra layers cost a per-path lobe
+ * record and a second per-pixel accumulator, only when requested. */
+mrs_status mrs_render_layers(mrs_ctx ctx, mrs_scene scene, int32_t W, int32_t H, int32_t spp,
+                             int32_t max_depth, int32_t rr_start, uint64_t seed, int32_t grid,
+                             const mrs_render_out* out, void* stream);
+
 /* Paths per wave for subsequent mrs_render calls on this scene (rounded to
  * whole samples of the image; default 16M paths).  For tests and tuning. */
 mrs_status mrs_scene_set_wave(mrs_scene scene, int64_t max_paths_per_wave);

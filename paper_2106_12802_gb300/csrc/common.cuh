@@ -146,6 +146,7 @@ struct PathSoA {
     float *sdx, *sdy, *sdz, *stmax;       // shadow ray direction and extent
     float *scx, *scy, *scz;               // unoccluded shadow contribution
     float *ax, *ay, *az, *nx, *ny, *nz, *dep;   // first-hit aux
+    int* lobe;                            // first-hit lobe (1 Lambertian, 2 GGX, 0 none); layers only
     int *q0, *q1, *qs;                    // queues (cur / next / shadow)
 };
 }  // namespace mrs

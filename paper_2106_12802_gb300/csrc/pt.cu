@@ -318,6 +318,7 @@ struct WaveParams {
     float cam[12];
     int W, H, max_depth, rr_start;
     int grid;            // camera sampling grid (1 = whole pixel footprint)
+    int layers;          // record the first-hit lobe (diffuse / specular / variance layers)
     int64_t wh;          // pixels
     int s0;              // first sample index of the wave
     int n_paths;         // paths in the wave (= k * wh)
@@ -354,6 +355,7 @@ __global__ void __launch_bounds__(kThreads) k_raygen(WaveParams w)
         P.pdf_b[p] = 0.0f; P.pdf_e[p] = 0.0f;
         P.ax[p] = 0.0f; P.ay[p] = 0.0f; P.az[p] = 0.0f;
         P.nx[p] = 0.0f; P.ny[p] = 0.0f; P.nz[p] = 0.0f; P.dep[p] = 0.0f;
+        if (w.layers) P.lobe[p] = 0;
     }
 }
 
@@ -434,6 +436,7 @@ __global__ void __launch_bounds__(kThreads) k_shade(WaveParams w, int b)
                 if (b == 0) {
                     P.ax[p] = m.albedo.x; P.ay[p] = m.albedo.y; P.az[p] = m.albedo.z;
                     P.nx[p] = ns.x; P.ny[p] = ns.y; P.nz[p] = ns.z; P.dep[p] = t;
+                    if (w.layers) P.lobe[p] = m.type == 0 ? 1 : 2;
                 }
                 if ((m.Le.x > 0.0f || m.Le.y > 0.0f || m.Le.z > 0.0f) && cos_o < 0.0f) {
                     float wgt = 1.0f;
@@ -583,6 +586,33 @@ __global__ void __launch_bounds__(kThreads) k_accumulate(WaveParams w, float* ac
     }
 }
 
+// extra layers, only when requested: per pixel the diffuse and specular sums
+// (each sample's radiance to the layer of its first-hit lobe) and the sum of
+// squares for the variance, plain FP32 sums in sample order
+__global__ void __launch_bounds__(kThreads) k_accumulate_layers(WaveParams w, float* acc2, int k)
+{
+    PathSoA& P = w.P;
+    int64_t wh = w.wh;
+    for (int64_t pix = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; pix < wh;
+         pix += (int64_t)gridDim.x * blockDim.x) {
+        float* e = acc2 + 9 * pix;
+        float d0 = e[0], d1 = e[1], d2 = e[2], p0 = e[3], p1 = e[4], p2 = e[5];
+        float q0 = e[6], q1 = e[7], q2 = e[8];
+        for (int s = 0; s < k; ++s) {
+            int64_t p = s * wh + pix;
+            const float lx = P.Lx[p], ly = P.Ly[p], lz = P.Lz[p];
+            const int lobe = P.lobe[p];
+            d0 = d0 + (lobe == 1 ? lx : 0.0f); d1 = d1 + (lobe == 1 ? ly : 0.0f);
+            d2 = d2 + (lobe == 1 ? lz : 0.0f);
+            p0 = p0 + (lobe == 2 ? lx : 0.0f); p1 = p1 + (lobe == 2 ? ly : 0.0f);
+            p2 = p2 + (lobe == 2 ? lz : 0.0f);
+            q0 = q0 + lx * lx; q1 = q1 + ly * ly; q2 = q2 + lz * lz;
+        }
+        e[0] = d0; e[1] = d1; e[2] = d2; e[3] = p0; e[4] = p1; e[5] = p2;
+        e[6] = q0; e[7] = q1; e[8] = q2;
+    }
+}
+
 __global__ void k_counts(const uint32_t* cnt, const uint32_t* scnt, int nb, uint64_t* counts,
                          uint64_t* shadow_counts)
 {
@@ -592,8 +622,9 @@ __global__ void k_counts(const uint32_t* cnt, const uint32_t* scnt, int nb, uint
     if (shadow_counts) shadow_counts[b] += scnt[b];
 }
 
-__global__ void k_resolve(const float* __restrict__ acc, int64_t wh, int spp, float* radiance,
-                          float* albedo, float* normal, float* depth)
+__global__ void k_resolve(const float* __restrict__ acc, const float* __restrict__ acc2, int64_t wh,
+                          int spp, float* radiance, float* albedo, float* normal, float* depth,
+                          float* diffuse, float* specular, float* variance)
 {
     float fs = (float)spp;
     for (int64_t pix = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; pix < wh;
@@ -603,6 +634,21 @@ __global__ void k_resolve(const float* __restrict__ acc, int64_t wh, int spp, fl
         if (albedo) { albedo[3 * pix] = a[6] / fs; albedo[3 * pix + 1] = a[7] / fs; albedo[3 * pix + 2] = a[8] / fs; }
         if (normal) { normal[3 * pix] = a[9] / fs; normal[3 * pix + 1] = a[10] / fs; normal[3 * pix + 2] = a[11] / fs; }
         if (depth) depth[pix] = a[12] / fs;
+        if (!acc2) continue;
+        const float* e = acc2 + 9 * pix;
+        if (diffuse) for (int c = 0; c < 3; ++c) diffuse[3 * pix + c] = e[c] / fs;
+        if (specular) for (int c = 0; c < 3; ++c) specular[3 * pix + c] = e[3 + c] / fs;
+        if (variance) {
+            // sample variance of the pixel mean: (sum L^2 - (sum L)^2 / N) / (N (N - 1))
+            for (int c = 0; c < 3; ++c) {
+                float v = 0.0f;
+                if (spp > 1) {
+                    v = (e[6 + c] - a[c] * a[c] / fs) / (fs * (fs - 1.0f));
+                    if (!(v > 0.0f)) v = 0.0f;
+                }
+                variance[3 * pix + c] = v;
+            }
+        }
     }
 }
 
@@ -656,6 +702,7 @@ static mrs_status render_impl(mrs_scene S, Buf& arena, int64_t wave_paths, int32
                               int32_t spp, int32_t max_depth, int32_t rr_start, uint64_t seed,
                               int32_t grid,
                               float* radiance, float* albedo, float* normal, float* depth,
+                              float* diffuse, float* specular, float* variance,
                               uint64_t* counts, uint64_t* shadow_counts,
                               unsigned long long* stats, void* stream)
 {
@@ -674,10 +721,14 @@ static mrs_status render_impl(mrs_scene S, Buf& arena, int64_t wave_paths, int32
     MRS_ARG(k * wh <= (int64_t(1) << 31) - 1, "wave too large");
     const int64_t P = k * wh;
     const int nb = max_depth + 1;
-    // arena: 30 float/int arrays of P + accum 13 * wh + counters
-    const int kArrays = 33;
+    // arena: 34 float / int arrays of P paths, accumulator 13 * wh, counters,
+    // then (extra layers only) accumulator 9 * wh
+    const int kArrays = 34;
+    const bool layers = diffuse || specular || variance;
     size_t arr = ((size_t)P * 4 + 255) & ~(size_t)255;
-    size_t need = arr * kArrays + (size_t)wh * 13 * 4 + 256 + 4 * 2 * 64;
+    size_t off_cnt = arr * kArrays + (size_t)wh * 13 * 4 + 256;
+    size_t off_acc2 = off_cnt + 4 * 2 * 64;
+    size_t need = off_acc2 + (layers ? (size_t)wh * 9 * 4 : 0);
     mrs_status s = arena.ensure(need);
     if (s != MRS_OK) return s;
     char* base = arena.as<char>();
@@ -694,9 +745,11 @@ static mrs_status render_impl(mrs_scene S, Buf& arena, int64_t wave_paths, int32
     soa.q0 = (int*)f[fi++];
     soa.q1 = (int*)f[fi++];
     soa.qs = (int*)f[fi++];
+    soa.lobe = (int*)f[fi++];
     float* acc = (float*)(base + arr * kArrays);
-    uint32_t* cnt = (uint32_t*)(base + arr * kArrays + (size_t)wh * 13 * 4 + 256);
+    uint32_t* cnt = (uint32_t*)(base + off_cnt);
     uint32_t* scnt = cnt + 64;
+    float* acc2 = layers ? (float*)(base + off_acc2) : nullptr;
 
     WaveParams w;
     w.S = view(S);
@@ -705,6 +758,7 @@ static mrs_status render_impl(mrs_scene S, Buf& arena, int64_t wave_paths, int32
     memcpy(w.cam, S->cam, sizeof(w.cam));
     w.W = W; w.H = H; w.max_depth = max_depth;
     w.grid = grid;
+    w.layers = layers ? 1 : 0;
     w.rr_start = rr_start < 0 ? 0x7fffffff : rr_start;
     w.wh = wh;
     w.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
@@ -713,6 +767,7 @@ static mrs_status render_impl(mrs_scene S, Buf& arena, int64_t wave_paths, int32
     w.stats = stats;
 
     MRS_CHECK(cudaMemsetAsync(acc, 0, (size_t)wh * 13 * 4, st));
+    if (acc2) MRS_CHECK(cudaMemsetAsync(acc2, 0, (size_t)wh * 9 * 4, st));
     if (counts) MRS_CHECK(cudaMemsetAsync(counts, 0, sizeof(uint64_t) * nb, st));
     if (shadow_counts) MRS_CHECK(cudaMemsetAsync(shadow_counts, 0, sizeof(uint64_t) * nb, st));
     for (int s0 = 0; s0 < spp; s0 += (int)k) {
@@ -735,12 +790,17 @@ static mrs_status render_impl(mrs_scene S, Buf& arena, int64_t wave_paths, int32
         }
         MRS_TIMED(PK_ACCUM, st, k_accumulate<<<grid_for(wh), kThreads, 0, st>>>(w, acc, kk));
         MRS_LAUNCHED(1);
+        if (acc2) {
+            MRS_TIMED(PK_ACCUM, st, k_accumulate_layers<<<grid_for(wh), kThreads, 0, st>>>(w, acc2, kk));
+            MRS_LAUNCHED(1);
+        }
         if (counts || shadow_counts) {
             k_counts<<<1, 64, 0, st>>>(cnt, scnt, nb, counts, shadow_counts);
             MRS_LAUNCHED(1);
         }
     }
-    k_resolve<<<grid_for(wh), kThreads, 0, st>>>(acc, wh, spp, radiance, albedo, normal, depth);
+    k_resolve<<<grid_for(wh), kThreads, 0, st>>>(acc, acc2, wh, spp, radiance, albedo, normal, depth,
+                                                 diffuse, specular, variance);
     MRS_LAUNCHED(1);
     return cuda_status(cudaGetLastError(), "render launch");
 }
@@ -752,7 +812,8 @@ extern "C" mrs_status mrs_render(mrs_scene S, int32_t W, int32_t H, int32_t spp,
 {
     MRS_ARG(S != nullptr, "scene is NULL");
     return render_impl(S, S->arena, S->wave_paths, W, H, spp, max_depth, rr_start, seed, 1, radiance,
-                       albedo, normal, depth, counts, shadow_counts, nullptr, stream);
+                       albedo, normal, depth, nullptr, nullptr, nullptr, counts, shadow_counts,
+                       nullptr, stream);
 }
 
 extern "C" mrs_status mrs_ctx_create(mrs_ctx* out)
@@ -787,7 +848,8 @@ extern "C" mrs_status mrs_render_ctx(mrs_ctx ctx, mrs_scene S, int32_t W, int32_
     MRS_ARG(ctx != nullptr, "ctx is NULL");
     MRS_ARG(S != nullptr, "scene is NULL");
     return render_impl(S, ctx->arena, ctx->wave_paths, W, H, spp, max_depth, rr_start, seed, 1,
-                       radiance, albedo, normal, depth, counts, shadow_counts, nullptr, stream);
+                       radiance, albedo, normal, depth, nullptr, nullptr, nullptr, counts,
+                       shadow_counts, nullptr, stream);
 }
 
 extern "C" mrs_status mrs_render_grid(mrs_ctx ctx, mrs_scene S, int32_t W, int32_t H, int32_t spp,
@@ -800,7 +862,21 @@ extern "C" mrs_status mrs_render_grid(mrs_ctx ctx, mrs_scene S, int32_t W, int32
     Buf& arena = ctx ? ctx->arena : S->arena;
     int64_t wave = ctx ? ctx->wave_paths : S->wave_paths;
     return render_impl(S, arena, wave, W, H, spp, max_depth, rr_start, seed, grid, radiance, albedo,
-                       normal, depth, counts, shadow_counts, nullptr, stream);
+                       normal, depth, nullptr, nullptr, nullptr, counts, shadow_counts, nullptr,
+                       stream);
+}
+
+extern "C" mrs_status mrs_render_layers(mrs_ctx ctx, mrs_scene S, int32_t W, int32_t H, int32_t spp,
+                                        int32_t max_depth, int32_t rr_start, uint64_t seed,
+                                        int32_t grid, const mrs_render_out* out, void* stream)
+{
+    MRS_ARG(S != nullptr, "scene is NULL");
+    MRS_ARG(out != nullptr, "out is NULL");
+    Buf& arena = ctx ? ctx->arena : S->arena;
+    int64_t wave = ctx ? ctx->wave_paths : S->wave_paths;
+    return render_impl(S, arena, wave, W, H, spp, max_depth, rr_start, seed, grid, out->radiance,
+                       out->albedo, out->normal, out->depth, out->diffuse, out->specular,
+                       out->variance, out->counts, out->shadow_counts, nullptr, stream);
 }
 
 extern "C" mrs_status mrs_render_stats(mrs_scene S, int32_t W, int32_t H, int32_t spp,
@@ -811,7 +887,8 @@ extern "C" mrs_status mrs_render_stats(mrs_scene S, int32_t W, int32_t H, int32_
     MRS_ARG(stats != nullptr, "stats is NULL");
     MRS_CHECK(cudaMemsetAsync(stats, 0, 4 * sizeof(uint64_t), (cudaStream_t)stream));
     return render_impl(S, S->arena, S->wave_paths, W, H, spp, max_depth, rr_start, seed, 1, radiance,
-                       nullptr, nullptr, nullptr, nullptr, nullptr, (unsigned long long*)stats, stream);
+                       nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                       (unsigned long long*)stats, stream);
 }
 
 extern "C" mrs_status mrs_cast(mrs_scene S, const float* orig, const float* dir, int32_t n,

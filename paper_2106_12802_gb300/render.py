@@ -133,12 +133,19 @@ class RenderContext:
             pass
 
 
+class _RenderOut(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_void_p) for k in ("radiance", "albedo", "normal", "depth", "diffuse",
+                                               "specular", "variance", "counts", "shadow_counts")]
+
+
 def render(scene: Scene, W, H, spp, max_depth, rr_start=None, seed=0, aux=True, counts=True,
-           out=None, stream=None, ctx: RenderContext | None = None, grid=1):
+           out=None, stream=None, ctx: RenderContext | None = None, grid=1, layers=False):
     """mrs_render (or mrs_render_ctx when ctx is given) into device tensors;
     returns dict of (device) tensors.  grid > 1 renders on the sparse
     camera-sampling grid (mrs_render_grid): each pixel samples only the centre
-    sub-pixel of its grid x grid block, the paper's nearest-neighbour LR."""
+    sub-pixel of its grid x grid block, the paper's nearest-neighbour LR.
+    layers=True also returns the extra HRLS layers diffuse, specular and
+    variance (mrs_render_layers)."""
     dev = torch.device("cuda")
     if out is None:
         out = {"radiance": torch.empty((H, W, 3), dtype=torch.float32, device=dev)}
@@ -149,12 +156,19 @@ def render(scene: Scene, W, H, spp, max_depth, rr_start=None, seed=0, aux=True, 
         if counts:
             out["counts"] = torch.zeros(max_depth + 1, dtype=torch.int64, device=dev)
             out["shadow_counts"] = torch.zeros(max_depth + 1, dtype=torch.int64, device=dev)
+        if layers:
+            for k in ("diffuse", "specular", "variance"):
+                out[k] = torch.empty((H, W, 3), dtype=torch.float32, device=dev)
     bufs = (_ptr(out["radiance"]), _ptr(out.get("albedo")), _ptr(out.get("normal")),
             _ptr(out.get("depth")), _ptr(out.get("counts")), _ptr(out.get("shadow_counts")),
             _stream(stream))
     head = (W, H, spp, max_depth, -1 if rr_start is None else rr_start, int(seed) & 0xFFFFFFFFFFFFFFFF)
     args = head + bufs
-    if grid != 1:
+    if any(k in out for k in ("diffuse", "specular", "variance")):
+        ro = _RenderOut(*[_ptr(out.get(k)) for k, _ in _RenderOut._fields_])
+        call("mrs_render_layers", ctx.handle if ctx is not None else None, scene.handle, *head,
+             int(grid), ctypes.byref(ro), _stream(stream))
+    elif grid != 1:
         call("mrs_render_grid", ctx.handle if ctx is not None else None, scene.handle, *head,
              int(grid), *bufs)
     elif ctx is None:

@@ -155,6 +155,41 @@ def test_render_sparse_grid_matches_oracle(mrs, orc):
             mrs.render(sc, 8, 8, 1, 2, grid=bad)
 
 
+@pytest.mark.parametrize("case", ["cornell", "procedural_ragged", "procedural_grid"])
+def test_render_extra_layers_match_oracle(mrs, orc, case):
+    # diffuse / specular / variance layers (Sec. 4) with the same parity bar as
+    # the radiance; requesting them leaves every other output bit-identical
+    desc, W, H, spp, D, rr, seed, grid, wave = {
+        "cornell": (scenes.cornell_box(sphere_subdiv=2), 32, 24, 8, 4, None, 1, 1, None),
+        "procedural_ragged": (scenes.procedural(0), 40, 32, 6, 8, 3, 2, 1, 40 * 32 * 4),
+        "procedural_grid": (scenes.procedural(0), 24, 24, 4, 8, 3, 5, 4, None),
+    }[case]
+    sc = mrs.Scene(desc)
+    if wave:
+        sc.set_wave(wave)
+    g = mrs.render(sc, W, H, spp, D, rr_start=rr, seed=seed, grid=grid, layers=True)
+    plain = mrs.render(sc, W, H, spp, D, rr_start=rr, seed=seed, grid=grid)
+    torch.cuda.synchronize()
+    g = {k: v.cpu().numpy() for k, v in g.items()}
+    plain = {k: v.cpu().numpy() for k, v in plain.items()}
+    for k in plain:
+        assert np.array_equal(g[k], plain[k]), k
+    r = orc.render(desc, W, H, spp, D, rr_start=rr, seed=seed, grid=grid)
+    assert np.array_equal(g["counts"].astype(np.uint64), r["counts"])
+    for k in ("radiance", "diffuse", "specular", "variance"):
+        assert_radiance_parity(g[k], r[k])
+    assert (g["diffuse"] + g["specular"] <= g["radiance"] * (1 + 1e-5) + 1e-6).all()
+
+
+def test_render_extra_layers_closed_form(mrs):
+    # diffuse plane under a uniform sky: diffuse = rho * L_sky, no specular,
+    # zero variance (every sample is the same value)
+    sc = mrs.Scene(scenes.sky_plane(0.6, 2.0))
+    g = mrs.render(sc, 16, 16, 8, 2, seed=3, layers=True)
+    assert np.allclose(g["diffuse"].cpu().numpy(), 1.2, rtol=2e-6)
+    assert not g["specular"].any().item() and (g["variance"] <= 1e-10).all().item()
+
+
 def test_render_full_size_sampled_rows(mrs, orc):
     # the 1024 x 1024, 64 spp, depth 8 (roulette from bounce 3) configuration on
     # the 200k-triangle procedural scene, in the launch configuration the bench
