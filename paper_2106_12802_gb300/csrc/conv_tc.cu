@@ -231,16 +231,22 @@ __device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// job -> (column block, image, rows [y0, y1)): a job is `rows_per_job`
-// consecutive output rows of one 128-pixel column strip of one image
-__device__ __forceinline__ void job_rows(int job, int XB, int segs, int rows_per_job, int H,
-                                         int& xb, int& n, int& y0, int& y1)
+// Work split: the layer is T = N * XB * H tiles (one tile = one output row of
+// one 120-pixel column strip), flattened as f = (n * XB + xb) * H + y.  CTA c
+// takes the contiguous run [T c / G, T (c + 1) / G), cut at strip boundaries
+// into pieces; a piece is a run of rows of one strip, streamed through the
+// input-row ring with its own halo rows.  piece_rows returns the piece that
+// starts at f (< f1) and advances f past it.
+__device__ __forceinline__ void piece_rows(long long& f, long long f1, int XB, int H, int& xb,
+                                           int& n, int& y0, int& y1)
 {
-    int seg = job % segs, rest = job / segs;
-    xb = rest % XB;
-    n = rest / XB;
-    y0 = seg * rows_per_job;
-    y1 = min(H, y0 + rows_per_job);
+    const long long k = f / H;
+    y0 = (int)(f - k * H);
+    const long long left = f1 - f;
+    y1 = (int)((long long)y0 + left < (long long)H ? (long long)y0 + left : (long long)H);
+    xb = (int)(k % XB);
+    n = (int)(k / XB);
+    f += y1 - y0;
 }
 
 // byte offset of 16-byte chunk j of row m in a SWIZZLE_128B tile
@@ -284,7 +290,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int XB = (a.W + kTileOut - 1) / kTileOut;
-    const int njobs = a.N * XB * a.segs;
+    const long long T = (long long)a.N * XB * a.H;
+    const long long f0 = T * blockIdx.x / gridDim.x, f1 = T * (blockIdx.x + 1) / gridDim.x;
     const bool bf_out = a.mode == TC_RELU_BF16 || a.mode == TC_RESID_BF16 ||
                         a.mode == TC_LIN_BF16 || a.mode == TC_MASK_BF16;
     const bool loads_res = a.mode == TC_RESID_BF16 || a.mode == TC_MASK_BF16;
@@ -323,9 +330,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int t = 0; t < 9; ++t) tma_load_2d(sW + t * NOUT * ROWB, &tmap_w, 0, t * NOUT, wbar);
             uint32_t it = 0;
             bool ok = true;
-            for (int job = blockIdx.x; ok && job < njobs; job += gridDim.x) {
+            for (long long f = f0; ok && f < f1;) {
                 int xb, n, y0, y1;
-                job_rows(job, XB, a.segs, a.rows_per_job, a.H, xb, n, y0, y1);
+                piece_rows(f, f1, XB, a.H, xb, n, y0, y1);
                 for (int r = y0 - 1; r <= y1; ++r, ++it) {
                     int s = it % stages;
                     if (!mbar_wait(&empty[s], ((it / stages) & 1) ^ 1, a.err)) { ok = false; break; }
@@ -342,9 +349,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) {
             uint32_t j = 0;
             bool ok = true;
-            for (int job = blockIdx.x; ok && job < njobs; job += gridDim.x) {
+            for (long long f = f0; ok && f < f1;) {
                 int xb, n, y0, y1;
-                job_rows(job, XB, a.segs, a.rows_per_job, a.H, xb, n, y0, y1);
+                piece_rows(f, f1, XB, a.H, xb, n, y0, y1);
                 for (int y = y0; y < y1; ++y, ++j) {
                     uint32_t slot = j % kSlots, use = j / kSlots;
                     if (!mbar_wait(&rempty[slot], (use & 1) ^ 1, a.err)) { ok = false; break; }
@@ -363,9 +370,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) {
             uint32_t j = 0;
             bool ok = true;
-            for (int job = blockIdx.x; ok && job < njobs; job += gridDim.x) {
+            for (long long f = f0; ok && f < f1;) {
                 int xb, n, y0, y1;
-                job_rows(job, XB, a.segs, a.rows_per_job, a.H, xb, n, y0, y1);
+                piece_rows(f, f1, XB, a.H, xb, n, y0, y1);
                 for (int y = y0; y < y1; ++y, ++j) {
                     uint32_t slot = j % kSlots, use = j / kSlots;
                     if (!mbar_wait(&edone[slot], use & 1, a.err)) { ok = false; break; }
@@ -386,9 +393,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             bool ok = mbar_wait(wbar, 0, a.err);
             uint32_t it = 0, lt = 0;
             const uint32_t wbase = smem_u32(sW), abase = smem_u32(sA);
-            for (int job = blockIdx.x; ok && job < njobs; job += gridDim.x) {
+            for (long long f = f0; ok && f < f1;) {
                 int xb, n, y0, y1;
-                job_rows(job, XB, a.segs, a.rows_per_job, a.H, xb, n, y0, y1);
+                piece_rows(f, f1, XB, a.H, xb, n, y0, y1);
                 const uint32_t base = it;
                 for (int y = y0; ok && y < y1; ++y, ++lt) {
                     uint32_t acc = lt & 1, use = lt >> 1;
@@ -407,9 +414,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                             if (OPER == TC_BF16) mma_f16(d, ad, bd, IDESC, (dy | k) != 0);
                             else mma_f8(d, ad, bd, IDESC, (dy | k) != 0);
                         }
+                        // row y-1 (kernel row 0) has no later use: its slot is
+                        // handed back as soon as these MMAs complete
+                        if (dy == 0) mma_commit(&empty[s]);
                     }
                     if (!ok) break;
-                    mma_commit(&empty[(base + (y - y0)) % stages]);   // row y-1 is done
                     mma_commit(&tfull[acc]);
                 }
                 if (ok) {
@@ -432,9 +441,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         const bool active = half * kEpiCh < NOUT;
         uint32_t lt = 0;
         bool stop = false;
-        for (int job = blockIdx.x; !stop && job < njobs; job += gridDim.x) {
+        for (long long f = f0; !stop && f < f1;) {
           int xb, n, y0, y1;
-          job_rows(job, XB, a.segs, a.rows_per_job, a.H, xb, n, y0, y1);
+          piece_rows(f, f1, XB, a.H, xb, n, y0, y1);
           for (int y = y0; y < y1; ++y, ++lt) {
             uint32_t acc = lt & 1, use = lt >> 1;
             uint32_t slot = lt % kSlots, suse = lt / kSlots;
@@ -592,18 +601,10 @@ mrs_status launch(const TcConvArgs& a, cudaStream_t st)
         if (e != cudaSuccess) return cuda_status(e, "conv smem attribute");
         attr = true;
     }
-    // jobs: each column strip of each image is cut into `segs` runs of rows so
-    // that there are at most as many jobs as SMs (whole strips when the image
-    // set already has more strips than SMs)
+    // one CTA per SM, each with an equal contiguous share of the tiles
     TcConvArgs b = a;
-    int strips = a.N * ((a.W + kTileOut - 1) / kTileOut);
-    int segs = sm_count() / strips;
-    if (segs < 1) segs = 1;
-    if (segs > a.H) segs = a.H;
-    b.rows_per_job = (a.H + segs - 1) / segs;
-    b.segs = (a.H + b.rows_per_job - 1) / b.rows_per_job;
-    int njobs = strips * b.segs;
-    int grid = njobs < sm_count() ? njobs : sm_count();
+    const long long T = (long long)a.N * ((a.W + kTileOut - 1) / kTileOut) * a.H;
+    int grid = T < sm_count() ? (int)T : sm_count();
     if (grid < 1) return MRS_OK;
     const CUtensorMap* res = a.tmap_res ? a.tmap_res : a.tmap_x;
     const CUtensorMap* out = a.tmap_out ? a.tmap_out : a.tmap_x;

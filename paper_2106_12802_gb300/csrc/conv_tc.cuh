@@ -40,7 +40,6 @@ struct TcConvArgs {
     int mode;
     int operand;                 // TC_BF16 / TC_FP8
     int* err;                    // device error word (timeouts)
-    int segs, rows_per_job;      // row runs per column strip (set by the launcher)
     // TC_RELU_BF16 / TC_RESID_BF16 with fp8 operands: also emit the fp8 copy
     void* out_fp8;
     float out_fp8_inv_scale;
