@@ -25,27 +25,49 @@ from __future__ import annotations
 import numpy as np
 
 C_IN = 12
+C_EXTRA = 9          # diffuse, specular, log(1 + variance) of the HRLS (Sec. 4)
 C_F = 64
 N_BLOCKS = 8
-LAYERS = [(C_IN, C_F)] + [(C_F, C_F)] * (2 * N_BLOCKS) + [(C_F, 3)]
 
 
-def layer_offsets():
+def layers_for(c_in=C_IN):
+    return [(c_in, C_F)] + [(C_F, C_F)] * (2 * N_BLOCKS) + [(C_F, 3)]
+
+
+LAYERS = layers_for(C_IN)
+
+
+def layer_offsets(c_in=C_IN):
     """[(w_off, b_off, cin, cout)] into the flat parameter array."""
     offs, o = [], 0
-    for cin, cout in LAYERS:
+    for cin, cout in layers_for(c_in):
         offs.append((o, o + cout * 9 * cin, cin, cout))
         o += cout * 9 * cin + cout
     return offs
 
 
-NPARAMS = sum(co * 9 * ci + co for ci, co in LAYERS)
+def nparams(c_in=C_IN):
+    return sum(co * 9 * ci + co for ci, co in layers_for(c_in))
+
+
+NPARAMS = nparams(C_IN)
+NPARAMS_EXTRA = nparams(C_IN + C_EXTRA)
+
+
+def input_channels(params):
+    """12 (base input) or 21 (with the extra HRLS layers), from the size."""
+    n = len(params)
+    if n == NPARAMS:
+        return C_IN
+    if n == NPARAMS_EXTRA:
+        return C_IN + C_EXTRA
+    raise ValueError(f"{n} parameters: expected {NPARAMS} or {NPARAMS_EXTRA}")
 
 
 def unpack(params):
     p = np.asarray(params, dtype=np.float64)
     out = []
-    for wo, bo, ci, co in layer_offsets():
+    for wo, bo, ci, co in layer_offsets(input_channels(p)):
         out.append((p[wo:bo].reshape(co, 3, 3, ci), p[bo:bo + co]))
     return out
 
@@ -105,15 +127,29 @@ def bilinear_up(x, s):
     return top * (1 - ly) + bot * ly
 
 
-def fusion_input(lrhs, hrls, albedo, normal, s):
+def extra_input(extra):
+    """The extra HRLS layers as network input channels: extra [N,H,W,9] =
+    diffuse, specular, variance as rendered -> diffuse, specular,
+    log(1 + variance) (the variance spans orders of magnitude)."""
+    e = np.asarray(extra, dtype=np.float64)
+    return np.concatenate([e[..., :6], np.log1p(np.maximum(e[..., 6:9], 0.0))], axis=-1)
+
+
+def fusion_input(lrhs, hrls, albedo, normal, s, extra=None):
+    """Network input: up(LRHS), HRLS, albedo, normal (12 channels), then the
+    extra layers (9 more) when given."""
     up = bilinear_up(lrhs, s)
-    return np.concatenate([up, hrls, albedo, normal], axis=-1).astype(np.float64), up
+    parts = [up, hrls, albedo, normal] + ([extra_input(extra)] if extra is not None else [])
+    return np.concatenate(parts, axis=-1).astype(np.float64), up
 
 
-def forward(params, lrhs, hrls, albedo, normal, s, keep=False):
-    """I_SR for batched NHWC inputs (LRHS [N,h,w,3]; the rest [N,s*h,s*w,3])."""
+def forward(params, lrhs, hrls, albedo, normal, s, keep=False, extra=None):
+    """I_SR for batched NHWC inputs (LRHS [N,h,w,3]; the rest [N,s*h,s*w,3];
+    extra [N,s*h,s*w,9] for a network with the extra-layer input)."""
     L = unpack(params)
-    x0, up = fusion_input(lrhs, hrls, albedo, normal, s)
+    if (extra is not None) != (L[0][0].shape[3] == C_IN + C_EXTRA):
+        raise ValueError("extra layers must be given exactly for a 21-channel network")
+    x0, up = fusion_input(lrhs, hrls, albedo, normal, s, extra)
     acts = {"x0": x0}
     a = conv3x3(x0, *L[0])
     acts["pre0"] = a
@@ -197,8 +233,9 @@ def backward(params, acts, dy):
     return pack(grads)
 
 
-def loss_and_grad(params, lrhs, hrls, albedo, normal, target, s, loss="l1log", beta=0.1):
-    y, acts = forward(params, lrhs, hrls, albedo, normal, s, keep=True)
+def loss_and_grad(params, lrhs, hrls, albedo, normal, target, s, loss="l1log", beta=0.1,
+                  extra=None):
+    y, acts = forward(params, lrhs, hrls, albedo, normal, s, keep=True, extra=extra)
     value, dy = loss_fn(y, target, loss, beta)
     return value, backward(params, acts, dy)
 
@@ -213,24 +250,29 @@ def adam(params, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
 
 
 def train_step(params, m, v, step, lr, lrhs, hrls, albedo, normal, target, s, clip=100.0,
-               loss="l1log", beta=0.1):
+               loss="l1log", beta=0.1, extra=None):
     """One training step as the method's learned part runs it: radiance inputs
     and target clipped at `clip` (firefly clipping, Sec. 3.2), the loss
     ("l1log", or "robust" = l_r with factor `beta`, Sec. 3), backward,
-    bias-corrected Adam at step `step` (counting from 1).
+    bias-corrected Adam at step `step` (counting from 1).  The extra layers'
+    diffuse and specular radiance are clipped like the HRLS.
     Returns (new params, m, v, loss, grad)."""
     lr_c = np.minimum(np.asarray(lrhs, np.float64), clip)
     hr_c = np.minimum(np.asarray(hrls, np.float64), clip)
     tg_c = np.minimum(np.asarray(target, np.float64), clip)
-    value, grad = loss_and_grad(params, lr_c, hr_c, albedo, normal, tg_c, s, loss, beta)
+    ex_c = None
+    if extra is not None:
+        ex_c = np.asarray(extra, np.float64).copy()
+        ex_c[..., :6] = np.minimum(ex_c[..., :6], clip)
+    value, grad = loss_and_grad(params, lr_c, hr_c, albedo, normal, tg_c, s, loss, beta, ex_c)
     p1, m1, v1 = adam(params, grad, m, v, step, lr)
     return p1, m1, v1, value, grad
 
 
-def kaiming(seed: int):
+def kaiming(seed: int, c_in: int = C_IN):
     """Kaiming-normal weights (std sqrt(2 / (9 Cin))), zero biases."""
     rng = np.random.default_rng(np.random.SeedSequence([0x6B61696D, int(seed)]))
     layers = []
-    for ci, co in LAYERS:
+    for ci, co in layers_for(c_in):
         layers.append((rng.normal(0, np.sqrt(2.0 / (9 * ci)), (co, 3, 3, ci)), np.zeros(co)))
     return pack(layers)

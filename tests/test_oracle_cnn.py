@@ -222,3 +222,70 @@ def test_network_gradient_robust_loss_matches_finite_differences():
             fd = (cnn.loss_and_grad(p1, lr, hr, alb, nrm, tgt, 2, loss="robust")[0]
                   - cnn.loss_and_grad(p0, lr, hr, alb, nrm, tgt, 2, loss="robust")[0]) / (2 * h)
             assert abs(fd - g[i]) <= 1e-6 * max(1e-3, abs(g[i])) + 1e-9, (i, fd, g[i])
+
+
+def _extra(rng, N, H, W):
+    d = rng.uniform(0, 2, (N, H, W, 3))
+    sp = rng.uniform(0, 1, (N, H, W, 3))
+    v = rng.gamma(0.5, 2.0, (N, H, W, 3))
+    return np.concatenate([d, sp, v], axis=-1)
+
+
+def test_extra_input_zero_weights_reduce_to_base_network():
+    # a 21-channel network whose layer-0 weights on the 9 extra channels are
+    # zero is the 12-channel network: the extra layers are appended after the
+    # base channels and nothing else changes
+    rng = np.random.default_rng(20)
+    lr, hr, alb, nrm = _inputs(rng, N=1, h=4, w=5, s=2)
+    ex = _extra(rng, 1, 8, 10)
+    base = cnn.kaiming(3) * 0.5
+    L = cnn.unpack(base)
+    w0, b0 = L[0]
+    w0x = np.concatenate([w0, np.zeros(w0.shape[:3] + (cnn.C_EXTRA,))], axis=-1)
+    px = cnn.pack([(w0x, b0)] + L[1:])
+    assert px.size == cnn.NPARAMS_EXTRA and cnn.input_channels(px) == 21
+    assert np.array_equal(cnn.forward(px, lr, hr, alb, nrm, 2, extra=ex),
+                          cnn.forward(base, lr, hr, alb, nrm, 2))
+    with pytest.raises(ValueError):
+        cnn.forward(px, lr, hr, alb, nrm, 2)
+    with pytest.raises(ValueError):
+        cnn.forward(base, lr, hr, alb, nrm, 2, extra=ex)
+
+
+@pytest.mark.parametrize("ch,value,want", [(12, 0.7, 0.7), (17, 0.25, 0.25),
+                                           (18, np.e - 1.0, 1.0), (20, 0.0, 0.0)])
+def test_extra_input_channel_order(ch, value, want):
+    # a network whose first layer only passes input channel `ch` through its
+    # centre tap (to feature 0, then identity to the output) sees diffuse at
+    # 12-14, specular at 15-17 and log(1 + variance) at 18-20
+    rng = np.random.default_rng(21)
+    lr, hr, alb, nrm = _inputs(rng, N=1, h=3, w=3, s=2)
+    ex = _extra(rng, 1, 6, 6)
+    ex[..., ch - 12] = value
+    layers = [(np.zeros((co, 3, 3, ci)), np.zeros(co)) for ci, co in cnn.layers_for(21)]
+    layers[0][0][0, 1, 1, ch] = 1.0
+    layers[-1][0][0, 1, 1, 0] = 1.0
+    p = cnn.pack(layers)
+    y = cnn.forward(p, np.zeros_like(lr), hr, alb, nrm, 2, extra=ex)
+    assert np.allclose(y[..., 0], want, rtol=0, atol=1e-12), (ch, y[..., 0].max())
+
+
+def test_extra_input_network_gradient_matches_finite_differences():
+    rng = np.random.default_rng(22)
+    lr, hr, alb, nrm = _inputs(rng, N=1, h=3, w=4, s=2)
+    ex = _extra(rng, 1, 6, 8)
+    tgt = rng.uniform(0, 2, hr.shape)
+    params = cnn.kaiming(4, c_in=21) * 0.5 + rng.normal(0, 0.01, cnn.NPARAMS_EXTRA)
+    _, g = cnn.loss_and_grad(params, lr, hr, alb, nrm, tgt, 2, extra=ex)
+    h = 1e-6
+    wo, bo, _, _ = cnn.layer_offsets(21)[0]
+    # layer-0 weights on the extra channels (c = 12..20) and a few elsewhere
+    picks = [wo + ((o * 3 + 1) * 3 + 1) * 21 + c for o, c in ((0, 12), (5, 16), (9, 20))]
+    picks += [int(i) for i in rng.integers(bo, cnn.NPARAMS_EXTRA, 4)]
+    for i in picks:
+        p1, p0 = params.copy(), params.copy()
+        p1[i] += h
+        p0[i] -= h
+        fd = (cnn.loss_and_grad(p1, lr, hr, alb, nrm, tgt, 2, extra=ex)[0]
+              - cnn.loss_and_grad(p0, lr, hr, alb, nrm, tgt, 2, extra=ex)[0]) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1e-3, abs(g[i])) + 1e-9, (i, fd, g[i])
