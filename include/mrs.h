@@ -268,14 +268,26 @@ mrs_status mrs_philox_uniforms(const uint32_t* triples, int32_t n, uint64_t seed
  * forward order, weight [Cout][3][3][Cin] then bias [Cout].
  * ------------------------------------------------------------------------ */
 #define MRS_NET_NPARAMS 599555
+/* The same network with the extra HRLS layers of Sec. 4 as nine more input
+ * channels (21 in all): after the 12 above come diffuse RGB, specular RGB and
+ * log(1 + max(variance, 0)) per channel (the log is this library's reading:
+ * the variance spans orders of magnitude).  Only the first conv grows, to
+ * weight [64][3][3][21]. */
+#define MRS_NET_NPARAMS_EXTRA 604739
+#define MRS_NET_EXTRA_CHANNELS 9
 #define MRS_PREC_FP32 0   /* FP32 SIMT convolutions (reference precision) */
 #define MRS_PREC_BF16 1   /* BF16 operands on tcgen05 tensor cores, FP32 accumulate */
 #define MRS_PREC_FP8 2    /* FP8-E4M3 operands, per-output-channel weight scales */
 
-/* params: HOST float [n_params] (must equal MRS_NET_NPARAMS), copied in as the
- * FP32 master weights; Adam moments start at zero. */
+/* params: HOST float [n_params], copied in as the FP32 master weights; Adam
+ * moments start at zero.  n_params = MRS_NET_NPARAMS makes the 12-channel
+ * network, MRS_NET_NPARAMS_EXTRA the 21-channel one (extra HRLS layers);
+ * anything else is MRS_ERR_ARG.  All later parameter arrays of the handle
+ * (set/get params, grads, state) have that many values. */
 mrs_status mrs_net_create(const float* params, int32_t n_params, mrs_net* out);
 mrs_status mrs_net_free(mrs_net net);
+/* Input channels of the net's first conv: 12 or 21 (HOST int32 out). */
+mrs_status mrs_net_input_channels(mrs_net net, int32_t* channels);
 /* Replace / read the FP32 master weights (HOST float [MRS_NET_NPARAMS]);
  * set also resets the Adam state.  Both synchronise the device. */
 mrs_status mrs_net_set_params(mrs_net net, const float* params);
@@ -289,6 +301,14 @@ mrs_status mrs_net_get_params(mrs_net net, float* params);
 mrs_status mrs_fuse(mrs_net net, const float* lrhs, const float* hrls, const float* albedo,
                     const float* normal, int32_t N, int32_t H, int32_t W, int32_t scale,
                     int32_t precision, float* out, void* stream);
+/* mrs_fuse with the extra HRLS layers as input (Sec. 4: the HRLS carries
+ * albedo, normal, diffuse, specular and variance layers).  extra device
+ * [N][H][W][9] = diffuse RGB, specular RGB, variance RGB as mrs_render_layers
+ * writes them; it must be non-NULL exactly for a 21-channel net (else
+ * MRS_ERR_ARG); mrs_fuse is this call with extra = NULL. */
+mrs_status mrs_fuse_extra(mrs_net net, const float* lrhs, const float* hrls, const float* albedo,
+                          const float* normal, const float* extra, int32_t N, int32_t H, int32_t W,
+                          int32_t scale, int32_t precision, float* out, void* stream);
 
 /* One training step of the fusion network (learned part of the method; the
  * paper trains with a robust loss and SGD, Sec. 4 "Loss function" and
@@ -312,7 +332,14 @@ mrs_status mrs_train_step(mrs_net net, const float* lrhs, const float* hrls, con
                           const float* normal, const float* target, int32_t N, int32_t H,
                           int32_t W, int32_t scale, float lr, int32_t precision, double* loss_out,
                           void* stream);
-/* Gradient of the last mrs_train_step (HOST float [MRS_NET_NPARAMS]; synchronises). */
+/* mrs_train_step with the extra HRLS layers (device [N][H][W][9], as in
+ * mrs_fuse_extra; non-NULL exactly for a 21-channel net).  Their diffuse and
+ * specular radiance is clipped at 100 like the HRLS; the variance is not. */
+mrs_status mrs_train_step_extra(mrs_net net, const float* lrhs, const float* hrls,
+                                const float* albedo, const float* normal, const float* extra,
+                                const float* target, int32_t N, int32_t H, int32_t W, int32_t scale,
+                                float lr, int32_t precision, double* loss_out, void* stream);
+/* Gradient of the last mrs_train_step (HOST float [n_params]; synchronises). */
 mrs_status mrs_net_get_grads(mrs_net net, float* grads);
 /* Checkpoint / resume: FP32 master weights, Adam moments (HOST float
  * [MRS_NET_NPARAMS] each) and the Adam step count.  Both synchronise. */

@@ -47,8 +47,11 @@ SIGS = {
     "mrs_net_set_params": [P, P],
     "mrs_net_get_params": [P, P],
     "mrs_fuse": [P, P, P, P, P, I32, I32, I32, I32, I32, P, P],
+    "mrs_fuse_extra": [P, P, P, P, P, P, I32, I32, I32, I32, I32, P, P],
+    "mrs_net_input_channels": [P, P],
     "mrs_image_metrics": [P, P, I64, F64, F64, P, P],
     "mrs_train_step": [P, P, P, P, P, P, I32, I32, I32, I32, F32, I32, P, P],
+    "mrs_train_step_extra": [P, P, P, P, P, P, P, I32, I32, I32, I32, F32, I32, P, P],
     "mrs_net_get_grads": [P, P],
     "mrs_net_get_state": [P, P, P, P, P],
     "mrs_net_set_state": [P, P, P, P, I64],

@@ -25,20 +25,25 @@ constexpr int kFeat = 64;
 
 struct LayerShape { int cin, cout; size_t woff, boff; };
 
-const std::vector<LayerShape>& shapes()
+// Layer shapes for a network whose first conv reads cin0 = 12 channels (the
+// base input) or 21 (with the extra HRLS layers: diffuse, specular, variance)
+const std::vector<LayerShape>& shapes(int cin0)
 {
-    static std::vector<LayerShape> v;
+    static std::vector<LayerShape> v12, v21;
+    std::vector<LayerShape>& v = cin0 == 21 ? v21 : v12;
     if (v.empty()) {
         size_t o = 0;
         for (int l = 0; l < kLayers; ++l) {
-            int cin = l == 0 ? 12 : kFeat, cout = l == kLayers - 1 ? 3 : kFeat;
+            int cin = l == 0 ? cin0 : kFeat, cout = l == kLayers - 1 ? 3 : kFeat;
             v.push_back({cin, cout, o, o + (size_t)cout * 9 * cin});
             o += (size_t)cout * 9 * cin + cout;
         }
     }
     return v;
 }
-constexpr size_t kParams = 599555;
+constexpr size_t kParams12 = 599555;
+constexpr size_t kParams21 = 604739;
+constexpr int kCinMax = 21;
 
 inline int nout_of(int l) { return l == kLayers - 1 ? 16 : 64; }
 
@@ -63,9 +68,14 @@ __device__ __forceinline__ void up_pixel(const float* __restrict__ lr, int h, in
     }
 }
 
-// 12 fusion-input channels of pixel p: up(LRHS), HRLS, albedo, normal
-__device__ __forceinline__ void input12(const float* lrhs, const float* hrls, const float* alb,
-                                        const float* nrm, int H, int W, int s, size_t p, float v[12])
+// Fusion-input channels of pixel p: up(LRHS), HRLS, albedo, normal (12) and,
+// when extra != NULL (extra [P][9] = diffuse, specular, variance of the HRLS,
+// Sec. 4), diffuse, specular and log(1 + max(variance, 0)) (21).  clip > 0:
+// the radiance channels (up(LRHS), HRLS, diffuse, specular) are clipped at
+// `clip` (the training data's firefly clipping, Sec. 3.2).  Returns the count.
+__device__ __forceinline__ int input_px(const float* lrhs, const float* hrls, const float* alb,
+                                        const float* nrm, const float* extra, int H, int W, int s,
+                                        size_t p, float clip, float* v)
 {
     int x = (int)(p % W);
     size_t r = p / W;
@@ -77,53 +87,69 @@ __device__ __forceinline__ void input12(const float* lrhs, const float* hrls, co
         v[6 + k] = __ldg(alb + 3 * p + k);
         v[9 + k] = __ldg(nrm + 3 * p + k);
     }
+    if (clip > 0.0f)
+        for (int k = 0; k < 6; ++k) v[k] = fminf(v[k], clip);
+    if (!extra) return 12;
+    for (int k = 0; k < 6; ++k) {
+        float e = __ldg(extra + 9 * p + k);
+        v[12 + k] = clip > 0.0f ? fminf(e, clip) : e;
+    }
+    for (int k = 0; k < 3; ++k) v[18 + k] = log1pf(fmaxf(__ldg(extra + 9 * p + 6 + k), 0.0f));
+    return 21;
 }
 
-// clip > 0: radiance inputs (LRHS, HRLS) clipped at `clip` before use (the
-// training data's firefly clipping, Sec. 3.2)
 __global__ void k_input_f32(const float* lrhs, const float* hrls, const float* alb,
-                            const float* nrm, int H, int W, int s, size_t P, float* x0,
-                            float clip = 0.0f)
+                            const float* nrm, const float* extra, int H, int W, int s, size_t P,
+                            float* x0, float clip = 0.0f)
 {
     for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < P;
          p += (size_t)gridDim.x * blockDim.x) {
-        float v[12];
-        input12(lrhs, hrls, alb, nrm, H, W, s, p, v);
-        if (clip > 0.0f)
-            for (int k = 0; k < 6; ++k) v[k] = fminf(v[k], clip);
-        for (int k = 0; k < 12; ++k) x0[12 * p + k] = v[k];
+        float v[kCinMax];
+        int c = input_px(lrhs, hrls, alb, nrm, extra, H, W, s, p, clip, v);
+        for (int k = 0; k < c; ++k) x0[c * p + k] = v[k];
     }
 }
 
-// bf16 [P][64] (channels 12..63 zero) or fp8 [P][64] scaled by inv_scale
+// bf16 [P][64] or fp8 [P][64] scaled by inv_scale; channels past the input's
+// 12 or 21 are zero (the first 24 bf16 / 32 fp8 channels are written from v,
+// the rest as zero 16-byte words)
 __global__ void k_input_q(const float* lrhs, const float* hrls, const float* alb,
-                          const float* nrm, int H, int W, int s, size_t P, void* x0, int fp8,
-                          float inv_scale)
+                          const float* nrm, const float* extra, int H, int W, int s, size_t P,
+                          void* x0, int fp8, float inv_scale, float clip = 0.0f)
 {
     for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < P;
          p += (size_t)gridDim.x * blockDim.x) {
-        float v[12];
-        input12(lrhs, hrls, alb, nrm, H, W, s, p, v);
+        float v[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) v[k] = 0.0f;
+        input_px(lrhs, hrls, alb, nrm, extra, H, W, s, p, clip, v);
+        const uint4 z = make_uint4(0, 0, 0, 0);
         if (!fp8) {
             uint4* o = (uint4*)((__nv_bfloat16*)x0 + p * 64);
-            uint4 u[2];
-            __nv_bfloat162* h2 = (__nv_bfloat162*)u;
-            for (int e = 0; e < 8; ++e)
-                h2[e] = __floats2bfloat162_rn(2 * e < 12 ? v[2 * e] : 0.0f,
-                                              2 * e + 1 < 12 ? v[2 * e + 1] : 0.0f);
-            o[0] = u[0];
-            o[1] = u[1];
-            uint4 z = make_uint4(0, 0, 0, 0);
-            for (int j = 2; j < 8; ++j) o[j] = z;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                uint4 u;
+                __nv_bfloat162* h2 = (__nv_bfloat162*)&u;
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    h2[e] = __floats2bfloat162_rn(v[8 * j + 2 * e], v[8 * j + 2 * e + 1]);
+                o[j] = u;
+            }
+#pragma unroll
+            for (int j = 3; j < 8; ++j) o[j] = z;
         } else {
             uint4* o = (uint4*)((uint8_t*)x0 + p * 64);
-            uint4 u;
-            uint8_t* b8 = (uint8_t*)&u;
-            for (int e = 0; e < 16; ++e)
-                b8[e] = e < 12 ? (uint8_t)__nv_cvt_float_to_fp8(v[e] * inv_scale, __NV_SATFINITE, __NV_E4M3) : 0;
-            o[0] = u;
-            uint4 z = make_uint4(0, 0, 0, 0);
-            for (int j = 1; j < 4; ++j) o[j] = z;
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                uint4 u;
+                uint8_t* b8 = (uint8_t*)&u;
+#pragma unroll
+                for (int e = 0; e < 16; ++e)
+                    b8[e] = (uint8_t)__nv_cvt_float_to_fp8(v[16 * j + e] * inv_scale, __NV_SATFINITE, __NV_E4M3);
+                o[j] = u;
+            }
+            o[2] = z;
+            o[3] = z;
         }
     }
 }
@@ -580,7 +606,9 @@ Scratch& scratch()
 using namespace mrs;
 
 struct mrs_net_s {
-    float* master = nullptr;       // [kParams]
+    int cin0 = 12;                 // input channels of the first conv (12 or 21)
+    size_t np = kParams12;         // parameter count
+    float* master = nullptr;       // [np]
     float* adam_m = nullptr;
     float* adam_v = nullptr;
     float* grad = nullptr;
@@ -611,7 +639,7 @@ namespace {
 mrs_status pack_bf16(mrs_net_s* net, cudaStream_t st)
 {
     if (net->bf_valid) return MRS_OK;
-    const auto& L = shapes();
+    const auto& L = shapes(net->cin0);
     for (int l = 0; l < kLayers; ++l) {
         int nout = nout_of(l);
         k_pack_bf16<<<(9 * nout * 64 + 255) / 256, 256, 0, st>>>(
@@ -628,7 +656,7 @@ mrs_status pack_bf16(mrs_net_s* net, cudaStream_t st)
 mrs_status pack_fp8(mrs_net_s* net, cudaStream_t st)
 {
     if (net->f8_valid) return MRS_OK;
-    const auto& L = shapes();
+    const auto& L = shapes(net->cin0);
     for (int l = 0; l < kLayers; ++l) {
         int nout = nout_of(l);
         k_pack_fp8<<<1, 256, 0, st>>>(net->master, L[l].woff, L[l].boff, L[l].cin, L[l].cout, nout,
@@ -643,19 +671,21 @@ mrs_status pack_fp8(mrs_net_s* net, cudaStream_t st)
 }
 
 mrs_status fuse_f32(mrs_net_s* net, const float* lrhs, const float* hrls, const float* alb,
-                    const float* nrm, int N, int H, int W, int s, float* out, cudaStream_t st)
+                    const float* nrm, const float* extra, int N, int H, int W, int s, float* out,
+                    cudaStream_t st)
 {
     size_t P = (size_t)N * H * W;
-    mrs_status rc = net->act.ensure(P * (12 + 64 + 64) * 4);
+    const int c0 = net->cin0;
+    mrs_status rc = net->act.ensure(P * (c0 + 64 + 64) * 4);
     if (rc != MRS_OK) return rc;
     float* x0 = net->act.as<float>();
-    float* h = x0 + P * 12;
+    float* h = x0 + P * c0;
     float* r = h + P * 64;
-    const auto& L = shapes();
+    const auto& L = shapes(net->cin0);
     k_input_f32<<<(int)((P + 255) / 256 < 65535 ? (P + 255) / 256 : 65535), 256, 0, st>>>(
-        lrhs, hrls, alb, nrm, H, W, s, P, x0);
+        lrhs, hrls, alb, nrm, extra, H, W, s, P, x0);
     MRS_LAUNCHED(1);
-    rc = conv_simt(x0, 12, net->master + L[0].woff, net->master + L[0].boff, 64, SIMT_PLAIN, 1,
+    rc = conv_simt(x0, c0, net->master + L[0].woff, net->master + L[0].boff, 64, SIMT_PLAIN, 1,
                    nullptr, h, nullptr, N, H, W, s, st);
     for (int k = 0; k < 8 && rc == MRS_OK; ++k) {
         const LayerShape& a = L[1 + 2 * k];
@@ -673,10 +703,11 @@ mrs_status fuse_f32(mrs_net_s* net, const float* lrhs, const float* hrls, const 
 }
 
 mrs_status calibrate_fp8(mrs_net_s* net, const float* lrhs, const float* hrls, const float* alb,
-                         const float* nrm, int N, int H, int W, int s, cudaStream_t st);
+                         const float* nrm, const float* extra, int N, int H, int W, int s,
+                         cudaStream_t st);
 
 mrs_status fuse_tc(mrs_net_s* net, const float* lrhs, const float* hrls, const float* alb,
-                   const float* nrm, int N, int H, int W, int s, int prec, float* out,
+                   const float* nrm, const float* extra, int N, int H, int W, int s, int prec, float* out,
                    cudaStream_t st, bool calib = false)
 {
     size_t P = (size_t)N * H * W;
@@ -686,7 +717,7 @@ mrs_status fuse_tc(mrs_net_s* net, const float* lrhs, const float* hrls, const f
     if (f8) {
         if ((rc = pack_fp8(net, st)) != MRS_OK) return rc;
         if (!net->xscale_valid &&
-            (rc = calibrate_fp8(net, lrhs, hrls, alb, nrm, N, H, W, s, st)) != MRS_OK)
+            (rc = calibrate_fp8(net, lrhs, hrls, alb, nrm, extra, N, H, W, s, st)) != MRS_OK)
             return rc;
     }
     // workspace: x0, h, r in bf16 (128 B/px each); fp8 adds x0, h, r copies (64 B/px)
@@ -700,7 +731,7 @@ mrs_status fuse_tc(mrs_net_s* net, const float* lrhs, const float* hrls, const f
     uint8_t* h8 = x08 + P * 64;
     uint8_t* r8 = h8 + P * 64;
     int g = (int)((P + 255) / 256 < 65535 ? (P + 255) / 256 : 65535);
-    k_input_q<<<g, 256, 0, st>>>(lrhs, hrls, alb, nrm, H, W, s, P, f8 ? (void*)x08 : x0, f8 ? 1 : 0,
+    k_input_q<<<g, 256, 0, st>>>(lrhs, hrls, alb, nrm, extra, H, W, s, P, f8 ? (void*)x08 : x0, f8 ? 1 : 0,
                                  f8 ? 1.0f / net->xscale[0] : 1.0f);
     MRS_LAUNCHED(1);
     if ((rc = cuda_status(cudaGetLastError(), "input")) != MRS_OK) return rc;
@@ -757,14 +788,14 @@ mrs_status fuse_tc(mrs_net_s* net, const float* lrhs, const float* hrls, const f
 // per-layer activation scales from one BF16 pass over the first input:
 // xscale[l] = amax(input of layer l) / 448
 mrs_status calibrate_fp8(mrs_net_s* net, const float* lrhs, const float* hrls, const float* alb,
-                         const float* nrm, int N, int H, int W, int s, cudaStream_t st)
+                         const float* nrm, const float* extra, int N, int H, int W, int s,
+                         cudaStream_t st)
 {
     mrs_status rc = net->aux.ensure(4096);
     if (rc != MRS_OK) return rc;
     MRS_CHECK(cudaMemsetAsync(net->aux.p, 0, 4096, st));
     size_t P = (size_t)N * H * W;
-    // layer 0 input amax: from the 12 input channels (computed in fp32 via the fp32 input kernel)
-    rc = fuse_tc(net, lrhs, hrls, alb, nrm, N, H, W, s, MRS_PREC_BF16, nullptr, st, true);
+    rc = fuse_tc(net, lrhs, hrls, alb, nrm, extra, N, H, W, s, MRS_PREC_BF16, nullptr, st, true);
     (void)P;
     if (rc != MRS_OK) return rc;
     // layer 0 input: amax of the bf16 fusion input x0
@@ -786,16 +817,19 @@ extern "C" mrs_status mrs_net_create(const float* params, int32_t n_params, mrs_
     MRS_ARG(out != nullptr, "out is NULL");
     *out = nullptr;
     MRS_ARG(params != nullptr, "params is NULL");
-    MRS_ARG(n_params == (int32_t)kParams, "n_params must equal MRS_NET_NPARAMS");
+    MRS_ARG(n_params == (int32_t)kParams12 || n_params == (int32_t)kParams21,
+            "n_params must equal MRS_NET_NPARAMS or MRS_NET_NPARAMS_EXTRA");
     mrs_net_s* net = new mrs_net_s();
+    net->np = (size_t)n_params;
+    net->cin0 = n_params == (int32_t)kParams21 ? 21 : 12;
     mrs_status s = MRS_OK;
     auto alloc = [&](void** p, size_t bytes) {
         if (s == MRS_OK) s = cuda_status(cudaMalloc(p, bytes), "cudaMalloc(net)");
     };
-    alloc((void**)&net->master, kParams * 4);
-    alloc((void**)&net->adam_m, kParams * 4);
-    alloc((void**)&net->adam_v, kParams * 4);
-    alloc((void**)&net->grad, kParams * 4);
+    alloc((void**)&net->master, net->np * 4);
+    alloc((void**)&net->adam_m, net->np * 4);
+    alloc((void**)&net->adam_v, net->np * 4);
+    alloc((void**)&net->grad, net->np * 4);
     alloc((void**)&net->wbf, (size_t)kLayers * 9 * 64 * 64 * 2);
     alloc((void**)&net->wbfT, (size_t)kLayers * 9 * 64 * 64 * 2);
     alloc((void**)&net->wf8, (size_t)kLayers * 9 * 64 * 64);
@@ -826,9 +860,9 @@ extern "C" mrs_status mrs_net_free(mrs_net net)
 extern "C" mrs_status mrs_net_set_params(mrs_net net, const float* params)
 {
     MRS_ARG(net && params, "NULL argument");
-    MRS_CHECK(cudaMemcpy(net->master, params, kParams * 4, cudaMemcpyHostToDevice));
-    MRS_CHECK(cudaMemset(net->adam_m, 0, kParams * 4));
-    MRS_CHECK(cudaMemset(net->adam_v, 0, kParams * 4));
+    MRS_CHECK(cudaMemcpy(net->master, params, net->np * 4, cudaMemcpyHostToDevice));
+    MRS_CHECK(cudaMemset(net->adam_m, 0, net->np * 4));
+    MRS_CHECK(cudaMemset(net->adam_v, 0, net->np * 4));
     MRS_CHECK(cudaMemset(net->err, 0, 4));
     net->step = 0;
     net->bf_valid = net->f8_valid = net->xscale_valid = net->bfT_valid = false;
@@ -838,7 +872,14 @@ extern "C" mrs_status mrs_net_set_params(mrs_net net, const float* params)
 extern "C" mrs_status mrs_net_get_params(mrs_net net, float* params)
 {
     MRS_ARG(net && params, "NULL argument");
-    MRS_CHECK(cudaMemcpy(params, net->master, kParams * 4, cudaMemcpyDeviceToHost));
+    MRS_CHECK(cudaMemcpy(params, net->master, net->np * 4, cudaMemcpyDeviceToHost));
+    return MRS_OK;
+}
+
+extern "C" mrs_status mrs_net_input_channels(mrs_net net, int32_t* channels)
+{
+    MRS_ARG(net && channels, "NULL argument");
+    *channels = net->cin0;
     return MRS_OK;
 }
 
@@ -846,8 +887,19 @@ extern "C" mrs_status mrs_fuse(mrs_net net, const float* lrhs, const float* hrls
                                const float* albedo, const float* normal, int32_t N, int32_t H,
                                int32_t W, int32_t scale, int32_t precision, float* out, void* stream)
 {
+    return mrs_fuse_extra(net, lrhs, hrls, albedo, normal, nullptr, N, H, W, scale, precision, out,
+                          stream);
+}
+
+extern "C" mrs_status mrs_fuse_extra(mrs_net net, const float* lrhs, const float* hrls,
+                                     const float* albedo, const float* normal, const float* extra,
+                                     int32_t N, int32_t H, int32_t W, int32_t scale,
+                                     int32_t precision, float* out, void* stream)
+{
     MRS_ARG(net != nullptr, "net is NULL");
     MRS_ARG(lrhs && hrls && albedo && normal && out, "NULL image pointer");
+    MRS_ARG((extra != nullptr) == (net->cin0 == 21),
+            "extra layers must be given exactly for a net with MRS_NET_NPARAMS_EXTRA parameters");
     MRS_ARG(scale == 1 || scale == 2 || scale == 4 || scale == 8, "scale must be 1, 2, 4 or 8");
     MRS_ARG(N >= 1 && H >= 1 && W >= 1, "N, H, W must be >= 1");
     MRS_ARG(H % scale == 0 && W % scale == 0, "H and W must be multiples of scale");
@@ -856,9 +908,9 @@ extern "C" mrs_status mrs_fuse(mrs_net net, const float* lrhs, const float* hrls
     cudaStream_t st = (cudaStream_t)stream;
     mrs_status rc;
     if (precision == MRS_PREC_FP32)
-        rc = fuse_f32(net, lrhs, hrls, albedo, normal, N, H, W, scale, out, st);
+        rc = fuse_f32(net, lrhs, hrls, albedo, normal, extra, N, H, W, scale, out, st);
     else
-        rc = fuse_tc(net, lrhs, hrls, albedo, normal, N, H, W, scale, precision, out, st);
+        rc = fuse_tc(net, lrhs, hrls, albedo, normal, extra, N, H, W, scale, precision, out, st);
     return rc;
 }
 
@@ -1019,7 +1071,7 @@ inline int grid1d(size_t n) { size_t g = (n + 255) / 256; return (int)(g < 4096 
 mrs_status layer_dw(mrs_net_s* net, int l, const float* x, const float* dy, int N, int H, int W,
                     float* part, float* dbpart, cudaStream_t st)
 {
-    const LayerShape& L = shapes()[l];
+    const LayerShape& L = shapes(net->cin0)[l];
     dim3 grid(kDwSplits, 9);
     MRS_TIMED(PK_TRAIN, st, (k_dw_partial<float, float><<<grid, 256, 0, st>>>(x, L.cin, L.cin, dy, L.cout, L.cout, N, H, W, part, dbpart)));
     MRS_LAUNCHED(1);
@@ -1034,7 +1086,7 @@ mrs_status layer_dw(mrs_net_s* net, int l, const float* x, const float* dy, int 
 mrs_status layer_dx(mrs_net_s* net, int l, const float* dy, float* wt, const float* zero,
                     int mode, const float* res, float* dx, int N, int H, int W, cudaStream_t st)
 {
-    const LayerShape& L = shapes()[l];
+    const LayerShape& L = shapes(net->cin0)[l];
     int n = L.cin * 9 * L.cout;
     k_wtrans<<<(n + 255) / 256, 256, 0, st>>>(net->master + L.woff, L.cin, L.cout, wt);
     MRS_LAUNCHED(1);
@@ -1042,21 +1094,22 @@ mrs_status layer_dx(mrs_net_s* net, int l, const float* dy, float* wt, const flo
 }
 
 mrs_status train_step_f32(mrs_net_s* net, const float* lrhs, const float* hrls, const float* alb,
-                          const float* nrm, const float* target, int N, int H, int W, int s,
-                          float lr, double* loss_out, cudaStream_t st)
+                          const float* nrm, const float* extra, const float* target, int N, int H,
+                          int W, int s, float lr, double* loss_out, cudaStream_t st)
 {
+    const int c0 = net->cin0;
     const size_t P = (size_t)N * H * W;
     const size_t F = P * 64;
     const size_t nlr = (size_t)N * (H / s) * (W / s) * 3;
     // activations: x0 | h0..h8 | r0..r7 | y | dy | dh | da | lrhs_clipped
-    size_t need = (P * 12 + 9 * F + 8 * F + 2 * P * 3 + 2 * F + nlr) * 4;
+    size_t need = (P * c0 + 9 * F + 8 * F + 2 * P * 3 + 2 * F + nlr) * 4;
     mrs_status rc = net->tact.ensure(need);
     if (rc != MRS_OK) return rc;
     size_t tneed = (64 * 9 * 64 + 64) * 4 + ((size_t)kDwSplits * 9 * 64 * 64 + kDwSplits * 64) * 4 +
                    (kRedBlocks + 8) * 8;
     if ((rc = net->ttmp.ensure(tneed)) != MRS_OK) return rc;
     float* x0 = net->tact.as<float>();
-    float* hs = x0 + P * 12;
+    float* hs = x0 + P * c0;
     float* rs = hs + 9 * F;
     float* y = rs + 8 * F;
     float* dy = y + P * 3;
@@ -1070,15 +1123,15 @@ mrs_status train_step_f32(mrs_net_s* net, const float* lrhs, const float* hrls, 
     double* lparts = (double*)(dbpart + kDwSplits * 64);
     double* lres = lparts + kRedBlocks;
     MRS_CHECK(cudaMemsetAsync(zero, 0, 64 * 4, st));
-    const auto& L = shapes();
+    const auto& L = shapes(net->cin0);
     const float* M = net->master;
 
     // forward, keeping every activation the backward needs
     k_clip_copy<<<grid1d(nlr), 256, 0, st>>>(lrhs, nlr, kClip, lrc);
     MRS_LAUNCHED(1);
-    k_input_f32<<<grid1d(P), 256, 0, st>>>(lrc, hrls, alb, nrm, H, W, s, P, x0, kClip);
+    k_input_f32<<<grid1d(P), 256, 0, st>>>(lrc, hrls, alb, nrm, extra, H, W, s, P, x0, kClip);
     MRS_LAUNCHED(1);
-    rc = conv_simt(x0, 12, M + L[0].woff, M + L[0].boff, 64, SIMT_PLAIN, 1, nullptr, hs, nullptr, N, H, W, s, st);
+    rc = conv_simt(x0, c0, M + L[0].woff, M + L[0].boff, 64, SIMT_PLAIN, 1, nullptr, hs, nullptr, N, H, W, s, st);
     for (int k = 0; k < 8 && rc == MRS_OK; ++k) {
         const LayerShape& a = L[1 + 2 * k];
         const LayerShape& b = L[2 + 2 * k];
@@ -1119,8 +1172,8 @@ mrs_status train_step_f32(mrs_net_s* net, const float* lrhs, const float* hrls, 
     const double b1 = 0.9, b2 = 0.999;
     float bc1 = (float)(1.0 - pow(b1, (double)net->step));
     float bc2 = (float)(1.0 - pow(b2, (double)net->step));
-    MRS_TIMED(PK_TRAIN, st, k_adam<<<grid1d(kParams), 256, 0, st>>>(net->master, net->grad, net->adam_m, net->adam_v,
-                                                        kParams, lr, (float)b1, (float)b2, 1e-8f, bc1, bc2));
+    MRS_TIMED(PK_TRAIN, st, k_adam<<<grid1d(net->np), 256, 0, st>>>(net->master, net->grad, net->adam_m, net->adam_v,
+                                                        net->np, lr, (float)b1, (float)b2, 1e-8f, bc1, bc2));
     MRS_LAUNCHED(1);
     net->bf_valid = net->f8_valid = net->xscale_valid = net->bfT_valid = false;
     if (loss_out) {
@@ -1135,7 +1188,7 @@ mrs_status train_step_f32(mrs_net_s* net, const float* lrhs, const float* hrls, 
 mrs_status pack_bf16_T(mrs_net_s* net, cudaStream_t st)
 {
     if (net->bfT_valid) return MRS_OK;
-    const auto& L = shapes();
+    const auto& L = shapes(net->cin0);
     for (int l = 1; l < kLayers; ++l) {
         __nv_bfloat16* wp = net->wbfT + (size_t)l * 9 * 64 * 64;
         k_pack_bf16_T<<<(9 * 64 * 64 + 255) / 256, 256, 0, st>>>(net->master, L[l].woff, L[l].cin,
@@ -1152,8 +1205,8 @@ mrs_status pack_bf16_T(mrs_net_s* net, cudaStream_t st)
 // kernel with BF16 activations / activation gradients, FP32 accumulation,
 // FP32 dW / db reductions and FP32 master weights + Adam
 mrs_status train_step_bf16(mrs_net_s* net, const float* lrhs, const float* hrls, const float* alb,
-                           const float* nrm, const float* target, int N, int H, int W, int s,
-                           float lr, double* loss_out, cudaStream_t st)
+                           const float* nrm, const float* extra, const float* target, int N, int H,
+                           int W, int s, float lr, double* loss_out, cudaStream_t st)
 {
     const size_t P = (size_t)N * H * W;
     const size_t F = P * 64;                       // bf16 elements of one [P][64] tensor
@@ -1182,7 +1235,7 @@ mrs_status train_step_bf16(mrs_net_s* net, const float* lrhs, const float* hrls,
     double* lparts = (double*)(dbpart + maxp * 64);
     double* lres = lparts + kRedBlocks;
     MRS_CHECK(cudaMemsetAsync(zero, 0, 64 * 4, st));
-    const auto& L = shapes();
+    const auto& L = shapes(net->cin0);
 
     // tensor maps: A operands (32-pixel boxes) and residual / output (120-pixel)
     auto amap = [&](CUtensorMap* m, const void* ptr) { return tc_make_act_map(m, ptr, N, H, W, TC_BF16, kABox); };
@@ -1228,7 +1281,7 @@ mrs_status train_step_bf16(mrs_net_s* net, const float* lrhs, const float* hrls,
     MRS_LAUNCHED(1);
     k_clip_copy<<<grid1d(P * 3), 256, 0, st>>>(hrls, P * 3, kClip, hrc);
     MRS_LAUNCHED(1);
-    k_input_q<<<grid1d(P), 256, 0, st>>>(lrc, hrc, alb, nrm, H, W, s, P, x0, 0, 1.0f);
+    k_input_q<<<grid1d(P), 256, 0, st>>>(lrc, hrc, alb, nrm, extra, H, W, s, P, x0, 0, 1.0f, kClip);
     MRS_LAUNCHED(1);
     rc = conv(&x0A, &net->wmap_bf[0], net->bias, TC_RELU_BF16, nullptr, &hO[0], 64);
     for (int k = 0; k < 8 && rc == MRS_OK; ++k) {
@@ -1288,8 +1341,8 @@ mrs_status train_step_bf16(mrs_net_s* net, const float* lrhs, const float* hrls,
     const double b1 = 0.9, b2 = 0.999;
     float bc1 = (float)(1.0 - pow(b1, (double)net->step));
     float bc2 = (float)(1.0 - pow(b2, (double)net->step));
-    MRS_TIMED(PK_TRAIN, st, k_adam<<<grid1d(kParams), 256, 0, st>>>(net->master, net->grad, net->adam_m, net->adam_v,
-                                                        kParams, lr, (float)b1, (float)b2, 1e-8f, bc1, bc2));
+    MRS_TIMED(PK_TRAIN, st, k_adam<<<grid1d(net->np), 256, 0, st>>>(net->master, net->grad, net->adam_m, net->adam_v,
+                                                        net->np, lr, (float)b1, (float)b2, 1e-8f, bc1, bc2));
     MRS_LAUNCHED(1);
     net->bf_valid = net->f8_valid = net->xscale_valid = net->bfT_valid = false;
     if (loss_out) {
@@ -1309,8 +1362,20 @@ extern "C" mrs_status mrs_train_step(mrs_net net, const float* lrhs, const float
                                      int32_t N, int32_t H, int32_t W, int32_t scale, float lr,
                                      int32_t precision, double* loss_out, void* stream)
 {
+    return mrs_train_step_extra(net, lrhs, hrls, albedo, normal, nullptr, target, N, H, W, scale,
+                                lr, precision, loss_out, stream);
+}
+
+extern "C" mrs_status mrs_train_step_extra(mrs_net net, const float* lrhs, const float* hrls,
+                                           const float* albedo, const float* normal,
+                                           const float* extra, const float* target, int32_t N,
+                                           int32_t H, int32_t W, int32_t scale, float lr,
+                                           int32_t precision, double* loss_out, void* stream)
+{
     MRS_ARG(net != nullptr, "net is NULL");
     MRS_ARG(lrhs && hrls && albedo && normal && target, "NULL image pointer");
+    MRS_ARG((extra != nullptr) == (net->cin0 == 21),
+            "extra layers must be given exactly for a net with MRS_NET_NPARAMS_EXTRA parameters");
     MRS_ARG(scale == 1 || scale == 2 || scale == 4 || scale == 8, "scale must be 1, 2, 4 or 8");
     MRS_ARG(N >= 1 && H >= 1 && W >= 1 && H % scale == 0 && W % scale == 0, "bad sizes");
     MRS_ARG((int64_t)N * H * W <= (int64_t(1) << 22), "training batch exceeds 2^22 pixels");
@@ -1318,16 +1383,16 @@ extern "C" mrs_status mrs_train_step(mrs_net net, const float* lrhs, const float
     MRS_ARG(precision == MRS_PREC_FP32 || precision == MRS_PREC_BF16,
             "training precision must be MRS_PREC_FP32 or MRS_PREC_BF16");
     if (precision == MRS_PREC_BF16)
-        return train_step_bf16(net, lrhs, hrls, albedo, normal, target, N, H, W, scale, lr, loss_out,
-                               (cudaStream_t)stream);
-    return train_step_f32(net, lrhs, hrls, albedo, normal, target, N, H, W, scale, lr, loss_out,
-                          (cudaStream_t)stream);
+        return train_step_bf16(net, lrhs, hrls, albedo, normal, extra, target, N, H, W, scale, lr,
+                               loss_out, (cudaStream_t)stream);
+    return train_step_f32(net, lrhs, hrls, albedo, normal, extra, target, N, H, W, scale, lr,
+                          loss_out, (cudaStream_t)stream);
 }
 
 extern "C" mrs_status mrs_net_get_grads(mrs_net net, float* grads)
 {
     MRS_ARG(net && grads, "NULL argument");
-    MRS_CHECK(cudaMemcpy(grads, net->grad, kParams * 4, cudaMemcpyDeviceToHost));
+    MRS_CHECK(cudaMemcpy(grads, net->grad, net->np * 4, cudaMemcpyDeviceToHost));
     return MRS_OK;
 }
 
@@ -1335,9 +1400,9 @@ extern "C" mrs_status mrs_net_get_state(mrs_net net, float* params, float* adam_
                                         int64_t* step)
 {
     MRS_ARG(net && params && adam_m && adam_v && step, "NULL argument");
-    MRS_CHECK(cudaMemcpy(params, net->master, kParams * 4, cudaMemcpyDeviceToHost));
-    MRS_CHECK(cudaMemcpy(adam_m, net->adam_m, kParams * 4, cudaMemcpyDeviceToHost));
-    MRS_CHECK(cudaMemcpy(adam_v, net->adam_v, kParams * 4, cudaMemcpyDeviceToHost));
+    MRS_CHECK(cudaMemcpy(params, net->master, net->np * 4, cudaMemcpyDeviceToHost));
+    MRS_CHECK(cudaMemcpy(adam_m, net->adam_m, net->np * 4, cudaMemcpyDeviceToHost));
+    MRS_CHECK(cudaMemcpy(adam_v, net->adam_v, net->np * 4, cudaMemcpyDeviceToHost));
     *step = net->step;
     return MRS_OK;
 }
@@ -1347,9 +1412,9 @@ extern "C" mrs_status mrs_net_set_state(mrs_net net, const float* params, const 
 {
     MRS_ARG(net && params && adam_m && adam_v, "NULL argument");
     MRS_ARG(step >= 0, "step < 0");
-    MRS_CHECK(cudaMemcpy(net->master, params, kParams * 4, cudaMemcpyHostToDevice));
-    MRS_CHECK(cudaMemcpy(net->adam_m, adam_m, kParams * 4, cudaMemcpyHostToDevice));
-    MRS_CHECK(cudaMemcpy(net->adam_v, adam_v, kParams * 4, cudaMemcpyHostToDevice));
+    MRS_CHECK(cudaMemcpy(net->master, params, net->np * 4, cudaMemcpyHostToDevice));
+    MRS_CHECK(cudaMemcpy(net->adam_m, adam_m, net->np * 4, cudaMemcpyHostToDevice));
+    MRS_CHECK(cudaMemcpy(net->adam_v, adam_v, net->np * 4, cudaMemcpyHostToDevice));
     net->step = step;
     net->bf_valid = net->f8_valid = net->xscale_valid = net->bfT_valid = false;
     return MRS_OK;

@@ -13,6 +13,7 @@ from ._lib import call, load
 from .render import _dev, _ptr, _stream
 
 NPARAMS = 599555
+NPARAMS_EXTRA = 604739      # 21 input channels: + diffuse, specular, variance of the HRLS
 PREC = {"fp32": 0, "bf16": 1, "fp8": 2}
 
 
@@ -25,15 +26,20 @@ def _prec(p):
 
 class Net:
     """Fusion network handle (FP32 master weights + packed BF16/FP8 copies +
-    Adam state) created from a flat float32 parameter array."""
+    Adam state) created from a flat float32 parameter array of NPARAMS
+    (12 input channels) or NPARAMS_EXTRA values (21: the extra HRLS layers)."""
 
     def __init__(self, params):
         load()
         p = np.ascontiguousarray(params, dtype=np.float32)
-        assert p.size == NPARAMS, p.size
+        assert p.size in (NPARAMS, NPARAMS_EXTRA), p.size
         h = ctypes.c_void_p()
-        call("mrs_net_create", ctypes.c_void_p(p.ctypes.data), NPARAMS, ctypes.byref(h))
+        call("mrs_net_create", ctypes.c_void_p(p.ctypes.data), p.size, ctypes.byref(h))
         self.handle = h
+        self.nparams = int(p.size)
+        c = ctypes.c_int32()
+        call("mrs_net_input_channels", h, ctypes.byref(c))
+        self.input_channels = int(c.value)
 
     def set_loss(self, loss="l1log", beta=0.1):
         """Training loss of train_step: "l1log" (L1 on log(1 + x)) or "robust"
@@ -54,23 +60,29 @@ class Net:
 
     def set_params(self, params):
         p = np.ascontiguousarray(params, dtype=np.float32)
-        assert p.size == NPARAMS
+        assert p.size == self.nparams
         call("mrs_net_set_params", self.handle, ctypes.c_void_p(p.ctypes.data))
 
     def get_params(self):
-        out = np.zeros(NPARAMS, np.float32)
+        out = np.zeros(self.nparams, np.float32)
         call("mrs_net_get_params", self.handle, ctypes.c_void_p(out.ctypes.data))
         return out
 
-    def fuse(self, lrhs, hrls, albedo, normal, scale, precision="bf16", out=None, stream=None):
-        """lrhs [N,h,w,3], others [N,H,W,3] float32 CUDA tensors -> [N,H,W,3]."""
-        for t in (lrhs, hrls, albedo, normal):
+    def fuse(self, lrhs, hrls, albedo, normal, scale, precision="bf16", out=None, stream=None,
+             extra=None):
+        """lrhs [N,h,w,3], others [N,H,W,3] float32 CUDA tensors -> [N,H,W,3].
+        extra [N,H,W,9] (diffuse, specular, variance) for a 21-channel net."""
+        for t in (lrhs, hrls, albedo, normal) + ((extra,) if extra is not None else ()):
             _dev(t, torch.float32)
         N, H, W, _ = hrls.shape
         if out is None:
             out = torch.empty((N, H, W, 3), dtype=torch.float32, device=hrls.device)
-        call("mrs_fuse", self.handle, _ptr(lrhs), _ptr(hrls), _ptr(albedo), _ptr(normal), N, H, W,
-             scale, _prec(precision), _ptr(out), _stream(stream))
+        if extra is None:
+            call("mrs_fuse", self.handle, _ptr(lrhs), _ptr(hrls), _ptr(albedo), _ptr(normal), N, H,
+                 W, scale, _prec(precision), _ptr(out), _stream(stream))
+        else:
+            call("mrs_fuse_extra", self.handle, _ptr(lrhs), _ptr(hrls), _ptr(albedo), _ptr(normal),
+                 _ptr(extra), N, H, W, scale, _prec(precision), _ptr(out), _stream(stream))
         return out
 
 
@@ -79,30 +91,36 @@ def _np_ptr(a):
 
 
 def train_step(net, lrhs, hrls, albedo, normal, target, scale, lr=1e-4, precision="fp32",
-               sync_loss=True, stream=None, loss=None, beta=0.1):
+               sync_loss=True, stream=None, loss=None, beta=0.1, extra=None):
     """One Adam step on a batch (CUDA float32 NHWC tensors); returns the loss
     (float) or None when sync_loss is False (no host synchronisation).
-    `loss` ("l1log" / "robust"), when given, first sets the net's loss."""
-    for t in (lrhs, hrls, albedo, normal, target):
+    `loss` ("l1log" / "robust"), when given, first sets the net's loss.
+    extra [N,H,W,9] for a 21-channel net."""
+    for t in (lrhs, hrls, albedo, normal, target) + ((extra,) if extra is not None else ()):
         _dev(t, torch.float32)
     if loss is not None:
         net.set_loss(loss, beta)
     N, H, W, _ = hrls.shape
     loss = ctypes.c_double()
-    call("mrs_train_step", net.handle, _ptr(lrhs), _ptr(hrls), _ptr(albedo), _ptr(normal),
-         _ptr(target), N, H, W, scale, float(lr), _prec(precision),
-         ctypes.byref(loss) if sync_loss else None, _stream(stream))
+    lp = ctypes.byref(loss) if sync_loss else None
+    if extra is None:
+        call("mrs_train_step", net.handle, _ptr(lrhs), _ptr(hrls), _ptr(albedo), _ptr(normal),
+             _ptr(target), N, H, W, scale, float(lr), _prec(precision), lp, _stream(stream))
+    else:
+        call("mrs_train_step_extra", net.handle, _ptr(lrhs), _ptr(hrls), _ptr(albedo),
+             _ptr(normal), _ptr(extra), _ptr(target), N, H, W, scale, float(lr), _prec(precision),
+             lp, _stream(stream))
     return float(loss.value) if sync_loss else None
 
 
 def get_grads(net):
-    out = np.zeros(NPARAMS, np.float32)
+    out = np.zeros(net.nparams, np.float32)
     call("mrs_net_get_grads", net.handle, _np_ptr(out))
     return out
 
 
 def get_state(net):
-    p, m, v = (np.zeros(NPARAMS, np.float32) for _ in range(3))
+    p, m, v = (np.zeros(net.nparams, np.float32) for _ in range(3))
     step = ctypes.c_int64()
     call("mrs_net_get_state", net.handle, _np_ptr(p), _np_ptr(m), _np_ptr(v), ctypes.byref(step))
     return {"params": p, "adam_m": m, "adam_v": v, "step": int(step.value)}
@@ -122,7 +140,7 @@ def save_checkpoint(net, path, seed=0):
     st = get_state(net)
     with open(path, "wb") as f:
         f.write(CKPT_MAGIC)
-        f.write(np.array([NPARAMS, st["step"]], dtype="<i8").tobytes())
+        f.write(np.array([net.nparams, st["step"]], dtype="<i8").tobytes())
         f.write(np.array([seed], dtype="<u8").tobytes())
         for k in ("params", "adam_m", "adam_v"):
             f.write(st[k].astype("<f4").tobytes())
@@ -134,10 +152,11 @@ def load_checkpoint(net, path):
         if f.read(8) != CKPT_MAGIC:
             raise ValueError("not an mrs checkpoint")
         n, step = np.frombuffer(f.read(16), dtype="<i8")
-        if n != NPARAMS:
-            raise ValueError(f"checkpoint has {n} parameters, expected {NPARAMS}")
+        if n != net.nparams:
+            raise ValueError(f"checkpoint has {n} parameters, expected {net.nparams}")
         seed = int(np.frombuffer(f.read(8), dtype="<u8")[0])
-        arrs = [np.frombuffer(f.read(4 * NPARAMS), dtype="<f4").astype(np.float32) for _ in range(3)]
+        arrs = [np.frombuffer(f.read(4 * net.nparams), dtype="<f4").astype(np.float32)
+                for _ in range(3)]
     set_state(net, {"params": arrs[0], "adam_m": arrs[1], "adam_v": arrs[2], "step": int(step)})
     return seed
 
