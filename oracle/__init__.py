@@ -8,6 +8,8 @@ import it.  The product path never routes through it.
 * `render`, `lbvh`, `cast`, `philox*`: ctypes wrappers over `orc_pt.c`, a plain
   C path tracer compiled with -ffp-contract=off (see that file's header).
 * `cnn`: the fusion network forward/backward, loss and Adam in float64 numpy.
+* `rdn`: the method's own two-encoder fusion network (Sec. 4) forward in
+  float64 numpy.
 * `metrics`: linear->sRGB (Eq. cvt_color), RelMSE and PSNR (Sec. 5), average
   spp (Sec. 5.1), box downsampling and the fallback gate.
 

@@ -1,0 +1,207 @@
+"""Float64 oracle of the method's own fusion network (Sec. 4, "two-encoder-one-
+decoder" network of Fig. network): forward pass.
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
+
+Steps, in the order and notation of Sec. 4:
+  F_LRHS   = H_lrhs(I_LRHS)                      3x3 conv, 3 -> 64, at LR
+  F0_HRLS  = H_hrls(I_HRLS)                      3x3 conv, C_h -> 64, at HR
+  F_HRLS   = DSF^D(... DSF^1(F0_HRLS))           D = log2(s) deshuffle layers, alpha = 2
+  F_0      = fuse(F_LRHS || F_HRLS)              1x1 conv, 64 + 64 s^2 -> 64
+  F_g      = RDB_B(... RDB_1(F_{g-1})) + F_{g-1} G = 3 residual dense groups of B = 5 blocks
+  F_DF     = F_G + F_0                           (Eq. F_DF)
+  I_SR     = H_Rec(UP(F_DF))                     UP: D x (3x3 conv 64 -> 256, shuffle x2);
+                                                 H_Rec: 3x3 conv 64 -> 3
+Every conv is followed by a ReLU except H_Rec, the last (Sec. 4, "Implement
+details"); all kernels are 3x3 except the 1x1 fuse conv; 64 feature channels.
+
+Readings (the paper does not fix these):
+* I_HRLS = HRLS RGB, albedo, normal (C_h = 9); with the extra layers, diffuse,
+  specular and log(1 + variance) follow (C_h = 18).
+* DSF is a pure rearrangement (pixel unshuffle, no weights): (H, W, C) ->
+  (H/2, W/2, 4C) with out channel 4c + 2 dy + dx = in[2y + dy, 2x + dx, c],
+  the channel order of torch's pixel_unshuffle; the shuffle of UP is its
+  inverse (torch's pixel_shuffle order).
+* An RDB has 4 convs, all 3x3 with 64 outputs: three dense layers, each over
+  the concatenation [F_in, F_1, ..., F_{c-1}] (64 c channels, in that order),
+  and a local-fusion conv over [F_in, F_1, F_2, F_3] (256 channels); with the
+  ReLU of every conv, RDB(F_in) = F_in + ReLU(fusion).
+* Eq. F_DF adds F_0 (the text says F_LRHS; the equation is taken), and the
+  equation's "RDB_1" inside the RDG chain is read as RDG_1.
+* No image-level skip: I_SR is the output of H_Rec.
+
+Parameter layout (flat): for each conv in the order above (H_lrhs, H_hrls,
+fuse, then per RDG, per RDB, convs 1-4, then the D upsampling convs, H_Rec),
+the weight [Cout][k][k][Cin] followed by the bias [Cout].
+
+Pins (tests/test_oracle_rdn.py): deshuffle / shuffle equal torch's
+pixel_unshuffle / pixel_shuffle; the 1x1 conv equals brute-force loops; an
+identity-kernel network gives I_SR = (1 + 2^G) * nearest_up_s(I_LRHS) in
+closed form (pins the group and global skips and the shuffle order); scaled
+identity kernels in one RDB give a closed-form factor that a misordered
+concatenation would change; a fuse conv that selects one deshuffled channel
+reproduces that HR pixel of F0_HRLS.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import cnn
+
+C_F = 64
+N_RDG = 3           # G
+N_RDB = 5           # B
+N_CONV = 4          # convs per RDB
+C_LR = 3
+C_HR = 9
+C_HR_EXTRA = 18
+SCALES = (2, 4, 8)
+
+
+def depth(s):
+    if s not in SCALES:
+        raise ValueError(f"scale {s} not in {SCALES}")
+    return {2: 1, 4: 2, 8: 3}[s]
+
+
+def layers_for(s, c_hr=C_HR):
+    """[(name, k, cin, cout)] in forward (= parameter) order."""
+    L = [("H_lrhs", 3, C_LR, C_F), ("H_hrls", 3, c_hr, C_F), ("fuse", 1, C_F + C_F * s * s, C_F)]
+    for g in range(N_RDG):
+        for b in range(N_RDB):
+            for c in range(1, N_CONV + 1):
+                L.append((f"rdg{g}.rdb{b}.conv{c}", 3, C_F * c, C_F))
+    for d in range(depth(s)):
+        L.append((f"up{d}", 3, C_F, 4 * C_F))
+    L.append(("H_rec", 3, C_F, 3))
+    return L
+
+
+def layer_offsets(s, c_hr=C_HR):
+    """[(name, w_off, b_off, k, cin, cout)] into the flat parameter array."""
+    out, o = [], 0
+    for name, k, ci, co in layers_for(s, c_hr):
+        out.append((name, o, o + co * k * k * ci, k, ci, co))
+        o += co * k * k * ci + co
+    return out
+
+
+def nparams(s, c_hr=C_HR):
+    return sum(co * k * k * ci + co for _, k, ci, co in layers_for(s, c_hr))
+
+
+def unpack(params, s, c_hr=C_HR):
+    p = np.asarray(params, dtype=np.float64)
+    if p.size != nparams(s, c_hr):
+        raise ValueError(f"{p.size} parameters: expected {nparams(s, c_hr)}")
+    return [(p[wo:bo].reshape(co, k, k, ci), p[bo:bo + co])
+            for _, wo, bo, k, ci, co in layer_offsets(s, c_hr)]
+
+
+def pack(layers):
+    return np.concatenate([np.concatenate([w.ravel(), b.ravel()]) for w, b in layers])
+
+
+def conv1x1(x, w, b):
+    """out[n,y,x,o] = b[o] + sum_c in[n,y,x,c] * w[o,0,0,c]."""
+    return np.asarray(x, np.float64) @ w[:, 0, 0, :].T + b
+
+
+def deshuffle(x):
+    """DSF with alpha = 2: (N, H, W, C) -> (N, H/2, W/2, 4C),
+    out[n, y, x, 4c + 2dy + dx] = in[n, 2y + dy, 2x + dx, c]."""
+    N, H, W, C = x.shape
+    t = x.reshape(N, H // 2, 2, W // 2, 2, C)          # n, y, dy, x, dx, c
+    return t.transpose(0, 1, 3, 5, 2, 4).reshape(N, H // 2, W // 2, 4 * C)
+
+
+def shuffle(x):
+    """Inverse of deshuffle (ESPCN pixel shuffle, x2): (N, h, w, 4C) ->
+    (N, 2h, 2w, C), out[n, 2y + dy, 2x + dx, c] = in[n, y, x, 4c + 2dy + dx]."""
+    N, h, w, C4 = x.shape
+    C = C4 // 4
+    t = x.reshape(N, h, w, C, 2, 2)                     # n, y, x, c, dy, dx
+    return t.transpose(0, 1, 4, 2, 5, 3).reshape(N, 2 * h, 2 * w, C)
+
+
+def relu(x):
+    return np.maximum(x, 0.0)
+
+
+def hr_input(hrls, albedo, normal, extra=None):
+    """I_HRLS as network input: RGB, albedo, normal (+ diffuse, specular,
+    log(1 + variance) when the extra layers are given)."""
+    parts = [hrls, albedo, normal] + ([cnn.extra_input(extra)] if extra is not None else [])
+    return np.concatenate([np.asarray(a, np.float64) for a in parts], axis=-1)
+
+
+def rdb(F_in, convs):
+    """One residual dense block: convs = [(w, b)] x 4."""
+    feats = [F_in]
+    for w, b in convs[:3]:
+        feats.append(relu(cnn.conv3x3(np.concatenate(feats, axis=-1), w, b)))
+    return F_in + relu(cnn.conv3x3(np.concatenate(feats, axis=-1), *convs[3]))
+
+
+def forward(params, lrhs, hrls, albedo, normal, s, extra=None, keep=False):
+    """I_SR [N, s h, s w, 3] from LRHS [N, h, w, 3] and the HRLS buffers
+    [N, s h, s w, 3] (extra [N, s h, s w, 9] for the 18-channel HRLS input)."""
+    c_hr = C_HR_EXTRA if extra is not None else C_HR
+    L = unpack(params, s, c_hr)
+    D = depth(s)
+    acts = {}
+    F_lr = relu(cnn.conv3x3(np.asarray(lrhs, np.float64), *L[0]))
+    F_h = relu(cnn.conv3x3(hr_input(hrls, albedo, normal, extra), *L[1]))
+    acts["F_LRHS"], acts["F0_HRLS"] = F_lr, F_h
+    for _ in range(D):
+        F_h = deshuffle(F_h)
+    F0 = relu(conv1x1(np.concatenate([F_lr, F_h], axis=-1), *L[2]))
+    acts["F_0"] = F0
+    F = F0
+    i = 3
+    for g in range(N_RDG):
+        F_prev = F
+        for b in range(N_RDB):
+            F = rdb(F, L[i:i + N_CONV])
+            i += N_CONV
+        F = F + F_prev
+        acts[f"F_{g + 1}"] = F
+    U = F + F0
+    acts["F_DF"] = U
+    for d in range(D):
+        U = shuffle(relu(cnn.conv3x3(U, *L[i])))
+        i += 1
+        acts[f"U_{d + 1}"] = U
+    y = cnn.conv3x3(U, *L[i])
+    return (y, acts) if keep else y
+
+
+def flops_per_lr_pixel(s, c_hr=C_HR):
+    """Multiply-adds x 2 of one forward pass per LR pixel (H_hrls and H_Rec run
+    at HR, the i-th upsampling conv at 4^i LR pixels)."""
+    total = 0
+    up = 0
+    for name, k, ci, co in layers_for(s, c_hr):
+        f = 2 * k * k * ci * co
+        if name in ("H_hrls", "H_rec"):
+            f *= s * s
+        elif name.startswith("up"):
+            f *= 4 ** up
+            up += 1
+        total += f
+    return total
+
+
+def kaiming(seed, s, c_hr=C_HR, fusion_damp=1.0):
+    """Kaiming-normal weights (std sqrt(2 / (k^2 Cin))), zero biases; the
+    RDBs' local-fusion convs scaled by fusion_damp (each RDB adds its fusion
+    output to its input, so undamped random blocks grow activations
+    geometrically through the 15 blocks)."""
+    rng = np.random.default_rng(np.random.SeedSequence([0x72646E, int(seed), s, c_hr]))
+    layers = []
+    for name, k, ci, co in layers_for(s, c_hr):
+        w = rng.normal(0, np.sqrt(2.0 / (k * k * ci)), (co, k, k, ci))
+        if name.endswith(f"conv{N_CONV}"):
+            w = w * fusion_damp
+        layers.append((w, np.zeros(co)))
+    return pack(layers)

@@ -1,0 +1,179 @@
+"""Pins of the oracle of the method's own fusion network (Sec. 4): the
+rearrangements against torch, the 1x1 conv by brute force, and closed forms
+of identity-kernel networks that fix the skips and the dense concatenation."""
+import numpy as np
+import pytest
+
+from oracle import cnn, rdn
+
+
+def test_param_count_and_flops_by_hand():
+    # H_lrhs 1,792 + H_hrls 5,248 + fuse 69,696 + 15 RDBs x 368,896
+    # + 2 upsampling convs x 147,712 + H_rec 1,731 (x4, 9 HRLS channels)
+    assert rdn.nparams(4) == 5_907_331
+    assert rdn.nparams(2) == 5_907_331 - 147_712 - 64 * 64 * 12
+    # per LR pixel: 3,456 + 16 x 10,368 + 139,264 + 15 x 737,280
+    # + (1 + 4) x 294,912 + 16 x 3,456
+    assert rdn.flops_per_lr_pixel(4) == 12_897_664
+    names = [n for n, *_ in rdn.layers_for(8)]
+    assert names[:3] == ["H_lrhs", "H_hrls", "fuse"] and names[-1] == "H_rec"
+    assert len(names) == 3 + 60 + 3 + 1
+
+
+@pytest.mark.parametrize("C", [1, 5])
+def test_deshuffle_and_shuffle_match_torch(C):
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(C)
+    x = rng.normal(size=(2, 8, 6, C))
+    t = torch.from_numpy(x).permute(0, 3, 1, 2)
+    want = torch.nn.functional.pixel_unshuffle(t, 2).permute(0, 2, 3, 1).numpy()
+    got = rdn.deshuffle(x)
+    assert got.shape == (2, 4, 3, 4 * C) and np.array_equal(got, want)
+    y = rng.normal(size=(2, 3, 5, 4 * C))
+    ty = torch.from_numpy(y).permute(0, 3, 1, 2)
+    want = torch.nn.functional.pixel_shuffle(ty, 2).permute(0, 2, 3, 1).numpy()
+    assert np.array_equal(rdn.shuffle(y), want)
+    assert np.array_equal(rdn.shuffle(rdn.deshuffle(x)), x)
+
+
+@pytest.mark.parametrize("s", [2, 4, 8])
+def test_stacked_deshuffle_index(s):
+    # D stacked stride-2 deshuffles: channel k = c * s^2 + sum over steps d of
+    # (2 dy_d + dx_d) * 4^(D - d) reads HR pixel (s y + sum dy_d 2^(d-1), ...)
+    D = rdn.depth(s)
+    rng = np.random.default_rng(s)
+    x = rng.normal(size=(1, 2 * s, 3 * s, 2))
+    z = x
+    for _ in range(D):
+        z = rdn.deshuffle(z)
+    for k in range(z.shape[-1]):
+        c, oy, ox = k >> (2 * D), 0, 0
+        for d in range(1, D + 1):
+            pair = (k >> (2 * (D - d))) & 3
+            oy += (pair >> 1) << (d - 1)
+            ox += (pair & 1) << (d - 1)
+        assert np.array_equal(z[0, :, :, k], x[0, oy::s, ox::s, c])
+
+
+def test_conv1x1_equals_brute_force():
+    rng = np.random.default_rng(0)
+    x = rng.normal(size=(1, 3, 2, 5))
+    w = rng.normal(size=(4, 1, 1, 5))
+    b = rng.normal(size=4)
+    got = rdn.conv1x1(x, w, b)
+    for yy in range(3):
+        for xx in range(2):
+            for o in range(4):
+                acc = b[o] + sum(x[0, yy, xx, c] * w[o, 0, 0, c] for c in range(5))
+                assert abs(got[0, yy, xx, o] - acc) <= 1e-12
+
+
+def _zero_layers(s, c_hr=rdn.C_HR):
+    return [(np.zeros((co, k, k, ci)), np.zeros(co)) for _, k, ci, co in rdn.layers_for(s, c_hr)]
+
+
+def _inputs(rng, s, h=3, w=4):
+    lr = rng.uniform(0, 2, (1, h, w, 3))
+    H, W = h * s, w * s
+    return (lr, rng.uniform(0, 2, (1, H, W, 3)), rng.uniform(0, 1, (1, H, W, 3)),
+            rng.uniform(-1, 1, (1, H, W, 3)))
+
+
+@pytest.mark.parametrize("s", [2, 4, 8])
+def test_identity_network_closed_form(s):
+    # identity kernels carry the LRHS RGB through H_lrhs, the fuse conv, the
+    # upsampling convs (nearest-neighbour through the shuffle) and H_Rec; zero
+    # RDBs are identities, each RDG doubles its input (group skip) and Eq. F_DF
+    # adds F_0 once more: I_SR = (1 + 2^3) * nearest_up_s(LRHS)
+    L = _zero_layers(s)
+    idx = {n: i for i, (n, *_) in enumerate(rdn.layers_for(s))}
+    for c in range(3):
+        L[idx["H_lrhs"]][0][c, 1, 1, c] = 1.0
+        L[idx["fuse"]][0][c, 0, 0, c] = 1.0
+        L[idx["H_rec"]][0][c, 1, 1, c] = 1.0
+        for d in range(rdn.depth(s)):
+            for sub in range(4):
+                L[idx[f"up{d}"]][0][4 * c + sub, 1, 1, c] = 1.0
+    rng = np.random.default_rng(s)
+    lr, hr, alb, nrm = _inputs(rng, s)
+    y = rdn.forward(rdn.pack(L), lr, hr, alb, nrm, s)
+    nn = np.repeat(np.repeat(lr, s, axis=1), s, axis=2)
+    assert np.allclose(y, 9.0 * nn, rtol=1e-15, atol=0)
+
+
+def test_rdb_dense_concatenation_closed_form():
+    # conv1 = 2 F_in, conv2 = 3 F_1 (second block), conv3 = F_2 / 2 (third),
+    # fusion = F_in + 10 F_1 + 100 F_2 + 1000 F_3 = 3621 F_in, so the block
+    # returns 3622 F_in; any other concatenation order gives another factor
+    def ident(cin, blocks):
+        w = np.zeros((64, 3, 3, cin))
+        for blk, a in blocks.items():
+            for o in range(64):
+                w[o, 1, 1, 64 * blk + o] = a
+        return w, np.zeros(64)
+
+    convs = [ident(64, {0: 2.0}), ident(128, {1: 3.0}), ident(192, {2: 0.5}),
+             ident(256, {0: 1.0, 1: 10.0, 2: 100.0, 3: 1000.0})]
+    F = np.random.default_rng(1).uniform(0, 1, (1, 3, 5, 64))
+    assert np.allclose(rdn.rdb(F, convs), 3622.0 * F, rtol=1e-14, atol=0)
+
+
+@pytest.mark.parametrize("s", [2, 4])
+def test_fuse_selects_a_deshuffled_hr_pixel(s):
+    # H_hrls copies the HRLS RGB; the fuse conv picks channel k of F_HRLS for
+    # output 0; the rest is the identity network above with the H_lrhs path
+    # off, so I_SR = 9 * nearest_up_s(that HR sub-pixel of the HRLS red)
+    L = _zero_layers(s)
+    idx = {n: i for i, (n, *_) in enumerate(rdn.layers_for(s))}
+    for c in range(3):
+        L[idx["H_hrls"]][0][c, 1, 1, c] = 1.0
+    D = rdn.depth(s)
+    k = s * s - 1                        # channel 0, last sub-pixel: offset (s-1, s-1)
+    L[idx["fuse"]][0][0, 0, 0, 64 + k] = 1.0
+    L[idx["H_rec"]][0][0, 1, 1, 0] = 1.0
+    for d in range(D):
+        for sub in range(4):
+            L[idx[f"up{d}"]][0][sub, 1, 1, 0] = 1.0
+    rng = np.random.default_rng(7)
+    lr, hr, alb, nrm = _inputs(rng, s)
+    y = rdn.forward(rdn.pack(L), lr, hr, alb, nrm, s)
+    sub = hr[:, s - 1::s, s - 1::s, 0]
+    want = 9.0 * np.repeat(np.repeat(sub, s, axis=1), s, axis=2)
+    assert np.allclose(y[..., 0], want, rtol=1e-15, atol=0)
+    assert not y[..., 1:].any()
+
+
+def test_extra_hrls_layers_with_zero_weights_change_nothing():
+    s = 2
+    rng = np.random.default_rng(3)
+    lr, hr, alb, nrm = _inputs(rng, s)
+    ex = rng.uniform(0, 1, hr.shape[:3] + (9,))
+    p9 = rdn.unpack(rdn.kaiming(0, s, fusion_damp=0.1), s)
+    w = np.zeros((64, 3, 3, 18))
+    w[..., :9] = p9[1][0]
+    p18 = rdn.pack(p9[:1] + [(w, p9[1][1])] + p9[2:])
+    a = rdn.forward(rdn.pack(p9), lr, hr, alb, nrm, s)
+    b = rdn.forward(p18, lr, hr, alb, nrm, s, extra=ex)
+    assert np.array_equal(a, b)
+    # and the extra channels do reach the network when their weights are not zero
+    w[..., 12] = 1.0
+    c = rdn.forward(rdn.pack(p9[:1] + [(w, p9[1][1])] + p9[2:]), lr, hr, alb, nrm, s, extra=ex)
+    assert not np.allclose(a, c)
+
+
+def test_kaiming_network_is_finite_and_local():
+    # receptive-field check: changing one LRHS pixel changes I_SR only within
+    # the LR receptive field of 1 + 60 + 2 3x3 LR convs (+ the HR-side convs)
+    s = 2
+    rng = np.random.default_rng(4)
+    lr, hr, alb, nrm = _inputs(rng, s, h=40, w=3)
+    p = rdn.kaiming(1, s, fusion_damp=0.1)
+    a = rdn.forward(p, lr, hr, alb, nrm, s)
+    lr2 = lr.copy()
+    lr2[0, 0, 0, 0] += 1.0
+    b = rdn.forward(p, lr2, hr, alb, nrm, s)
+    assert np.isfinite(a).all()
+    rows = np.nonzero(np.abs(a - b).max(axis=(0, 2, 3)) > 0)[0]
+    # LR rows 0 .. 62 at most (61 LR 3x3 convs before the upsampling conv, one
+    # at LR in UP), one more HR row each for the x2 part and H_rec
+    assert rows.max() <= s * 63 + 2
