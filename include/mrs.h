@@ -383,7 +383,10 @@ mrs_status mrs_gate_async(const float* fused, const float* lrhs, const float* pl
  * [cout][3][3][cin], b HOST float [cout], out device float [N][H][W][cout];
  * relu != 0 applies max(0, .).  precision MRS_PREC_FP32 computes in FP32;
  * MRS_PREC_BF16 / MRS_PREC_FP8 round x and w to the operand type and
- * accumulate in FP32 on the tensor cores (cin <= 64, cout <= 64). */
+ * accumulate in FP32 on the tensor cores (cout <= 64; cin <= 64 for FP8,
+ * cin <= 1024 for BF16: past 64 input channels the conv runs as one launch
+ * per 64-channel chunk accumulating into `out`, which must then be 16-byte
+ * aligned). */
 mrs_status mrs_conv3x3(const float* x, int32_t N, int32_t H, int32_t W, int32_t cin,
                        int32_t cout, const float* w, const float* b, int32_t relu,
                        int32_t precision, float* out, void* stream);
@@ -415,6 +418,53 @@ mrs_status mrs_net_set_loss(mrs_net net, int32_t loss, float beta);
 mrs_status mrs_conv3x3_wgrad(const float* x, const float* dy, int32_t N, int32_t H, int32_t W,
                              int32_t cin, int32_t cout, int32_t precision, float* dw, float* db,
                              void* stream);
+
+/* ------------------------------------------------------------------------
+ * The method's own fusion network (Sec. 4, Fig. network): a two-encoder-one-
+ * decoder network that works at the LRHS resolution.
+ *   F_LRHS = ReLU(H_lrhs(I_LRHS))            3x3 conv 3 -> 64 at h x w
+ *   F0_HRLS = ReLU(H_hrls(I_HRLS))           3x3 conv C_h -> 64 at H x W
+ *   F_HRLS = DSF^D(F0_HRLS)                  D = log2(scale) deshuffle layers
+ *                                            (stride 2, no weights)
+ *   F_0 = ReLU(fuse(F_LRHS || F_HRLS))       1x1 conv 64 + 64 scale^2 -> 64
+ *   F_g = RDB_5(...RDB_1(F_{g-1})) + F_{g-1} g = 1..3 (Eq. RDG)
+ *   F_DF = F_3 + F_0                         (Eq. F_DF)
+ *   I_SR = H_Rec(UP(F_DF))                   UP: D x (3x3 conv 64 -> 256 +
+ *                                            ReLU, shuffle x2); H_Rec 3x3
+ *                                            conv 64 -> 3
+ * A residual dense block RDB has three dense 3x3 convs (64 c -> 64 over the
+ * concatenation [F_in, F_1 .. F_{c-1}], ReLU) and a 3x3 local-fusion conv
+ * (256 -> 64, ReLU); RDB(F_in) = F_in + fusion.  I_HRLS = HRLS RGB, albedo,
+ * normal (C_h = 9) or those plus diffuse, specular and log(1 + variance)
+ * (C_h = 18).  Deshuffle channel 4c + 2dy + dx holds input channel c of
+ * pixel (2y + dy, 2x + dx); the shuffle is its inverse.
+ * Parameters (float32, HOST): for each conv in the order above (H_lrhs,
+ * H_hrls, fuse, per group per block convs 1-4, the D upsampling convs,
+ * H_Rec) the weight [Cout][k][k][Cin] then the bias [Cout]; count from
+ * mrs_rdn_nparams.
+ * ------------------------------------------------------------------------ */
+typedef struct mrs_rdn_s* mrs_rdn;
+/* Parameter count for scale in {2, 4, 8} and hr_channels in {9, 18}. */
+mrs_status mrs_rdn_nparams(int32_t scale, int32_t hr_channels, int64_t* n);
+/* Copies the parameters in (FP32 master copy and packed BF16 tensor-core
+ * weights); n_params must equal mrs_rdn_nparams(scale, hr_channels). */
+mrs_status mrs_rdn_create(int32_t scale, int32_t hr_channels, const float* params,
+                          int64_t n_params, mrs_rdn* out);
+mrs_status mrs_rdn_free(mrs_rdn rdn);
+/* I_SR of N frames.  lrhs device [N][H/scale][W/scale][3]; hrls, albedo,
+ * normal device [N][H][W][3]; extra device [N][H][W][9] (diffuse, specular,
+ * variance as mrs_render_layers writes them) exactly when hr_channels = 18,
+ * else NULL; out device [N][H][W][3].  precision MRS_PREC_FP32 (SIMT,
+ * reference precision) or MRS_PREC_BF16 (tensor cores: BF16 activations and
+ * weights, FP32 accumulation, a conv over more than 64 input channels
+ * accumulates its 64-channel chunks in FP32).  Workspace lives in the handle
+ * (grown on demand).  Limit: N*H*W <= 2^26. */
+mrs_status mrs_rdn_fuse(mrs_rdn rdn, const float* lrhs, const float* hrls, const float* albedo,
+                        const float* normal, const float* extra, int32_t N, int32_t H, int32_t W,
+                        int32_t precision, float* out, void* stream);
+/* MRS_ERR_TIMEOUT (and the error word cleared) if a tensor-core wait of an
+ * earlier mrs_rdn_fuse gave up; synchronises the device. */
+mrs_status mrs_rdn_check(mrs_rdn rdn);
 
 #ifdef __cplusplus
 }

@@ -9,3 +9,5 @@ from .render import (PROFILE_KERNELS, RenderContext, Scene, philox_uniforms, pro
                      profile_read, render, render_stats)
 from .fusion import (NPARAMS, NPARAMS_EXTRA, Net, conv3x3, conv3x3_wgrad, gate, gate_async, get_grads, get_state, image_metrics,  # noqa: F401
                      load_checkpoint, save_checkpoint, set_state, train_step)
+from .rdn import RDN  # noqa: F401
+from .rdn import nparams as rdn_nparams  # noqa: F401

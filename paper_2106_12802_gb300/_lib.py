@@ -60,6 +60,11 @@ SIGS = {
     "mrs_conv3x3": [P, I32, I32, I32, I32, I32, P, P, I32, I32, P, P],
     "mrs_conv3x3_wgrad": [P, P, I32, I32, I32, I32, I32, I32, P, P, P],
     "mrs_net_set_loss": [P, I32, F32],
+    "mrs_rdn_nparams": [I32, I32, P],
+    "mrs_rdn_create": [I32, I32, P, I64, P],
+    "mrs_rdn_free": [P],
+    "mrs_rdn_fuse": [P, P, P, P, P, P, I32, I32, I32, I32, P, P],
+    "mrs_rdn_check": [P],
     "mrs_selftest_wait_timeout": [I32, P],
     "mrs_status_string": [I32],
     "mrs_last_error": [],

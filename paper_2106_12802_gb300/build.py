@@ -23,6 +23,7 @@ UNITS = {
     "pt.cu": ["--fmad=false"],
     "conv_tc.cu": [],
     "fuse.cu": [],
+    "rdn.cu": [],
 }
 
 

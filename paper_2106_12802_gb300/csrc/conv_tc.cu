@@ -293,8 +293,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     const long long T = (long long)a.N * XB * a.H;
     const long long f0 = T * blockIdx.x / gridDim.x, f1 = T * (blockIdx.x + 1) / gridDim.x;
     const bool bf_out = a.mode == TC_RELU_BF16 || a.mode == TC_RESID_BF16 ||
-                        a.mode == TC_LIN_BF16 || a.mode == TC_MASK_BF16;
-    const bool loads_res = a.mode == TC_RESID_BF16 || a.mode == TC_MASK_BF16;
+                        a.mode == TC_LIN_BF16 || a.mode == TC_MASK_BF16 ||
+                        a.mode == TC_RESRELU_BF16;
+    const bool loads_res = a.mode == TC_RESID_BF16 || a.mode == TC_MASK_BF16 ||
+                           a.mode == TC_RESRELU_BF16;
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < stages; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
@@ -478,6 +480,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                     float o[16];
 #pragma unroll
                     for (int e = 0; e < 16; ++e) o[e] = v[e] + sBias[c0 + e];
+                    if (a.acc_in && valid) {
+                        const float4* ap = (const float4*)(a.acc_in + p * 64 + c0);
+#pragma unroll
+                        for (int i4 = 0; i4 < 4; ++i4) {
+                            float4 t = ap[i4];
+                            o[4 * i4] += t.x; o[4 * i4 + 1] += t.y;
+                            o[4 * i4 + 2] += t.z; o[4 * i4 + 3] += t.w;
+                        }
+                    }
                     if (a.mode == TC_RELU_BF16) {
 #pragma unroll
                         for (int e = 0; e < 16; ++e) o[e] = fmaxf(o[e], 0.0f);
@@ -493,7 +504,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                                 if (!(f.y > 0.0f)) o[8 * jj + 2 * e + 1] = 0.0f;
                             }
                         }
-                    } else if (a.mode == TC_RESID_BF16) {
+                    } else if (a.mode == TC_RESID_BF16 || a.mode == TC_RESRELU_BF16) {
+                        const bool rl = a.mode == TC_RESRELU_BF16;
 #pragma unroll
                         for (int jj = 0; jj < 2; ++jj) {
                             uint4 u = *(const uint4*)(srow + sw128(j, c0 / 8 + jj));
@@ -501,8 +513,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                             for (int e = 0; e < 4; ++e) {
                                 float2 f = __bfloat1622float2(h2[e]);
-                                o[8 * jj + 2 * e] = f.x + o[8 * jj + 2 * e];
-                                o[8 * jj + 2 * e + 1] = f.y + o[8 * jj + 2 * e + 1];
+                                float o0 = o[8 * jj + 2 * e], o1 = o[8 * jj + 2 * e + 1];
+                                if (rl) { o0 = fmaxf(o0, 0.0f); o1 = fmaxf(o1, 0.0f); }
+                                o[8 * jj + 2 * e] = f.x + o0;
+                                o[8 * jj + 2 * e + 1] = f.y + o1;
                             }
                         }
                     }
@@ -533,12 +547,35 @@ __global__ void __launch_bounds__(kThreads, 1)
                             float* op = (float*)a.out + p * 3;
                             for (int c = 0; c < 3; ++c) op[c] = (v[c] + sBias[c]) + up[c];
                         }
+                    } else if (a.cout == 64 && ((uintptr_t)a.out & 15) == 0) {
+                        // full 64-channel rows: 16-byte accesses, optional
+                        // partial-sum input (may alias the output: same
+                        // thread, same elements)
+                        float4* op = (float4*)((float*)a.out + p * 64 + c0);
+                        const float4* ap = a.acc_in ? (const float4*)(a.acc_in + p * 64 + c0) : nullptr;
+#pragma unroll
+                        for (int i4 = 0; i4 < 4; ++i4) {
+                            float4 t = make_float4(v[4 * i4] + sBias[c0 + 4 * i4],
+                                                   v[4 * i4 + 1] + sBias[c0 + 4 * i4 + 1],
+                                                   v[4 * i4 + 2] + sBias[c0 + 4 * i4 + 2],
+                                                   v[4 * i4 + 3] + sBias[c0 + 4 * i4 + 3]);
+                            if (ap) {
+                                float4 u = ap[i4];
+                                t.x += u.x; t.y += u.y; t.z += u.z; t.w += u.w;
+                            }
+                            if (a.relu) {
+                                t.x = fmaxf(t.x, 0.0f); t.y = fmaxf(t.y, 0.0f);
+                                t.z = fmaxf(t.z, 0.0f); t.w = fmaxf(t.w, 0.0f);
+                            }
+                            op[i4] = t;
+                        }
                     } else {
                         float* op = (float*)a.out + p * a.cout;
 #pragma unroll
                         for (int e = 0; e < 16; ++e) {
                             if (c0 + e < a.cout) {
                                 float o = v[e] + sBias[c0 + e];
+                                if (a.acc_in) o += a.acc_in[p * a.cout + c0 + e];
                                 op[c0 + e] = a.relu ? fmaxf(o, 0.0f) : o;
                             }
                         }
@@ -633,6 +670,27 @@ mrs_status tc_make_act_map(CUtensorMap* m, const void* ptr, int N, int H, int W,
     return MRS_OK;
 }
 
+mrs_status tc_make_view_map(CUtensorMap* m, const void* ptr, int N, int H, int W,
+                            long long px_stride, long long row_stride, long long img_stride,
+                            int box_px)
+{
+    auto fn = encode_fn();
+    if (!fn) { set_error("cuTensorMapEncodeTiled unavailable"); return MRS_ERR_CUDA; }
+    if (((uintptr_t)ptr & 15) || (px_stride & 15) || (row_stride & 15) || (img_stride & 15)) {
+        set_error("tc_make_view_map: base and strides must be multiples of 16 bytes");
+        return MRS_ERR_ARG;
+    }
+    cuuint64_t dims[4] = {64, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)N};
+    cuuint64_t strides[3] = {(cuuint64_t)px_stride, (cuuint64_t)row_stride, (cuuint64_t)img_stride};
+    cuuint32_t box[4] = {64, (cuuint32_t)box_px, 1, 1};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(ptr), dims, strides,
+                    box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) { set_error("cuTensorMapEncodeTiled(view) failed: %d", (int)r); return MRS_ERR_CUDA; }
+    return MRS_OK;
+}
+
 mrs_status tc_make_w_map(CUtensorMap* m, const void* ptr, int rows, int nout, int operand)
 {
     auto fn = encode_fn();
@@ -686,6 +744,10 @@ mrs_status tc_wait_selftest(long long limit_cycles, int* gave_up, cudaStream_t s
 
 mrs_status tc_conv3x3(const TcConvArgs& a, cudaStream_t st)
 {
+    if (a.acc_in && (((uintptr_t)a.acc_in & 15) || a.operand != TC_BF16)) {
+        set_error("tc_conv3x3: acc_in must be 16-byte aligned, with bf16 operands");
+        return MRS_ERR_ARG;
+    }
     if (a.nout == 64) return a.operand == TC_BF16 ? launch<64, TC_BF16>(a, st) : launch<64, TC_FP8>(a, st);
     if (a.nout == 16) return a.operand == TC_BF16 ? launch<16, TC_BF16>(a, st) : launch<16, TC_FP8>(a, st);
     set_error("tc_conv3x3: nout must be 64 or 16");

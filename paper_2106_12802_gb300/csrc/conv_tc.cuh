@@ -18,6 +18,7 @@ enum TcMode : int {
     TC_PLAIN_F32 = 3,   // out_f32[p][cout] = acc + b, optional relu
     TC_LIN_BF16 = 4,    // out_bf16[p][64] = acc + b
     TC_MASK_BF16 = 5,   // out_bf16[p][64] = mask[p] > 0 ? acc + b : 0   (mask via tmap_res)
+    TC_RESRELU_BF16 = 6,// out_bf16[p][64] = res[p] + relu(acc + b)
 };
 
 enum TcOperand : int { TC_BF16 = 0, TC_FP8 = 1 };
@@ -43,6 +44,12 @@ struct TcConvArgs {
     // TC_RELU_BF16 / TC_RESID_BF16 with fp8 operands: also emit the fp8 copy
     void* out_fp8;
     float out_fp8_inv_scale;
+    // optional FP32 partial sum [p][64] (stride 64 floats; stride cout for
+    // TC_PLAIN_F32) added to acc before the epilogue: a convolution over more
+    // than 64 input channels is a chain of launches, one per 64-channel
+    // chunk, each adding its chunk's contribution (TC_PLAIN_F32 with acc_in =
+    // out) and the last applying the layer's epilogue.  BF16 operands only.
+    const float* acc_in;
 };
 
 // Box widths (pixels): A operands are loaded as four 32-pixel boxes per input
@@ -54,6 +61,14 @@ constexpr int kOutBox = 120;
 // bytes in bf16, 64 in fp8): box = box_px pixels of one image row.
 mrs_status tc_make_act_map(CUtensorMap* m, const void* ptr, int N, int H, int W, int operand,
                            int box_px = 128);
+// Tensor map for a strided view of a bf16 activation tensor: element (x, y, n)
+// of the view is the 64-channel row at ptr + x * px_stride + y * row_stride +
+// n * img_stride (bytes, multiples of 16).  Views select a sub-pixel grid of
+// a larger image (a deshuffle chunk as an A operand, or a shuffle target as
+// an output) without moving data.
+mrs_status tc_make_view_map(CUtensorMap* m, const void* ptr, int N, int H, int W,
+                            long long px_stride, long long row_stride, long long img_stride,
+                            int box_px);
 // Tensor map for packed weights [rows][64 (bf16) | 64 (fp8)].
 mrs_status tc_make_w_map(CUtensorMap* m, const void* ptr, int rows, int nout, int operand);
 

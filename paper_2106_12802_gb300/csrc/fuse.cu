@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "conv_tc.cuh"
+#include "fuse.cuh"
 
 namespace mrs {
 namespace {
@@ -158,12 +159,13 @@ __global__ void k_input_q(const float* lrhs, const float* hrls, const float* alb
 // block = 16 x 8 output pixels, 16 output channels (grid.z over channel groups);
 // input channels staged through shared memory 4 at a time with a 1-pixel halo
 constexpr int kTX = 16, kTY = 8, kCT = 16, kCC = 4;
-enum SimtMode { SIMT_PLAIN = 0, SIMT_RESID = 1, SIMT_FINAL = 2, SIMT_MASK = 3 };
-
+// x [P][xs] (first cin channels read), out / res [P][os] / [P][rs] (first
+// cout written / read): strides let a layer read a prefix of a concatenation
+// buffer and write into a channel slice of another
 __global__ void __launch_bounds__(kTX * kTY)
-    k_conv_simt(const float* __restrict__ x, int cin, const float* __restrict__ w,
+    k_conv_simt(const float* __restrict__ x, int cin, int xs, const float* __restrict__ w,
                 const float* __restrict__ b, int cout, int mode, int relu,
-                const float* __restrict__ res, float* __restrict__ out,
+                const float* __restrict__ res, int rs, float* __restrict__ out, int os,
                 const float* __restrict__ lrhs, int H, int W, int s)
 {
     __shared__ float sin_[kTY + 2][kTX + 2][kCC];
@@ -172,7 +174,7 @@ __global__ void __launch_bounds__(kTX * kTY)
     const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
     const int n = blockIdx.z / ((cout + kCT - 1) / kCT);
     const int o0 = (blockIdx.z % ((cout + kCT - 1) / kCT)) * kCT;
-    const float* xin = x + (size_t)n * H * W * cin;
+    const float* xin = x + (size_t)n * H * W * xs;
     float acc[kCT];
 #pragma unroll
     for (int o = 0; o < kCT; ++o) acc[o] = 0.0f;
@@ -182,7 +184,7 @@ __global__ void __launch_bounds__(kTX * kTY)
             int gx = x0 + px - 1, gy = y0 + py - 1;
             float v = 0.0f;
             if (gx >= 0 && gx < W && gy >= 0 && gy < H && c0 + c < cin)
-                v = __ldg(xin + ((size_t)gy * W + gx) * cin + c0 + c);
+                v = __ldg(xin + ((size_t)gy * W + gx) * xs + c0 + c);
             sin_[py][px][c] = v;
         }
         for (int i = threadIdx.x; i < 9 * kCC * kCT; i += kTX * kTY) {
@@ -225,21 +227,34 @@ __global__ void __launch_bounds__(kTX * kTY)
     for (int o = 0; o < kCT; ++o) {
         if (o0 + o >= cout) break;
         float v = acc[o] + __ldg(b + o0 + o);
-        if (mode == SIMT_RESID) v = res[p * cout + o0 + o] + v;
-        else if (mode == SIMT_MASK) v = res[p * cout + o0 + o] > 0.0f ? v : 0.0f;
+        if (mode == SIMT_RESID) v = res[p * rs + o0 + o] + v;
+        else if (mode == SIMT_MASK) v = res[p * rs + o0 + o] > 0.0f ? v : 0.0f;
+        else if (mode == SIMT_RESRELU) v = res[p * rs + o0 + o] + fmaxf(v, 0.0f);
         else if (relu) v = fmaxf(v, 0.0f);
-        out[p * cout + o0 + o] = v;
+        out[p * os + o0 + o] = v;
     }
 }
+
+}  // namespace
+
+mrs_status simt_conv3x3(const float* x, int cin, int xs, const float* w, const float* b, int cout,
+                        int mode, int relu, const float* res, int rs, float* out, int os,
+                        const float* lrhs, int N, int H, int W, int s, cudaStream_t st)
+{
+    dim3 grid((W + kTX - 1) / kTX, (H + kTY - 1) / kTY, N * ((cout + kCT - 1) / kCT));
+    MRS_TIMED(PK_CONV_SIMT, st, k_conv_simt<<<grid, kTX * kTY, 0, st>>>(x, cin, xs, w, b, cout, mode, relu, res, rs, out, os, lrhs, H, W, s));
+    MRS_LAUNCHED(1);
+    return cuda_status(cudaGetLastError(), "conv_simt launch");
+}
+
+namespace {
 
 mrs_status conv_simt(const float* x, int cin, const float* w, const float* b, int cout, int mode,
                      int relu, const float* res, float* out, const float* lrhs, int N, int H,
                      int W, int s, cudaStream_t st)
 {
-    dim3 grid((W + kTX - 1) / kTX, (H + kTY - 1) / kTY, N * ((cout + kCT - 1) / kCT));
-    MRS_TIMED(PK_CONV_SIMT, st, k_conv_simt<<<grid, kTX * kTY, 0, st>>>(x, cin, w, b, cout, mode, relu, res, out, lrhs, H, W, s));
-    MRS_LAUNCHED(1);
-    return cuda_status(cudaGetLastError(), "conv_simt launch");
+    return simt_conv3x3(x, cin, cin, w, b, cout, mode, relu, res, cout, out, cout, lrhs, N, H, W,
+                        s, st);
 }
 
 // ---- weight packing ---------------------------------------------------------
@@ -364,6 +379,28 @@ __global__ void k_gate_partial(const float* __restrict__ fused, const float* __r
         __syncthreads();
     }
     if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+// bf16 [P][64] rows of input channels c0 .. c0 + 63 of x [P][cin] (zero past cin)
+__global__ void k_to_operand_chunk(const float* x, size_t P, int cin, int c0, __nv_bfloat16* o)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < P * 64;
+         i += (size_t)gridDim.x * blockDim.x) {
+        size_t p = i / 64;
+        int c = c0 + (int)(i % 64);
+        o[i] = __float2bfloat16_rn(c < cin ? x[p * cin + c] : 0.0f);
+    }
+}
+
+// packed[tap][o][c] of input channels c0 .. c0 + 63 of w [cout][3][3][cin]
+__global__ void k_pack_bf16_chunk(const float* __restrict__ w, int cin, int c0, int cout, int nout,
+                                  __nv_bfloat16* __restrict__ wp)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 9 * nout * 64) return;
+    int c = i % 64, o = (i / 64) % nout, t = i / (64 * nout);
+    float v = (o < cout && c0 + c < cin) ? w[((size_t)o * 9 + t) * cin + c0 + c] : 0.0f;
+    wp[i] = __float2bfloat16_rn(v);
 }
 
 __global__ void k_to_operand(const float* x, size_t P, int cin, void* o, int fp8, float inv)
@@ -973,17 +1010,85 @@ extern "C" mrs_status mrs_gate(const float* fused, const float* lrhs, const floa
     return MRS_OK;
 }
 
+namespace mrs {
+namespace {
+// BF16 3x3 conv over more than 64 input channels: one tensor-core launch per
+// 64-channel chunk, each adding its contribution to the FP32 output (the
+// first with the bias, the last with the ReLU)
+mrs_status conv3x3_chunked(Scratch& S, const float* x, int N, int H, int W, int cin, int cout,
+                           const float* w, const float* b, int relu, float* out, cudaStream_t st)
+{
+    const size_t P = (size_t)N * H * W;
+    const int nch = (cin + 63) / 64;
+    const int nout = cout > 16 ? 64 : 16;
+    const size_t wbytes = (size_t)cout * 9 * cin * 4;
+    const size_t chw = (size_t)9 * 64 * 64 * 2;
+    size_t need = wbytes + 2 * 64 * 4 + nch * chw + P * 128 + 4096;
+    mrs_status rc = S.b.ensure(need);
+    if (rc != MRS_OK) return rc;
+    uint8_t* base = S.b.as<uint8_t>();
+    float* dw = (float*)base;
+    float* db = dw + (size_t)cout * 9 * cin;
+    float* zb = db + 64;
+    uint8_t* q = (uint8_t*)(((uintptr_t)(zb + 64) + 1023) & ~(uintptr_t)1023);
+    __nv_bfloat16* xq = (__nv_bfloat16*)(q + nch * chw);
+    MRS_CHECK(cudaMemsetAsync(db, 0, 128 * 4, st));
+    MRS_CHECK(cudaMemcpyAsync(dw, w, wbytes, cudaMemcpyHostToDevice, st));
+    MRS_CHECK(cudaMemcpyAsync(db, b, cout * 4, cudaMemcpyHostToDevice, st));
+    static int* err = nullptr;
+    if (!err) { MRS_CHECK(cudaMalloc(&err, 4)); MRS_CHECK(cudaMemset(err, 0, 4)); }
+    std::vector<CUtensorMap> wm(nch);
+    for (int j = 0; j < nch; ++j) {
+        k_pack_bf16_chunk<<<(9 * nout * 64 + 255) / 256, 256, 0, st>>>(dw, cin, 64 * j, cout, nout,
+                                                                       (__nv_bfloat16*)(q + j * chw));
+        MRS_LAUNCHED(1);
+        if ((rc = tc_make_w_map(&wm[j], q + j * chw, 9 * nout, nout, TC_BF16)) != MRS_OK) return rc;
+    }
+    CUtensorMap mx;
+    if ((rc = tc_make_act_map(&mx, xq, N, H, W, TC_BF16, kABox)) != MRS_OK) return rc;
+    TcConvArgs a;
+    memset(&a, 0, sizeof(a));
+    a.tmap_x = &mx; a.out = out; a.N = N; a.H = H; a.W = W; a.scale = 1; a.nout = nout;
+    a.cout = cout; a.mode = TC_PLAIN_F32; a.operand = TC_BF16; a.err = err;
+    for (int j = 0; j < nch && rc == MRS_OK; ++j) {
+        // the operand buffer is reused: the previous chunk's conv has read it
+        // by the time this stream-ordered conversion runs
+        k_to_operand_chunk<<<1024, 256, 0, st>>>(x, P, cin, 64 * j, xq);
+        MRS_LAUNCHED(1);
+        a.tmap_w = &wm[j];
+        a.bias = j == 0 ? db : zb;
+        a.acc_in = j == 0 ? nullptr : out;
+        a.relu = j == nch - 1 ? relu : 0;
+        rc = tc_conv3x3(a, st);
+    }
+    if (rc == MRS_OK) rc = cuda_status(cudaStreamSynchronize(st), "conv3x3 sync");
+    int herr = 0;
+    if (rc == MRS_OK) {
+        MRS_CHECK(cudaMemcpy(&herr, err, 4, cudaMemcpyDeviceToHost));
+        if (herr) { cudaMemset(err, 0, 4); set_error("tensor-core conv wait timed out"); return MRS_ERR_TIMEOUT; }
+    }
+    return rc;
+}
+}  // namespace
+}  // namespace mrs
+
 extern "C" mrs_status mrs_conv3x3(const float* x, int32_t N, int32_t H, int32_t W, int32_t cin,
                                   int32_t cout, const float* w, const float* b, int32_t relu,
                                   int32_t precision, float* out, void* stream)
 {
     MRS_ARG(x && w && b && out, "NULL pointer");
     MRS_ARG(N >= 1 && H >= 1 && W >= 1 && cin >= 1 && cout >= 1, "sizes must be >= 1");
-    MRS_ARG(precision == MRS_PREC_FP32 || (cin <= 64 && cout <= 64), "tensor-core conv needs cin, cout <= 64");
+    MRS_ARG(precision == MRS_PREC_FP32 || cout <= 64, "tensor-core conv needs cout <= 64");
+    MRS_ARG(precision == MRS_PREC_FP32 || cin <= 64 || (precision == MRS_PREC_BF16 && cin <= 1024),
+            "tensor-core conv needs cin <= 64 (FP8) or cin <= 1024 (BF16)");
+    MRS_ARG(precision != MRS_PREC_BF16 || cin <= 64 || ((uintptr_t)out & 15) == 0,
+            "out must be 16-byte aligned for cin > 64");
     cudaStream_t st = (cudaStream_t)stream;
     size_t P = (size_t)N * H * W;
     Scratch& S = scratch();
     std::lock_guard<std::mutex> g(S.mu);
+    if (precision == MRS_PREC_BF16 && cin > 64)
+        return conv3x3_chunked(S, x, N, H, W, cin, cout, w, b, relu, out, st);
     size_t wbytes = (size_t)cout * 9 * cin * 4;
     size_t need = wbytes + cout * 4 + 9 * 64 * 64 * 2 + 64 * 4 * 2 + 1024 +
                   (precision == MRS_PREC_FP32 ? 0 : P * 128) + 16;

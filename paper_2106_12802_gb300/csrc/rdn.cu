@@ -1,0 +1,670 @@
+// The method's own fusion network (Sec. 4, "two-encoder-one-decoder"): two
+// shallow encoders (H_lrhs on the LRHS at low resolution, H_hrls on the HRLS
+// and its layers at high resolution), D = log2(s) deshuffle layers that bring
+// the HRLS features down to the LRHS grid, a 1x1 fuse conv, G = 3 residual
+// dense groups of B = 5 blocks (Eqs. RDG, F_DF), shuffle upscaling and H_Rec.
+// Readings: each block has three dense 3x3 convs and a 3x3 local-fusion conv
+// over the 256-channel concatenation, then the local residual; every conv but
+// H_Rec is followed by a ReLU; Eq. F_DF adds F_0; the deshuffle / shuffle
+// channel order is that of pixel_unshuffle / pixel_shuffle (stride 2).
+//
+// FP32 path (reference precision): SIMT convolutions over concatenation
+// buffers ([P][256] per block: F_in, F_1, F_2, F_3 side by side), the fuse conv
+// over an explicitly deshuffled [P][64 + 64 s^2] buffer.
+//
+// BF16 path (tensor cores, conv_tc.cu): every conv is a chain of 64-input-
+// channel chunk launches accumulating in an FP32 partial sum; the last launch
+// applies the layer's epilogue.  Nothing is concatenated or rearranged in
+// memory: a dense block's inputs stay separate [P][64] tensors, a deshuffle
+// chunk is a strided tensor-map view of the HR feature map (sub-pixel
+// (oy, ox) of every s x s block), the 1x1 fuse conv is the centre tap of a 3x3
+// chunk, and a shuffle is four launches whose outputs are strided views of
+// the 2x larger feature map.
+#include <cuda_bf16.h>
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "conv_tc.cuh"
+#include "fuse.cuh"
+
+namespace mrs {
+namespace {
+
+constexpr int kF = 64;       // feature channels
+constexpr int kRDG = 3;      // G
+constexpr int kRDB = 5;      // B
+constexpr int kConv = 4;     // convs per block
+
+int depth_of(int s) { return s == 2 ? 1 : s == 4 ? 2 : s == 8 ? 3 : -1; }
+
+struct RLayer {
+    int k, cin, cout;
+    size_t woff, boff;
+};
+
+// layers in forward (= parameter) order: H_lrhs, H_hrls, fuse, 60 block
+// convs, D upsampling convs, H_Rec
+std::vector<RLayer> rdn_layers(int s, int c_hr)
+{
+    std::vector<RLayer> L;
+    size_t o = 0;
+    auto add = [&](int k, int ci, int co) {
+        L.push_back({k, ci, co, o, o + (size_t)co * k * k * ci});
+        o += (size_t)co * k * k * ci + co;
+    };
+    add(3, 3, kF);
+    add(3, c_hr, kF);
+    add(1, kF + kF * s * s, kF);
+    for (int g = 0; g < kRDG; ++g)
+        for (int b = 0; b < kRDB; ++b)
+            for (int c = 1; c <= kConv; ++c) add(3, kF * c, kF);
+    for (int d = 0; d < depth_of(s); ++d) add(3, kF, 4 * kF);
+    add(3, kF, 3);
+    return L;
+}
+
+size_t rdn_nparams(int s, int c_hr)
+{
+    const auto L = rdn_layers(s, c_hr);
+    return L.back().boff + L.back().cout;
+}
+
+// channel of the D-times deshuffled map that holds channel c of HR sub-pixel
+// (oy, ox) of each s x s block: c s^2 + sum over steps d = 1..D of
+// (2 dy_d + dx_d) 4^(D - d), dy_d / dx_d bit d - 1 of oy / ox
+__host__ __device__ __forceinline__ int dsf_channel(int c, int oy, int ox, int D)
+{
+    int k = c;
+    for (int d = 1; d <= D; ++d) k = 4 * k + 2 * ((oy >> (d - 1)) & 1) + ((ox >> (d - 1)) & 1);
+    return k;
+}
+
+// ---- elementwise kernels ----------------------------------------------------
+// I_HRLS of one pixel: RGB, albedo, normal (+ diffuse, specular, log(1 + var))
+__device__ __forceinline__ int hr_pixel(const float* hrls, const float* alb, const float* nrm,
+                                        const float* extra, size_t p, float* v)
+{
+    for (int k = 0; k < 3; ++k) {
+        v[k] = __ldg(hrls + 3 * p + k);
+        v[3 + k] = __ldg(alb + 3 * p + k);
+        v[6 + k] = __ldg(nrm + 3 * p + k);
+    }
+    if (!extra) return 9;
+    for (int k = 0; k < 6; ++k) v[9 + k] = __ldg(extra + 9 * p + k);
+    for (int k = 0; k < 3; ++k) v[15 + k] = log1pf(fmaxf(__ldg(extra + 9 * p + 6 + k), 0.0f));
+    return 18;
+}
+
+__global__ void k_hr_input_f32(const float* hrls, const float* alb, const float* nrm,
+                               const float* extra, size_t P, float* out)
+{
+    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < P;
+         p += (size_t)gridDim.x * blockDim.x) {
+        float v[18];
+        int c = hr_pixel(hrls, alb, nrm, extra, p, v);
+        for (int k = 0; k < c; ++k) out[p * c + k] = v[k];
+    }
+}
+
+// bf16 [P][64] rows, channels past the input's zero
+__global__ void k_hr_input_bf16(const float* hrls, const float* alb, const float* nrm,
+                                const float* extra, size_t P, __nv_bfloat16* out)
+{
+    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < P;
+         p += (size_t)gridDim.x * blockDim.x) {
+        float v[24];
+#pragma unroll
+        for (int k = 0; k < 24; ++k) v[k] = 0.0f;
+        hr_pixel(hrls, alb, nrm, extra, p, v);
+        uint4* o = (uint4*)(out + p * 64);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            uint4 u;
+            __nv_bfloat162* h2 = (__nv_bfloat162*)&u;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) h2[e] = __floats2bfloat162_rn(v[8 * j + 2 * e], v[8 * j + 2 * e + 1]);
+            o[j] = u;
+        }
+        const uint4 z = make_uint4(0, 0, 0, 0);
+#pragma unroll
+        for (int j = 3; j < 8; ++j) o[j] = z;
+    }
+}
+
+__global__ void k_lr_input_bf16(const float* lrhs, size_t P, __nv_bfloat16* out)
+{
+    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < P;
+         p += (size_t)gridDim.x * blockDim.x) {
+        uint4* o = (uint4*)(out + p * 64);
+        uint4 u;
+        __nv_bfloat162* h2 = (__nv_bfloat162*)&u;
+        h2[0] = __floats2bfloat162_rn(__ldg(lrhs + 3 * p), __ldg(lrhs + 3 * p + 1));
+        h2[1] = __floats2bfloat162_rn(__ldg(lrhs + 3 * p + 2), 0.0f);
+        h2[2] = h2[3] = __floats2bfloat162_rn(0.0f, 0.0f);
+        o[0] = u;
+        const uint4 z = make_uint4(0, 0, 0, 0);
+#pragma unroll
+        for (int j = 1; j < 8; ++j) o[j] = z;
+    }
+}
+
+// D-times deshuffle of F [N][H][W][64] into channels [64, 64 + 64 s^2) of
+// cat [N][H/s][W/s][os]: one thread per (HR pixel, channel)
+__global__ void k_deshuffle_f32(const float* __restrict__ F, int N, int H, int W, int s, int D,
+                                float* __restrict__ cat, int os)
+{
+    const size_t total = (size_t)N * H * W * 64;
+    const int h = H / s, w = W / s;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        int c = (int)(i % 64);
+        size_t px = i / 64;
+        int X = (int)(px % W);
+        size_t r = px / W;
+        int Y = (int)(r % H), n = (int)(r / H);
+        int k = dsf_channel(c, Y % s, X % s, D);
+        cat[(((size_t)n * h + Y / s) * w + X / s) * os + 64 + k] = F[i];
+    }
+}
+
+// x2 shuffle: T [N][h][w][ts] (256 channels used) -> U [N][2h][2w][64],
+// U[2y + dy][2x + dx][c] = T[y][x][4c + 2dy + dx]
+__global__ void k_shuffle_f32(const float* __restrict__ T, int ts, int N, int h, int w,
+                              float* __restrict__ U)
+{
+    const size_t total = (size_t)N * 4 * h * w * 64;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        int c = (int)(i % 64);
+        size_t px = i / 64;
+        int X = (int)(px % (2 * w));
+        size_t r = px / (2 * w);
+        int Y = (int)(r % (2 * h)), n = (int)(r / (2 * h));
+        U[i] = T[(((size_t)n * h + Y / 2) * w + X / 2) * ts + 4 * c + 2 * (Y & 1) + (X & 1)];
+    }
+}
+
+// dst[p][c] (+)= src[p][c] for c < 64 (pixel strides ds, ss)
+__global__ void k_ch64_f32(float* __restrict__ dst, int ds, const float* __restrict__ src, int ss,
+                           size_t P, int add)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < P * 64;
+         i += (size_t)gridDim.x * blockDim.x) {
+        size_t p = i / 64;
+        int c = (int)(i % 64);
+        float v = src[p * ss + c];
+        dst[p * ds + c] = add ? dst[p * ds + c] + v : v;
+    }
+}
+
+// dst += src over bf16 [n] (8 values per thread)
+__global__ void k_add_bf16(__nv_bfloat16* __restrict__ dst, const __nv_bfloat16* __restrict__ src,
+                           size_t n8)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n8;
+         i += (size_t)gridDim.x * blockDim.x) {
+        uint4 a = ((const uint4*)dst)[i], b = ((const uint4*)src)[i];
+        __nv_bfloat162* pa = (__nv_bfloat162*)&a;
+        const __nv_bfloat162* pb = (const __nv_bfloat162*)&b;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            float2 x = __bfloat1622float2(pa[e]), y = __bfloat1622float2(pb[e]);
+            pa[e] = __floats2bfloat162_rn(x.x + y.x, x.y + y.y);
+        }
+        ((uint4*)dst)[i] = a;
+    }
+}
+
+// the 1x1 fuse weights [64][cin] as 3x3 weights with only the centre tap
+__global__ void k_centre_tap(const float* __restrict__ w1, int cin, float* __restrict__ w3)
+{
+    size_t n = (size_t)64 * 9 * cin;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        int c = (int)(i % cin);
+        int t = (int)((i / cin) % 9);
+        size_t o = i / ((size_t)cin * 9);
+        w3[i] = t == 4 ? w1[o * cin + c] : 0.0f;
+    }
+}
+
+inline int grid_for(size_t n)
+{
+    size_t g = (n + 255) / 256;
+    return (int)(g < 8192 ? (g ? g : 1) : 8192);
+}
+
+struct WChunk {
+    size_t off;          // bf16 elements into wbf ([9][nout][64])
+    int nout;            // 64 or 16
+    CUtensorMap map;
+};
+
+}  // namespace
+}  // namespace mrs
+
+using namespace mrs;
+
+struct mrs_rdn_s {
+    int s = 0, D = 0, c_hr = 0;
+    size_t np = 0;
+    std::vector<RLayer> L;
+    float* master = nullptr;       // FP32 parameters (oracle layout)
+    float* w_fuse3 = nullptr;      // fuse weights as 3x3 centre taps (FP32 path)
+    __nv_bfloat16* wbf = nullptr;  // packed BF16 chunks
+    float* bch = nullptr;          // chunk biases [nchunks][64]
+    std::vector<WChunk> ch;
+    std::vector<int> first;        // first chunk of each layer
+    Buf f32, bf;                   // activation workspaces
+    int* err = nullptr;
+};
+
+namespace mrs {
+namespace {
+
+// BF16 chunks of every layer, packed on the host as [tap][o][c] (o < nout,
+// c < 64) for conv_tc, with per-chunk biases (the layer bias on the chunk that
+// starts a chain, zero elsewhere)
+mrs_status pack_chunks(mrs_rdn_s* r, const float* P)
+{
+    std::vector<__nv_bfloat16> wb;
+    std::vector<float> bb;
+    r->ch.clear();
+    r->first.clear();
+    auto chunk = [&](int nout, auto wfun, auto bfun) {
+        WChunk c;
+        c.off = wb.size();
+        c.nout = nout;
+        for (int t = 0; t < 9; ++t)
+            for (int o = 0; o < nout; ++o)
+                for (int k = 0; k < 64; ++k) wb.push_back(__float2bfloat16_rn(wfun(t, o, k)));
+        for (int o = 0; o < 64; ++o) bb.push_back(o < nout ? bfun(o) : 0.0f);
+        r->ch.push_back(c);
+    };
+    const int D = r->D, s = r->s;
+    for (size_t li = 0; li < r->L.size(); ++li) {
+        const RLayer& l = r->L[li];
+        r->first.push_back((int)r->ch.size());
+        const float* w = P + l.woff;
+        const float* b = P + l.boff;
+        const bool is_up = li + 1 < r->L.size() && l.cout == 4 * kF;
+        if (li == 2) {
+            // fuse: chunk 0 = F_LRHS channels, chunk 1 + oy s + ox = HR sub-pixel (oy, ox)
+            for (int q = 0; q <= s * s; ++q) {
+                int oy = q ? (q - 1) / s : 0, ox = q ? (q - 1) % s : 0;
+                chunk(64, [&](int t, int o, int k) -> float {
+                    if (t != 4) return 0.0f;
+                    int ci = q == 0 ? k : 64 + dsf_channel(k, oy, ox, D);
+                    return w[(size_t)o * l.cin + ci];
+                }, [&](int o) -> float { return q == 0 ? b[o] : 0.0f; });
+            }
+        } else if (is_up) {
+            // upsampling conv: chunk q = 2 dy + dx computes output channels 4c + q
+            for (int q = 0; q < 4; ++q)
+                chunk(64, [&](int t, int o, int k) -> float {
+                    return w[((size_t)(4 * o + q) * 9 + t) * l.cin + k];
+                }, [&](int o) -> float { return b[4 * o + q]; });
+        } else {
+            const int nout = l.cout > 16 ? 64 : 16;
+            const int nch = (l.cin + 63) / 64;
+            for (int j = 0; j < nch; ++j)
+                chunk(nout, [&](int t, int o, int k) -> float {
+                    int ci = 64 * j + k;
+                    return (o < l.cout && ci < l.cin) ? w[((size_t)o * 9 + t) * l.cin + ci] : 0.0f;
+                }, [&](int o) -> float { return (j == 0 && o < l.cout) ? b[o] : 0.0f; });
+        }
+    }
+    if (r->wbf) cudaFree(r->wbf);
+    if (r->bch) cudaFree(r->bch);
+    r->wbf = nullptr;
+    r->bch = nullptr;
+    MRS_CHECK(cudaMalloc(&r->wbf, wb.size() * sizeof(__nv_bfloat16)));
+    MRS_CHECK(cudaMalloc(&r->bch, bb.size() * sizeof(float)));
+    MRS_CHECK(cudaMemcpy(r->wbf, wb.data(), wb.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice));
+    MRS_CHECK(cudaMemcpy(r->bch, bb.data(), bb.size() * sizeof(float), cudaMemcpyHostToDevice));
+    for (auto& c : r->ch) {
+        mrs_status st = tc_make_w_map(&c.map, r->wbf + c.off, 9 * c.nout, c.nout, TC_BF16);
+        if (st != MRS_OK) return st;
+    }
+    return MRS_OK;
+}
+
+mrs_status rdn_f32(mrs_rdn_s* r, const float* lrhs, const float* hrls, const float* alb,
+                   const float* nrm, const float* extra, int N, int H, int W, float* out,
+                   cudaStream_t st)
+{
+    const int s = r->s, D = r->D, h = H / s, w = W / s;
+    const size_t Pl = (size_t)N * h * w, Ph = (size_t)N * H * W;
+    const int Ccat = kF + kF * s * s;
+    // workspace: inH | cat | Fh0 | A | B | F0 | Pg | T | U  (floats)
+    const size_t nT = Ph / 4 * 256, nU = Ph * 64;
+    const size_t need = (Ph * r->c_hr + Pl * Ccat + Ph * 64 + 2 * Pl * 256 + 2 * Pl * 64 + nT + nU) * 4;
+    mrs_status rc = r->f32.ensure(need);
+    if (rc != MRS_OK) return rc;
+    float* inH = r->f32.as<float>();
+    float* cat = inH + Ph * r->c_hr;
+    float* Fh0 = cat + Pl * Ccat;
+    float* A = Fh0 + Ph * 64;
+    float* B = A + Pl * 256;
+    float* F0 = B + Pl * 256;
+    float* Pg = F0 + Pl * 64;
+    float* T = Pg + Pl * 64;
+    float* U = T + nT;
+    const float* M = r->master;
+    const auto& L = r->L;
+
+    k_hr_input_f32<<<grid_for(Ph), 256, 0, st>>>(hrls, alb, nrm, extra, Ph, inH);
+    MRS_LAUNCHED(1);
+    // F_LRHS into cat[:, 0:64]; F0_HRLS; deshuffle into cat[:, 64:]
+    rc = simt_conv3x3(lrhs, 3, 3, M + L[0].woff, M + L[0].boff, kF, SIMT_PLAIN, 1, nullptr, 0, cat,
+                      Ccat, nullptr, N, h, w, 1, st);
+    if (rc == MRS_OK)
+        rc = simt_conv3x3(inH, r->c_hr, r->c_hr, M + L[1].woff, M + L[1].boff, kF, SIMT_PLAIN, 1,
+                          nullptr, 0, Fh0, kF, nullptr, N, H, W, 1, st);
+    if (rc != MRS_OK) return rc;
+    k_deshuffle_f32<<<grid_for(Ph * 64), 256, 0, st>>>(Fh0, N, H, W, s, D, cat, Ccat);
+    MRS_LAUNCHED(1);
+    k_centre_tap<<<grid_for((size_t)64 * 9 * Ccat), 256, 0, st>>>(M + L[2].woff, Ccat, r->w_fuse3);
+    MRS_LAUNCHED(1);
+    // F_0 = relu(fuse(cat)) into A[:, 0:64] and F0
+    rc = simt_conv3x3(cat, Ccat, Ccat, r->w_fuse3, M + L[2].boff, kF, SIMT_PLAIN, 1, nullptr, 0, A,
+                      256, nullptr, N, h, w, 1, st);
+    if (rc != MRS_OK) return rc;
+    k_ch64_f32<<<grid_for(Pl * 64), 256, 0, st>>>(F0, 64, A, 256, Pl, 0);
+    MRS_LAUNCHED(1);
+    int li = 3;
+    for (int g = 0; g < kRDG && rc == MRS_OK; ++g) {
+        k_ch64_f32<<<grid_for(Pl * 64), 256, 0, st>>>(Pg, 64, A, 256, Pl, 0);
+        MRS_LAUNCHED(1);
+        for (int b = 0; b < kRDB && rc == MRS_OK; ++b) {
+            for (int c = 1; c < kConv && rc == MRS_OK; ++c, ++li)
+                rc = simt_conv3x3(A, kF * c, 256, M + L[li].woff, M + L[li].boff, kF, SIMT_PLAIN, 1,
+                                  nullptr, 0, A + kF * c, 256, nullptr, N, h, w, 1, st);
+            if (rc != MRS_OK) break;
+            rc = simt_conv3x3(A, 256, 256, M + L[li].woff, M + L[li].boff, kF, SIMT_RESRELU, 0, A,
+                              256, B, 256, nullptr, N, h, w, 1, st);
+            ++li;
+            float* t = A;
+            A = B;
+            B = t;
+        }
+        k_ch64_f32<<<grid_for(Pl * 64), 256, 0, st>>>(A, 256, Pg, 64, Pl, 1);
+        MRS_LAUNCHED(1);
+    }
+    if (rc != MRS_OK) return rc;
+    k_ch64_f32<<<grid_for(Pl * 64), 256, 0, st>>>(A, 256, F0, 64, Pl, 1);
+    MRS_LAUNCHED(1);
+    // UP: D x (conv 64 -> 256 + ReLU, shuffle); U alternates between U and Fh0
+    const float* cur = A;
+    int cs = 256, ch = h, cw = w;
+    float* dst = U;
+    for (int d = 0; d < D && rc == MRS_OK; ++d, ++li) {
+        rc = simt_conv3x3(cur, kF, cs, M + L[li].woff, M + L[li].boff, 4 * kF, SIMT_PLAIN, 1,
+                          nullptr, 0, T, 256, nullptr, N, ch, cw, 1, st);
+        if (rc != MRS_OK) break;
+        k_shuffle_f32<<<grid_for((size_t)N * 4 * ch * cw * 64), 256, 0, st>>>(T, 256, N, ch, cw, dst);
+        MRS_LAUNCHED(1);
+        cur = dst;
+        cs = kF;
+        ch *= 2;
+        cw *= 2;
+        dst = dst == U ? Fh0 : U;
+    }
+    if (rc != MRS_OK) return rc;
+    rc = simt_conv3x3(cur, kF, kF, M + L[li].woff, M + L[li].boff, 3, SIMT_PLAIN, 0, nullptr, 0, out,
+                      3, nullptr, N, H, W, 1, st);
+    if (rc != MRS_OK) return rc;
+    return cuda_status(cudaGetLastError(), "rdn fp32");
+}
+
+mrs_status rdn_bf16(mrs_rdn_s* r, const float* lrhs, const float* hrls, const float* alb,
+                    const float* nrm, const float* extra, int N, int H, int W, float* out,
+                    cudaStream_t st)
+{
+    const int s = r->s, D = r->D, h = H / s, w = W / s;
+    const size_t Pl = (size_t)N * h * w, Ph = (size_t)N * H * W;
+    // bf16 workspace: inL | inH | Flr | Fh0 | F0 | X[0..5] | U (sum of 4^d Pl, d = 1..D)
+    size_t nU = 0;
+    for (int d = 1; d <= D; ++d) nU += Pl << (2 * d);
+    const int kX = 6;
+    const size_t elems = (Pl + Ph + Pl + Ph + Pl + kX * Pl + nU) * 64;
+    const size_t need = elems * 2 + Pl * 64 * 4 + 4096;
+    mrs_status rc = r->bf.ensure(need);
+    if (rc != MRS_OK) return rc;
+    __nv_bfloat16* inL = r->bf.as<__nv_bfloat16>();
+    __nv_bfloat16* inH = inL + Pl * 64;
+    __nv_bfloat16* Flr = inH + Ph * 64;
+    __nv_bfloat16* Fh0 = Flr + Pl * 64;
+    __nv_bfloat16* F0 = Fh0 + Ph * 64;
+    __nv_bfloat16* X[kX];
+    X[0] = F0 + Pl * 64;
+    for (int i = 1; i < kX; ++i) X[i] = X[i - 1] + Pl * 64;
+    __nv_bfloat16* Ud[4];
+    Ud[0] = nullptr;
+    __nv_bfloat16* u = X[kX - 1] + Pl * 64;
+    for (int d = 1; d <= D; ++d) { Ud[d] = u; u += (Pl << (2 * d)) * 64; }
+    float* part = (float*)(((uintptr_t)u + 255) & ~(uintptr_t)255);
+
+    k_lr_input_bf16<<<grid_for(Pl), 256, 0, st>>>(lrhs, Pl, inL);
+    MRS_LAUNCHED(1);
+    k_hr_input_bf16<<<grid_for(Ph), 256, 0, st>>>(hrls, alb, nrm, extra, Ph, inH);
+    MRS_LAUNCHED(1);
+    if ((rc = cuda_status(cudaGetLastError(), "rdn input")) != MRS_OK) return rc;
+
+    // tensor maps: A operands (kABox boxes) and outputs / residuals (kOutBox)
+    auto amap = [&](CUtensorMap* m, const void* p, int n, int hh, int ww) {
+        return tc_make_act_map(m, p, n, hh, ww, TC_BF16, kABox);
+    };
+    auto omap = [&](CUtensorMap* m, const void* p, int n, int hh, int ww) {
+        return tc_make_act_map(m, p, n, hh, ww, TC_BF16, kOutBox);
+    };
+    CUtensorMap inLA, inHA, FlrA, FlrO, Fh0O, F0A, F0O, XA[kX], XO[kX];
+    if ((rc = amap(&inLA, inL, N, h, w)) != MRS_OK) return rc;
+    if ((rc = amap(&inHA, inH, N, H, W)) != MRS_OK) return rc;
+    if ((rc = amap(&FlrA, Flr, N, h, w)) != MRS_OK) return rc;
+    if ((rc = omap(&FlrO, Flr, N, h, w)) != MRS_OK) return rc;
+    if ((rc = omap(&Fh0O, Fh0, N, H, W)) != MRS_OK) return rc;
+    if ((rc = amap(&F0A, F0, N, h, w)) != MRS_OK) return rc;
+    if ((rc = omap(&F0O, F0, N, h, w)) != MRS_OK) return rc;
+    for (int i = 0; i < kX; ++i) {
+        if ((rc = amap(&XA[i], X[i], N, h, w)) != MRS_OK) return rc;
+        if ((rc = omap(&XO[i], X[i], N, h, w)) != MRS_OK) return rc;
+    }
+    // deshuffle chunks: sub-pixel (oy, ox) of every s x s block of Fh0
+    std::vector<CUtensorMap> dsf(s * s);
+    for (int q = 0; q < s * s && rc == MRS_OK; ++q) {
+        int oy = q / s, ox = q % s;
+        rc = tc_make_view_map(&dsf[q], Fh0 + ((size_t)oy * W + ox) * 64, N, h, w, (long long)s * 128,
+                              (long long)s * W * 128, (long long)H * W * 128, kABox);
+    }
+    if (rc != MRS_OK) return rc;
+
+    TcConvArgs a;
+    memset(&a, 0, sizeof(a));
+    a.N = N; a.scale = 1; a.operand = TC_BF16; a.err = r->err; a.nout = 64; a.cout = 64;
+    // one conv over the chunk inputs A[0..n) of layer li: chunks 0..n-2 accumulate
+    // in `part`, the last applies `mode` (bf16 out via `o`, residual via `res`)
+    auto layer = [&](int li, const CUtensorMap* const* A, int n, int hh, int ww, int mode,
+                     const CUtensorMap* o, const CUtensorMap* res) {
+        a.H = hh; a.W = ww;
+        for (int j = 0; j < n; ++j) {
+            const WChunk& c = r->ch[r->first[li] + j];
+            a.tmap_x = A[j];
+            a.tmap_w = &c.map;
+            a.bias = r->bch + (size_t)(r->first[li] + j) * 64;
+            a.nout = c.nout;
+            a.acc_in = j ? part : nullptr;
+            a.tmap_res = nullptr;
+            a.tmap_out = nullptr;
+            a.relu = 0;
+            if (j + 1 < n) {
+                a.mode = TC_PLAIN_F32; a.out = part; a.cout = 64;
+            } else {
+                a.mode = mode; a.tmap_out = o; a.tmap_res = res;
+            }
+            mrs_status e = tc_conv3x3(a, st);
+            if (e != MRS_OK) return e;
+        }
+        return MRS_OK;
+    };
+
+    // encoders
+    const CUtensorMap* one[1];
+    one[0] = &inLA;
+    if ((rc = layer(0, one, 1, h, w, TC_RELU_BF16, &FlrO, nullptr)) != MRS_OK) return rc;
+    one[0] = &inHA;
+    a.N = N;
+    if ((rc = layer(1, one, 1, H, W, TC_RELU_BF16, &Fh0O, nullptr)) != MRS_OK) return rc;
+    // fuse: F_LRHS chunk + s^2 deshuffle views
+    std::vector<const CUtensorMap*> fin(1 + s * s);
+    fin[0] = &FlrA;
+    for (int q = 0; q < s * s; ++q) fin[1 + q] = &dsf[q];
+    if ((rc = layer(2, fin.data(), 1 + s * s, h, w, TC_RELU_BF16, &F0O, nullptr)) != MRS_OK) return rc;
+
+    // residual dense groups.  Buffers: F0 stays; X[0..2] rotate as block
+    // inputs / outputs, X[3..5] hold the dense features F_1..F_3
+    int li = 3;
+    int pg = -1;          // index into X of the group input (-1 = F0)
+    int cur = -1;         // block input
+    for (int g = 0; g < kRDG; ++g) {
+        pg = cur;
+        for (int b = 0; b < kRDB; ++b) {
+            const CUtensorMap* inA = cur < 0 ? &F0A : &XA[cur];
+            const CUtensorMap* inO = cur < 0 ? &F0O : &XO[cur];
+            int outi = 0;
+            while (outi == cur || outi == pg) ++outi;
+            const CUtensorMap* ins[4] = {inA, &XA[3], &XA[4], &XA[5]};
+            for (int c = 1; c < kConv; ++c, ++li)
+                if ((rc = layer(li, ins, c, h, w, TC_RELU_BF16, &XO[2 + c], nullptr)) != MRS_OK) return rc;
+            if ((rc = layer(li, ins, kConv, h, w, TC_RESRELU_BF16, &XO[outi], inO)) != MRS_OK) return rc;
+            ++li;
+            cur = outi;
+        }
+        // group skip: F_g = blocks + F_{g-1}
+        k_add_bf16<<<grid_for(Pl * 8), 256, 0, st>>>(X[cur], pg < 0 ? F0 : X[pg], Pl * 8);
+        MRS_LAUNCHED(1);
+    }
+    // Eq. F_DF: + F_0
+    k_add_bf16<<<grid_for(Pl * 8), 256, 0, st>>>(X[cur], F0, Pl * 8);
+    MRS_LAUNCHED(1);
+    if ((rc = cuda_status(cudaGetLastError(), "rdn add")) != MRS_OK) return rc;
+
+    // UP: stage d reads U_d (U_0 = F_DF) and writes the four sub-pixel views of U_{d+1}
+    CUtensorMap UA;
+    const CUtensorMap* src = &XA[cur];
+    int ch = h, cw = w;
+    for (int d = 0; d < D; ++d, ++li) {
+        __nv_bfloat16* nx = Ud[d + 1];
+        for (int q = 0; q < 4; ++q) {
+            int dy = q >> 1, dx = q & 1;
+            CUtensorMap vo;
+            rc = tc_make_view_map(&vo, nx + ((size_t)dy * 2 * cw + dx) * 64, N, ch, cw, 256,
+                                  (long long)4 * cw * 128, (long long)4 * ch * cw * 128, kOutBox);
+            if (rc != MRS_OK) return rc;
+            a.H = ch; a.W = cw;
+            const WChunk& c = r->ch[r->first[li] + q];
+            a.tmap_x = src; a.tmap_w = &c.map; a.bias = r->bch + (size_t)(r->first[li] + q) * 64;
+            a.nout = 64; a.acc_in = nullptr; a.tmap_res = nullptr; a.tmap_out = &vo;
+            a.mode = TC_RELU_BF16; a.relu = 0;
+            if ((rc = tc_conv3x3(a, st)) != MRS_OK) return rc;
+        }
+        ch *= 2;
+        cw *= 2;
+        if ((rc = amap(&UA, nx, N, ch, cw)) != MRS_OK) return rc;
+        src = &UA;
+    }
+    // H_Rec: 64 -> 3, no ReLU, FP32 out
+    const WChunk& c = r->ch[r->first[li]];
+    a.H = H; a.W = W; a.tmap_x = src; a.tmap_w = &c.map; a.bias = r->bch + (size_t)r->first[li] * 64;
+    a.nout = c.nout; a.acc_in = nullptr; a.tmap_out = nullptr; a.tmap_res = nullptr;
+    a.mode = TC_PLAIN_F32; a.out = out; a.cout = 3; a.relu = 0;
+    return tc_conv3x3(a, st);
+}
+
+}  // namespace
+}  // namespace mrs
+
+extern "C" mrs_status mrs_rdn_nparams(int32_t scale, int32_t hr_channels, int64_t* n)
+{
+    MRS_ARG(n != nullptr, "n is NULL");
+    MRS_ARG(depth_of(scale) > 0, "scale must be 2, 4 or 8");
+    MRS_ARG(hr_channels == 9 || hr_channels == 18, "hr_channels must be 9 or 18");
+    *n = (int64_t)rdn_nparams(scale, hr_channels);
+    return MRS_OK;
+}
+
+extern "C" mrs_status mrs_rdn_free(mrs_rdn r)
+{
+    if (!r) return MRS_OK;
+    cudaDeviceSynchronize();
+    void* ptrs[] = {r->master, r->w_fuse3, r->wbf, r->bch, r->err};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    r->f32.release();
+    r->bf.release();
+    delete r;
+    return MRS_OK;
+}
+
+extern "C" mrs_status mrs_rdn_create(int32_t scale, int32_t hr_channels, const float* params,
+                                     int64_t n_params, mrs_rdn* out)
+{
+    MRS_ARG(out != nullptr, "out is NULL");
+    *out = nullptr;
+    MRS_ARG(params != nullptr, "params is NULL");
+    MRS_ARG(depth_of(scale) > 0, "scale must be 2, 4 or 8");
+    MRS_ARG(hr_channels == 9 || hr_channels == 18, "hr_channels must be 9 or 18");
+    MRS_ARG(n_params == (int64_t)rdn_nparams(scale, hr_channels), "n_params must equal mrs_rdn_nparams");
+    mrs_rdn_s* r = new mrs_rdn_s();
+    r->s = scale;
+    r->D = depth_of(scale);
+    r->c_hr = hr_channels;
+    r->np = (size_t)n_params;
+    r->L = rdn_layers(scale, hr_channels);
+    const int Ccat = kF + kF * scale * scale;
+    mrs_status s = cuda_status(cudaMalloc(&r->master, r->np * 4), "cudaMalloc(rdn)");
+    if (s == MRS_OK) s = cuda_status(cudaMalloc(&r->w_fuse3, (size_t)64 * 9 * Ccat * 4), "cudaMalloc(rdn)");
+    if (s == MRS_OK) s = cuda_status(cudaMalloc(&r->err, 4), "cudaMalloc(rdn)");
+    if (s == MRS_OK) s = cuda_status(cudaMemset(r->err, 0, 4), "memset");
+    if (s == MRS_OK)
+        s = cuda_status(cudaMemcpy(r->master, params, r->np * 4, cudaMemcpyHostToDevice), "params");
+    if (s == MRS_OK) s = pack_chunks(r, params);
+    if (s != MRS_OK) { mrs_rdn_free(r); return s; }
+    *out = r;
+    return MRS_OK;
+}
+
+extern "C" mrs_status mrs_rdn_fuse(mrs_rdn r, const float* lrhs, const float* hrls,
+                                   const float* albedo, const float* normal, const float* extra,
+                                   int32_t N, int32_t H, int32_t W, int32_t precision, float* out,
+                                   void* stream)
+{
+    MRS_ARG(r != nullptr, "rdn is NULL");
+    MRS_ARG(lrhs && hrls && albedo && normal && out, "NULL image pointer");
+    MRS_ARG((extra != nullptr) == (r->c_hr == 18), "extra must be given exactly for hr_channels 18");
+    MRS_ARG(N >= 1 && H >= 1 && W >= 1, "N, H, W must be >= 1");
+    MRS_ARG(H % r->s == 0 && W % r->s == 0, "H and W must be multiples of the scale");
+    MRS_ARG((int64_t)N * H * W <= (int64_t(1) << 26), "N*H*W exceeds 2^26 pixels");
+    MRS_ARG(precision == MRS_PREC_FP32 || precision == MRS_PREC_BF16,
+            "precision must be MRS_PREC_FP32 or MRS_PREC_BF16");
+    cudaStream_t st = (cudaStream_t)stream;
+    mrs_status rc = precision == MRS_PREC_FP32
+                        ? rdn_f32(r, lrhs, hrls, albedo, normal, extra, N, H, W, out, st)
+                        : rdn_bf16(r, lrhs, hrls, albedo, normal, extra, N, H, W, out, st);
+    return rc;
+}
+
+extern "C" mrs_status mrs_rdn_check(mrs_rdn r)
+{
+    MRS_ARG(r != nullptr, "rdn is NULL");
+    int h = 0;
+    MRS_CHECK(cudaMemcpy(&h, r->err, 4, cudaMemcpyDeviceToHost));
+    if (h) {
+        cudaMemset(r->err, 0, 4);
+        set_error("tensor-core conv wait timed out");
+        return MRS_ERR_TIMEOUT;
+    }
+    return MRS_OK;
+}

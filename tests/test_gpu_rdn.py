@@ -1,0 +1,191 @@
+"""The method's own fusion network (Sec. 4) on the GPU against the float64
+oracle, through the C ABI (mrs_rdn_*), and the multi-chunk BF16 convolution
+it is built from (mrs_conv3x3 with more than 64 input channels).
+
+Tolerances:
+* FP32 SIMT path: max |gpu - oracle| <= 1e-5 * max(1, max |oracle|).
+* BF16 chunked conv: the float64 conv of the same BF16-rounded operands, within
+  K * 2^-23 * sum |x w| per output (K = 9 cin), the FP32 accumulation error.
+* Identity-kernel networks with BF16-exact inputs: bit-exact (every
+  intermediate is exactly representable, so the deshuffle views, the shuffle
+  views, the chunk chains and the skips are checked exactly).
+* Whole network in BF16: PSNR against float64 with a floor.
+"""
+import numpy as np
+import pytest
+
+from oracle import cnn, rdn
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mrs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2106_12802_gb300 as m
+    m.load()
+    return m
+
+
+def _cuda(*a):
+    return [torch.from_numpy(np.ascontiguousarray(t, dtype=np.float32)).cuda() for t in a]
+
+
+def _inputs(seed, N, h, w, s, extra=False):
+    rng = np.random.default_rng(seed)
+    H, W = h * s, w * s
+    out = [rng.gamma(2.0, 0.5, (N, h, w, 3)), rng.gamma(1.0, 1.0, (N, H, W, 3)),
+           rng.uniform(0, 1, (N, H, W, 3)), rng.uniform(-1, 1, (N, H, W, 3))]
+    if extra:
+        out.append(np.concatenate([rng.gamma(1.0, 0.5, (N, H, W, 6)),
+                                   rng.gamma(0.5, 1.0, (N, H, W, 3))], axis=-1))
+    return [a.astype(np.float32) for a in out]
+
+
+def _psnr(got, ref):
+    mse = np.mean((np.asarray(got, np.float64) - ref) ** 2)
+    return float("inf") if mse == 0 else 10 * np.log10(np.ptp(ref) ** 2 / mse)
+
+
+def _bf16(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def test_param_count_matches_oracle(mrs):
+    for s in (2, 4, 8):
+        for c in (9, 18):
+            assert mrs.rdn_nparams(s, c) == rdn.nparams(s, c)
+
+
+@pytest.mark.parametrize("cin,cout,relu", [(128, 64, 1), (256, 64, 0), (200, 3, 0), (192, 64, 1)])
+def test_conv_bf16_multichunk_matches_oracle(mrs, cin, cout, relu):
+    rng = np.random.default_rng(cin + cout)
+    N, H, W = 1, 5, 250
+    x = rng.normal(size=(N, H, W, cin)).astype(np.float32)
+    w = (rng.normal(size=(cout, 3, 3, cin)) * np.sqrt(2.0 / (9 * cin))).astype(np.float32)
+    b = (rng.normal(size=cout) * 0.1).astype(np.float32)
+    got = mrs.conv3x3(torch.from_numpy(x).cuda(), w, b, relu=relu, precision="bf16").cpu().numpy()
+    xq, wq = _bf16(x), _bf16(w)
+    ref = cnn.conv3x3(xq, wq, b.astype(np.float64))
+    bound = 9 * cin * 2.0**-23 * cnn.conv3x3(np.abs(xq), np.abs(wq), np.zeros(cout)) + 1e-6
+    if relu:
+        ref = np.maximum(ref, 0)
+    err = np.abs(got - ref)
+    assert (err <= bound).all(), err.max()
+
+
+@pytest.mark.parametrize("s,N,h,w", [(2, 2, 5, 7), (4, 1, 6, 9), (8, 1, 3, 4)])
+def test_rdn_fp32_matches_oracle(mrs, s, N, h, w):
+    lr, hr, alb, nrm = _inputs(s, N, h, w, s)
+    p = rdn.kaiming(s, s, fusion_damp=0.1).astype(np.float32)
+    net = mrs.RDN(p, s)
+    got = net.fuse(*_cuda(lr, hr, alb, nrm), precision="fp32").cpu().numpy()
+    ref = rdn.forward(p.astype(np.float64), lr, hr, alb, nrm, s)
+    assert np.abs(got - ref).max() <= 1e-5 * max(1.0, np.abs(ref).max())
+
+
+def test_rdn_fp32_with_extra_layers_matches_oracle(mrs):
+    s = 2
+    lr, hr, alb, nrm, ex = _inputs(11, 1, 6, 5, s, extra=True)
+    p = rdn.kaiming(3, s, c_hr=18, fusion_damp=0.1).astype(np.float32)
+    net = mrs.RDN(p, s, hr_channels=18)
+    got = net.fuse(*_cuda(lr, hr, alb, nrm), precision="fp32", extra=_cuda(ex)[0]).cpu().numpy()
+    ref = rdn.forward(p.astype(np.float64), lr, hr, alb, nrm, s, extra=ex)
+    assert np.abs(got - ref).max() <= 1e-5 * max(1.0, np.abs(ref).max())
+    with pytest.raises(Exception):
+        net.fuse(*_cuda(lr, hr, alb, nrm), precision="fp32")
+
+
+def _zero_layers(s, c_hr=rdn.C_HR):
+    return [(np.zeros((co, k, k, ci)), np.zeros(co)) for _, k, ci, co in rdn.layers_for(s, c_hr)]
+
+
+@pytest.mark.parametrize("s,w", [(2, 130), (4, 37), (8, 20)])
+def test_rdn_bf16_identity_network_is_exact(mrs, s, w):
+    # identity kernels and LRHS values k / 4 (k <= 8): every intermediate is a
+    # BF16-exact multiple of 1/4, so I_SR = 9 nearest_up_s(LRHS) exactly; fails
+    # on any misplaced shuffle view, chunk or skip
+    L = _zero_layers(s)
+    idx = {n: i for i, (n, *_) in enumerate(rdn.layers_for(s))}
+    for c in range(3):
+        L[idx["H_lrhs"]][0][c, 1, 1, c] = 1.0
+        L[idx["fuse"]][0][c, 0, 0, c] = 1.0
+        L[idx["H_rec"]][0][c, 1, 1, c] = 1.0
+        for d in range(rdn.depth(s)):
+            for sub in range(4):
+                L[idx[f"up{d}"]][0][4 * c + sub, 1, 1, c] = 1.0
+    p = rdn.pack(L).astype(np.float32)
+    rng = np.random.default_rng(s)
+    h = 3
+    lr = rng.integers(0, 9, (1, h, w, 3)).astype(np.float32) / 4
+    _, hr, alb, nrm = _inputs(s, 1, h, w, s)
+    got = mrs.RDN(p, s).fuse(*_cuda(lr, hr, alb, nrm), precision="bf16").cpu().numpy()
+    ref = rdn.forward(p.astype(np.float64), lr, hr, alb, nrm, s)
+    assert np.array_equal(got, ref.astype(np.float32))
+    assert np.array_equal(got, 9 * np.repeat(np.repeat(lr, s, axis=1), s, axis=2))
+
+
+@pytest.mark.parametrize("s,k", [(2, 3), (4, 5), (4, 15), (8, 42)])
+def test_rdn_bf16_deshuffle_view_is_exact(mrs, s, k):
+    # the fuse conv picks deshuffled channel k (channel 0 of one HR sub-pixel)
+    # of F0_HRLS = HRLS red; BF16-exact HRLS values give I_SR exactly
+    L = _zero_layers(s)
+    idx = {n: i for i, (n, *_) in enumerate(rdn.layers_for(s))}
+    L[idx["H_hrls"]][0][0, 1, 1, 0] = 1.0
+    L[idx["fuse"]][0][0, 0, 0, 64 + k] = 1.0
+    L[idx["H_rec"]][0][0, 1, 1, 0] = 1.0
+    for d in range(rdn.depth(s)):
+        for sub in range(4):
+            L[idx[f"up{d}"]][0][sub, 1, 1, 0] = 1.0
+    p = rdn.pack(L).astype(np.float32)
+    rng = np.random.default_rng(k)
+    lr, _, alb, nrm = _inputs(k, 1, 4, 33, s)
+    hr = rng.integers(0, 9, alb.shape).astype(np.float32) / 4
+    got = mrs.RDN(p, s).fuse(*_cuda(lr, hr, alb, nrm), precision="bf16").cpu().numpy()
+    ref = rdn.forward(p.astype(np.float64), lr, hr, alb, nrm, s)
+    assert ref[..., 0].any()
+    assert np.array_equal(got, ref.astype(np.float32))
+
+
+@pytest.mark.parametrize("s", [2, 4])
+def test_rdn_bf16_close_to_fp64(mrs, s):
+    N, h, w = 1, 6, 130 // s * 2
+    lr, hr, alb, nrm = _inputs(20 + s, N, h, w, s)
+    p = rdn.kaiming(7, s, fusion_damp=0.1).astype(np.float32)
+    net = mrs.RDN(p, s)
+    c = _cuda(lr, hr, alb, nrm)
+    got = net.fuse(*c, precision="bf16").cpu().numpy()
+    f32 = net.fuse(*c, precision="fp32").cpu().numpy()
+    net.check()
+    ref = rdn.forward(p.astype(np.float64), lr, hr, alb, nrm, s)
+    assert np.abs(f32 - ref).max() <= 1e-5 * max(1.0, np.abs(ref).max())
+    psnr = _psnr(got, ref)
+    print(f"rdn bf16 x{s}: PSNR {psnr:.1f} dB vs float64")
+    assert psnr >= 50.0, psnr
+
+
+def test_rdn_bf16_full_size_sampled_windows(mrs):
+    # x4 to 1024 x 1024 from 256 x 256 LRHS (the hybrid frame), as the bench
+    # runs it; the oracle recomputes a corner window and an interior window
+    # from crops that contain their whole receptive field (61 LR 3x3 convs,
+    # the LR upsampling conv, one conv at 2x and H_Rec / H_hrls at HR: 64 LR
+    # pixels of margin suffice)
+    s, m = 4, 64
+    lr, hr, alb, nrm = _inputs(31, 1, 256, 256, s)
+    p = rdn.kaiming(9, s, fusion_damp=0.1).astype(np.float32)
+    net = mrs.RDN(p, s)
+    got = net.fuse(*_cuda(lr, hr, alb, nrm), precision="bf16").cpu().numpy()
+    net.check()
+    for (ly, lx) in ((0, 0), (120, 96)):
+        y0, x0 = max(0, ly - m), max(0, lx - m)
+        y1, x1 = min(256, ly + 8 + m), min(256, lx + 8 + m)
+        hs = (slice(None), slice(s * y0, s * y1), slice(s * x0, s * x1))
+        ref = rdn.forward(p.astype(np.float64), lr[:, y0:y1, x0:x1], hr[hs], alb[hs], nrm[hs], s)
+        oy, ox = s * (ly - y0), s * (lx - x0)
+        r = ref[:, oy:oy + 32, ox:ox + 32]
+        g = got[:, s * ly:s * ly + 32, s * lx:s * lx + 32]
+        psnr = _psnr(g, r)
+        print(f"rdn bf16 1024^2 window ({ly},{lx}): PSNR {psnr:.1f} dB")
+        assert psnr >= 50.0, psnr
