@@ -403,6 +403,60 @@ def batched_serving(mrs, params, n_jobs=32, n_scenes=4, psnr_jobs=4, seed=5):
 
 
 # ----------------------------------------------------------------------------
+# the method's own fusion network (Sec. 4): x4 two-encoder network at 1024^2
+# ----------------------------------------------------------------------------
+def paper_network(mrs, flush, s=S, reps=10):
+    """Device time of the method's own x4 network (BF16 tensor cores, Kaiming
+    weights: the time does not depend on them) on a 256^2 LRHS + 1024^2 HRLS
+    frame, L2 flushed before every rep, plus one FP32 pass for reference."""
+    import torch
+
+    from paper_2106_12802_gb300 import rdn
+    net = mrs.RDN(rdn.kaiming_params(s), s)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    lr = torch.rand((1, LR, LR, 3), device="cuda", generator=g)
+    hr = [torch.rand((1, HR, HR, 3), device="cuda", generator=g) for _ in range(3)]
+    out = torch.empty((1, HR, HR, 3), device="cuda")
+    for _ in range(2):
+        net.fuse(lr, *hr, precision="bf16", out=out)
+    torch.cuda.synchronize()
+    mrs.profile_read()
+    mrs.profile_enable(True)
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        net.fuse(lr, *hr, precision="bf16", out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    mrs.profile_enable(False)
+    prof = mrs.profile_read()
+    net.check()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    net.fuse(lr, *hr, precision="fp32", out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = float(np.median(ts))
+    flop = rdn.flops_per_lr_pixel(s) * LR * LR
+    peaks = _peaks()
+    conv_ms = prof["conv_tc"][0] / reps
+    tf = flop / (ms * 1e-3) / 1e12
+    res = {"network": "Sec. 4 two-encoder network, x4: H_lrhs, H_hrls, 2 deshuffles, 1x1 fuse, "
+                      "3 RDG x 5 RDB x 4 convs, 2 shuffle upscalings, H_Rec; Kaiming weights",
+           "lrhs": [LR, LR], "hr": [HR, HR], "bf16_ms": ms, "fp32_ms": e0.elapsed_time(e1),
+           "gflop": flop / 1e9, "bf16_tflops": tf,
+           "tensor_frac_of_measured_sustained": tf / peaks["bf16_tflops_sustained"],
+           "conv_tc_ms": conv_ms, "conv_tc_launches": prof["conv_tc"][1] // reps,
+           "conv_tc_tflops": flop / (conv_ms * 1e-3) / 1e12 if conv_ms else None,
+           "l2": "flushed before every rep (512 MiB write)"}
+    net.close()
+    return res
+
+
+# ----------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------
 def run_gpu(args, rank, world):
@@ -523,6 +577,8 @@ def run_gpu(args, rank, world):
         extra["equal_psnr"] = equal_psnr(mrs, scene, S, net, training)
     if rank == 0 and not args.quick and not args.no_batched:
         extra["batched_serving"] = batched_serving(mrs, params)
+    if rank == 0 and not args.no_paper_network:
+        extra["paper_network_x4"] = paper_network(mrs, flush)
     if rank == 0 and not args.quick:
         stats_lr = mrs.render_stats(scene, LR, LR, SPP_LR, DEPTH, RR, 0)
         stats_hr = mrs.render_stats(scene, HR, HR, SPP_HR, DEPTH, RR, 1)
@@ -619,6 +675,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-equal-psnr", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-paper-network", action="store_true")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -449,12 +449,22 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int y = y0; y < y1; ++y, ++lt) {
             uint32_t acc = lt & 1, use = lt >> 1;
             uint32_t slot = lt % kSlots, suse = lt / kSlots;
-            if (!mbar_wait_warp(&tfull[acc], use & 1, a.err)) { stop = true; break; }
-            tc_fence_after();
-            if (!mbar_wait_warp(&rfull[slot], suse & 1, a.err)) { stop = true; break; }
             const int x = xb * kTileOut + j;
             const bool valid = lane < kQuarter && x < a.W;
             const size_t p = ((size_t)n * a.H + y) * a.W + (valid ? x : 0);
+            // the partial sum of this lane's 16 channels (one chunk per warp)
+            // is loaded before the accumulator wait, so its latency overlaps
+            // the MMAs instead of following the TMEM read
+            float4 pre[4];
+            const bool pre_ok = a.acc_in && valid && active && CHUNKS == 1 && (bf_out || a.cout == 64);
+            if (pre_ok) {
+                const float4* ap = (const float4*)(a.acc_in + p * 64 + half * kEpiCh);
+#pragma unroll
+                for (int i4 = 0; i4 < 4; ++i4) pre[i4] = ap[i4];
+            }
+            if (!mbar_wait_warp(&tfull[acc], use & 1, a.err)) { stop = true; break; }
+            tc_fence_after();
+            if (!mbar_wait_warp(&rfull[slot], suse & 1, a.err)) { stop = true; break; }
             uint8_t* srow = sS + slot * SBYTES;
             for (int cc = 0; cc < CHUNKS && active; ++cc) {
                 const int c0 = half * kEpiCh + cc * 16;
@@ -484,7 +494,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const float4* ap = (const float4*)(a.acc_in + p * 64 + c0);
 #pragma unroll
                         for (int i4 = 0; i4 < 4; ++i4) {
-                            float4 t = ap[i4];
+                            float4 t = pre_ok ? pre[i4] : ap[i4];
                             o[4 * i4] += t.x; o[4 * i4 + 1] += t.y;
                             o[4 * i4 + 2] += t.z; o[4 * i4 + 3] += t.w;
                         }
@@ -553,6 +563,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                         // thread, same elements)
                         float4* op = (float4*)((float*)a.out + p * 64 + c0);
                         const float4* ap = a.acc_in ? (const float4*)(a.acc_in + p * 64 + c0) : nullptr;
+                        // all partial-sum loads before any store (they may
+                        // alias the output)
+                        float4 u4[4];
+#pragma unroll
+                        for (int i4 = 0; i4 < 4; ++i4)
+                            u4[i4] = pre_ok ? pre[i4] : (ap ? ap[i4] : make_float4(0.f, 0.f, 0.f, 0.f));
 #pragma unroll
                         for (int i4 = 0; i4 < 4; ++i4) {
                             float4 t = make_float4(v[4 * i4] + sBias[c0 + 4 * i4],
@@ -560,7 +576,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                                                    v[4 * i4 + 2] + sBias[c0 + 4 * i4 + 2],
                                                    v[4 * i4 + 3] + sBias[c0 + 4 * i4 + 3]);
                             if (ap) {
-                                float4 u = ap[i4];
+                                const float4 u = u4[i4];
                                 t.x += u.x; t.y += u.y; t.z += u.z; t.w += u.w;
                             }
                             if (a.relu) {

@@ -2,9 +2,11 @@
 
   python -m paper_2106_12802_gb300.profile_case fuse   --size 1024 --prec bf16
   python -m paper_2106_12802_gb300.profile_case render --size 256 --spp 4
+  python -m paper_2106_12802_gb300.profile_case rdn    --size 1024 --prec bf16
 
 `fuse` runs the x4 fusion network once at size x size output (inputs random,
-Kaiming weights); `render` renders the 200k-triangle procedural scene once.
+Kaiming weights); `rdn` the method's own x4 two-encoder network (the same);
+`render` renders the 200k-triangle procedural scene once.
 Each case runs one warm-up call first, so the profiled launches are steady-state.
 """
 from __future__ import annotations
@@ -18,7 +20,7 @@ import numpy as np
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["fuse", "render"])
+    ap.add_argument("case", choices=["fuse", "render", "rdn"])
     ap.add_argument("--size", type=int, default=1024)
     ap.add_argument("--prec", default="bf16")
     ap.add_argument("--spp", type=int, default=4)
@@ -43,6 +45,19 @@ def main(argv=None):
             out = net.fuse(lr, hr, hr, hr, s, precision=a.prec)
         torch.cuda.synchronize()
         print("fuse ok", float(out.abs().mean()))
+    elif a.case == "rdn":
+        from paper_2106_12802_gb300 import rdn
+        s = 4
+        net = mrs.RDN(rdn.kaiming_params(s), s)
+        H = W = a.size
+        g = torch.Generator(device="cuda").manual_seed(0)
+        lr = torch.rand((1, H // s, W // s, 3), device="cuda", generator=g)
+        hr = torch.rand((1, H, W, 3), device="cuda", generator=g)
+        for _ in range(2):
+            out = net.fuse(lr, hr, hr, hr, precision=a.prec)
+        torch.cuda.synchronize()
+        net.check()
+        print("rdn ok", float(out.abs().mean()))
     else:
         sc = mrs.Scene(scenes.procedural(0))
         for _ in range(2):

@@ -14,6 +14,47 @@ from .fusion import _prec
 from .render import _dev, _ptr, _stream
 
 
+def layers(scale: int, hr_channels: int = 9):
+    """[(name, k, cin, cout)] in parameter order, as include/mrs.h documents
+    it: H_lrhs, H_hrls, fuse (1x1), 3 groups x 5 blocks x 4 convs, the
+    log2(scale) upsampling convs, H_Rec."""
+    D = {2: 1, 4: 2, 8: 3}[scale]
+    L = [("H_lrhs", 3, 3, 64), ("H_hrls", 3, hr_channels, 64), ("fuse", 1, 64 + 64 * scale * scale, 64)]
+    L += [(f"rdg{g}.rdb{b}.conv{c}", 3, 64 * c, 64) for g in range(3) for b in range(5)
+          for c in range(1, 5)]
+    L += [(f"up{d}", 3, 64, 256) for d in range(D)] + [("H_rec", 3, 64, 3)]
+    return L
+
+
+def kaiming_params(scale: int, hr_channels: int = 9, seed: int = 0, fusion_damp: float = 0.1):
+    """Kaiming-normal weights (std sqrt(2 / (k^2 Cin))), zero biases, the
+    blocks' local-fusion convs scaled by fusion_damp (random weights for
+    throughput measurements; each block adds its fusion output to its input)."""
+    rng = np.random.default_rng(np.random.SeedSequence([0x6B726E, int(seed), scale, hr_channels]))
+    parts = []
+    for name, k, ci, co in layers(scale, hr_channels):
+        w = rng.normal(0.0, np.sqrt(2.0 / (k * k * ci)), (co, k, k, ci))
+        if name.endswith("conv4"):
+            w *= fusion_damp
+        parts += [w.ravel(), np.zeros(co)]
+    return np.concatenate(parts).astype(np.float32)
+
+
+def flops_per_lr_pixel(scale: int, hr_channels: int = 9) -> int:
+    """2 x multiply-adds of one forward pass per LR pixel (H_hrls and H_Rec
+    at scale^2 HR pixels, the i-th upsampling conv at 4^i LR pixels)."""
+    total, up = 0, 0
+    for name, k, ci, co in layers(scale, hr_channels):
+        f = 2 * k * k * ci * co
+        if name in ("H_hrls", "H_rec"):
+            f *= scale * scale
+        elif name.startswith("up"):
+            f *= 4 ** up
+            up += 1
+        total += f
+    return total
+
+
 def nparams(scale: int, hr_channels: int = 9) -> int:
     load()
     n = ctypes.c_int64()

@@ -62,3 +62,15 @@ def test_invalid_arguments_rejected_without_cuda(lib):
                                ctypes.byref(h)) == -1
     assert lib.mrs_philox_uniforms(None, -1, 0, None, None) == -1
     assert lib.mrs_free_scene(None) == 0
+
+
+def test_rdn_host_helpers_match_the_oracle_layout():
+    # the binding's documented parameter layout, Kaiming initialiser and FLOP
+    # count agree with the oracle's network definition and with the library
+    from oracle import rdn as ordn
+    from paper_2106_12802_gb300 import rdn
+    for s in (2, 4, 8):
+        for c in (9, 18):
+            assert rdn.layers(s, c) == ordn.layers_for(s, c)
+            assert rdn.nparams(s, c) == ordn.nparams(s, c) == rdn.kaiming_params(s, c).size
+            assert rdn.flops_per_lr_pixel(s, c) == ordn.flops_per_lr_pixel(s, c)
