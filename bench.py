@@ -403,6 +403,33 @@ def batched_serving(mrs, params, n_jobs=32, n_scenes=4, psnr_jobs=4, seed=5):
 
 
 # ----------------------------------------------------------------------------
+# the spp study of Sec. 5 (Table comp_spp) on procedural scenes
+# ----------------------------------------------------------------------------
+def spp_study(mrs, s=S, size=512, train_scenes=12, steps=2000):
+    """Trains the x4 network with the method's spp randomisation and scores it
+    over the (LRHS spp, HRLS spp) grid of Table comp_spp on 4 held-out scenes
+    against 2048-spp renders (mean sRGB PSNR / RelMSE, with the method
+    without the network for comparison)."""
+    from paper_2106_12802_gb300 import trainer
+    t0 = time.perf_counter()
+    data = trainer.make_dataset(range(500, 500 + train_scenes), size=size, s=s, spp_tgt=512,
+                                spp_random=True, examples_per_scene=2, seed=2)
+    net = mrs.Net(trainer.init_params(0))
+    trainer.train(net, data, steps, batch=16, crop=128, s=s, lr=1e-3, seed=0, precision="bf16",
+                  loss="robust")
+    del data
+    t_train = time.perf_counter() - t0
+    g = trainer.spp_grid(net, range(600, 604), size=size, s=s, spp_tgt=2048)
+    net.close()
+    cells = [{"lrhs_spp": a, "hrls_spp": b, **{k: round(v, 4) for k, v in r.items()}}
+             for (a, b), r in sorted(g.items())]
+    return {"training": f"{train_scenes} procedural scenes x 2 examples at {size}^2, spp pairs "
+                        f"drawn per example (Sec. 4), 512-spp targets; {steps} BF16 Adam steps, "
+                        f"batch 16 x 128^2, robust loss ({t_train:.1f} s incl. rendering)",
+            "eval": f"4 held-out scenes at {size}^2, x{s}, 2048-spp targets", "cells": cells}
+
+
+# ----------------------------------------------------------------------------
 # the method's own fusion network (Sec. 4): x4 two-encoder network at 1024^2
 # ----------------------------------------------------------------------------
 def paper_network(mrs, flush, s=S, reps=10):
@@ -579,6 +606,8 @@ def run_gpu(args, rank, world):
         extra["batched_serving"] = batched_serving(mrs, params)
     if rank == 0 and not args.no_paper_network:
         extra["paper_network_x4"] = paper_network(mrs, flush)
+    if rank == 0 and not args.quick and not args.no_spp_study:
+        extra["spp_study_x4"] = spp_study(mrs)
     if rank == 0 and not args.quick:
         stats_lr = mrs.render_stats(scene, LR, LR, SPP_LR, DEPTH, RR, 0)
         stats_hr = mrs.render_stats(scene, HR, HR, SPP_HR, DEPTH, RR, 1)
@@ -676,6 +705,7 @@ def main():
     ap.add_argument("--no-equal-psnr", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-paper-network", action="store_true")
+    ap.add_argument("--no-spp-study", action="store_true")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

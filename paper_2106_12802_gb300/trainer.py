@@ -145,3 +145,46 @@ def evaluate(net, data, s=4, precision="fp32"):
     zero.close()
     return {k: {"psnr": float(np.mean([a for a, _ in v])), "relmse": float(np.mean([b for _, b in v]))}
             for k, v in acc.items()}
+
+
+# the spp grid of the method's spp study (Sec. 5, Table comp_spp): LRHS spp
+# rows, HRLS spp columns, cells with HRLS spp below LRHS spp
+SPP_GRID_LRHS = (2, 4, 8, 16, 32, 64, 128)
+SPP_GRID_HRLS = (1, 2, 4)
+
+
+def spp_grid(net, scene_seeds, size=256, s=4, spp_tgt=1024, depth=8, rr=3, lr_spps=SPP_GRID_LRHS,
+             hr_spps=SPP_GRID_HRLS, precision="bf16", scene_fn=None, seed=7):
+    """Mean sRGB PSNR / RelMSE against a spp_tgt render, over the scenes of
+    `scene_seeds`, of the fused image and of the method without the network
+    (upsampled LRHS) for every (LRHS spp, HRLS spp) cell with HRLS < LRHS.
+    Returns {(lr_spp, hr_spp): {"psnr", "relmse", "up_psnr", "up_relmse"}}."""
+    from synth import scenes
+    scene_fn = scene_fn or (lambda sd: scenes.procedural(sd, n_spheres=24, n_large=8))
+    zero = fusion.Net(np.zeros(NPARAMS, np.float32))
+    acc = {}
+    for k, sd in enumerate(scene_seeds):
+        sc = Scene(scene_fn(sd))
+        tgt = render_image(sc, size, size, spp_tgt, depth, rr, 1000 * seed + 3 * k, aux=False,
+                           counts=False)["radiance"]
+        for a in lr_spps:
+            lr = render_image(sc, size // s, size // s, a, depth, rr, 1000 * seed + 3 * k + 1,
+                              aux=False, counts=False)["radiance"][None]
+            for b in hr_spps:
+                if b >= a:
+                    continue
+                hr = render_image(sc, size, size, b, depth, rr, 1000 * seed + 3 * k + 2, aux=True,
+                                  counts=False)
+                args = (lr, hr["radiance"][None], hr["albedo"][None], hr["normal"][None], s)
+                fused = net.fuse(*args, precision=precision)
+                up = zero.fuse(*args, precision="fp32")
+                p, r, _ = fusion.image_metrics(fused[0].contiguous(), tgt)
+                pu, ru, _ = fusion.image_metrics(up[0].contiguous(), tgt)
+                acc.setdefault((a, b), []).append((p, r, pu, ru))
+        sc.close()
+    zero.close()
+    return {key: {"psnr": float(np.mean([v[0] for v in vals])),
+                  "relmse": float(np.mean([v[1] for v in vals])),
+                  "up_psnr": float(np.mean([v[2] for v in vals])),
+                  "up_relmse": float(np.mean([v[3] for v in vals]))}
+            for key, vals in acc.items()}
