@@ -194,6 +194,16 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
         : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15,%16};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+        "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // bilinear x s upsampling of LRHS at HR pixel (x, y): half-pixel centres,
 // clamped at the borders
@@ -619,6 +629,391 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
+// ---------------------------------------------------------------------------
+// BF16 3x3 convolution with the kernel ROWS folded into the MMA N dimension.
+//
+// Input row r of a column strip meets the weights of all three kernel rows in
+// one MMA: B = [w(dy 0, dx); w(dy 1, dx); w(dy 2, dx)] (3 NOUT rows) gives
+// column block j = the contribution of row r to output row r + 1 - j.  The
+// accumulators of consecutive output rows sit in consecutive NOUT-column
+// slots of TMEM in DEcreasing order (slot(t) = (-t) mod NS for the CTA's t-th
+// output row), so one MMA with D at slot(r + 1) adds to output rows r + 1, r,
+// r - 1 at once; where the three slots wrap around the end of TMEM the MMA is
+// split in two.  The column taps dx are row-shifted A descriptors into one
+// 130-pixel box per input row (x0 - 1 .. x0 + 128), so an output pixel's sum
+// is complete in its own TMEM lane: the epilogue reads one NOUT-column slot
+// per output row, without cross-lane shuffles, and zeroes it for reuse (every
+// MMA accumulates onto zeroed TMEM).  Each input row is consumed by the 12
+// MMAs (3 dx x 4 K steps) issued right after it lands and then released, so
+// the whole ring is prefetch depth.  An output tile is 128 pixels of one row.
+//
+// Warp roles as in k_conv_tc: 0 A producer (TMA), 1 TMEM allocator + MMA
+// issuer, 2-17 epilogue (quarter q = warp % 4 of the TMEM lanes, 16 output
+// channels each), 18 residual prefetch, 19 output TMA stores.  Every wait is
+// bounded; on timeout the kernel sets *err and all roles unwind.
+constexpr int kFoldTile = 128;               // output pixels per tile (= MMA M)
+constexpr int kFoldABox = kFoldTile + 2;     // input pixels per row box (one halo each side)
+constexpr int kFoldABytes = ((kFoldABox * 128 + 1023) / 1024) * 1024;  // ring slot (1024-aligned)
+
+template <int NOUT> size_t fold_smem_bytes(int stages)
+{
+    return 1024 + 9 * NOUT * 128 + (size_t)stages * kFoldABytes + (size_t)kSlots * kFoldTile * 128 +
+           64 * 4 + 8 * (2 * stages + 1 + 2 * (512 / NOUT) + 3 * kSlots) + 16;
+}
+
+template <int NOUT>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_conv_fold(const __grid_constant__ CUtensorMap tmap_x, const __grid_constant__ CUtensorMap tmap_w,
+                const __grid_constant__ CUtensorMap tmap_res,
+                const __grid_constant__ CUtensorMap tmap_out, TcConvArgs a, int stages)
+{
+    constexpr int NS = 512 / NOUT;                            // TMEM accumulator slots
+    constexpr int WBYTES = 9 * NOUT * 128;
+    constexpr int SBYTES = kFoldTile * 128;
+    constexpr int BROWS = 3 * NOUT;                           // B rows per dx: dy 0, 1, 2
+    constexpr uint32_t kTmemCols = 512;
+
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* sW = smem;
+    uint8_t* sA = smem + ((WBYTES + 1023) & ~1023);
+    uint8_t* sS = sA + stages * kFoldABytes;
+    float* sBias = (float*)(sS + kSlots * SBYTES);
+    uint64_t* bars = (uint64_t*)(sBias + 64);
+    uint64_t* full = bars;
+    uint64_t* empty = bars + stages;
+    uint64_t* wbar = bars + 2 * stages;
+    uint64_t* tfull = wbar + 1;                               // [NS] output row complete
+    uint64_t* sfree = tfull + NS;                             // [NS] slot read and zeroed
+    uint64_t* rfull = sfree + NS;
+    uint64_t* rempty = rfull + kSlots;
+    uint64_t* edone = rempty + kSlots;
+    uint32_t* tslot = (uint32_t*)(edone + kSlots);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int XB = (a.W + kFoldTile - 1) / kFoldTile;
+    const long long T = (long long)a.N * XB * a.H;
+    const long long f0 = T * blockIdx.x / gridDim.x, f1 = T * (blockIdx.x + 1) / gridDim.x;
+    const bool bf_out = a.mode == TC_RELU_BF16 || a.mode == TC_RESID_BF16 ||
+                        a.mode == TC_LIN_BF16 || a.mode == TC_MASK_BF16 ||
+                        a.mode == TC_RESRELU_BF16;
+    const bool loads_res = a.mode == TC_RESID_BF16 || a.mode == TC_MASK_BF16 ||
+                           a.mode == TC_RESRELU_BF16;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < stages; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
+        mbar_init(wbar, 1);
+        for (int i = 0; i < NS; ++i) {
+            mbar_init(&tfull[i], 1);
+            mbar_init(&sfree[i], kEpiWarps);
+        }
+        for (int i = 0; i < kSlots; ++i) {
+            mbar_init(&rfull[i], 1);
+            mbar_init(&rempty[i], 1);
+            mbar_init(&edone[i], kEpiWarps);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (threadIdx.x < 64) sBias[threadIdx.x] = threadIdx.x < NOUT ? a.bias[threadIdx.x] : 0.0f;
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tslot)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *(volatile uint32_t*)tslot;
+    // every accumulator slot starts at zero (the MMAs always accumulate)
+    if (warp >= 2 && warp < 2 + kEpiWarps) {
+        const int q = warp & 3, grp = (warp - 2) >> 2;
+        uint32_t z[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) z[e] = 0u;
+        for (int c = grp * 16; c < (int)kTmemCols; c += 64) tmem_st16(tmem + ((uint32_t)(q * 32) << 16) + c, z);
+        tmem_wait_st();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+
+    if (warp == 0) {
+        // A producer: input rows y0-1 .. y1 of each piece, 130 pixels from x0-1
+        if (lane == 0) {
+            mbar_expect_tx(wbar, WBYTES);
+            // tap (dy, dx) at B row (3 dx + dy) NOUT: per dx the three kernel rows are contiguous
+            for (int t = 0; t < 9; ++t)
+                tma_load_2d(sW + ((t % 3) * 3 + t / 3) * NOUT * 128, &tmap_w, 0, t * NOUT, wbar);
+            uint32_t it = 0;
+            bool ok = true;
+            for (long long f = f0; ok && f < f1;) {
+                int xb, n, y0, y1;
+                piece_rows(f, f1, XB, a.H, xb, n, y0, y1);
+                for (int r = y0 - 1; r <= y1; ++r, ++it) {
+                    int s = it % stages;
+                    if (!mbar_wait(&empty[s], ((it / stages) & 1) ^ 1, a.err)) { ok = false; break; }
+                    mbar_expect_tx(&full[s], kFoldABox * 128);
+                    tma_load_4d(sA + s * kFoldABytes, &tmap_x, 0, xb * kFoldTile - 1, r, n, &full[s]);
+                }
+            }
+        }
+    } else if (warp == kResWarp) {
+        if (lane == 0) {
+            uint32_t j = 0;
+            bool ok = true;
+            for (long long f = f0; ok && f < f1;) {
+                int xb, n, y0, y1;
+                piece_rows(f, f1, XB, a.H, xb, n, y0, y1);
+                for (int y = y0; y < y1; ++y, ++j) {
+                    uint32_t slot = j % kSlots, use = j / kSlots;
+                    if (!mbar_wait(&rempty[slot], (use & 1) ^ 1, a.err)) { ok = false; break; }
+                    if (loads_res) {
+                        mbar_expect_tx(&rfull[slot], SBYTES);
+                        tma_load_4d(sS + slot * SBYTES, &tmap_res, 0, xb * kFoldTile, y, n, &rfull[slot]);
+                    } else {
+                        mbar_arrive(&rfull[slot]);
+                    }
+                }
+            }
+        }
+    } else if (warp == kStoreWarp) {
+        if (lane == 0) {
+            uint32_t j = 0;
+            bool ok = true;
+            for (long long f = f0; ok && f < f1;) {
+                int xb, n, y0, y1;
+                piece_rows(f, f1, XB, a.H, xb, n, y0, y1);
+                for (int y = y0; y < y1; ++y, ++j) {
+                    uint32_t slot = j % kSlots, use = j / kSlots;
+                    if (!mbar_wait(&edone[slot], use & 1, a.err)) { ok = false; break; }
+                    if (bf_out) {
+                        tma_store_4d(&tmap_out, sS + slot * SBYTES, 0, xb * kFoldTile, y, n);
+                        bulk_commit();
+                        bulk_wait_read0();
+                    }
+                    mbar_arrive(&rempty[slot]);
+                }
+            }
+            bulk_wait_all();
+        }
+    } else if (warp == 1) {
+        // MMA issuer: for each input row r of a piece, the blocks j whose output
+        // row r + 1 - j lies in the piece, in one MMA per (dx, K step) (two
+        // where the slots wrap)
+        if (lane == 0) {
+            bool ok = mbar_wait(wbar, 0, a.err);
+            uint32_t it = 0;
+            long long t0 = 0;                                   // CTA output-row counter at piece start
+            const uint32_t wbase = smem_u32(sW), abase = smem_u32(sA);
+            for (long long f = f0; ok && f < f1;) {
+                int xb, n, y0, y1;
+                piece_rows(f, f1, XB, a.H, xb, n, y0, y1);
+                for (int r = y0 - 1; ok && r <= y1; ++r, ++it) {
+                    const int jlo = max(0, r + 2 - y1), jhi = min(2, r + 1 - y0);
+                    const int s = it % stages;
+                    // output row of block j: CTA counter tj = t0 + (r + 1 - j - y0)
+                    const long long tlo = t0 + (r + 1 - jlo - y0);   // newest row (highest t)
+                    if (jlo == 0) {
+                        // block 0 starts output row tlo: its slot must have been read and
+                        // zeroed by the epilogue of row tlo - NS
+                        const int sl = (int)(tlo % NS);
+                        const uint32_t use = (uint32_t)(tlo / NS);
+                        if (!mbar_wait(&sfree[(NS - sl) % NS], (use & 1) ^ 1, a.err)) { ok = false; break; }
+                    }
+                    if (!mbar_wait(&full[s], (it / stages) & 1, a.err)) { ok = false; break; }
+                    tc_fence_after();
+                    const int nb = jhi - jlo + 1;
+                    const int c0 = (int)((NS - (int)(tlo % NS)) % NS);   // slot of block jlo
+                    const int n1 = min(nb, NS - c0);                    // blocks before the wrap
+                    // all MMAs of one D region back to back: the region before
+                    // the wrap, then (rarely) the one after it; consecutive
+                    // MMAs into different regions do not pipeline
+                    for (int part = 0; part < (n1 < nb ? 2 : 1); ++part) {
+                        const uint32_t dcol = part ? 0u : (uint32_t)(c0 * NOUT);
+                        const int b0 = part ? n1 : 0, nbp = part ? nb - n1 : n1;
+                        const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) |
+                                               ((uint32_t)((nbp * NOUT) >> 3) << 17) |
+                                               ((uint32_t)(kFoldTile >> 4) << 24);
+#pragma unroll
+                        for (int dx = 0; dx < 3; ++dx) {
+                            const uint32_t brow = (uint32_t)(dx * BROWS + (jlo + b0) * NOUT);
+#pragma unroll
+                            for (int k = 0; k < 4; ++k)
+                                mma_f16(tmem + dcol, sdesc(abase + s * kFoldABytes + dx * 128 + k * 32, 128),
+                                        sdesc(wbase + brow * 128 + k * 32, 128), idesc, 1u);
+                        }
+                    }
+                    mma_commit(&empty[s]);
+                    if (jhi == 2) {
+                        // output row r - 1 (block 2) is complete
+                        const long long td = tlo - (2 - jlo);
+                        mma_commit(&tfull[(NS - (int)(td % NS)) % NS]);
+                    }
+                }
+                t0 += y1 - y0;
+            }
+        }
+    } else {
+        // epilogue: warp w reads TMEM lanes 32 q .. 32 q + 31 (output pixels
+        // x0 + 32 q + lane) and channels [16 grp, 16 grp + 16) of the finished
+        // output row's slot, then zeroes them
+        const int q = warp & 3, grp = (warp - 2) >> 2;
+        const int j = q * 32 + lane;
+        const bool active = grp * 16 < NOUT;
+        uint32_t lt = 0;
+        bool stop = false;
+        for (long long f = f0; !stop && f < f1;) {
+          int xb, n, y0, y1;
+          piece_rows(f, f1, XB, a.H, xb, n, y0, y1);
+          for (int y = y0; y < y1; ++y, ++lt) {
+            const int sl = (int)((NS - (int)(lt % NS)) % NS);
+            const uint32_t use = lt / NS;
+            const uint32_t slot = lt % kSlots, suse = lt / kSlots;
+            const int x = xb * kFoldTile + j;
+            const bool valid = x < a.W;
+            const size_t p = ((size_t)n * a.H + y) * a.W + (valid ? x : 0);
+            float4 pre[4];
+            const bool pre_ok = a.acc_in && valid && active && (bf_out || a.cout == 64);
+            if (pre_ok) {
+                const float4* ap = (const float4*)(a.acc_in + p * 64 + grp * 16);
+#pragma unroll
+                for (int i4 = 0; i4 < 4; ++i4) pre[i4] = ap[i4];
+            }
+            if (!mbar_wait_warp(&tfull[sl], use & 1, a.err)) { stop = true; break; }
+            tc_fence_after();
+            if (!mbar_wait_warp(&rfull[slot], suse & 1, a.err)) { stop = true; break; }
+            uint8_t* srow = sS + slot * SBYTES;
+            if (active) {
+                const int c0 = grp * 16;
+                const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(sl * NOUT + c0);
+                uint32_t r0[16];
+                tmem_ld16(taddr, r0);
+                tmem_wait_ld();
+                uint32_t z[16];
+#pragma unroll
+                for (int e = 0; e < 16; ++e) z[e] = 0u;
+                tmem_st16(taddr, z);
+                float v[16];
+#pragma unroll
+                for (int e = 0; e < 16; ++e) v[e] = __uint_as_float(r0[e]);
+                if (bf_out) {
+                    float o[16];
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) o[e] = v[e] + sBias[c0 + e];
+                    if (pre_ok) {
+#pragma unroll
+                        for (int i4 = 0; i4 < 4; ++i4) {
+                            o[4 * i4] += pre[i4].x; o[4 * i4 + 1] += pre[i4].y;
+                            o[4 * i4 + 2] += pre[i4].z; o[4 * i4 + 3] += pre[i4].w;
+                        }
+                    } else if (a.acc_in && valid) {
+                        const float* ap = a.acc_in + p * 64 + c0;
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) o[e] += ap[e];
+                    }
+                    if (a.mode == TC_RELU_BF16) {
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) o[e] = fmaxf(o[e], 0.0f);
+                    } else if (a.mode == TC_MASK_BF16) {
+#pragma unroll
+                        for (int jj = 0; jj < 2; ++jj) {
+                            uint4 u = *(const uint4*)(srow + sw128(j, c0 / 8 + jj));
+                            const __nv_bfloat162* h2 = (const __nv_bfloat162*)&u;
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                float2 fv = __bfloat1622float2(h2[e]);
+                                if (!(fv.x > 0.0f)) o[8 * jj + 2 * e] = 0.0f;
+                                if (!(fv.y > 0.0f)) o[8 * jj + 2 * e + 1] = 0.0f;
+                            }
+                        }
+                    } else if (a.mode == TC_RESID_BF16 || a.mode == TC_RESRELU_BF16) {
+                        const bool rl = a.mode == TC_RESRELU_BF16;
+#pragma unroll
+                        for (int jj = 0; jj < 2; ++jj) {
+                            uint4 u = *(const uint4*)(srow + sw128(j, c0 / 8 + jj));
+                            const __nv_bfloat162* h2 = (const __nv_bfloat162*)&u;
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                float2 fv = __bfloat1622float2(h2[e]);
+                                float o0 = o[8 * jj + 2 * e], o1 = o[8 * jj + 2 * e + 1];
+                                if (rl) { o0 = fmaxf(o0, 0.0f); o1 = fmaxf(o1, 0.0f); }
+                                o[8 * jj + 2 * e] = fv.x + o0;
+                                o[8 * jj + 2 * e + 1] = fv.y + o1;
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int jj = 0; jj < 2; ++jj) {
+                        uint4 u;
+                        __nv_bfloat162* h2 = (__nv_bfloat162*)&u;
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            h2[e] = __floats2bfloat162_rn(o[8 * jj + 2 * e], o[8 * jj + 2 * e + 1]);
+                        *(uint4*)(srow + sw128(j, c0 / 8 + jj)) = u;
+                    }
+                } else if (valid) {
+                    if (a.mode == TC_FINAL_F32) {
+                        if (c0 == 0) {
+                            float up[3];
+                            bilinear(a.lrhs + (size_t)n * (a.H / a.scale) * (a.W / a.scale) * 3,
+                                     a.H / a.scale, a.W / a.scale, a.scale, x, y, up);
+                            float* op = (float*)a.out + p * 3;
+                            for (int c = 0; c < 3; ++c) op[c] = (v[c] + sBias[c]) + up[c];
+                        }
+                    } else if (a.cout == 64 && ((uintptr_t)a.out & 15) == 0) {
+                        float4* op = (float4*)((float*)a.out + p * 64 + c0);
+                        const float4* ap = a.acc_in ? (const float4*)(a.acc_in + p * 64 + c0) : nullptr;
+                        float4 u4[4];
+#pragma unroll
+                        for (int i4 = 0; i4 < 4; ++i4)
+                            u4[i4] = pre_ok ? pre[i4] : (ap ? ap[i4] : make_float4(0.f, 0.f, 0.f, 0.f));
+#pragma unroll
+                        for (int i4 = 0; i4 < 4; ++i4) {
+                            float4 t = make_float4(v[4 * i4] + sBias[c0 + 4 * i4],
+                                                   v[4 * i4 + 1] + sBias[c0 + 4 * i4 + 1],
+                                                   v[4 * i4 + 2] + sBias[c0 + 4 * i4 + 2],
+                                                   v[4 * i4 + 3] + sBias[c0 + 4 * i4 + 3]);
+                            t.x += u4[i4].x; t.y += u4[i4].y; t.z += u4[i4].z; t.w += u4[i4].w;
+                            if (a.relu) {
+                                t.x = fmaxf(t.x, 0.0f); t.y = fmaxf(t.y, 0.0f);
+                                t.z = fmaxf(t.z, 0.0f); t.w = fmaxf(t.w, 0.0f);
+                            }
+                            op[i4] = t;
+                        }
+                    } else {
+                        float* op = (float*)a.out + p * a.cout;
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) {
+                            if (c0 + e < a.cout) {
+                                float o = v[e] + sBias[c0 + e];
+                                if (a.acc_in) o += a.acc_in[p * a.cout + c0 + e];
+                                op[c0 + e] = a.relu ? fmaxf(o, 0.0f) : o;
+                            }
+                        }
+                    }
+                }
+                tmem_wait_st();
+            }
+            // the slot is read and zeroed; the staging slot goes to the store warp
+            tc_fence_before();
+            if (bf_out) fence_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&sfree[sl]);
+                mbar_arrive(&edone[slot]);
+            }
+          }
+        }
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kTmemCols));
+    }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -662,6 +1057,30 @@ mrs_status launch(const TcConvArgs& a, cudaStream_t st)
     const CUtensorMap* res = a.tmap_res ? a.tmap_res : a.tmap_x;
     const CUtensorMap* out = a.tmap_out ? a.tmap_out : a.tmap_x;
     MRS_TIMED(PK_CONV_TC, st, (k_conv_tc<NOUT, OPER><<<grid, kThreads, smem, st>>>(*a.tmap_x, *a.tmap_w, *res, *out, b, stages)));
+    MRS_LAUNCHED(1);
+    return cuda_status(cudaGetLastError(), "conv launch");
+}
+
+template <int NOUT>
+mrs_status launch_fold(const TcConvArgs& a, cudaStream_t st)
+{
+    int stages = 4;
+    while (fold_smem_bytes<NOUT>(stages + 1) <= 227 * 1024 && stages < 12) ++stages;
+    size_t smem = fold_smem_bytes<NOUT>(stages);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_conv_fold<NOUT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_status(e, "conv smem attribute");
+        attr = true;
+    }
+    TcConvArgs b = a;
+    const long long T = (long long)a.N * ((a.W + kFoldTile - 1) / kFoldTile) * a.H;
+    int grid = T < sm_count() ? (int)T : sm_count();
+    if (grid < 1) return MRS_OK;
+    const CUtensorMap* res = a.tmap_res ? a.tmap_res : a.tmap_x;
+    const CUtensorMap* out = a.tmap_out ? a.tmap_out : a.tmap_x;
+    MRS_TIMED(PK_CONV_TC, st, (k_conv_fold<NOUT><<<grid, kThreads, smem, st>>>(*a.tmap_x, *a.tmap_w, *res, *out, b, stages)));
     MRS_LAUNCHED(1);
     return cuda_status(cudaGetLastError(), "conv launch");
 }
@@ -764,8 +1183,8 @@ mrs_status tc_conv3x3(const TcConvArgs& a, cudaStream_t st)
         set_error("tc_conv3x3: acc_in must be 16-byte aligned, with bf16 operands");
         return MRS_ERR_ARG;
     }
-    if (a.nout == 64) return a.operand == TC_BF16 ? launch<64, TC_BF16>(a, st) : launch<64, TC_FP8>(a, st);
-    if (a.nout == 16) return a.operand == TC_BF16 ? launch<16, TC_BF16>(a, st) : launch<16, TC_FP8>(a, st);
+    if (a.nout == 64) return a.operand == TC_BF16 ? launch_fold<64>(a, st) : launch<64, TC_FP8>(a, st);
+    if (a.nout == 16) return a.operand == TC_BF16 ? launch_fold<16>(a, st) : launch<16, TC_FP8>(a, st);
     set_error("tc_conv3x3: nout must be 64 or 16");
     return MRS_ERR_ARG;
 }

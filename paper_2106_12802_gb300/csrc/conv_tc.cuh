@@ -57,6 +57,11 @@ struct TcConvArgs {
 // pixel on each side); residual and output maps move a tile's 120 pixels.
 constexpr int kABox = 32;
 constexpr int kOutBox = 120;
+// BF16 operands run the row-folded kernel: one 130-pixel A box per input
+// row (128 outputs plus a halo pixel on each side) and 128-pixel residual /
+// output boxes.  Maps passed to tc_conv3x3 use these box widths.
+inline int tc_a_box(int operand) { return operand == TC_BF16 ? 130 : kABox; }
+inline int tc_out_box(int operand) { return operand == TC_BF16 ? 128 : kOutBox; }
 // Encode a tiled tensor map for a [N][H][W][64] activation tensor (rows of 128
 // bytes in bf16, 64 in fp8): box = box_px pixels of one image row.
 mrs_status tc_make_act_map(CUtensorMap* m, const void* ptr, int N, int H, int W, int operand,

@@ -776,11 +776,12 @@ mrs_status fuse_tc(mrs_net_s* net, const float* lrhs, const float* hrls, const f
     // residual / output maps (128-pixel boxes)
     CUtensorMap mx, mh, mr, oh, orr;
     int oper = f8 ? TC_FP8 : TC_BF16;
-    if ((rc = tc_make_act_map(&mx, f8 ? (void*)x08 : x0, N, H, W, oper, kABox)) != MRS_OK) return rc;
-    if ((rc = tc_make_act_map(&mh, f8 ? (void*)h8 : h, N, H, W, oper, kABox)) != MRS_OK) return rc;
-    if ((rc = tc_make_act_map(&mr, f8 ? (void*)r8 : r, N, H, W, oper, kABox)) != MRS_OK) return rc;
-    if ((rc = tc_make_act_map(&oh, h, N, H, W, TC_BF16, kOutBox)) != MRS_OK) return rc;
-    if ((rc = tc_make_act_map(&orr, r, N, H, W, TC_BF16, kOutBox)) != MRS_OK) return rc;
+    const int abox = tc_a_box(oper), obox = tc_out_box(oper);
+    if ((rc = tc_make_act_map(&mx, f8 ? (void*)x08 : x0, N, H, W, oper, abox)) != MRS_OK) return rc;
+    if ((rc = tc_make_act_map(&mh, f8 ? (void*)h8 : h, N, H, W, oper, abox)) != MRS_OK) return rc;
+    if ((rc = tc_make_act_map(&mr, f8 ? (void*)r8 : r, N, H, W, oper, abox)) != MRS_OK) return rc;
+    if ((rc = tc_make_act_map(&oh, h, N, H, W, TC_BF16, obox)) != MRS_OK) return rc;
+    if ((rc = tc_make_act_map(&orr, r, N, H, W, TC_BF16, obox)) != MRS_OK) return rc;
     TcConvArgs a;
     memset(&a, 0, sizeof(a));
     a.N = N; a.H = H; a.W = W; a.scale = s;
@@ -1045,7 +1046,7 @@ mrs_status conv3x3_chunked(Scratch& S, const float* x, int N, int H, int W, int 
         if ((rc = tc_make_w_map(&wm[j], q + j * chw, 9 * nout, nout, TC_BF16)) != MRS_OK) return rc;
     }
     CUtensorMap mx;
-    if ((rc = tc_make_act_map(&mx, xq, N, H, W, TC_BF16, kABox)) != MRS_OK) return rc;
+    if ((rc = tc_make_act_map(&mx, xq, N, H, W, TC_BF16, tc_a_box(TC_BF16))) != MRS_OK) return rc;
     TcConvArgs a;
     memset(&a, 0, sizeof(a));
     a.tmap_x = &mx; a.out = out; a.N = N; a.H = H; a.W = W; a.scale = 1; a.nout = nout;
@@ -1139,7 +1140,7 @@ extern "C" mrs_status mrs_conv3x3(const float* x, int32_t N, int32_t H, int32_t 
     k_to_operand<<<1024, 256, 0, st>>>(x, P, cin, xq, oper == TC_FP8, 1.0f / xscale);
     MRS_LAUNCHED(1);
     CUtensorMap mx, mw;
-    if ((rc = tc_make_act_map(&mx, xq, N, H, W, oper, kABox)) != MRS_OK) return rc;
+    if ((rc = tc_make_act_map(&mx, xq, N, H, W, oper, tc_a_box(oper))) != MRS_OK) return rc;
     if ((rc = tc_make_w_map(&mw, wp, 9 * nout, nout, oper)) != MRS_OK) return rc;
     TcConvArgs a;
     memset(&a, 0, sizeof(a));
@@ -1343,8 +1344,8 @@ mrs_status train_step_bf16(mrs_net_s* net, const float* lrhs, const float* hrls,
     const auto& L = shapes(net->cin0);
 
     // tensor maps: A operands (32-pixel boxes) and residual / output (120-pixel)
-    auto amap = [&](CUtensorMap* m, const void* ptr) { return tc_make_act_map(m, ptr, N, H, W, TC_BF16, kABox); };
-    auto omap = [&](CUtensorMap* m, const void* ptr) { return tc_make_act_map(m, ptr, N, H, W, TC_BF16, kOutBox); };
+    auto amap = [&](CUtensorMap* m, const void* ptr) { return tc_make_act_map(m, ptr, N, H, W, TC_BF16, tc_a_box(TC_BF16)); };
+    auto omap = [&](CUtensorMap* m, const void* ptr) { return tc_make_act_map(m, ptr, N, H, W, TC_BF16, tc_out_box(TC_BF16)); };
     std::vector<CUtensorMap> hA(9), hO(9), rA(8), rO(8);
     CUtensorMap x0A, dybA, dhA, dhO, daA, daO;
     for (int k = 0; k < 9 && rc == MRS_OK; ++k) {

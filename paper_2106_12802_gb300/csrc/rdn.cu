@@ -453,12 +453,13 @@ mrs_status rdn_bf16(mrs_rdn_s* r, const float* lrhs, const float* hrls, const fl
     MRS_LAUNCHED(1);
     if ((rc = cuda_status(cudaGetLastError(), "rdn input")) != MRS_OK) return rc;
 
-    // tensor maps: A operands (kABox boxes) and outputs / residuals (kOutBox)
+    // tensor maps: A operands and outputs / residuals, with the box widths of
+    // the BF16 tensor-core conv
     auto amap = [&](CUtensorMap* m, const void* p, int n, int hh, int ww) {
-        return tc_make_act_map(m, p, n, hh, ww, TC_BF16, kABox);
+        return tc_make_act_map(m, p, n, hh, ww, TC_BF16, tc_a_box(TC_BF16));
     };
     auto omap = [&](CUtensorMap* m, const void* p, int n, int hh, int ww) {
-        return tc_make_act_map(m, p, n, hh, ww, TC_BF16, kOutBox);
+        return tc_make_act_map(m, p, n, hh, ww, TC_BF16, tc_out_box(TC_BF16));
     };
     CUtensorMap inLA, inHA, FlrA, FlrO, Fh0O, F0A, F0O, XA[kX], XO[kX];
     if ((rc = amap(&inLA, inL, N, h, w)) != MRS_OK) return rc;
@@ -477,7 +478,7 @@ mrs_status rdn_bf16(mrs_rdn_s* r, const float* lrhs, const float* hrls, const fl
     for (int q = 0; q < s * s && rc == MRS_OK; ++q) {
         int oy = q / s, ox = q % s;
         rc = tc_make_view_map(&dsf[q], Fh0 + ((size_t)oy * W + ox) * 64, N, h, w, (long long)s * 128,
-                              (long long)s * W * 128, (long long)H * W * 128, kABox);
+                              (long long)s * W * 128, (long long)H * W * 128, tc_a_box(TC_BF16));
     }
     if (rc != MRS_OK) return rc;
 
@@ -561,7 +562,8 @@ mrs_status rdn_bf16(mrs_rdn_s* r, const float* lrhs, const float* hrls, const fl
             int dy = q >> 1, dx = q & 1;
             CUtensorMap vo;
             rc = tc_make_view_map(&vo, nx + ((size_t)dy * 2 * cw + dx) * 64, N, ch, cw, 256,
-                                  (long long)4 * cw * 128, (long long)4 * ch * cw * 128, kOutBox);
+                                  (long long)4 * cw * 128, (long long)4 * ch * cw * 128,
+                                  tc_out_box(TC_BF16));
             if (rc != MRS_OK) return rc;
             a.H = ch; a.W = cw;
             const WChunk& c = r->ch[r->first[li] + q];
