@@ -30,6 +30,7 @@
 // freed, and the host reports MRS_ERR_TIMEOUT.
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
+#include <string.h>
 
 #include "conv_tc.cuh"
 
@@ -737,6 +738,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    // programmatic dependent launch: the next conv may be scheduled now; every
+    // access to data of the previous kernel in the stream waits for its
+    // completion (griddepcontrol.wait).  The weights and biases come from
+    // before the previous kernel (packed at set-up or by a non-overlapping
+    // kernel), so the weight load is issued before that wait.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    if (!(warp == 0 && lane == 0)) asm volatile("griddepcontrol.wait;" ::: "memory");
 
     if (warp == 0) {
         // A producer: input rows y0-1 .. y1 of each piece, 130 pixels from x0-1
@@ -745,6 +753,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             // tap (dy, dx) at B row (3 dx + dy) NOUT: per dx the three kernel rows are contiguous
             for (int t = 0; t < 9; ++t)
                 tma_load_2d(sW + ((t % 3) * 3 + t / 3) * NOUT * 128, &tmap_w, 0, t * NOUT, wbar);
+            asm volatile("griddepcontrol.wait;" ::: "memory");
             uint32_t it = 0;
             bool ok = true;
             for (long long f = f0; ok && f < f1;) {
@@ -1080,8 +1089,21 @@ mrs_status launch_fold(const TcConvArgs& a, cudaStream_t st)
     if (grid < 1) return MRS_OK;
     const CUtensorMap* res = a.tmap_res ? a.tmap_res : a.tmap_x;
     const CUtensorMap* out = a.tmap_out ? a.tmap_out : a.tmap_x;
-    MRS_TIMED(PK_CONV_TC, st, (k_conv_fold<NOUT><<<grid, kThreads, smem, st>>>(*a.tmap_x, *a.tmap_w, *res, *out, b, stages)));
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute la[1];
+    la[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    la[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = la;
+    cfg.numAttrs = 1;
+    cudaError_t le = cudaSuccess;
+    MRS_TIMED(PK_CONV_TC, st, (le = cudaLaunchKernelEx(&cfg, k_conv_fold<NOUT>, *a.tmap_x, *a.tmap_w, *res, *out, b, stages)));
     MRS_LAUNCHED(1);
+    if (le != cudaSuccess) return cuda_status(le, "conv launch");
     return cuda_status(cudaGetLastError(), "conv launch");
 }
 
