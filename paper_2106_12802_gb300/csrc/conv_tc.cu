@@ -1,33 +1,30 @@
 // 3x3 convolution as an implicit GEMM on the 5th-generation tensor cores
-// (tcgen05.mma, accumulators in TMEM, operands staged by TMA).
+// (tcgen05.mma, accumulators in TMEM, operands staged by TMA), BF16 or
+// FP8-E4M3 operands with FP32 accumulation, and the weight gradient of the
+// same convolution (k_wgrad_tc, below).
 //
-// GEMM view of one layer: M = output pixels, N = output channels (64, or 16
-// for the 3-channel head padded to 16), K = 9 taps x 64 input channels.  A CTA
-// tile is 128 consecutive pixels of one image row.  Each activation row (64
-// channels) is 128 bytes (bf16) or 64 bytes (fp8), stored with the matching
-// TMA swizzle so the smem descriptors address it directly.
-//   bf16: per kernel row dy one TMA box of 130 pixels (columns x0-1 .. x0+128
-//         of input row y+dy-1) feeds the three taps dx = 0, 1, 2 through
-//         descriptors whose start is shifted by dx rows (3 boxes per tile);
-//   fp8:  one 128-pixel box per tap (9 per tile; a 64-byte row shift is not
-//         expressible within the 64B swizzle pattern).
-// Out-of-range parts of a box are zero-filled: this is the zero padding.  All
-// 9 taps of the layer's weights stay resident in shared memory for the whole
-// persistent CTA.
+// The convolution (k_conv_fold) folds the three kernel ROWS into the MMA N
+// dimension; see the comment above the kernel for the schedule.  Each
+// activation row (64 channels) is 128 bytes (bf16) or 64 bytes (fp8), stored
+// with the matching TMA swizzle (128B / 64B) so that the shared-memory
+// descriptors address it directly; out-of-range parts of a TMA box are
+// zero-filled, which is the convolution's zero padding.  All 9 taps of the
+// layer's weights stay resident in shared memory for the whole persistent CTA.
 //
 // Warp roles (640 threads, one CTA per SM):
-//   warp 0: TMA producer (weights once, then A boxes through an S-stage ring)
-//   warp 18: residual prefetch into one of three staging slots
-//   warp 19: output TMA stores from the staging slots
+//   warp 0: TMA producer (weights once, then one A box per input row through
+//           an S-stage ring)
 //   warp 1: TMEM allocator and MMA issuer (one thread)
 //   warps 2-17: epilogue; warp w reads TMEM lanes 32 (w % 4) .. + 31 and 16 of
-//           the 64 output channels: bias, ReLU / residual / bilinear skip,
-//           BF16 results written into the staging slot (swizzled) and sent out
-//           by one TMA store per tile
-// The TMEM accumulator is double-buffered so the epilogue of tile i overlaps
-// the MMAs of tile i+1.  Every wait is bounded (no hardware barrier inside the
-// role loops): on timeout the kernel sets *err, all roles unwind, TMEM is
-// freed, and the host reports MRS_ERR_TIMEOUT.
+//           the 64 output channels: dequantisation (fp8), bias, ReLU /
+//           residual / mask / FP32 partial sum / bilinear skip, BF16 results
+//           written into the staging slot (swizzled) and sent out by one TMA
+//           store per tile, or FP32 results stored directly
+//   warp 18: residual prefetch into one of three staging slots
+//   warp 19: output TMA stores from the staging slots
+// Every wait is bounded (no hardware barrier inside the role loops): on
+// timeout the kernel sets *err, all roles unwind, TMEM is freed, and the host
+// reports MRS_ERR_TIMEOUT.
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 #include <string.h>
@@ -37,13 +34,7 @@
 namespace mrs {
 namespace {
 
-constexpr int kTileM = 128;          // MMA M: pixels x0-1 .. x0+126 of one image row
-constexpr int kQuarter = 30;         // output pixels per 32-lane TMEM quarter
-constexpr int kTileOut = 4 * kQuarter;   // output pixels per tile
 constexpr int kEpiWarps = 16;                  // 4 per TMEM lane quarter
-constexpr int kEpiGroups = kEpiWarps / 4;      // channel groups per quarter
-constexpr int kEpiCh = 64 / kEpiGroups;        // output channels per epilogue warp
-constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kResWarp = 2 + kEpiWarps;        // residual-prefetch warp
 constexpr int kStoreWarp = kResWarp + 1;       // output-store warp
 constexpr int kThreads = 32 * (kStoreWarp + 1);  // A-TMA, MMA, epilogue, residual, store warps
@@ -243,7 +234,7 @@ __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wa
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // Work split: the layer is T = N * XB * H tiles (one tile = one output row of
-// one 120-pixel column strip), flattened as f = (n * XB + xb) * H + y.  CTA c
+// one 128-pixel column strip), flattened as f = (n * XB + xb) * H + y.  CTA c
 // takes the contiguous run [T c / G, T (c + 1) / G), cut at strip boundaries
 // into pieces; a piece is a run of rows of one strip, streamed through the
 // input-row ring with its own halo rows.  piece_rows returns the piece that
@@ -263,375 +254,8 @@ __device__ __forceinline__ void piece_rows(long long& f, long long f1, int XB, i
 // byte offset of 16-byte chunk j of row m in a SWIZZLE_128B tile
 __device__ __forceinline__ uint32_t sw128(int m, int j) { return m * 128 + ((j ^ (m & 7)) << 4); }
 
-template <int NOUT, int OPER>
-__global__ void __launch_bounds__(kThreads, 1)
-    k_conv_tc(const __grid_constant__ CUtensorMap tmap_x, const __grid_constant__ CUtensorMap tmap_w,
-              const __grid_constant__ CUtensorMap tmap_res,
-              const __grid_constant__ CUtensorMap tmap_out, TcConvArgs a, int stages)
-{
-    constexpr int ROWB = OPER == TC_BF16 ? 128 : 64;          // bytes per activation row
-    constexpr int ABYTES = kTileM * ROWB;                     // one input row of the ring
-    constexpr int NF = 3 * NOUT;                              // MMA N: (dx, cout) columns
-    constexpr int WBYTES = 9 * NOUT * ROWB;                   // all taps of the weights
-    constexpr int KSTEPS = OPER == TC_BF16 ? 4 : 2;           // MMAs per kernel row (K 16 / 32)
-    constexpr int SBYTES = kTileM * 128;                      // residual / output staging slot
-    constexpr int ACCSTRIDE = 256;                            // TMEM columns per accumulator
-    constexpr int CHUNKS = NOUT == 64 ? kEpiCh / 16 : 1;      // 16-channel chunks per warp
-    constexpr uint32_t IDESC =
-        (1u << 4) | ((OPER == TC_BF16 ? 1u : 0u) << 7) | ((OPER == TC_BF16 ? 1u : 0u) << 10) |
-        ((uint32_t)(NF >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
-    constexpr uint32_t kTmemCols = 512;
-
-    extern __shared__ uint8_t smem_raw[];
-    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint8_t* sW = smem;
-    uint8_t* sA = smem + ((WBYTES + 1023) & ~1023);
-    uint8_t* sS = sA + stages * ABYTES;                       // kSlots staging slots
-    float* sBias = (float*)(sS + kSlots * SBYTES);            // 64 floats
-    uint64_t* bars = (uint64_t*)(sBias + 64);
-    uint64_t* full = bars;
-    uint64_t* empty = bars + stages;
-    uint64_t* wbar = bars + 2 * stages;
-    uint64_t* tfull = wbar + 1;
-    uint64_t* tempty = tfull + 2;
-    uint64_t* rfull = tempty + 2;
-    uint64_t* rempty = rfull + kSlots;
-    uint64_t* edone = rempty + kSlots;                        // epilogue warps done with a slot
-    uint32_t* tslot = (uint32_t*)(edone + kSlots);
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int XB = (a.W + kTileOut - 1) / kTileOut;
-    const long long T = (long long)a.N * XB * a.H;
-    const long long f0 = T * blockIdx.x / gridDim.x, f1 = T * (blockIdx.x + 1) / gridDim.x;
-    const bool bf_out = a.mode == TC_RELU_BF16 || a.mode == TC_RESID_BF16 ||
-                        a.mode == TC_LIN_BF16 || a.mode == TC_MASK_BF16 ||
-                        a.mode == TC_RESRELU_BF16;
-    const bool loads_res = a.mode == TC_RESID_BF16 || a.mode == TC_MASK_BF16 ||
-                           a.mode == TC_RESRELU_BF16;
-
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < stages; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
-        mbar_init(wbar, 1);
-        for (int i = 0; i < 2; ++i) {
-            mbar_init(&tfull[i], 1);
-            mbar_init(&tempty[i], kEpiWarps);
-        }
-        for (int i = 0; i < kSlots; ++i) {
-            mbar_init(&rfull[i], 1);
-            mbar_init(&rempty[i], 1);
-            mbar_init(&edone[i], kEpiWarps);
-        }
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    }
-    if (threadIdx.x < 64) sBias[threadIdx.x] = threadIdx.x < NOUT ? a.bias[threadIdx.x] : 0.0f;
-    if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                         smem_u32(tslot)),
-                     "r"(kTmemCols));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = *(volatile uint32_t*)tslot;
-
-    if (warp == 0) {
-        // A producer: input rows y0-1 .. y1 of the job's strip, 128 pixels from
-        // x0-1, each loaded once into the ring
-        if (lane == 0) {
-            mbar_expect_tx(wbar, WBYTES);
-            for (int t = 0; t < 9; ++t) tma_load_2d(sW + t * NOUT * ROWB, &tmap_w, 0, t * NOUT, wbar);
-            uint32_t it = 0;
-            bool ok = true;
-            for (long long f = f0; ok && f < f1;) {
-                int xb, n, y0, y1;
-                piece_rows(f, f1, XB, a.H, xb, n, y0, y1);
-                for (int r = y0 - 1; r <= y1; ++r, ++it) {
-                    int s = it % stages;
-                    if (!mbar_wait(&empty[s], ((it / stages) & 1) ^ 1, a.err)) { ok = false; break; }
-                    mbar_expect_tx(&full[s], ABYTES);
-                    // MMA rows 32q .. 32q+31 <- pixels x0-1+30q .. x0+30+30q
-                    for (int q = 0; q < 4; ++q)
-                        tma_load_4d(sA + s * ABYTES + q * 32 * ROWB, &tmap_x, 0,
-                                    xb * kTileOut - 1 + q * kQuarter, r, n, &full[s]);
-                }
-            }
-        }
-    } else if (warp == kResWarp) {
-        // residual tiles (or just the slot hand-over) for the epilogue, kSlots ahead
-        if (lane == 0) {
-            uint32_t j = 0;
-            bool ok = true;
-            for (long long f = f0; ok && f < f1;) {
-                int xb, n, y0, y1;
-                piece_rows(f, f1, XB, a.H, xb, n, y0, y1);
-                for (int y = y0; y < y1; ++y, ++j) {
-                    uint32_t slot = j % kSlots, use = j / kSlots;
-                    if (!mbar_wait(&rempty[slot], (use & 1) ^ 1, a.err)) { ok = false; break; }
-                    if (loads_res) {
-                        mbar_expect_tx(&rfull[slot], kTileOut * 128);
-                        tma_load_4d(sS + slot * SBYTES, &tmap_res, 0, xb * kTileOut, y, n, &rfull[slot]);
-                    } else {
-                        mbar_arrive(&rfull[slot]);
-                    }
-                }
-            }
-        }
-    } else if (warp == kStoreWarp) {
-        // output stores: one TMA store per finished staging slot, then the slot
-        // is handed back to the residual warp once the store has read it
-        if (lane == 0) {
-            uint32_t j = 0;
-            bool ok = true;
-            for (long long f = f0; ok && f < f1;) {
-                int xb, n, y0, y1;
-                piece_rows(f, f1, XB, a.H, xb, n, y0, y1);
-                for (int y = y0; y < y1; ++y, ++j) {
-                    uint32_t slot = j % kSlots, use = j / kSlots;
-                    if (!mbar_wait(&edone[slot], use & 1, a.err)) { ok = false; break; }
-                    if (bf_out) {
-                        tma_store_4d(&tmap_out, sS + slot * SBYTES, 0, xb * kTileOut, y, n);
-                        bulk_commit();
-                        bulk_wait_read0();
-                    }
-                    mbar_arrive(&rempty[slot]);
-                }
-            }
-            bulk_wait_all();
-        }
-    } else if (warp == 1) {
-        // MMA issuer: per output row, for each kernel row dy one A row of the
-        // ring against the (dx, cout) x cin weight block of that dy
-        if (lane == 0) {
-            bool ok = mbar_wait(wbar, 0, a.err);
-            uint32_t it = 0, lt = 0;
-            const uint32_t wbase = smem_u32(sW), abase = smem_u32(sA);
-            for (long long f = f0; ok && f < f1;) {
-                int xb, n, y0, y1;
-                piece_rows(f, f1, XB, a.H, xb, n, y0, y1);
-                const uint32_t base = it;
-                for (int y = y0; ok && y < y1; ++y, ++lt) {
-                    uint32_t acc = lt & 1, use = lt >> 1;
-                    if (!mbar_wait(&tempty[acc], (use & 1) ^ 1, a.err)) { ok = false; break; }
-                    tc_fence_after();
-                    const uint32_t d = tmem + acc * ACCSTRIDE;
-                    for (int dy = 0; dy < 3; ++dy) {
-                        uint32_t pos = base + (y - y0) + dy;        // ring position of row y-1+dy
-                        int s = pos % stages;
-                        if (!mbar_wait(&full[s], (pos / stages) & 1, a.err)) { ok = false; break; }
-                        tc_fence_after();
-#pragma unroll
-                        for (int k = 0; k < KSTEPS; ++k) {
-                            uint64_t ad = sdesc(abase + s * ABYTES + k * 32, ROWB);
-                            uint64_t bd = sdesc(wbase + dy * NF * ROWB + k * 32, ROWB);
-                            if (OPER == TC_BF16) mma_f16(d, ad, bd, IDESC, (dy | k) != 0);
-                            else mma_f8(d, ad, bd, IDESC, (dy | k) != 0);
-                        }
-                        // row y-1 (kernel row 0) has no later use: its slot is
-                        // handed back as soon as these MMAs complete
-                        if (dy == 0) mma_commit(&empty[s]);
-                    }
-                    if (!ok) break;
-                    mma_commit(&tfull[acc]);
-                }
-                if (ok) {
-                    uint32_t rows = (uint32_t)(y1 - y0);
-                    mma_commit(&empty[(base + rows) % stages]);
-                    mma_commit(&empty[(base + rows + 1) % stages]);
-                    it = base + rows + 2;
-                }
-            }
-        }
-    } else {
-        // epilogue: kEpiWarps warps; warp w reads TMEM lanes 32 q .. 32 q + 31
-        // (q = w % 4, pixels x0-1+30q+lane) and output channels
-        // [kEpiCh h, kEpiCh (h + 1)), h = (w - 2) / 4.  Lane k < 30 produces
-        // output pixel x0 + 30q + k:
-        // out[c] = D[k][dx0][c] + D[k+1][dx1][c] + D[k+2][dx2][c], the two
-        // neighbours by warp shuffles within the quarter.
-        const int q = warp & 3, half = (warp - 2) >> 2;
-        const int j = q * kQuarter + lane;                     // output pixel in the tile
-        const bool active = half * kEpiCh < NOUT;
-        uint32_t lt = 0;
-        bool stop = false;
-        for (long long f = f0; !stop && f < f1;) {
-          int xb, n, y0, y1;
-          piece_rows(f, f1, XB, a.H, xb, n, y0, y1);
-          for (int y = y0; y < y1; ++y, ++lt) {
-            uint32_t acc = lt & 1, use = lt >> 1;
-            uint32_t slot = lt % kSlots, suse = lt / kSlots;
-            const int x = xb * kTileOut + j;
-            const bool valid = lane < kQuarter && x < a.W;
-            const size_t p = ((size_t)n * a.H + y) * a.W + (valid ? x : 0);
-            // the partial sum of this lane's 16 channels (one chunk per warp)
-            // is loaded before the accumulator wait, so its latency overlaps
-            // the MMAs instead of following the TMEM read
-            float4 pre[4];
-            const bool pre_ok = a.acc_in && valid && active && CHUNKS == 1 && (bf_out || a.cout == 64);
-            if (pre_ok) {
-                const float4* ap = (const float4*)(a.acc_in + p * 64 + half * kEpiCh);
-#pragma unroll
-                for (int i4 = 0; i4 < 4; ++i4) pre[i4] = ap[i4];
-            }
-            if (!mbar_wait_warp(&tfull[acc], use & 1, a.err)) { stop = true; break; }
-            tc_fence_after();
-            if (!mbar_wait_warp(&rfull[slot], suse & 1, a.err)) { stop = true; break; }
-            uint8_t* srow = sS + slot * SBYTES;
-            for (int cc = 0; cc < CHUNKS && active; ++cc) {
-                const int c0 = half * kEpiCh + cc * 16;
-                const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + acc * ACCSTRIDE + c0;
-                uint32_t r0[16], r1[16], r2[16];
-                tmem_ld16(taddr, r0);
-                tmem_ld16(taddr + NOUT, r1);
-                tmem_ld16(taddr + 2 * NOUT, r2);
-                tmem_wait_ld();
-                float v[16];
-#pragma unroll
-                for (int e = 0; e < 16; ++e) {
-                    float s1 = __shfl_down_sync(0xffffffffu, __uint_as_float(r1[e]), 1);
-                    float s2 = __shfl_down_sync(0xffffffffu, __uint_as_float(r2[e]), 2);
-                    v[e] = __uint_as_float(r0[e]) + s1 + s2;
-                }
-                if (OPER == TC_FP8) {
-#pragma unroll
-                    for (int e = 0; e < 16; ++e)
-                        v[e] = v[e] * (__ldg(a.wscale + (c0 + e < NOUT ? c0 + e : 0)) * a.xscale);
-                }
-                if (bf_out && lane < kQuarter) {
-                    float o[16];
-#pragma unroll
-                    for (int e = 0; e < 16; ++e) o[e] = v[e] + sBias[c0 + e];
-                    if (a.acc_in && valid) {
-                        const float4* ap = (const float4*)(a.acc_in + p * 64 + c0);
-#pragma unroll
-                        for (int i4 = 0; i4 < 4; ++i4) {
-                            float4 t = pre_ok ? pre[i4] : ap[i4];
-                            o[4 * i4] += t.x; o[4 * i4 + 1] += t.y;
-                            o[4 * i4 + 2] += t.z; o[4 * i4 + 3] += t.w;
-                        }
-                    }
-                    if (a.mode == TC_RELU_BF16) {
-#pragma unroll
-                        for (int e = 0; e < 16; ++e) o[e] = fmaxf(o[e], 0.0f);
-                    } else if (a.mode == TC_MASK_BF16) {
-#pragma unroll
-                        for (int jj = 0; jj < 2; ++jj) {
-                            uint4 u = *(const uint4*)(srow + sw128(j, c0 / 8 + jj));
-                            const __nv_bfloat162* h2 = (const __nv_bfloat162*)&u;
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-                                float2 f = __bfloat1622float2(h2[e]);
-                                if (!(f.x > 0.0f)) o[8 * jj + 2 * e] = 0.0f;
-                                if (!(f.y > 0.0f)) o[8 * jj + 2 * e + 1] = 0.0f;
-                            }
-                        }
-                    } else if (a.mode == TC_RESID_BF16 || a.mode == TC_RESRELU_BF16) {
-                        const bool rl = a.mode == TC_RESRELU_BF16;
-#pragma unroll
-                        for (int jj = 0; jj < 2; ++jj) {
-                            uint4 u = *(const uint4*)(srow + sw128(j, c0 / 8 + jj));
-                            const __nv_bfloat162* h2 = (const __nv_bfloat162*)&u;
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-                                float2 f = __bfloat1622float2(h2[e]);
-                                float o0 = o[8 * jj + 2 * e], o1 = o[8 * jj + 2 * e + 1];
-                                if (rl) { o0 = fmaxf(o0, 0.0f); o1 = fmaxf(o1, 0.0f); }
-                                o[8 * jj + 2 * e] = f.x + o0;
-                                o[8 * jj + 2 * e + 1] = f.y + o1;
-                            }
-                        }
-                    }
-#pragma unroll
-                    for (int jj = 0; jj < 2; ++jj) {
-                        uint4 u;
-                        __nv_bfloat162* h2 = (__nv_bfloat162*)&u;
-#pragma unroll
-                        for (int e = 0; e < 4; ++e)
-                            h2[e] = __floats2bfloat162_rn(o[8 * jj + 2 * e], o[8 * jj + 2 * e + 1]);
-                        *(uint4*)(srow + sw128(j, c0 / 8 + jj)) = u;
-                    }
-                    if (a.out_fp8 && valid) {
-                        uint4 u;
-                        uint8_t* b8 = (uint8_t*)&u;
-#pragma unroll
-                        for (int e = 0; e < 16; ++e)
-                            b8[e] = (uint8_t)__nv_cvt_float_to_fp8(o[e] * a.out_fp8_inv_scale,
-                                                                   __NV_SATFINITE, __NV_E4M3);
-                        *(uint4*)((uint8_t*)a.out_fp8 + p * 64 + c0) = u;
-                    }
-                } else if (valid) {
-                    if (a.mode == TC_FINAL_F32) {
-                        if (c0 == 0) {
-                            float up[3];
-                            bilinear(a.lrhs + (size_t)n * (a.H / a.scale) * (a.W / a.scale) * 3,
-                                     a.H / a.scale, a.W / a.scale, a.scale, x, y, up);
-                            float* op = (float*)a.out + p * 3;
-                            for (int c = 0; c < 3; ++c) op[c] = (v[c] + sBias[c]) + up[c];
-                        }
-                    } else if (a.cout == 64 && ((uintptr_t)a.out & 15) == 0) {
-                        // full 64-channel rows: 16-byte accesses, optional
-                        // partial-sum input (may alias the output: same
-                        // thread, same elements)
-                        float4* op = (float4*)((float*)a.out + p * 64 + c0);
-                        const float4* ap = a.acc_in ? (const float4*)(a.acc_in + p * 64 + c0) : nullptr;
-                        // all partial-sum loads before any store (they may
-                        // alias the output)
-                        float4 u4[4];
-#pragma unroll
-                        for (int i4 = 0; i4 < 4; ++i4)
-                            u4[i4] = pre_ok ? pre[i4] : (ap ? ap[i4] : make_float4(0.f, 0.f, 0.f, 0.f));
-#pragma unroll
-                        for (int i4 = 0; i4 < 4; ++i4) {
-                            float4 t = make_float4(v[4 * i4] + sBias[c0 + 4 * i4],
-                                                   v[4 * i4 + 1] + sBias[c0 + 4 * i4 + 1],
-                                                   v[4 * i4 + 2] + sBias[c0 + 4 * i4 + 2],
-                                                   v[4 * i4 + 3] + sBias[c0 + 4 * i4 + 3]);
-                            if (ap) {
-                                const float4 u = u4[i4];
-                                t.x += u.x; t.y += u.y; t.z += u.z; t.w += u.w;
-                            }
-                            if (a.relu) {
-                                t.x = fmaxf(t.x, 0.0f); t.y = fmaxf(t.y, 0.0f);
-                                t.z = fmaxf(t.z, 0.0f); t.w = fmaxf(t.w, 0.0f);
-                            }
-                            op[i4] = t;
-                        }
-                    } else {
-                        float* op = (float*)a.out + p * a.cout;
-#pragma unroll
-                        for (int e = 0; e < 16; ++e) {
-                            if (c0 + e < a.cout) {
-                                float o = v[e] + sBias[c0 + e];
-                                if (a.acc_in) o += a.acc_in[p * a.cout + c0 + e];
-                                op[c0 + e] = a.relu ? fmaxf(o, 0.0f) : o;
-                            }
-                        }
-                    }
-                }
-            }
-            if (stop) break;
-            // TMEM of this accumulator is free again; the staging slot goes to
-            // the store warp
-            tc_fence_before();
-            if (bf_out) fence_async_smem();
-            __syncwarp();
-            if (lane == 0) {
-                mbar_arrive(&tempty[acc]);
-                mbar_arrive(&edone[slot]);
-            }
-          }
-        }
-    }
-    __syncthreads();
-    if (warp == 1) {
-        tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "r"(kTmemCols));
-    }
-}
-
 // ---------------------------------------------------------------------------
-// BF16 3x3 convolution with the kernel ROWS folded into the MMA N dimension.
+// 3x3 convolution with the kernel ROWS folded into the MMA N dimension.
 //
 // Input row r of a column strip meets the weights of all three kernel rows in
 // one MMA: B = [w(dy 0, dx); w(dy 1, dx); w(dy 2, dx)] (3 NOUT rows) gives
@@ -647,29 +271,35 @@ __global__ void __launch_bounds__(kThreads, 1)
 // MMA accumulates onto zeroed TMEM).  Each input row is consumed by the 12
 // MMAs (3 dx x 4 K steps) issued right after it lands and then released, so
 // the whole ring is prefetch depth.  An output tile is 128 pixels of one row.
-//
-// Warp roles as in k_conv_tc: 0 A producer (TMA), 1 TMEM allocator + MMA
-// issuer, 2-17 epilogue (quarter q = warp % 4 of the TMEM lanes, 16 output
-// channels each), 18 residual prefetch, 19 output TMA stores.  Every wait is
-// bounded; on timeout the kernel sets *err and all roles unwind.
+// FP8 operands (kind::f8f6f4, K = 32 per MMA, 64-byte rows with the 64B
+// swizzle) follow the same schedule with one-row (64-byte) descriptor shifts,
+// per-output-channel weight scales and a per-layer activation scale; their
+// BF16 outputs also leave an FP8 copy for the next layer's operand.
+// Consecutive MMAs into different D regions do not pipeline, so the wrap
+// rows issue all MMAs of one region before the other.
 constexpr int kFoldTile = 128;               // output pixels per tile (= MMA M)
 constexpr int kFoldABox = kFoldTile + 2;     // input pixels per row box (one halo each side)
-constexpr int kFoldABytes = ((kFoldABox * 128 + 1023) / 1024) * 1024;  // ring slot (1024-aligned)
+// bytes per activation row of the operand type, ring slot (1024-aligned)
+constexpr int fold_rowb(int oper) { return oper == TC_BF16 ? 128 : 64; }
+constexpr int fold_aslot(int oper) { return ((kFoldABox * fold_rowb(oper) + 1023) / 1024) * 1024; }
 
-template <int NOUT> size_t fold_smem_bytes(int stages)
+template <int NOUT, int OPER> size_t fold_smem_bytes(int stages)
 {
-    return 1024 + 9 * NOUT * 128 + (size_t)stages * kFoldABytes + (size_t)kSlots * kFoldTile * 128 +
-           64 * 4 + 8 * (2 * stages + 1 + 2 * (512 / NOUT) + 3 * kSlots) + 16;
+    return 1024 + ((9 * NOUT * fold_rowb(OPER) + 1023) & ~1023) + (size_t)stages * fold_aslot(OPER) +
+           (size_t)kSlots * kFoldTile * 128 + 64 * 4 + 8 * (2 * stages + 1 + 2 * (512 / NOUT) + 3 * kSlots) + 16;
 }
 
-template <int NOUT>
+template <int NOUT, int OPER>
 __global__ void __launch_bounds__(kThreads, 1)
     k_conv_fold(const __grid_constant__ CUtensorMap tmap_x, const __grid_constant__ CUtensorMap tmap_w,
                 const __grid_constant__ CUtensorMap tmap_res,
                 const __grid_constant__ CUtensorMap tmap_out, TcConvArgs a, int stages)
 {
     constexpr int NS = 512 / NOUT;                            // TMEM accumulator slots
-    constexpr int WBYTES = 9 * NOUT * 128;
+    constexpr int ROWB = fold_rowb(OPER);                     // bytes per operand row
+    constexpr int ASLOT = fold_aslot(OPER);
+    constexpr int KSTEPS = OPER == TC_BF16 ? 4 : 2;           // MMAs per 64 input channels (K 16 / 32)
+    constexpr int WBYTES = 9 * NOUT * ROWB;
     constexpr int SBYTES = kFoldTile * 128;
     constexpr int BROWS = 3 * NOUT;                           // B rows per dx: dy 0, 1, 2
     constexpr uint32_t kTmemCols = 512;
@@ -678,7 +308,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* sW = smem;
     uint8_t* sA = smem + ((WBYTES + 1023) & ~1023);
-    uint8_t* sS = sA + stages * kFoldABytes;
+    uint8_t* sS = sA + stages * ASLOT;
     float* sBias = (float*)(sS + kSlots * SBYTES);
     uint64_t* bars = (uint64_t*)(sBias + 64);
     uint64_t* full = bars;
@@ -752,7 +382,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_expect_tx(wbar, WBYTES);
             // tap (dy, dx) at B row (3 dx + dy) NOUT: per dx the three kernel rows are contiguous
             for (int t = 0; t < 9; ++t)
-                tma_load_2d(sW + ((t % 3) * 3 + t / 3) * NOUT * 128, &tmap_w, 0, t * NOUT, wbar);
+                tma_load_2d(sW + ((t % 3) * 3 + t / 3) * NOUT * ROWB, &tmap_w, 0, t * NOUT, wbar);
             asm volatile("griddepcontrol.wait;" ::: "memory");
             uint32_t it = 0;
             bool ok = true;
@@ -762,8 +392,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int r = y0 - 1; r <= y1; ++r, ++it) {
                     int s = it % stages;
                     if (!mbar_wait(&empty[s], ((it / stages) & 1) ^ 1, a.err)) { ok = false; break; }
-                    mbar_expect_tx(&full[s], kFoldABox * 128);
-                    tma_load_4d(sA + s * kFoldABytes, &tmap_x, 0, xb * kFoldTile - 1, r, n, &full[s]);
+                    mbar_expect_tx(&full[s], kFoldABox * ROWB);
+                    tma_load_4d(sA + s * ASLOT, &tmap_x, 0, xb * kFoldTile - 1, r, n, &full[s]);
                 }
             }
         }
@@ -841,16 +471,20 @@ __global__ void __launch_bounds__(kThreads, 1)
                     for (int part = 0; part < (n1 < nb ? 2 : 1); ++part) {
                         const uint32_t dcol = part ? 0u : (uint32_t)(c0 * NOUT);
                         const int b0 = part ? n1 : 0, nbp = part ? nb - n1 : n1;
-                        const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) |
+                        const uint32_t idesc = (1u << 4) | ((OPER == TC_BF16 ? 1u : 0u) << 7) |
+                                               ((OPER == TC_BF16 ? 1u : 0u) << 10) |
                                                ((uint32_t)((nbp * NOUT) >> 3) << 17) |
                                                ((uint32_t)(kFoldTile >> 4) << 24);
 #pragma unroll
                         for (int dx = 0; dx < 3; ++dx) {
                             const uint32_t brow = (uint32_t)(dx * BROWS + (jlo + b0) * NOUT);
 #pragma unroll
-                            for (int k = 0; k < 4; ++k)
-                                mma_f16(tmem + dcol, sdesc(abase + s * kFoldABytes + dx * 128 + k * 32, 128),
-                                        sdesc(wbase + brow * 128 + k * 32, 128), idesc, 1u);
+                            for (int k = 0; k < KSTEPS; ++k) {
+                                const uint64_t ad = sdesc(abase + s * ASLOT + dx * ROWB + k * 32, ROWB);
+                                const uint64_t bd = sdesc(wbase + brow * ROWB + k * 32, ROWB);
+                                if (OPER == TC_BF16) mma_f16(tmem + dcol, ad, bd, idesc, 1u);
+                                else mma_f8(tmem + dcol, ad, bd, idesc, 1u);
+                            }
                         }
                     }
                     mma_commit(&empty[s]);
@@ -906,6 +540,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                 float v[16];
 #pragma unroll
                 for (int e = 0; e < 16; ++e) v[e] = __uint_as_float(r0[e]);
+                if (OPER == TC_FP8) {
+#pragma unroll
+                    for (int e = 0; e < 16; ++e)
+                        v[e] = v[e] * (__ldg(a.wscale + (c0 + e < NOUT ? c0 + e : 0)) * a.xscale);
+                }
                 if (bf_out) {
                     float o[16];
 #pragma unroll
@@ -960,6 +599,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                         for (int e = 0; e < 4; ++e)
                             h2[e] = __floats2bfloat162_rn(o[8 * jj + 2 * e], o[8 * jj + 2 * e + 1]);
                         *(uint4*)(srow + sw128(j, c0 / 8 + jj)) = u;
+                    }
+                    if (a.out_fp8 && valid) {
+                        // the next layer's FP8 operand row
+                        uint4 u;
+                        uint8_t* b8 = (uint8_t*)&u;
+#pragma unroll
+                        for (int e = 0; e < 16; ++e)
+                            b8[e] = (uint8_t)__nv_cvt_float_to_fp8(o[e] * a.out_fp8_inv_scale,
+                                                                   __NV_SATFINITE, __NV_E4M3);
+                        *(uint4*)((uint8_t*)a.out_fp8 + p * 64 + c0) = u;
                     }
                 } else if (valid) {
                     if (a.mode == TC_FINAL_F32) {
@@ -1037,48 +686,15 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
     return fn;
 }
 
-template <int NOUT, int OPER> size_t smem_bytes(int stages)
-{
-    constexpr int ROWB = OPER == TC_BF16 ? 128 : 64;
-    return 1024 + ((9 * NOUT * ROWB + 1023) & ~1023) + (size_t)stages * kTileM * ROWB +
-           (size_t)kSlots * kTileM * 128 + 64 * 4 + 8 * (2 * stages + 5 + 3 * kSlots) + 16;
-}
-
 template <int NOUT, int OPER>
-mrs_status launch(const TcConvArgs& a, cudaStream_t st)
-{
-    // input-row ring: as many rows as fit next to the weights and staging
-    int stages = 4;
-    while (smem_bytes<NOUT, OPER>(stages + 1) <= 227 * 1024 && stages < 12) ++stages;
-    size_t smem = smem_bytes<NOUT, OPER>(stages);
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_conv_tc<NOUT, OPER>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return cuda_status(e, "conv smem attribute");
-        attr = true;
-    }
-    // one CTA per SM, each with an equal contiguous share of the tiles
-    TcConvArgs b = a;
-    const long long T = (long long)a.N * ((a.W + kTileOut - 1) / kTileOut) * a.H;
-    int grid = T < sm_count() ? (int)T : sm_count();
-    if (grid < 1) return MRS_OK;
-    const CUtensorMap* res = a.tmap_res ? a.tmap_res : a.tmap_x;
-    const CUtensorMap* out = a.tmap_out ? a.tmap_out : a.tmap_x;
-    MRS_TIMED(PK_CONV_TC, st, (k_conv_tc<NOUT, OPER><<<grid, kThreads, smem, st>>>(*a.tmap_x, *a.tmap_w, *res, *out, b, stages)));
-    MRS_LAUNCHED(1);
-    return cuda_status(cudaGetLastError(), "conv launch");
-}
-
-template <int NOUT>
 mrs_status launch_fold(const TcConvArgs& a, cudaStream_t st)
 {
     int stages = 4;
-    while (fold_smem_bytes<NOUT>(stages + 1) <= 227 * 1024 && stages < 12) ++stages;
-    size_t smem = fold_smem_bytes<NOUT>(stages);
+    while (fold_smem_bytes<NOUT, OPER>(stages + 1) <= 227 * 1024 && stages < 12) ++stages;
+    size_t smem = fold_smem_bytes<NOUT, OPER>(stages);
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_conv_fold<NOUT>,
+        cudaError_t e = cudaFuncSetAttribute(k_conv_fold<NOUT, OPER>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return cuda_status(e, "conv smem attribute");
         attr = true;
@@ -1101,7 +717,7 @@ mrs_status launch_fold(const TcConvArgs& a, cudaStream_t st)
     cfg.attrs = la;
     cfg.numAttrs = 1;
     cudaError_t le = cudaSuccess;
-    MRS_TIMED(PK_CONV_TC, st, (le = cudaLaunchKernelEx(&cfg, k_conv_fold<NOUT>, *a.tmap_x, *a.tmap_w, *res, *out, b, stages)));
+    MRS_TIMED(PK_CONV_TC, st, (le = cudaLaunchKernelEx(&cfg, k_conv_fold<NOUT, OPER>, *a.tmap_x, *a.tmap_w, *res, *out, b, stages)));
     MRS_LAUNCHED(1);
     if (le != cudaSuccess) return cuda_status(le, "conv launch");
     return cuda_status(cudaGetLastError(), "conv launch");
@@ -1205,8 +821,8 @@ mrs_status tc_conv3x3(const TcConvArgs& a, cudaStream_t st)
         set_error("tc_conv3x3: acc_in must be 16-byte aligned, with bf16 operands");
         return MRS_ERR_ARG;
     }
-    if (a.nout == 64) return a.operand == TC_BF16 ? launch_fold<64>(a, st) : launch<64, TC_FP8>(a, st);
-    if (a.nout == 16) return a.operand == TC_BF16 ? launch_fold<16>(a, st) : launch<16, TC_FP8>(a, st);
+    if (a.nout == 64) return a.operand == TC_BF16 ? launch_fold<64, TC_BF16>(a, st) : launch_fold<64, TC_FP8>(a, st);
+    if (a.nout == 16) return a.operand == TC_BF16 ? launch_fold<16, TC_BF16>(a, st) : launch_fold<16, TC_FP8>(a, st);
     set_error("tc_conv3x3: nout must be 64 or 16");
     return MRS_ERR_ARG;
 }

@@ -52,16 +52,14 @@ struct TcConvArgs {
     const float* acc_in;
 };
 
-// Box widths (pixels): A operands are loaded as four 32-pixel boxes per input
-// row (each covering one TMEM lane quarter: 30 output pixels plus one halo
-// pixel on each side); residual and output maps move a tile's 120 pixels.
-constexpr int kABox = 32;
-constexpr int kOutBox = 120;
-// BF16 operands run the row-folded kernel: one 130-pixel A box per input
-// row (128 outputs plus a halo pixel on each side) and 128-pixel residual /
-// output boxes.  Maps passed to tc_conv3x3 use these box widths.
-inline int tc_a_box(int operand) { return operand == TC_BF16 ? 130 : kABox; }
-inline int tc_out_box(int operand) { return operand == TC_BF16 ? 128 : kOutBox; }
+// Box widths (pixels): the conv reads one 130-pixel A box per input row (a
+// tile's 128 outputs plus a halo pixel on each side) and moves 128-pixel
+// residual / output boxes.  Maps passed to tc_conv3x3 use these widths (the
+// same for both operand types).
+constexpr int kABox = 130;
+constexpr int kOutBox = 128;
+inline int tc_a_box(int /*operand*/) { return kABox; }
+inline int tc_out_box(int /*operand*/) { return kOutBox; }
 // Encode a tiled tensor map for a [N][H][W][64] activation tensor (rows of 128
 // bytes in bf16, 64 in fp8): box = box_px pixels of one image row.
 mrs_status tc_make_act_map(CUtensorMap* m, const void* ptr, int N, int H, int W, int operand,

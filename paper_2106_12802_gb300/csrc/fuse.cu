@@ -1343,7 +1343,7 @@ mrs_status train_step_bf16(mrs_net_s* net, const float* lrhs, const float* hrls,
     MRS_CHECK(cudaMemsetAsync(zero, 0, 64 * 4, st));
     const auto& L = shapes(net->cin0);
 
-    // tensor maps: A operands (32-pixel boxes) and residual / output (120-pixel)
+    // tensor maps: A operands (130-pixel boxes) and residual / output (128-pixel)
     auto amap = [&](CUtensorMap* m, const void* ptr) { return tc_make_act_map(m, ptr, N, H, W, TC_BF16, tc_a_box(TC_BF16)); };
     auto omap = [&](CUtensorMap* m, const void* ptr) { return tc_make_act_map(m, ptr, N, H, W, TC_BF16, tc_out_box(TC_BF16)); };
     std::vector<CUtensorMap> hA(9), hO(9), rA(8), rO(8);
