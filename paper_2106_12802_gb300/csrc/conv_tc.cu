@@ -279,6 +279,7 @@ __device__ __forceinline__ uint32_t sw128(int m, int j) { return m * 128 + ((j ^
 // rows issue all MMAs of one region before the other.
 constexpr int kFoldTile = 128;               // output pixels per tile (= MMA M)
 constexpr int kFoldABox = kFoldTile + 2;     // input pixels per row box (one halo each side)
+constexpr int kFoldMaxRows = 6;              // output rows per sub-piece of a multi-chunk conv
 // bytes per activation row of the operand type, ring slot (1024-aligned)
 constexpr int fold_rowb(int oper) { return oper == TC_BF16 ? 128 : 64; }
 constexpr int fold_aslot(int oper) { return ((kFoldABox * fold_rowb(oper) + 1023) / 1024) * 1024; }
@@ -286,7 +287,7 @@ constexpr int fold_aslot(int oper) { return ((kFoldABox * fold_rowb(oper) + 1023
 template <int NOUT, int OPER> size_t fold_smem_bytes(int stages)
 {
     return 1024 + ((9 * NOUT * fold_rowb(OPER) + 1023) & ~1023) + (size_t)stages * fold_aslot(OPER) +
-           (size_t)kSlots * kFoldTile * 128 + 64 * 4 + 8 * (2 * stages + 1 + 2 * (512 / NOUT) + 3 * kSlots) + 16;
+           (size_t)kSlots * kFoldTile * 128 + 64 * 4 + 8 * (2 * stages + 2 + 2 * (512 / NOUT) + 3 * kSlots) + 16;
 }
 
 template <int NOUT, int OPER>
@@ -313,8 +314,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t* bars = (uint64_t*)(sBias + 64);
     uint64_t* full = bars;
     uint64_t* empty = bars + stages;
-    uint64_t* wbar = bars + 2 * stages;
-    uint64_t* tfull = wbar + 1;                               // [NS] output row complete
+    uint64_t* wbar = bars + 2 * stages;                       // weights landed
+    uint64_t* wempty = wbar + 1;                              // weight buffer free
+    uint64_t* tfull = wempty + 1;                             // [NS] output row complete
     uint64_t* sfree = tfull + NS;                             // [NS] slot read and zeroed
     uint64_t* rfull = sfree + NS;
     uint64_t* rempty = rfull + kSlots;
@@ -334,6 +336,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (threadIdx.x == 0) {
         for (int i = 0; i < stages; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
         mbar_init(wbar, 1);
+        mbar_init(wempty, 1);
         for (int i = 0; i < NS; ++i) {
             mbar_init(&tfull[i], 1);
             mbar_init(&sfree[i], kEpiWarps);
@@ -376,25 +379,64 @@ __global__ void __launch_bounds__(kThreads, 1)
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (!(warp == 0 && lane == 0)) asm volatile("griddepcontrol.wait;" ::: "memory");
 
+    // A convolution over kc > 1 inputs (64-channel chunks, each its own tensor
+    // map in a.amaps, weights chunk after chunk in tmap_w) accumulates all
+    // chunks in TMEM: a piece is cut into sub-pieces of at most kMaxRows
+    // output rows, whose accumulators all stay live while the chunks pass
+    // (chunk-major order; the weight buffer is reloaded per chunk).
+    const int kc = a.kc > 1 ? a.kc : 1;
+    const int maxr = kc > 1 ? kFoldMaxRows : (1 << 30);
     if (warp == 0) {
-        // A producer: input rows y0-1 .. y1 of each piece, 130 pixels from x0-1
         if (lane == 0) {
+            // A producer: per (sub-piece, chunk), input rows ys-1 .. ye, 130
+            // pixels from x0-1; the first weights are loaded here, before the
+            // wait for the previous kernel
             mbar_expect_tx(wbar, WBYTES);
             // tap (dy, dx) at B row (3 dx + dy) NOUT: per dx the three kernel rows are contiguous
             for (int t = 0; t < 9; ++t)
-                tma_load_2d(sW + ((t % 3) * 3 + t / 3) * NOUT * ROWB, &tmap_w, 0, t * NOUT, wbar);
+                tma_load_2d(sW + ((t % 3) * 3 + t / 3) * NOUT * ROWB, &tmap_w, 0, a.w_row0 + t * NOUT, wbar);
             asm volatile("griddepcontrol.wait;" ::: "memory");
             uint32_t it = 0;
             bool ok = true;
             for (long long f = f0; ok && f < f1;) {
                 int xb, n, y0, y1;
                 piece_rows(f, f1, XB, a.H, xb, n, y0, y1);
-                for (int r = y0 - 1; r <= y1; ++r, ++it) {
-                    int s = it % stages;
-                    if (!mbar_wait(&empty[s], ((it / stages) & 1) ^ 1, a.err)) { ok = false; break; }
-                    mbar_expect_tx(&full[s], kFoldABox * ROWB);
-                    tma_load_4d(sA + s * ASLOT, &tmap_x, 0, xb * kFoldTile - 1, r, n, &full[s]);
+                for (int ys = y0; ok && ys < y1; ys += maxr) {
+                    const int ye = min(y1, ys + maxr);
+                    for (int j = 0; ok && j < kc; ++j) {
+                        const CUtensorMap* am = kc > 1 ? a.amaps + j : &tmap_x;
+                        // a map in global memory, written by the host before
+                        // the launch: acquire it for the tensor-map proxy
+                        if (kc > 1)
+                            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                                             (uint64_t)am)
+                                         : "memory");
+                        for (int r = ys - 1; r <= ye; ++r, ++it) {
+                            int s = it % stages;
+                            if (!mbar_wait(&empty[s], ((it / stages) & 1) ^ 1, a.err)) { ok = false; break; }
+                            mbar_expect_tx(&full[s], kFoldABox * ROWB);
+                            tma_load_4d(sA + s * ASLOT, am, 0, xb * kFoldTile - 1, r, n, &full[s]);
+                        }
+                    }
                 }
+            }
+        } else if (lane == 16 && kc > 1) {
+            // weight loader for every (sub-piece, chunk) pass after the first:
+            // waits for the MMAs of the previous pass to finish with the buffer
+            uint32_t k = 0;
+            bool ok = true;
+            for (long long f = f0; ok && f < f1;) {
+                int xb, n, y0, y1;
+                piece_rows(f, f1, XB, a.H, xb, n, y0, y1);
+                for (int ys = y0; ok && ys < y1; ys += maxr)
+                    for (int j = 0; ok && j < kc; ++j, ++k) {
+                        if (k == 0) continue;
+                        if (!mbar_wait(wempty, (k - 1) & 1, a.err)) { ok = false; break; }
+                        mbar_expect_tx(wbar, WBYTES);
+                        for (int t = 0; t < 9; ++t)
+                            tma_load_2d(sW + ((t % 3) * 3 + t / 3) * NOUT * ROWB, &tmap_w, 0,
+                                        a.w_row0 + (j * 9 + t) * NOUT, wbar);
+                    }
             }
         }
     } else if (warp == kResWarp) {
@@ -441,60 +483,69 @@ __global__ void __launch_bounds__(kThreads, 1)
         // row r + 1 - j lies in the piece, in one MMA per (dx, K step) (two
         // where the slots wrap)
         if (lane == 0) {
-            bool ok = mbar_wait(wbar, 0, a.err);
-            uint32_t it = 0;
-            long long t0 = 0;                                   // CTA output-row counter at piece start
+            bool ok = true;
+            uint32_t it = 0, k = 0;
+            long long t0 = 0;                                   // CTA output-row counter at sub-piece start
             const uint32_t wbase = smem_u32(sW), abase = smem_u32(sA);
             for (long long f = f0; ok && f < f1;) {
                 int xb, n, y0, y1;
                 piece_rows(f, f1, XB, a.H, xb, n, y0, y1);
-                for (int r = y0 - 1; ok && r <= y1; ++r, ++it) {
-                    const int jlo = max(0, r + 2 - y1), jhi = min(2, r + 1 - y0);
-                    const int s = it % stages;
-                    // output row of block j: CTA counter tj = t0 + (r + 1 - j - y0)
-                    const long long tlo = t0 + (r + 1 - jlo - y0);   // newest row (highest t)
-                    if (jlo == 0) {
-                        // block 0 starts output row tlo: its slot must have been read and
-                        // zeroed by the epilogue of row tlo - NS
-                        const int sl = (int)(tlo % NS);
-                        const uint32_t use = (uint32_t)(tlo / NS);
-                        if (!mbar_wait(&sfree[(NS - sl) % NS], (use & 1) ^ 1, a.err)) { ok = false; break; }
-                    }
-                    if (!mbar_wait(&full[s], (it / stages) & 1, a.err)) { ok = false; break; }
-                    tc_fence_after();
-                    const int nb = jhi - jlo + 1;
-                    const int c0 = (int)((NS - (int)(tlo % NS)) % NS);   // slot of block jlo
-                    const int n1 = min(nb, NS - c0);                    // blocks before the wrap
-                    // all MMAs of one D region back to back: the region before
-                    // the wrap, then (rarely) the one after it; consecutive
-                    // MMAs into different regions do not pipeline
-                    for (int part = 0; part < (n1 < nb ? 2 : 1); ++part) {
-                        const uint32_t dcol = part ? 0u : (uint32_t)(c0 * NOUT);
-                        const int b0 = part ? n1 : 0, nbp = part ? nb - n1 : n1;
-                        const uint32_t idesc = (1u << 4) | ((OPER == TC_BF16 ? 1u : 0u) << 7) |
-                                               ((OPER == TC_BF16 ? 1u : 0u) << 10) |
-                                               ((uint32_t)((nbp * NOUT) >> 3) << 17) |
-                                               ((uint32_t)(kFoldTile >> 4) << 24);
+                for (int ys = y0; ok && ys < y1; ys += maxr) {
+                  const int ye = min(y1, ys + maxr);
+                  for (int j = 0; ok && j < kc; ++j, ++k) {
+                    // weights of this pass (loaded once when kc == 1)
+                    if ((kc > 1 || k == 0) && !mbar_wait(wbar, k & 1, a.err)) { ok = false; break; }
+                    for (int r = ys - 1; ok && r <= ye; ++r, ++it) {
+                        const int jlo = max(0, r + 2 - ye), jhi = min(2, r + 1 - ys);
+                        const int s = it % stages;
+                        // output row of block jb: CTA counter t0 + (r + 1 - jb - ys)
+                        const long long tlo = t0 + (r + 1 - jlo - ys);   // newest row (highest t)
+                        if (jlo == 0 && j == 0) {
+                            // block 0 of the first chunk starts output row tlo: its slot must
+                            // have been read and zeroed by the epilogue of row tlo - NS
+                            const int sl = (int)(tlo % NS);
+                            const uint32_t use = (uint32_t)(tlo / NS);
+                            if (!mbar_wait(&sfree[(NS - sl) % NS], (use & 1) ^ 1, a.err)) { ok = false; break; }
+                        }
+                        if (!mbar_wait(&full[s], (it / stages) & 1, a.err)) { ok = false; break; }
+                        tc_fence_after();
+                        const int nb = jhi - jlo + 1;
+                        const int c0 = (int)((NS - (int)(tlo % NS)) % NS);   // slot of block jlo
+                        const int n1 = min(nb, NS - c0);                    // blocks before the wrap
+                        // all MMAs of one D region back to back: the region before
+                        // the wrap, then (rarely) the one after it; consecutive
+                        // MMAs into different regions do not pipeline
+                        for (int part = 0; part < (n1 < nb ? 2 : 1); ++part) {
+                            const uint32_t dcol = part ? 0u : (uint32_t)(c0 * NOUT);
+                            const int b0 = part ? n1 : 0, nbp = part ? nb - n1 : n1;
+                            const uint32_t idesc = (1u << 4) | ((OPER == TC_BF16 ? 1u : 0u) << 7) |
+                                                   ((OPER == TC_BF16 ? 1u : 0u) << 10) |
+                                                   ((uint32_t)((nbp * NOUT) >> 3) << 17) |
+                                                   ((uint32_t)(kFoldTile >> 4) << 24);
 #pragma unroll
-                        for (int dx = 0; dx < 3; ++dx) {
-                            const uint32_t brow = (uint32_t)(dx * BROWS + (jlo + b0) * NOUT);
+                            for (int dx = 0; dx < 3; ++dx) {
+                                const uint32_t brow = (uint32_t)(dx * BROWS + (jlo + b0) * NOUT);
 #pragma unroll
-                            for (int k = 0; k < KSTEPS; ++k) {
-                                const uint64_t ad = sdesc(abase + s * ASLOT + dx * ROWB + k * 32, ROWB);
-                                const uint64_t bd = sdesc(wbase + brow * ROWB + k * 32, ROWB);
-                                if (OPER == TC_BF16) mma_f16(tmem + dcol, ad, bd, idesc, 1u);
-                                else mma_f8(tmem + dcol, ad, bd, idesc, 1u);
+                                for (int kk = 0; kk < KSTEPS; ++kk) {
+                                    const uint64_t ad = sdesc(abase + s * ASLOT + dx * ROWB + kk * 32, ROWB);
+                                    const uint64_t bd = sdesc(wbase + brow * ROWB + kk * 32, ROWB);
+                                    if (OPER == TC_BF16) mma_f16(tmem + dcol, ad, bd, idesc, 1u);
+                                    else mma_f8(tmem + dcol, ad, bd, idesc, 1u);
+                                }
                             }
                         }
+                        mma_commit(&empty[s]);
+                        if (jhi == 2 && j == kc - 1) {
+                            // output row r - 1 (block 2 of the last chunk) is complete
+                            const long long td = tlo - (2 - jlo);
+                            mma_commit(&tfull[(NS - (int)(td % NS)) % NS]);
+                        }
                     }
-                    mma_commit(&empty[s]);
-                    if (jhi == 2) {
-                        // output row r - 1 (block 2) is complete
-                        const long long td = tlo - (2 - jlo);
-                        mma_commit(&tfull[(NS - (int)(td % NS)) % NS]);
-                    }
+                    // the weight buffer is free once this pass's MMAs complete
+                    if (kc > 1) mma_commit(wempty);
+                  }
+                  t0 += ye - ys;
                 }
-                t0 += y1 - y0;
             }
         }
     } else {

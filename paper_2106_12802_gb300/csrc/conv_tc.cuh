@@ -50,6 +50,14 @@ struct TcConvArgs {
     // chunk, each adding its chunk's contribution (TC_PLAIN_F32 with acc_in =
     // out) and the last applying the layer's epilogue.  BF16 operands only.
     const float* acc_in;
+    // A convolution over kc > 1 input tensors of 64 channels each (the
+    // concatenation of their channels) in ONE launch: amaps = DEVICE array of
+    // kc A-operand maps (64-byte aligned, alive until the kernel completes),
+    // weights of chunk j at rows w_row0 + (9 j + t) nout of tmap_w.  kc <= 1:
+    // tmap_x, weights at rows w_row0 + t nout.
+    const CUtensorMap* amaps;
+    int kc;
+    int w_row0;
 };
 
 // Box widths (pixels): the conv reads one 130-pixel A box per input row (a

@@ -12,14 +12,15 @@
 // buffers ([P][256] per block: F_in, F_1, F_2, F_3 side by side), the fuse conv
 // over an explicitly deshuffled [P][64 + 64 s^2] buffer.
 //
-// BF16 path (tensor cores, conv_tc.cu): every conv is a chain of 64-input-
-// channel chunk launches accumulating in an FP32 partial sum; the last launch
-// applies the layer's epilogue.  Nothing is concatenated or rearranged in
-// memory: a dense block's inputs stay separate [P][64] tensors, a deshuffle
-// chunk is a strided tensor-map view of the HR feature map (sub-pixel
-// (oy, ox) of every s x s block), the 1x1 fuse conv is the centre tap of a 3x3
-// chunk, and a shuffle is four launches whose outputs are strided views of
-// the 2x larger feature map.
+// BF16 path (tensor cores, conv_tc.cu): a conv over 64 c input channels is
+// ONE launch that accumulates its c 64-channel chunks in TMEM (chunk-major
+// over sub-pieces of at most six output rows; the chunk maps are passed in
+// device memory).  Nothing is concatenated or rearranged in memory: a dense
+// block's inputs stay separate [P][64] tensors, a deshuffle chunk is a
+// strided tensor-map view of the HR feature map (sub-pixel (oy, ox) of every
+// s x s block), the 1x1 fuse conv is the centre tap of 3x3 chunks, and a
+// shuffle is four launches whose outputs are strided views of the 2x larger
+// feature map.
 #include <cuda_bf16.h>
 #include <math.h>
 #include <string.h>
@@ -257,6 +258,9 @@ struct mrs_rdn_s {
     float* bch = nullptr;          // chunk biases [nchunks][64]
     std::vector<WChunk> ch;
     std::vector<int> first;        // first chunk of each layer
+    CUtensorMap wmap_all;          // every chunk's weights as one [rows][64] tensor
+    std::vector<CUtensorMap> hmaps;  // A-operand maps of the multi-chunk convs of a call
+    Buf dmaps;                     // their device copy
     Buf f32, bf;                   // activation workspaces
     int* err = nullptr;
 };
@@ -328,7 +332,8 @@ mrs_status pack_chunks(mrs_rdn_s* r, const float* P)
         mrs_status st = tc_make_w_map(&c.map, r->wbf + c.off, 9 * c.nout, c.nout, TC_BF16);
         if (st != MRS_OK) return st;
     }
-    return MRS_OK;
+    // chunk c of a 64-output layer starts at row c.off / 64 of this map
+    return tc_make_w_map(&r->wmap_all, r->wbf, (int)(wb.size() / 64), 64, TC_BF16);
 }
 
 mrs_status rdn_f32(mrs_rdn_s* r, const float* lrhs, const float* hrls, const float* alb,
@@ -430,7 +435,7 @@ mrs_status rdn_bf16(mrs_rdn_s* r, const float* lrhs, const float* hrls, const fl
     for (int d = 1; d <= D; ++d) nU += Pl << (2 * d);
     const int kX = 6;
     const size_t elems = (Pl + Ph + Pl + Ph + Pl + kX * Pl + nU) * 64;
-    const size_t need = elems * 2 + Pl * 64 * 4 + 4096;
+    const size_t need = elems * 2 + 4096;
     mrs_status rc = r->bf.ensure(need);
     if (rc != MRS_OK) return rc;
     __nv_bfloat16* inL = r->bf.as<__nv_bfloat16>();
@@ -445,7 +450,6 @@ mrs_status rdn_bf16(mrs_rdn_s* r, const float* lrhs, const float* hrls, const fl
     Ud[0] = nullptr;
     __nv_bfloat16* u = X[kX - 1] + Pl * 64;
     for (int d = 1; d <= D; ++d) { Ud[d] = u; u += (Pl << (2 * d)) * 64; }
-    float* part = (float*)(((uintptr_t)u + 255) & ~(uintptr_t)255);
 
     k_lr_input_bf16<<<grid_for(Pl), 256, 0, st>>>(lrhs, Pl, inL);
     MRS_LAUNCHED(1);
@@ -485,40 +489,56 @@ mrs_status rdn_bf16(mrs_rdn_s* r, const float* lrhs, const float* hrls, const fl
     TcConvArgs a;
     memset(&a, 0, sizeof(a));
     a.N = N; a.scale = 1; a.operand = TC_BF16; a.err = r->err; a.nout = 64; a.cout = 64;
-    // one conv over the chunk inputs A[0..n) of layer li: chunks 0..n-2 accumulate
-    // in `part`, the last applies `mode` (bf16 out via `o`, residual via `res`)
+    // The launch sequence runs twice: a dry pass collects the A-operand maps
+    // of the multi-chunk convs (a conv over 64 c input channels is ONE launch
+    // accumulating its c chunks in TMEM; the kernel reads the chunk maps from
+    // device memory), they are copied to the device, then the real pass
+    // launches.
+    bool dry = true;
+    size_t mc = 0;                 // next multi-chunk conv's first map
     auto layer = [&](int li, const CUtensorMap* const* A, int n, int hh, int ww, int mode,
-                     const CUtensorMap* o, const CUtensorMap* res) {
-        a.H = hh; a.W = ww;
-        for (int j = 0; j < n; ++j) {
-            const WChunk& c = r->ch[r->first[li] + j];
-            a.tmap_x = A[j];
-            a.tmap_w = &c.map;
-            a.bias = r->bch + (size_t)(r->first[li] + j) * 64;
-            a.nout = c.nout;
-            a.acc_in = j ? part : nullptr;
-            a.tmap_res = nullptr;
-            a.tmap_out = nullptr;
-            a.relu = 0;
-            if (j + 1 < n) {
-                a.mode = TC_PLAIN_F32; a.out = part; a.cout = 64;
-            } else {
-                a.mode = mode; a.tmap_out = o; a.tmap_res = res;
+                     const CUtensorMap* o, const CUtensorMap* res) -> mrs_status {
+        if (n > 1) {
+            if (dry) {
+                for (int j = 0; j < n; ++j) r->hmaps.push_back(*A[j]);
+                return MRS_OK;
             }
+            const WChunk& c0 = r->ch[r->first[li]];
+            a.H = hh; a.W = ww;
+            a.tmap_x = A[0];
+            a.amaps = r->dmaps.as<CUtensorMap>() + mc;
+            a.kc = n;
+            a.w_row0 = (int)(c0.off / 64);
+            a.tmap_w = &r->wmap_all;
+            a.bias = r->bch + (size_t)r->first[li] * 64;
+            a.nout = 64; a.acc_in = nullptr; a.relu = 0;
+            a.mode = mode; a.tmap_out = o; a.tmap_res = res;
+            mc += n;
             mrs_status e = tc_conv3x3(a, st);
-            if (e != MRS_OK) return e;
+            a.amaps = nullptr; a.kc = 0; a.w_row0 = 0;
+            return e;
         }
-        return MRS_OK;
+        if (dry) return MRS_OK;
+        const WChunk& c = r->ch[r->first[li]];
+        a.H = hh; a.W = ww;
+        a.tmap_x = A[0];
+        a.tmap_w = &c.map;
+        a.bias = r->bch + (size_t)r->first[li] * 64;
+        a.nout = c.nout;
+        a.acc_in = nullptr; a.relu = 0;
+        a.mode = mode; a.tmap_out = o; a.tmap_res = res;
+        return tc_conv3x3(a, st);
     };
 
+    auto run = [&]() -> mrs_status {
+    mrs_status rc = MRS_OK;
     // encoders
     const CUtensorMap* one[1];
     one[0] = &inLA;
     if ((rc = layer(0, one, 1, h, w, TC_RELU_BF16, &FlrO, nullptr)) != MRS_OK) return rc;
     one[0] = &inHA;
-    a.N = N;
     if ((rc = layer(1, one, 1, H, W, TC_RELU_BF16, &Fh0O, nullptr)) != MRS_OK) return rc;
-    // fuse: F_LRHS chunk + s^2 deshuffle views
+    // fuse: F_LRHS chunk + s^2 deshuffle views, one launch
     std::vector<const CUtensorMap*> fin(1 + s * s);
     fin[0] = &FlrA;
     for (int q = 0; q < s * s; ++q) fin[1 + q] = &dsf[q];
@@ -544,14 +564,16 @@ mrs_status rdn_bf16(mrs_rdn_s* r, const float* lrhs, const float* hrls, const fl
             cur = outi;
         }
         // group skip: F_g = blocks + F_{g-1}
-        k_add_bf16<<<grid_for(Pl * 8), 256, 0, st>>>(X[cur], pg < 0 ? F0 : X[pg], Pl * 8);
-        MRS_LAUNCHED(1);
+        if (!dry) {
+            k_add_bf16<<<grid_for(Pl * 8), 256, 0, st>>>(X[cur], pg < 0 ? F0 : X[pg], Pl * 8);
+            MRS_LAUNCHED(1);
+        }
     }
+    if (dry) return MRS_OK;
     // Eq. F_DF: + F_0
     k_add_bf16<<<grid_for(Pl * 8), 256, 0, st>>>(X[cur], F0, Pl * 8);
     MRS_LAUNCHED(1);
     if ((rc = cuda_status(cudaGetLastError(), "rdn add")) != MRS_OK) return rc;
-
     // UP: stage d reads U_d (U_0 = F_DF) and writes the four sub-pixel views of U_{d+1}
     CUtensorMap UA;
     const CUtensorMap* src = &XA[cur];
@@ -583,7 +605,17 @@ mrs_status rdn_bf16(mrs_rdn_s* r, const float* lrhs, const float* hrls, const fl
     a.nout = c.nout; a.acc_in = nullptr; a.tmap_out = nullptr; a.tmap_res = nullptr;
     a.mode = TC_PLAIN_F32; a.out = out; a.cout = 3; a.relu = 0;
     return tc_conv3x3(a, st);
+    };
+
+    r->hmaps.clear();
+    if ((rc = run()) != MRS_OK) return rc;
+    if ((rc = r->dmaps.ensure(r->hmaps.size() * sizeof(CUtensorMap) + 64)) != MRS_OK) return rc;
+    MRS_CHECK(cudaMemcpyAsync(r->dmaps.p, r->hmaps.data(), r->hmaps.size() * sizeof(CUtensorMap),
+                              cudaMemcpyHostToDevice, st));
+    dry = false;
+    return run();
 }
+
 
 }  // namespace
 }  // namespace mrs
@@ -606,6 +638,7 @@ extern "C" mrs_status mrs_rdn_free(mrs_rdn r)
         if (p) cudaFree(p);
     r->f32.release();
     r->bf.release();
+    r->dmaps.release();
     delete r;
     return MRS_OK;
 }
