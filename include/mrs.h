@@ -384,9 +384,8 @@ mrs_status mrs_gate_async(const float* fused, const float* lrhs, const float* pl
  * relu != 0 applies max(0, .).  precision MRS_PREC_FP32 computes in FP32;
  * MRS_PREC_BF16 / MRS_PREC_FP8 round x and w to the operand type and
  * accumulate in FP32 on the tensor cores (cout <= 64; cin <= 64 for FP8,
- * cin <= 1024 for BF16: past 64 input channels the conv runs as one launch
- * per 64-channel chunk accumulating into `out`, which must then be 16-byte
- * aligned). */
+ * cin <= 1024 for BF16: past 64 input channels one launch accumulates the
+ * 64-channel chunks in tensor memory). */
 mrs_status mrs_conv3x3(const float* x, int32_t N, int32_t H, int32_t W, int32_t cin,
                        int32_t cout, const float* w, const float* b, int32_t relu,
                        int32_t precision, float* out, void* stream);

@@ -567,13 +567,6 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int x = xb * kFoldTile + j;
             const bool valid = x < a.W;
             const size_t p = ((size_t)n * a.H + y) * a.W + (valid ? x : 0);
-            float4 pre[4];
-            const bool pre_ok = a.acc_in && valid && active && (bf_out || a.cout == 64);
-            if (pre_ok) {
-                const float4* ap = (const float4*)(a.acc_in + p * 64 + grp * 16);
-#pragma unroll
-                for (int i4 = 0; i4 < 4; ++i4) pre[i4] = ap[i4];
-            }
             if (!mbar_wait_warp(&tfull[sl], use & 1, a.err)) { stop = true; break; }
             tc_fence_after();
             if (!mbar_wait_warp(&rfull[slot], suse & 1, a.err)) { stop = true; break; }
@@ -600,17 +593,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                     float o[16];
 #pragma unroll
                     for (int e = 0; e < 16; ++e) o[e] = v[e] + sBias[c0 + e];
-                    if (pre_ok) {
-#pragma unroll
-                        for (int i4 = 0; i4 < 4; ++i4) {
-                            o[4 * i4] += pre[i4].x; o[4 * i4 + 1] += pre[i4].y;
-                            o[4 * i4 + 2] += pre[i4].z; o[4 * i4 + 3] += pre[i4].w;
-                        }
-                    } else if (a.acc_in && valid) {
-                        const float* ap = a.acc_in + p * 64 + c0;
-#pragma unroll
-                        for (int e = 0; e < 16; ++e) o[e] += ap[e];
-                    }
                     if (a.mode == TC_RELU_BF16) {
 #pragma unroll
                         for (int e = 0; e < 16; ++e) o[e] = fmaxf(o[e], 0.0f);
@@ -672,18 +654,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                         }
                     } else if (a.cout == 64 && ((uintptr_t)a.out & 15) == 0) {
                         float4* op = (float4*)((float*)a.out + p * 64 + c0);
-                        const float4* ap = a.acc_in ? (const float4*)(a.acc_in + p * 64 + c0) : nullptr;
-                        float4 u4[4];
-#pragma unroll
-                        for (int i4 = 0; i4 < 4; ++i4)
-                            u4[i4] = pre_ok ? pre[i4] : (ap ? ap[i4] : make_float4(0.f, 0.f, 0.f, 0.f));
 #pragma unroll
                         for (int i4 = 0; i4 < 4; ++i4) {
                             float4 t = make_float4(v[4 * i4] + sBias[c0 + 4 * i4],
                                                    v[4 * i4 + 1] + sBias[c0 + 4 * i4 + 1],
                                                    v[4 * i4 + 2] + sBias[c0 + 4 * i4 + 2],
                                                    v[4 * i4 + 3] + sBias[c0 + 4 * i4 + 3]);
-                            t.x += u4[i4].x; t.y += u4[i4].y; t.z += u4[i4].z; t.w += u4[i4].w;
                             if (a.relu) {
                                 t.x = fmaxf(t.x, 0.0f); t.y = fmaxf(t.y, 0.0f);
                                 t.z = fmaxf(t.z, 0.0f); t.w = fmaxf(t.w, 0.0f);
@@ -696,7 +672,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                         for (int e = 0; e < 16; ++e) {
                             if (c0 + e < a.cout) {
                                 float o = v[e] + sBias[c0 + e];
-                                if (a.acc_in) o += a.acc_in[p * a.cout + c0 + e];
                                 op[c0 + e] = a.relu ? fmaxf(o, 0.0f) : o;
                             }
                         }
@@ -868,8 +843,8 @@ mrs_status tc_wait_selftest(long long limit_cycles, int* gave_up, cudaStream_t s
 
 mrs_status tc_conv3x3(const TcConvArgs& a, cudaStream_t st)
 {
-    if (a.acc_in && (((uintptr_t)a.acc_in & 15) || a.operand != TC_BF16)) {
-        set_error("tc_conv3x3: acc_in must be 16-byte aligned, with bf16 operands");
+    if (a.kc > 1 && (!a.amaps || ((uintptr_t)a.amaps & 63))) {
+        set_error("tc_conv3x3: kc > 1 needs a 64-byte aligned device array of kc maps");
         return MRS_ERR_ARG;
     }
     if (a.nout == 64) return a.operand == TC_BF16 ? launch_fold<64, TC_BF16>(a, st) : launch_fold<64, TC_FP8>(a, st);

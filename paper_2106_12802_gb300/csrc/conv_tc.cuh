@@ -44,12 +44,6 @@ struct TcConvArgs {
     // TC_RELU_BF16 / TC_RESID_BF16 with fp8 operands: also emit the fp8 copy
     void* out_fp8;
     float out_fp8_inv_scale;
-    // optional FP32 partial sum [p][64] (stride 64 floats; stride cout for
-    // TC_PLAIN_F32) added to acc before the epilogue: a convolution over more
-    // than 64 input channels is a chain of launches, one per 64-channel
-    // chunk, each adding its chunk's contribution (TC_PLAIN_F32 with acc_in =
-    // out) and the last applying the layer's epilogue.  BF16 operands only.
-    const float* acc_in;
     // A convolution over kc > 1 input tensors of 64 channels each (the
     // concatenation of their channels) in ONE launch: amaps = DEVICE array of
     // kc A-operand maps (64-byte aligned, alive until the kernel completes),

@@ -1013,9 +1013,9 @@ extern "C" mrs_status mrs_gate(const float* fused, const float* lrhs, const floa
 
 namespace mrs {
 namespace {
-// BF16 3x3 conv over more than 64 input channels: one tensor-core launch per
-// 64-channel chunk, each adding its contribution to the FP32 output (the
-// first with the bias, the last with the ReLU)
+// BF16 3x3 conv over more than 64 input channels: the input is split into
+// 64-channel operand tensors and ONE tensor-core launch accumulates all of
+// them (multi-chunk conv, chunk maps passed in device memory)
 mrs_status conv3x3_chunked(Scratch& S, const float* x, int N, int H, int W, int cin, int cout,
                            const float* w, const float* b, int relu, float* out, cudaStream_t st)
 {
@@ -1023,45 +1023,43 @@ mrs_status conv3x3_chunked(Scratch& S, const float* x, int N, int H, int W, int 
     const int nch = (cin + 63) / 64;
     const int nout = cout > 16 ? 64 : 16;
     const size_t wbytes = (size_t)cout * 9 * cin * 4;
-    const size_t chw = (size_t)9 * 64 * 64 * 2;
-    size_t need = wbytes + 2 * 64 * 4 + nch * chw + P * 128 + 4096;
+    const size_t chunk_el = (size_t)9 * nout * 64;               // packed bf16 weights per chunk
+    const size_t wpk_bytes = ((nch * chunk_el * 2 + 1023) / 1024) * 1024;
+    const size_t xq_bytes = ((P * 128 + 1023) / 1024) * 1024;    // one [P][64] bf16 operand
+    size_t need = wbytes + 64 * 4 + 1024 + wpk_bytes + nch * xq_bytes + nch * sizeof(CUtensorMap) + 1024;
     mrs_status rc = S.b.ensure(need);
     if (rc != MRS_OK) return rc;
     uint8_t* base = S.b.as<uint8_t>();
     float* dw = (float*)base;
     float* db = dw + (size_t)cout * 9 * cin;
-    float* zb = db + 64;
-    uint8_t* q = (uint8_t*)(((uintptr_t)(zb + 64) + 1023) & ~(uintptr_t)1023);
-    __nv_bfloat16* xq = (__nv_bfloat16*)(q + nch * chw);
-    MRS_CHECK(cudaMemsetAsync(db, 0, 128 * 4, st));
+    uint8_t* wpk = (uint8_t*)(((uintptr_t)(db + 64) + 1023) & ~(uintptr_t)1023);
+    uint8_t* xq = wpk + wpk_bytes;
+    CUtensorMap* dmaps = (CUtensorMap*)(xq + nch * xq_bytes);
+    MRS_CHECK(cudaMemsetAsync(db, 0, 64 * 4, st));
     MRS_CHECK(cudaMemcpyAsync(dw, w, wbytes, cudaMemcpyHostToDevice, st));
     MRS_CHECK(cudaMemcpyAsync(db, b, cout * 4, cudaMemcpyHostToDevice, st));
     static int* err = nullptr;
     if (!err) { MRS_CHECK(cudaMalloc(&err, 4)); MRS_CHECK(cudaMemset(err, 0, 4)); }
-    std::vector<CUtensorMap> wm(nch);
+    std::vector<CUtensorMap> hm(nch);
     for (int j = 0; j < nch; ++j) {
-        k_pack_bf16_chunk<<<(9 * nout * 64 + 255) / 256, 256, 0, st>>>(dw, cin, 64 * j, cout, nout,
-                                                                       (__nv_bfloat16*)(q + j * chw));
+        k_pack_bf16_chunk<<<(9 * nout * 64 + 255) / 256, 256, 0, st>>>(
+            dw, cin, 64 * j, cout, nout, (__nv_bfloat16*)wpk + j * chunk_el);
         MRS_LAUNCHED(1);
-        if ((rc = tc_make_w_map(&wm[j], q + j * chw, 9 * nout, nout, TC_BF16)) != MRS_OK) return rc;
+        __nv_bfloat16* xj = (__nv_bfloat16*)(xq + j * xq_bytes);
+        k_to_operand_chunk<<<1024, 256, 0, st>>>(x, P, cin, 64 * j, xj);
+        MRS_LAUNCHED(1);
+        if ((rc = tc_make_act_map(&hm[j], xj, N, H, W, TC_BF16, tc_a_box(TC_BF16))) != MRS_OK) return rc;
     }
-    CUtensorMap mx;
-    if ((rc = tc_make_act_map(&mx, xq, N, H, W, TC_BF16, tc_a_box(TC_BF16))) != MRS_OK) return rc;
+    CUtensorMap wm;
+    if ((rc = tc_make_w_map(&wm, wpk, nch * 9 * nout, nout, TC_BF16)) != MRS_OK) return rc;
+    MRS_CHECK(cudaMemcpyAsync(dmaps, hm.data(), nch * sizeof(CUtensorMap), cudaMemcpyHostToDevice, st));
     TcConvArgs a;
     memset(&a, 0, sizeof(a));
-    a.tmap_x = &mx; a.out = out; a.N = N; a.H = H; a.W = W; a.scale = 1; a.nout = nout;
-    a.cout = cout; a.mode = TC_PLAIN_F32; a.operand = TC_BF16; a.err = err;
-    for (int j = 0; j < nch && rc == MRS_OK; ++j) {
-        // the operand buffer is reused: the previous chunk's conv has read it
-        // by the time this stream-ordered conversion runs
-        k_to_operand_chunk<<<1024, 256, 0, st>>>(x, P, cin, 64 * j, xq);
-        MRS_LAUNCHED(1);
-        a.tmap_w = &wm[j];
-        a.bias = j == 0 ? db : zb;
-        a.acc_in = j == 0 ? nullptr : out;
-        a.relu = j == nch - 1 ? relu : 0;
-        rc = tc_conv3x3(a, st);
-    }
+    a.tmap_x = &hm[0]; a.tmap_w = &wm; a.amaps = dmaps; a.kc = nch; a.w_row0 = 0;
+    a.bias = db; a.out = out; a.N = N; a.H = H; a.W = W; a.scale = 1; a.nout = nout;
+    a.cout = cout; a.relu = relu; a.mode = TC_PLAIN_F32; a.operand = TC_BF16; a.err = err;
+    rc = tc_conv3x3(a, st);
+    // the host map array and the scratch stay valid until the stream is synchronised
     if (rc == MRS_OK) rc = cuda_status(cudaStreamSynchronize(st), "conv3x3 sync");
     int herr = 0;
     if (rc == MRS_OK) {
@@ -1082,8 +1080,6 @@ extern "C" mrs_status mrs_conv3x3(const float* x, int32_t N, int32_t H, int32_t 
     MRS_ARG(precision == MRS_PREC_FP32 || cout <= 64, "tensor-core conv needs cout <= 64");
     MRS_ARG(precision == MRS_PREC_FP32 || cin <= 64 || (precision == MRS_PREC_BF16 && cin <= 1024),
             "tensor-core conv needs cin <= 64 (FP8) or cin <= 1024 (BF16)");
-    MRS_ARG(precision != MRS_PREC_BF16 || cin <= 64 || ((uintptr_t)out & 15) == 0,
-            "out must be 16-byte aligned for cin > 64");
     cudaStream_t st = (cudaStream_t)stream;
     size_t P = (size_t)N * H * W;
     Scratch& S = scratch();

@@ -511,7 +511,7 @@ mrs_status rdn_bf16(mrs_rdn_s* r, const float* lrhs, const float* hrls, const fl
             a.w_row0 = (int)(c0.off / 64);
             a.tmap_w = &r->wmap_all;
             a.bias = r->bch + (size_t)r->first[li] * 64;
-            a.nout = 64; a.acc_in = nullptr; a.relu = 0;
+            a.nout = 64; a.relu = 0;
             a.mode = mode; a.tmap_out = o; a.tmap_res = res;
             mc += n;
             mrs_status e = tc_conv3x3(a, st);
@@ -525,7 +525,7 @@ mrs_status rdn_bf16(mrs_rdn_s* r, const float* lrhs, const float* hrls, const fl
         a.tmap_w = &c.map;
         a.bias = r->bch + (size_t)r->first[li] * 64;
         a.nout = c.nout;
-        a.acc_in = nullptr; a.relu = 0;
+        a.relu = 0;
         a.mode = mode; a.tmap_out = o; a.tmap_res = res;
         return tc_conv3x3(a, st);
     };
@@ -590,7 +590,7 @@ mrs_status rdn_bf16(mrs_rdn_s* r, const float* lrhs, const float* hrls, const fl
             a.H = ch; a.W = cw;
             const WChunk& c = r->ch[r->first[li] + q];
             a.tmap_x = src; a.tmap_w = &c.map; a.bias = r->bch + (size_t)(r->first[li] + q) * 64;
-            a.nout = 64; a.acc_in = nullptr; a.tmap_res = nullptr; a.tmap_out = &vo;
+            a.nout = 64; a.tmap_res = nullptr; a.tmap_out = &vo;
             a.mode = TC_RELU_BF16; a.relu = 0;
             if ((rc = tc_conv3x3(a, st)) != MRS_OK) return rc;
         }
@@ -602,7 +602,7 @@ mrs_status rdn_bf16(mrs_rdn_s* r, const float* lrhs, const float* hrls, const fl
     // H_Rec: 64 -> 3, no ReLU, FP32 out
     const WChunk& c = r->ch[r->first[li]];
     a.H = H; a.W = W; a.tmap_x = src; a.tmap_w = &c.map; a.bias = r->bch + (size_t)r->first[li] * 64;
-    a.nout = c.nout; a.acc_in = nullptr; a.tmap_out = nullptr; a.tmap_res = nullptr;
+    a.nout = c.nout; a.tmap_out = nullptr; a.tmap_res = nullptr;
     a.mode = TC_PLAIN_F32; a.out = out; a.cout = 3; a.relu = 0;
     return tc_conv3x3(a, st);
     };

@@ -59,10 +59,13 @@ def test_param_count_matches_oracle(mrs):
             assert mrs.rdn_nparams(s, c) == rdn.nparams(s, c)
 
 
-@pytest.mark.parametrize("cin,cout,relu", [(128, 64, 1), (256, 64, 0), (200, 3, 0), (192, 64, 1)])
-def test_conv_bf16_multichunk_matches_oracle(mrs, cin, cout, relu):
+@pytest.mark.parametrize("N,H,W,cin,cout,relu", [(1, 5, 250, 128, 64, 1), (1, 5, 250, 256, 64, 0),
+                                                 (1, 5, 250, 200, 3, 0), (1, 5, 250, 192, 64, 1),
+                                                 (2, 400, 130, 128, 64, 1)])
+def test_conv_bf16_multichunk_matches_oracle(mrs, N, H, W, cin, cout, relu):
+    # one launch accumulates the 64-channel chunks in TMEM; the last case gives
+    # each CTA about ten rows, i.e. two sub-pieces with their own halo rows
     rng = np.random.default_rng(cin + cout)
-    N, H, W = 1, 5, 250
     x = rng.normal(size=(N, H, W, cin)).astype(np.float32)
     w = (rng.normal(size=(cout, 3, 3, cin)) * np.sqrt(2.0 / (9 * cin))).astype(np.float32)
     b = (rng.normal(size=cout) * 0.1).astype(np.float32)
