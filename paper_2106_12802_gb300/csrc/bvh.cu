@@ -151,28 +151,36 @@ __global__ void k_sort_hist(const uint32_t* __restrict__ keys, int n, int shift,
     counts[threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
 }
 
-// exclusive scan of counts[0..m) in place, one block of 1024 threads
+// exclusive scan of counts[0..m) in place, one block of 1024 threads: each
+// thread sums a contiguous run of ceil(m / 1024) counts, one block-wide scan
+// of the 1024 run totals gives each run's offset, and each thread writes its
+// run's exclusive prefix (integer sums: the order does not change the result)
 __global__ void k_sort_scan(uint32_t* __restrict__ counts, int m)
 {
     __shared__ uint32_t s[1024];
-    __shared__ uint32_t carry;
-    if (threadIdx.x == 0) carry = 0;
+    const int per = (m + 1023) / 1024;
+    const int b0 = threadIdx.x * per;
+    uint32_t sum = 0;
+    for (int k = 0; k < per; ++k) {
+        int i = b0 + k;
+        if (i < m) sum += counts[i];
+    }
+    s[threadIdx.x] = sum;
     __syncthreads();
-    for (int base = 0; base < m; base += 1024) {
-        int i = base + threadIdx.x;
-        uint32_t v = i < m ? counts[i] : 0u;
-        s[threadIdx.x] = v;
+    for (int off = 1; off < 1024; off <<= 1) {
+        uint32_t t = threadIdx.x >= off ? s[threadIdx.x - off] : 0u;
         __syncthreads();
-        for (int off = 1; off < 1024; off <<= 1) {
-            uint32_t t = threadIdx.x >= off ? s[threadIdx.x - off] : 0u;
-            __syncthreads();
-            s[threadIdx.x] += t;
-            __syncthreads();
+        s[threadIdx.x] += t;
+        __syncthreads();
+    }
+    uint32_t run = s[threadIdx.x] - sum;
+    for (int k = 0; k < per; ++k) {
+        int i = b0 + k;
+        if (i < m) {
+            uint32_t v = counts[i];
+            counts[i] = run;
+            run += v;
         }
-        if (i < m) counts[i] = carry + s[threadIdx.x] - v;
-        __syncthreads();
-        if (threadIdx.x == 1023) carry += s[1023];
-        __syncthreads();
     }
 }
 

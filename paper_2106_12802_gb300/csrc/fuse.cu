@@ -338,13 +338,23 @@ __global__ void k_metrics_partial(const float* __restrict__ x, const float* __re
     if (threadIdx.x < 3) part[blockIdx.x * 3 + threadIdx.x] = s[threadIdx.x][0];
 }
 
+// out[c] = sum over i of part[i k + c] (c < k <= 4), one block of 256
+// threads: strided per-thread sums, then a fixed-order tree (deterministic)
 __global__ void k_reduce_parts(const double* part, int nparts, int k, double* out)
 {
-    if (threadIdx.x < k) {
+    __shared__ double sh[4][256];
+    for (int c = 0; c < k; ++c) {
         double acc = 0;
-        for (int i = 0; i < nparts; ++i) acc += part[i * k + threadIdx.x];
-        out[threadIdx.x] = acc;
+        for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc += part[i * k + c];
+        sh[c][threadIdx.x] = acc;
     }
+    __syncthreads();
+    for (int w = 128; w; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int c = 0; c < k; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < k) out[threadIdx.x] = sh[threadIdx.x][0];
 }
 
 // per LR pixel: RelMSE terms of box_s(fused) vs LRHS
@@ -586,9 +596,18 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float
 __global__ void k_gate_decide(const double* part, int nparts, double count, double tau,
                               int use_plain_avail, int* used_plain, double* D)
 {
+    // the same fixed-order reduction as k_reduce_parts
+    __shared__ double sh[256];
+    double a = 0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) a += part[i];
+    sh[threadIdx.x] = a;
+    __syncthreads();
+    for (int w = 128; w; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
     if (threadIdx.x == 0) {
-        double acc = 0;
-        for (int i = 0; i < nparts; ++i) acc += part[i];
+        double acc = sh[0];
         double d = acc / count;
         if (D) *D = d;
         int u = d > tau ? 1 : 0;
@@ -966,7 +985,7 @@ extern "C" mrs_status mrs_image_metrics(const float* x, const float* ref, int64_
     double* res = part + kRedBlocks * 3;
     k_metrics_partial<<<kRedBlocks, 256, 0, st>>>(x, ref, n, l1, l2, part);
     MRS_LAUNCHED(1);
-    k_reduce_parts<<<1, 32, 0, st>>>(part, kRedBlocks, 3, res);
+    k_reduce_parts<<<1, 256, 0, st>>>(part, kRedBlocks, 3, res);
     MRS_LAUNCHED(1);
     double h[3];
     MRS_CHECK(cudaMemcpyAsync(h, res, sizeof(h), cudaMemcpyDeviceToHost, st));
@@ -994,7 +1013,7 @@ extern "C" mrs_status mrs_gate(const float* fused, const float* lrhs, const floa
     double* res = part + kRedBlocks;
     k_gate_partial<<<kRedBlocks, 256, 0, st>>>(fused, lrhs, N, H, W, scale, part);
     MRS_LAUNCHED(1);
-    k_reduce_parts<<<1, 32, 0, st>>>(part, kRedBlocks, 1, res);
+    k_reduce_parts<<<1, 256, 0, st>>>(part, kRedBlocks, 1, res);
     MRS_LAUNCHED(1);
     double d;
     MRS_CHECK(cudaMemcpyAsync(&d, res, sizeof(d), cudaMemcpyDeviceToHost, st));
@@ -1252,7 +1271,7 @@ mrs_status train_step_f32(mrs_net_s* net, const float* lrhs, const float* hrls, 
     MRS_TIMED(PK_TRAIN, st, k_loss<<<kRedBlocks, 256, 0, st>>>(y, target, P * 3, kClip, net->loss_kind,
                                                                net->loss_beta, dy, lparts));
     MRS_LAUNCHED(1);
-    k_reduce_parts<<<1, 32, 0, st>>>(lparts, kRedBlocks, 1, lres);
+    k_reduce_parts<<<1, 256, 0, st>>>(lparts, kRedBlocks, 1, lres);
     MRS_LAUNCHED(1);
 
     // backward
@@ -1403,7 +1422,7 @@ mrs_status train_step_bf16(mrs_net_s* net, const float* lrhs, const float* hrls,
     MRS_TIMED(PK_TRAIN, st, k_loss<<<kRedBlocks, 256, 0, st>>>(y, target, P * 3, kClip, net->loss_kind,
                                                                net->loss_beta, dy, lparts));
     MRS_LAUNCHED(1);
-    k_reduce_parts<<<1, 32, 0, st>>>(lparts, kRedBlocks, 1, lres);
+    k_reduce_parts<<<1, 256, 0, st>>>(lparts, kRedBlocks, 1, lres);
     MRS_LAUNCHED(1);
 
     // backward: weight gradients on the tensor cores (per-CTA partials, then a
@@ -1554,7 +1573,7 @@ extern "C" mrs_status mrs_gate_async(const float* fused, const float* lrhs, cons
     if (rc != MRS_OK) return rc;
     k_gate_partial<<<kRedBlocks, 256, 0, st>>>(fused, lrhs, N, H, W, scale, parts.as<double>());
     MRS_LAUNCHED(1);
-    k_gate_decide<<<1, 32, 0, st>>>(parts.as<double>(), kRedBlocks,
+    k_gate_decide<<<1, 256, 0, st>>>(parts.as<double>(), kRedBlocks,
                                     (double)N * (H / scale) * (W / scale) * 3, tau,
                                     plain ? 1 : 0, used_plain, D);
     MRS_LAUNCHED(1);
