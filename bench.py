@@ -681,10 +681,16 @@ def run_gpu(args, rank, world):
                     "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": ach / peaks["hbm_gbs"], "traffic": _traffic("k_conv_tc", "conv_tc.cu"),
                     "peak_source": peaks["source"] + " HBM copy"}
-    elif dom in ("trace", "shadow") and stats_lr:
-        key = "" if dom == "trace" else "shadow_"
-        ops = OPS_PER_NODE_VISIT * (stats_lr[key + "visits"] + stats_hr[key + "visits"]) + \
-            OPS_PER_TRI_TEST * (stats_lr[key + "tests"] + stats_hr[key + "tests"])
+    elif dom in ("trace", "shadow", "tail") and stats_lr:
+        # traversal work of the kernel's own launches: the tail kernel's share
+        # (late bounces, closest-hit and shadow rays) is counted apart
+        def work(kind, part):
+            tail = stats_lr["tail_" + kind] + stats_hr["tail_" + kind]
+            return tail if part == "tail" else stats_lr[kind] + stats_hr[kind] - tail
+        kinds = {"trace": ("",), "shadow": ("shadow_",), "tail": ("", "shadow_")}[dom]
+        visits = sum(work(k + "visits", dom) for k in kinds)
+        tests = sum(work(k + "tests", dom) for k in kinds)
+        ops = OPS_PER_NODE_VISIT * visits + OPS_PER_TRI_TEST * tests
         kms = family_ms[dom]
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         peak = sms * 128 * peaks["sm_max_mhz"] * 1e6 / 1e12
@@ -694,9 +700,8 @@ def run_gpu(args, rank, world):
                     "traffic": _traffic(f"k_{dom}", "pt.cu"),
                     "peak_source": f"{sms} SMs x 128 FP32 lanes x {peaks['sm_max_mhz']} MHz "
                                    "(non-FMA ops; the kernel is built with --fmad=false)",
-                    "ops_per_frame": ops,
-                    "node_visits_per_frame": stats_lr[key + "visits"] + stats_hr[key + "visits"],
-                    "tri_tests_per_frame": stats_lr[key + "tests"] + stats_hr[key + "tests"]}
+                    "ops_per_frame": ops, "node_visits_per_frame": visits,
+                    "tri_tests_per_frame": tests}
 
     if rank == 0:
         cpu = None

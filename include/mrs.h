@@ -162,10 +162,12 @@ mrs_status mrs_render(mrs_scene scene, int32_t W, int32_t H, int32_t spp, int32_
                       float* normal, float* depth, uint64_t* counts, uint64_t* shadow_counts,
                       void* stream);
 
-/* The same render with instrumented traversal: stats device uint64[4] receives
+/* The same render with instrumented traversal: stats device uint64[8] receives
  * BVH node visits and triangle tests of the closest-hit traversals, then of
- * the shadow (any-hit) traversals.  The radiance equals mrs_render's.  For
- * measuring algorithmic work (roofline accounting); no paper counterpart. */
+ * the shadow (any-hit) traversals (entries 0-3, all bounces), then the part
+ * of those four done inside the tail kernel (entries 4-7; see
+ * mrs_scene_set_tail).  The radiance equals mrs_render's.  For measuring
+ * algorithmic work (roofline accounting); no paper counterpart. */
 mrs_status mrs_render_stats(mrs_scene scene, int32_t W, int32_t H, int32_t spp, int32_t max_depth,
                             int32_t rr_start, uint64_t seed, float* radiance, uint64_t* stats,
                             void* stream);
@@ -177,7 +179,9 @@ mrs_status mrs_render_stats(mrs_scene scene, int32_t W, int32_t H, int32_t spp, 
  * 0 closest-hit traversal, 1 shade, 2 shadow traversal, 3 ray generation,
  * 4 accumulation, 5 LBVH build (whole), 6 tensor-core conv, 7 SIMT conv,
  * 8 fusion input, 9 metrics, 10 training kernels (other than 11),
- * 11 tensor-core weight gradient.  Instrumentation only. */
+ * 11 tensor-core weight gradient, 12 the render's tail kernel (the late
+ * bounces' traversal, shading and shadow rays in one launch).
+ * Instrumentation only. */
 mrs_status mrs_profile_enable(int32_t on);
 mrs_status mrs_profile_read(int32_t kernel, double* total_ms, int64_t* launches);
 
@@ -248,6 +252,17 @@ mrs_status mrs_render_layers(mrs_ctx ctx, mrs_scene scene, int32_t W, int32_t H,
 /* Paths per wave for subsequent mrs_render calls on this scene (rounded to
  * whole samples of the image; default 16M paths).  For tests and tuning. */
 mrs_status mrs_scene_set_wave(mrs_scene scene, int64_t max_paths_per_wave);
+
+/* First bounce that the renders of this scene (mrs_scene_set_tail: those
+ * without a context) or of this context (mrs_ctx_set_tail) shade in the tail
+ * kernel instead of one launch per step: every bounce b >= `bounce` of a
+ * path runs in a single persistent launch that takes each path left in the
+ * queue of bounce `bounce` to its end.  The result is bit-identical either
+ * way (same per-path operations, same counts); only the launch structure
+ * changes.  -1 (default): bounce 2; any value > max_depth: no tail.  Range
+ * [-1, 64], else MRS_ERR_ARG. */
+mrs_status mrs_scene_set_tail(mrs_scene scene, int32_t bounce);
+mrs_status mrs_ctx_set_tail(mrs_ctx ctx, int32_t bounce);
 
 /* The 8 Philox uniforms of each (pixel, sample, bounce) triple given in
  * `triples` (device uint32 [n][3]) for key = seed: out device float [n][8]. */

@@ -35,6 +35,8 @@ SIGS = {
     "mrs_ctx_create": [P],
     "mrs_ctx_free": [P],
     "mrs_ctx_set_wave": [P, I64],
+    "mrs_ctx_set_tail": [P, I32],
+    "mrs_scene_set_tail": [P, I32],
     "mrs_render_ctx": [P, P, I32, I32, I32, I32, I32, U64, P, P, P, P, P, P, P],
     "mrs_render_grid": [P, P, I32, I32, I32, I32, I32, U64, I32, P, P, P, P, P, P, P],
     "mrs_render_layers": [P, P, I32, I32, I32, I32, I32, U64, I32, P, P],

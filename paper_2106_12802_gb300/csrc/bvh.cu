@@ -771,6 +771,14 @@ extern "C" mrs_status mrs_scene_set_wave(mrs_scene S, int64_t max_paths)
     return MRS_OK;
 }
 
+extern "C" mrs_status mrs_scene_set_tail(mrs_scene S, int32_t bounce)
+{
+    MRS_ARG(S != nullptr, "scene is NULL");
+    MRS_ARG(bounce >= -1 && bounce <= 64, "tail bounce out of range [-1, 64]");
+    S->tail_bounce = bounce;
+    return MRS_OK;
+}
+
 extern "C" mrs_status mrs_lbvh_build_static(const float* V, int32_t n, uint32_t* morton,
                                             int32_t* order, int32_t* left, int32_t* right,
                                             float* box, void* stream)

@@ -22,7 +22,7 @@ std::atomic<unsigned long long>& launch_counter();
 // events are recorded on the launching stream around each timed launch.
 enum ProfKernel {
     PK_TRACE = 0, PK_SHADE, PK_SHADOW, PK_RAYGEN, PK_ACCUM, PK_LBVH, PK_CONV_TC, PK_CONV_SIMT,
-    PK_INPUT, PK_METRICS, PK_TRAIN, PK_WGRAD_TC, PK_COUNT
+    PK_INPUT, PK_METRICS, PK_TRAIN, PK_WGRAD_TC, PK_TAIL, PK_COUNT
 };
 bool prof_on();
 cudaEvent_t prof_record(cudaStream_t st);
@@ -125,6 +125,7 @@ struct mrs_scene_s {
     mrs::Buf export_tmp;         // full-scene LBVH built on export
     mrs::Buf arena;              // render path state
     int64_t wave_paths = int64_t(1) << 24;
+    int32_t tail_bounce = -1;    // first bounce of the tail kernel (-1: bounce 2)
 };
 
 // Render context: a path-state arena of its own, so that several renders of
@@ -132,6 +133,7 @@ struct mrs_scene_s {
 struct mrs_ctx_s {
     mrs::Buf arena;
     int64_t wave_paths = int64_t(1) << 24;
+    int32_t tail_bounce = -1;
 };
 
 // Layout of the render arena for a wave of P paths (floats unless noted).

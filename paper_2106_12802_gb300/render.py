@@ -78,6 +78,10 @@ class Scene:
     def set_wave(self, paths: int):
         call("mrs_scene_set_wave", self.handle, int(paths))
 
+    def set_tail(self, bounce: int):
+        """First bounce of the tail kernel (-1: automatic; > max_depth: none)."""
+        call("mrs_scene_set_tail", self.handle, int(bounce))
+
     def export_bvh(self, stream=None):
         n = self.n
         dev = torch.device("cuda")
@@ -120,6 +124,10 @@ class RenderContext:
 
     def set_wave(self, paths: int):
         call("mrs_ctx_set_wave", self.handle, int(paths))
+
+    def set_tail(self, bounce: int):
+        """First bounce of the tail kernel (-1: automatic; > max_depth: none)."""
+        call("mrs_ctx_set_tail", self.handle, int(bounce))
 
     def close(self):
         if getattr(self, "handle", None):
@@ -179,18 +187,22 @@ def render(scene: Scene, W, H, spp, max_depth, rr_start=None, seed=0, aux=True, 
 
 
 def render_stats(scene: Scene, W, H, spp, max_depth, rr_start=None, seed=0, stream=None):
-    """Node visits / triangle tests of the closest-hit and shadow traversals."""
+    """Node visits / triangle tests of the closest-hit and shadow traversals
+    (all bounces), and the part of them done in the tail kernel (tail_*)."""
     dev = torch.device("cuda")
     rad = torch.empty((H, W, 3), dtype=torch.float32, device=dev)
-    st = torch.zeros(4, dtype=torch.int64, device=dev)
+    st = torch.zeros(8, dtype=torch.int64, device=dev)
     call("mrs_render_stats", scene.handle, W, H, spp, max_depth, -1 if rr_start is None else rr_start,
          int(seed), _ptr(rad), _ptr(st), _stream(stream))
     v = st.cpu().tolist()
-    return {"visits": v[0], "tests": v[1], "shadow_visits": v[2], "shadow_tests": v[3]}
+    names = ("visits", "tests", "shadow_visits", "shadow_tests")
+    out = dict(zip(names, v[:4]))
+    out.update({"tail_" + k: x for k, x in zip(names, v[4:])})
+    return out
 
 
 PROFILE_KERNELS = ["trace", "shade", "shadow", "raygen", "accumulate", "lbvh", "conv_tc",
-                   "conv_simt", "input", "metrics", "train", "wgrad_tc"]
+                   "conv_simt", "input", "metrics", "train", "wgrad_tc", "tail"]
 
 
 def profile_enable(on=True):

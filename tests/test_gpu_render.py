@@ -181,6 +181,45 @@ def test_render_extra_layers_match_oracle(mrs, orc, case):
     assert (g["diffuse"] + g["specular"] <= g["radiance"] * (1 + 1e-5) + 1e-6).all()
 
 
+@pytest.mark.parametrize("tail", [0, 2, 5])
+def test_render_tail_kernel_bit_identical(mrs, orc, tail):
+    # the late bounces in one persistent launch (every bounce >= tail) against
+    # the oracle and against the wavefront-only render: same counts, same bits,
+    # same traversal work; two waves (the work counter restarts per wave)
+    desc = scenes.procedural(0)
+    W, H, spp, D, rr, seed = 40, 24, 4, 8, 3, 5
+    sc = mrs.Scene(desc)
+    sc.set_wave(W * H * 2)
+    sc.set_tail(64)   # > max_depth: no tail
+    ref = mrs.render(sc, W, H, spp, D, rr_start=rr, seed=seed)
+    ref_stats = mrs.render_stats(sc, W, H, spp, D, rr, seed)
+    sc.set_tail(tail)
+    g = mrs.render(sc, W, H, spp, D, rr_start=rr, seed=seed)
+    stats = mrs.render_stats(sc, W, H, spp, D, rr, seed)
+    ctx = mrs.RenderContext()
+    ctx.set_tail(tail)
+    gc = mrs.render(sc, W, H, spp, D, rr_start=rr, seed=seed, ctx=ctx, layers=True)
+    torch.cuda.synchronize()
+    ref = {k: v.cpu().numpy() for k, v in ref.items()}
+    g = {k: v.cpu().numpy() for k, v in g.items()}
+    gc = {k: v.cpu().numpy() for k, v in gc.items()}
+    for k in ref:
+        assert np.array_equal(g[k], ref[k]), k
+        assert np.array_equal(gc[k], ref[k]), k
+    for k in ("visits", "tests", "shadow_visits", "shadow_tests"):
+        assert stats[k] == ref_stats[k], k
+        assert ref_stats["tail_" + k] == 0
+    if tail <= D:
+        assert stats["tail_visits"] > 0
+    r = orc.render(desc, W, H, spp, D, rr_start=rr, seed=seed)
+    assert np.array_equal(g["counts"].astype(np.uint64), r["counts"])
+    assert np.array_equal(g["shadow_counts"].astype(np.uint64), r["shadow_counts"])
+    assert_radiance_parity(g["radiance"], r["radiance"])
+    for bad in (-2, 65):
+        with pytest.raises(Exception):
+            sc.set_tail(bad)
+
+
 def test_render_extra_layers_closed_form(mrs):
     # diffuse plane under a uniform sky: diffuse = rho * L_sky, no specular,
     # zero variance (every sample is the same value)
