@@ -154,32 +154,61 @@ __global__ void k_sort_hist(const uint32_t* __restrict__ keys, int n, int shift,
 // exclusive scan of counts[0..m) in place, one block of 1024 threads: each
 // thread sums a contiguous run of ceil(m / 1024) counts, one block-wide scan
 // of the 1024 run totals gives each run's offset, and each thread writes its
-// run's exclusive prefix (integer sums: the order does not change the result)
+// run's exclusive prefix (integer sums: the order does not change the result).
+// A run is read in groups of 8 independent loads, so that a thread waits for
+// the memory once per group rather than once per count.
+constexpr int kScanGroup = 8;
 __global__ void k_sort_scan(uint32_t* __restrict__ counts, int m)
 {
-    __shared__ uint32_t s[1024];
+    __shared__ uint32_t s[32];
     const int per = (m + 1023) / 1024;
     const int b0 = threadIdx.x * per;
     uint32_t sum = 0;
-    for (int k = 0; k < per; ++k) {
-        int i = b0 + k;
-        if (i < m) sum += counts[i];
+    for (int k0 = 0; k0 < per; k0 += kScanGroup) {
+        uint32_t v[kScanGroup];
+#pragma unroll
+        for (int j = 0; j < kScanGroup; ++j) {
+            const int i = b0 + k0 + j;
+            v[j] = (k0 + j < per && i < m) ? counts[i] : 0u;
+        }
+#pragma unroll
+        for (int j = 0; j < kScanGroup; ++j) sum += v[j];
     }
-    s[threadIdx.x] = sum;
+    // block-wide inclusive scan of the run totals: within each warp by
+    // shuffles, then over the 32 warp totals
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = sum;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += t;
+    }
+    if (lane == 31) s[warp] = incl;
     __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        uint32_t t = threadIdx.x >= off ? s[threadIdx.x - off] : 0u;
-        __syncthreads();
-        s[threadIdx.x] += t;
-        __syncthreads();
+    if (warp == 0) {
+        uint32_t w = s[lane];
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, w, off);
+            if (lane >= off) w += t;
+        }
+        s[lane] = w;
     }
-    uint32_t run = s[threadIdx.x] - sum;
-    for (int k = 0; k < per; ++k) {
-        int i = b0 + k;
-        if (i < m) {
-            uint32_t v = counts[i];
-            counts[i] = run;
-            run += v;
+    __syncthreads();
+    incl += warp > 0 ? s[warp - 1] : 0u;
+    uint32_t run = incl - sum;
+    for (int k0 = 0; k0 < per; k0 += kScanGroup) {
+        uint32_t v[kScanGroup];
+#pragma unroll
+        for (int j = 0; j < kScanGroup; ++j) {
+            const int i = b0 + k0 + j;
+            v[j] = (k0 + j < per && i < m) ? counts[i] : 0u;
+        }
+#pragma unroll
+        for (int j = 0; j < kScanGroup; ++j) {
+            const int i = b0 + k0 + j;
+            if (k0 + j < per && i < m) counts[i] = run;
+            run += v[j];
         }
     }
 }
