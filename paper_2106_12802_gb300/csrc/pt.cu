@@ -321,7 +321,8 @@ struct WaveParams {
     int layers;          // record the first-hit lobe (diffuse / specular / variance layers)
     int64_t wh;          // pixels
     int s0;              // first sample index of the wave
-    int n_paths;         // paths in the wave (= k * wh)
+    int kk;              // samples per pixel in the wave
+    int n_paths;         // paths in the wave (= kk * wh)
     uint2 key;
     uint32_t* cnt;       // [max_depth + 2] extension rays per bounce
     uint32_t* scnt;      // [max_depth + 1] shadow rays per bounce
@@ -333,8 +334,8 @@ __global__ void __launch_bounds__(kThreads) k_raygen(WaveParams w)
     PathSoA& P = w.P;
     if (blockIdx.x == 0 && threadIdx.x == 0) w.cnt[0] = (uint32_t)w.n_paths;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < w.n_paths; p += gridDim.x * blockDim.x) {
-        int pix = (int)(p % w.wh);
-        int sample = w.s0 + (int)(p / w.wh);
+        int pix = p / w.kk;
+        int sample = w.s0 + p % w.kk;
         int px = pix % w.W, py = pix / w.W;
         float4 g1 = draws((uint32_t)pix, (uint32_t)sample, 0u, 1u, w.key);
         const float* cam = w.cam;
@@ -469,8 +470,8 @@ __device__ __forceinline__ void shade_path(const WaveParams& w, const ShadeConst
         if (b == w.max_depth) break;
         if (!(m.albedo.x > 0.0f || m.albedo.y > 0.0f || m.albedo.z > 0.0f)) break;
 
-        int pix = (int)(p % w.wh);
-        uint32_t sample = (uint32_t)(w.s0 + (int)(p / w.wh));
+        int pix = p / w.kk;
+        uint32_t sample = (uint32_t)(w.s0 + p % w.kk);
         float4 g0 = draws((uint32_t)pix, sample, (uint32_t)b, 0u, w.key);
         float4 g1 = draws((uint32_t)pix, sample, (uint32_t)b, 1u, w.key);
         V3 T, B;
@@ -665,25 +666,60 @@ __global__ void __launch_bounds__(kThreads) k_tail(WaveParams w, int b0)
     }
 }
 
+// Path p of a wave is sample p % kk of pixel p / kk: a pixel's samples are
+// consecutive paths, so a warp's camera rays leave through one or a few
+// pixels (coherent bounce-0 traversal and shading).  The accumulation reads
+// each pixel's kk consecutive samples, V at a time (one 16-byte load per
+// field when kk is a multiple of 4: a warp's loads are then contiguous).
+template <int V> struct Vec;
+template <> struct Vec<1> {
+    float v[1];
+    __device__ __forceinline__ void load(const float* p) { v[0] = p[0]; }
+    __device__ __forceinline__ void load_int(const int* p) { v[0] = __int_as_float(p[0]); }
+};
+template <> struct Vec<4> {
+    float v[4];
+    __device__ __forceinline__ void load(const float* p)
+    {
+        const float4 q = *reinterpret_cast<const float4*>(p);
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    }
+    __device__ __forceinline__ void load_int(const int* p)
+    {
+        const int4 q = *reinterpret_cast<const int4*>(p);
+        v[0] = __int_as_float(q.x); v[1] = __int_as_float(q.y);
+        v[2] = __int_as_float(q.z); v[3] = __int_as_float(q.w);
+    }
+};
+
 // per pixel: add this wave's samples in sample order (Kahan for radiance)
-__global__ void __launch_bounds__(kThreads) k_accumulate(WaveParams w, float* acc, int k)
+template <int V>
+__global__ void __launch_bounds__(kThreads) k_accumulate(WaveParams w, float* acc, int kk)
 {
     PathSoA& P = w.P;
-    int64_t wh = w.wh;
+    const int64_t wh = w.wh;
     for (int64_t pix = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; pix < wh;
          pix += (int64_t)gridDim.x * blockDim.x) {
         float* a = acc + 13 * pix;
         float s0 = a[0], s1 = a[1], s2 = a[2], c0 = a[3], c1 = a[4], c2 = a[5];
         float ax = a[6], ay = a[7], az = a[8], nx = a[9], ny = a[10], nz = a[11], ds = a[12];
-        for (int s = 0; s < k; ++s) {
-            int64_t p = s * wh + pix;
-            float y, t;
-            y = P.Lx[p] - c0; t = s0 + y; c0 = (t - s0) - y; s0 = t;
-            y = P.Ly[p] - c1; t = s1 + y; c1 = (t - s1) - y; s1 = t;
-            y = P.Lz[p] - c2; t = s2 + y; c2 = (t - s2) - y; s2 = t;
-            ax = ax + P.ax[p]; ay = ay + P.ay[p]; az = az + P.az[p];
-            nx = nx + P.nx[p]; ny = ny + P.ny[p]; nz = nz + P.nz[p];
-            ds = ds + P.dep[p];
+        for (int sb = 0; sb < kk; sb += V) {
+            const int64_t p = pix * kk + sb;
+            Vec<V> Lx, Ly, Lz, Ax, Ay, Az, Nx, Ny, Nz, D;
+            Lx.load(P.Lx + p); Ly.load(P.Ly + p); Lz.load(P.Lz + p);
+            Ax.load(P.ax + p); Ay.load(P.ay + p); Az.load(P.az + p);
+            Nx.load(P.nx + p); Ny.load(P.ny + p); Nz.load(P.nz + p);
+            D.load(P.dep + p);
+#pragma unroll
+            for (int j = 0; j < V; ++j) {
+                float y, t;
+                y = Lx.v[j] - c0; t = s0 + y; c0 = (t - s0) - y; s0 = t;
+                y = Ly.v[j] - c1; t = s1 + y; c1 = (t - s1) - y; s1 = t;
+                y = Lz.v[j] - c2; t = s2 + y; c2 = (t - s2) - y; s2 = t;
+                ax = ax + Ax.v[j]; ay = ay + Ay.v[j]; az = az + Az.v[j];
+                nx = nx + Nx.v[j]; ny = ny + Ny.v[j]; nz = nz + Nz.v[j];
+                ds = ds + D.v[j];
+            }
         }
         a[0] = s0; a[1] = s1; a[2] = s2; a[3] = c0; a[4] = c1; a[5] = c2;
         a[6] = ax; a[7] = ay; a[8] = az; a[9] = nx; a[10] = ny; a[11] = nz; a[12] = ds;
@@ -693,24 +729,31 @@ __global__ void __launch_bounds__(kThreads) k_accumulate(WaveParams w, float* ac
 // extra layers, only when requested: per pixel the diffuse and specular sums
 // (each sample's radiance to the layer of its first-hit lobe) and the sum of
 // squares for the variance, plain FP32 sums in sample order
-__global__ void __launch_bounds__(kThreads) k_accumulate_layers(WaveParams w, float* acc2, int k)
+template <int V>
+__global__ void __launch_bounds__(kThreads) k_accumulate_layers(WaveParams w, float* acc2, int kk)
 {
     PathSoA& P = w.P;
-    int64_t wh = w.wh;
+    const int64_t wh = w.wh;
     for (int64_t pix = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; pix < wh;
          pix += (int64_t)gridDim.x * blockDim.x) {
         float* e = acc2 + 9 * pix;
         float d0 = e[0], d1 = e[1], d2 = e[2], p0 = e[3], p1 = e[4], p2 = e[5];
         float q0 = e[6], q1 = e[7], q2 = e[8];
-        for (int s = 0; s < k; ++s) {
-            int64_t p = s * wh + pix;
-            const float lx = P.Lx[p], ly = P.Ly[p], lz = P.Lz[p];
-            const int lobe = P.lobe[p];
-            d0 = d0 + (lobe == 1 ? lx : 0.0f); d1 = d1 + (lobe == 1 ? ly : 0.0f);
-            d2 = d2 + (lobe == 1 ? lz : 0.0f);
-            p0 = p0 + (lobe == 2 ? lx : 0.0f); p1 = p1 + (lobe == 2 ? ly : 0.0f);
-            p2 = p2 + (lobe == 2 ? lz : 0.0f);
-            q0 = q0 + lx * lx; q1 = q1 + ly * ly; q2 = q2 + lz * lz;
+        for (int sb = 0; sb < kk; sb += V) {
+            const int64_t p = pix * kk + sb;
+            Vec<V> Lx, Ly, Lz, Lo;
+            Lx.load(P.Lx + p); Ly.load(P.Ly + p); Lz.load(P.Lz + p);
+            Lo.load_int(P.lobe + p);
+#pragma unroll
+            for (int j = 0; j < V; ++j) {
+                const float lx = Lx.v[j], ly = Ly.v[j], lz = Lz.v[j];
+                const int lobe = __float_as_int(Lo.v[j]);
+                d0 = d0 + (lobe == 1 ? lx : 0.0f); d1 = d1 + (lobe == 1 ? ly : 0.0f);
+                d2 = d2 + (lobe == 1 ? lz : 0.0f);
+                p0 = p0 + (lobe == 2 ? lx : 0.0f); p1 = p1 + (lobe == 2 ? ly : 0.0f);
+                p2 = p2 + (lobe == 2 ? lz : 0.0f);
+                q0 = q0 + lx * lx; q1 = q1 + ly * ly; q2 = q2 + lz * lz;
+            }
         }
         e[0] = d0; e[1] = d1; e[2] = d2; e[3] = p0; e[4] = p1; e[5] = p2;
         e[6] = q0; e[7] = q1; e[8] = q2;
@@ -894,6 +937,7 @@ static mrs_status render_impl(mrs_scene S, Buf& arena, int64_t wave_paths, int32
     for (int s0 = 0; s0 < spp; s0 += (int)k) {
         int kk = (int)((spp - s0) < k ? (spp - s0) : k);
         w.s0 = s0;
+        w.kk = kk;
         w.n_paths = (int)(kk * wh);
         MRS_CHECK(cudaMemsetAsync(cnt, 0, 4 * 2 * 64, st));
         int g = grid_for(w.n_paths);
@@ -920,10 +964,17 @@ static mrs_status render_impl(mrs_scene S, Buf& arena, int64_t wave_paths, int32
             else MRS_TIMED(PK_TAIL, st, k_tail<false><<<gt, kThreads, 0, st>>>(w, b_tail));
             MRS_LAUNCHED(1);
         }
-        MRS_TIMED(PK_ACCUM, st, k_accumulate<<<grid_for(wh), kThreads, 0, st>>>(w, acc, kk));
+        // 16-byte sample loads when every pixel's run of kk samples starts on
+        // a 16-byte boundary (the arrays are 256-byte aligned)
+        const bool v4 = kk % 4 == 0;
+        if (v4) MRS_TIMED(PK_ACCUM, st, k_accumulate<4><<<grid_for(wh), kThreads, 0, st>>>(w, acc, kk));
+        else MRS_TIMED(PK_ACCUM, st, k_accumulate<1><<<grid_for(wh), kThreads, 0, st>>>(w, acc, kk));
         MRS_LAUNCHED(1);
         if (acc2) {
-            MRS_TIMED(PK_ACCUM, st, k_accumulate_layers<<<grid_for(wh), kThreads, 0, st>>>(w, acc2, kk));
+            if (v4)
+                MRS_TIMED(PK_ACCUM, st, k_accumulate_layers<4><<<grid_for(wh), kThreads, 0, st>>>(w, acc2, kk));
+            else
+                MRS_TIMED(PK_ACCUM, st, k_accumulate_layers<1><<<grid_for(wh), kThreads, 0, st>>>(w, acc2, kk));
             MRS_LAUNCHED(1);
         }
         if (counts || shadow_counts) {
