@@ -601,9 +601,11 @@ __global__ void __launch_bounds__(kThreads, 8) k_shadow(WaveParams w, int b)
 // wavefront kernels (trace, shade, shadow; a path's state lives in P), so
 // its radiance is bit-identical; the per-bounce counts are the same numbers,
 // gathered per block in shared memory.  cnt[kWorkSlot] hands out the paths.
+// 32 registers and 8 blocks per SM, as the traversal kernels: with 64
+// registers (4 blocks) the tail ran 2-7% slower despite no spills.
 constexpr int kWorkSlot = 63;
 template <bool kCount>
-__global__ void __launch_bounds__(kThreads) k_tail(WaveParams w, int b0)
+__global__ void __launch_bounds__(kThreads, 8) k_tail(WaveParams w, int b0)
 {
     __shared__ uint32_t s_cnt[64], s_scnt[64];
     for (int j = threadIdx.x; j < 64; j += blockDim.x) { s_cnt[j] = 0u; s_scnt[j] = 0u; }
