@@ -259,7 +259,7 @@ mrs_status mrs_scene_set_wave(mrs_scene scene, int64_t max_paths_per_wave);
  * path runs in a single persistent launch that takes each path left in the
  * queue of bounce `bounce` to its end.  The result is bit-identical either
  * way (same per-path operations, same counts); only the launch structure
- * changes.  -1 (default): bounce 2; any value > max_depth: no tail.  Range
+ * changes.  -1 (default): bounce 1; any value > max_depth: no tail.  Range
  * [-1, 64], else MRS_ERR_ARG. */
 mrs_status mrs_scene_set_tail(mrs_scene scene, int32_t bounce);
 mrs_status mrs_ctx_set_tail(mrs_ctx ctx, int32_t bounce);

@@ -125,7 +125,7 @@ struct mrs_scene_s {
     mrs::Buf export_tmp;         // full-scene LBVH built on export
     mrs::Buf arena;              // render path state
     int64_t wave_paths = int64_t(1) << 24;
-    int32_t tail_bounce = -1;    // first bounce of the tail kernel (-1: bounce 2)
+    int32_t tail_bounce = -1;    // first bounce of the tail kernel (-1: bounce 1)
 };
 
 // Render context: a path-state arena of its own, so that several renders of

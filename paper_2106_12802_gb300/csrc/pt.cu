@@ -945,11 +945,11 @@ static mrs_status render_impl(mrs_scene S, Buf& arena, int64_t wave_paths, int32
         int g = grid_for(w.n_paths);
         MRS_TIMED(PK_RAYGEN, st, k_raygen<<<g, kThreads, 0, st>>>(w));
         MRS_LAUNCHED(1);
-        // first bounce of the tail kernel: by default bounce 2 (on the 200k-
+        // first bounce of the tail kernel: by default bounce 1 (on the 200k-
         // triangle scene at 1024^2, 4 and 16 spp, with and without roulette,
-        // and 256^2 at 64 spp, tails from bounce 1-3 beat the wavefront by
-        // 8-25%, from bounce 2 the most or within 1% of it)
-        const int b_tail = tail >= 0 ? tail : 2;
+        // and 256^2 at 64 spp, tails from bounce 0-3 beat the wavefront alone;
+        // from bounce 1 by 3-5% more than from bounce 2, the next best)
+        const int b_tail = tail >= 0 ? tail : 1;
         for (int b = 0; b <= max_depth && b < b_tail; ++b) {
             if (stats) MRS_TIMED(PK_TRACE, st, k_trace<true><<<g, kThreads, 0, st>>>(w, b));
             else MRS_TIMED(PK_TRACE, st, k_trace<false><<<g, kThreads, 0, st>>>(w, b));
