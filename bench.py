@@ -113,9 +113,10 @@ class ClockSampler:
                 "samples": len(self.rows)}
 
 
-def _traffic(kernel, src):
-    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if the
-    kernel source is unchanged since the capture (else None)."""
+def _traffic(kernel, src, key="dram_bytes_per_launch"):
+    """Per-launch DRAM bytes (or another per-launch counter, `key`) of `kernel`
+    from the committed ncu summary, if the kernel source is unchanged since the
+    capture (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -125,7 +126,7 @@ def _traffic(kernel, src):
         return None
     with open(os.path.join(ROOT, "paper_2106_12802_gb300", "csrc", src), "rb") as f:
         sha = hashlib.sha256(f.read()).hexdigest()[:16]
-    return d["dram_bytes_per_launch"] if d.get("src_sha256_16") == sha else None
+    return d.get(key) if d.get("src_sha256_16") == sha else None
 
 
 # ----------------------------------------------------------------------------
@@ -695,13 +696,26 @@ def run_gpu(args, rank, world):
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         peak = sms * 128 * peaks["sm_max_mhz"] * 1e6 / 1e12
         ach = ops / (kms * 1e-3) / 1e12
-        roofline = {"kernel": f"k_{dom} (BVH traversal)", "bound": "alu", "achieved": ach,
+        # L2 side of the same kernel (the LBVH is L2-resident): ncu's L2 bytes
+        # per launch over the live launch time, against the measured L2 read rate
+        l2b = _traffic(f"k_{dom}", "pt.cu", "lts_bytes_per_launch")
+        per_frame = prof[dom][1] / prof_steps
+        l2_gbs = l2b * per_frame / (kms * 1e-3) / 1e9 if l2b else None
+        l2_peak = mrs.l2_read_gbs() if rank == 0 else None
+        label = {"trace": "k_trace (closest-hit traversal, bounce 0)",
+                 "shadow": "k_shadow (shadow-ray traversal, bounce 0)",
+                 "tail": "k_tail (traversal, shading and shadow rays of bounces >= 1)"}[dom]
+        roofline = {"kernel": label, "bound": "alu", "achieved": ach,
                     "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                     "traffic": _traffic(f"k_{dom}", "pt.cu"),
                     "peak_source": f"{sms} SMs x 128 FP32 lanes x {peaks['sm_max_mhz']} MHz "
                                    "(non-FMA ops; the kernel is built with --fmad=false)",
                     "ops_per_frame": ops, "node_visits_per_frame": visits,
-                    "tri_tests_per_frame": tests}
+                    "tri_tests_per_frame": tests,
+                    "l2": {"achieved_gbs": l2_gbs, "peak_gbs": l2_peak,
+                           "frac": l2_gbs / l2_peak if l2_gbs and l2_peak else None,
+                           "peak_source": "measured here: mrs_l2_read_probe, 64 MB L2-resident, "
+                                          "L2-only loads"}}
 
     if rank == 0:
         cpu = None

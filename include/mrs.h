@@ -185,6 +185,16 @@ mrs_status mrs_render_stats(mrs_scene scene, int32_t W, int32_t H, int32_t spp, 
 mrs_status mrs_profile_enable(int32_t on);
 mrs_status mrs_profile_read(int32_t kernel, double* total_ms, int64_t* launches);
 
+/* L2 read-bandwidth probe (measurement only, no paper counterpart): reads the
+ * `bytes` bytes of device buffer buf (16-byte aligned, bytes a positive
+ * multiple of 16) `reps` times (1 .. 1000) with L2-only loads, 4 blocks of 256
+ * threads per SM; sink is a device float[1] that is written only if the sum
+ * of the data is -1 (never for finite non-negative data).  Timed by the
+ * caller with events on `stream`: with buf smaller than the L2, bytes * reps
+ * / time is the L2 read bandwidth that traversal L2 traffic is compared with. */
+mrs_status mrs_l2_read_probe(const void* buf, int64_t bytes, int32_t reps, float* sink,
+                             void* stream);
+
 /* Failure-detection self-test (no paper counterpart): launches a kernel whose
  * bounded device-side wait (the kind every tensor-core kernel uses on its
  * mbarriers) waits for an event that never happens.  The wait must give up

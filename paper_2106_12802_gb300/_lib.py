@@ -68,6 +68,7 @@ SIGS = {
     "mrs_rdn_fuse": [P, P, P, P, P, P, I32, I32, I32, I32, P, P],
     "mrs_rdn_check": [P],
     "mrs_selftest_wait_timeout": [I32, P],
+    "mrs_l2_read_probe": [P, I64, I32, P, P],
     "mrs_status_string": [I32],
     "mrs_last_error": [],
     "mrs_kernel_launches": [],
