@@ -551,20 +551,23 @@ def run_gpu(args, rank, world):
     ctx_lr, ctx_hr = mrs.RenderContext(), mrs.RenderContext()
     s_lr, s_hr = torch.cuda.Stream(), torch.cuda.Stream()
 
-    def renders(seed):
-        s_lr.wait_stream(stream)
-        s_hr.wait_stream(stream)
-        with torch.cuda.stream(s_hr):
+    def renders(seed, serial=False):
+        # serial: both renders one after the other on the main stream (the
+        # profiled frames, so that each kernel's events time that kernel alone)
+        s_a, s_b = (stream, stream) if serial else (s_hr, s_lr)
+        s_a.wait_stream(stream)
+        s_b.wait_stream(stream)
+        with torch.cuda.stream(s_a):
             mrs.render(scene, HR, HR, SPP_HR, DEPTH, RR, seed + 1, ctx=ctx_hr,
                        out={"radiance": hrls[0], "albedo": alb[0], "normal": nrm[0], "depth": dep[0]})
-        with torch.cuda.stream(s_lr):
+        with torch.cuda.stream(s_b):
             mrs.render(scene, LR, LR, SPP_LR, DEPTH, RR, seed, ctx=ctx_lr, out={"radiance": lrhs[0]})
-        stream.wait_stream(s_lr)
-        stream.wait_stream(s_hr)
+        stream.wait_stream(s_a)
+        stream.wait_stream(s_b)
 
-    def frame(seed):
+    def frame(seed, serial=False):
         scene.rebuild()
-        renders(seed)
+        renders(seed, serial)
         net.fuse(lrhs, hrls, alb, nrm, S, precision="bf16", out=fused)
         _, used, D = mrs.gate(fused, lrhs, None, S, 0.01, out=out)
         gate_info.update(used_plain=used, D=D)
@@ -590,13 +593,15 @@ def run_gpu(args, rank, world):
     launches = (mrs.kernel_launches() - launches0) // max(args.steps, 1)
     step_ms = [a.elapsed_time(b) for a, b in ev]
     # per-kernel-family split from extra frames with CUDA events around every
-    # launch (outside the timed region: the events serialise the launches)
+    # launch (outside the timed region: the events serialise the launches),
+    # the two renders one after the other so that no kernel's events also
+    # cover the other render's kernels
     prof_steps = max(3, args.steps // 4)
     mrs.profile_read()
     mrs.profile_enable(True)
     for k in range(prof_steps):
         flush.zero_()
-        frame(500 + k)
+        frame(500 + k, serial=True)
     torch.cuda.synchronize()
     mrs.profile_enable(False)
     prof = mrs.profile_read()
@@ -735,8 +740,9 @@ def run_gpu(args, rank, world):
             "gpu_launches": int(launches),
             "stage_ms_per_frame": {k: round(v, 4) for k, v in family_ms.items()},
             "stage_note": f"per-kernel-family CUDA-event totals over {prof_steps} extra frames "
-                          "after the timed region (events around every launch); the two "
-                          "renders overlap, so render stages can sum to more than the frame",
+                          "after the timed region (events around every launch, the two renders "
+                          "one after the other on one stream): the families sum to about a "
+                          "serialised frame, more than the timed frame, whose renders overlap",
             "conv_tflops": conv_flop / (conv_ms * 1e-3) / 1e12 if conv_ms else None,
             "conv_roofline": conv_roof,
             "gate": gate_info, "training": training, **extra,
