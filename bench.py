@@ -508,6 +508,72 @@ def paper_network(mrs, flush, s=S, reps=10):
     return res
 
 
+def fp8_gemm_tflops(n=8192, reps=10):
+    """Dense FP8-E4M3 GEMM throughput of the vendor library (torch._scaled_mm,
+    n^3, best of `reps`): the denominator for the FP8 fusion, which the peaks
+    file does not measure.  None (with the reason) where it is unavailable."""
+    import torch
+    try:
+        a = torch.randn(n, n, device="cuda").to(torch.float8_e4m3fn)
+        b = torch.randn(n, n, device="cuda").to(torch.float8_e4m3fn).t()
+        one = torch.ones((), device="cuda")
+        torch._scaled_mm(a, b, one, one, out_dtype=torch.bfloat16)
+        torch.cuda.synchronize()
+        best = None
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch._scaled_mm(a, b, one, one, out_dtype=torch.bfloat16)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        return 2.0 * n ** 3 / (best * 1e-3) / 1e12, "torch._scaled_mm e4m3 %d^3, best of %d" % (n, reps)
+    except Exception as e:  # noqa: BLE001
+        return None, "unavailable: %s" % str(e).splitlines()[0][:120]
+
+
+def fusion_precisions(mrs, net, flush, reps=10):
+    """Device time of the x4 fusion network alone at 1024^2 (L2 flushed before
+    every rep) in BF16, FP8-E4M3 and FP32, with the tensor-core rates against
+    the measured BF16 and FP8 GEMM peaks, and the FP8 / BF16 output agreement."""
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(3)
+    lr = torch.rand((1, LR, LR, 3), device="cuda", generator=g)
+    hr = [torch.rand((1, HR, HR, 3), device="cuda", generator=g) for _ in range(3)]
+    outs = {}
+    res = {"hr": [HR, HR], "scale": S, "l2": "flushed before every rep (512 MiB write)"}
+    flop = CONV_FLOP_PER_PX * HR * HR
+    peaks = _peaks()
+    fp8_peak, fp8_src = fp8_gemm_tflops()
+    for prec in ("bf16", "fp8", "fp32"):
+        out = torch.empty((1, HR, HR, 3), device="cuda")
+        net.fuse(lr, *hr, S, precision=prec, out=out)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps if prec != "fp32" else 2):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            net.fuse(lr, *hr, S, precision=prec, out=out)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = float(np.median(ts))
+        tf = flop / (ms * 1e-3) / 1e12
+        res[prec] = {"ms": ms, "tflops": tf}
+        outs[prec] = out
+    res["bf16"]["tensor_frac_of_measured_sustained"] = res["bf16"]["tflops"] / peaks["bf16_tflops_sustained"]
+    res["fp8"]["tensor_frac_of_fp8_gemm"] = res["fp8"]["tflops"] / fp8_peak if fp8_peak else None
+    res["fp8_gemm_tflops"] = fp8_peak
+    res["fp8_gemm_source"] = fp8_src
+    res["fp8_vs_bf16_psnr_db"] = mrs.image_metrics(outs["fp8"][0].contiguous(),
+                                                   outs["bf16"][0].contiguous())[0]
+    res["bf16_vs_fp32_psnr_db"] = mrs.image_metrics(outs["bf16"][0].contiguous(),
+                                                    outs["fp32"][0].contiguous())[0]
+    return res
+
+
 # ----------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------
@@ -643,6 +709,8 @@ def run_gpu(args, rank, world):
         extra["batched_serving"] = batched_serving(mrs, params)
     if rank == 0 and not args.no_paper_network:
         extra["paper_network_x4"] = paper_network(mrs, flush)
+    if rank == 0 and not args.quick:
+        extra["fusion_precisions_1024"] = fusion_precisions(mrs, net, flush)
     if rank == 0 and not args.quick and not args.no_spp_study:
         extra["spp_study_x4"] = spp_study(mrs)
     if rank == 0 and not args.quick:
