@@ -631,12 +631,16 @@ def run_gpu(args, rank, world):
         stream.wait_stream(s_a)
         stream.wait_stream(s_b)
 
+    # the gate's decision stays on the device (no host synchronisation inside
+    # a frame); it is read after the frames
+    used_d = torch.zeros(2, dtype=torch.int32, device=dev)
+    D_d = torch.zeros(1, dtype=torch.float64, device=dev)
+
     def frame(seed, serial=False):
         scene.rebuild()
         renders(seed, serial)
         net.fuse(lrhs, hrls, alb, nrm, S, precision="bf16", out=fused)
-        _, used, D = mrs.gate(fused, lrhs, None, S, 0.01, out=out)
-        gate_info.update(used_plain=used, D=D)
+        mrs.gate_async(fused, lrhs, None, S, 0.01, out=out, used=used_d, D=D_d)
 
     for k in range(args.warmup):
         frame(1000 + k)
@@ -658,6 +662,7 @@ def run_gpu(args, rank, world):
         torch.cuda.synchronize()
     launches = (mrs.kernel_launches() - launches0) // max(args.steps, 1)
     step_ms = [a.elapsed_time(b) for a, b in ev]
+    gate_info.update(used_plain=bool(used_d[0].item()), D=float(D_d.item()))
     # per-kernel-family split from extra frames with CUDA events around every
     # launch (outside the timed region: the events serialise the launches),
     # the two renders one after the other so that no kernel's events also
@@ -682,13 +687,19 @@ def run_gpu(args, rank, world):
     # ---- end to end through the public API with host buffers -----------------
     Vh = torch.from_numpy(np.ascontiguousarray(desc["V"], np.float32)).pin_memory()
     out_h = torch.empty((1, HR, HR, 3), dtype=torch.float32).pin_memory()
+    used_h = torch.empty(2, dtype=torch.int32).pin_memory()
+    D_h = torch.empty(1, dtype=torch.float64).pin_memory()
 
     def frame_e2e(seed):
+        # geometry in from pinned host memory; image and gate decision back,
+        # one synchronisation per frame
         scene.update_vertices(Vh)
         renders(seed)
         net.fuse(lrhs, hrls, alb, nrm, S, precision="bf16", out=fused)
-        mrs.gate(fused, lrhs, None, S, 0.01, out=out)
+        mrs.gate_async(fused, lrhs, None, S, 0.01, out=out, used=used_d, D=D_d)
         out_h.copy_(out, non_blocking=True)
+        used_h.copy_(used_d, non_blocking=True)
+        D_h.copy_(D_d, non_blocking=True)
         torch.cuda.synchronize()
 
     frame_e2e(0)
@@ -699,7 +710,19 @@ def run_gpu(args, rank, world):
         frame_e2e(k)
     e2e_ms = 1e3 * (time.perf_counter() - t0) / e2e_steps
     h2d = Vh.numel() * 4
-    d2h = out_h.numel() * 4
+    d2h = out_h.numel() * 4 + used_h.numel() * 4 + D_h.numel() * 8
+    # the two copies alone (device-timed, same pinned buffers), to split the
+    # end-to-end time into copies and the rest
+    v_dev = torch.empty(Vh.shape, dtype=torch.float32, device=dev)
+    c0, c1, c2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    c0.record(stream)
+    v_dev.copy_(Vh, non_blocking=True)
+    c1.record(stream)
+    out_h.copy_(out, non_blocking=True)
+    c2.record(stream)
+    torch.cuda.synchronize()
+    copy_ms = {"h2d_ms": c0.elapsed_time(c1), "d2h_ms": c1.elapsed_time(c2)}
+    del v_dev
 
     # ---- context measurements (outside the timed region) --------------------
     extra = {}
@@ -803,7 +826,7 @@ def run_gpu(args, rank, world):
             "data": "synthetic", "config": WORKLOAD,
             "parallelism": "replicas" if world > 1 else "single-gpu",
             "e2e": {"value": e2e_ms, "unit": "ms/frame", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h},
+                    "d2h_bytes_per_step": d2h, **copy_ms},
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clk.summary(),
             "gpu_launches": int(launches),
             "stage_ms_per_frame": {k: round(v, 4) for k, v in family_ms.items()},
