@@ -442,49 +442,114 @@ mrs_status build_lbvh(mrs_scene_s* S, cudaStream_t st)
 }
 
 // Large triangles: AABB extent >= 1/4 of the centroid bounds' largest extent,
-// at most kMaxBig of them (else none); computed on the host from the vertices.
+// at most kMaxBig of them (else none).  They are tested before the tree by
+// every ray; the others go into the LBVH.  Classified on the device: centroid
+// bounds of all triangles, a flag and a per-block count, one scan, and a
+// stable scatter (both index lists in increasing triangle order); only the two
+// counts come back to the host, which sizes the build's launches with them.
 constexpr int kMaxBig = 64;
-void classify(const float* V, int n, std::vector<int>& small, std::vector<int>& big)
+
+// largest extent of the centroid bounds from the block partials (warp 0)
+__device__ float bounds_extent(const float* __restrict__ part, int nparts)
 {
-    small.clear();
-    big.clear();
-    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (int i = 0; i < n; ++i)
-        for (int a = 0; a < 3; ++a) {
-            const float* p = V + (size_t)i * 9;
-            float c = ((p[a] + p[3 + a]) + p[6 + a]) * (1.0f / 3.0f);
-            lo[a] = fminf(lo[a], c);
-            hi[a] = fmaxf(hi[a], c);
+    __shared__ float s_L;
+    if (threadIdx.x < 32) {
+        float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (int b = threadIdx.x; b < nparts; b += 32)
+            for (int a = 0; a < 3; ++a) {
+                lo[a] = fminf(lo[a], part[6 * b + a]);
+                hi[a] = fmaxf(hi[a], part[6 * b + 3 + a]);
+            }
+        for (int off = 16; off > 0; off >>= 1)
+            for (int a = 0; a < 3; ++a) {
+                lo[a] = fminf(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], off));
+                hi[a] = fmaxf(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], off));
+            }
+        if (threadIdx.x == 0) {
+            float L = 0.0f;
+            for (int a = 0; a < 3; ++a) L = fmaxf(L, hi[a] - lo[a]);
+            s_L = L;
         }
-    float L = 0.0f;
-    for (int a = 0; a < 3; ++a) L = fmaxf(L, hi[a] - lo[a]);
-    for (int i = 0; i < n; ++i) {
+    }
+    __syncthreads();
+    return s_L;
+}
+
+// flag[i] = triangle i is large; cnt[block] = large triangles of the block
+__global__ void k_class_count(const float* __restrict__ V, int n, const float* __restrict__ part,
+                              int nparts, uint8_t* __restrict__ flag, uint32_t* __restrict__ cnt)
+{
+    const float L = bounds_extent(part, nparts);
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    bool big = false;
+    if (i < n) {
         const float* p = V + (size_t)i * 9;
         float e = 0.0f;
         for (int a = 0; a < 3; ++a)
             e = fmaxf(e, fmaxf(fmaxf(p[a], p[3 + a]), p[6 + a]) - fminf(fminf(p[a], p[3 + a]), p[6 + a]));
-        (L > 0.0f && e >= 0.25f * L ? big : small).push_back(i);
+        big = L > 0.0f && e >= 0.25f * L;
+        flag[i] = big ? 1 : 0;
     }
-    if ((int)big.size() > kMaxBig) {
-        small.resize(n);
-        for (int i = 0; i < n; ++i) small[i] = i;
-        big.clear();
+    const int c = __syncthreads_count(big);
+    if (threadIdx.x == 0) cnt[blockIdx.x] = (uint32_t)c;
+}
+
+// small_idx / big_idx in increasing triangle order (off: exclusive scan of the
+// block counts, off[nblk] = total); more than kMaxBig large ones: none large.
+// counts[0] = small, counts[1] = large
+__global__ void k_class_scatter(const uint8_t* __restrict__ flag, int n, const uint32_t* __restrict__ off,
+                                int nblk, int* __restrict__ small_idx, int* __restrict__ big_idx,
+                                int* __restrict__ counts)
+{
+    __shared__ uint32_t wsum[kBlock / 32];
+    const uint32_t total = off[nblk];
+    const bool none = total > (uint32_t)kMaxBig;
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    const bool big = !none && i < n && flag[i];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned m = __ballot_sync(0xffffffffu, big);
+    if (lane == 0) wsum[warp] = (uint32_t)__popc(m);
+    __syncthreads();
+    uint32_t before = off[blockIdx.x] + (uint32_t)__popc(m & ((1u << lane) - 1u));
+    for (int w = 0; w < warp; ++w) before += wsum[w];
+    if (none) before = 0;
+    if (i < n) {
+        if (big) big_idx[before] = i;
+        else small_idx[i - (int)before] = i;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        counts[0] = none ? n : n - (int)total;
+        counts[1] = none ? 0 : (int)total;
     }
 }
 
-mrs_status upload_classes(mrs_scene_s* S, const float* V, cudaStream_t st)
+mrs_status classify_on_device(mrs_scene_s* S, cudaStream_t st)
 {
-    std::vector<int> small, big;
-    classify(V, S->n, small, big);
-    S->ns = (int)small.size();
-    if (!small.empty())
-        MRS_CHECK(cudaMemcpyAsync(S->small_idx, small.data(), sizeof(int) * small.size(),
-                                  cudaMemcpyHostToDevice, st));
-    if (!big.empty())
-        MRS_CHECK(cudaMemcpyAsync(S->big_idx, big.data(), sizeof(int) * big.size(),
-                                  cudaMemcpyHostToDevice, st));
-    // the vectors must outlive the copies
+    const int n = S->n;
+    const int nparts = 2 * sm_count();
+    const int nblk = (n + kBlock - 1) / kBlock;
+    size_t need = sizeof(float) * 6 * nparts + sizeof(uint32_t) * ((size_t)nblk + 1) + 16 + (size_t)n + 256;
+    mrs_status s = S->class_tmp.ensure(need);
+    if (s != MRS_OK) return s;
+    char* p = S->class_tmp.as<char>();
+    float* part = (float*)p; p += sizeof(float) * 6 * nparts;
+    uint32_t* cnt = (uint32_t*)p; p += sizeof(uint32_t) * ((size_t)nblk + 1);
+    p = (char*)(((uintptr_t)p + 15) & ~(uintptr_t)15);
+    int* counts = (int*)p; p += 16;
+    uint8_t* flag = (uint8_t*)p;
+    if (!S->class_host) MRS_CHECK(cudaMallocHost((void**)&S->class_host, 2 * sizeof(int)));
+    k_bounds_partial<<<nparts, kBlock, 0, st>>>(S->V, n, part);
+    MRS_LAUNCHED(1);
+    MRS_CHECK(cudaMemsetAsync(cnt + nblk, 0, sizeof(uint32_t), st));
+    k_class_count<<<nblk, kBlock, 0, st>>>(S->V, n, part, nparts, flag, cnt);
+    MRS_LAUNCHED(1);
+    k_sort_scan<<<1, 1024, 0, st>>>(cnt, nblk + 1);
+    MRS_LAUNCHED(1);
+    k_class_scatter<<<nblk, kBlock, 0, st>>>(flag, n, cnt, nblk, S->small_idx, S->big_idx, counts);
+    MRS_LAUNCHED(1);
+    MRS_CHECK(cudaMemcpyAsync(S->class_host, counts, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     MRS_CHECK(cudaStreamSynchronize(st));
+    S->ns = S->class_host[0];
     return MRS_OK;
 }
 
@@ -497,7 +562,9 @@ void free_scene(mrs_scene_s* S)
         if (q) cudaFree(q);
     S->sort_tmp.release();
     S->export_tmp.release();
+    S->class_tmp.release();
     S->arena.release();
+    if (S->class_host) cudaFreeHost(S->class_host);
     delete S;
 }
 
@@ -720,7 +787,7 @@ extern "C" mrs_status mrs_build_scene(const float* V, int32_t n, const int32_t* 
         TRY(cuda_status(cudaMemcpyAsync(S->mats, mats, sizeof(float) * 8 * n_mats, cudaMemcpyHostToDevice, st), "copy mats"));
     if (n_lights > 0)
         TRY(cuda_status(cudaMemcpyAsync(S->lights, lights, sizeof(float) * 12 * n_lights, cudaMemcpyHostToDevice, st), "copy lights"));
-    if (n > 0) TRY(upload_classes(S, V, st));
+    if (n > 0) TRY(classify_on_device(S, st));
     TRY(build_lbvh(S, st));
     TRY(cuda_status(cudaStreamSynchronize(st), "build_scene sync"));
 #undef TRY
@@ -744,7 +811,7 @@ extern "C" mrs_status mrs_scene_update_vertices(mrs_scene S, const float* V, int
     cudaStream_t st = (cudaStream_t)stream;
     if (n > 0) {
         MRS_CHECK(cudaMemcpyAsync(S->V, V, sizeof(float) * 9 * (size_t)n, cudaMemcpyHostToDevice, st));
-        mrs_status s = upload_classes(S, V, st);
+        mrs_status s = classify_on_device(S, st);
         if (s != MRS_OK) return s;
     }
     return build_lbvh(S, st);

@@ -122,6 +122,8 @@ struct mrs_scene_s {
     float4* tris = nullptr;      // [n][3]: (v0, prim bits), (e1, 0), (e2, 0) in sorted order
     int2* tri_ml = nullptr;      // [n]: material, light in sorted order
     mrs::Buf sort_tmp;           // radix-sort scratch
+    mrs::Buf class_tmp;          // large / small classification scratch
+    int* class_host = nullptr;   // pinned [2]: small and large triangle counts
     mrs::Buf export_tmp;         // full-scene LBVH built on export
     mrs::Buf arena;              // render path state
     int64_t wave_paths = int64_t(1) << 24;
