@@ -485,8 +485,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) {
             bool ok = true;
             uint32_t it = 0, k = 0;
+            int s = 0;                                          // ring slot of row `it`
+            uint32_t ph = 0;                                    // its fill phase parity
             long long t0 = 0;                                   // CTA output-row counter at sub-piece start
             const uint32_t wbase = smem_u32(sW), abase = smem_u32(sA);
+            // descriptors differ only in their start-address field (address / 16,
+            // bits 0-13): each MMA's pair is a base pair plus a constant offset
+            const uint64_t adesc0 = sdesc(abase, ROWB), bdesc0 = sdesc(wbase, ROWB);
             for (long long f = f0; ok && f < f1;) {
                 int xb, n, y0, y1;
                 piece_rows(f, f1, XB, a.H, xb, n, y0, y1);
@@ -495,9 +500,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                   for (int j = 0; ok && j < kc; ++j, ++k) {
                     // weights of this pass (loaded once when kc == 1)
                     if ((kc > 1 || k == 0) && !mbar_wait(wbar, k & 1, a.err)) { ok = false; break; }
-                    for (int r = ys - 1; ok && r <= ye; ++r, ++it) {
+                    for (int r = ys - 1; ok && r <= ye; ++r, ++it, s = (s + 1 == stages ? 0 : s + 1),
+                                                        ph ^= (s == 0 ? 1u : 0u)) {
                         const int jlo = max(0, r + 2 - ye), jhi = min(2, r + 1 - ys);
-                        const int s = it % stages;
                         // output row of block jb: CTA counter t0 + (r + 1 - jb - ys)
                         const long long tlo = t0 + (r + 1 - jlo - ys);   // newest row (highest t)
                         if (jlo == 0 && j == 0) {
@@ -507,7 +512,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                             const uint32_t use = (uint32_t)(tlo / NS);
                             if (!mbar_wait(&sfree[(NS - sl) % NS], (use & 1) ^ 1, a.err)) { ok = false; break; }
                         }
-                        if (!mbar_wait(&full[s], (it / stages) & 1, a.err)) { ok = false; break; }
+                        if (!mbar_wait(&full[s], ph, a.err)) { ok = false; break; }
                         tc_fence_after();
                         const int nb = jhi - jlo + 1;
                         const int c0 = (int)((NS - (int)(tlo % NS)) % NS);   // slot of block jlo
@@ -522,13 +527,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                                                    ((OPER == TC_BF16 ? 1u : 0u) << 10) |
                                                    ((uint32_t)((nbp * NOUT) >> 3) << 17) |
                                                    ((uint32_t)(kFoldTile >> 4) << 24);
+                            const uint64_t arow = adesc0 + (uint64_t)((s * ASLOT) >> 4);
+                            const uint64_t brow0 = bdesc0 + (uint64_t)(((jlo + b0) * NOUT * ROWB) >> 4);
 #pragma unroll
                             for (int dx = 0; dx < 3; ++dx) {
-                                const uint32_t brow = (uint32_t)(dx * BROWS + (jlo + b0) * NOUT);
 #pragma unroll
                                 for (int kk = 0; kk < KSTEPS; ++kk) {
-                                    const uint64_t ad = sdesc(abase + s * ASLOT + dx * ROWB + kk * 32, ROWB);
-                                    const uint64_t bd = sdesc(wbase + brow * ROWB + kk * 32, ROWB);
+                                    const uint64_t ad = arow + (uint64_t)((dx * ROWB + kk * 32) >> 4);
+                                    const uint64_t bd = brow0 + (uint64_t)((dx * BROWS * ROWB + kk * 32) >> 4);
                                     if (OPER == TC_BF16) mma_f16(tmem + dcol, ad, bd, idesc, 1u);
                                     else mma_f8(tmem + dcol, ad, bd, idesc, 1u);
                                 }
