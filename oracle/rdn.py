@@ -1,5 +1,5 @@
 """Float64 oracle of the method's own fusion network (Sec. 4, "two-encoder-one-
-decoder" network of Fig. network): forward pass.
+decoder" network of Fig. network): forward and backward passes.
 
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 
@@ -34,13 +34,20 @@ Parameter layout (flat): for each conv in the order above (H_lrhs, H_hrls,
 fuse, then per RDG, per RDB, convs 1-4, then the D upsampling convs, H_Rec),
 the weight [Cout][k][k][Cin] followed by the bias [Cout].
 
+Backward (backward(), from forward_tape()): the same steps in reverse, for
+training the network with the losses of oracle/cnn.py.
+
 Pins (tests/test_oracle_rdn.py): deshuffle / shuffle equal torch's
 pixel_unshuffle / pixel_shuffle; the 1x1 conv equals brute-force loops; an
 identity-kernel network gives I_SR = (1 + 2^G) * nearest_up_s(I_LRHS) in
 closed form (pins the group and global skips and the shuffle order); scaled
 identity kernels in one RDB give a closed-form factor that a misordered
 concatenation would change; a fuse conv that selects one deshuffled channel
-reproduces that HR pixel of F0_HRLS.
+reproduces that HR pixel of F0_HRLS; forward_tape() equals forward(); the
+backward matches central finite differences of the float64 forward on a small
+network at every scale (weights, biases of every layer kind, and the extra
+layers' input), and for a linear output functional every gradient entry of
+the last layer equals its closed form.
 """
 from __future__ import annotations
 
@@ -174,6 +181,132 @@ def forward(params, lrhs, hrls, albedo, normal, s, extra=None, keep=False):
         acts[f"U_{d + 1}"] = U
     y = cnn.conv3x3(U, *L[i])
     return (y, acts) if keep else y
+
+
+def conv1x1_backward(x, w, dout):
+    """Gradients of conv1x1 w.r.t. input, weight [Cout][1][1][Cin] and bias."""
+    x = np.asarray(x, np.float64)
+    dw = np.einsum("nyxo,nyxc->oc", dout, x)[:, None, None, :]
+    return dout @ w[:, 0, 0, :], dw, dout.sum(axis=(0, 1, 2))
+
+
+def forward_tape(params, lrhs, hrls, albedo, normal, s, extra=None):
+    """forward() that also records every conv's input and pre-activation, in
+    forward order, for backward(): returns (I_SR, tape)."""
+    c_hr = C_HR_EXTRA if extra is not None else C_HR
+    L = unpack(params, s, c_hr)
+    D = depth(s)
+    tape = {"s": s, "c_hr": c_hr}
+    x_lr = np.asarray(lrhs, np.float64)
+    z = cnn.conv3x3(x_lr, *L[0])
+    tape["lr"] = (x_lr, z)
+    F_lr = relu(z)
+    x_hr = hr_input(hrls, albedo, normal, extra)
+    z = cnn.conv3x3(x_hr, *L[1])
+    tape["hr"] = (x_hr, z)
+    F_h = relu(z)
+    for _ in range(D):
+        F_h = deshuffle(F_h)
+    x_f = np.concatenate([F_lr, F_h], axis=-1)
+    z = conv1x1(x_f, *L[2])
+    tape["fuse"] = (x_f, z)
+    F0 = relu(z)
+    F = F0
+    i = 3
+    blocks = []
+    for g in range(N_RDG):
+        F_prev = F
+        for b in range(N_RDB):
+            feats = [F]
+            convs = []
+            for c in range(N_CONV):
+                x_c = np.concatenate(feats, axis=-1)
+                z_c = cnn.conv3x3(x_c, *L[i + c])
+                convs.append((x_c, z_c))
+                if c < N_CONV - 1:
+                    feats.append(relu(z_c))
+            blocks.append(convs)
+            F = F + relu(convs[-1][1])
+            i += N_CONV
+        F = F + F_prev
+    tape["blocks"] = blocks
+    U = F + F0
+    ups = []
+    for d in range(D):
+        z = cnn.conv3x3(U, *L[i])
+        ups.append((U, z))
+        U = shuffle(relu(z))
+        i += 1
+    tape["ups"] = ups
+    tape["rec_in"] = U
+    return cnn.conv3x3(U, *L[i]), tape
+
+
+def backward(params, tape, dy):
+    """Gradient of a loss w.r.t. the flat params, given dL/dI_SR: the forward
+    steps of Sec. 4 in reverse (each conv's input / weight / bias gradients,
+    ReLU masks from the recorded pre-activations, deshuffle and shuffle
+    exchanged, the dense concatenations split back into their parts, the
+    block, group and Eq. F_DF skips adding their gradients)."""
+    s, c_hr = tape["s"], tape["c_hr"]
+    L = unpack(params, s, c_hr)
+    D = depth(s)
+    grads = [None] * len(L)
+    i = len(L) - 1
+    dU, dw, db = cnn.conv3x3_backward(tape["rec_in"], L[i][0], dy)
+    grads[i] = (dw, db)
+    for d in reversed(range(D)):
+        i -= 1
+        U_in, z = tape["ups"][d]
+        dz = deshuffle(dU) * (z > 0.0)
+        dU, dw, db = cnn.conv3x3_backward(U_in, L[i][0], dz)
+        grads[i] = (dw, db)
+    # U = F_G + F_0
+    dF = dU
+    dF0 = dU.copy()
+    blocks = tape["blocks"]
+    bi = len(blocks)
+    for g in reversed(range(N_RDG)):
+        d_skip = dF                       # F_g = chain(F_{g-1}) + F_{g-1}
+        for b in reversed(range(N_RDB)):
+            bi -= 1
+            convs = blocks[bi]
+            # RDB(F_in) = F_in + ReLU(z_4); z_c = conv_c([F_in, f_1, ..., f_{c-1}])
+            d_parts = [dF] + [np.zeros_like(dF) for _ in range(N_CONV - 1)]
+            dz = dF * (convs[-1][1] > 0.0)
+            for c in reversed(range(N_CONV)):
+                x_c, z_c = convs[c]
+                if c < N_CONV - 1:
+                    dz = d_parts[c + 1] * (z_c > 0.0)
+                dx, dw, db = cnn.conv3x3_backward(x_c, L[3 + bi * N_CONV + c][0], dz)
+                grads[3 + bi * N_CONV + c] = (dw, db)
+                for k in range(c + 1):
+                    d_parts[k] = d_parts[k] + dx[..., C_F * k:C_F * (k + 1)]
+            dF = d_parts[0]
+        dF = dF + d_skip
+    dF0 = dF0 + dF
+    x_f, z = tape["fuse"]
+    dx_f, dw, db = conv1x1_backward(x_f, L[2][0], dF0 * (z > 0.0))
+    grads[2] = (dw, db)
+    dF_lr, dF_h = dx_f[..., :C_F], dx_f[..., C_F:]
+    for _ in range(D):
+        dF_h = shuffle(dF_h)
+    x_hr, z = tape["hr"]
+    _, dw, db = cnn.conv3x3_backward(x_hr, L[1][0], dF_h * (z > 0.0))
+    grads[1] = (dw, db)
+    x_lr, z = tape["lr"]
+    _, dw, db = cnn.conv3x3_backward(x_lr, L[0][0], dF_lr * (z > 0.0))
+    grads[0] = (dw, db)
+    return pack(grads)
+
+
+def loss_and_grad(params, lrhs, hrls, albedo, normal, target, s, loss="robust", beta=0.1,
+                  extra=None):
+    """The training loss of I_SR against `target` (cnn.loss_fn: "robust" = the
+    method's l_r, or "l1log") and its gradient w.r.t. the flat params."""
+    y, tape = forward_tape(params, lrhs, hrls, albedo, normal, s, extra)
+    value, dy = cnn.loss_fn(y, target, loss, beta)
+    return value, backward(params, tape, dy)
 
 
 def flops_per_lr_pixel(s, c_hr=C_HR):

@@ -177,3 +177,96 @@ def test_kaiming_network_is_finite_and_local():
     # LR rows 0 .. 62 at most (61 LR 3x3 convs before the upsampling conv, one
     # at LR in UP), one more HR row each for the x2 part and H_rec
     assert rows.max() <= s * 63 + 2
+
+
+def _small_case(s, seed, c_hr=rdn.C_HR, h=2, w=3):
+    rng = np.random.default_rng(seed)
+    L = rdn.unpack(rdn.kaiming(seed, s, c_hr, fusion_damp=0.3), s, c_hr)
+    # small positive biases keep most ReLUs away from their kink
+    L = [(wt + rng.normal(0, 0.01, wt.shape), np.full(b.shape, 0.05)) for wt, b in L]
+    p = rdn.pack(L)
+    H, W = h * s, w * s
+    lr = rng.gamma(2.0, 0.5, (1, h, w, 3))
+    hr = rng.gamma(1.0, 1.0, (1, H, W, 3))
+    alb = rng.uniform(0, 1, (1, H, W, 3))
+    nrm = rng.uniform(-1, 1, (1, H, W, 3))
+    extra = rng.gamma(1.0, 0.5, (1, H, W, 9)) if c_hr == rdn.C_HR_EXTRA else None
+    return p, lr, hr, alb, nrm, extra, rng
+
+
+@pytest.mark.parametrize("s", [2, 4])
+def test_forward_tape_equals_forward(s):
+    p, lr, hr, alb, nrm, ex, _ = _small_case(s, 1)
+    y, _ = rdn.forward_tape(p, lr, hr, alb, nrm, s, ex)
+    assert np.array_equal(y, rdn.forward(p, lr, hr, alb, nrm, s, ex))
+
+
+@pytest.mark.parametrize("s,c_hr", [(2, rdn.C_HR), (4, rdn.C_HR), (8, rdn.C_HR),
+                                    (2, rdn.C_HR_EXTRA)])
+def test_backward_matches_finite_differences(s, c_hr):
+    # L = sum(I_SR * G): dL/dI_SR = G; central differences of the float64
+    # forward at weights and biases of every layer kind (H_lrhs, H_hrls, the
+    # fuse conv behind the deshuffles, the four convs of a dense block in the
+    # first and the last group, every upsampling conv, H_Rec)
+    p, lr, hr, alb, nrm, ex, rng = _small_case(s, 7 + s, c_hr)
+    y, tape = rdn.forward_tape(p, lr, hr, alb, nrm, s, ex)
+    G = rng.normal(size=y.shape)
+    g = rdn.backward(p, tape, G)
+    assert g.shape == p.shape
+    offs = rdn.layer_offsets(s, c_hr)
+    nconv = rdn.N_RDG * rdn.N_RDB * rdn.N_CONV
+    pick = offs[:3] + offs[3:7] + offs[3 + nconv - 4:3 + nconv] + offs[3 + nconv:]
+    idx = []
+    for _, wo, bo, k, ci, co in pick:
+        idx += [wo + int(rng.integers(0, bo - wo)), bo + int(rng.integers(0, co))]
+    eps = 1e-6
+    checked = 0
+    for j in idx:
+        e = np.zeros_like(p)
+        e[j] = eps
+        fp = (rdn.forward(p + e, lr, hr, alb, nrm, s, ex) * G).sum()
+        fm = (rdn.forward(p - e, lr, hr, alb, nrm, s, ex) * G).sum()
+        fd = (fp - fm) / (2 * eps)
+        assert abs(g[j] - fd) <= 1e-5 * max(1.0, abs(fd)), (j, g[j], fd)
+        checked += fd != 0.0
+    assert checked >= len(idx) // 2
+
+
+def test_backward_last_layer_closed_form():
+    # for L = sum(I_SR * G) the H_Rec bias gradient is the per-channel sum of
+    # G, and its weight gradient the correlation of G with H_Rec's input,
+    # written out with explicit loops
+    s = 2
+    p, lr, hr, alb, nrm, ex, rng = _small_case(s, 3)
+    y, tape = rdn.forward_tape(p, lr, hr, alb, nrm, s, ex)
+    G = rng.normal(size=y.shape)
+    g = rdn.backward(p, tape, G)
+    _, wo, bo, k, ci, co = rdn.layer_offsets(s)[-1]
+    assert np.allclose(g[bo:bo + co], G.sum(axis=(0, 1, 2)), rtol=1e-12, atol=1e-12)
+    U = tape["rec_in"]
+    N, H, W, C = U.shape
+    dw = np.zeros((co, 3, 3, ci))
+    for o in range(co):
+        for dy in range(3):
+            for dx in range(3):
+                for yy in range(H):
+                    for xx in range(W):
+                        sy, sx = yy + dy - 1, xx + dx - 1
+                        if 0 <= sy < H and 0 <= sx < W:
+                            dw[o, dy, dx] += G[0, yy, xx, o] * U[0, sy, sx]
+    assert np.allclose(g[wo:bo].reshape(co, 3, 3, ci), dw, rtol=1e-10, atol=1e-12)
+
+
+def test_loss_and_grad_robust_loss_by_finite_differences():
+    s = 2
+    p, lr, hr, alb, nrm, ex, rng = _small_case(s, 5)
+    target = rng.gamma(1.0, 1.0, (1, 2 * s, 3 * s, 3))
+    v, g = rdn.loss_and_grad(p, lr, hr, alb, nrm, target, s, loss="robust", beta=0.1)
+    off = rdn.layer_offsets(s)
+    for j in (off[0][1] + 5, off[2][2] + 1, off[-1][1] + 17):
+        e = np.zeros_like(p)
+        e[j] = 1e-6
+        vp, _ = rdn.loss_and_grad(p + e, lr, hr, alb, nrm, target, s, loss="robust", beta=0.1)
+        vm, _ = rdn.loss_and_grad(p - e, lr, hr, alb, nrm, target, s, loss="robust", beta=0.1)
+        fd = (vp - vm) / 2e-6
+        assert abs(g[j] - fd) <= 1e-5 * max(1e-3, abs(fd)), (j, g[j], fd)
