@@ -29,6 +29,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liborc.so")
 _lock = threading.Lock()
+_est_lock = threading.Lock()   # the estimator switch is process-global in orc_pt.c
 _lib = None
 
 
@@ -66,6 +67,9 @@ def lib():
                                      i32, u64, i32, i32, i32, P, P, P, P, P, P, P, P, P]
             L.orc_render.restype = i32
             L.orc_num_threads.restype = i32
+            L.orc_set_estimator.argtypes = [i32]
+            L.orc_bsdf_eval_batch.argtypes = [P, P, P, i32, P, P]
+            L.orc_bsdf_sample_batch.argtypes = [P, P, P, i32, P, P, P, P]
             _lib = L
     return _lib
 
@@ -135,11 +139,44 @@ def cast(V, orig, dirs, brute: bool = False):
     return prim, t
 
 
+def bsdf_eval(mat, wo, wi):
+    """f (without cosine) [n,3] and sampling pdf [n] of one material row
+    (type, albedo rgb, alpha, Le rgb) for local directions wo, wi [n,3]
+    (shading normal +z)."""
+    m = np.ascontiguousarray(mat, dtype=np.float32).reshape(8)
+    wo = np.ascontiguousarray(np.broadcast_to(wo, np.shape(wi)), dtype=np.float32)
+    wi = np.ascontiguousarray(wi, dtype=np.float32)
+    n = len(wi)
+    f = np.zeros((n, 3), np.float32)
+    pdf = np.zeros(n, np.float32)
+    lib().orc_bsdf_eval_batch(_p(m), _p(wo), _p(wi), n, _p(f), _p(pdf))
+    return f, pdf
+
+
+def bsdf_sample(mat, wo, u):
+    """Sample wi for local wo [n,3] with uniforms u [n,2]: returns wi [n,3],
+    weight = f cos / pdf [n,3], pdf [n] and ok [n] (False: below the surface)."""
+    m = np.ascontiguousarray(mat, dtype=np.float32).reshape(8)
+    u = np.ascontiguousarray(u, dtype=np.float32)
+    n = len(u)
+    wo = np.ascontiguousarray(np.broadcast_to(wo, (n, 3)), dtype=np.float32)
+    wi = np.zeros((n, 3), np.float32)
+    wt = np.zeros((n, 3), np.float32)
+    pdf = np.zeros(n, np.float32)
+    ok = np.zeros(n, np.int32)
+    lib().orc_bsdf_sample_batch(_p(m), _p(wo), _p(u), n, _p(wi), _p(wt), _p(pdf), _p(ok))
+    return wi, wt, pdf, ok.astype(bool)
+
+
+ESTIMATORS = {"mis": 0, "light": 1, "bsdf": 2}
+
+
 def num_threads() -> int:
     return int(lib().orc_num_threads())
 
 
-def render(scene, W, H, spp, max_depth, rr_start=None, seed=0, rows=None, threads=0, grid=1):
+def render(scene, W, H, spp, max_depth, rr_start=None, seed=0, rows=None, threads=0, grid=1,
+           estimator="mis"):
     """Path-trace the scene; returns dict(radiance[H,W,3], albedo, normal,
     depth[H,W], counts[max_depth+1], shadow_counts[max_depth+1]).
 
@@ -149,7 +186,12 @@ def render(scene, W, H, spp, max_depth, rr_start=None, seed=0, rows=None, thread
     block (nearest-neighbour downsampling of a g-times finer render).
     Also returns the extra layers diffuse, specular and variance [H,W,3]:
     the radiance of the samples whose first hit is Lambertian / GGX, and the
-    per-channel sample variance of the pixel mean."""
+    per-channel sample variance of the pixel mean.
+
+    estimator selects how lights and the environment are reached: "mis" (the
+    renderer's: next-event estimation and BSDF sampling, power heuristic),
+    "light" (next-event estimation only) or "bsdf" (BSDF sampling only).  The
+    last two exist to test the first: all three estimate the same integral."""
     if rr_start is None:
         rr_start = 1 << 30
     r0, r1 = (0, H) if rows is None else rows
@@ -166,12 +208,22 @@ def render(scene, W, H, spp, max_depth, rr_start=None, seed=0, rows=None, thread
         "shadow_counts": np.zeros(max_depth + 1, np.uint64),
     }
     s = scene
-    rc = lib().orc_render(_p(s["V"]), len(s["V"]), _p(s["tri_mat"]), _p(s["tri_light"]),
+    L = lib()
+    with _est_lock:
+        L.orc_set_estimator(ESTIMATORS[estimator])
+        try:
+            rc = _render_call(s, W, H, spp, max_depth, rr_start, grid, seed, r0, r1, threads, out)
+        finally:
+            L.orc_set_estimator(0)
+    if rc != 0:
+        raise ValueError(f"orc_render failed ({rc})")
+    return out
+
+
+def _render_call(s, W, H, spp, max_depth, rr_start, grid, seed, r0, r1, threads, out):
+    return lib().orc_render(_p(s["V"]), len(s["V"]), _p(s["tri_mat"]), _p(s["tri_light"]),
                           _p(s["mats"]), _p(s["lights"]), len(s["lights"]), _p(s["env"]),
                           _p(s["cam"]), W, H, spp, max_depth, rr_start, grid, seed, r0, r1, threads,
                           _p(out["radiance"]), _p(out["albedo"]), _p(out["normal"]),
                           _p(out["depth"]), _p(out["diffuse"]), _p(out["specular"]),
                           _p(out["variance"]), _p(out["counts"]), _p(out["shadow_counts"]))
-    if rc != 0:
-        raise ValueError(f"orc_render failed ({rc})")
-    return out

@@ -18,7 +18,14 @@
  * Pins (tests/test_oracle_*.py): Philox known-answer vectors of Salmon et al.
  * (SC'11); closest hit == brute force on random triangle soups; radix tree
  * invariants; white furnace L = Le * sum_{k<=D} rho^k; diffuse plane under a
- * uniform sky L = rho * L_sky; 1/sqrt(N) error decay with spp.
+ * uniform sky L = rho * L_sky; 1/sqrt(N) error decay with spp.  Materials:
+ * the GGX pdf integrates to 1 (quadrature over half vectors), the sampler
+ * draws from it (chi-square), its weight is f cos / pdf and its mean the
+ * directional albedo, reciprocity, the Fresnel limit of a near mirror.
+ * Direct lighting: a Lambertian plane under two quad lights and an
+ * environment equals Lambert's closed form (projected solid angles of the
+ * quads) with MIS, light sampling alone and BSDF sampling alone, and the
+ * three agree on rough GGX planes.
  */
 #include <math.h>
 #include <stdint.h>
@@ -584,6 +591,47 @@ static int bsdf_sample(const mat_t* m, v3 wo, float u1, float u2, v3* wi, v3* we
     return 1;
 }
 
+/* Test hooks: the BSDF of one material (a row of the scene's material table:
+ * type, albedo rgb, alpha, Le rgb) over n pairs of local directions (shading
+ * normal = +z).  eval: f (without the cosine) and the sampling pdf of wi;
+ * sample: wi, weight = f cos / pdf, pdf and ok (0 = sample below the surface,
+ * then the other outputs are 0) for uniforms u [n][2]. */
+void orc_bsdf_eval_batch(const float* mat8, const float* wo, const float* wi, int n, float* f,
+                         float* pdf)
+{
+    mat_t m;
+    m.type = (int)mat8[0];
+    m.albedo = mk(mat8[1], mat8[2], mat8[3]);
+    m.alpha = mat8[4];
+    m.Le = mk(mat8[5], mat8[6], mat8[7]);
+    for (int i = 0; i < n; ++i) {
+        v3 o = mk(wo[3 * i], wo[3 * i + 1], wo[3 * i + 2]);
+        v3 w = mk(wi[3 * i], wi[3 * i + 1], wi[3 * i + 2]);
+        v3 r = bsdf_eval(&m, o, w, pdf + i);
+        f[3 * i] = r.x; f[3 * i + 1] = r.y; f[3 * i + 2] = r.z;
+    }
+}
+
+void orc_bsdf_sample_batch(const float* mat8, const float* wo, const float* u, int n, float* wi,
+                           float* weight, float* pdf, int32_t* ok)
+{
+    mat_t m;
+    m.type = (int)mat8[0];
+    m.albedo = mk(mat8[1], mat8[2], mat8[3]);
+    m.alpha = mat8[4];
+    m.Le = mk(mat8[5], mat8[6], mat8[7]);
+    for (int i = 0; i < n; ++i) {
+        v3 o = mk(wo[3 * i], wo[3 * i + 1], wo[3 * i + 2]);
+        v3 w = mk(0, 0, 0), wt = mk(0, 0, 0);
+        float p = 0.0f;
+        ok[i] = bsdf_sample(&m, o, u[2 * i], u[2 * i + 1], &w, &wt, &p);
+        if (!ok[i]) { w = mk(0, 0, 0); wt = mk(0, 0, 0); p = 0.0f; }
+        wi[3 * i] = w.x; wi[3 * i + 1] = w.y; wi[3 * i + 2] = w.z;
+        weight[3 * i] = wt.x; weight[3 * i + 1] = wt.y; weight[3 * i + 2] = wt.z;
+        pdf[i] = p;
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* the path tracer                                                           */
 /* ------------------------------------------------------------------------ */
@@ -591,7 +639,23 @@ typedef struct {
     int W, H, spp, max_depth, rr_start;
     int grid;   /* camera sampling grid: 1 = whole pixel footprint */
     uint32_t key[2];
+    int estimator;   /* ORC_EST_* below */
 } rparams_t;
+
+/* Direct-lighting estimator.  ORC_EST_MIS is the renderer's: next-event
+ * estimation and BSDF sampling combined by the power heuristic.  The two
+ * single-technique estimators exist only to test that combination: with
+ * ORC_EST_LIGHT every light and the environment are reached only through
+ * next-event estimation (weight 1; BSDF-sampled hits on them add nothing),
+ * with ORC_EST_BSDF only through BSDF sampling (no shadow rays; weight 1).
+ * All three are unbiased for the same integral, so their means must agree;
+ * a light pdf, an MIS weight or a BSDF pdf that is wrong breaks that. */
+#define ORC_EST_MIS 0
+#define ORC_EST_LIGHT 1
+#define ORC_EST_BSDF 2
+static int g_estimator = ORC_EST_MIS;
+
+void orc_set_estimator(int mode) { g_estimator = mode; }
 
 /* one path; returns radiance, writes first-hit aux (albedo, shading normal,
    depth, lobe = 1 Lambertian / 2 GGX / 0 no hit), counts rays per bounce */
@@ -632,7 +696,9 @@ static v3 trace_path(const scene_t* S, const rparams_t* P, int px, int py, int s
         if (prim < 0) {
             if (env_on) {
                 float w = 1.0f;
-                if (b > 0 && pdf_e > 0.0f) w = (pdf_b * pdf_b) / (pdf_b * pdf_b + pdf_e * pdf_e);
+                if (b > 0 && P->estimator == ORC_EST_LIGHT) w = 0.0f;
+                else if (b > 0 && P->estimator == ORC_EST_MIS && pdf_e > 0.0f)
+                    w = (pdf_b * pdf_b) / (pdf_b * pdf_b + pdf_e * pdf_e);
                 L = mk(L.x + beta.x * S->env.x * w, L.y + beta.y * S->env.y * w,
                        L.z + beta.z * S->env.z * w);
             }
@@ -648,7 +714,9 @@ static v3 trace_path(const scene_t* S, const rparams_t* P, int px, int py, int s
         if ((m.Le.x > 0.0f || m.Le.y > 0.0f || m.Le.z > 0.0f) && cos_o < 0.0f) {
             float w = 1.0f;
             int li = S->tri_light[prim];
-            if (b > 0 && li >= 0) {
+            if (b > 0 && li >= 0 && P->estimator == ORC_EST_LIGHT) {
+                w = 0.0f;
+            } else if (b > 0 && li >= 0 && P->estimator == ORC_EST_MIS) {
                 const float* lq = S->lights + (size_t)li * 12;
                 v3 ln = cross(mk(lq[3], lq[4], lq[5]), mk(lq[6], lq[7], lq[8]));
                 float area = sqrtf(dot(ln, ln));
@@ -669,7 +737,7 @@ static v3 trace_path(const scene_t* S, const rparams_t* P, int px, int py, int s
         v3 org = madd(p, ns, RAY_EPS);
 
         /* next-event estimation: one light (or the environment), power-heuristic MIS */
-        if (n_choices > 0) {
+        if (n_choices > 0 && P->estimator != ORC_EST_BSDF) {
             int k = (int)(g1[0] * (float)n_choices);
             if (k > n_choices - 1) k = n_choices - 1;
             if (k < S->n_lights) {
@@ -689,7 +757,7 @@ static v3 trace_path(const scene_t* S, const rparams_t* P, int px, int py, int s
                     float pb;
                     v3 f = bsdf_eval(&m, wo, to_local(wi, T, B, ns), &pb);
                     float pl = pick * d2 / (cos_l * area);
-                    float w = (pl * pl) / (pl * pl + pb * pb);
+                    float w = P->estimator == ORC_EST_LIGHT ? 1.0f : (pl * pl) / (pl * pl + pb * pb);
                     float sc = (cos_s / pl) * w;
                     v3 c = mk(beta.x * f.x * Le.x * sc, beta.y * f.y * Le.y * sc,
                               beta.z * f.z * Le.z * sc);
@@ -703,7 +771,7 @@ static v3 trace_path(const scene_t* S, const rparams_t* P, int px, int py, int s
                     float pb;
                     v3 f = bsdf_eval(&m, wo, wl, &pb);
                     float pe = pick * wl.z * INV_PI_F;
-                    float w = (pe * pe) / (pe * pe + pb * pb);
+                    float w = P->estimator == ORC_EST_LIGHT ? 1.0f : (pe * pe) / (pe * pe + pb * pb);
                     float sc = (wl.z / pe) * w;
                     v3 c = mk(beta.x * f.x * S->env.x * sc, beta.y * f.y * S->env.y * sc,
                               beta.z * f.z * S->env.z * sc);
@@ -757,7 +825,8 @@ int orc_render(const float* V, int n, const int32_t* tri_mat, const int32_t* tri
         scene_free(&S);
         return -2;
     }
-    rparams_t P = {W, H, spp, max_depth, rr_start, grid, {(uint32_t)seed, (uint32_t)(seed >> 32)}};
+    rparams_t P = {W, H, spp, max_depth, rr_start, grid, {(uint32_t)seed, (uint32_t)(seed >> 32)},
+                   g_estimator};
     int nb = max_depth + 1;
     uint64_t tot[64] = {0}, stot[64] = {0};
 #ifdef _OPENMP

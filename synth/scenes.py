@@ -246,8 +246,9 @@ def procedural(seed: int, n_spheres: int = 64, n_large: int = 31, aspect: float 
         c = np.array([rng.uniform(-8, 8), rng.uniform(4.0, 8.0), rng.uniform(-8, 8)])
         le = rng.uniform(5.0, 20.0)
         p0 = c - np.array([size[0] / 2, 0, size[1] / 2])
-        # e1 along +z, e2 along +x -> cross(e1, e2) = -y: the light faces down
-        b.quad_light(p0, np.array([0, 0, size[1]]), np.array([size[0], 0, 0]),
+        # e1 along +x, e2 along +z -> cross(e1, e2) = x^ x z^ = -y: the light
+        # faces down, onto the spheres and the ground
+        b.quad_light(p0, np.array([size[0], 0, 0]), np.array([0, 0, size[1]]),
                      np.array([le, le, le]))
     cam = camera((0.0, 6.0, 18.0), (0.0, 0.5, 0.0), (0, 1, 0), 45.0, aspect)
     return b.finish((0.5, 0.5, 0.5), cam)
@@ -272,6 +273,29 @@ def sky_plane(rho: float, L_sky: float):
     b.add(_quad_tris((-50, 0, -50), (0, 0, 100), (100, 0, 0)), m)
     cam = camera((0, 5, 0), (0, 0, 0), (0, 0, -1), 30.0)
     return b.finish((L_sky, L_sky, L_sky), cam)
+
+
+LIGHTS_OVER_PLANE = (
+    # p0, e1, e2, Le of two disjoint quads at height 1 facing down
+    # (cross(e1, e2) = x^ x z^ = -y); different areas and colours
+    ((-0.7, 1.0, -0.5), (0.5, 0.0, 0.0), (0.0, 0.0, 0.8), (6.0, 3.0, 1.5)),
+    ((0.1, 1.0, -0.2), (0.4, 0.0, 0.0), (0.0, 0.0, 0.6), (2.0, 5.0, 8.0)),
+)
+
+
+def lights_over_plane(kind: int = LAMBERT, albedo=(0.6, 0.6, 0.6), alpha: float = 1.0,
+                      env: float = 0.3):
+    """A large plane y = 0 under the two quad lights of LIGHTS_OVER_PLANE and a
+    uniform environment, seen straight down by a camera at height 0.5 (below
+    the lights, which stay out of view): every camera ray hits the plane, and
+    at one scattering event its pixel sees only direct light."""
+    b = _Builder()
+    m = b.material(kind, albedo, alpha)
+    b.add(_quad_tris((-50, 0, -50), (0, 0, 100), (100, 0, 0)), m)
+    for p0, e1, e2, le in LIGHTS_OVER_PLANE:
+        b.quad_light(np.array(p0), np.array(e1), np.array(e2), np.array(le))
+    cam = camera((0.0, 0.5, 0.0), (0.0, 0.0, 0.0), (0, 0, -1), 50.0)
+    return b.finish((env, env, env), cam)
 
 
 def random_triangles(seed: int, n: int, spread: float = 1.0, size: float = 0.3):

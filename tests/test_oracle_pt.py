@@ -179,3 +179,115 @@ def test_variance_layer_matches_spread_of_independent_renders(orc):
     est = np.stack([r["variance"] for r in runs]).astype(np.float64).mean(axis=0)
     ratio = est.sum() / emp.sum()
     assert 0.85 < ratio < 1.15, ratio
+
+
+# --------------------------------------------------------------------------
+# area lights: next-event estimation, BSDF sampling and their MIS combination
+# --------------------------------------------------------------------------
+
+def _plane_points(cam, W, H, k=8):
+    """Points where the camera rays of a k x k midpoint grid inside every
+    pixel meet the plane y = 0 (the scene's pinhole model: pixel (x, y) spans
+    image coordinates a = 2 (x + jx) / W - 1, b = 1 - 2 (y + jy) / H)."""
+    cam = cam.astype(np.float64)
+    eye, fwd, rgt, up = cam[0:3], cam[3:6], cam[6:9], cam[9:12]
+    j = (np.arange(k) + 0.5) / k
+    sx = (np.arange(W)[:, None] + j[None, :]).reshape(-1) / W
+    sy = (np.arange(H)[:, None] + j[None, :]).reshape(-1) / H
+    a = 2 * sx - 1
+    b = 1 - 2 * sy
+    d = fwd[None, None] + b[:, None, None] * up + a[None, :, None] * rgt   # [H k, W k, 3]
+    t = -eye[1] / d[..., 1]
+    return eye + d * t[..., None]
+
+
+def _projected_solid_angle(x, quad):
+    """Lambert's closed form for a polygon seen from points x [.., 3] on a
+    surface with normal +y: the integral of cos(theta) over the solid angle
+    it subtends, 1/2 |sum_i gamma_i n . unit(r_i x r_i+1)| with r_i the unit
+    vectors to its vertices and gamma_i the angle between consecutive ones."""
+    r = [v - x for v in quad]
+    r = [v / np.linalg.norm(v, axis=-1, keepdims=True) for v in r]
+    acc = 0.0
+    for i in range(len(r)):
+        a, b = r[i], r[(i + 1) % len(r)]
+        c = np.cross(a, b)
+        gam = np.arccos(np.clip(np.sum(a * b, -1), -1, 1))
+        acc = acc + gam * c[..., 1] / np.linalg.norm(c, axis=-1)
+    return 0.5 * np.abs(acc)
+
+
+def _direct_light_closed_form(sc, rho, W, H, k=8):
+    """Expected pixel radiance of a Lambertian plane under quad lights (Le_k,
+    projected solid angle P_k) and an environment L_env that the lights
+    block: rho / pi * (sum_k Le_k P_k + L_env (pi - sum_k P_k)), averaged
+    over each pixel's footprint."""
+    x = _plane_points(sc["cam"], W, H, k)
+    env = sc["env"].astype(np.float64)
+    E = np.zeros(x.shape[:2] + (3,)) + env * np.pi
+    for p0, e1, e2, le in scenes.LIGHTS_OVER_PLANE:
+        p0, e1, e2, le = (np.array(v, np.float64) for v in (p0, e1, e2, le))
+        P = _projected_solid_angle(x, [p0, p0 + e1, p0 + e1 + e2, p0 + e2])
+        E = E + P[..., None] * (le - env)
+    L = rho / np.pi * E
+    return L.reshape(H, k, W, k, 3).mean(axis=(1, 3))
+
+
+def _z_scores(r, want, block=8):
+    """z of the image sum and of each block sum against want, with the
+    estimator's own per-pixel variance of the mean."""
+    d = r["radiance"].astype(np.float64) - want
+    v = r["variance"].astype(np.float64)
+    H, W, _ = d.shape
+    zs = [d.sum(axis=(0, 1)) / np.sqrt(v.sum(axis=(0, 1)))]
+    db = d.reshape(H // block, block, W // block, block, 3).sum(axis=(1, 3))
+    vb = v.reshape(H // block, block, W // block, block, 3).sum(axis=(1, 3))
+    zs.append((db / np.sqrt(vb)).reshape(-1, 3))
+    return np.abs(zs[0]).max(), np.abs(zs[1]).max()
+
+
+@pytest.mark.parametrize("env", [0.0, 0.3])
+@pytest.mark.parametrize("estimator", ["mis", "light", "bsdf"])
+def test_quad_lights_over_diffuse_plane_closed_form(orc, estimator, env):
+    # one scattering event on a Lambertian plane: the pixel sees the direct
+    # light of two quads (different areas and colours) and of the environment
+    # they block; with the environment there are 3 choices of light to pick
+    rho = 0.6
+    sc = scenes.lights_over_plane(scenes.LAMBERT, (rho, rho, rho), env=env)
+    W = H = 32
+    want = _direct_light_closed_form(sc, rho, W, H)
+    r = orc.render(sc, W, H, 256, 1, seed=21, estimator=estimator)
+    assert np.allclose(r["albedo"], rho) and np.allclose(r["normal"], [0, 1, 0])
+    z_all, z_blk = _z_scores(r, want)
+    assert z_all < 4.0 and z_blk < 4.5, (z_all, z_blk)
+    rel = abs(r["radiance"].mean() - want.mean()) / want.mean()
+    assert rel < 0.02, rel
+    shadow = r["shadow_counts"]
+    if estimator == "bsdf":
+        assert shadow.sum() == 0
+    else:
+        assert shadow[0] > 0
+
+
+@pytest.mark.parametrize("alpha", [0.15, 0.5])
+def test_quad_lights_over_ggx_plane_estimators_agree(orc, alpha):
+    # no closed form for a rough conductor, but light sampling alone, BSDF
+    # sampling alone and their MIS combination estimate the same integral:
+    # the BSDF value of the evaluator (light sampling), the weight of the
+    # sampler (BSDF sampling) and both pdfs inside the MIS weights must agree
+    sc = scenes.lights_over_plane(scenes.GGX, (0.9, 0.6, 0.3), alpha=alpha, env=0.3)
+    W = H = 32
+    rs = {e: orc.render(sc, W, H, 512, 1, seed=30 + i, estimator=e)
+          for i, e in enumerate(("mis", "light", "bsdf"))}
+    for a, b in (("mis", "light"), ("mis", "bsdf"), ("light", "bsdf")):
+        d = rs[a]["radiance"].astype(np.float64) - rs[b]["radiance"]
+        v = rs[a]["variance"].astype(np.float64) + rs[b]["variance"]
+        z = np.abs(d.sum(axis=(0, 1)) / np.sqrt(v.sum(axis=(0, 1)))).max()
+        db = d.reshape(4, 8, 4, 8, 3).sum(axis=(1, 3))
+        vb = v.reshape(4, 8, 4, 8, 3).sum(axis=(1, 3))
+        zb = np.abs(db / np.sqrt(vb)).max()
+        assert z < 4.0 and zb < 4.5, (a, b, z, zb)
+    # MIS is never the worse of the two techniques it combines (it need not
+    # be the best: the power heuristic is near-optimal, not optimal)
+    var = {e: rs[e]["variance"].sum() for e in rs}
+    assert var["mis"] < max(var["light"], var["bsdf"]), var
