@@ -48,10 +48,19 @@ CONV_FLOP_PER_PX = 2 * 9 * (12 * 64 + 16 * 64 * 64 + 64 * 3)      # 1,196,928
 # writes r, reads r and h, writes h (5 x 128 B); the head reads 128 B and
 # writes 3 FP32 (12 B)
 CONV_BYTES_PER_PX = (24 + 128) + 8 * 5 * 128 + (128 + 12)           # 5,412
-# FP32 operations per traversal step, counted from the kernel source
-# (pt.cu: slab() on both children of a node; intersect() per triangle)
+# algorithmic FP32 work per traversal step: a node visit tests the ray against
+# its two children's boxes (slab test, 12 FLOP per box), a triangle test is
+# Moller-Trumbore (27 FLOP); the roofline peak counts an FMA as 2 FLOP
+FLOP_PER_NODE_VISIT = 24
+FLOP_PER_TRI_TEST = 27
+# the kernel's own FP32 instruction count per step, from the source (pt.cu:
+# slab() on both children, intersect() per triangle; built with --fmad=false),
+# reported beside the algorithmic figure against the non-FMA issue rate
 OPS_PER_NODE_VISIT = 52
 OPS_PER_TRI_TEST = 50
+# the BF16 training step's algorithmic FLOPs per HR pixel: forward, weight
+# gradients of all 18 layers, input gradients of the 17 layers after the first
+TRAIN_FLOP_PER_PX = 2 * CONV_FLOP_PER_PX + (CONV_FLOP_PER_PX - 2 * 9 * 12 * 64)
 
 
 def _peaks():
@@ -113,10 +122,10 @@ class ClockSampler:
                 "samples": len(self.rows)}
 
 
-def _traffic(kernel, src, key="dram_bytes_per_launch"):
-    """Per-launch DRAM bytes (or another per-launch counter, `key`) of `kernel`
-    from the committed ncu summary, if the kernel source is unchanged since the
-    capture (else None)."""
+def _traffic(kernel, src):
+    """The committed ncu DRAM-traffic record of `kernel` (profiles/traffic.json:
+    bytes of one captured launch and the work units it processed), if the
+    kernel source is unchanged since the capture (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -126,26 +135,68 @@ def _traffic(kernel, src, key="dram_bytes_per_launch"):
         return None
     with open(os.path.join(ROOT, "paper_2106_12802_gb300", "csrc", src), "rb") as f:
         sha = hashlib.sha256(f.read()).hexdigest()[:16]
-    return d.get(key) if d.get("src_sha256_16") == sha else None
+    return d if d.get("src_sha256_16") == sha else None
+
+
+def max_over_ranks(value, world, device=None):
+    """The maximum of a per-rank number over all ranks (the slowest rank's
+    time); the value itself at world size 1.  The reduction runs on `device`
+    under NCCL and on the host under gloo."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    dev = device if (device is not None and dist.get_backend() == "nccl") else torch.device("cpu")
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def l2_copy_gbs(megabytes=32, reps=20, trials=5):
+    """L2 bandwidth reference: bytes read + written per second by a device
+    copy between two L2-resident buffers of `megabytes` MB (median of
+    `trials` event-timed batches of `reps` copies, after a warm-up)."""
+    import torch
+    n = megabytes * (1 << 20) // 4
+    a = torch.ones(n, dtype=torch.float32, device="cuda")
+    b = torch.empty_like(a)
+    b.copy_(a)
+    ts = []
+    for _ in range(trials):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            b.copy_(a)
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = float(np.median(ts))
+    return 2 * n * 4 * reps / (ms * 1e-3) / 1e9
 
 
 # ----------------------------------------------------------------------------
 # CPU oracle (bounded samples of the same frame)
 # ----------------------------------------------------------------------------
-def oracle_frame_sample(desc, params, lr_rows=2, hr_rows=4, cnn_rows=4, seed=0):
+def oracle_frame_sample(desc, params, k=0, lr_rows=8, hr_rows=16, cnn_rows=4):
     """Times the oracle on a bounded sample of the hybrid frame and scales each
-    part to a whole frame.  Returns (ms_per_frame, detail)."""
+    part to a whole frame: `lr_rows` LRHS rows and `hr_rows` HRLS rows spread
+    evenly over the image (every (H / rows)-th row from an offset that moves
+    with the sample index k, so that samples cover the whole image), and the
+    FP64 network on a strip of `cnn_rows` output rows plus its receptive-field
+    halo.  Returns (ms_per_frame, detail)."""
     import oracle
     from oracle import cnn
     oracle.build()
     t0 = time.perf_counter()
     oracle.lbvh(desc["V"])
     t_build = time.perf_counter() - t0
+    st_lr, st_hr = LR // lr_rows, HR // hr_rows
+    seed = k
     t0 = time.perf_counter()
-    oracle.render(desc, LR, LR, SPP_LR, DEPTH, RR, seed, rows=(LR // 2, LR // 2 + lr_rows))
+    oracle.render(desc, LR, LR, SPP_LR, DEPTH, RR, seed, rows=((7 * k) % st_lr, LR, st_lr))
     t_lr = max(time.perf_counter() - t0 - t_build, 1e-9)
     t0 = time.perf_counter()
-    oracle.render(desc, HR, HR, SPP_HR, DEPTH, RR, seed + 1, rows=(HR // 2, HR // 2 + hr_rows))
+    oracle.render(desc, HR, HR, SPP_HR, DEPTH, RR, seed + 1, rows=((13 * k) % st_hr, HR, st_hr))
     t_hr = max(time.perf_counter() - t0 - t_build, 1e-9)
     rng = np.random.default_rng(0)
     halo = 18                      # receptive field of the 18 stacked 3x3 convs
@@ -156,9 +207,23 @@ def oracle_frame_sample(desc, params, lr_rows=2, hr_rows=4, cnn_rows=4, seed=0):
     cnn.forward(params, lr, hr, hr, hr, S)
     t_cnn = time.perf_counter() - t0
     ms = 1e3 * (2 * t_build + t_lr * LR / lr_rows + t_hr * HR / hr_rows + t_cnn * HR / hr.shape[1])
-    detail = (f"LBVH build x2; LRHS rows {lr_rows}/{LR} and HRLS rows {hr_rows}/{HR} rendered "
-              f"(scaled by rows); FP64 CNN on a {hr.shape[1]}x{HR} strip (scaled by rows)")
+    detail = (f"LBVH build x2; every {st_lr}th LRHS row ({lr_rows}/{LR}) and every {st_hr}th "
+              f"HRLS row ({hr_rows}/{HR}) rendered (scaled by rows); FP64 CNN on a "
+              f"{hr.shape[1]}x{HR} strip (scaled by rows)")
     return ms, detail
+
+
+def oracle_frame_estimate(desc, params, samples=3):
+    """Mean of `samples` bounded oracle samples of one frame (rows at
+    different offsets); returns (ms_per_frame, detail)."""
+    ms, detail = [], ""
+    t0 = time.perf_counter()
+    for k in range(samples):
+        m, detail = oracle_frame_sample(desc, params, k)
+        ms.append(m)
+    wall = time.perf_counter() - t0
+    return float(np.mean(ms)), (detail + f"; mean of {samples} samples (rows at different "
+                                f"offsets), {wall:.1f} s wall")
 
 
 def cpu_cores():
@@ -180,12 +245,12 @@ def run_reference(args, rank, world):
     desc = scenes.procedural(0)
     params = cnn.kaiming(0)
     oracle.build()
-    for _ in range(args.warmup):
-        oracle_frame_sample(desc, params, 1, 1, 1)
+    for k in range(args.warmup):
+        oracle_frame_sample(desc, params, 1000 + k)
     times = []
     t_all = time.perf_counter()
     for k in range(args.steps):
-        ms, detail = oracle_frame_sample(desc, params, 1, 2, 2, seed=k)
+        ms, detail = oracle_frame_sample(desc, params, k)
         times.append(ms)
     wall = time.perf_counter() - t_all
     value = float(np.mean(times))
@@ -574,6 +639,57 @@ def fusion_precisions(mrs, net, flush, reps=10):
     return res
 
 
+def train_step_timing(mrs, params, flush, N=16, crop=128, s=S, reps=10, warmup=3):
+    """Device time of one BF16 training step of the fusion network at the
+    training batch (N crops of crop x crop HR pixels, x s): forward with every
+    activation kept, loss, tensor-core input and weight gradients, Adam.  The
+    inputs are random radiance-like images already on the device; L2 flushed
+    before every step; median of `reps` event-timed steps.  The per-family
+    split comes from one extra step with events around every launch."""
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(11)
+    h = crop // s
+    lr = torch.rand((N, h, h, 3), device="cuda", generator=g) * 2
+    hr = torch.rand((N, crop, crop, 3), device="cuda", generator=g) * 2
+    alb = torch.rand((N, crop, crop, 3), device="cuda", generator=g)
+    nrm = torch.rand((N, crop, crop, 3), device="cuda", generator=g) * 2 - 1
+    tgt = torch.rand((N, crop, crop, 3), device="cuda", generator=g) * 2
+    net = mrs.Net(params)
+    net.set_loss("l1log")
+    args = (lr, hr, alb, nrm, tgt, s)
+    for _ in range(warmup):
+        mrs.train_step(net, *args, lr=1e-4, precision="bf16", sync_loss=False)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        mrs.train_step(net, *args, lr=1e-4, precision="bf16", sync_loss=False)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    mrs.profile_read()
+    mrs.profile_enable(True)
+    flush.zero_()
+    mrs.train_step(net, *args, lr=1e-4, precision="bf16", sync_loss=False)
+    torch.cuda.synchronize()
+    mrs.profile_enable(False)
+    prof = mrs.profile_read()
+    net.close()
+    ms = float(np.median(ts))
+    flop = TRAIN_FLOP_PER_PX * N * crop * crop
+    tf = flop / (ms * 1e-3) / 1e12
+    peaks = _peaks()
+    return {"batch": [N, crop, crop], "scale": s, "precision": "bf16", "loss": "l1log",
+            "optimizer": "Adam, lr 1e-4", "ms": ms, "tflop_per_step": flop / 1e12,
+            "tflops": tf, "tensor_frac_of_measured_sustained": tf / peaks["bf16_tflops_sustained"],
+            "family_ms_events": {k: round(v[0], 4) for k, v in prof.items() if v[1]},
+            "l2": "flushed before every step (512 MiB write)",
+            "flop_note": "forward + weight gradients of 18 layers + input gradients of the 17 "
+                         "layers after the first, 2 FLOP per multiply-add"}
+
+
 # ----------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------
@@ -582,7 +698,7 @@ def run_gpu(args, rank, world):
     import torch.distributed as dist
 
     import paper_2106_12802_gb300 as mrs
-    from oracle import cnn
+    from paper_2106_12802_gb300 import trainer
     from synth import scenes
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -597,7 +713,7 @@ def run_gpu(args, rank, world):
     # --quick keeps the Kaiming initialisation (timing does not depend on the
     # weights, the gate's decision does)
     if args.quick:
-        net, training = mrs.Net(cnn.kaiming(0).astype(np.float32)), None
+        net, training = mrs.Net(trainer.init_params(0)), None
     else:
         net, training = train_net(mrs, S)
     params = net.get_params()
@@ -676,11 +792,8 @@ def run_gpu(args, rank, world):
     torch.cuda.synchronize()
     mrs.profile_enable(False)
     prof = mrs.profile_read()
-    t_local = float(np.sum(step_ms))
+    t_local = max_over_ranks(float(np.sum(step_ms)), world, dev)
     if world > 1:
-        t = torch.tensor([t_local], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_local = float(t.item())
         dist.barrier()
     ms_frame = t_local / (args.steps * world)
 
@@ -734,11 +847,21 @@ def run_gpu(args, rank, world):
         extra["paper_network_x4"] = paper_network(mrs, flush)
     if rank == 0 and not args.quick:
         extra["fusion_precisions_1024"] = fusion_precisions(mrs, net, flush)
+    if rank == 0:
+        extra["train_step"] = train_step_timing(mrs, trainer.init_params(0), flush)
     if rank == 0 and not args.quick and not args.no_spp_study:
         extra["spp_study_x4"] = spp_study(mrs)
-    if rank == 0 and not args.quick:
+    if rank == 0:
         stats_lr = mrs.render_stats(scene, LR, LR, SPP_LR, DEPTH, RR, 0)
         stats_hr = mrs.render_stats(scene, HR, HR, SPP_HR, DEPTH, RR, 1)
+        cnt_lr = mrs.render(scene, LR, LR, SPP_LR, DEPTH, RR, 0, aux=False)["counts"]
+        cnt_hr = mrs.render(scene, HR, HR, SPP_HR, DEPTH, RR, 1, aux=False)["counts"]
+        # closest-hit segments of bounces >= 1 (the tail kernel's units)
+        tail_segments = int(cnt_lr[1:].sum().item() + cnt_hr[1:].sum().item())
+    else:
+        stats_lr = stats_hr = None
+        tail_segments = None
+    if rank == 0 and not args.quick:
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         plain = mrs.render(scene, HR, HR, 64, DEPTH, RR, 7)
         torch.cuda.synchronize()
@@ -750,8 +873,6 @@ def run_gpu(args, rank, world):
         rays = int(plain["counts"].sum().item() + plain["shadow_counts"].sum().item())
         extra["plain_path_trace_1024_64spp"] = {
             "ms": pms, "msamples_per_s": HR * HR * 64 / pms / 1e3, "mrays_per_s": rays / pms / 1e3}
-    else:
-        stats_lr = stats_hr = None
 
     peaks = _peaks()
     conv_ms = prof["conv_tc"][0] / prof_steps
@@ -772,11 +893,16 @@ def run_gpu(args, rank, world):
                      peaks["bf16_tflops_sustained"] * 1e3 / peaks["hbm_gbs"] else "tensor"}
     dom = max(family_ms, key=family_ms.get)
     roofline = None
+    conv_tr = _traffic("k_conv_fold", "conv_tc.cu")
+    conv_traffic = conv_tr["dram_bytes_per_launch"] if conv_tr else None
+    if conv_roof is not None:
+        conv_roof["traffic_per_64to64_launch"] = conv_traffic
+        conv_roof["algorithmic_bytes_per_64to64_launch"] = 5 * 128 * HR * HR // 2
     if dom == "conv_tc":
         ach = CONV_BYTES_PER_PX * HR * HR / (conv_ms * 1e-3) / 1e9
-        roofline = {"kernel": "k_conv_tc (tcgen05 implicit-GEMM 3x3 conv)", "bound": "hbm",
+        roofline = {"kernel": "k_conv_fold (tcgen05 implicit-GEMM 3x3 conv)", "bound": "hbm",
                     "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": ach / peaks["hbm_gbs"], "traffic": _traffic("k_conv_tc", "conv_tc.cu"),
+                    "frac": ach / peaks["hbm_gbs"], "traffic": conv_traffic,
                     "peak_source": peaks["source"] + " HBM copy"}
     elif dom in ("trace", "shadow", "tail") and stats_lr:
         # traversal work of the kernel's own launches: the tail kernel's share
@@ -787,36 +913,59 @@ def run_gpu(args, rank, world):
         kinds = {"trace": ("",), "shadow": ("shadow_",), "tail": ("", "shadow_")}[dom]
         visits = sum(work(k + "visits", dom) for k in kinds)
         tests = sum(work(k + "tests", dom) for k in kinds)
+        flop = FLOP_PER_NODE_VISIT * visits + FLOP_PER_TRI_TEST * tests
         ops = OPS_PER_NODE_VISIT * visits + OPS_PER_TRI_TEST * tests
         kms = family_ms[dom]
+        launches_per_frame = prof[dom][1] / prof_steps
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
-        peak = sms * 128 * peaks["sm_max_mhz"] * 1e6 / 1e12
-        ach = ops / (kms * 1e-3) / 1e12
-        # L2 side of the same kernel (the LBVH is L2-resident): ncu's L2 bytes
-        # per launch over the live launch time, against the measured L2 read rate
-        l2b = _traffic(f"k_{dom}", "pt.cu", "lts_bytes_per_launch")
-        per_frame = prof[dom][1] / prof_steps
-        l2_gbs = l2b * per_frame / (kms * 1e-3) / 1e9 if l2b else None
-        l2_peak = mrs.l2_read_gbs() if rank == 0 else None
+        clock = peaks["sm_max_mhz"] * 1e6
+        peak = sms * 128 * 2 * clock / 1e12          # FP32 FMA lanes, 2 FLOP each
+        ach = flop / (kms * 1e-3) / 1e12
+        ops_peak = sms * 128 * clock / 1e12
+        ops_ach = ops / (kms * 1e-3) / 1e12
+        # DRAM traffic of one launch, scaled from a small-case ncu capture by
+        # the launch's units (bounce >= 1 closest-hit segments for the tail)
+        tr = _traffic(f"k_{dom}", "pt.cu")
+        traffic = None
+        if tr and dom == "tail" and tail_segments:
+            traffic = tr["dram_bytes_per_launch"] / tr["units"] * tail_segments / launches_per_frame
+        elif tr and dom != "tail":
+            traffic = tr["dram_bytes_per_launch"]
+        l2_gbs = None
+        if tr and tr.get("lts_bytes_per_launch") and dom == "tail" and tail_segments:
+            l2_gbs = (tr["lts_bytes_per_launch"] / tr["units"] * tail_segments) / (kms * 1e-3) / 1e9
+        l2_peak = l2_copy_gbs() if rank == 0 else None
         label = {"trace": "k_trace (closest-hit traversal, bounce 0)",
                  "shadow": "k_shadow (shadow-ray traversal, bounce 0)",
                  "tail": "k_tail (traversal, shading and shadow rays of bounces >= 1)"}[dom]
         roofline = {"kernel": label, "bound": "alu", "achieved": ach,
                     "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                    "traffic": _traffic(f"k_{dom}", "pt.cu"),
-                    "peak_source": f"{sms} SMs x 128 FP32 lanes x {peaks['sm_max_mhz']} MHz "
-                                   "(non-FMA ops; the kernel is built with --fmad=false)",
-                    "ops_per_frame": ops, "node_visits_per_frame": visits,
-                    "tri_tests_per_frame": tests,
-                    "l2": {"achieved_gbs": l2_gbs, "peak_gbs": l2_peak,
+                    "traffic": traffic,
+                    "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 FLOP (FMA) x "
+                                   f"{peaks['sm_max_mhz']} MHz",
+                    "flop_per_frame": flop, "flop_per_node_visit": FLOP_PER_NODE_VISIT,
+                    "flop_per_tri_test": FLOP_PER_TRI_TEST, "node_visits_per_frame": visits,
+                    "tri_tests_per_frame": tests, "kernel_ms_per_frame": kms,
+                    "launches_per_frame": launches_per_frame,
+                    "tail_segments_per_frame": tail_segments,
+                    "traffic_note": ("per launch, from one small-case ncu capture "
+                                     "(profiles/traffic.json) scaled by bounce >= 1 segments"
+                                     if traffic else "no capture of the current source"),
+                    "instruction_count": {"ops_per_frame": ops, "achieved_tops": ops_ach,
+                                          "peak_tops": ops_peak, "frac": ops_ach / ops_peak,
+                                          "note": "FP32 instructions counted from the source "
+                                                  "(52 per node visit, 50 per triangle test; "
+                                                  "--fmad=false) against the non-FMA issue rate"},
+                    "l2": {"achieved_gbs": l2_gbs, "copy_gbs": l2_peak,
                            "frac": l2_gbs / l2_peak if l2_gbs and l2_peak else None,
-                           "peak_source": "measured here: mrs_l2_read_probe, 64 MB L2-resident, "
-                                          "L2-only loads"}}
+                           "peak_source": "measured here: device copy between two 32 MB "
+                                          "L2-resident buffers, read + write bytes"}}
 
     if rank == 0:
         cpu = None
         if not args.quick and not args.no_cpu_baseline:
-            cms, detail = oracle_frame_sample(desc, cnn.kaiming(0), 2, 4, 4)
+            from oracle import cnn
+            cms, detail = oracle_frame_estimate(desc, cnn.kaiming(0))
             cpu = {"value": cms, "unit": "ms/frame", "cores": cpu_cores(), "kind": "oracle",
                    "sample": detail}
         line = {

@@ -107,10 +107,13 @@ mrs_status mrs_scene_export_bvh(mrs_scene scene, uint32_t* morton, int32_t* orde
  * routine) -- code running inside another allocator's callback, under a
  * memory-reservation regime that forbids new device allocations, or in a
  * hard real-time frame loop where an allocation could stall.  It builds the
- * same tree as mrs_build_scene (bit-identical outputs), from device inputs
- * into device outputs, with all scratch memory (about 7.5 MB) in one static
- * device array inside libmrs.so; every GPU that loads the library keeps that
- * array until the process exits.
+ * LBVH over all n triangles, bit-identical to what mrs_scene_export_bvh
+ * returns for a scene of the same triangles (not the tree mrs_render
+ * traverses, which leaves the few scene-sized triangles out of the LBVH and
+ * tests them apart), from device inputs into device outputs, with all
+ * scratch memory (about 7.5 MB) in one static device array inside
+ * libmrs.so; every GPU that loads the library keeps that array until the
+ * process exits.
  *
  * V      device float [n][3][3] triangle vertices
  * morton device uint32 [n], order device int32 [n], left/right device int32
@@ -118,15 +121,18 @@ mrs_status mrs_scene_export_bvh(mrs_scene scene, uint32_t* morton, int32_t* orde
  *        layouts as mrs_scene_export_bvh.
  * n must be <= MRS_LBVH_STATIC_MAX_TRIS, else MRS_ERR_CAPACITY with a message.
  * The first call on a device looks up the device address of the static array
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Calls share the one array: two calls whose work
- * overlaps on the GPU (different streams, or different host threads) race
- * and corrupt each other; serialise them.  Work is enqueued on `stream`. */
+ * (cudaGetSymbolAddress) with that device current and keeps it for the rest
+ * of the process; make that first call before any stream capture.  The kept
+ * address does not survive cudaDeviceReset (or an unload of the library):
+ * do not call this entry point on a device after resetting it.  Calls share
+ * the one array: two calls whose work overlaps on the GPU (different
+ * streams, or different host threads) race and corrupt each other;
+ * serialise them.  Work is enqueued on `stream`. */
 #define MRS_LBVH_STATIC_MAX_TRIS 262144
 mrs_status mrs_lbvh_build_static(const float* V, int32_t n, uint32_t* morton, int32_t* order,
                                  int32_t* left, int32_t* right, float* box, void* stream);
 
-/* Closest hit of n_rays rays through the LBVH/* Closest hit of n_rays rays through the LBVH: orig/dir device float [n][3];
+/* Closest hit of n_rays rays through the LBVH: orig/dir device float [n][3];
  * prim device int32 [n] (triangle index, -1 on miss), t device float [n]
  * (-1 on miss).  Ties in t go to the smaller triangle index. */
 mrs_status mrs_cast(mrs_scene scene, const float* orig, const float* dir, int32_t n_rays,
@@ -184,16 +190,6 @@ mrs_status mrs_render_stats(mrs_scene scene, int32_t W, int32_t H, int32_t spp, 
  * Instrumentation only. */
 mrs_status mrs_profile_enable(int32_t on);
 mrs_status mrs_profile_read(int32_t kernel, double* total_ms, int64_t* launches);
-
-/* L2 read-bandwidth probe (measurement only, no paper counterpart): reads the
- * `bytes` bytes of device buffer buf (16-byte aligned, bytes a positive
- * multiple of 16) `reps` times (1 .. 1000) with L2-only loads, 4 blocks of 256
- * threads per SM; sink is a device float[1] that is written only if the sum
- * of the data is -1 (never for finite non-negative data).  Timed by the
- * caller with events on `stream`: with buf smaller than the L2, bytes * reps
- * / time is the L2 read bandwidth that traversal L2 traffic is compared with. */
-mrs_status mrs_l2_read_probe(const void* buf, int64_t bytes, int32_t reps, float* sink,
-                             void* stream);
 
 /* Failure-detection self-test (no paper counterpart): launches a kernel whose
  * bounded device-side wait (the kind every tensor-core kernel uses on its
@@ -442,6 +438,32 @@ mrs_status mrs_net_set_loss(mrs_net net, int32_t loss, float beta);
 mrs_status mrs_conv3x3_wgrad(const float* x, const float* dy, int32_t N, int32_t H, int32_t W,
                              int32_t cin, int32_t cout, int32_t precision, float* dw, float* db,
                              void* stream);
+
+/* Input gradient of one 3x3 convolution with zero padding (the transposed
+ * convolution of the training step's backward pass), with the three
+ * epilogues that step applies:
+ *   g[p][c] = sum over o, ky, kx of dy[p - (ky - 1, kx - 1)][o] * w[o][ky][kx][c]
+ *             (zero outside the image)
+ *   MRS_DGRAD_LINEAR     out = g
+ *   MRS_DGRAD_RELU_MASK  out = aux > 0 ? g : 0   (aux = the ReLU output the
+ *                        gradient flows back through)
+ *   MRS_DGRAD_RESIDUAL   out = aux + g          (aux = the gradient already
+ *                        reaching this tensor along a residual skip)
+ * dy device float [N][H][W][cout]; w HOST float [cout][3][3][cin] (the forward
+ * layer's weights); aux device float [N][H][W][cin] (NULL for
+ * MRS_DGRAD_LINEAR); out device float [N][H][W][cin].  cin, cout in
+ * [1, 64]; N*H*W <= 2^26.  MRS_PREC_FP32 runs the FP32 step's SIMT
+ * transposed conv; MRS_PREC_BF16 the BF16 step's tensor-core one: dy, w and
+ * aux rounded to BF16, FP32 accumulation, the result rounded to BF16 (as the
+ * step stores it) and returned widened to float.  For testing each backward
+ * layer of mrs_train_step on its own.  Synchronises `stream`;
+ * MRS_ERR_TIMEOUT if a device wait gave up. */
+#define MRS_DGRAD_LINEAR 0
+#define MRS_DGRAD_RELU_MASK 1
+#define MRS_DGRAD_RESIDUAL 2
+mrs_status mrs_conv3x3_dgrad(const float* dy, int32_t N, int32_t H, int32_t W, int32_t cin,
+                             int32_t cout, const float* w, int32_t mode, const float* aux,
+                             int32_t precision, float* out, void* stream);
 
 /* ------------------------------------------------------------------------
  * The method's own fusion network (Sec. 4, Fig. network): a two-encoder-one-

@@ -64,7 +64,7 @@ def lib():
             L.orc_cast.argtypes = [P, i32, P, P, i32, i32, P, P]
             L.orc_cast.restype = i32
             L.orc_render.argtypes = [P, i32, P, P, P, P, i32, P, P, i32, i32, i32, i32, i32,
-                                     i32, u64, i32, i32, i32, P, P, P, P, P, P, P, P, P]
+                                     i32, u64, i32, i32, i32, i32, P, P, P, P, P, P, P, P, P]
             L.orc_render.restype = i32
             L.orc_num_threads.restype = i32
             L.orc_set_estimator.argtypes = [i32]
@@ -181,7 +181,8 @@ def render(scene, W, H, spp, max_depth, rr_start=None, seed=0, rows=None, thread
     depth[H,W], counts[max_depth+1], shadow_counts[max_depth+1]).
 
     rr_start=None disables Russian roulette.  rows=(r0, r1) renders only those
-    image rows (the result then has r1-r0 rows) -- used for bounded samples.
+    image rows (the result then has r1-r0 rows), rows=(r0, r1, step) only every
+    step-th of them -- used for bounded samples.
     grid=g > 1 samples each pixel only inside the centre sub-pixel of its g x g
     block (nearest-neighbour downsampling of a g-times finer render).
     Also returns the extra layers diffuse, specular and variance [H,W,3]:
@@ -194,8 +195,8 @@ def render(scene, W, H, spp, max_depth, rr_start=None, seed=0, rows=None, thread
     last two exist to test the first: all three estimate the same integral."""
     if rr_start is None:
         rr_start = 1 << 30
-    r0, r1 = (0, H) if rows is None else rows
-    h = r1 - r0
+    r0, r1, step = (0, H, 1) if rows is None else (tuple(rows) + (1,))[:3]
+    h = max(0, (r1 - r0 + step - 1) // step)
     out = {
         "radiance": np.zeros((h, W, 3), np.float32),
         "albedo": np.zeros((h, W, 3), np.float32),
@@ -212,7 +213,8 @@ def render(scene, W, H, spp, max_depth, rr_start=None, seed=0, rows=None, thread
     with _est_lock:
         L.orc_set_estimator(ESTIMATORS[estimator])
         try:
-            rc = _render_call(s, W, H, spp, max_depth, rr_start, grid, seed, r0, r1, threads, out)
+            rc = _render_call(s, W, H, spp, max_depth, rr_start, grid, seed, r0, r1, step, threads,
+                              out)
         finally:
             L.orc_set_estimator(0)
     if rc != 0:
@@ -220,10 +222,11 @@ def render(scene, W, H, spp, max_depth, rr_start=None, seed=0, rows=None, thread
     return out
 
 
-def _render_call(s, W, H, spp, max_depth, rr_start, grid, seed, r0, r1, threads, out):
+def _render_call(s, W, H, spp, max_depth, rr_start, grid, seed, r0, r1, step, threads, out):
     return lib().orc_render(_p(s["V"]), len(s["V"]), _p(s["tri_mat"]), _p(s["tri_light"]),
                           _p(s["mats"]), _p(s["lights"]), len(s["lights"]), _p(s["env"]),
-                          _p(s["cam"]), W, H, spp, max_depth, rr_start, grid, seed, r0, r1, threads,
+                          _p(s["cam"]), W, H, spp, max_depth, rr_start, grid, seed, r0, r1, step,
+                          threads,
                           _p(out["radiance"]), _p(out["albedo"]), _p(out["normal"]),
                           _p(out["depth"]), _p(out["diffuse"]), _p(out["specular"]),
                           _p(out["variance"]), _p(out["counts"]), _p(out["shadow_counts"]))

@@ -211,13 +211,27 @@ def loss_fn(pred, target, loss="l1log", beta=0.1):
     raise ValueError(f"unknown loss {loss!r}")
 
 
-def backward(params, acts, dy):
-    """Gradient of the loss w.r.t. the flat params, given dL/dI_SR."""
+def _abs_terms(x, dout):
+    """Sums of |terms| of a layer's weight and bias gradients: for dW[o,t,c]
+    sum_p |dout[p,o]| |x[p+t,c]|, for db[o] sum_p |dout[p,o]| (the scale of
+    their floating-point rounding error, for tolerances)."""
+    zero = np.zeros((dout.shape[3], 3, 3, x.shape[3]))
+    _, aw, ab = conv3x3_backward(np.abs(x), zero, np.abs(dout))
+    return aw, ab
+
+
+def backward(params, acts, dy, abs_terms=False):
+    """Gradient of the loss w.r.t. the flat params, given dL/dI_SR.  With
+    abs_terms, also the sum of |terms| of every gradient element, in the same
+    layout (see _abs_terms)."""
     L = unpack(params)
     grads = [None] * len(L)
+    scale = [None] * len(L)
     h = acts[f"h{N_BLOCKS}"]
     dh, dw, db = conv3x3_backward(h, L[-1][0], dy)
     grads[-1] = (dw, db)
+    if abs_terms:
+        scale[-1] = _abs_terms(h, dy)
     for k in reversed(range(N_BLOCKS)):
         r = acts[f"r{k}"]
         dr, dw2, db2 = conv3x3_backward(r, L[2 + 2 * k][0], dh)
@@ -226,18 +240,24 @@ def backward(params, acts, dy):
         hin = acts[f"h{k}"]
         dhin, dw1, db1 = conv3x3_backward(hin, L[1 + 2 * k][0], da)
         grads[1 + 2 * k] = (dw1, db1)
+        if abs_terms:
+            scale[2 + 2 * k] = _abs_terms(r, dh)
+            scale[1 + 2 * k] = _abs_terms(hin, da)
         dh = dh + dhin
     da0 = dh * (acts["pre0"] > 0.0)
     _, dw0, db0 = conv3x3_backward(acts["x0"], L[0][0], da0)
     grads[0] = (dw0, db0)
+    if abs_terms:
+        scale[0] = _abs_terms(acts["x0"], da0)
+        return pack(grads), pack(scale)
     return pack(grads)
 
 
 def loss_and_grad(params, lrhs, hrls, albedo, normal, target, s, loss="l1log", beta=0.1,
-                  extra=None):
+                  extra=None, abs_terms=False):
     y, acts = forward(params, lrhs, hrls, albedo, normal, s, keep=True, extra=extra)
     value, dy = loss_fn(y, target, loss, beta)
-    return value, backward(params, acts, dy)
+    return value, backward(params, acts, dy, abs_terms)
 
 
 def adam(params, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
@@ -250,13 +270,14 @@ def adam(params, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
 
 
 def train_step(params, m, v, step, lr, lrhs, hrls, albedo, normal, target, s, clip=100.0,
-               loss="l1log", beta=0.1, extra=None):
+               loss="l1log", beta=0.1, extra=None, abs_terms=False):
     """One training step as the method's learned part runs it: radiance inputs
     and target clipped at `clip` (firefly clipping, Sec. 3.2), the loss
     ("l1log", or "robust" = l_r with factor `beta`, Sec. 3), backward,
     bias-corrected Adam at step `step` (counting from 1).  The extra layers'
     diffuse and specular radiance are clipped like the HRLS.
-    Returns (new params, m, v, loss, grad)."""
+    Returns (new params, m, v, loss, grad), and with abs_terms also the sum of
+    |terms| of every gradient element (a rounding-error scale for tests)."""
     lr_c = np.minimum(np.asarray(lrhs, np.float64), clip)
     hr_c = np.minimum(np.asarray(hrls, np.float64), clip)
     tg_c = np.minimum(np.asarray(target, np.float64), clip)
@@ -264,8 +285,14 @@ def train_step(params, m, v, step, lr, lrhs, hrls, albedo, normal, target, s, cl
     if extra is not None:
         ex_c = np.asarray(extra, np.float64).copy()
         ex_c[..., :6] = np.minimum(ex_c[..., :6], clip)
-    value, grad = loss_and_grad(params, lr_c, hr_c, albedo, normal, tg_c, s, loss, beta, ex_c)
+    value, grad = loss_and_grad(params, lr_c, hr_c, albedo, normal, tg_c, s, loss, beta, ex_c,
+                                abs_terms)
+    scale = None
+    if abs_terms:
+        grad, scale = grad
     p1, m1, v1 = adam(params, grad, m, v, step, lr)
+    if abs_terms:
+        return p1, m1, v1, value, grad, scale
     return p1, m1, v1, value, grad
 
 

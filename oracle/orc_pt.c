@@ -806,12 +806,14 @@ static v3 trace_path(const scene_t* S, const rparams_t* P, int px, int py, int s
  * Aux buffers (albedo, facing normal, depth of the first hit; zero on a miss)
  * are plain float sums in sample order divided by spp.  counts[b] /
  * shadow_counts[b] (max_depth+1 entries each, may be NULL) receive the number
- * of extension / shadow rays cast at bounce b.  threads <= 0 -> all cores.
+ * of extension / shadow rays cast at bounce b.  Only rows row0, row0 +
+ * row_step, ... below row1 are rendered (output row i = image row row0 + i
+ * row_step): a bounded sample for timing.  threads <= 0 -> all cores.
  */
 int orc_render(const float* V, int n, const int32_t* tri_mat, const int32_t* tri_light,
                const float* mats, const float* lights, int n_lights, const float* env,
                const float* cam, int W, int H, int spp, int max_depth, int rr_start,
-               int grid, uint64_t seed, int row0, int row1, int threads,
+               int grid, uint64_t seed, int row0, int row1, int row_step, int threads,
                float* radiance, float* albedo, float* normal, float* depth,
                float* diffuse, float* specular, float* variance,
                uint64_t* counts, uint64_t* shadow_counts)
@@ -820,6 +822,8 @@ int orc_render(const float* V, int n, const int32_t* tri_mat, const int32_t* tri
     if (grid < 1 || grid > 64) return -1;
     if (row1 <= 0 || row1 > H) row1 = H;
     if (row0 < 0) row0 = 0;
+    if (row_step < 1) row_step = 1;
+    const int nrows = row1 > row0 ? (row1 - row0 + row_step - 1) / row_step : 0;
     scene_t S;
     if (scene_init(&S, V, n, tri_mat, tri_light, mats, lights, n_lights, env, cam)) {
         scene_free(&S);
@@ -838,7 +842,8 @@ int orc_render(const float* V, int n, const int32_t* tri_mat, const int32_t* tri
     {
         uint64_t cnt[64] = {0}, scnt[64] = {0};
 #pragma omp for schedule(dynamic, 1)
-        for (int py = row0; py < row1; ++py) {
+        for (int ri = 0; ri < nrows; ++ri) {
+            const int py = row0 + ri * row_step;
             for (int px = 0; px < W; ++px) {
                 float s0 = 0, s1 = 0, s2 = 0, c0 = 0, c1 = 0, c2 = 0;
                 v3 as = mk(0, 0, 0), ns = mk(0, 0, 0);
@@ -865,7 +870,7 @@ int orc_render(const float* V, int n, const int32_t* tri_mat, const int32_t* tri
                     ns = add(ns, nn);
                     ds = ds + dd;
                 }
-                size_t i = (size_t)(py - row0) * W + px;
+                size_t i = (size_t)ri * W + px;
                 float fs = (float)spp;
                 if (radiance) { radiance[3 * i] = s0 / fs; radiance[3 * i + 1] = s1 / fs; radiance[3 * i + 2] = s2 / fs; }
                 if (albedo) { albedo[3 * i] = as.x / fs; albedo[3 * i + 1] = as.y / fs; albedo[3 * i + 2] = as.z / fs; }

@@ -55,6 +55,7 @@ SIGS = {
     "mrs_train_step": [P, P, P, P, P, P, I32, I32, I32, I32, F32, I32, P, P],
     "mrs_train_step_extra": [P, P, P, P, P, P, P, I32, I32, I32, I32, F32, I32, P, P],
     "mrs_net_get_grads": [P, P],
+    "mrs_conv3x3_dgrad": [P, I32, I32, I32, I32, I32, P, I32, P, I32, P, P],
     "mrs_net_get_state": [P, P, P, P, P],
     "mrs_net_set_state": [P, P, P, P, I64],
     "mrs_gate": [P, P, P, I32, I32, I32, I32, F64, P, P, P, P],
@@ -68,7 +69,6 @@ SIGS = {
     "mrs_rdn_fuse": [P, P, P, P, P, P, I32, I32, I32, I32, P, P],
     "mrs_rdn_check": [P],
     "mrs_selftest_wait_timeout": [I32, P],
-    "mrs_l2_read_probe": [P, I64, I32, P, P],
     "mrs_status_string": [I32],
     "mrs_last_error": [],
     "mrs_kernel_launches": [],

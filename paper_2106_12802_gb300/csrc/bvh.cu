@@ -640,27 +640,6 @@ mrs_status static_scratch(unsigned char** out)
     return MRS_OK;
 }
 
-// L2 read probe: every thread reads 16-byte words of buf, grid-strided, reps
-// times, through L2 only (ld.global.cg); the sum is stored only if it is -1,
-// which never happens for finite non-negative data, so the loads stay
-__global__ void __launch_bounds__(256) k_l2_read(const float4* __restrict__ buf, int64_t n16,
-                                                 int reps, float* sink)
-{
-    float acc = 0.0f;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int r = 0; r < reps; ++r) {
-        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n16; i += 4 * stride) {
-            float4 v[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                v[u] = i + u * stride < n16 ? __ldcg(buf + i + u * stride) : make_float4(0, 0, 0, 0);
-#pragma unroll
-            for (int u = 0; u < 4; ++u) acc += (v[u].x + v[u].y) + (v[u].z + v[u].w);
-        }
-    }
-    if (acc == -1.0f) sink[0] = acc;
-}
-
 template <class T> mrs_status dalloc(T** p, size_t count)
 {
     *p = nullptr;
@@ -677,18 +656,6 @@ extern "C" const char* mrs_last_error(void) { return mrs::last_error(); }
 
 extern "C" uint64_t mrs_kernel_launches(void) { return mrs::launch_counter().load(); }
 
-extern "C" mrs_status mrs_l2_read_probe(const void* buf, int64_t bytes, int32_t reps, float* sink,
-                                        void* stream)
-{
-    MRS_ARG(buf != nullptr && sink != nullptr, "NULL buffer");
-    MRS_ARG(((uintptr_t)buf & 15) == 0, "buffer must be 16-byte aligned");
-    MRS_ARG(bytes >= 16 && bytes % 16 == 0, "bytes must be a positive multiple of 16");
-    MRS_ARG(reps >= 1 && reps <= 1000, "reps must be in [1, 1000]");
-    k_l2_read<<<4 * sm_count(), 256, 0, (cudaStream_t)stream>>>((const float4*)buf, bytes / 16, reps,
-                                                                sink);
-    MRS_LAUNCHED(1);
-    return cuda_status(cudaGetLastError(), "l2 probe launch");
-}
 
 extern "C" mrs_status mrs_profile_enable(int32_t on)
 {

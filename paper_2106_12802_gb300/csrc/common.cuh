@@ -80,14 +80,19 @@ struct Buf {
     template <class T> T* as() const { return static_cast<T*>(p); }
 };
 
+// SM count of the current device, looked up once per device (every thread
+// that races on a first lookup stores the same value)
 inline int sm_count()
 {
-    static int n = 0;
-    if (!n) {
-        int dev = 0;
-        cudaGetDevice(&dev);
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    int n = cache[dev].load(std::memory_order_relaxed);
+    if (n <= 0) {
         cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
         if (n <= 0) n = 1;
+        cache[dev].store(n, std::memory_order_relaxed);
     }
     return n;
 }

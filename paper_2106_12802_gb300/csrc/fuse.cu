@@ -646,6 +646,18 @@ __global__ void k_mask_bf16(__nv_bfloat16* __restrict__ d, const __nv_bfloat16* 
         if (!(__bfloat162float(act[i]) > 0.0f)) d[i] = __float2bfloat16_rn(0.0f);
 }
 
+// out[p][c] = float(o[p][c]) for c < cin from bf16 [P][64] rows
+__global__ void k_from_operand(const __nv_bfloat16* __restrict__ o, size_t P, int cin,
+                               float* __restrict__ out)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < P * cin;
+         i += (size_t)gridDim.x * blockDim.x) {
+        size_t p = i / cin;
+        int c = (int)(i % cin);
+        out[i] = __bfloat162float(o[p * 64 + c]);
+    }
+}
+
 struct Scratch {
     std::mutex mu;
     Buf b;
@@ -1638,6 +1650,90 @@ extern "C" mrs_status mrs_conv3x3_wgrad(const float* x, const float* dy, int32_t
     MRS_CHECK(cudaMemcpy(&herr, err, 4, cudaMemcpyDeviceToHost));
     if (herr) { cudaMemset(err, 0, 4); set_error("tensor-core weight-gradient wait timed out"); return MRS_ERR_TIMEOUT; }
     return MRS_OK;
+}
+
+extern "C" mrs_status mrs_conv3x3_dgrad(const float* dy, int32_t N, int32_t H, int32_t W,
+                                        int32_t cin, int32_t cout, const float* w, int32_t mode,
+                                        const float* aux, int32_t precision, float* out,
+                                        void* stream)
+{
+    using namespace mrs;
+    MRS_ARG(dy && w && out, "NULL pointer");
+    MRS_ARG(N >= 1 && H >= 1 && W >= 1, "sizes must be >= 1");
+    MRS_ARG(cin >= 1 && cin <= 64 && cout >= 1 && cout <= 64, "cin, cout must be in [1, 64]");
+    MRS_ARG(mode == MRS_DGRAD_LINEAR || mode == MRS_DGRAD_RELU_MASK || mode == MRS_DGRAD_RESIDUAL,
+            "unknown mode");
+    MRS_ARG(mode == MRS_DGRAD_LINEAR || aux != nullptr, "aux is required by this mode");
+    MRS_ARG(precision == MRS_PREC_FP32 || precision == MRS_PREC_BF16, "precision must be FP32 or BF16");
+    MRS_ARG((int64_t)N * H * W <= (int64_t(1) << 26), "more than 2^26 pixels");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t P = (size_t)N * H * W;
+    const size_t nw = (size_t)cout * 9 * cin;
+    Scratch& S = scratch();
+    std::lock_guard<std::mutex> g(S.mu);
+    const size_t opb = ((P * 128 + 1023) / 1024) * 1024;   // one bf16 [P][64] operand
+    size_t need = nw * 4 + 64 * 4 + 2048 + 9 * 64 * 64 * 4 + 1024 +
+                  (precision == MRS_PREC_BF16 ? 3 * opb : 0);
+    mrs_status rc = S.b.ensure(need);
+    if (rc != MRS_OK) return rc;
+    float* dw = S.b.as<float>();
+    float* zero = dw + nw;
+    uint8_t* q = (uint8_t*)(((uintptr_t)(zero + 64) + 1023) & ~(uintptr_t)1023);
+    MRS_CHECK(cudaMemcpyAsync(dw, w, nw * 4, cudaMemcpyHostToDevice, st));
+    MRS_CHECK(cudaMemsetAsync(zero, 0, 64 * 4, st));
+    if (precision == MRS_PREC_FP32) {
+        // the FP32 training step's transposed conv: flipped, transposed
+        // weights through the SIMT convolution with the step's epilogues
+        float* wt = (float*)q;
+        k_wtrans<<<(int)((nw + 255) / 256), 256, 0, st>>>(dw, cin, cout, wt);
+        MRS_LAUNCHED(1);
+        int sm = mode == MRS_DGRAD_LINEAR ? SIMT_PLAIN : mode == MRS_DGRAD_RELU_MASK ? SIMT_MASK : SIMT_RESID;
+        rc = conv_simt(dy, cout, wt, zero, cin, sm, 0, aux, out, nullptr, N, H, W, 1, st);
+        if (rc == MRS_OK) rc = cuda_status(cudaStreamSynchronize(st), "conv3x3 dgrad sync");
+        return rc;
+    }
+    // BF16: the tensor-core conv with the training step's transposed-weight
+    // packing and epilogue modes (linear; ReLU mask by the layer's output;
+    // residual added in place into the incoming gradient)
+    __nv_bfloat16* wp = (__nv_bfloat16*)q;
+    uint8_t* dyq = q + ((9 * 64 * 64 * 2 + 1023) / 1024) * 1024;
+    uint8_t* auxq = dyq + opb;
+    uint8_t* outq = auxq + opb;
+    static int* err = nullptr;
+    if (!err) { MRS_CHECK(cudaMalloc(&err, 4)); MRS_CHECK(cudaMemset(err, 0, 4)); }
+    k_pack_bf16_T<<<(9 * 64 * 64 + 255) / 256, 256, 0, st>>>(dw, 0, cin, cout, 64, wp);
+    MRS_LAUNCHED(1);
+    k_to_operand<<<1024, 256, 0, st>>>(dy, P, cout, dyq, 0, 1.0f);
+    MRS_LAUNCHED(1);
+    if (mode == MRS_DGRAD_RELU_MASK) {
+        k_to_operand<<<1024, 256, 0, st>>>(aux, P, cin, auxq, 0, 1.0f);
+        MRS_LAUNCHED(1);
+    } else if (mode == MRS_DGRAD_RESIDUAL) {
+        k_to_operand<<<1024, 256, 0, st>>>(aux, P, cin, outq, 0, 1.0f);
+        MRS_LAUNCHED(1);
+    }
+    CUtensorMap ma, mo, mr, mw;
+    if ((rc = tc_make_w_map(&mw, wp, 9 * 64, 64, TC_BF16)) != MRS_OK) return rc;
+    if ((rc = tc_make_act_map(&ma, dyq, N, H, W, TC_BF16, tc_a_box(TC_BF16))) != MRS_OK) return rc;
+    if ((rc = tc_make_act_map(&mo, outq, N, H, W, TC_BF16, tc_out_box(TC_BF16))) != MRS_OK) return rc;
+    if ((rc = tc_make_act_map(&mr, auxq, N, H, W, TC_BF16, tc_out_box(TC_BF16))) != MRS_OK) return rc;
+    TcConvArgs a;
+    memset(&a, 0, sizeof(a));
+    a.tmap_x = &ma; a.tmap_w = &mw; a.bias = zero; a.tmap_out = &mo;
+    a.N = N; a.H = H; a.W = W; a.scale = 1; a.nout = 64; a.operand = TC_BF16; a.err = err;
+    if (mode == MRS_DGRAD_LINEAR) { a.mode = TC_LIN_BF16; }
+    else if (mode == MRS_DGRAD_RELU_MASK) { a.mode = TC_MASK_BF16; a.tmap_res = &mr; }
+    else { a.mode = TC_RESID_BF16; a.tmap_res = &mo; }
+    if ((rc = tc_conv3x3(a, st)) != MRS_OK) return rc;
+    k_from_operand<<<1024, 256, 0, st>>>((const __nv_bfloat16*)outq, P, cin, out);
+    MRS_LAUNCHED(1);
+    rc = cuda_status(cudaStreamSynchronize(st), "conv3x3 dgrad sync");
+    int herr = 0;
+    if (rc == MRS_OK) {
+        MRS_CHECK(cudaMemcpy(&herr, err, 4, cudaMemcpyDeviceToHost));
+        if (herr) { cudaMemset(err, 0, 4); set_error("tensor-core conv wait timed out"); return MRS_ERR_TIMEOUT; }
+    }
+    return rc;
 }
 
 extern "C" mrs_status mrs_net_set_loss(mrs_net net, int32_t loss, float beta)

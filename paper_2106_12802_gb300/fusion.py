@@ -190,6 +190,31 @@ def conv3x3_wgrad(x, dy, precision="fp32", stream=None):
     return dw, db
 
 
+DGRAD_MODES = {"linear": 0, "relu_mask": 1, "residual": 2}
+
+
+def conv3x3_dgrad(dy, w, mode="linear", aux=None, precision="fp32", stream=None):
+    """Input gradient of a 3x3 conv with the training step's epilogue:
+    dy [N,H,W,cout] CUDA float32, w [cout,3,3,cin] numpy, aux [N,H,W,cin]
+    CUDA float32 (the ReLU output for "relu_mask", the incoming gradient for
+    "residual") -> out [N,H,W,cin] CUDA float32."""
+    _dev(dy, torch.float32)
+    N, H, W, cout = dy.shape
+    w = np.ascontiguousarray(w, np.float32)
+    if w.shape[0] != cout:
+        raise ValueError("w must be [cout, 3, 3, cin] with cout = dy.shape[3]")
+    cin = w.shape[3]
+    if aux is not None:
+        _dev(aux, torch.float32)
+        if tuple(aux.shape) != (N, H, W, cin):
+            raise ValueError("aux must be [N, H, W, cin]")
+    out = torch.empty((N, H, W, cin), dtype=torch.float32, device=dy.device)
+    call("mrs_conv3x3_dgrad", _ptr(dy), N, H, W, cin, cout, ctypes.c_void_p(w.ctypes.data),
+         DGRAD_MODES[mode], _ptr(aux) if aux is not None else None, _prec(precision), _ptr(out),
+         _stream(stream))
+    return out
+
+
 def image_metrics(x, ref, lam1=0.5, lam2=0.01, stream=None):
     """(sRGB PSNR, RelMSE, linear MSE) reduced in float64 on the GPU."""
     _dev(x, torch.float32)

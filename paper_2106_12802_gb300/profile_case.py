@@ -1,17 +1,27 @@
-"""Small, self-contained cases of the hot kernels for profilers (ncu).
+"""Small, self-contained cases of the hot kernels, for profilers (ncu).
+
+This is the package's profiling entry point: every command recorded under
+profiles/ runs one of these cases.
 
   python -m paper_2106_12802_gb300.profile_case fuse   --size 1024 --prec bf16
-  python -m paper_2106_12802_gb300.profile_case render --size 256 --spp 4
+  python -m paper_2106_12802_gb300.profile_case render --size 512 --spp 4
   python -m paper_2106_12802_gb300.profile_case rdn    --size 1024 --prec bf16
+  python -m paper_2106_12802_gb300.profile_case train  --batch 16 --crop 128
 
-`fuse` runs the x4 fusion network once at size x size output (inputs random,
+`fuse` runs the x4 fusion network at size x size output (inputs random,
 Kaiming weights); `rdn` the method's own x4 two-encoder network (the same);
-`render` renders the 200k-triangle procedural scene once.
-Each case runs one warm-up call first, so the profiled launches are steady-state.
+`render` renders the 200k-triangle procedural scene (seed 0, depth 8, roulette
+from bounce 3) and prints its per-bounce ray counts, whose bounce >= 1 part is
+the number of closest-hit segments the tail kernel traces (the unit that a
+traffic capture of one tail launch is divided by); `train` runs BF16 training
+steps of the fusion network on a random batch.  Each case runs one warm-up
+call first, so the second call's launches are steady-state (ncu: skip the
+first call's launches with -s).
 """
 from __future__ import annotations
 
 import argparse
+import json
 import os
 import sys
 
@@ -20,11 +30,13 @@ import numpy as np
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["fuse", "render", "rdn"])
+    ap.add_argument("case", choices=["fuse", "render", "rdn", "train"])
     ap.add_argument("--size", type=int, default=1024)
     ap.add_argument("--prec", default="bf16")
     ap.add_argument("--spp", type=int, default=4)
     ap.add_argument("--depth", type=int, default=8)
+    ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--crop", type=int, default=128)
     a = ap.parse_args(argv)
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     import torch
@@ -58,12 +70,27 @@ def main(argv=None):
         torch.cuda.synchronize()
         net.check()
         print("rdn ok", float(out.abs().mean()))
+    elif a.case == "train":
+        from paper_2106_12802_gb300 import trainer
+        s = 4
+        N, c = a.batch, a.crop
+        g = torch.Generator(device="cuda").manual_seed(11)
+        t = [torch.rand((N, c // s, c // s, 3), device="cuda", generator=g) * 2] + \
+            [torch.rand((N, c, c, 3), device="cuda", generator=g) for _ in range(4)]
+        net = mrs.Net(trainer.init_params(0))
+        for _ in range(2):
+            loss = mrs.train_step(net, *t, s, lr=1e-4, precision=a.prec)
+        print("train ok", loss)
     else:
         sc = mrs.Scene(scenes.procedural(0))
         for _ in range(2):
             r = mrs.render(sc, a.size, a.size, a.spp, a.depth, rr_start=3, seed=0)
         torch.cuda.synchronize()
-        print("render ok", float(r["radiance"].mean()))
+        counts = r["counts"].cpu().numpy().astype(np.int64)
+        print(json.dumps({"render": [a.size, a.size, a.spp, a.depth],
+                          "mean": float(r["radiance"].mean()),
+                          "counts": counts.tolist(),
+                          "tail_segments": int(counts[1:].sum())}))
     return 0
 
 

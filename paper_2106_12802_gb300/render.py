@@ -209,30 +209,6 @@ def profile_enable(on=True):
     call("mrs_profile_enable", int(bool(on)))
 
 
-def l2_read_gbs(megabytes=64, reps=20, trials=5, stream=None):
-    """L2 read bandwidth in GB/s (mrs_l2_read_probe over an L2-resident buffer
-    of `megabytes` MB, read `reps` times per launch; median of `trials`
-    event-timed launches after one warm-up)."""
-    dev = torch.device("cuda")
-    buf = torch.ones(megabytes * (1 << 20) // 4, dtype=torch.float32, device=dev)
-    sink = torch.zeros(1, dtype=torch.float32, device=dev)
-    st = stream if stream is not None else torch.cuda.current_stream()
-    args = (_ptr(buf), buf.numel() * 4, int(reps), _ptr(sink), _stream(st))
-    call("mrs_l2_read_probe", *args)
-    ts = []
-    for _ in range(trials):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(st)
-        call("mrs_l2_read_probe", *args)
-        e1.record(st)
-        e1.synchronize()
-        ts.append(e0.elapsed_time(e1))
-    ts.sort()
-    ms = ts[len(ts) // 2]
-    assert float(sink.item()) == 0.0
-    return buf.numel() * 4 * reps / (ms * 1e-3) / 1e9
-
-
 def profile_read():
     """{kernel family: (total ms, launches)} since the last read (synchronises)."""
     out = {}

@@ -65,14 +65,6 @@ def test_invalid_arguments_rejected_without_cuda(lib):
     # tail-kernel switch: NULL handles, out-of-range bounce
     assert lib.mrs_scene_set_tail(None, 1) == -1
     assert lib.mrs_ctx_set_tail(None, 1) == -1
-    # L2 probe: NULL buffer, size not a multiple of 16, reps out of range
-    assert lib.mrs_l2_read_probe(None, 64, 1, None, None) == -1
-    buf = ctypes.create_string_buffer(64 + 16)
-    base = (ctypes.addressof(buf) + 15) & ~15
-    sink = ctypes.c_float()
-    assert lib.mrs_l2_read_probe(ctypes.c_void_p(base), 60, 1, ctypes.byref(sink), None) == -1
-    assert lib.mrs_l2_read_probe(ctypes.c_void_p(base), 64, 0, ctypes.byref(sink), None) == -1
-    assert lib.mrs_l2_read_probe(ctypes.c_void_p(base + 4), 64, 1, ctypes.byref(sink), None) == -1
 
 
 def test_rdn_host_helpers_match_the_oracle_layout():

@@ -2,7 +2,7 @@
 against the float64 oracle, through the C ABI.
 
 Tolerances:
-* FP32 SIMT path: max |gpu - oracle| <= 1e-5 * max(1, max |oracle|).
+* FP32 SIMT path: max |gpu - oracle| <= 1e-5 (absolute, the stated bar).
 * Tensor-core layers (BF16 / FP8 operands, FP32 accumulation): the oracle is
   evaluated on the *same rounded operands*, so the only difference is the
   order and rounding of the FP32 accumulation over K = 9 * 64 terms; the bound
@@ -57,7 +57,7 @@ def test_conv_fp32_matches_oracle(mrs, N, H, W, cin, cout, relu):
     ref = cnn.conv3x3(x, w.astype(np.float64), b.astype(np.float64))
     if relu:
         ref = np.maximum(ref, 0)
-    assert np.abs(got - ref).max() <= 1e-5 * max(1.0, np.abs(ref).max())
+    assert np.abs(got - ref).max() <= 1e-5, np.abs(got - ref).max()
 
 
 @pytest.mark.parametrize("N,H,W,cin,cout,relu", [(2, 9, 150, 64, 64, 1), (1, 5, 128, 12, 64, 0),
@@ -127,7 +127,7 @@ def test_fuse_fp32_matches_oracle(mrs, N, h, w, s):
     net = mrs.Net(p)
     got = net.fuse(*_cuda(lr, hr, alb, nrm), s, precision="fp32").cpu().numpy()
     ref = cnn.forward(p.astype(np.float64), lr, hr, alb, nrm, s)
-    assert np.abs(got - ref).max() <= 1e-5 * max(1.0, np.abs(ref).max())
+    assert np.abs(got - ref).max() <= 1e-5, np.abs(got - ref).max()
 
 
 @pytest.mark.parametrize("prec,min_psnr", [("bf16", 45.0), ("fp8", 28.0)])
@@ -183,7 +183,7 @@ def test_fuse_full_size_sampled_window(mrs, prec):
         ref = _crop_oracle(p, lr, hr, alb, nrm, s, y0, x0, 32)
         g = got[:, y0:y0 + 32, x0:x0 + 32]
         if prec == "fp32":
-            assert np.abs(g - ref).max() <= 1e-5 * max(1.0, np.abs(ref).max())
+            assert np.abs(g - ref).max() <= 1e-5, np.abs(g - ref).max()
         else:
             mse = np.mean((g - ref) ** 2)
             assert 10 * np.log10(np.ptp(ref) ** 2 / mse) >= 45.0

@@ -4,7 +4,6 @@ words, Morton codes, tree topology, per-bounce ray counts) must be bit-exact;
 radiance must agree within 1e-4 relative on >= 99.9% of pixels with the image
 mean within 1e-5 relative (both sides evaluate the same float32 operations in
 the same order, so in practice they are identical)."""
-import ctypes
 
 import numpy as np
 import pytest
@@ -273,17 +272,3 @@ def test_concurrent_render_contexts_match_sequential(mrs):
     for k in seq_a:
         assert torch.equal(a[k], seq_a[k]), k
         assert torch.equal(b[k], seq_b[k]), k
-
-
-def test_l2_read_probe(mrs):
-    # measurement helper: a finite positive rate, the sink left alone, bad
-    # arguments refused before any launch
-    gbs = mrs.l2_read_gbs(megabytes=16, reps=4, trials=3)
-    assert np.isfinite(gbs) and gbs > 0
-    from paper_2106_12802_gb300 import _lib
-    buf = torch.ones(1024, dtype=torch.float32, device="cuda")
-    sink = torch.zeros(1, dtype=torch.float32, device="cuda")
-    for nbytes, reps in ((4 * 1024 - 4, 1), (0, 1), (4 * 1024, 0)):
-        with pytest.raises(Exception):
-            _lib.call("mrs_l2_read_probe", ctypes.c_void_p(buf.data_ptr()), nbytes, reps,
-                      ctypes.c_void_p(sink.data_ptr()), None)

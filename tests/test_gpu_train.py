@@ -2,10 +2,18 @@
 Adam) against the float64 oracle, through the C ABI.
 
 Tolerances: the GPU step runs in FP32 (SIMT convolutions), the oracle in
-float64; per layer the gradient must agree to 1e-4 in relative L2 norm, the
-loss to 1e-6 relative, and the Adam update to 1% of lr where the oracle
+float64.  Every weight and bias gradient element must agree within 1e-4 of
+the sum of |terms| of that element (sum over pixels of |dout| |x|, from the
+oracle): the rounding of the FP32 activations, activation gradients and
+accumulations of the whole step stays far below it, while a wrong tap,
+channel, pixel or mask gives errors of the order of the terms.  The loss must
+agree to 1e-6 relative and the Adam update to 1% of lr where the oracle
 gradient is not tiny (the first Adam step is lr * g / (|g| + eps): where
-|g| ~ eps its direction is ill-conditioned)."""
+|g| ~ eps its direction is ill-conditioned).  The BF16 step rounds every
+activation to BF16 between layers (the precision choice itself); each of its
+backward convolutions is checked element by element on its own
+(test_gpu_dgrad.py, test_gpu_wgrad.py), and the whole step here by cosine
+similarity to the float64 gradient."""
 import numpy as np
 import pytest
 
@@ -49,6 +57,15 @@ def _cuda(*a):
     return [torch.from_numpy(np.ascontiguousarray(t)).cuda() for t in a]
 
 
+def _assert_grads_elementwise(g, rg, terms):
+    err = np.abs(g.astype(np.float64) - rg)
+    bound = 1e-4 * terms + 1e-12
+    for li, (wo, bo, ci, co) in enumerate(cnn.layer_offsets()):
+        for a, b in ((wo, bo), (bo, bo + co)):
+            e, t = err[a:b], bound[a:b]
+            assert (e <= t).all(), (li, a, (e / t).max())
+
+
 @pytest.mark.parametrize("N,h,w,s", [(2, 4, 6, 4), (1, 8, 8, 2)])
 def test_train_step_gradients_and_update_match_oracle(mrs, N, h, w, s):
     lr, hr, alb, nrm, tgt = _batch(1, N, h, w, s)
@@ -58,13 +75,10 @@ def test_train_step_gradients_and_update_match_oracle(mrs, N, h, w, s):
     g = mrs.get_grads(net)
     p1 = net.get_params()
     z = np.zeros(mrs.NPARAMS)
-    rp, _, _, rloss, rg = cnn.train_step(p.astype(np.float64), z, z, 1, 1e-3, lr, hr, alb, nrm, tgt, s)
+    rp, _, _, rloss, rg, terms = cnn.train_step(p.astype(np.float64), z, z, 1, 1e-3, lr, hr, alb,
+                                                nrm, tgt, s, abs_terms=True)
     assert abs(loss - rloss) <= 1e-6 * rloss
-    for li, (wo, bo, ci, co) in enumerate(cnn.layer_offsets()):
-        for a, b in ((wo, bo), (bo, bo + co)):
-            ref = rg[a:b]
-            err = np.linalg.norm(g[a:b] - ref) / max(np.linalg.norm(ref), 1e-30)
-            assert err < 1e-4, (li, a, err)
+    _assert_grads_elementwise(g, rg, terms)
     ok = np.abs(rg) > 1e-6
     assert np.abs((p1 - p) - (rp - p))[ok].max() <= 0.01 * 1e-3
 
@@ -98,8 +112,10 @@ def test_checkpoint_resume_is_bit_identical(mrs, tmp_path):
 
 
 def test_bf16_train_step_gradients_close_to_oracle(mrs):
-    # BF16 activations / activation gradients with FP32 accumulation: every
-    # layer's gradient stays within a few per cent of the float64 gradient
+    # whole-step summary: BF16 activations / activation gradients with FP32
+    # accumulation keep every layer's gradient within a few per cent of the
+    # float64 gradient (each backward conv is checked element by element in
+    # test_gpu_dgrad.py and test_gpu_wgrad.py)
     lr, hr, alb, nrm, tgt = _batch(4, 2, 8, 16, 4)
     p = _params(3)
     net = mrs.Net(p)
@@ -135,14 +151,11 @@ def test_robust_loss_train_step_matches_oracle(mrs, N, h, w, s):
     g = mrs.get_grads(net)
     p1 = net.get_params()
     z = np.zeros(mrs.NPARAMS)
-    rp, _, _, rloss, rg = cnn.train_step(p.astype(np.float64), z, z, 1, 1e-3, lr, hr, alb, nrm, tgt, s,
-                                         loss="robust", beta=0.1)
+    rp, _, _, rloss, rg, terms = cnn.train_step(p.astype(np.float64), z, z, 1, 1e-3, lr, hr, alb,
+                                                nrm, tgt, s, loss="robust", beta=0.1,
+                                                abs_terms=True)
     assert abs(loss - rloss) <= 1e-6 * rloss
-    for li, (wo, bo, ci, co) in enumerate(cnn.layer_offsets()):
-        for a, b in ((wo, bo), (bo, bo + co)):
-            ref = rg[a:b]
-            err = np.linalg.norm(g[a:b] - ref) / max(np.linalg.norm(ref), 1e-30)
-            assert err < 1e-4, (li, a, err)
+    _assert_grads_elementwise(g, rg, terms)
     ok = np.abs(rg) > 1e-6
     assert np.abs((p1 - p) - (rp - p))[ok].max() <= 0.01 * 1e-3
 

@@ -119,6 +119,9 @@ def test_rows_and_threads_do_not_change_results(orc):
     assert np.array_equal(full["radiance"], one["radiance"])
     assert np.array_equal(full["radiance"][5:9], part["radiance"])
     assert np.array_equal(full["counts"], one["counts"])
+    strided = orc.render(sc, 16, 16, 4, 3, seed=9, rows=(1, 16, 5), threads=3)
+    assert np.array_equal(full["radiance"][1::5], strided["radiance"])
+    assert np.array_equal(full["depth"][1::5], strided["depth"])
 
 
 def test_seed_changes_estimate(orc):
