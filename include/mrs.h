@@ -42,6 +42,8 @@ typedef int32_t mrs_status;
 #define MRS_ERR_TIMEOUT (-4)   /* a bounded device-side wait gave up */
 #define MRS_ERR_CAPACITY (-5)  /* a size exceeds a documented capacity */
 #define MRS_ERR_STATE (-6)     /* handle used in the wrong state */
+#define MRS_ERR_FORMAT (-7)    /* a file is not a valid checkpoint (magic, size, checksum) */
+#define MRS_ERR_IO (-8)        /* a file could not be opened, read or written */
 
 typedef struct mrs_scene_s* mrs_scene;
 typedef struct mrs_net_s* mrs_net;
@@ -82,6 +84,39 @@ mrs_status mrs_build_scene(const float* V, int32_t n_tris, const int32_t* tri_ma
                            const int32_t* tri_light, const float* mats, int32_t n_mats,
                            const float* lights, int32_t n_lights, const float* env,
                            const float* cam, void* stream, mrs_scene* out);
+
+/* Seeded scene + LBVH: the scene is generated on the host from (seed, kind,
+ * params) -- the workloads this library is measured on; the paper's scenes
+ * are Blender scenes (Sec. 3.1) that these procedural stand-ins replace --
+ * and then built exactly as mrs_build_scene builds the arrays it is given.
+ *   MRS_SCENE_CORNELL     Cornell box: 5 Lambertian quads (white 0.75,
+ *                         red / green 0.6), a Lambert and a GGX (alpha 0.3)
+ *                         icosphere of radius 0.25 (subdivision
+ *                         params->sphere_subdiv), one 0.5 x 0.5 quad light of
+ *                         Le 15; no environment; seed unused
+ *   MRS_SCENE_PROCEDURAL  ground quad 30 x 30 (Lambert 0.5) with
+ *                         params->n_spheres icospheres of radius U(0.1, 1)
+ *                         displaced by value noise (amplitude 0.2 r), the
+ *                         n_large largest at subdivision 4 and the rest at 3,
+ *                         50/50 Lambert / GGX with alpha U(0.05, 1) and albedo
+ *                         U(0.1, 0.9); 3 downward quad lights of Le U(5, 20);
+ *                         environment 0.5 (the defaults give 200,968 triangles)
+ * params (HOST, may be NULL: n_spheres 64, n_large 31, sphere_subdiv 4,
+ * aspect 1) -- n_spheres in [1, 4096], n_large in [0, n_spheres],
+ * sphere_subdiv in [0, 6], aspect (camera width / height) in (0, 16], else
+ * MRS_ERR_ARG.  Random numbers are one splitmix64 stream seeded from `seed`;
+ * the generator uses integer and IEEE arithmetic only, so a seed gives the
+ * same scene on every host.  Synchronises `stream` like mrs_build_scene. */
+#define MRS_SCENE_CORNELL 0
+#define MRS_SCENE_PROCEDURAL 1
+typedef struct {
+    int32_t n_spheres;
+    int32_t n_large;
+    int32_t sphere_subdiv;
+    float aspect;
+} mrs_scene_params;
+mrs_status mrs_build_scene_seeded(uint64_t seed, int32_t kind, const mrs_scene_params* params,
+                                  void* stream, mrs_scene* out);
 
 /* Re-run the GPU LBVH build (Morton codes, sort, radix tree, refit) over the
  * scene's resident triangles, asynchronously on `stream`. */
@@ -368,6 +403,37 @@ mrs_status mrs_net_get_state(mrs_net net, float* params, float* adam_m, float* a
                              int64_t* step);
 mrs_status mrs_net_set_state(mrs_net net, const float* params, const float* adam_m,
                              const float* adam_v, int64_t step);
+
+/* Checkpoint / resume to a file (the paper keeps the best model during
+ * training, Sec. 4 "Implement details"; the file format is this library's).
+ * mrs_net_save writes the FP32 master weights, both Adam moments, the Adam
+ * step, the training loss (kind and beta) and the caller's `seed` (e.g. the
+ * data-sampling seed, returned by mrs_net_load so that a resumed run draws
+ * the same batches) to `path`: a 64-byte little-endian header
+ *   "MRSNETv2", uint32 64, uint32 2, int64 n_params, int64 step,
+ *   uint64 seed, int32 input channels (12 / 21), int32 loss, float beta,
+ *   uint32 0, uint64 FNV-1a-64 checksum of the payload
+ * then params, adam_m, adam_v as float32 [n_params] each.  The file is
+ * written to `path`.tmp and renamed over `path`.  mrs_net_load restores such
+ * a file into a net of the same parameter count (MRS_ERR_FORMAT on a wrong
+ * magic, version, size, loss or checksum, or trailing bytes; MRS_ERR_IO if
+ * the file cannot be read; the net is left unchanged on any error); seed
+ * (HOST, may be NULL) receives the stored seed.  Both synchronise the
+ * device.  Resuming from a file continues bit-identically to a run that was
+ * never interrupted. */
+mrs_status mrs_net_save(mrs_net net, const char* path, uint64_t seed);
+mrs_status mrs_net_load(mrs_net net, const char* path, uint64_t* seed);
+
+/* A net with seeded initial weights instead of caller-given ones:
+ * input_channels 12 (MRS_NET_NPARAMS) or 21 (MRS_NET_NPARAMS_EXTRA); every
+ * conv weight zero-mean with the Kaiming variance 2 / (9 Cin), drawn as the
+ * sum of 12 splitmix64 uniforms minus 6 (integer and IEEE arithmetic only:
+ * the same seed gives the same weights on every host); the second conv of
+ * each residual block scaled by resid_gain (in [0, 1]); the 3-channel head
+ * and every bias zero, so the untrained net outputs the upsampled LRHS
+ * exactly (training starts from the method without the network). */
+mrs_status mrs_net_create_seeded(int32_t input_channels, uint64_t init_seed, float resid_gain,
+                                 mrs_net* out);
 
 /* Image error metrics of x against ref (device float, n values each, both in
  * scene-linear space), reduced in float64 on the GPU (Sec. 5):

@@ -24,6 +24,7 @@ F64 = ctypes.c_double
 # name -> argtypes (restype is always int32 mrs_status unless listed in _RES)
 SIGS = {
     "mrs_build_scene": [P, I32, P, P, P, I32, P, I32, P, P, P, P],
+    "mrs_build_scene_seeded": [U64, I32, P, P, P],
     "mrs_scene_rebuild": [P, P],
     "mrs_scene_update_vertices": [P, P, I32, P],
     "mrs_free_scene": [P],
@@ -56,6 +57,9 @@ SIGS = {
     "mrs_train_step_extra": [P, P, P, P, P, P, P, I32, I32, I32, I32, F32, I32, P, P],
     "mrs_net_get_grads": [P, P],
     "mrs_conv3x3_dgrad": [P, I32, I32, I32, I32, I32, P, I32, P, I32, P, P],
+    "mrs_net_save": [P, ctypes.c_char_p, U64],
+    "mrs_net_load": [P, ctypes.c_char_p, P],
+    "mrs_net_create_seeded": [I32, U64, F32, P],
     "mrs_net_get_state": [P, P, P, P, P],
     "mrs_net_set_state": [P, P, P, P, I64],
     "mrs_gate": [P, P, P, I32, I32, I32, I32, F64, P, P, P, P],

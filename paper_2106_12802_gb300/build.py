@@ -34,8 +34,15 @@ def nvcc() -> str:
     return p
 
 
+# the seeded scene generator shared with the test side (host C, compiled by
+# gcc with -ffp-contract=off: the same scenes on every host)
+SYNTH = os.path.join(os.path.dirname(HERE), "synth")
+HOST_UNITS = {"scenegen.c": ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC"]}
+
+
 def _sources():
     srcs = [os.path.join(CSRC, u) for u in UNITS]
+    srcs += [os.path.join(SYNTH, u) for u in HOST_UNITS] + [os.path.join(SYNTH, "scenegen.h")]
     return srcs + [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
 
 
@@ -64,8 +71,17 @@ def build(force: bool = False, verbose: bool = False) -> str:
             raise RuntimeError(f"nvcc failed on {u}:\n{r.stdout}\n{r.stderr}")
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
-        objs = list(ex.map(compile_unit, UNITS))
+    def compile_host(u):
+        obj = os.path.join(OUT, u.replace(".c", ".host.o"))
+        cmd = ["gcc", *HOST_UNITS[u], "-c", os.path.join(SYNTH, u), "-o", obj]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"gcc failed on {u}:\n{r.stdout}\n{r.stderr}")
+        return obj
+
+    with cf.ThreadPoolExecutor(max_workers=len(UNITS) + len(HOST_UNITS)) as ex:
+        host = [ex.submit(compile_host, u) for u in HOST_UNITS]
+        objs = list(ex.map(compile_unit, UNITS)) + [f.result() for f in host]
     tmp = SO + f".{os.getpid()}.tmp"
     cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)

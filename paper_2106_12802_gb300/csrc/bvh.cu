@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "../../synth/scenegen.h"
 
 namespace mrs {
 
@@ -694,8 +695,40 @@ extern "C" const char* mrs_status_string(mrs_status s)
     case MRS_ERR_TIMEOUT: return "device wait timed out";
     case MRS_ERR_CAPACITY: return "capacity exceeded";
     case MRS_ERR_STATE: return "invalid handle state";
+    case MRS_ERR_FORMAT: return "invalid checkpoint file";
+    case MRS_ERR_IO: return "file I/O error";
     default: return "unknown status";
     }
+}
+
+extern "C" mrs_status mrs_build_scene_seeded(uint64_t seed, int32_t kind,
+                                             const mrs_scene_params* params, void* stream,
+                                             mrs_scene* out)
+{
+    MRS_ARG(out != nullptr, "out is NULL");
+    *out = nullptr;
+    MRS_ARG(kind == MRS_SCENE_CORNELL || kind == MRS_SCENE_PROCEDURAL, "unknown scene kind");
+    synth_scene_params p;
+    synth_default_params(&p);
+    if (params) {
+        p.n_spheres = params->n_spheres;
+        p.n_large = params->n_large;
+        p.sphere_subdiv = params->sphere_subdiv;
+        p.aspect = params->aspect;
+    }
+    const int sk = kind == MRS_SCENE_CORNELL ? SYNTH_CORNELL : SYNTH_PROCEDURAL;
+    int32_t nt = 0, nm = 0, nl = 0;
+    MRS_ARG(synth_scene_counts(sk, &p, &nt, &nm, &nl) == 0, "scene parameters out of range");
+    std::vector<float> V((size_t)nt * 9), mats((size_t)nm * 8), lights((size_t)nl * 12 + 1);
+    std::vector<int32_t> tri_mat(nt), tri_light(nt);
+    float env[3], cam[12];
+    if (synth_scene_generate(seed, sk, &p, V.data(), tri_mat.data(), tri_light.data(), mats.data(),
+                             lights.data(), env, cam) != 0) {
+        set_error("scene generation failed");
+        return MRS_ERR_ARG;
+    }
+    return mrs_build_scene(V.data(), nt, tri_mat.data(), tri_light.data(), mats.data(), nm,
+                           lights.data(), nl, env, cam, stream, out);
 }
 
 extern "C" mrs_status mrs_build_scene(const float* V, int32_t n, const int32_t* tri_mat,

@@ -9,9 +9,11 @@
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 #include <math.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
+#include <string>
 #include <mutex>
 #include <vector>
 
@@ -1551,6 +1553,157 @@ extern "C" mrs_status mrs_net_set_state(mrs_net net, const float* params, const 
     net->step = step;
     net->bf_valid = net->f8_valid = net->xscale_valid = net->bfT_valid = false;
     return MRS_OK;
+}
+
+// ---- checkpoints and seeded initialisation ----------------------------------
+namespace mrs {
+namespace {
+
+static_assert(__BYTE_ORDER__ == __ORDER_LITTLE_ENDIAN__, "checkpoint I/O assumes a little-endian host");
+
+constexpr char kCkptMagic[8] = {'M', 'R', 'S', 'N', 'E', 'T', 'v', '2'};
+constexpr uint32_t kCkptVersion = 2;
+
+// header of a checkpoint file (64 bytes, little-endian, no padding)
+struct CkptHeader {
+    char magic[8];
+    uint32_t header_bytes;   // 64
+    uint32_t version;        // 2
+    int64_t n_params;
+    int64_t step;
+    uint64_t seed;           // the caller's data / RNG seed, stored for resume
+    int32_t input_channels;  // 12 or 21
+    int32_t loss;            // MRS_LOSS_*
+    float beta;
+    uint32_t reserved;
+    uint64_t checksum;       // FNV-1a 64 over the three float arrays' bytes
+};
+static_assert(sizeof(CkptHeader) == 64, "checkpoint header layout");
+
+uint64_t fnv1a(uint64_t h, const void* data, size_t n)
+{
+    const unsigned char* p = (const unsigned char*)data;
+    for (size_t i = 0; i < n; ++i) { h ^= p[i]; h *= 0x100000001B3ull; }
+    return h;
+}
+
+// splitmix64 (Steele, Lea, Flood 2014): the initialiser's uniform stream
+uint64_t splitmix64(uint64_t& x)
+{
+    uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// zero-mean, unit-variance approximately normal draw: the sum of 12
+// uniforms minus 6 (Irwin-Hall), integer and IEEE arithmetic only, so that
+// the same seed gives the same weights on every host
+double normal12(uint64_t& x)
+{
+    double s = 0.0;
+    for (int i = 0; i < 12; ++i) s += (double)(splitmix64(x) >> 11) * (1.0 / 9007199254740992.0);
+    return s - 6.0;
+}
+
+}  // namespace
+}  // namespace mrs
+
+extern "C" mrs_status mrs_net_save(mrs_net net, const char* path, uint64_t seed)
+{
+    using namespace mrs;
+    MRS_ARG(net != nullptr && path != nullptr, "NULL argument");
+    std::vector<float> host(3 * net->np);
+    int64_t step = 0;
+    mrs_status rc = mrs_net_get_state(net, host.data(), host.data() + net->np,
+                                      host.data() + 2 * net->np, &step);
+    if (rc != MRS_OK) return rc;
+    CkptHeader h;
+    memset(&h, 0, sizeof(h));
+    memcpy(h.magic, kCkptMagic, 8);
+    h.header_bytes = sizeof(CkptHeader);
+    h.version = kCkptVersion;
+    h.n_params = (int64_t)net->np;
+    h.step = step;
+    h.seed = seed;
+    h.input_channels = net->cin0;
+    h.loss = net->loss_kind;
+    h.beta = net->loss_beta;
+    h.checksum = fnv1a(0xCBF29CE484222325ull, host.data(), host.size() * 4);
+    std::string tmp = std::string(path) + ".tmp";
+    FILE* f = fopen(tmp.c_str(), "wb");
+    if (!f) { set_error("cannot open %s for writing", tmp.c_str()); return MRS_ERR_IO; }
+    bool ok = fwrite(&h, sizeof(h), 1, f) == 1 && fwrite(host.data(), 4, host.size(), f) == host.size();
+    ok = (fclose(f) == 0) && ok;
+    if (!ok || rename(tmp.c_str(), path) != 0) {
+        remove(tmp.c_str());
+        set_error("writing checkpoint %s failed", path);
+        return MRS_ERR_IO;
+    }
+    return MRS_OK;
+}
+
+extern "C" mrs_status mrs_net_load(mrs_net net, const char* path, uint64_t* seed)
+{
+    using namespace mrs;
+    MRS_ARG(net != nullptr && path != nullptr, "NULL argument");
+    FILE* f = fopen(path, "rb");
+    if (!f) { set_error("cannot open %s", path); return MRS_ERR_IO; }
+    CkptHeader h;
+    std::vector<float> host;
+    mrs_status rc = MRS_OK;
+    if (fread(&h, sizeof(h), 1, f) != 1 || memcmp(h.magic, kCkptMagic, 8) != 0 ||
+        h.header_bytes != sizeof(CkptHeader) || h.version != kCkptVersion) {
+        set_error("%s is not a version-%u fusion-network checkpoint", path, kCkptVersion);
+        rc = MRS_ERR_FORMAT;
+    } else if (h.n_params != (int64_t)net->np || h.input_channels != net->cin0) {
+        set_error("checkpoint holds %lld parameters (%d input channels), the net %zu (%d)",
+                  (long long)h.n_params, h.input_channels, net->np, net->cin0);
+        rc = MRS_ERR_FORMAT;
+    } else if ((h.loss != MRS_LOSS_L1LOG && h.loss != MRS_LOSS_ROBUST) || !(h.beta > 0.0f) ||
+               h.step < 0) {
+        set_error("checkpoint %s has an invalid loss, beta or step", path);
+        rc = MRS_ERR_FORMAT;
+    } else {
+        host.resize(3 * net->np);
+        if (fread(host.data(), 4, host.size(), f) != host.size() || fgetc(f) != EOF) {
+            set_error("checkpoint %s is truncated or has trailing bytes", path);
+            rc = MRS_ERR_FORMAT;
+        } else if (fnv1a(0xCBF29CE484222325ull, host.data(), host.size() * 4) != h.checksum) {
+            set_error("checkpoint %s fails its checksum", path);
+            rc = MRS_ERR_FORMAT;
+        }
+    }
+    fclose(f);
+    if (rc != MRS_OK) return rc;
+    rc = mrs_net_set_state(net, host.data(), host.data() + net->np, host.data() + 2 * net->np, h.step);
+    if (rc != MRS_OK) return rc;
+    net->loss_kind = h.loss;
+    net->loss_beta = h.beta;
+    if (seed) *seed = h.seed;
+    return MRS_OK;
+}
+
+extern "C" mrs_status mrs_net_create_seeded(int32_t input_channels, uint64_t init_seed,
+                                            float resid_gain, mrs_net* out)
+{
+    using namespace mrs;
+    MRS_ARG(out != nullptr, "out is NULL");
+    *out = nullptr;
+    MRS_ARG(input_channels == 12 || input_channels == 21, "input_channels must be 12 or 21");
+    MRS_ARG(resid_gain >= 0.0f && resid_gain <= 1.0f, "resid_gain must be in [0, 1]");
+    const auto& L = shapes(input_channels);
+    size_t np = input_channels == 21 ? kParams21 : kParams12;
+    std::vector<float> p(np, 0.0f);
+    uint64_t x = init_seed ^ 0x6D72732D6E657430ull;
+    for (int l = 0; l < kLayers; ++l) {
+        if (l == kLayers - 1) break;   // the 3-channel head starts at zero
+        double sd = sqrt(2.0 / (9.0 * L[l].cin));
+        if (l >= 1 && l % 2 == 0) sd *= resid_gain;   // second conv of a residual block
+        for (size_t i = 0; i < (size_t)L[l].cout * 9 * L[l].cin; ++i)
+            p[L[l].woff + i] = (float)(sd * normal12(x));
+    }
+    return mrs_net_create(p.data(), (int32_t)np, out);
 }
 
 extern "C" mrs_status mrs_selftest_wait_timeout(int32_t limit_us, void* stream)

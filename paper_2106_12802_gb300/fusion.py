@@ -5,6 +5,7 @@ Marshalling only: every computation runs in libmrs.so's kernels.
 from __future__ import annotations
 
 import ctypes
+import os
 
 import numpy as np
 import torch
@@ -29,17 +30,26 @@ class Net:
     Adam state) created from a flat float32 parameter array of NPARAMS
     (12 input channels) or NPARAMS_EXTRA values (21: the extra HRLS layers)."""
 
-    def __init__(self, params):
+    def __init__(self, params=None, *, seed=None, input_channels=12, resid_gain=0.1):
+        """Net(params) copies a flat parameter array in; Net(seed=k) makes the
+        library's seeded initialisation (mrs_net_create_seeded) for a net of
+        `input_channels` (12 or 21) input channels."""
         load()
-        p = np.ascontiguousarray(params, dtype=np.float32)
-        assert p.size in (NPARAMS, NPARAMS_EXTRA), p.size
         h = ctypes.c_void_p()
-        call("mrs_net_create", ctypes.c_void_p(p.ctypes.data), p.size, ctypes.byref(h))
+        if params is None:
+            if seed is None:
+                raise ValueError("give params or seed")
+            call("mrs_net_create_seeded", int(input_channels), int(seed), float(resid_gain),
+                 ctypes.byref(h))
+        else:
+            p = np.ascontiguousarray(params, dtype=np.float32)
+            assert p.size in (NPARAMS, NPARAMS_EXTRA), p.size
+            call("mrs_net_create", ctypes.c_void_p(p.ctypes.data), p.size, ctypes.byref(h))
         self.handle = h
-        self.nparams = int(p.size)
         c = ctypes.c_int32()
         call("mrs_net_input_channels", h, ctypes.byref(c))
         self.input_channels = int(c.value)
+        self.nparams = NPARAMS_EXTRA if self.input_channels == 21 else NPARAMS
 
     def set_loss(self, loss="l1log", beta=0.1):
         """Training loss of train_step: "l1log" (L1 on log(1 + x)) or "robust"
@@ -131,34 +141,21 @@ def set_state(net, st):
     call("mrs_net_set_state", net.handle, _np_ptr(p), _np_ptr(m), _np_ptr(v), int(st["step"]))
 
 
-CKPT_MAGIC = b"MRSNET01"
 
 
 def save_checkpoint(net, path, seed=0):
-    """Flat little-endian file: magic, nparams (int64), step (int64), data seed
-    (uint64), then params, Adam m, Adam v as float32."""
-    st = get_state(net)
-    with open(path, "wb") as f:
-        f.write(CKPT_MAGIC)
-        f.write(np.array([net.nparams, st["step"]], dtype="<i8").tobytes())
-        f.write(np.array([seed], dtype="<u8").tobytes())
-        for k in ("params", "adam_m", "adam_v"):
-            f.write(st[k].astype("<f4").tobytes())
+    """Checkpoint of the net (weights, Adam state and step, loss) and `seed`
+    to `path` through mrs_net_save (flat little-endian file with a
+    checksum)."""
+    call("mrs_net_save", net.handle, os.fsencode(str(path)), int(seed))
 
 
 def load_checkpoint(net, path):
-    """Restores a save_checkpoint file into `net`; returns the stored data seed."""
-    with open(path, "rb") as f:
-        if f.read(8) != CKPT_MAGIC:
-            raise ValueError("not an mrs checkpoint")
-        n, step = np.frombuffer(f.read(16), dtype="<i8")
-        if n != net.nparams:
-            raise ValueError(f"checkpoint has {n} parameters, expected {net.nparams}")
-        seed = int(np.frombuffer(f.read(8), dtype="<u8")[0])
-        arrs = [np.frombuffer(f.read(4 * net.nparams), dtype="<f4").astype(np.float32)
-                for _ in range(3)]
-    set_state(net, {"params": arrs[0], "adam_m": arrs[1], "adam_v": arrs[2], "step": int(step)})
-    return seed
+    """Restores a save_checkpoint file into `net` (mrs_net_load); returns the
+    stored seed."""
+    seed = ctypes.c_uint64()
+    call("mrs_net_load", net.handle, os.fsencode(str(path)), ctypes.byref(seed))
+    return int(seed.value)
 
 
 def conv3x3(x, w, b, relu=False, precision="fp32", stream=None):

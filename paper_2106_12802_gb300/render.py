@@ -30,9 +30,36 @@ def _dev(t, dtype):
     return t
 
 
+class _SceneParams(ctypes.Structure):
+    _fields_ = [("n_spheres", ctypes.c_int32), ("n_large", ctypes.c_int32),
+                ("sphere_subdiv", ctypes.c_int32), ("aspect", ctypes.c_float)]
+
+
+SCENE_KINDS = {"cornell": 0, "procedural": 1}
+
+
 class Scene:
     """Device-resident scene + LBVH (mrs_build_scene).  `desc` is the dict of
-    arrays produced by the seeded scene generators."""
+    arrays produced by the seeded scene generators; Scene.seeded builds a
+    generated scene inside the library instead (mrs_build_scene_seeded)."""
+
+    @classmethod
+    def seeded(cls, seed, kind="procedural", n_spheres=64, n_large=31, sphere_subdiv=4,
+               aspect=1.0, stream=None):
+        load()
+        self = cls.__new__(cls)
+        prm = _SceneParams(n_spheres, n_large, sphere_subdiv, aspect)
+        h = ctypes.c_void_p()
+        call("mrs_build_scene_seeded", int(seed) & (2**64 - 1), SCENE_KINDS[kind],
+             ctypes.byref(prm), _stream(stream), ctypes.byref(h))
+        self.handle = h
+        self.desc = None
+        k = SCENE_KINDS[kind]
+        if k == 0:
+            self.n = 12 + 2 * 20 * 4 ** sphere_subdiv
+        else:
+            self.n = 2 + n_large * 5120 + (n_spheres - n_large) * 1280 + 6
+        return self
 
     def __init__(self, desc, stream=None):
         load()

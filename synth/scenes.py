@@ -2,8 +2,11 @@
 
 This module only *describes* scenes (triangles, materials, lights, camera).  It
 holds none of the rendering arithmetic; both the CUDA path and the CPU oracle
-consume the arrays it returns.  Every value is produced in float64 numpy and
-rounded once to float32, so a scene is a pure function of its arguments.
+consume the arrays it returns.  Every value is produced in float64 and rounded
+once to float32, so a scene is a pure function of its arguments.  The two
+measured workloads (cornell_box, procedural) come from scenegen.c, which the
+CUDA library also links for its seeded scene build; the small analytic test
+scenes are built here in numpy.
 
 Scene dictionary (all arrays C-contiguous):
 
@@ -29,7 +32,11 @@ procedural stand-ins replace its dataset.
 """
 from __future__ import annotations
 
+import ctypes
 import math
+import os
+import subprocess
+import threading
 
 import numpy as np
 
@@ -98,39 +105,6 @@ def _quad_tris(p0, e1, e2):
     return np.array([[a, b, c], [a, c, d]], dtype=np.float64)
 
 
-def _hash3(ix, iy, iz, salt):
-    """Integer lattice hash -> [0, 1) (splitmix-style, uint64 numpy)."""
-    with np.errstate(over="ignore"):
-        h = (ix.astype(np.uint64) * np.uint64(0x9E3779B97F4A7C15)
-             ^ iy.astype(np.uint64) * np.uint64(0xC2B2AE3D27D4EB4F)
-             ^ iz.astype(np.uint64) * np.uint64(0x165667B19E3779F9)
-             ^ np.uint64(salt) * np.uint64(0xD6E8FEB86659FD93))
-        h ^= h >> np.uint64(31)
-        h *= np.uint64(0xBF58476D1CE4E5B9)
-        h ^= h >> np.uint64(29)
-        h *= np.uint64(0x94D049BB133111EB)
-        h ^= h >> np.uint64(32)
-    return (h >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
-
-
-def value_noise(p: np.ndarray, salt: int) -> np.ndarray:
-    """Trilinear value noise in [0, 1] with smoothstep fade; p is [K, 3]."""
-    fl = np.floor(p)
-    i = fl.astype(np.int64) + (1 << 20)
-    f = p - fl
-    w = f * f * (3.0 - 2.0 * f)
-    acc = np.zeros(p.shape[0])
-    for dx in (0, 1):
-        for dy in (0, 1):
-            for dz in (0, 1):
-                h = _hash3(i[:, 0] + dx, i[:, 1] + dy, i[:, 2] + dz, salt)
-                wx = w[:, 0] if dx else 1.0 - w[:, 0]
-                wy = w[:, 1] if dy else 1.0 - w[:, 1]
-                wz = w[:, 2] if dz else 1.0 - w[:, 2]
-                acc += h * wx * wy * wz
-    return acc
-
-
 def camera(eye, target, up, fov_deg, aspect=1.0):
     eye, target, up = (np.asarray(x, dtype=np.float64) for x in (eye, target, up))
     fwd = target - eye
@@ -186,30 +160,80 @@ class _Builder:
 # --------------------------------------------------------------------------
 
 
+# --------------------------------------------------------------------------
+# the measured workloads: generated by scenegen.c (the same code the CUDA
+# library links for its seeded scene build)
+# --------------------------------------------------------------------------
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "libsynth.so")
+_lock = threading.Lock()
+_lib = None
+CORNELL, PROCEDURAL = 0, 1
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("n_spheres", ctypes.c_int32), ("n_large", ctypes.c_int32),
+                ("sphere_subdiv", ctypes.c_int32), ("aspect", ctypes.c_float)]
+
+
+def build(force: bool = False) -> str:
+    """Compile scenegen.c into synth/_build/libsynth.so (gcc, -ffp-contract=off)."""
+    src = [os.path.join(_HERE, f) for f in ("scenegen.c", "scenegen.h")]
+    if not force and os.path.exists(_SO) and all(os.path.getmtime(_SO) >= os.path.getmtime(f)
+                                                 for f in src):
+        return _SO
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = _SO + f".{os.getpid()}.tmp"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-shared",
+                    "-fPIC", "-o", tmp, src[0], "-lm"], check=True)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_SO)
+            P = ctypes.c_void_p
+            L.synth_scene_counts.argtypes = [ctypes.c_int32, ctypes.POINTER(_Params), P, P, P]
+            L.synth_scene_counts.restype = ctypes.c_int
+            L.synth_scene_generate.argtypes = [ctypes.c_uint64, ctypes.c_int32,
+                                               ctypes.POINTER(_Params), P, P, P, P, P, P, P]
+            L.synth_scene_generate.restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def generate(kind: int, seed: int = 0, n_spheres: int = 64, n_large: int = 31,
+             sphere_subdiv: int = 4, aspect: float = 1.0):
+    """The scene dictionary of scenegen.c for (kind, seed, parameters)."""
+    L = _load()
+    prm = _Params(n_spheres, n_large, sphere_subdiv, aspect)
+    nt, nm, nl = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    if L.synth_scene_counts(kind, ctypes.byref(prm), ctypes.byref(nt), ctypes.byref(nm),
+                            ctypes.byref(nl)):
+        raise ValueError("invalid scene kind or parameters")
+    d = {"V": np.zeros((nt.value, 3, 3), np.float32), "tri_mat": np.zeros(nt.value, np.int32),
+         "tri_light": np.zeros(nt.value, np.int32), "mats": np.zeros((nm.value, 8), np.float32),
+         "lights": np.zeros((nl.value, 12), np.float32), "env": np.zeros(3, np.float32),
+         "cam": np.zeros(12, np.float32)}
+    p = [ctypes.c_void_p(d[k].ctypes.data) for k in ("V", "tri_mat", "tri_light", "mats", "lights",
+                                                      "env", "cam")]
+    if L.synth_scene_generate(int(seed) & (2**64 - 1), kind, ctypes.byref(prm), *p):
+        raise RuntimeError("scene generation failed")
+    return d
+
+
 def cornell_box(sphere_subdiv: int = 4, aspect: float = 1.0):
     """Cornell box: 5 Lambertian quads (white 0.75, red/green 0.6), a Lambert
     and a GGX (alpha 0.3) sphere of radius 0.25, one quad light with Le=15.
 
     Box spans x in [-1,1], y in [0,2], z in [-1,1]; the camera looks down -z.
     """
-    b = _Builder()
-    white = b.material(LAMBERT, (0.75, 0.75, 0.75))
-    red = b.material(LAMBERT, (0.6, 0.05, 0.05))
-    green = b.material(LAMBERT, (0.05, 0.6, 0.05))
-    b.add(_quad_tris((-1, 0, -1), (0, 0, 2), (2, 0, 0)), white)      # floor, normal +y
-    b.add(_quad_tris((-1, 2, -1), (2, 0, 0), (0, 0, 2)), white)      # ceiling, normal -y
-    b.add(_quad_tris((-1, 0, -1), (2, 0, 0), (0, 2, 0)), white)      # back wall, normal +z
-    b.add(_quad_tris((-1, 0, -1), (0, 2, 0), (0, 0, 2)), red)        # left wall, normal +x
-    b.add(_quad_tris((1, 0, -1), (0, 0, 2), (0, 2, 0)), green)       # right wall, normal -x
-    b.quad_light(np.array([-0.25, 1.98, -0.25]), np.array([0.5, 0, 0]),
-                 np.array([0, 0, 0.5]), np.array([15.0, 15.0, 15.0]))
-    v, f = icosphere(sphere_subdiv)
-    lam = b.material(LAMBERT, (0.75, 0.75, 0.75))
-    ggx = b.material(GGX, (0.75, 0.75, 0.75), 0.3)
-    for center, m in (((-0.4, 0.25, -0.3), lam), ((0.4, 0.25, 0.2), ggx)):
-        b.add(v[f] * 0.25 + np.array(center), m)
-    cam = camera((0.0, 1.0, 3.4), (0.0, 1.0, 0.0), (0, 1, 0), 40.0, aspect)
-    return b.finish((0.0, 0.0, 0.0), cam)
+    return generate(CORNELL, 0, sphere_subdiv=sphere_subdiv, aspect=aspect)
 
 
 def procedural(seed: int, n_spheres: int = 64, n_large: int = 31, aspect: float = 1.0):
@@ -220,38 +244,10 @@ def procedural(seed: int, n_spheres: int = 64, n_large: int = 31, aspect: float 
     so the default scene has 31*5120 + 33*1280 + 2 = 200,962 triangles plus
     6 light triangles.  Displacement is value noise of amplitude 0.2*r.
     Materials are 50/50 Lambert/GGX with alpha U(0.05, 1) and albedo
-    U(0.1, 0.9) per channel; 3 quad lights with Le U(5, 20); environment 0.5.
+    U(0.1, 0.9) per channel; 3 quad lights with Le U(5, 20) facing down;
+    environment 0.5.
     """
-    rng = np.random.default_rng(np.random.SeedSequence([0x6D7273, int(seed)]))
-    b = _Builder()
-    ground = b.material(LAMBERT, (0.5, 0.5, 0.5))
-    b.add(_quad_tris((-15, 0, -15), (0, 0, 30), (30, 0, 0)), ground)
-    radius = rng.uniform(0.1, 1.0, n_spheres)
-    pos = rng.uniform(-10.0, 10.0, (n_spheres, 2))
-    kinds = rng.integers(0, 2, n_spheres)
-    alphas = rng.uniform(0.05, 1.0, n_spheres)
-    albedos = rng.uniform(0.1, 0.9, (n_spheres, 3))
-    salts = rng.integers(0, 2**31, n_spheres)
-    order = sorted(range(n_spheres), key=lambda i: (-radius[i], i))
-    large = set(order[:n_large])
-    for i in range(n_spheres):
-        v, f = icosphere(4 if i in large else 3)
-        r = radius[i]
-        disp = 1.0 + 0.2 * (2.0 * value_noise(v * 2.5, int(salts[i])) - 1.0)
-        pv = v * (disp[:, None] * r) + np.array([pos[i, 0], r, pos[i, 1]])
-        m = b.material(GGX if kinds[i] else LAMBERT, albedos[i], alphas[i])
-        b.add(pv[f], m)
-    for _ in range(3):
-        size = rng.uniform(1.0, 3.0, 2)
-        c = np.array([rng.uniform(-8, 8), rng.uniform(4.0, 8.0), rng.uniform(-8, 8)])
-        le = rng.uniform(5.0, 20.0)
-        p0 = c - np.array([size[0] / 2, 0, size[1] / 2])
-        # e1 along +x, e2 along +z -> cross(e1, e2) = x^ x z^ = -y: the light
-        # faces down, onto the spheres and the ground
-        b.quad_light(p0, np.array([size[0], 0, 0]), np.array([0, 0, size[1]]),
-                     np.array([le, le, le]))
-    cam = camera((0.0, 6.0, 18.0), (0.0, 0.5, 0.0), (0, 1, 0), 45.0, aspect)
-    return b.finish((0.5, 0.5, 0.5), cam)
+    return generate(PROCEDURAL, seed, n_spheres=n_spheres, n_large=n_large, aspect=aspect)
 
 
 def furnace_sphere(Le: float, rho: float, subdiv: int = 2):

@@ -65,6 +65,27 @@ def test_invalid_arguments_rejected_without_cuda(lib):
     # tail-kernel switch: NULL handles, out-of-range bounce
     assert lib.mrs_scene_set_tail(None, 1) == -1
     assert lib.mrs_ctx_set_tail(None, 1) == -1
+    assert lib.mrs_status_string(-7) == b"invalid checkpoint file"
+    assert lib.mrs_status_string(-8) == b"file I/O error"
+
+
+def test_boundary_calls_of_the_method_reject_bad_arguments(lib):
+    # the seeded scene build, checkpoint save / load and the seeded network
+    # refuse invalid arguments before any device work
+    from paper_2106_12802_gb300.render import _SceneParams
+    h = ctypes.c_void_p()
+    assert lib.mrs_build_scene_seeded(0, 1, None, None, None) == -1           # out NULL
+    assert lib.mrs_build_scene_seeded(0, 7, None, None, ctypes.byref(h)) == -1  # unknown kind
+    for prm in (_SceneParams(0, 0, 4, 1.0), _SceneParams(64, 65, 4, 1.0),
+                _SceneParams(64, 31, 4, 0.0), _SceneParams(64, 31, 7, 1.0)):
+        kind = 0 if prm.sphere_subdiv == 7 else 1
+        assert lib.mrs_build_scene_seeded(3, kind, ctypes.byref(prm), None, ctypes.byref(h)) == -1
+        assert h.value is None
+    assert lib.mrs_net_save(None, b"/nonexistent/x.ckpt", 0) == -1
+    assert lib.mrs_net_load(None, b"x.ckpt", None) == -1
+    assert lib.mrs_net_create_seeded(13, 0, ctypes.c_float(0.1), ctypes.byref(h)) == -1
+    assert lib.mrs_net_create_seeded(12, 0, ctypes.c_float(2.0), ctypes.byref(h)) == -1
+    assert lib.mrs_net_create_seeded(12, 0, ctypes.c_float(0.1), None) == -1
 
 
 def test_rdn_host_helpers_match_the_oracle_layout():
