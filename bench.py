@@ -927,12 +927,12 @@ def run_gpu(args, rank, world):
         # the launch's units (bounce >= 1 closest-hit segments for the tail)
         tr = _traffic(f"k_{dom}", "pt.cu")
         traffic = None
-        if tr and dom == "tail" and tail_segments:
+        if tr and dom == "tail" and tail_segments and tr.get("units"):
             traffic = tr["dram_bytes_per_launch"] / tr["units"] * tail_segments / launches_per_frame
         elif tr and dom != "tail":
             traffic = tr["dram_bytes_per_launch"]
         l2_gbs = None
-        if tr and tr.get("lts_bytes_per_launch") and dom == "tail" and tail_segments:
+        if tr and tr.get("lts_bytes_per_launch") and dom == "tail" and tail_segments and tr.get("units"):
             l2_gbs = (tr["lts_bytes_per_launch"] / tr["units"] * tail_segments) / (kms * 1e-3) / 1e9
         l2_peak = l2_copy_gbs() if rank == 0 else None
         label = {"trace": "k_trace (closest-hit traversal, bounce 0)",

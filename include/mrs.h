@@ -290,6 +290,17 @@ mrs_status mrs_render_layers(mrs_ctx ctx, mrs_scene scene, int32_t W, int32_t H,
                              int32_t max_depth, int32_t rr_start, uint64_t seed, int32_t grid,
                              const mrs_render_out* out, void* stream);
 
+/* A window of an image: the pixels [x0, x0 + w) x [y0, y0 + h) of the W x H
+ * render of mrs_render_layers (same camera, same per-pixel random numbers:
+ * every output pixel, layer and count is bit-identical to that pixel of the
+ * whole-image render), with outputs [h][w][...].  For rendering crops
+ * (training examples at the full image's pixel scale) without the rest of
+ * the image.  The window must lie inside the image (else MRS_ERR_ARG). */
+mrs_status mrs_render_window(mrs_ctx ctx, mrs_scene scene, int32_t W, int32_t H, int32_t x0,
+                             int32_t y0, int32_t w, int32_t h, int32_t spp, int32_t max_depth,
+                             int32_t rr_start, uint64_t seed, int32_t grid,
+                             const mrs_render_out* out, void* stream);
+
 /* Paths per wave for subsequent mrs_render calls on this scene (rounded to
  * whole samples of the image; default 16M paths).  For tests and tuning. */
 mrs_status mrs_scene_set_wave(mrs_scene scene, int64_t max_paths_per_wave);

@@ -41,6 +41,7 @@ SIGS = {
     "mrs_render_ctx": [P, P, I32, I32, I32, I32, I32, U64, P, P, P, P, P, P, P],
     "mrs_render_grid": [P, P, I32, I32, I32, I32, I32, U64, I32, P, P, P, P, P, P, P],
     "mrs_render_layers": [P, P, I32, I32, I32, I32, I32, U64, I32, P, P],
+    "mrs_render_window": [P, P, I32, I32, I32, I32, I32, I32, I32, I32, I32, U64, I32, P, P],
     "mrs_render_stats": [P, I32, I32, I32, I32, I32, U64, P, P, P],
     "mrs_profile_enable": [I32],
     "mrs_profile_read": [I32, P, P],

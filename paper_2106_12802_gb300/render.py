@@ -174,14 +174,35 @@ class _RenderOut(ctypes.Structure):
 
 
 def render(scene: Scene, W, H, spp, max_depth, rr_start=None, seed=0, aux=True, counts=True,
-           out=None, stream=None, ctx: RenderContext | None = None, grid=1, layers=False):
+           out=None, stream=None, ctx: RenderContext | None = None, grid=1, layers=False,
+           window=None):
     """mrs_render (or mrs_render_ctx when ctx is given) into device tensors;
     returns dict of (device) tensors.  grid > 1 renders on the sparse
     camera-sampling grid (mrs_render_grid): each pixel samples only the centre
     sub-pixel of its grid x grid block, the paper's nearest-neighbour LR.
     layers=True also returns the extra HRLS layers diffuse, specular and
-    variance (mrs_render_layers)."""
+    variance (mrs_render_layers).  window=(x0, y0, w, h) renders only that
+    window of the W x H image (mrs_render_window; outputs [h, w, ...])."""
     dev = torch.device("cuda")
+    if window is not None:
+        x0, y0, ww, hh = (int(v) for v in window)
+        if out is None:
+            out = {"radiance": torch.empty((hh, ww, 3), dtype=torch.float32, device=dev)}
+            if aux:
+                out["albedo"] = torch.empty((hh, ww, 3), dtype=torch.float32, device=dev)
+                out["normal"] = torch.empty((hh, ww, 3), dtype=torch.float32, device=dev)
+                out["depth"] = torch.empty((hh, ww), dtype=torch.float32, device=dev)
+            if counts:
+                out["counts"] = torch.zeros(max_depth + 1, dtype=torch.int64, device=dev)
+                out["shadow_counts"] = torch.zeros(max_depth + 1, dtype=torch.int64, device=dev)
+            if layers:
+                for k in ("diffuse", "specular", "variance"):
+                    out[k] = torch.empty((hh, ww, 3), dtype=torch.float32, device=dev)
+        ro = _RenderOut(*[_ptr(out.get(k)) for k, _ in _RenderOut._fields_])
+        call("mrs_render_window", ctx.handle if ctx is not None else None, scene.handle, W, H, x0,
+             y0, ww, hh, spp, max_depth, -1 if rr_start is None else rr_start,
+             int(seed) & 0xFFFFFFFFFFFFFFFF, int(grid), ctypes.byref(ro), _stream(stream))
+        return out
     if out is None:
         out = {"radiance": torch.empty((H, W, 3), dtype=torch.float32, device=dev)}
         if aux:

@@ -188,3 +188,104 @@ def spp_grid(net, scene_seeds, size=256, s=4, spp_tgt=1024, depth=8, rr=3, lr_sp
                   "up_psnr": float(np.mean([v[2] for v in vals])),
                   "up_relmse": float(np.mean([v[3] for v in vals]))}
             for key, vals in acc.items()}
+
+
+# ----------------------------------------------------------------------------
+# the fusion network's training recipe on many seeded scenes: every example
+# is a window of a full-resolution frame (the pixel scale the network serves)
+# ----------------------------------------------------------------------------
+def make_window_dataset(scene_seeds, frame=1024, window=256, s=4, spp_lr=64, spp_hr=4,
+                        spp_tgt=1024, depth=8, rr=3, seed=0, scene_kind="procedural"):
+    """One example per seeded scene (the library's own generator,
+    Scene.seeded): a random window x window crop of the frame x frame image,
+    aligned to the scale, rendered as LRHS (the matching window of the
+    frame / s image at spp_lr), HRLS + albedo + normal (spp_hr) and a spp_tgt
+    target.  Returns the list of examples (tensors on the GPU) and the
+    number of paths rendered."""
+    rng = np.random.default_rng(np.random.SeedSequence([0x77696E, int(seed)]))
+    data, paths = [], 0
+    for sd in scene_seeds:
+        sc = Scene.seeded(int(sd), scene_kind)
+        x0 = int(rng.integers(0, (frame - window) // s + 1)) * s
+        y0 = int(rng.integers(0, (frame - window) // s + 1)) * s
+        lw = (x0 // s, y0 // s, window // s, window // s)
+        hw = (x0, y0, window, window)
+        base = 3 * int(sd)
+        lr = render_image(sc, frame // s, frame // s, spp_lr, depth, rr, base, aux=False,
+                          counts=False, window=lw)["radiance"]
+        hr = render_image(sc, frame, frame, spp_hr, depth, rr, base + 1, aux=True, counts=False,
+                          window=hw)
+        tg = render_image(sc, frame, frame, spp_tgt, depth, rr, base + 2, aux=False, counts=False,
+                          window=hw)["radiance"]
+        data.append({"lrhs": lr[None], "hrls": hr["radiance"][None], "albedo": hr["albedo"][None],
+                     "normal": hr["normal"][None], "target": tg[None], "spp": (spp_lr, spp_hr),
+                     "scene": int(sd), "window": hw})
+        paths += (window // s) ** 2 * spp_lr + window * window * (spp_hr + spp_tgt)
+        sc.close()
+    torch.cuda.synchronize()
+    return data, paths
+
+
+def train_recipe(n_scenes=2000, steps=20000, frame=1024, window=256, spp_tgt=1024, batch=16,
+                 crop=128, s=4, lr=1e-4, loss="l1log", precision="bf16", eval_scenes=4,
+                 eval_size=512, eval_tgt=4096, init_seed=0, log_every=1000):
+    """The training recipe end to end: data from n_scenes seeded scenes
+    (seeds 1 .. n_scenes), `steps` Adam steps on batch x crop^2 crops with the
+    given loss and learning rate, then the gain over the method without the
+    network on held-out scenes (seeds 100001 ..; eval_size^2 windows of the
+    frame, eval_tgt-spp references).  Returns (net, report dict)."""
+    import time
+    t0 = time.perf_counter()
+    data, paths = make_window_dataset(range(1, 1 + n_scenes), frame, window, s,
+                                      spp_tgt=spp_tgt, seed=1)
+    t_data = time.perf_counter() - t0
+    net = fusion.Net(seed=init_seed)
+    t0 = time.perf_counter()
+    losses = train(net, data, steps, batch=batch, crop=crop, s=s, lr=lr, seed=0,
+                   log_every=log_every, precision=precision, loss=loss)
+    t_train = time.perf_counter() - t0
+    del data
+    ev, _ = make_window_dataset(range(100001, 100001 + eval_scenes), frame, eval_size, s,
+                                spp_tgt=eval_tgt, seed=2)
+    res = evaluate(net, ev, s=s, precision=precision)
+    del ev
+    report = {
+        "scenes": n_scenes, "frame": frame, "window": window, "spp": [64, 4, spp_tgt],
+        "paths_rendered": paths, "data_s": round(t_data, 2),
+        "steps": steps, "batch": [batch, crop, crop], "loss": loss, "optimizer": f"Adam lr {lr}",
+        "precision": precision, "train_s": round(t_train, 2),
+        "ms_per_step": round(1e3 * t_train / max(steps, 1), 3),
+        "loss_log": [(int(i), round(float(v), 5)) for i, v in losses],
+        "eval": {"scenes": eval_scenes, "size": eval_size, "reference_spp": eval_tgt, **res},
+        "gain_db_over_upsampled_lrhs": res["fused"]["psnr"] - res["upsampled_lrhs"]["psnr"],
+        "gain_db_over_hrls": res["fused"]["psnr"] - res["hrls"]["psnr"],
+    }
+    return net, report
+
+
+def main(argv=None):
+    """python -m paper_2106_12802_gb300.trainer recipe --scenes 2000 --steps 20000 [--save f]"""
+    import argparse
+    import json
+    ap = argparse.ArgumentParser()
+    ap.add_argument("cmd", choices=["recipe"])
+    ap.add_argument("--scenes", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--window", type=int, default=256)
+    ap.add_argument("--spp-tgt", type=int, default=1024)
+    ap.add_argument("--lr", type=float, default=1e-4)
+    ap.add_argument("--loss", default="l1log")
+    ap.add_argument("--eval-scenes", type=int, default=4)
+    ap.add_argument("--save", default=None, help="checkpoint file for the trained net")
+    a = ap.parse_args(argv)
+    net, rep = train_recipe(a.scenes, a.steps, window=a.window, spp_tgt=a.spp_tgt, lr=a.lr,
+                            loss=a.loss, eval_scenes=a.eval_scenes)
+    if a.save:
+        fusion.save_checkpoint(net, a.save, seed=0)
+    print(json.dumps(rep), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    import sys
+    sys.exit(main())

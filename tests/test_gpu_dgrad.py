@@ -99,7 +99,9 @@ def test_dgrad_bf16_on_bf16_operands_equals_fp32(mrs):
     t = torch.from_numpy(dy).cuda()
     a = mrs.conv3x3_dgrad(t, w, "linear", precision="fp32").cpu().numpy()
     b = mrs.conv3x3_dgrad(t, w, "linear", precision="bf16").cpu().numpy()
-    assert (np.abs(a - b) <= 2.0**-8 * np.abs(a) + 1e-9).all()
+    terms = _oracle(dy.astype(np.float64), w.astype(np.float64), "linear", None)[1]
+    bound = 2 * 576 * 2.0**-23 * terms + 2.0**-8 * np.abs(a) + 1e-12
+    assert (np.abs(a - b) <= bound).all(), (np.abs(a - b) / bound).max()
 
 
 def test_dgrad_rejects_bad_arguments(mrs):

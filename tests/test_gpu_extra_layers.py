@@ -3,7 +3,9 @@ carries diffuse, specular and variance layers besides albedo and normal):
 21 input channels, through mrs_fuse_extra / mrs_train_step_extra, against the
 float64 oracle.
 
-Tolerances as for the 12-channel network: FP32 within 1e-5 absolute;
+Tolerances as for the 12-channel network: FP32 within 1e-5 * max(1, max|y|)
+(outputs with the variance layers reach |y| > 10, where FP32 rounding alone
+exceeds 1e-5 absolute);
 BF16 / FP8 as PSNR floors against float64; training gradients per layer
 within 1e-4 relative (FP32) or cosine > 0.995 (BF16)."""
 import numpy as np
@@ -73,7 +75,7 @@ def test_fuse_extra_fp32_matches_oracle(mrs, N, h, w, s):
     c = _cuda(lr, hr, alb, nrm, ex)
     got = net.fuse(*c[:4], s, precision="fp32", extra=c[4]).cpu().numpy()
     ref = cnn.forward(p.astype(np.float64), lr, hr, alb, nrm, s, extra=ex)
-    assert np.abs(got - ref).max() <= 1e-5, np.abs(got - ref).max()
+    assert np.abs(got - ref).max() <= 1e-5 * max(1.0, np.abs(ref).max()), np.abs(got - ref).max()
 
 
 @pytest.mark.parametrize("prec,min_psnr", [("bf16", 45.0), ("fp8", 28.0)])
@@ -189,4 +191,4 @@ def test_rendered_layers_feed_the_network(mrs):
     got = net.fuse(*args, s, precision="fp32", extra=ex).cpu().numpy()
     host = [a.cpu().numpy() for a in args]
     ref = cnn.forward(p.astype(np.float64), *host, s, extra=ex.cpu().numpy())
-    assert np.abs(got - ref).max() <= 1e-5, np.abs(got - ref).max()
+    assert np.abs(got - ref).max() <= 1e-5 * max(1.0, np.abs(ref).max()), np.abs(got - ref).max()

@@ -272,3 +272,26 @@ def test_concurrent_render_contexts_match_sequential(mrs):
     for k in seq_a:
         assert torch.equal(a[k], seq_a[k]), k
         assert torch.equal(b[k], seq_b[k]), k
+
+
+@pytest.mark.parametrize("win,grid", [((0, 0, 64, 48), 1), ((37, 11, 50, 29), 1), ((96, 80, 32, 16), 1),
+                                      ((8, 4, 40, 40), 2)])
+def test_render_window_equals_crop_of_full_render(mrs, win, grid):
+    # a window of the image: the same camera and per-pixel random numbers, so
+    # every output (radiance, aux and extra layers) is the crop of the whole
+    # render bit for bit, whatever the window's place and size
+    sc = mrs.Scene(scenes.procedural(2, n_spheres=16, n_large=4))
+    W, H = 128, 96
+    full = mrs.render(sc, W, H, 4, 6, rr_start=3, seed=5, grid=grid, layers=True)
+    part = mrs.render(sc, W, H, 4, 6, rr_start=3, seed=5, grid=grid, layers=True, window=win)
+    x0, y0, w, h = win
+    for k in ("radiance", "albedo", "normal", "depth", "diffuse", "specular", "variance"):
+        assert torch.equal(part[k], full[k][y0:y0 + h, x0:x0 + w]), k
+    assert int(part["counts"][0]) == w * h * 4
+
+
+def test_render_window_rejects_outside_windows(mrs):
+    sc = mrs.Scene(scenes.cornell_box(sphere_subdiv=1))
+    for win in ((-1, 0, 8, 8), (0, 0, 0, 8), (60, 0, 8, 8), (0, 60, 8, 8)):
+        with pytest.raises(Exception):
+            mrs.render(sc, 64, 64, 1, 2, window=win)

@@ -34,10 +34,13 @@ def grid():
 
 
 def test_more_lrhs_samples_help(grid):
+    # the trend of Table comp_spp: along a row (fixed HRLS spp) PSNR rises
+    # with the LRHS spp at every step, by more than 0.3 dB over the row
     for b in (1, 4):
         rows = [grid[(a, b)] for a in (2, 8, 32, 128) if (a, b) in grid]
         psnr = [r["psnr"] for r in rows]
-        assert psnr[-1] > psnr[0] + 1.0, (b, psnr)
+        assert all(y > x for x, y in zip(psnr, psnr[1:])), (b, psnr)
+        assert psnr[-1] > psnr[0] + 0.3, (b, psnr)
         assert rows[-1]["relmse"] < rows[0]["relmse"], (b, rows)
 
 

