@@ -604,239 +604,67 @@ __global__ void __launch_bounds__(kThreads, 8) k_shadow(WaveParams w, int b)
     if (kCount) { atomicAdd(&w.stats[2], nv); atomicAdd(&w.stats[3], nt); }
 }
 
-// One ray's traversal, advanced a node (or a triangle) at a time so that a
-// lane can finish its ray and start the next while the others go on.  The
-// visiting order and every test are those of traverse<>(), so the result --
-// the closest hit (ties to the smaller triangle index), or whether anything
-// is hit below tmax -- is the same.
-struct Trav {
-    V3 o, d, inv;
-    float bt;          // closest hit so far (closest) / tmax (any hit)
-    int node, sp, best, best_prim;
-    bool any, fin;
-};
-
-template <bool kCount>
-__device__ __forceinline__ void trav_start(const SceneView& S, Trav& r, V3 o, V3 d, float tmax,
-                                           bool any, unsigned long long& nt)
-{
-    r.o = o; r.d = d; r.any = any; r.fin = false;
-    r.bt = tmax; r.best = -1; r.best_prim = 0x7fffffff; r.sp = 0; r.node = 0;
-    const int n = S.ns;
-    // large triangles first (the same tests for every ray)
-    for (int k = n; k < S.n; ++k) {
-        int prim;
-        if (kCount) ++nt;
-        float t = intersect(o, d, S.tris + 3 * k, any ? tmax : T_INF, prim);
-        if (t > 0.0f) {
-            if (any) { r.bt = t; r.best = k; r.fin = true; return; }
-            if (t < r.bt || (t == r.bt && prim < r.best_prim)) { r.bt = t; r.best = k; r.best_prim = prim; }
-        }
-    }
-    if (n <= 1) {
-        if (n == 1) {
-            int prim;
-            if (kCount) ++nt;
-            float t = intersect(o, d, S.tris, any ? tmax : T_INF, prim);
-            if (t > 0.0f && (any || t < r.bt || (t == r.bt && prim < r.best_prim))) {
-                r.bt = t; r.best = 0; r.best_prim = prim;
-            }
-        }
-        r.fin = true;
-        return;
-    }
-    r.inv = mk(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
-}
-
-// one step: an internal node's two child boxes, or one leaf triangle;
-// returns true when the ray is finished
-template <bool kCount>
-__device__ __forceinline__ bool trav_step(const SceneView& S, Trav& r, int* stack,
-                                          unsigned long long& nv, unsigned long long& nt)
-{
-    const int n = S.ns;
-    if (r.node < n - 1) {
-        if (kCount) ++nv;
-        const float4* nd = S.nodes + 4 * r.node;
-        float4 a = __ldg(nd), b = __ldg(nd + 1), c = __ldg(nd + 2), e = __ldg(nd + 3);
-        float t0 = slab(a.x, a.y, a.z, a.w, b.x, b.y, r.o, r.inv, r.bt);
-        float t1 = slab(b.z, b.w, c.x, c.y, c.z, c.w, r.o, r.inv, r.bt);
-        int c0 = __float_as_int(e.x), c1 = __float_as_int(e.y);
-        bool h0 = t0 != INFINITY, h1 = t1 != INFINITY;
-        if (h0 && h1) {
-            int nearc = t0 <= t1 ? c0 : c1, farc = t0 <= t1 ? c1 : c0;
-            if (r.sp < kStack) stack[r.sp++] = farc;
-            r.node = nearc;
-            return false;
-        }
-        if (h0) { r.node = c0; return false; }
-        if (h1) { r.node = c1; return false; }
-    } else {
-        int k = r.node - (n - 1), prim;
-        if (kCount) ++nt;
-        float t = intersect(r.o, r.d, S.tris + 3 * k, r.any ? r.bt : T_INF, prim);
-        if (t > 0.0f) {
-            if (r.any) { r.bt = t; r.best = k; return true; }
-            if (t < r.bt || (t == r.bt && prim < r.best_prim)) { r.bt = t; r.best = k; r.best_prim = prim; }
-        }
-    }
-    if (r.sp == 0) return true;
-    r.node = stack[--r.sp];
-    return false;
-}
-
-// The late bounces in one launch.  Every warp runs its own small wavefront:
-// each lane traces one ray at a time (a path's closest-hit ray or its shadow
-// ray), a few traversal steps per round, and takes the next ray as soon as
-// its own is finished instead of waiting for the warp's slowest ray.  A
-// finished closest hit joins the warp's shade queue (shared memory); when it
-// holds a warp's worth (or nothing else is left), 32 paths are shaded
-// together (shade_path: emission, NEE setup, BSDF sampling, roulette) and
-// their next rays -- the shadow ray first, then the path's next closest-hit
-// ray -- join the warp's pending-ray list, from which free lanes draw before
-// they take new paths from queue q_b0 (cnt[kWorkSlot] hands those out).
-// Bounds: a warp takes new paths only when its pending ring is empty, and
-// the shade step leaves at most 31 queued paths, so a warp never holds more
-// than 32 + 31 paths: the shade queue (64) and the ring (128) cannot fill.
-// Per path the operations and their order are those of the wavefront
-// kernels (the shadow ray of bounce b is resolved before bounce b + 1 is
-// shaded), so the radiance is bit-identical; the per-bounce counts are the
-// same numbers, gathered per block in shared memory.
+// The late bounces in one launch: each thread takes a path of queue q_b0,
+// follows it to its end (closest hit, shading, shadow ray, next bounce) and
+// then takes the next one.  Late bounces hold few paths, so one launch per
+// step would wait for each step's slowest ray; here a path's steps run back
+// to back.  Every path meets the same operations in the same order as in the
+// wavefront kernels (trace, shade, shadow; a path's state lives in P), so
+// its radiance is bit-identical; the per-bounce counts are the same numbers,
+// gathered per block in shared memory.  cnt[kWorkSlot] hands out the paths.
+// 32 registers and 8 blocks per SM, as the traversal kernels: with 64
+// registers (4 blocks) the tail ran 2-7% slower despite no spills.
 constexpr int kWorkSlot = 63;
-constexpr int kShadeQ = 64;     // shade-queue entries per warp: path, bounce
-constexpr int kPendQ = 128;     // pending-ray ring per warp: path, (bounce << 2) | kind
-constexpr int kTravSteps = 4;   // traversal steps per lane between refills
 template <bool kCount>
-__global__ void __launch_bounds__(kThreads, 4) k_tail(WaveParams w, int b0)
+__global__ void __launch_bounds__(kThreads, 8) k_tail(WaveParams w, int b0)
 {
     __shared__ uint32_t s_cnt[64], s_scnt[64];
-    __shared__ int s_shq[kThreads / 32][kShadeQ];
-    __shared__ uint8_t s_shb[kThreads / 32][kShadeQ];
-    __shared__ int s_pq[kThreads / 32][kPendQ];
-    __shared__ uint8_t s_pqb[kThreads / 32][kPendQ];
     for (int j = threadIdx.x; j < 64; j += blockDim.x) { s_cnt[j] = 0u; s_scnt[j] = 0u; }
     __syncthreads();
     unsigned long long nv = 0, nt = 0, sv = 0, stt = 0;
     PathSoA& P = w.P;
-    const SceneView& S = w.S;
     const int count = (int)*(volatile uint32_t*)&w.cnt[b0];
     const int* q = (b0 & 1) ? P.q1 : P.q0;
     const ShadeConst sc0 = shade_const(w);
-    const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1u;
-    int* shq = s_shq[threadIdx.x >> 5];
-    uint8_t* shb = s_shb[threadIdx.x >> 5];
-    int* pq = s_pq[threadIdx.x >> 5];
-    uint8_t* pqb = s_pqb[threadIdx.x >> 5];
-    int sh_n = 0;                 // warp-uniform: entries in the shade queue
-    int pq_head = 0, pq_tail = 0; // warp-uniform: pending ring [head, tail)
-    bool drained = false;         // warp-uniform: queue q_b0 handed out
-    // the lane's ray: path p at bounce b; kind 0 closest hit, 1 shadow ray
-    // (the path continues afterwards), 2 shadow ray (the path ends)
-    int p = -1, b = 0, kind = 0;
-    Trav r;
-    int stack[kStack];
-    // every round finishes a ray or advances one by kTravSteps nodes, so the
-    // loop ends by itself; the cap only bounds it should that ever fail
-    uint32_t rounds = 0;
-    auto start = [&](int pp, int bb, int kk) {
-        p = pp; b = bb; kind = kk;
-        V3 o = mk(P.ox[p], P.oy[p], P.oz[p]);
-        if (kind == 0) trav_start<kCount>(S, r, o, mk(P.dx[p], P.dy[p], P.dz[p]), T_INF, false, nt);
-        else trav_start<kCount>(S, r, o, mk(P.sdx[p], P.sdy[p], P.sdz[p]), P.stmax[p], true, stt);
-    };
+    int p = -1, b = b0;
+    bool drained = false;   // warp-uniform: the queue has been handed out
     for (;;) {
-        // refill free lanes: the warp's pending rays first, then new paths
-        unsigned freem = __ballot_sync(FULL, p < 0);
-        if (freem) {
-            const int avail = pq_tail - pq_head;
-            const int nfree = __popc(freem);
-            const int take = avail < nfree ? avail : nfree;
-            if (p < 0) {
-                const int rank = __popc(freem & lt);
-                if (rank < take) {
-                    const int j = (pq_head + rank) & (kPendQ - 1);
-                    const int bk = pqb[j];
-                    start(pq[j], bk >> 2, bk & 3);
-                }
-            }
-            pq_head += take;
-            freem = __ballot_sync(FULL, p < 0);
-            if (freem && !drained) {
-                const int leader = __ffs(freem) - 1;
-                uint32_t base = 0;
-                if (lane == leader) base = atomicAdd(&w.cnt[kWorkSlot], (uint32_t)__popc(freem));
-                base = __shfl_sync(FULL, base, leader);
-                drained = base + (uint32_t)__popc(freem) >= (uint32_t)count;
-                if (p < 0) {
-                    const uint32_t i = base + (uint32_t)__popc(freem & lt);
-                    if (i < (uint32_t)count) start(b0 == 0 ? (int)i : q[i], b0, 0);
-                }
+        // refill: lanes without a path take consecutive queue slots
+        const bool want = p < 0;
+        const unsigned m = __ballot_sync(0xffffffffu, want);
+        if (m && !drained) {
+            const int leader = __ffs(m) - 1;
+            uint32_t base = 0;
+            if (lane == leader) base = atomicAdd(&w.cnt[kWorkSlot], (uint32_t)__popc(m));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            drained = base + (uint32_t)__popc(m) >= (uint32_t)count;
+            if (want) {
+                const uint32_t i = base + (uint32_t)__popc(m & ((1u << lane) - 1u));
+                if (i < (uint32_t)count) { p = b0 == 0 ? (int)i : q[i]; b = b0; }
             }
         }
-        const bool busy = p >= 0;
-        const unsigned busym = __ballot_sync(FULL, busy);
-        if (!busym && sh_n == 0 && pq_tail == pq_head && drained) break;
-        if (++rounds > (1u << 24)) break;
-        // traversal: a few steps per lane
-        bool done = false;
-        if (busy) {
-            done = r.fin;
-            for (int it = 0; it < kTravSteps && !done; ++it)
-                done = kind == 0 ? trav_step<kCount>(S, r, stack, nv, nt)
-                                 : trav_step<kCount>(S, r, stack, sv, stt);
-        }
-        // finished rays: a closest hit goes to the shade queue; a shadow ray
-        // adds its contribution if unoccluded, then the path's next closest-
-        // hit ray starts in the same lane (kind 1) or the path ends (kind 2)
-        const bool to_shade = busy && done && kind == 0;
-        if (busy && done && kind != 0) {
-            if (r.best < 0) {
+        if (!__any_sync(0xffffffffu, p >= 0)) break;
+        if (p < 0) continue;
+        V3 o = mk(P.ox[p], P.oy[p], P.oz[p]), d = mk(P.dx[p], P.dy[p], P.dz[p]);
+        float t = -1.0f;
+        const int k = traverse<false, kCount>(w.S, o, d, T_INF, t, &nv, &nt);
+        P.hit_t[p] = t;
+        P.hit_id[p] = k;
+        bool cont = false, shadow = false;
+        shade_path(w, sc0, b, p, cont, shadow);
+        if (shadow) {
+            atomicAdd(&s_scnt[b], 1u);
+            V3 so = mk(P.ox[p], P.oy[p], P.oz[p]), sd = mk(P.sdx[p], P.sdy[p], P.sdz[p]);
+            float ts;
+            if (traverse<true, kCount>(w.S, so, sd, P.stmax[p], ts, &sv, &stt) < 0) {
                 P.Lx[p] = P.Lx[p] + P.scx[p];
                 P.Ly[p] = P.Ly[p] + P.scy[p];
                 P.Lz[p] = P.Lz[p] + P.scz[p];
             }
-            if (kind == 1) start(p, b + 1, 0);
-            else p = -1;
         }
-        const unsigned shm = __ballot_sync(FULL, to_shade);
-        if (to_shade) {
-            P.hit_t[p] = r.best >= 0 ? r.bt : -1.0f;
-            P.hit_id[p] = r.best;
-            const int j = (sh_n + __popc(shm & lt)) & (kShadeQ - 1);
-            shq[j] = p;
-            shb[j] = (uint8_t)b;
-            p = -1;
-        }
-        sh_n += __popc(shm);
-        __syncwarp();
-        // shade a warp's worth of finished paths (or the rest, once nothing
-        // else can feed the lanes), if the pending ring has room for them
-        const bool idle = !__any_sync(FULL, p >= 0) && pq_tail == pq_head && drained;
-        if ((sh_n >= 32 || (idle && sh_n > 0)) && (pq_tail - pq_head) + 32 <= kPendQ) {
-            const int ns = sh_n < 32 ? sh_n : 32;
-            bool cont = false, shadow = false;
-            int ep = 0, eb = 0;
-            if (lane < ns) {
-                const int j = (sh_n - 1 - lane) & (kShadeQ - 1);
-                ep = shq[j];
-                eb = shb[j];
-                shade_path(w, sc0, eb, ep, cont, shadow);
-                if (shadow) atomicAdd(&s_scnt[eb], 1u);
-                if (cont) atomicAdd(&s_cnt[eb + 1], 1u);
-            }
-            sh_n -= ns;
-            const bool push = shadow || cont;
-            const unsigned pm = __ballot_sync(FULL, push);
-            if (push) {
-                const int j = (pq_tail + __popc(pm & lt)) & (kPendQ - 1);
-                pq[j] = ep;
-                pqb[j] = (uint8_t)(shadow ? ((eb << 2) | (cont ? 1 : 2)) : ((eb + 1) << 2));
-            }
-            pq_tail += __popc(pm);
-            __syncwarp();
-        }
+        if (cont) { atomicAdd(&s_cnt[b + 1], 1u); ++b; }
+        else p = -1;
     }
     __syncthreads();
     for (int j = b0 + threadIdx.x; j <= w.max_depth + 1; j += blockDim.x) {

@@ -58,7 +58,7 @@ def _cuda(*a):
     return [torch.from_numpy(np.ascontiguousarray(t)).cuda() for t in a]
 
 
-def _assert_grads_elementwise(g, rg, terms):
+def _assert_grads_elementwise(g, rg, terms, max_r=2e-3):
     # r = |error| / sum |terms| per gradient element.  FP32 rounding alone
     # keeps r near 1e-6; a ReLU whose pre-activation lies within rounding of
     # 0 may be decided differently by the two sides, moving one pixel's
@@ -69,7 +69,7 @@ def _assert_grads_elementwise(g, rg, terms):
         for a, b in ((wo, bo), (bo, bo + co)):
             x = r[a:b]
             q = np.quantile(x, [0.5, 0.99, 1.0])
-            assert q[2] <= 2e-3 and q[1] <= 1e-4 and q[0] <= 1e-5, (li, a, q)
+            assert q[2] <= max_r and q[1] <= 1e-4 and q[0] <= 1e-5, (li, a, q)
 
 
 @pytest.mark.parametrize("N,h,w,s", [(2, 4, 6, 4), (1, 8, 8, 2)])
@@ -161,7 +161,10 @@ def test_robust_loss_train_step_matches_oracle(mrs, N, h, w, s):
                                                 nrm, tgt, s, loss="robust", beta=0.1,
                                                 abs_terms=True)
     assert abs(loss - rloss) <= 1e-6 * rloss
-    _assert_grads_elementwise(g, rg, terms)
+    # l_r's gradient sign(e) beta / (beta + |e|)^2 also turns on a decision:
+    # an output within rounding of its target takes the other sign, moving
+    # that value's whole contribution (more than a ReLU mask: up to 1e-2)
+    _assert_grads_elementwise(g, rg, terms, max_r=1e-2)
     ok = np.abs(rg) > 1e-6
     assert np.abs((p1 - p) - (rp - p))[ok].max() <= 0.01 * 1e-3
 
