@@ -35,9 +35,9 @@ WORKLOAD = {
                 "x4 fusion CNN (12->64, 8 residual blocks, 64->3) in BF16 on tcgen05; fallback gate; "
                 "the two renders run concurrently on two streams",
     "scene_seed": 0, "lrhs": [256, 256, 64], "hrls": [1024, 1024, 4], "scale": 4,
-    "max_depth": 8, "rr_start": 3, "precision": "bf16", "net_init": "trained before the timed region (BF16 training step, robust loss l_r with "
-                "beta 0.1, 3000 Adam steps on 8 held-out procedural scenes); Kaiming-normal seed 0 "
-                "under --quick",
+    "max_depth": 8, "rr_start": 3, "precision": "bf16",
+    "net_init": "trained before the timed region by the training recipe (reduced: see "
+                "`training`); the seeded initialisation under --quick",
     "l2": "flushed between steps (512 MiB write)",
 }
 LR, HR, S = 256, 1024, 4
@@ -272,28 +272,22 @@ def run_reference(args, rank, world):
 # ----------------------------------------------------------------------------
 # equal-PSNR comparison: hybrid frame vs plain high-resolution path tracing
 # ----------------------------------------------------------------------------
-def train_net(mrs, s, train_scenes=8, train_steps=3000, batch=16, crop=128, precision="bf16",
-              loss="robust", beta=0.1):
-    """Trains the fusion network on held-out procedural scenes (seeds 1..,
-    never the bench scene) with the library's training step; returns the net
-    and a description of the training."""
+def train_net(mrs, s, n_scenes=160, steps=6000):
+    """Trains the fusion network by the training recipe (seeded 200k-triangle
+    scenes, seeds 1.. -- never the bench scene -- one 256^2 window of the
+    1024^2 frame per scene with LRHS 64 spp, HRLS 4 spp and a 1024-spp
+    target; 128^2 crops at batch 16, L1 on log(1 + x), Adam lr 1e-4, BF16
+    training step) reduced to n_scenes scenes and `steps` steps, and scores
+    the gain over the method without the network on 4 held-out scenes
+    (512^2 windows, 4096-spp references).  Returns the net and the report."""
     from paper_2106_12802_gb300 import trainer
-    from synth import scenes
-    t0 = time.perf_counter()
-    data = trainer.make_dataset(range(1, 1 + train_scenes), size=HR, s=s, spp_lr=SPP_LR,
-                                spp_hr=SPP_HR, spp_tgt=256, depth=DEPTH, rr=RR,
-                                scene_fn=scenes.procedural)
-    t_data = time.perf_counter() - t0
-    net = mrs.Net(trainer.init_params(0))
-    t0 = time.perf_counter()
-    trainer.train(net, data, train_steps, batch=batch, crop=crop, s=s, lr=1e-3, seed=0,
-                  precision=precision, loss=loss, beta=beta)
-    t_train = time.perf_counter() - t0
-    del data
-    return net, (f"{train_scenes} procedural scenes (seeds 1..{train_scenes}) at {HR}^2, targets "
-                 f"256 spp ({t_data:.1f} s to render); {train_steps} Adam steps, batch {batch} x "
-                 f"{crop}^2, lr 1e-3, {loss} loss" + (f" (beta {beta})" if loss == "robust" else "") +
-                 f", {precision} training step ({t_train:.1f} s)")
+    net, rep = trainer.train_recipe(n_scenes=n_scenes, steps=steps, window=256, spp_tgt=1024,
+                                    lr=1e-4, loss="l1log", eval_scenes=4, eval_size=512,
+                                    eval_tgt=4096, log_every=0)
+    rep["reduction"] = (f"{n_scenes} of the recipe's 2,000 scenes and {steps} steps; each scene "
+                        "renders one 256^2 window of its 1024^2 frame (windows are bit-identical "
+                        "to those pixels of the whole render)")
+    return net, rep
 
 
 def equal_psnr(mrs, scene, s, net, training, ref_spp=4096):
@@ -840,7 +834,8 @@ def run_gpu(args, rank, world):
     # ---- context measurements (outside the timed region) --------------------
     extra = {}
     if rank == 0 and not args.quick and not args.no_equal_psnr:
-        extra["equal_psnr"] = equal_psnr(mrs, scene, S, net, training)
+        extra["equal_psnr"] = equal_psnr(mrs, scene, S, net, "the bench's trained network "
+                                         "(`training`)")
     if rank == 0 and not args.quick and not args.no_batched:
         extra["batched_serving"] = batched_serving(mrs, params)
     if rank == 0 and not args.no_paper_network:
