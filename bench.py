@@ -365,100 +365,150 @@ def equal_psnr(mrs, scene, s, net, training, ref_spp=4096):
 # ----------------------------------------------------------------------------
 # batched serving: many frames of uneven size, scale and spp in one CUDA graph
 # ----------------------------------------------------------------------------
-def batched_serving(mrs, params, n_jobs=32, n_scenes=4, psnr_jobs=4, seed=5):
-    """32 hybrid frames (HR in {512, 1024, 2048}^2, scale in {2, 4}, HRLS spp in
-    {1, 2, 4, 8}, LRHS 64 spp) over a pool of procedural scenes, each frame =
-    LRHS + HRLS renders, fusion and the device-side gate, all captured in one
-    CUDA graph per fusion precision.  Render wave sizes are autotuned per
-    shape.  PSNR against 4096-spp references is reported for the first
-    `psnr_jobs` frames that are at most 1024^2."""
+def batched_serving(mrs, params, n_jobs=32, seed=5, psnr_window=256, ref_spp=4096, reps=3):
+    """32 hybrid frames of 32 different seeded 200k-triangle scenes: HR in
+    {512, 1024, 2048}^2, scale in {2, 4}, HRLS spp in {1, 2, 4, 8}, LRHS
+    64 spp.  All 64 renders are one batched render (mrs_render_batch: the
+    frames' paths share waves, one launch per wavefront stage over all of
+    them); the fusion runs once per (size, scale) group of frames (N frames
+    per launch) in BF16 or FP8; the device-side gate per frame; the whole
+    batch is one CUDA graph per precision.  The autotuner picks the wave
+    size, the tail kernel's first bounce and the conv's ring depth.  Every
+    frame's fused image is scored (sRGB PSNR) against a ref_spp-spp render
+    over its central psnr_window^2 window (a window render is bit-identical
+    to those pixels of the whole render).  For comparison the same frames
+    are also timed with one render call per frame (the batch as 64 separate
+    renders in one graph)."""
     import torch
 
     from paper_2106_12802_gb300 import autotune
-    from synth import scenes
     rng = np.random.default_rng(seed)
-    pool = [mrs.Scene(scenes.procedural(100 + k)) for k in range(n_scenes)]
-    jobs = []
+    frames = []
     for j in range(n_jobs):
-        jobs.append({"scene": int(rng.integers(n_scenes)), "hr": int(rng.choice([512, 1024, 2048])),
-                     "s": int(rng.choice([2, 4])), "spp_h": int(rng.choice([1, 2, 4, 8])),
-                     "seed": 1000 + j})
+        frames.append({"scene": mrs.Scene.seeded(200 + j), "hr": int(rng.choice([512, 1024, 2048])),
+                       "s": int(rng.choice([2, 4])), "spp_h": int(rng.choice([1, 2, 4, 8])),
+                       "seed": 1000 + j})
     net = mrs.Net(params)
     dev = torch.device("cuda")
-    bufs, waves = [], {}
-    for jb in jobs:
-        H, s = jb["hr"], jb["s"]
-        bufs.append({"lr": torch.empty((1, H // s, H // s, 3), device=dev),
-                     "hr": torch.empty((1, H, H, 3), device=dev),
-                     "alb": torch.empty((1, H, H, 3), device=dev),
-                     "nrm": torch.empty((1, H, H, 3), device=dev),
-                     "dep": torch.empty((1, H, H), device=dev),
-                     "fused": torch.empty((1, H, H, 3), device=dev),
-                     "out": torch.empty((1, H, H, 3), device=dev),
-                     "used": torch.zeros(2, dtype=torch.int32, device=dev),
-                     "D": torch.zeros(1, dtype=torch.float64, device=dev)})
-    # autotune the wave per render shape (outside the graph)
-    for jb in jobs:
-        sc = pool[jb["scene"]]
-        for (W, spp) in ((jb["hr"] // jb["s"], SPP_LR), (jb["hr"], jb["spp_h"])):
-            if (W, spp) not in waves:
-                waves[(W, spp)] = autotune.tune_wave(sc, W, W, spp, DEPTH, RR, cache=None, reps=1)[0]
+    groups = {}
+    for f in frames:
+        groups.setdefault((f["hr"], f["s"]), []).append(f)
+    bufs = {}
+    for (H, s), fs in groups.items():
+        n = len(fs)
+        bufs[(H, s)] = {"lr": torch.empty((n, H // s, H // s, 3), device=dev),
+                        "hr": torch.empty((n, H, H, 3), device=dev),
+                        "alb": torch.empty((n, H, H, 3), device=dev),
+                        "nrm": torch.empty((n, H, H, 3), device=dev),
+                        "dep": torch.empty((n, H, H), device=dev),
+                        "fused": torch.empty((n, H, H, 3), device=dev),
+                        "out": torch.empty((n, H, H, 3), device=dev),
+                        "used": torch.zeros((n, 2), dtype=torch.int32, device=dev),
+                        "D": torch.zeros(n, dtype=torch.float64, device=dev)}
+        for i, f in enumerate(fs):
+            f["group"], f["index"] = (H, s), i
+    jobs = []
+    for f in frames:
+        b, i, H, s = bufs[f["group"]], f["index"], f["hr"], f["s"]
+        jobs.append({"scene": f["scene"], "W": H // s, "H": H // s, "spp": SPP_LR, "max_depth": DEPTH,
+                     "rr_start": RR, "seed": f["seed"], "out": {"radiance": b["lr"][i]}})
+        jobs.append({"scene": f["scene"], "W": H, "H": H, "spp": f["spp_h"], "max_depth": DEPTH,
+                     "rr_start": RR, "seed": f["seed"] + 7,
+                     "out": {"radiance": b["hr"][i], "albedo": b["alb"][i], "normal": b["nrm"][i],
+                             "depth": b["dep"][i]}})
+    ctx = mrs.RenderContext()
 
-    def batch(prec):
-        for jb, b in zip(jobs, bufs):
-            sc = pool[jb["scene"]]
-            H, s = jb["hr"], jb["s"]
-            sc.set_wave(waves[(H // s, SPP_LR)])
-            mrs.render(sc, H // s, H // s, SPP_LR, DEPTH, RR, jb["seed"], out={"radiance": b["lr"][0]})
-            sc.set_wave(waves[(H, jb["spp_h"])])
-            mrs.render(sc, H, H, jb["spp_h"], DEPTH, RR, jb["seed"] + 7,
-                       out={"radiance": b["hr"][0], "albedo": b["alb"][0], "normal": b["nrm"][0],
-                            "depth": b["dep"][0]})
+    def render_all():
+        mrs.render_batch(ctx, jobs)
+
+    def fuse_all(prec):
+        for (H, s), b in bufs.items():
             net.fuse(b["lr"], b["hr"], b["alb"], b["nrm"], s, precision=prec, out=b["fused"])
-            mrs.gate_async(b["fused"], b["lr"], None, s, 0.01, out=b["out"], used=b["used"], D=b["D"])
+            for i in range(b["lr"].shape[0]):
+                mrs.gate_async(b["fused"][i:i + 1], b["lr"][i:i + 1], None, s, 0.01,
+                               out=b["out"][i:i + 1], used=b["used"][i], D=b["D"][i:i + 1])
 
-    result = {"jobs": n_jobs, "distinct_scenes": n_scenes,
-              "hr_mix": {str(r): sum(1 for jb in jobs if jb["hr"] == r) for r in (512, 1024, 2048)},
-              "paths_per_batch": int(sum((jb["hr"] // jb["s"]) ** 2 * SPP_LR + jb["hr"] ** 2 * jb["spp_h"]
-                                         for jb in jobs))}
-    refs = {}
-    for prec in ("bf16", "fp8"):
+    # autotuning (outside the graph): wave size, tail start, conv ring depth
+    tuned = {}
+    tuned["wave"], t_wave = autotune.tune("batch:wave", [{"wave": c} for c in autotune.WAVE_CANDIDATES],
+                                          lambda c: ctx.set_wave(c["wave"]), render_all, reps=1, cache=None)
+    tuned["tail"], t_tail = autotune.tune("batch:tail", [{"tail": b} for b in autotune.TAIL_CANDIDATES],
+                                          lambda c: ctx.set_tail(c["tail"]), render_all, reps=1, cache=None)
+    tuned["ring"], t_ring = autotune.tune("batch:ring", [{"ring": r} for r in autotune.RING_CANDIDATES],
+                                          lambda c: mrs.conv_set_ring(c["ring"]),
+                                          lambda: fuse_all("bf16"), reps=2, cache=None)
+    result = {"jobs": n_jobs, "distinct_scenes": n_jobs,
+              "hr_mix": {str(r): sum(1 for f in frames if f["hr"] == r) for r in (512, 1024, 2048)},
+              "groups": {f"{H}x{H}/s{s}": len(fs) for (H, s), fs in groups.items()},
+              "paths_per_batch": int(sum((f["hr"] // f["s"]) ** 2 * SPP_LR + f["hr"] ** 2 * f["spp_h"]
+                                         for f in frames)),
+              "autotuned": tuned, "autotune_ms": {"wave": t_wave, "tail": t_tail, "ring": t_ring}}
+
+    def timed_graph(fn):
         side = torch.cuda.Stream()
         side.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(side):
-            batch(prec)                      # warm-up: sizes buffers, packs / calibrates weights
+            fn()                      # warm-up: sizes arenas, packs / calibrates weights
         torch.cuda.current_stream().wait_stream(side)
         torch.cuda.synchronize()
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g):
-            batch(prec)
+            fn()
         g.replay()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        reps = 3
         e0.record()
         for _ in range(reps):
             g.replay()
         e1.record()
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / reps
-        ps = []
-        for jb, b in zip(jobs, bufs):
-            if len(ps) >= psnr_jobs:
-                break
-            if jb["hr"] > 1024:
-                continue
-            key = id(b)
-            if key not in refs:
-                refs[key] = mrs.render(pool[jb["scene"]], jb["hr"], jb["hr"], 4096, DEPTH, RR,
-                                       99991, aux=False, counts=False)["radiance"]
-            ps.append(mrs.image_metrics(b["fused"][0].contiguous(), refs[key])[0])
-        result[prec] = {"ms_per_batch": ms, "frames_per_s": n_jobs / ms * 1e3,
-                        "mean_psnr_db_vs_4096spp": float(np.mean(ps)) if ps else None,
-                        "psnr_frames": len(ps)}
         del g
-    for sc in pool:
-        sc.close()
+        return e0.elapsed_time(e1) / reps
+
+    renders_ms = timed_graph(render_all)
+    # the same 64 renders as separate calls (one context per frame pair)
+    ctx_f = mrs.RenderContext()
+    ctx_f.set_wave(tuned["wave"]["wave"])
+    ctx_f.set_tail(tuned["tail"]["tail"])
+
+    def render_per_call():
+        for jb in jobs:
+            mrs.render(jb["scene"], jb["W"], jb["H"], jb["spp"], DEPTH, RR, jb["seed"],
+                       out=jb["out"], ctx=ctx_f, counts=False)
+    per_call_ms = timed_graph(render_per_call)
+    ctx_f.close()
+    refs = []
+    for f in frames:
+        H = f["hr"]
+        w = min(psnr_window, H)
+        win = ((H - w) // 2, (H - w) // 2, w, w)
+        ref = mrs.render(f["scene"], H, H, ref_spp, DEPTH, RR, 99991, aux=False, counts=False,
+                         window=win)["radiance"]
+        refs.append((win, ref))
+    per_frame = [{"hr": f["hr"], "s": f["s"], "hrls_spp": f["spp_h"]} for f in frames]
+    for prec in ("bf16", "fp8"):
+        ms = timed_graph(lambda: (render_all(), fuse_all(prec)))
+        ps = []
+        for f, (win, ref), pf in zip(frames, refs, per_frame):
+            x0, y0, w, _ = win
+            img = bufs[f["group"]]["fused"][f["index"], y0:y0 + w, x0:x0 + w].contiguous()
+            p = mrs.image_metrics(img, ref)[0]
+            pf[f"psnr_{prec}"] = round(p, 3)
+            ps.append(p)
+        result[prec] = {"ms_per_batch": ms, "ms_per_frame": ms / n_jobs,
+                        "frames_per_s": n_jobs / ms * 1e3,
+                        "mean_psnr_db_vs_4096spp": float(np.mean(ps)), "psnr_frames": len(ps)}
+    result["renders_ms_batched"] = renders_ms
+    result["renders_ms_one_call_per_render"] = per_call_ms
+    result["render_msamples_per_s_batched"] = result["paths_per_batch"] / renders_ms / 1e3
+    result["per_frame"] = per_frame
+    result["psnr_note"] = (f"each frame's central {psnr_window}^2 window (the whole frame if smaller) "
+                           f"against a {ref_spp}-spp window render")
+    mrs.conv_set_ring(0)
+    ctx.close()
+    for f in frames:
+        f["scene"].close()
+    net.close()
     return result
 
 

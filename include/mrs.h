@@ -301,6 +301,36 @@ mrs_status mrs_render_window(mrs_ctx ctx, mrs_scene scene, int32_t W, int32_t H,
                              int32_t rr_start, uint64_t seed, int32_t grid,
                              const mrs_render_out* out, void* stream);
 
+/* Many renders in one pass (serving many frames of different scenes, sizes
+ * and sample counts): each job is the render mrs_render_grid would produce
+ * for its arguments (radiance and the albedo / normal / depth layers; every
+ * output bit-identical to that call's), but the jobs' paths share waves:
+ * each job's samples are cut into chunks that fit the context's wave size
+ * (mrs_ctx_set_wave, whole samples of every pixel, at least one), and
+ * consecutive chunks of up to 32 jobs fill one wave, whose ray generation,
+ * bounce-0 traversal / shading / shadow rays and persistent tail kernel
+ * are one launch each over all of its jobs (the jobs' scenes, cameras and
+ * seeds travel as a table in the launch).  Each chunk's samples are then
+ * added to its job's per-pixel sums in sample order, so chunking changes
+ * nothing.  Per-bounce ray counts are not reported per job.  ctx is
+ * required (its arena holds the largest wave's path state and every job's
+ * accumulator; make the first call of a size before any stream capture).
+ * jobs HOST array [n_jobs] (1 .. 4096), read before the call returns; each
+ * job's radiance (required) and albedo, normal, depth (may be NULL) are
+ * device buffers as for mrs_render; grid as mrs_render_grid; other
+ * arguments as mrs_render. */
+typedef struct {
+    mrs_scene scene;
+    int32_t W, H, spp, max_depth, rr_start;
+    uint64_t seed;
+    int32_t grid;
+    float* radiance;
+    float* albedo;
+    float* normal;
+    float* depth;
+} mrs_render_job;
+mrs_status mrs_render_batch(mrs_ctx ctx, const mrs_render_job* jobs, int32_t n_jobs, void* stream);
+
 /* Paths per wave for subsequent mrs_render calls on this scene (rounded to
  * whole samples of the image; default 16M paths).  For tests and tuning. */
 mrs_status mrs_scene_set_wave(mrs_scene scene, int64_t max_paths_per_wave);
@@ -487,6 +517,14 @@ mrs_status mrs_gate_async(const float* fused, const float* lrhs, const float* pl
 mrs_status mrs_conv3x3(const float* x, int32_t N, int32_t H, int32_t W, int32_t cin,
                        int32_t cout, const float* w, const float* b, int32_t relu,
                        int32_t precision, float* out, void* stream);
+
+/* Tuning of the tensor-core convolution (for autotuners; no paper
+ * counterpart): the depth of its ring of input rows in shared memory,
+ * i.e. how many rows the TMA producer may load ahead of the MMAs, for every
+ * later launch in the process.  0 (the default) takes the most that fits
+ * the shared memory beside the weights and staging slots; 3 .. 12 asks for
+ * that many (capped at what fits).  Results do not depend on it. */
+mrs_status mrs_conv_set_ring(int32_t stages);
 
 /* Training loss of mrs_train_step (a property of the net, default
  * MRS_LOSS_L1LOG):

@@ -42,6 +42,7 @@ SIGS = {
     "mrs_render_grid": [P, P, I32, I32, I32, I32, I32, U64, I32, P, P, P, P, P, P, P],
     "mrs_render_layers": [P, P, I32, I32, I32, I32, I32, U64, I32, P, P],
     "mrs_render_window": [P, P, I32, I32, I32, I32, I32, I32, I32, I32, I32, U64, I32, P, P],
+    "mrs_render_batch": [P, P, I32, P],
     "mrs_render_stats": [P, I32, I32, I32, I32, I32, U64, P, P, P],
     "mrs_profile_enable": [I32],
     "mrs_profile_read": [I32, P, P],
@@ -58,6 +59,7 @@ SIGS = {
     "mrs_train_step_extra": [P, P, P, P, P, P, P, I32, I32, I32, I32, F32, I32, P, P],
     "mrs_net_get_grads": [P, P],
     "mrs_conv3x3_dgrad": [P, I32, I32, I32, I32, I32, P, I32, P, I32, P, P],
+    "mrs_conv_set_ring": [I32],
     "mrs_net_save": [P, ctypes.c_char_p, U64],
     "mrs_net_load": [P, ctypes.c_char_p, P],
     "mrs_net_create_seeded": [I32, U64, F32, P],

@@ -29,6 +29,8 @@
 #include <cuda_fp8.h>
 #include <string.h>
 
+#include <atomic>
+
 #include "conv_tc.cuh"
 
 namespace mrs {
@@ -718,19 +720,25 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
     return fn;
 }
 
+// input-row ring depth of the conv (0: the most that fits shared memory)
+std::atomic<int> g_fold_ring{0};
+
 template <int NOUT, int OPER>
 mrs_status launch_fold(const TcConvArgs& a, cudaStream_t st)
 {
-    int stages = 4;
-    while (fold_smem_bytes<NOUT, OPER>(stages + 1) <= 227 * 1024 && stages < 12) ++stages;
-    size_t smem = fold_smem_bytes<NOUT, OPER>(stages);
+    int smax = 4;
+    while (fold_smem_bytes<NOUT, OPER>(smax + 1) <= 227 * 1024 && smax < 12) ++smax;
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_conv_fold<NOUT, OPER>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)fold_smem_bytes<NOUT, OPER>(smax));
         if (e != cudaSuccess) return cuda_status(e, "conv smem attribute");
         attr = true;
     }
+    const int want = g_fold_ring.load(std::memory_order_relaxed);
+    const int stages = want >= 3 ? (want < smax ? want : smax) : smax;
+    size_t smem = fold_smem_bytes<NOUT, OPER>(stages);
     TcConvArgs b = a;
     const long long T = (long long)a.N * ((a.W + kFoldTile - 1) / kFoldTile) * a.H;
     int grid = T < sm_count() ? (int)T : sm_count();
@@ -846,6 +854,8 @@ mrs_status tc_wait_selftest(long long limit_cycles, int* gave_up, cudaStream_t s
     *gave_up = h[1] && h[0];
     return MRS_OK;
 }
+
+void tc_set_ring(int stages) { g_fold_ring.store(stages, std::memory_order_relaxed); }
 
 mrs_status tc_conv3x3(const TcConvArgs& a, cudaStream_t st)
 {

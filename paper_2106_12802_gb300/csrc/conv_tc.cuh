@@ -78,6 +78,8 @@ mrs_status tc_make_view_map(CUtensorMap* m, const void* ptr, int N, int H, int W
 mrs_status tc_make_w_map(CUtensorMap* m, const void* ptr, int rows, int nout, int operand);
 
 mrs_status tc_conv3x3(const TcConvArgs& a, cudaStream_t st);
+// input-row ring depth of every later conv launch (0: the most that fits)
+void tc_set_ring(int stages);
 
 // Weight and bias gradients of a 3x3 conv (zero padding 1) on the tensor
 // cores, as per-CTA partial sums:

@@ -1889,6 +1889,13 @@ extern "C" mrs_status mrs_conv3x3_dgrad(const float* dy, int32_t N, int32_t H, i
     return rc;
 }
 
+extern "C" mrs_status mrs_conv_set_ring(int32_t stages)
+{
+    MRS_ARG(stages == 0 || (stages >= 3 && stages <= 12), "stages must be 0 or in [3, 12]");
+    mrs::tc_set_ring(stages);
+    return MRS_OK;
+}
+
 extern "C" mrs_status mrs_net_set_loss(mrs_net net, int32_t loss, float beta)
 {
     MRS_ARG(net != nullptr, "net is NULL");

@@ -10,6 +10,9 @@
 // single correctly rounded binary32 operation in the order written, which is
 // what makes the per-bounce ray counts and the radiance reproducible
 // bit-for-bit by an independent CPU implementation of the same estimator.
+#include <algorithm>
+#include <vector>
+
 #include "common.cuh"
 
 namespace mrs {
@@ -311,52 +314,92 @@ __device__ bool bsdf_sample(const Mat& m, V3 wo, float u1, float u2, V3& wi, V3&
 }
 
 // ---- wave kernels -----------------------------------------------------------
-struct WaveParams {
+// One render job's part of a wave: its scene, camera and image, and the
+// samples of its pixels that the wave holds -- paths path_off .. path_off +
+// n_paths - 1, path path_off + q being sample s0 + q % kk of the job's
+// (window) pixel q / kk
+struct JobView {
     SceneView S;
-    PathSoA P;
     float env[3];
     float cam[12];
     int W, H, max_depth, rr_start;   // W x H: the whole image (camera, RNG pixel ids)
     int win_x0, win_y0, win_w;       // the rendered window of it (its width); whole image:
     bool windowed;                   // 0, 0, W and windowed = false
     int grid;            // camera sampling grid (1 = whole pixel footprint)
-    int layers;          // record the first-hit lobe (diffuse / specular / variance layers)
-    int64_t wh;          // pixels
     int s0;              // first sample index of the wave
     int kk;              // samples per pixel in the wave
-    int n_paths;         // paths in the wave (= kk * wh)
+    int path_off;        // the job's first path in the wave
+    int n_paths;         // its paths in the wave (= kk * pixels)
     uint2 key;
+};
+
+struct WaveParams {
+    JobView J;           // the job of a one-job wave (a single render)
+    PathSoA P;
+    int layers;          // record the first-hit lobe (diffuse / specular / variance layers)
+    int64_t wh;          // pixels of the job (accumulation)
+    int n_paths;         // paths in the wave (every job's)
     uint32_t* cnt;       // [max_depth + 2] extension rays per bounce
     uint32_t* scnt;      // [max_depth + 1] shadow rays per bounce
     unsigned long long* stats;   // counting variant: node visits / triangle tests (closest, shadow)
 };
 
-// image pixel id of path p (the Philox counter's pixel): path p is sample
-// p % kk of window pixel p / kk
-__device__ __forceinline__ int pixel_of(const WaveParams& w, int p)
+// A batched wave holds several jobs (different scenes, images, sample
+// counts); their table travels as a kernel parameter.  The job of path p is
+// the one wave job (OneJob) or the table entry whose paths contain p
+// (ManyJobs: binary search over path_off).
+constexpr int kMaxWaveJobs = 32;
+struct JobTable {
+    int n;
+    JobView J[kMaxWaveJobs];
+};
+struct OneJob {
+    const JobView& J;
+    __device__ __forceinline__ const JobView& operator()(int) const { return J; }
+};
+struct ManyJobs {
+    const JobTable& T;
+    __device__ __forceinline__ const JobView& operator()(int p) const
+    {
+        int lo = 0, hi = T.n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (T.J[mid].path_off <= p) lo = mid;
+            else hi = mid - 1;
+        }
+        return T.J[lo];
+    }
+};
+
+// image pixel id of the job's path q (relative to path_off; the Philox
+// counter's pixel): sample q % kk of window pixel q / kk
+__device__ __forceinline__ int pixel_of(const JobView& J, int q)
 {
-    const int lp = p / w.kk;
-    if (!w.windowed) return lp;
-    return (w.win_y0 + lp / w.win_w) * w.W + (w.win_x0 + lp % w.win_w);
+    const int lp = q / J.kk;
+    if (!J.windowed) return lp;
+    return (J.win_y0 + lp / J.win_w) * J.W + (J.win_x0 + lp % J.win_w);
 }
 
-__global__ void __launch_bounds__(kThreads) k_raygen(WaveParams w)
+template <class Jobs>
+__device__ __forceinline__ void raygen_body(const WaveParams& w, const Jobs& jobs)
 {
-    PathSoA& P = w.P;
+    const PathSoA& P = w.P;
     if (blockIdx.x == 0 && threadIdx.x == 0) w.cnt[0] = (uint32_t)w.n_paths;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < w.n_paths; p += gridDim.x * blockDim.x) {
-        int pix = pixel_of(w, p);
-        int sample = w.s0 + p % w.kk;
-        int px = pix % w.W, py = pix / w.W;
-        float4 g1 = draws((uint32_t)pix, (uint32_t)sample, 0u, 1u, w.key);
-        const float* cam = w.cam;
+        const JobView& J = jobs(p);
+        const int q = p - J.path_off;
+        int pix = pixel_of(J, q);
+        int sample = J.s0 + q % J.kk;
+        int px = pix % J.W, py = pix / J.W;
+        float4 g1 = draws((uint32_t)pix, (uint32_t)sample, 0u, 1u, J.key);
+        const float* cam = J.cam;
         // grid g > 1: only the centre sub-pixel (g px + g/2, g py + g/2) of the
         // pixel's g x g block is sampled (nearest-neighbour downsampling of a
         // g-times finer image: the low-resolution renders of Sec. 3); g = 1 is
         // the whole pixel footprint, the same operations as without a grid
-        const int g = w.grid;
-        float sx = ((float)(px * g + g / 2) + g1.z) / (float)(w.W * g);
-        float sy = ((float)(py * g + g / 2) + g1.w) / (float)(w.H * g);
+        const int g = J.grid;
+        float sx = ((float)(px * g + g / 2) + g1.z) / (float)(J.W * g);
+        float sy = ((float)(py * g + g / 2) + g1.w) / (float)(J.H * g);
         float a = 2.0f * sx - 1.0f, bq = 1.0f - 2.0f * sy;
         V3 d = normalize(mk(cam[3] + cam[6] * a + cam[9] * bq, cam[4] + cam[7] * a + cam[10] * bq,
                             cam[5] + cam[8] * a + cam[11] * bq));
@@ -371,18 +414,18 @@ __global__ void __launch_bounds__(kThreads) k_raygen(WaveParams w)
     }
 }
 
-template <bool kCount>
-__global__ void __launch_bounds__(kThreads, 8) k_trace(WaveParams w, int b)
+template <bool kCount, class Jobs>
+__device__ __forceinline__ void trace_body(const WaveParams& w, const Jobs& jobs, int b)
 {
     unsigned long long nv = 0, nt = 0;
-    PathSoA& P = w.P;
+    const PathSoA& P = w.P;
     const int count = (int)*(volatile uint32_t*)&w.cnt[b];
     const int* q = (b & 1) ? P.q1 : P.q0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
         int p = b == 0 ? i : q[i];
         V3 o = mk(P.ox[p], P.oy[p], P.oz[p]), d = mk(P.dx[p], P.dy[p], P.dz[p]);
         float t = -1.0f;
-        int k = traverse<false, kCount>(w.S, o, d, T_INF, t, &nv, &nt);
+        int k = traverse<false, kCount>(jobs(p).S, o, d, T_INF, t, &nv, &nt);
         P.hit_t[p] = t;
         P.hit_id[p] = k;
     }
@@ -409,12 +452,12 @@ struct ShadeConst {
     int n_choices;
     float pick;
 };
-__device__ __forceinline__ ShadeConst shade_const(const WaveParams& w)
+__device__ __forceinline__ ShadeConst shade_const(const JobView& J)
 {
     ShadeConst c;
-    c.env = mk(w.env[0], w.env[1], w.env[2]);
+    c.env = mk(J.env[0], J.env[1], J.env[2]);
     c.env_on = c.env.x > 0.0f || c.env.y > 0.0f || c.env.z > 0.0f;
-    c.n_choices = w.S.n_lights + (c.env_on ? 1 : 0);
+    c.n_choices = J.S.n_lights + (c.env_on ? 1 : 0);
     c.pick = c.n_choices > 0 ? 1.0f / (float)c.n_choices : 0.0f;
     return c;
 }
@@ -425,11 +468,12 @@ __device__ __forceinline__ ShadeConst shade_const(const WaveParams& w)
 // roulette.  cont: the path continues to bounce b + 1; shadow: a shadow ray
 // was set up.  Shared by the wavefront kernel and the tail kernel, so that a
 // path's arithmetic does not depend on which one shades it.
-__device__ __forceinline__ void shade_path(const WaveParams& w, const ShadeConst& sc0, int b,
-                                           int p, bool& cont, bool& shadow)
+__device__ __forceinline__ void shade_path(const WaveParams& w, const JobView& J,
+                                           const ShadeConst& sc0, int b, int p, bool& cont,
+                                           bool& shadow)
 {
     const PathSoA& P = w.P;
-    const SceneView& S = w.S;
+    const SceneView& S = J.S;
     const V3 env = sc0.env;
     const bool env_on = sc0.env_on;
     const int n_choices = sc0.n_choices;
@@ -478,13 +522,14 @@ __device__ __forceinline__ void shade_path(const WaveParams& w, const ShadeConst
             L = mk(L.x + beta.x * m.Le.x * wgt, L.y + beta.y * m.Le.y * wgt,
                    L.z + beta.z * m.Le.z * wgt);
         }
-        if (b == w.max_depth) break;
+        if (b == J.max_depth) break;
         if (!(m.albedo.x > 0.0f || m.albedo.y > 0.0f || m.albedo.z > 0.0f)) break;
 
-        int pix = pixel_of(w, p);
-        uint32_t sample = (uint32_t)(w.s0 + p % w.kk);
-        float4 g0 = draws((uint32_t)pix, sample, (uint32_t)b, 0u, w.key);
-        float4 g1 = draws((uint32_t)pix, sample, (uint32_t)b, 1u, w.key);
+        const int qj = p - J.path_off;
+        int pix = pixel_of(J, qj);
+        uint32_t sample = (uint32_t)(J.s0 + qj % J.kk);
+        float4 g0 = draws((uint32_t)pix, sample, (uint32_t)b, 0u, J.key);
+        float4 g1 = draws((uint32_t)pix, sample, (uint32_t)b, 1u, J.key);
         V3 T, B;
         basis(ns, T, B);
         V3 wo = to_local(d * -1.0f, T, B, ns);
@@ -548,7 +593,7 @@ __device__ __forceinline__ void shade_path(const WaveParams& w, const ShadeConst
         pdf_b = pb;
         pdf_e = env_on ? pick * wl.z * INV_PI_F : 0.0f;
         if (!(maxc(beta) > 0.0f)) break;
-        if (b >= w.rr_start) {
+        if (b >= J.rr_start) {
             float qq = fminf(0.95f, maxc(beta));
             if (g1.y >= qq) break;
             beta = mk(beta.x / qq, beta.y / qq, beta.z / qq);
@@ -562,13 +607,13 @@ __device__ __forceinline__ void shade_path(const WaveParams& w, const ShadeConst
     P.Lx[p] = L.x; P.Ly[p] = L.y; P.Lz[p] = L.z;
 }
 
-__global__ void __launch_bounds__(kThreads) k_shade(WaveParams w, int b)
+template <class Jobs>
+__device__ __forceinline__ void shade_body(const WaveParams& w, const Jobs& jobs, int b)
 {
-    PathSoA& P = w.P;
+    const PathSoA& P = w.P;
     const int count = (int)*(volatile uint32_t*)&w.cnt[b];
     const int* q = (b & 1) ? P.q1 : P.q0;
     int* qn = (b & 1) ? P.q0 : P.q1;
-    const ShadeConst sc0 = shade_const(w);
     const int stride = gridDim.x * blockDim.x;
     const int end = (count + 31) & ~31;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < end; i += stride) {
@@ -576,7 +621,8 @@ __global__ void __launch_bounds__(kThreads) k_shade(WaveParams w, int b)
         int p = 0;
         if (i < count) {
             p = b == 0 ? i : q[i];
-            shade_path(w, sc0, b, p, cont, shadow);
+            const JobView& J = jobs(p);
+            shade_path(w, J, shade_const(J), b, p, cont, shadow);
         }
         int slot = warp_append(cont, &w.cnt[b + 1]);
         if (cont) qn[slot] = p;
@@ -585,17 +631,17 @@ __global__ void __launch_bounds__(kThreads) k_shade(WaveParams w, int b)
     }
 }
 
-template <bool kCount>
-__global__ void __launch_bounds__(kThreads, 8) k_shadow(WaveParams w, int b)
+template <bool kCount, class Jobs>
+__device__ __forceinline__ void shadow_body(const WaveParams& w, const Jobs& jobs, int b)
 {
     unsigned long long nv = 0, nt = 0;
-    PathSoA& P = w.P;
+    const PathSoA& P = w.P;
     const int count = (int)*(volatile uint32_t*)&w.scnt[b];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
         int p = P.qs[i];
         V3 o = mk(P.ox[p], P.oy[p], P.oz[p]), d = mk(P.sdx[p], P.sdy[p], P.sdz[p]);
         float t;
-        if (traverse<true, kCount>(w.S, o, d, P.stmax[p], t, &nv, &nt) < 0) {
+        if (traverse<true, kCount>(jobs(p).S, o, d, P.stmax[p], t, &nv, &nt) < 0) {
             P.Lx[p] = P.Lx[p] + P.scx[p];
             P.Ly[p] = P.Ly[p] + P.scy[p];
             P.Lz[p] = P.Lz[p] + P.scz[p];
@@ -615,17 +661,17 @@ __global__ void __launch_bounds__(kThreads, 8) k_shadow(WaveParams w, int b)
 // 32 registers and 8 blocks per SM, as the traversal kernels: with 64
 // registers (4 blocks) the tail ran 2-7% slower despite no spills.
 constexpr int kWorkSlot = 63;
-template <bool kCount>
-__global__ void __launch_bounds__(kThreads, 8) k_tail(WaveParams w, int b0)
+template <bool kCount, class Jobs>
+__device__ __forceinline__ void tail_body(const WaveParams& w, const Jobs& jobs, int b0,
+                                          int max_depth)
 {
     __shared__ uint32_t s_cnt[64], s_scnt[64];
     for (int j = threadIdx.x; j < 64; j += blockDim.x) { s_cnt[j] = 0u; s_scnt[j] = 0u; }
     __syncthreads();
     unsigned long long nv = 0, nt = 0, sv = 0, stt = 0;
-    PathSoA& P = w.P;
+    const PathSoA& P = w.P;
     const int count = (int)*(volatile uint32_t*)&w.cnt[b0];
     const int* q = (b0 & 1) ? P.q1 : P.q0;
-    const ShadeConst sc0 = shade_const(w);
     const int lane = threadIdx.x & 31;
     int p = -1, b = b0;
     bool drained = false;   // warp-uniform: the queue has been handed out
@@ -646,18 +692,19 @@ __global__ void __launch_bounds__(kThreads, 8) k_tail(WaveParams w, int b0)
         }
         if (!__any_sync(0xffffffffu, p >= 0)) break;
         if (p < 0) continue;
+        const JobView& J = jobs(p);
         V3 o = mk(P.ox[p], P.oy[p], P.oz[p]), d = mk(P.dx[p], P.dy[p], P.dz[p]);
         float t = -1.0f;
-        const int k = traverse<false, kCount>(w.S, o, d, T_INF, t, &nv, &nt);
+        const int k = traverse<false, kCount>(J.S, o, d, T_INF, t, &nv, &nt);
         P.hit_t[p] = t;
         P.hit_id[p] = k;
         bool cont = false, shadow = false;
-        shade_path(w, sc0, b, p, cont, shadow);
+        shade_path(w, J, shade_const(J), b, p, cont, shadow);
         if (shadow) {
             atomicAdd(&s_scnt[b], 1u);
             V3 so = mk(P.ox[p], P.oy[p], P.oz[p]), sd = mk(P.sdx[p], P.sdy[p], P.sdz[p]);
             float ts;
-            if (traverse<true, kCount>(w.S, so, sd, P.stmax[p], ts, &sv, &stt) < 0) {
+            if (traverse<true, kCount>(J.S, so, sd, P.stmax[p], ts, &sv, &stt) < 0) {
                 P.Lx[p] = P.Lx[p] + P.scx[p];
                 P.Ly[p] = P.Ly[p] + P.scy[p];
                 P.Lz[p] = P.Lz[p] + P.scz[p];
@@ -667,9 +714,9 @@ __global__ void __launch_bounds__(kThreads, 8) k_tail(WaveParams w, int b0)
         else p = -1;
     }
     __syncthreads();
-    for (int j = b0 + threadIdx.x; j <= w.max_depth + 1; j += blockDim.x) {
+    for (int j = b0 + threadIdx.x; j <= max_depth + 1; j += blockDim.x) {
         if (j > b0 && s_cnt[j]) atomicAdd(&w.cnt[j], s_cnt[j]);
-        if (j <= w.max_depth && s_scnt[j]) atomicAdd(&w.scnt[j], s_scnt[j]);
+        if (j <= max_depth && s_scnt[j]) atomicAdd(&w.scnt[j], s_scnt[j]);
     }
     if (kCount) {
         atomicAdd(&w.stats[0], nv); atomicAdd(&w.stats[1], nt);
@@ -677,6 +724,57 @@ __global__ void __launch_bounds__(kThreads, 8) k_tail(WaveParams w, int b0)
         atomicAdd(&w.stats[4], nv); atomicAdd(&w.stats[5], nt);
         atomicAdd(&w.stats[6], sv); atomicAdd(&w.stats[7], stt);
     }
+}
+
+// The kernels: a one-job wave (a render) and a batched wave (a table of jobs)
+__global__ void __launch_bounds__(kThreads) k_raygen(const __grid_constant__ WaveParams w)
+{
+    raygen_body(w, OneJob{w.J});
+}
+__global__ void __launch_bounds__(kThreads)
+    k_raygen_b(const __grid_constant__ WaveParams w, const __grid_constant__ JobTable T)
+{
+    raygen_body(w, ManyJobs{T});
+}
+template <bool kCount>
+__global__ void __launch_bounds__(kThreads, 8) k_trace(const __grid_constant__ WaveParams w, int b)
+{
+    trace_body<kCount>(w, OneJob{w.J}, b);
+}
+__global__ void __launch_bounds__(kThreads, 8)
+    k_trace_b(const __grid_constant__ WaveParams w, const __grid_constant__ JobTable T, int b)
+{
+    trace_body<false>(w, ManyJobs{T}, b);
+}
+__global__ void __launch_bounds__(kThreads) k_shade(const __grid_constant__ WaveParams w, int b)
+{
+    shade_body(w, OneJob{w.J}, b);
+}
+__global__ void __launch_bounds__(kThreads)
+    k_shade_b(const __grid_constant__ WaveParams w, const __grid_constant__ JobTable T, int b)
+{
+    shade_body(w, ManyJobs{T}, b);
+}
+template <bool kCount>
+__global__ void __launch_bounds__(kThreads, 8) k_shadow(const __grid_constant__ WaveParams w, int b)
+{
+    shadow_body<kCount>(w, OneJob{w.J}, b);
+}
+__global__ void __launch_bounds__(kThreads, 8)
+    k_shadow_b(const __grid_constant__ WaveParams w, const __grid_constant__ JobTable T, int b)
+{
+    shadow_body<false>(w, ManyJobs{T}, b);
+}
+template <bool kCount>
+__global__ void __launch_bounds__(kThreads, 8) k_tail(const __grid_constant__ WaveParams w, int b0)
+{
+    tail_body<kCount>(w, OneJob{w.J}, b0, w.J.max_depth);
+}
+__global__ void __launch_bounds__(kThreads, 8)
+    k_tail_b(const __grid_constant__ WaveParams w, const __grid_constant__ JobTable T, int b0,
+             int max_depth)
+{
+    tail_body<false>(w, ManyJobs{T}, b0, max_depth);
 }
 
 // Path p of a wave is sample p % kk of pixel p / kk: a pixel's samples are
@@ -707,9 +805,11 @@ template <> struct Vec<4> {
 
 // per pixel: add this wave's samples in sample order (Kahan for radiance)
 template <int V>
-__global__ void __launch_bounds__(kThreads) k_accumulate(WaveParams w, float* acc, int kk)
+__global__ void __launch_bounds__(kThreads) k_accumulate(const __grid_constant__ WaveParams w,
+                                                          float* acc, int kk)
 {
-    PathSoA& P = w.P;
+    const PathSoA& P = w.P;
+    const int64_t poff = w.J.path_off;
     const int64_t wh = w.wh;
     for (int64_t pix = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; pix < wh;
          pix += (int64_t)gridDim.x * blockDim.x) {
@@ -717,7 +817,7 @@ __global__ void __launch_bounds__(kThreads) k_accumulate(WaveParams w, float* ac
         float s0 = a[0], s1 = a[1], s2 = a[2], c0 = a[3], c1 = a[4], c2 = a[5];
         float ax = a[6], ay = a[7], az = a[8], nx = a[9], ny = a[10], nz = a[11], ds = a[12];
         for (int sb = 0; sb < kk; sb += V) {
-            const int64_t p = pix * kk + sb;
+            const int64_t p = poff + pix * kk + sb;
             Vec<V> Lx, Ly, Lz, Ax, Ay, Az, Nx, Ny, Nz, D;
             Lx.load(P.Lx + p); Ly.load(P.Ly + p); Lz.load(P.Lz + p);
             Ax.load(P.ax + p); Ay.load(P.ay + p); Az.load(P.az + p);
@@ -743,9 +843,11 @@ __global__ void __launch_bounds__(kThreads) k_accumulate(WaveParams w, float* ac
 // (each sample's radiance to the layer of its first-hit lobe) and the sum of
 // squares for the variance, plain FP32 sums in sample order
 template <int V>
-__global__ void __launch_bounds__(kThreads) k_accumulate_layers(WaveParams w, float* acc2, int kk)
+__global__ void __launch_bounds__(kThreads) k_accumulate_layers(const __grid_constant__ WaveParams w,
+                                                                 float* acc2, int kk)
 {
-    PathSoA& P = w.P;
+    const PathSoA& P = w.P;
+    const int64_t poff = w.J.path_off;
     const int64_t wh = w.wh;
     for (int64_t pix = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; pix < wh;
          pix += (int64_t)gridDim.x * blockDim.x) {
@@ -753,7 +855,7 @@ __global__ void __launch_bounds__(kThreads) k_accumulate_layers(WaveParams w, fl
         float d0 = e[0], d1 = e[1], d2 = e[2], p0 = e[3], p1 = e[4], p2 = e[5];
         float q0 = e[6], q1 = e[7], q2 = e[8];
         for (int sb = 0; sb < kk; sb += V) {
-            const int64_t p = pix * kk + sb;
+            const int64_t p = poff + pix * kk + sb;
             Vec<V> Lx, Ly, Lz, Lo;
             Lx.load(P.Lx + p); Ly.load(P.Ly + p); Lz.load(P.Lz + p);
             Lo.load_int(P.lobe + p);
@@ -861,6 +963,17 @@ int tail_grid(bool counting)
     return v;
 }
 
+int tail_grid_batch()
+{
+    static int v = 0;
+    if (!v) {
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tail_b, kThreads, 0);
+        v = sm_count() * (per_sm < 1 ? 1 : per_sm);
+    }
+    return v;
+}
+
 inline int grid_for(int64_t n)
 {
     int64_t g = (n + kThreads - 1) / kThreads;
@@ -935,18 +1048,19 @@ static mrs_status render_impl(mrs_scene S, Buf& arena, int64_t wave_paths, int32
     float* acc2 = layers ? (float*)(base + off_acc2) : nullptr;
 
     WaveParams w;
-    w.S = view(S);
+    w.J.S = view(S);
     w.P = soa;
-    memcpy(w.env, S->env, sizeof(w.env));
-    memcpy(w.cam, S->cam, sizeof(w.cam));
-    w.W = W; w.H = H; w.max_depth = max_depth;
-    w.win_x0 = wx0; w.win_y0 = wy0; w.win_w = ww;
-    w.windowed = ww != W || wh_ != H;
-    w.grid = grid;
+    memcpy(w.J.env, S->env, sizeof(w.J.env));
+    memcpy(w.J.cam, S->cam, sizeof(w.J.cam));
+    w.J.W = W; w.J.H = H; w.J.max_depth = max_depth;
+    w.J.win_x0 = wx0; w.J.win_y0 = wy0; w.J.win_w = ww;
+    w.J.windowed = ww != W || wh_ != H;
+    w.J.grid = grid;
     w.layers = layers ? 1 : 0;
-    w.rr_start = rr_start < 0 ? 0x7fffffff : rr_start;
+    w.J.rr_start = rr_start < 0 ? 0x7fffffff : rr_start;
+    w.J.path_off = 0;
     w.wh = wh;
-    w.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    w.J.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
     w.cnt = cnt;
     w.scnt = scnt;
     w.stats = stats;
@@ -957,9 +1071,10 @@ static mrs_status render_impl(mrs_scene S, Buf& arena, int64_t wave_paths, int32
     if (shadow_counts) MRS_CHECK(cudaMemsetAsync(shadow_counts, 0, sizeof(uint64_t) * nb, st));
     for (int s0 = 0; s0 < spp; s0 += (int)k) {
         int kk = (int)((spp - s0) < k ? (spp - s0) : k);
-        w.s0 = s0;
-        w.kk = kk;
-        w.n_paths = (int)(kk * wh);
+        w.J.s0 = s0;
+        w.J.kk = kk;
+        w.J.n_paths = (int)(kk * wh);
+        w.n_paths = w.J.n_paths;
         MRS_CHECK(cudaMemsetAsync(cnt, 0, 4 * 2 * 64, st));
         int g = grid_for(w.n_paths);
         MRS_TIMED(PK_RAYGEN, st, k_raygen<<<g, kThreads, 0, st>>>(w));
@@ -1107,6 +1222,173 @@ extern "C" mrs_status mrs_render_window(mrs_ctx ctx, mrs_scene S, int32_t W, int
     return render_impl(S, arena, wave, tail, W, H, spp, max_depth, rr_start, seed, grid, out->radiance,
                        out->albedo, out->normal, out->depth, out->diffuse, out->specular,
                        out->variance, out->counts, out->shadow_counts, nullptr, stream, win);
+}
+
+namespace mrs {
+namespace {
+
+// one job's chunk of samples: samples s0 .. s0 + kk - 1 of every pixel
+struct Chunk { int job, s0, kk; int64_t paths; };
+
+mrs_status render_batch_impl(mrs_ctx ctx, const mrs_render_job* jobs, int32_t n_jobs,
+                             cudaStream_t st)
+{
+    MRS_ARG(ctx != nullptr, "ctx is NULL (a batch keeps its path state in a render context)");
+    MRS_ARG(jobs != nullptr && n_jobs >= 1 && n_jobs <= 4096, "n_jobs must be in [1, 4096]");
+    for (int j = 0; j < n_jobs; ++j) {
+        const mrs_render_job& J = jobs[j];
+        MRS_ARG(J.scene != nullptr, "job scene is NULL");
+        MRS_ARG(J.W >= 1 && J.W <= 16384 && J.H >= 1 && J.H <= 16384, "job W, H must be in [1, 16384]");
+        MRS_ARG(J.spp >= 1 && J.spp <= 65536, "job spp must be in [1, 65536]");
+        MRS_ARG(J.max_depth >= 0 && J.max_depth <= 32, "job max_depth must be in [0, 32]");
+        MRS_ARG(J.grid >= 1 && J.grid <= 64, "job grid must be in [1, 64]");
+        MRS_ARG((int64_t)J.W * J.grid <= 65536 && (int64_t)J.H * J.grid <= 65536,
+                "job W * grid, H * grid must be <= 65536");
+        MRS_ARG(J.radiance != nullptr, "job radiance is NULL");
+    }
+    const int64_t cap = ctx->wave_paths;
+    // chunks: as many samples per pixel as fit the wave (at least one), in
+    // sample order; then waves: consecutive chunks up to the capacity (a job
+    // never has two chunks in one wave: two would exceed it)
+    std::vector<Chunk> chunks;
+    int64_t total_px = 0;
+    std::vector<int64_t> acc_off(n_jobs);
+    for (int j = 0; j < n_jobs; ++j) {
+        const int64_t wh = (int64_t)jobs[j].W * jobs[j].H;
+        acc_off[j] = total_px;
+        total_px += wh;
+        int64_t k = cap / wh;
+        if (k < 1) k = 1;
+        if (k > jobs[j].spp) k = jobs[j].spp;
+        MRS_ARG(k * wh <= (int64_t(1) << 31) - 1, "wave too large");
+        for (int s0 = 0; s0 < jobs[j].spp; s0 += (int)k) {
+            const int kk = (int)((jobs[j].spp - s0) < k ? (jobs[j].spp - s0) : k);
+            chunks.push_back({j, s0, kk, kk * wh});
+        }
+    }
+    std::vector<std::pair<size_t, size_t>> waves;   // chunk ranges [a, b)
+    int64_t pmax = 0;
+    for (size_t a = 0; a < chunks.size();) {
+        size_t b = a + 1;
+        int64_t n = chunks[a].paths;
+        while (b < chunks.size() && (int)(b - a) < kMaxWaveJobs && n + chunks[b].paths <= cap &&
+               n + chunks[b].paths <= (int64_t(1) << 31) - 1) {
+            n += chunks[b].paths;
+            ++b;
+        }
+        waves.push_back({a, b});
+        if (n > pmax) pmax = n;
+        a = b;
+    }
+    // arena: the path arrays of the largest wave, then every job's accumulator
+    const int kArrays = 34;
+    size_t arr = ((size_t)pmax * 4 + 255) & ~(size_t)255;
+    size_t off_acc = arr * kArrays;
+    size_t off_cnt = off_acc + (((size_t)total_px * 13 * 4 + 255) & ~(size_t)255);
+    mrs_status rc = ctx->arena.ensure(off_cnt + 4 * 2 * 64);
+    if (rc != MRS_OK) return rc;
+    char* base = ctx->arena.as<char>();
+    float* f[kArrays];
+    for (int i = 0; i < kArrays; ++i) f[i] = (float*)(base + arr * i);
+    PathSoA soa;
+    float** fields[] = {&soa.ox, &soa.oy, &soa.oz, &soa.dx, &soa.dy, &soa.dz, &soa.bx, &soa.by,
+                        &soa.bz, &soa.Lx, &soa.Ly, &soa.Lz, &soa.pdf_b, &soa.pdf_e, &soa.hit_t,
+                        &soa.sdx, &soa.sdy, &soa.sdz, &soa.stmax, &soa.scx, &soa.scy, &soa.scz,
+                        &soa.ax, &soa.ay, &soa.az, &soa.nx, &soa.ny, &soa.nz, &soa.dep};
+    int fi = 0;
+    for (float** fp : fields) *fp = f[fi++];
+    soa.hit_id = (int*)f[fi++];
+    soa.q0 = (int*)f[fi++];
+    soa.q1 = (int*)f[fi++];
+    soa.qs = (int*)f[fi++];
+    soa.lobe = (int*)f[fi++];
+    float* acc = (float*)(base + off_acc);
+    uint32_t* cnt = (uint32_t*)(base + off_cnt);
+    uint32_t* scnt = cnt + 64;
+    MRS_CHECK(cudaMemsetAsync(acc, 0, (size_t)total_px * 13 * 4, st));
+
+    auto job_view = [&](const Chunk& c, int64_t path_off) {
+        const mrs_render_job& J = jobs[c.job];
+        JobView v;
+        memset(&v, 0, sizeof(v));
+        v.S = view(J.scene);
+        memcpy(v.env, J.scene->env, sizeof(v.env));
+        memcpy(v.cam, J.scene->cam, sizeof(v.cam));
+        v.W = J.W; v.H = J.H; v.max_depth = J.max_depth;
+        v.rr_start = J.rr_start < 0 ? 0x7fffffff : J.rr_start;
+        v.win_x0 = 0; v.win_y0 = 0; v.win_w = J.W; v.windowed = false;
+        v.grid = J.grid;
+        v.s0 = c.s0; v.kk = c.kk;
+        v.path_off = (int)path_off; v.n_paths = (int)c.paths;
+        v.key = make_uint2((uint32_t)J.seed, (uint32_t)(J.seed >> 32));
+        return v;
+    };
+    const int32_t tail = ctx->tail_bounce;
+    const int b_tail = tail >= 0 ? tail : 1;
+    for (const auto& wv : waves) {
+        JobTable T;
+        memset(&T, 0, sizeof(T));
+        T.n = (int)(wv.second - wv.first);
+        int64_t off = 0;
+        int maxd = 0;
+        for (size_t c = wv.first; c < wv.second; ++c) {
+            T.J[c - wv.first] = job_view(chunks[c], off);
+            off += chunks[c].paths;
+            maxd = std::max(maxd, jobs[chunks[c].job].max_depth);
+        }
+        WaveParams w;
+        memset(&w, 0, sizeof(w));
+        w.J = T.J[0];
+        w.P = soa;
+        w.layers = 0;
+        w.n_paths = (int)off;
+        w.cnt = cnt;
+        w.scnt = scnt;
+        w.stats = nullptr;
+        MRS_CHECK(cudaMemsetAsync(cnt, 0, 4 * 2 * 64, st));
+        const int g = grid_for(off);
+        MRS_TIMED(PK_RAYGEN, st, k_raygen_b<<<g, kThreads, 0, st>>>(w, T));
+        MRS_LAUNCHED(1);
+        for (int b = 0; b <= maxd && b < b_tail; ++b) {
+            MRS_TIMED(PK_TRACE, st, k_trace_b<<<g, kThreads, 0, st>>>(w, T, b));
+            MRS_TIMED(PK_SHADE, st, k_shade_b<<<g, kThreads, 0, st>>>(w, T, b));
+            MRS_TIMED(PK_SHADOW, st, k_shadow_b<<<g, kThreads, 0, st>>>(w, T, b));
+            MRS_LAUNCHED(3);
+        }
+        if (b_tail <= maxd) {
+            MRS_TIMED(PK_TAIL, st, k_tail_b<<<tail_grid_batch(), kThreads, 0, st>>>(w, T, b_tail, maxd));
+            MRS_LAUNCHED(1);
+        }
+        // each chunk's samples into its job's accumulator, in sample order
+        for (size_t c = wv.first; c < wv.second; ++c) {
+            const Chunk& ch = chunks[c];
+            WaveParams wc = w;
+            wc.J = T.J[c - wv.first];
+            wc.wh = (int64_t)jobs[ch.job].W * jobs[ch.job].H;
+            float* a = acc + acc_off[ch.job] * 13;
+            const bool v4 = ch.kk % 4 == 0 && wc.J.path_off % 4 == 0;
+            if (v4) MRS_TIMED(PK_ACCUM, st, k_accumulate<4><<<grid_for(wc.wh), kThreads, 0, st>>>(wc, a, ch.kk));
+            else MRS_TIMED(PK_ACCUM, st, k_accumulate<1><<<grid_for(wc.wh), kThreads, 0, st>>>(wc, a, ch.kk));
+            MRS_LAUNCHED(1);
+        }
+    }
+    for (int j = 0; j < n_jobs; ++j) {
+        const int64_t wh = (int64_t)jobs[j].W * jobs[j].H;
+        k_resolve<<<grid_for(wh), kThreads, 0, st>>>(acc + acc_off[j] * 13, nullptr, wh, jobs[j].spp,
+                                                     jobs[j].radiance, jobs[j].albedo, jobs[j].normal,
+                                                     jobs[j].depth, nullptr, nullptr, nullptr);
+        MRS_LAUNCHED(1);
+    }
+    return cuda_status(cudaGetLastError(), "batch render launch");
+}
+
+}  // namespace
+}  // namespace mrs
+
+extern "C" mrs_status mrs_render_batch(mrs_ctx ctx, const mrs_render_job* jobs, int32_t n_jobs,
+                                       void* stream)
+{
+    return render_batch_impl(ctx, jobs, n_jobs, (cudaStream_t)stream);
 }
 
 extern "C" mrs_status mrs_render_stats(mrs_scene S, int32_t W, int32_t H, int32_t spp,

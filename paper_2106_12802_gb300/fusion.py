@@ -187,6 +187,12 @@ def conv3x3_wgrad(x, dy, precision="fp32", stream=None):
     return dw, db
 
 
+def conv_set_ring(stages: int):
+    """Input-row ring depth of every later tensor-core conv launch (0: the
+    most that fits; 3 .. 12 otherwise).  Results do not depend on it."""
+    call("mrs_conv_set_ring", int(stages))
+
+
 DGRAD_MODES = {"linear": 0, "relu_mask": 1, "residual": 2}
 
 

@@ -234,6 +234,42 @@ def render(scene: Scene, W, H, spp, max_depth, rr_start=None, seed=0, aux=True, 
     return out
 
 
+class _RenderJob(ctypes.Structure):
+    _fields_ = [("scene", ctypes.c_void_p), ("W", ctypes.c_int32), ("H", ctypes.c_int32),
+                ("spp", ctypes.c_int32), ("max_depth", ctypes.c_int32),
+                ("rr_start", ctypes.c_int32), ("seed", ctypes.c_uint64), ("grid", ctypes.c_int32),
+                ("radiance", ctypes.c_void_p), ("albedo", ctypes.c_void_p),
+                ("normal", ctypes.c_void_p), ("depth", ctypes.c_void_p)]
+
+
+def render_batch(ctx, jobs, stream=None):
+    """mrs_render_batch: jobs is a list of dicts with scene, W, H, spp,
+    max_depth, and optionally rr_start, seed, grid, aux (default True) and
+    out (dict of device tensors).  Returns the list of output dicts
+    (radiance [H,W,3]; albedo, normal [H,W,3], depth [H,W] when aux)."""
+    dev = torch.device("cuda")
+    arr = (_RenderJob * len(jobs))()
+    outs = []
+    for i, j in enumerate(jobs):
+        W, H = int(j["W"]), int(j["H"])
+        out = j.get("out")
+        if out is None:
+            out = {"radiance": torch.empty((H, W, 3), dtype=torch.float32, device=dev)}
+            if j.get("aux", True):
+                out["albedo"] = torch.empty((H, W, 3), dtype=torch.float32, device=dev)
+                out["normal"] = torch.empty((H, W, 3), dtype=torch.float32, device=dev)
+                out["depth"] = torch.empty((H, W), dtype=torch.float32, device=dev)
+        rr = j.get("rr_start")
+        arr[i] = _RenderJob(j["scene"].handle.value, W, H, int(j["spp"]), int(j["max_depth"]),
+                            -1 if rr is None else int(rr), int(j.get("seed", 0)) & (2**64 - 1),
+                            int(j.get("grid", 1)), _ptr(out["radiance"]).value,
+                            *[(_ptr(out[k]).value if out.get(k) is not None else None)
+                              for k in ("albedo", "normal", "depth")])
+        outs.append(out)
+    call("mrs_render_batch", ctx.handle, arr, len(jobs), _stream(stream))
+    return outs
+
+
 def render_stats(scene: Scene, W, H, spp, max_depth, rr_start=None, seed=0, stream=None):
     """Node visits / triangle tests of the closest-hit and shadow traversals
     (all bounces), and the part of them done in the tail kernel (tail_*)."""

@@ -81,6 +81,8 @@ def test_boundary_calls_of_the_method_reject_bad_arguments(lib):
         kind = 0 if prm.sphere_subdiv == 7 else 1
         assert lib.mrs_build_scene_seeded(3, kind, ctypes.byref(prm), None, ctypes.byref(h)) == -1
         assert h.value is None
+    assert lib.mrs_render_batch(None, None, 0, None) == -1                    # no context
+    assert lib.mrs_render_window(None, None, 8, 8, 0, 0, 4, 4, 1, 1, -1, 0, 1, None, None) == -1
     assert lib.mrs_net_save(None, b"/nonexistent/x.ckpt", 0) == -1
     assert lib.mrs_net_load(None, b"x.ckpt", None) == -1
     assert lib.mrs_net_create_seeded(13, 0, ctypes.c_float(0.1), ctypes.byref(h)) == -1
