@@ -334,6 +334,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                         a.mode == TC_RESRELU_BF16;
     const bool loads_res = a.mode == TC_RESID_BF16 || a.mode == TC_MASK_BF16 ||
                            a.mode == TC_RESRELU_BF16;
+    // a bf16 result that nobody reads (fp8 operands: only the fp8 copy) is
+    // neither staged nor stored
+    const bool stores_bf = bf_out && !(a.fp8_only && a.out_fp8);
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < stages; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
@@ -470,7 +473,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int y = y0; y < y1; ++y, ++j) {
                     uint32_t slot = j % kSlots, use = j / kSlots;
                     if (!mbar_wait(&edone[slot], use & 1, a.err)) { ok = false; break; }
-                    if (bf_out) {
+                    if (stores_bf) {
                         tma_store_4d(&tmap_out, sS + slot * SBYTES, 0, xb * kFoldTile, y, n);
                         bulk_commit();
                         bulk_wait_read0();
@@ -632,14 +635,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                             }
                         }
                     }
+                    if (stores_bf) {
 #pragma unroll
-                    for (int jj = 0; jj < 2; ++jj) {
-                        uint4 u;
-                        __nv_bfloat162* h2 = (__nv_bfloat162*)&u;
+                        for (int jj = 0; jj < 2; ++jj) {
+                            uint4 u;
+                            __nv_bfloat162* h2 = (__nv_bfloat162*)&u;
 #pragma unroll
-                        for (int e = 0; e < 4; ++e)
-                            h2[e] = __floats2bfloat162_rn(o[8 * jj + 2 * e], o[8 * jj + 2 * e + 1]);
-                        *(uint4*)(srow + sw128(j, c0 / 8 + jj)) = u;
+                            for (int e = 0; e < 4; ++e)
+                                h2[e] = __floats2bfloat162_rn(o[8 * jj + 2 * e], o[8 * jj + 2 * e + 1]);
+                            *(uint4*)(srow + sw128(j, c0 / 8 + jj)) = u;
+                        }
                     }
                     if (a.out_fp8 && valid) {
                         // the next layer's FP8 operand row
@@ -689,7 +694,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             // the slot is read and zeroed; the staging slot goes to the store warp
             tc_fence_before();
-            if (bf_out) fence_async_smem();
+            if (stores_bf) fence_async_smem();
             __syncwarp();
             if (lane == 0) {
                 mbar_arrive(&sfree[sl]);

@@ -44,6 +44,8 @@ struct TcConvArgs {
     // TC_RELU_BF16 / TC_RESID_BF16 with fp8 operands: also emit the fp8 copy
     void* out_fp8;
     float out_fp8_inv_scale;
+    // with out_fp8: write only the fp8 copy (the bf16 result has no reader)
+    int fp8_only;
     // A convolution over kc > 1 input tensors of 64 channels each (the
     // concatenation of their channels) in ONE launch: amaps = DEVICE array of
     // kc A-operand maps (64-byte aligned, alive until the kernel completes),

@@ -828,6 +828,7 @@ mrs_status fuse_tc(mrs_net_s* net, const float* lrhs, const float* hrls, const f
         a.xscale = f8 ? net->xscale[l] : 1.0f;
         a.nout = nout_of(l);
         a.out_fp8 = nullptr;
+        a.fp8_only = 0;
         a.tmap_res = nullptr;
         a.tmap_out = nullptr;
         if (l == 0) {
@@ -837,7 +838,10 @@ mrs_status fuse_tc(mrs_net_s* net, const float* lrhs, const float* hrls, const f
             a.tmap_x = &mh; a.mode = TC_FINAL_F32; a.out = out; a.lrhs = lrhs; a.cout = 3;
         } else if (l % 2 == 1) {
             a.tmap_x = &mh; a.mode = TC_RELU_BF16; a.out = r; a.res = nullptr; a.tmap_out = &orr;
-            if (f8) { a.out_fp8 = r8; a.out_fp8_inv_scale = 1.0f / net->xscale[l + 1]; }
+            // r is read only as the next conv's operand: with fp8 operands
+            // only its fp8 copy is written (not during calibration, which
+            // measures the bf16 r)
+            if (f8) { a.out_fp8 = r8; a.out_fp8_inv_scale = 1.0f / net->xscale[l + 1]; a.fp8_only = 1; }
         } else {
             a.tmap_x = &mr; a.mode = TC_RESID_BF16; a.out = h; a.res = h;
             a.tmap_res = &oh; a.tmap_out = &oh;
