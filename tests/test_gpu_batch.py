@@ -61,7 +61,7 @@ def test_batch_without_aux_and_tail_settings(mrs, pool):
     # same images
     jobs = [dict(j, aux=False) for j in _jobs(pool)[:5]]
     outs = []
-    for tail in (-1, 0, 99):
+    for tail in (-1, 0, 64):
         ctx = mrs.RenderContext()
         ctx.set_tail(tail)
         ctx.set_wave(20000)
