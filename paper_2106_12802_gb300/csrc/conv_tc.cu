@@ -966,13 +966,14 @@ __global__ void __launch_bounds__(kWgThreads, 1)
     const uint32_t tmem = *(volatile uint32_t*)tslot;
 
     if (warp == 0 && lane == 0) {
-        uint32_t it = 0;
-        for (long long j = j0; j < j1; ++j, ++it) {
+        uint32_t it = 0, ph = 0;
+        int s = 0;
+        for (long long j = j0; j < j1; ++j, ++it, s = (s + 1 == stages ? 0 : s + 1),
+                       ph ^= (s == 0 ? 1u : 0u)) {
             int xs = (int)(j % XS);
             long long rest = j / XS;
             int y = (int)(rest % a.H), n = (int)(rest / a.H);
-            int s = it % stages;
-            if (!mbar_wait(&empty[s], ((it / stages) & 1) ^ 1, a.err)) break;
+            if (!mbar_wait(&empty[s], ph ^ 1, a.err)) break;
             mbar_expect_tx(&full[s], kWgTx);
             uint8_t* sb = smem + (size_t)s * kWgStage;
             for (int r = 0; r < 3; ++r)
@@ -983,27 +984,37 @@ __global__ void __launch_bounds__(kWgThreads, 1)
         for (uint32_t i = it > (uint32_t)stages ? it - stages : 0; i < it; ++i)
             mbar_drain(&full[i % stages], (i / stages) & 1, kTimeoutCycles);
     } else if (warp == 1 && lane == 0) {
+        // MMA issuer.  A job's 24 MMAs use 6 A descriptors (tap pairs q) and
+        // one B descriptor, all built once per job; each K step of 16 pixels
+        // (2048 bytes further into every operand) only adds 2048 / 16 = 128
+        // to their start-address field (bits 0-13; shared-memory addresses
+        // stay far below the field's 256 KB).  The ring slot and its phase
+        // advance incrementally (no division per job).
         const uint32_t ones = smem_u32(sOnes);
-        uint32_t it = 0;
+        const uint32_t sbase = smem_u32(smem);
+        uint32_t it = 0, ph = 0;
+        int s = 0;
         for (long long j = j0; j < j1; ++j, ++it) {
-            int s = it % stages;
-            if (!mbar_wait(&full[s], (it / stages) & 1, a.err)) break;
+            if (!mbar_wait(&full[s], ph, a.err)) break;
             tc_fence_after();
-            const uint32_t base = smem_u32(smem + (size_t)s * kWgStage);
-            const uint32_t bB = base + 3 * kWgRB;
+            const uint32_t base = sbase + (uint32_t)s * kWgStage;
+            const uint32_t top2 = base + 2 * kWgRB;
+            uint64_t ad[6];
+#pragma unroll
+            for (int q = 0; q < 6; ++q)
+                ad[q] = sdesc_mn((q < 3 ? base : top2) + (q % 3) * 128,
+                                 q < 3 ? (uint32_t)kWgRB : ones - top2);
+            const uint64_t bd0 = sdesc_mn(base + 3 * kWgRB, kWgBB);
 #pragma unroll
             for (int kk = 0; kk < kWgKB / 16; ++kk) {
-                const uint64_t bd = sdesc_mn(bB + kk * 2048, kWgBB);
+                const uint64_t step = (uint64_t)(kk * 128);
 #pragma unroll
-                for (int q = 0; q < 6; ++q) {
-                    const int kx = q % 3;
-                    const uint32_t top = base + (q < 3 ? 0 : 2 * kWgRB);
-                    const uint32_t lbo = q < 3 ? (uint32_t)kWgRB : ones - top;
-                    mma_f16(tmem + q * 64, sdesc_mn(top + kx * 128 + kk * 2048, lbo), bd, IDESC,
+                for (int q = 0; q < 6; ++q)
+                    mma_f16(tmem + q * 64, ad[q] + step, bd0 + step, IDESC,
                             (it > 0 || kk > 0) ? 1u : 0u);
-                }
             }
             mma_commit(&empty[s]);
+            if (++s == stages) { s = 0; ph ^= 1u; }
         }
         mma_commit(done);   // arrives once every MMA issued above has completed
     }
