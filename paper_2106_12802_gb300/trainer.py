@@ -263,12 +263,39 @@ def train_recipe(n_scenes=2000, steps=20000, frame=1024, window=256, spp_tgt=102
     return net, report
 
 
+def loss_study(n_scenes=160, steps=6000, betas=(0.01, 0.1, 1.0, 100.0), window=256, spp_tgt=1024,
+               lr=1e-4, eval_scenes=4, eval_size=512, eval_tgt=4096, seed=0):
+    """The method's loss ablation (Sec. 5, Fig. comp_loss): nets trained on the
+    same data (n_scenes seeded scenes, one window each, as train_recipe), the
+    same batch draws and the same initialisation with the robust loss l_r at
+    each beta of `betas` and with L1 on log(1 + x), scored on the same
+    held-out windows.  l_r with a large beta (|e| / (beta + |e|) ~ |e| / beta)
+    is L1 on radiance up to scale, which Adam does not see.  Returns
+    {loss name: {"psnr", "relmse", "gain_db_over_upsampled_lrhs"}}."""
+    data, _ = make_window_dataset(range(1, 1 + n_scenes), 1024, window, 4, spp_tgt=spp_tgt, seed=1)
+    ev, _ = make_window_dataset(range(100001, 100001 + eval_scenes), 1024, eval_size, 4,
+                                spp_tgt=eval_tgt, seed=2)
+    runs = [("l1log", "l1log", 0.1)] + [(f"robust_beta_{b:g}", "robust", b) for b in betas]
+    out = {}
+    for name, loss, beta in runs:
+        net = fusion.Net(seed=seed)
+        train(net, data, steps, batch=16, crop=128, s=4, lr=lr, seed=0, precision="bf16",
+              loss=loss, beta=beta)
+        r = evaluate(net, ev, s=4, precision="bf16")
+        out[name] = {"psnr": r["fused"]["psnr"], "relmse": r["fused"]["relmse"],
+                     "gain_db_over_upsampled_lrhs": r["fused"]["psnr"] - r["upsampled_lrhs"]["psnr"]}
+        net.close()
+    out["upsampled_lrhs"] = {"psnr": r["upsampled_lrhs"]["psnr"], "relmse": r["upsampled_lrhs"]["relmse"]}
+    return out
+
+
 def main(argv=None):
-    """python -m paper_2106_12802_gb300.trainer recipe --scenes 2000 --steps 20000 [--save f]"""
+    """python -m paper_2106_12802_gb300.trainer recipe --scenes 2000 --steps 20000 [--save f]
+    python -m paper_2106_12802_gb300.trainer loss-study --scenes 160 --steps 6000"""
     import argparse
     import json
     ap = argparse.ArgumentParser()
-    ap.add_argument("cmd", choices=["recipe"])
+    ap.add_argument("cmd", choices=["recipe", "loss-study"])
     ap.add_argument("--scenes", type=int, default=2000)
     ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--window", type=int, default=256)
@@ -278,6 +305,10 @@ def main(argv=None):
     ap.add_argument("--eval-scenes", type=int, default=4)
     ap.add_argument("--save", default=None, help="checkpoint file for the trained net")
     a = ap.parse_args(argv)
+    if a.cmd == "loss-study":
+        print(json.dumps(loss_study(a.scenes, a.steps, window=a.window, spp_tgt=a.spp_tgt,
+                                    lr=a.lr, eval_scenes=a.eval_scenes)), flush=True)
+        return 0
     net, rep = train_recipe(a.scenes, a.steps, window=a.window, spp_tgt=a.spp_tgt, lr=a.lr,
                             loss=a.loss, eval_scenes=a.eval_scenes)
     if a.save:
