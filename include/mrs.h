@@ -627,6 +627,45 @@ mrs_status mrs_rdn_fuse(mrs_rdn rdn, const float* lrhs, const float* hrls, const
  * earlier mrs_rdn_fuse gave up; synchronises the device. */
 mrs_status mrs_rdn_check(mrs_rdn rdn);
 
+/* One training step of the network (Sec. 4 "Implement details": trained
+ * with Adam; the loss l_r of Sec. 3 "Loss function", or the L1-log loss):
+ * the FP32 forward of mrs_rdn_fuse (the same arithmetic in the same order,
+ * so `out` equals mrs_rdn_fuse's FP32 result bit for bit) keeping every
+ * block's concatenation and every ReLU output, the loss of I_SR against
+ * min(target, 100) (firefly clipping of the training target, Sec. 3.2; the
+ * inputs are used as given) over N*H*W*3 values reduced in float64, the
+ * backward of every step in reverse (transposed convolutions with flipped
+ * taps, ReLU masks from the stored outputs, deshuffle / shuffle exchanged,
+ * the dense concatenations' gradients summed per part, the block, group and
+ * Eq. F_DF skips adding theirs; dW / db reduced in a fixed order), and one
+ * bias-corrected Adam update (beta1 0.9, beta2 0.999, eps 1e-8) of the FP32
+ * weights at learning rate lr (>= 0).
+ * Images as in mrs_rdn_fuse plus target device [N][H][W][3].  loss one of
+ * MRS_LOSS_L1LOG / MRS_LOSS_ROBUST (beta > 0 for the latter).  precision:
+ * MRS_PREC_FP32 (SIMT; the only one accepted).  out (device [N][H][W][3],
+ * may be NULL) receives I_SR of the forward; loss_out (HOST, may be NULL)
+ * the mean loss, which synchronises `stream`.  The first step allocates the
+ * gradient and Adam moments (3 x n_params floats, moments zero); the
+ * workspace (about 20 KB per LR pixel plus 1.3 KB per HR pixel) lives in the
+ * handle.  A later MRS_PREC_BF16 mrs_rdn_fuse repacks its BF16 weights from
+ * the updated FP32 ones.  Limit: N*H*W <= 2^24. */
+mrs_status mrs_rdn_train_step(mrs_rdn rdn, const float* lrhs, const float* hrls,
+                              const float* albedo, const float* normal, const float* extra,
+                              const float* target, int32_t N, int32_t H, int32_t W, int32_t loss,
+                              float beta, float lr, int32_t precision, float* out,
+                              double* loss_out, void* stream);
+/* The gradient of the last training step (HOST float [n_params], parameter
+ * layout).  MRS_ERR_ARG before the first step.  Synchronises the device. */
+mrs_status mrs_rdn_get_grads(mrs_rdn rdn, float* grads, int64_t n_params);
+/* Training state: FP32 weights, Adam moments (HOST float [n_params] each;
+ * adam_m / adam_v may be NULL, and read as zero before the first step) and
+ * the Adam step count (may be NULL).  set_state with NULL moments zeroes
+ * them.  Both synchronise the device. */
+mrs_status mrs_rdn_get_state(mrs_rdn rdn, float* params, float* adam_m, float* adam_v,
+                             int64_t n_params, int64_t* step);
+mrs_status mrs_rdn_set_state(mrs_rdn rdn, const float* params, const float* adam_m,
+                             const float* adam_v, int64_t n_params, int64_t step);
+
 #ifdef __cplusplus
 }
 #endif

@@ -242,25 +242,41 @@ def forward_tape(params, lrhs, hrls, albedo, normal, s, extra=None):
     return cnn.conv3x3(U, *L[i]), tape
 
 
-def backward(params, tape, dy):
+def _abs_terms_1x1(x, dz):
+    """Sums of |terms| of a 1x1 conv's weight and bias gradients."""
+    ax, ad = np.abs(np.asarray(x, np.float64)), np.abs(dz)
+    return np.einsum("nyxo,nyxc->oc", ad, ax)[:, None, None, :], ad.sum(axis=(0, 1, 2))
+
+
+def backward(params, tape, dy, abs_terms=False):
     """Gradient of a loss w.r.t. the flat params, given dL/dI_SR: the forward
     steps of Sec. 4 in reverse (each conv's input / weight / bias gradients,
     ReLU masks from the recorded pre-activations, deshuffle and shuffle
     exchanged, the dense concatenations split back into their parts, the
-    block, group and Eq. F_DF skips adding their gradients)."""
+    block, group and Eq. F_DF skips adding their gradients).  With abs_terms,
+    also the sum of |terms| of every gradient element in the same layout
+    (sum over pixels of |dz| |x| for a weight, |dz| for a bias: the scale of
+    their rounding error, for tolerances)."""
     s, c_hr = tape["s"], tape["c_hr"]
     L = unpack(params, s, c_hr)
     D = depth(s)
     grads = [None] * len(L)
+    terms = [None] * len(L)
+
+    def conv_grad(i, x, dz):
+        dx, dw, db = cnn.conv3x3_backward(x, L[i][0], dz)
+        grads[i] = (dw, db)
+        if abs_terms:
+            terms[i] = cnn._abs_terms(x, dz)
+        return dx
+
     i = len(L) - 1
-    dU, dw, db = cnn.conv3x3_backward(tape["rec_in"], L[i][0], dy)
-    grads[i] = (dw, db)
+    dU = conv_grad(i, tape["rec_in"], dy)
     for d in reversed(range(D)):
         i -= 1
         U_in, z = tape["ups"][d]
         dz = deshuffle(dU) * (z > 0.0)
-        dU, dw, db = cnn.conv3x3_backward(U_in, L[i][0], dz)
-        grads[i] = (dw, db)
+        dU = conv_grad(i, U_in, dz)
     # U = F_G + F_0
     dF = dU
     dF0 = dU.copy()
@@ -278,35 +294,37 @@ def backward(params, tape, dy):
                 x_c, z_c = convs[c]
                 if c < N_CONV - 1:
                     dz = d_parts[c + 1] * (z_c > 0.0)
-                dx, dw, db = cnn.conv3x3_backward(x_c, L[3 + bi * N_CONV + c][0], dz)
-                grads[3 + bi * N_CONV + c] = (dw, db)
+                dx = conv_grad(3 + bi * N_CONV + c, x_c, dz)
                 for k in range(c + 1):
                     d_parts[k] = d_parts[k] + dx[..., C_F * k:C_F * (k + 1)]
             dF = d_parts[0]
         dF = dF + d_skip
     dF0 = dF0 + dF
     x_f, z = tape["fuse"]
-    dx_f, dw, db = conv1x1_backward(x_f, L[2][0], dF0 * (z > 0.0))
+    dz = dF0 * (z > 0.0)
+    dx_f, dw, db = conv1x1_backward(x_f, L[2][0], dz)
     grads[2] = (dw, db)
+    if abs_terms:
+        terms[2] = _abs_terms_1x1(x_f, dz)
     dF_lr, dF_h = dx_f[..., :C_F], dx_f[..., C_F:]
     for _ in range(D):
         dF_h = shuffle(dF_h)
     x_hr, z = tape["hr"]
-    _, dw, db = cnn.conv3x3_backward(x_hr, L[1][0], dF_h * (z > 0.0))
-    grads[1] = (dw, db)
+    conv_grad(1, x_hr, dF_h * (z > 0.0))
     x_lr, z = tape["lr"]
-    _, dw, db = cnn.conv3x3_backward(x_lr, L[0][0], dF_lr * (z > 0.0))
-    grads[0] = (dw, db)
-    return pack(grads)
+    conv_grad(0, x_lr, dF_lr * (z > 0.0))
+    return (pack(grads), pack(terms)) if abs_terms else pack(grads)
 
 
 def loss_and_grad(params, lrhs, hrls, albedo, normal, target, s, loss="robust", beta=0.1,
-                  extra=None):
+                  extra=None, abs_terms=False):
     """The training loss of I_SR against `target` (cnn.loss_fn: "robust" = the
-    method's l_r, or "l1log") and its gradient w.r.t. the flat params."""
+    method's l_r, or "l1log") and its gradient w.r.t. the flat params (and,
+    with abs_terms, the gradient's sums of |terms|, see backward())."""
     y, tape = forward_tape(params, lrhs, hrls, albedo, normal, s, extra)
     value, dy = cnn.loss_fn(y, target, loss, beta)
-    return value, backward(params, tape, dy)
+    g = backward(params, tape, dy, abs_terms)
+    return (value,) + g if abs_terms else (value, g)
 
 
 def flops_per_lr_pixel(s, c_hr=C_HR):

@@ -75,6 +75,10 @@ SIGS = {
     "mrs_rdn_free": [P],
     "mrs_rdn_fuse": [P, P, P, P, P, P, I32, I32, I32, I32, P, P],
     "mrs_rdn_check": [P],
+    "mrs_rdn_train_step": [P, P, P, P, P, P, P, I32, I32, I32, I32, F32, F32, I32, P, P, P],
+    "mrs_rdn_get_grads": [P, P, I64],
+    "mrs_rdn_get_state": [P, P, P, P, I64, P],
+    "mrs_rdn_set_state": [P, P, P, P, I64, I64],
     "mrs_selftest_wait_timeout": [I32, P],
     "mrs_status_string": [I32],
     "mrs_last_error": [],

@@ -315,6 +315,7 @@ __device__ __forceinline__ double srgb(double l)
 }
 
 constexpr int kRedBlocks = 1024;
+static_assert(kRedBlocks == kLossParts, "loss partial sums");
 
 __global__ void k_metrics_partial(const float* __restrict__ x, const float* __restrict__ ref,
                                   int64_t n, double l1, double l2, double* part)
@@ -447,7 +448,11 @@ __global__ void k_wtrans(const float* __restrict__ w, int cin, int cout, float* 
 }
 
 // dW[o][t][c] = sum_p dy[p][o] * x[p shifted by tap t][c] (zero padded), db[o] = sum_p dy[p][o]
-// grid (G, 9): block (g, t) reduces pixel tiles g, g+G, ... for tap t into part[g][t][o][c]
+// grid (G, ntaps, otiles * ctiles): block (g, j, z) reduces pixel tiles g, g+G, ... for tap
+// t = t0 + j of the 64 x 64 channel tile z = (output tile ot, input tile ct) into
+// part[z][g][j][o][c] (each z a [G][ntaps][64 * 64] slab holding the tile's cout_t x cin_t
+// values packed) and, for ct = 0 and j = 0, db into dbpart[ot][g][o] (a [G * 64] slab per
+// ot, cout_t values per g packed)
 constexpr int kDwTile = 64;
 __device__ __forceinline__ float ldf(const float* p) { return *p; }
 __device__ __forceinline__ float ldf(const __nv_bfloat16* p) { return __bfloat162float(*p); }
@@ -456,11 +461,18 @@ __device__ __forceinline__ float ldf(const __nv_bfloat16* p) { return __bfloat16
 template <typename TX, typename TY>
 __global__ void __launch_bounds__(256)
     k_dw_partial(const TX* __restrict__ x, int cin, int xs, const TY* __restrict__ dy, int cout,
-                 int ys, int N, int H, int W, float* __restrict__ part, float* __restrict__ dbpart)
+                 int ys, int N, int H, int W, float* __restrict__ part, float* __restrict__ dbpart,
+                 int t0, int ctiles)
 {
     __shared__ __align__(16) float sdy[kDwTile][64];
     __shared__ __align__(16) float sx[kDwTile][64];
-    const int t = blockIdx.y, g = blockIdx.x, G = gridDim.x;
+    const int j = blockIdx.y, t = t0 + j, g = blockIdx.x, G = gridDim.x;
+    const int ot = blockIdx.z / ctiles, ct = blockIdx.z % ctiles;
+    x += 64 * ct;
+    dy += 64 * ot;
+    cin = min(64, cin - 64 * ct);
+    cout = min(64, cout - 64 * ot);
+    const bool do_db = j == 0 && ct == 0;
     const int dyo = t / 3 - 1, dxo = t % 3 - 1;
     const int og = threadIdx.x / 16, cg = threadIdx.x % 16;
     const size_t P = (size_t)N * H * W;
@@ -493,21 +505,21 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] += av[i] * bv[j];
-            if (t == 0 && cg == 0)
+                for (int k = 0; k < 4; ++k) acc[i][k] += av[i] * bv[k];
+            if (do_db && cg == 0)
                 for (int i = 0; i < 4; ++i) dbacc[i] += av[i];
         }
         __syncthreads();
     }
-    float* out = part + ((size_t)g * 9 + t) * cout * cin;
+    float* out = part + (size_t)blockIdx.z * G * gridDim.y * 4096 + ((size_t)g * gridDim.y + j) * cout * cin;
     for (int i = 0; i < 4; ++i) {
         int o = og * 4 + i;
         if (o >= cout) continue;
-        for (int j = 0; j < 4; ++j) {
-            int c = cg * 4 + j;
-            if (c < cin) out[(size_t)o * cin + c] = acc[i][j];
+        for (int k = 0; k < 4; ++k) {
+            int c = cg * 4 + k;
+            if (c < cin) out[(size_t)o * cin + c] = acc[i][k];
         }
-        if (t == 0 && cg == 0) dbpart[(size_t)g * cout + o] = dbacc[i];
+        if (do_db && cg == 0) dbpart[(size_t)ot * G * 64 + (size_t)g * cout + o] = dbacc[i];
     }
 }
 
@@ -593,6 +605,52 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float
         p[i] = p[i] - lr * mh / (sqrtf(vh) + eps);
     }
 }
+
+}  // namespace
+
+// ---- training launches shared with the method's own network (rdn.cu) -------
+mrs_status dw_tiles_f32(const float* x, int cin, int xs, const float* dy, int cout, int ys, int N,
+                        int H, int W, int centre_only, float* part, float* dbpart, cudaStream_t st)
+{
+    const int ctiles = (cin + 63) / 64, otiles = (cout + 63) / 64;
+    dim3 grid(kDwParts, centre_only ? 1 : 9, otiles * ctiles);
+    k_dw_partial<float, float><<<grid, 256, 0, st>>>(x, cin, xs, dy, cout, ys, N, H, W, part, dbpart,
+                                                     centre_only ? 4 : 0, ctiles);
+    MRS_LAUNCHED(1);
+    return cuda_status(cudaGetLastError(), "dw tiles");
+}
+
+void wtrans_f32(const float* w, int cin, int cout, float* wt, cudaStream_t st)
+{
+    int n = cin * 9 * cout;
+    k_wtrans<<<(n + 255) / 256, 256, 0, st>>>(w, cin, cout, wt);
+    MRS_LAUNCHED(1);
+}
+
+mrs_status loss_grad_f32(const float* y, const float* tgt, size_t n, float clip, int kind,
+                         float beta, float* dy, double* parts, double* sum, cudaStream_t st)
+{
+    k_loss<<<kRedBlocks, 256, 0, st>>>(y, tgt, n, clip, kind, beta, dy, parts);
+    MRS_LAUNCHED(1);
+    k_reduce_parts<<<1, 256, 0, st>>>(parts, kRedBlocks, 1, sum);
+    MRS_LAUNCHED(1);
+    return cuda_status(cudaGetLastError(), "loss");
+}
+
+mrs_status adam_f32(float* p, const float* g, float* m, float* v, size_t n, float lr, int64_t step,
+                    cudaStream_t st)
+{
+    const double b1 = 0.9, b2 = 0.999;
+    float bc1 = (float)(1.0 - pow(b1, (double)step));
+    float bc2 = (float)(1.0 - pow(b2, (double)step));
+    size_t gsz = (n + 255) / 256;
+    k_adam<<<(int)(gsz < 4096 ? (gsz ? gsz : 1) : 4096), 256, 0, st>>>(p, g, m, v, n, lr, (float)b1,
+                                                                     (float)b2, 1e-8f, bc1, bc2);
+    MRS_LAUNCHED(1);
+    return cuda_status(cudaGetLastError(), "adam");
+}
+
+namespace {
 
 // gate decision on the device: D = sum / count; use_plain = D > tau
 __global__ void k_gate_decide(const double* part, int nparts, double count, double tau,
@@ -1212,7 +1270,7 @@ mrs_status layer_dw(mrs_net_s* net, int l, const float* x, const float* dy, int 
 {
     const LayerShape& L = shapes(net->cin0)[l];
     dim3 grid(kDwSplits, 9);
-    MRS_TIMED(PK_TRAIN, st, (k_dw_partial<float, float><<<grid, 256, 0, st>>>(x, L.cin, L.cin, dy, L.cout, L.cout, N, H, W, part, dbpart)));
+    MRS_TIMED(PK_TRAIN, st, (k_dw_partial<float, float><<<grid, 256, 0, st>>>(x, L.cin, L.cin, dy, L.cout, L.cout, N, H, W, part, dbpart, 0, 1)));
     MRS_LAUNCHED(1);
     int nw = L.cout * 9 * L.cin + L.cout;
     MRS_TIMED(PK_TRAIN, st, k_dw_reduce<<<(nw + 255) / 256, 256, 0, st>>>(part, dbpart, kDwSplits, L.cin, L.cout,
@@ -1780,7 +1838,7 @@ extern "C" mrs_status mrs_conv3x3_wgrad(const float* x, const float* dy, int32_t
     int np = 0;
     if (precision == MRS_PREC_FP32) {
         k_dw_partial<float, float><<<dim3(kDwSplits, 9), 256, 0, st>>>(x, cin, cin, dy, cout, cout, N, H, W,
-                                                                      part, dbpart);
+                                                                      part, dbpart, 0, 1);
         MRS_LAUNCHED(1);
         np = kDwSplits;
     } else {

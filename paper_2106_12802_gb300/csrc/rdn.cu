@@ -231,6 +231,120 @@ __global__ void k_centre_tap(const float* __restrict__ w1, int cin, float* __res
     }
 }
 
+// ---- training (FP32): elementwise steps of the backward pass --------------
+// dst[p][c] = ((a + b) + c2) + d2 for c < 64, the sources added in that order
+// (c2 / d2 may be NULL); pixel strides ds, as, bs, cs, es
+__global__ void k_sum64(float* __restrict__ dst, int ds, const float* a, int as, const float* b,
+                        int bs, const float* c2, int cs, const float* d2, int es, size_t P)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < P * 64;
+         i += (size_t)gridDim.x * blockDim.x) {
+        size_t p = i / 64;
+        int c = (int)(i % 64);
+        float v = a[p * as + c] + b[p * bs + c];
+        if (c2) v = v + c2[p * cs + c];
+        if (d2) v = v + d2[p * es + c];
+        dst[p * ds + c] = v;
+    }
+}
+
+// out[p][c] = act[p][c] > 0 ? d[p][c] : 0 for c < 64 (a ReLU's gradient mask
+// from its output; out may be d)
+__global__ void k_mask64(const float* d, int dstr, const float* __restrict__ act, int astr,
+                         float* out, int ostr, size_t P)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < P * 64;
+         i += (size_t)gridDim.x * blockDim.x) {
+        size_t p = i / 64;
+        int c = (int)(i % 64);
+        out[p * ostr + c] = act[p * astr + c] > 0.0f ? d[p * dstr + c] : 0.0f;
+    }
+}
+
+// start of a dense block's backward: dCat [P][256] holds dF_out in channels
+// 0..63 (the block's residual skip passes it to F_in unchanged); dz4 = dF_out
+// masked by the local-fusion ReLU (R = its output), channels 64..255 cleared
+__global__ void k_block_bwd_init(float* __restrict__ dcat, const float* __restrict__ R,
+                                 float* __restrict__ dz4, size_t P)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < P * 256;
+         i += (size_t)gridDim.x * blockDim.x) {
+        size_t p = i / 256;
+        int c = (int)(i % 256);
+        if (c < 64) dz4[p * 64 + c] = R[p * 64 + c] > 0.0f ? dcat[i] : 0.0f;
+        else dcat[i] = 0.0f;
+    }
+}
+
+// gradient of the x2 shuffle, masked by the upsampling conv's ReLU:
+// dz[y][x][4c + 2dy + dx] = dU[2y + dy][2x + dx][c] if T[y][x][4c + 2dy + dx] > 0
+// (T = that conv's ReLU output [N][h][w][256], dU [N][2h][2w][64])
+__global__ void k_unshuffle_mask(const float* __restrict__ dU, const float* __restrict__ T, int N,
+                                 int h, int w, float* __restrict__ dz)
+{
+    const size_t total = (size_t)N * h * w * 256;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        int k = (int)(i % 256);
+        size_t px = i / 256;
+        int x = (int)(px % w);
+        size_t r = px / w;
+        int y = (int)(r % h), n = (int)(r / h);
+        int c = k >> 2, dy = (k >> 1) & 1, dx = k & 1;
+        float g = dU[(((size_t)n * 2 * h + 2 * y + dy) * 2 * w + 2 * x + dx) * 64 + c];
+        dz[i] = T[i] > 0.0f ? g : 0.0f;
+    }
+}
+
+// gradient of the D deshuffles, masked by H_hrls's ReLU: dz [N][H][W][64] from
+// channels [64, 64 + 64 s^2) of dcat [N][H/s][W/s][cs] (the inverse of
+// k_deshuffle_f32's permutation); F = H_hrls's ReLU output
+__global__ void k_dsf_grad_mask(const float* __restrict__ dcat, int cs, const float* __restrict__ F,
+                                int N, int H, int W, int s, int D, float* __restrict__ dz)
+{
+    const size_t total = (size_t)N * H * W * 64;
+    const int h = H / s, w = W / s;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        int c = (int)(i % 64);
+        size_t px = i / 64;
+        int X = (int)(px % W);
+        size_t r = px / W;
+        int Y = (int)(r % H), n = (int)(r / H);
+        int k = dsf_channel(c, Y % s, X % s, D);
+        float g = dcat[(((size_t)n * h + Y / s) * w + X / s) * cs + 64 + k];
+        dz[i] = F[i] > 0.0f ? g : 0.0f;
+    }
+}
+
+// gw[o][t][c] (a layer's [cout][ntaps][cin] gradient) and gb[o] = sums over
+// the kDwParts pixel splits of dw_tiles_f32's 64 x 64 tiles, in split order
+__global__ void k_dw_reduce_tiles(const float* __restrict__ part, const float* __restrict__ dbpart,
+                                  int ntaps, int cin, int cout, float* __restrict__ gw,
+                                  float* __restrict__ gb)
+{
+    const size_t nw = (size_t)cout * ntaps * cin;
+    const int ctiles = (cin + 63) / 64;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nw + cout;
+         i += (size_t)gridDim.x * blockDim.x) {
+        float acc = 0.0f;
+        if (i < nw) {
+            int c = (int)(i % cin), t = (int)((i / cin) % ntaps), o = (int)(i / ((size_t)cin * ntaps));
+            int ct = c / 64, ot = o / 64;
+            int cin_t = min(64, cin - 64 * ct), cout_t = min(64, cout - 64 * ot);
+            const float* q = part + (size_t)(ot * ctiles + ct) * kDwParts * ntaps * 4096 +
+                             (size_t)t * cout_t * cin_t + (size_t)(o % 64) * cin_t + c % 64;
+            for (int g = 0; g < kDwParts; ++g) acc += q[(size_t)g * ntaps * cout_t * cin_t];
+            gw[i] = acc;
+        } else {
+            int o = (int)(i - nw), ot = o / 64, cout_t = min(64, cout - 64 * ot);
+            const float* q = dbpart + (size_t)ot * kDwParts * 64 + o % 64;
+            for (int g = 0; g < kDwParts; ++g) acc += q[(size_t)g * cout_t];
+            gb[o] = acc;
+        }
+    }
+}
+
 inline int grid_for(size_t n)
 {
     size_t g = (n + 255) / 256;
@@ -263,6 +377,13 @@ struct mrs_rdn_s {
     Buf dmaps;                     // their device copy
     Buf f32, bf;                   // activation workspaces
     int* err = nullptr;
+    // training state (allocated by the first training step)
+    float* grad = nullptr;         // gradient of the last step (parameter layout)
+    float* adam_m = nullptr;
+    float* adam_v = nullptr;
+    int64_t step = 0;              // Adam steps taken
+    bool bf_stale = false;         // BF16 chunks older than the FP32 weights
+    Buf tr;                        // training workspace (tape + backward)
 };
 
 namespace mrs {
@@ -617,6 +738,265 @@ mrs_status rdn_bf16(mrs_rdn_s* r, const float* lrhs, const float* hrls, const fl
 }
 
 
+// ---- training step (FP32) ----------------------------------------------------
+constexpr float kTrainClip = 100.0f;   // firefly clipping of the training target (Sec. 3.2)
+
+// gradient of one layer: partial sums over 64 x 64 channel tiles, then the
+// fixed-order reduction into grad (parameter layout)
+mrs_status layer_grad(mrs_rdn_s* r, int li, const float* x, int xs, const float* dz, int zs, int N,
+                      int H, int W, float* part, float* dbpart, cudaStream_t st)
+{
+    const RLayer& l = r->L[li];
+    mrs_status rc = dw_tiles_f32(x, l.cin, xs, dz, l.cout, zs, N, H, W, l.k == 1, part, dbpart, st);
+    if (rc != MRS_OK) return rc;
+    const size_t n = (size_t)l.cout * l.k * l.k * l.cin + l.cout;
+    k_dw_reduce_tiles<<<grid_for(n), 256, 0, st>>>(part, dbpart, l.k * l.k, l.cin, l.cout,
+                                                   r->grad + l.woff, r->grad + l.boff);
+    MRS_LAUNCHED(1);
+    return cuda_status(cudaGetLastError(), "rdn layer grad");
+}
+
+// forward keeping the activations the backward reads (the same arithmetic, in
+// the same order, as rdn_f32), the loss, the backward of every step in
+// reverse, one Adam update
+mrs_status rdn_train_f32(mrs_rdn_s* r, const float* lrhs, const float* hrls, const float* alb,
+                         const float* nrm, const float* extra, const float* tgt, int N, int H, int W,
+                         int kind, float beta, float lr, float* yout, double* loss_out,
+                         cudaStream_t st)
+{
+    const int s = r->s, D = r->D, h = H / s, w = W / s, c_hr = r->c_hr;
+    const int Ccat = kF + kF * s * s, nblk = kRDG * kRDB;
+    const size_t Pl = (size_t)N * h * w, Ph = (size_t)N * H * W;
+    size_t Pd[4];
+    Pd[0] = Pl;
+    for (int d = 0; d < D; ++d) Pd[d + 1] = Pd[d] * 4;
+    size_t nT = 0, nU = 0;
+    for (int d = 0; d < D; ++d) nT += Pd[d] * 256;
+    for (int d = 0; d <= D; ++d) nU += Pd[d] * 64;
+    const size_t nwt = (size_t)(Ccat > 256 ? Ccat : 256) * 9 * 64;
+    const size_t npart = (size_t)kDwParts * 4096 * (Ccat / 64 > 36 ? Ccat / 64 : 36);
+    // floats: inH cat Fh0 F0 blk R T U y | dy dA dB dCat dz dSkip dxf wt zero part dbpart
+    const size_t nf = Ph * c_hr + Pl * Ccat + Ph * 64 + Pl * 64 + nblk * Pl * 256 + nblk * Pl * 64 +
+                      nT + nU + Ph * 3 + Ph * 3 + 2 * Ph * 64 + Pl * 256 + 2 * Pl * 64 + Pl * Ccat +
+                      nwt + Ccat + npart + 4 * kDwParts * 64;
+    mrs_status rc = r->tr.ensure(nf * 4 + (kLossParts + 2) * 8 + 256);
+    if (rc != MRS_OK) return rc;
+    double* lparts = r->tr.as<double>();
+    double* lsum = lparts + kLossParts;
+    float* inH = (float*)(lsum + 2);
+    float* cat = inH + Ph * c_hr;
+    float* Fh0 = cat + Pl * Ccat;
+    float* F0 = Fh0 + Ph * 64;
+    float* blk = F0 + Pl * 64;
+    float* R = blk + nblk * Pl * 256;
+    float* Tb = R + nblk * Pl * 64;
+    float* Ub = Tb + nT;
+    float* y = Ub + nU;
+    float* dy = y + Ph * 3;
+    float* dA = dy + Ph * 3;
+    float* dB = dA + Ph * 64;
+    float* dCat = dB + Ph * 64;
+    float* dz = dCat + Pl * 256;
+    float* dSkip = dz + Pl * 64;
+    float* dxf = dSkip + Pl * 64;
+    float* wt = dxf + Pl * Ccat;
+    float* zero = wt + nwt;
+    float* part = zero + Ccat;
+    float* dbpart = part + npart;
+    float* T[3];
+    float* U[4];
+    {
+        float* t = Tb;
+        for (int d = 0; d < D; ++d) { T[d] = t; t += Pd[d] * 256; }
+        float* u = Ub;
+        for (int d = 0; d <= D; ++d) { U[d] = u; u += Pd[d] * 64; }
+    }
+    auto X = [&](int k) { return blk + (size_t)k * Pl * 256; };
+    auto Rk = [&](int k) { return R + (size_t)k * Pl * 64; };
+    const float* M = r->master;
+    const auto& L = r->L;
+    MRS_CHECK(cudaMemsetAsync(zero, 0, (size_t)Ccat * 4, st));
+
+    // ---- forward with the tape
+    k_hr_input_f32<<<grid_for(Ph), 256, 0, st>>>(hrls, alb, nrm, extra, Ph, inH);
+    MRS_LAUNCHED(1);
+    rc = simt_conv3x3(lrhs, 3, 3, M + L[0].woff, M + L[0].boff, kF, SIMT_PLAIN, 1, nullptr, 0, cat,
+                      Ccat, nullptr, N, h, w, 1, st);
+    if (rc == MRS_OK)
+        rc = simt_conv3x3(inH, c_hr, c_hr, M + L[1].woff, M + L[1].boff, kF, SIMT_PLAIN, 1, nullptr,
+                          0, Fh0, kF, nullptr, N, H, W, 1, st);
+    if (rc != MRS_OK) return rc;
+    k_deshuffle_f32<<<grid_for(Ph * 64), 256, 0, st>>>(Fh0, N, H, W, s, D, cat, Ccat);
+    MRS_LAUNCHED(1);
+    k_centre_tap<<<grid_for((size_t)64 * 9 * Ccat), 256, 0, st>>>(M + L[2].woff, Ccat, r->w_fuse3);
+    MRS_LAUNCHED(1);
+    rc = simt_conv3x3(cat, Ccat, Ccat, r->w_fuse3, M + L[2].boff, kF, SIMT_PLAIN, 1, nullptr, 0, F0,
+                      kF, nullptr, N, h, w, 1, st);
+    if (rc != MRS_OK) return rc;
+    k_ch64_f32<<<grid_for(Pl * 64), 256, 0, st>>>(X(0), 256, F0, 64, Pl, 0);
+    MRS_LAUNCHED(1);
+    int li = 3;
+    for (int g = 0; g < kRDG; ++g) {
+        const float* Fprev = X(kRDB * g);
+        for (int b = 0; b < kRDB; ++b) {
+            const int k = kRDB * g + b;
+            float* x = X(k);
+            for (int c = 1; c < kConv && rc == MRS_OK; ++c, ++li)
+                rc = simt_conv3x3(x, kF * c, 256, M + L[li].woff, M + L[li].boff, kF, SIMT_PLAIN, 1,
+                                  nullptr, 0, x + kF * c, 256, nullptr, N, h, w, 1, st);
+            if (rc == MRS_OK)
+                rc = simt_conv3x3(x, 256, 256, M + L[li].woff, M + L[li].boff, kF, SIMT_PLAIN, 1,
+                                  nullptr, 0, Rk(k), 64, nullptr, N, h, w, 1, st);
+            if (rc != MRS_OK) return rc;
+            ++li;
+            // block output F_in + relu(z4); after a group's last block + F_{g-1};
+            // after the last group + F_0 (Eq. F_DF)
+            const bool last = b == kRDB - 1;
+            float* dst = k + 1 < nblk ? X(k + 1) : U[0];
+            k_sum64<<<grid_for(Pl * 64), 256, 0, st>>>(dst, k + 1 < nblk ? 256 : 64, x, 256, Rk(k), 64,
+                                                      last ? Fprev : nullptr, 256,
+                                                      k + 1 == nblk ? F0 : nullptr, 64, Pl);
+            MRS_LAUNCHED(1);
+        }
+    }
+    int ch = h, cw = w;
+    for (int d = 0; d < D; ++d, ++li) {
+        rc = simt_conv3x3(U[d], kF, kF, M + L[li].woff, M + L[li].boff, 4 * kF, SIMT_PLAIN, 1, nullptr,
+                          0, T[d], 256, nullptr, N, ch, cw, 1, st);
+        if (rc != MRS_OK) return rc;
+        k_shuffle_f32<<<grid_for(Pd[d + 1] * 64), 256, 0, st>>>(T[d], 256, N, ch, cw, U[d + 1]);
+        MRS_LAUNCHED(1);
+        ch *= 2;
+        cw *= 2;
+    }
+    rc = simt_conv3x3(U[D], kF, kF, M + L[li].woff, M + L[li].boff, 3, SIMT_PLAIN, 0, nullptr, 0, y, 3,
+                      nullptr, N, H, W, 1, st);
+    if (rc != MRS_OK) return rc;
+    if (yout) MRS_CHECK(cudaMemcpyAsync(yout, y, Ph * 3 * 4, cudaMemcpyDeviceToDevice, st));
+
+    // ---- loss and dL/dI_SR
+    if ((rc = loss_grad_f32(y, tgt, Ph * 3, kTrainClip, kind, beta, dy, lparts, lsum, st)) != MRS_OK)
+        return rc;
+
+    // ---- backward: H_Rec, then the upsampling convs through the shuffles
+    if ((rc = layer_grad(r, li, U[D], kF, dy, 3, N, H, W, part, dbpart, st)) != MRS_OK) return rc;
+    wtrans_f32(M + L[li].woff, kF, 3, wt, st);
+    rc = simt_conv3x3(dy, 3, 3, wt, zero, kF, SIMT_PLAIN, 0, nullptr, 0, dA, kF, nullptr, N, H, W, 1, st);
+    if (rc != MRS_OK) return rc;
+    for (int d = D - 1; d >= 0; --d) {
+        --li;
+        ch /= 2;
+        cw /= 2;
+        k_unshuffle_mask<<<grid_for(Pd[d] * 256), 256, 0, st>>>(dA, T[d], N, ch, cw, dB);
+        MRS_LAUNCHED(1);
+        if ((rc = layer_grad(r, li, U[d], kF, dB, 256, N, ch, cw, part, dbpart, st)) != MRS_OK) return rc;
+        wtrans_f32(M + L[li].woff, kF, 4 * kF, wt, st);
+        rc = simt_conv3x3(dB, 4 * kF, 4 * kF, wt, zero, kF, SIMT_PLAIN, 0, nullptr, 0, dA, kF, nullptr,
+                          N, ch, cw, 1, st);
+        if (rc != MRS_OK) return rc;
+    }
+    // dA = dF_DF: to F_G (the chain) and to F_0 (kept in dA)
+    k_ch64_f32<<<grid_for(Pl * 64), 256, 0, st>>>(dCat, 256, dA, 64, Pl, 0);
+    MRS_LAUNCHED(1);
+    // ---- residual dense groups in reverse; dCat [Pl][256] holds the current
+    // block's concatenation gradient, channels 0..63 the gradient of its F_in
+    for (int g = kRDG - 1; g >= 0; --g) {
+        k_ch64_f32<<<grid_for(Pl * 64), 256, 0, st>>>(dSkip, 64, dCat, 256, Pl, 0);
+        MRS_LAUNCHED(1);
+        for (int b = kRDB - 1; b >= 0; --b) {
+            const int k = kRDB * g + b, lb = 3 + kConv * k;
+            const float* x = X(k);
+            k_block_bwd_init<<<grid_for(Pl * 256), 256, 0, st>>>(dCat, Rk(k), dz, Pl);
+            MRS_LAUNCHED(1);
+            // local fusion: dCat[:, 0:256] += conv^T(dz)
+            if ((rc = layer_grad(r, lb + 3, x, 256, dz, kF, N, h, w, part, dbpart, st)) != MRS_OK) return rc;
+            wtrans_f32(M + L[lb + 3].woff, 256, kF, wt, st);
+            rc = simt_conv3x3(dz, kF, kF, wt, zero, 256, SIMT_RESID, 0, dCat, 256, dCat, 256, nullptr, N,
+                              h, w, 1, st);
+            // dense conv c: its output's gradient (channels 64 (c + 1) ..) is
+            // complete once the later convs have added theirs
+            for (int c = kConv - 2; c >= 0 && rc == MRS_OK; --c) {
+                float* dzc = dCat + kF * (c + 1);
+                k_mask64<<<grid_for(Pl * 64), 256, 0, st>>>(dzc, 256, x + kF * (c + 1), 256, dzc, 256, Pl);
+                MRS_LAUNCHED(1);
+                const int ci = kF * (c + 1);
+                if ((rc = layer_grad(r, lb + c, x, 256, dzc, 256, N, h, w, part, dbpart, st)) != MRS_OK)
+                    return rc;
+                wtrans_f32(M + L[lb + c].woff, ci, kF, wt, st);
+                rc = simt_conv3x3(dzc, kF, 256, wt, zero, ci, SIMT_RESID, 0, dCat, 256, dCat, 256,
+                                  nullptr, N, h, w, 1, st);
+            }
+            if (rc != MRS_OK) return rc;
+        }
+        // F_g = chain(F_{g-1}) + F_{g-1}
+        k_sum64<<<grid_for(Pl * 64), 256, 0, st>>>(dCat, 256, dCat, 256, dSkip, 64, nullptr, 0, nullptr,
+                                                  0, Pl);
+        MRS_LAUNCHED(1);
+    }
+    // ---- fuse: dz = (dF_DF + chain gradient) masked by relu(F_0)
+    k_sum64<<<grid_for(Pl * 64), 256, 0, st>>>(dz, 64, dA, 64, dCat, 256, nullptr, 0, nullptr, 0, Pl);
+    MRS_LAUNCHED(1);
+    k_mask64<<<grid_for(Pl * 64), 256, 0, st>>>(dz, 64, F0, 64, dz, 64, Pl);
+    MRS_LAUNCHED(1);
+    if ((rc = layer_grad(r, 2, cat, Ccat, dz, kF, N, h, w, part, dbpart, st)) != MRS_OK) return rc;
+    wtrans_f32(r->w_fuse3, Ccat, kF, wt, st);
+    rc = simt_conv3x3(dz, kF, kF, wt, zero, Ccat, SIMT_PLAIN, 0, nullptr, 0, dxf, Ccat, nullptr, N, h, w,
+                      1, st);
+    if (rc != MRS_OK) return rc;
+    // ---- encoders: H_lrhs from channels 0..63, H_hrls through the deshuffles
+    k_mask64<<<grid_for(Pl * 64), 256, 0, st>>>(dxf, Ccat, cat, Ccat, dz, 64, Pl);
+    MRS_LAUNCHED(1);
+    if ((rc = layer_grad(r, 0, lrhs, 3, dz, kF, N, h, w, part, dbpart, st)) != MRS_OK) return rc;
+    k_dsf_grad_mask<<<grid_for(Ph * 64), 256, 0, st>>>(dxf, Ccat, Fh0, N, H, W, s, D, dB);
+    MRS_LAUNCHED(1);
+    if ((rc = layer_grad(r, 1, inH, c_hr, dB, kF, N, H, W, part, dbpart, st)) != MRS_OK) return rc;
+
+    // ---- Adam on the FP32 weights
+    r->step += 1;
+    if ((rc = adam_f32(r->master, r->grad, r->adam_m, r->adam_v, r->np, lr, r->step, st)) != MRS_OK)
+        return rc;
+    r->bf_stale = true;
+    if (loss_out) {
+        double hsum = 0;
+        MRS_CHECK(cudaMemcpyAsync(&hsum, lsum, sizeof(double), cudaMemcpyDeviceToHost, st));
+        MRS_CHECK(cudaStreamSynchronize(st));
+        *loss_out = hsum / (double)(Ph * 3);
+    }
+    return cuda_status(cudaGetLastError(), "rdn train step");
+}
+
+mrs_status ensure_train_state(mrs_rdn_s* r)
+{
+    if (r->grad) return MRS_OK;
+    float* p[3] = {nullptr, nullptr, nullptr};
+    for (int i = 0; i < 3; ++i) {
+        if (cudaMalloc(&p[i], r->np * 4) != cudaSuccess || cudaMemset(p[i], 0, r->np * 4) != cudaSuccess) {
+            for (int j = 0; j <= i; ++j)
+                if (p[j]) cudaFree(p[j]);
+            cudaGetLastError();
+            set_error("cudaMalloc(rdn training state) failed");
+            return MRS_ERR_OOM;
+        }
+    }
+    r->grad = p[0];
+    r->adam_m = p[1];
+    r->adam_v = p[2];
+    r->step = 0;
+    return MRS_OK;
+}
+
+// the BF16 chunks from the current FP32 weights (after training steps)
+mrs_status repack_if_stale(mrs_rdn_s* r, cudaStream_t st)
+{
+    if (!r->bf_stale) return MRS_OK;
+    std::vector<float> host(r->np);
+    MRS_CHECK(cudaStreamSynchronize(st));
+    MRS_CHECK(cudaMemcpy(host.data(), r->master, r->np * 4, cudaMemcpyDeviceToHost));
+    mrs_status rc = pack_chunks(r, host.data());
+    if (rc == MRS_OK) r->bf_stale = false;
+    return rc;
+}
+
 }  // namespace
 }  // namespace mrs
 
@@ -633,11 +1013,12 @@ extern "C" mrs_status mrs_rdn_free(mrs_rdn r)
 {
     if (!r) return MRS_OK;
     cudaDeviceSynchronize();
-    void* ptrs[] = {r->master, r->w_fuse3, r->wbf, r->bch, r->err};
+    void* ptrs[] = {r->master, r->w_fuse3, r->wbf, r->bch, r->err, r->grad, r->adam_m, r->adam_v};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     r->f32.release();
     r->bf.release();
+    r->tr.release();
     r->dmaps.release();
     delete r;
     return MRS_OK;
@@ -685,10 +1066,85 @@ extern "C" mrs_status mrs_rdn_fuse(mrs_rdn r, const float* lrhs, const float* hr
     MRS_ARG(precision == MRS_PREC_FP32 || precision == MRS_PREC_BF16,
             "precision must be MRS_PREC_FP32 or MRS_PREC_BF16");
     cudaStream_t st = (cudaStream_t)stream;
+    if (precision == MRS_PREC_BF16) {
+        mrs_status rc = repack_if_stale(r, st);
+        if (rc != MRS_OK) return rc;
+    }
     mrs_status rc = precision == MRS_PREC_FP32
                         ? rdn_f32(r, lrhs, hrls, albedo, normal, extra, N, H, W, out, st)
                         : rdn_bf16(r, lrhs, hrls, albedo, normal, extra, N, H, W, out, st);
     return rc;
+}
+
+extern "C" mrs_status mrs_rdn_train_step(mrs_rdn r, const float* lrhs, const float* hrls,
+                                         const float* albedo, const float* normal, const float* extra,
+                                         const float* target, int32_t N, int32_t H, int32_t W,
+                                         int32_t loss, float beta, float lr, int32_t precision,
+                                         float* out, double* loss_out, void* stream)
+{
+    MRS_ARG(r != nullptr, "rdn is NULL");
+    MRS_ARG(lrhs && hrls && albedo && normal && target, "NULL image pointer");
+    MRS_ARG((extra != nullptr) == (r->c_hr == 18), "extra must be given exactly for hr_channels 18");
+    MRS_ARG(N >= 1 && H >= 1 && W >= 1, "N, H, W must be >= 1");
+    MRS_ARG(H % r->s == 0 && W % r->s == 0, "H and W must be multiples of the scale");
+    MRS_ARG((int64_t)N * H * W <= (int64_t(1) << 24), "N*H*W exceeds 2^24 pixels");
+    MRS_ARG(loss == MRS_LOSS_L1LOG || loss == MRS_LOSS_ROBUST, "loss must be MRS_LOSS_L1LOG or MRS_LOSS_ROBUST");
+    MRS_ARG(loss != MRS_LOSS_ROBUST || beta > 0.0f, "beta must be > 0");
+    MRS_ARG(lr >= 0.0f, "lr must be >= 0");
+    MRS_ARG(precision == MRS_PREC_FP32, "precision must be MRS_PREC_FP32");
+    mrs_status rc = ensure_train_state(r);
+    if (rc != MRS_OK) return rc;
+    return rdn_train_f32(r, lrhs, hrls, albedo, normal, extra, target, N, H, W, loss, beta, lr, out,
+                         loss_out, (cudaStream_t)stream);
+}
+
+extern "C" mrs_status mrs_rdn_get_grads(mrs_rdn r, float* grads, int64_t n_params)
+{
+    MRS_ARG(r != nullptr && grads != nullptr, "NULL argument");
+    MRS_ARG(n_params == (int64_t)r->np, "n_params must equal mrs_rdn_nparams");
+    MRS_ARG(r->grad != nullptr, "no training step taken");
+    MRS_CHECK(cudaDeviceSynchronize());
+    MRS_CHECK(cudaMemcpy(grads, r->grad, r->np * 4, cudaMemcpyDeviceToHost));
+    return MRS_OK;
+}
+
+extern "C" mrs_status mrs_rdn_get_state(mrs_rdn r, float* params, float* adam_m, float* adam_v,
+                                        int64_t n_params, int64_t* step)
+{
+    MRS_ARG(r != nullptr && params != nullptr, "NULL argument");
+    MRS_ARG(n_params == (int64_t)r->np, "n_params must equal mrs_rdn_nparams");
+    MRS_CHECK(cudaDeviceSynchronize());
+    MRS_CHECK(cudaMemcpy(params, r->master, r->np * 4, cudaMemcpyDeviceToHost));
+    float* mv[2] = {adam_m, adam_v};
+    float* dv[2] = {r->adam_m, r->adam_v};
+    for (int i = 0; i < 2; ++i) {
+        if (!mv[i]) continue;
+        if (dv[i]) MRS_CHECK(cudaMemcpy(mv[i], dv[i], r->np * 4, cudaMemcpyDeviceToHost));
+        else memset(mv[i], 0, r->np * 4);
+    }
+    if (step) *step = r->step;
+    return MRS_OK;
+}
+
+extern "C" mrs_status mrs_rdn_set_state(mrs_rdn r, const float* params, const float* adam_m,
+                                        const float* adam_v, int64_t n_params, int64_t step)
+{
+    MRS_ARG(r != nullptr && params != nullptr, "NULL argument");
+    MRS_ARG(n_params == (int64_t)r->np, "n_params must equal mrs_rdn_nparams");
+    MRS_ARG(step >= 0, "step must be >= 0");
+    mrs_status rc = ensure_train_state(r);
+    if (rc != MRS_OK) return rc;
+    MRS_CHECK(cudaDeviceSynchronize());
+    MRS_CHECK(cudaMemcpy(r->master, params, r->np * 4, cudaMemcpyHostToDevice));
+    const float* mv[2] = {adam_m, adam_v};
+    float* dv[2] = {r->adam_m, r->adam_v};
+    for (int i = 0; i < 2; ++i) {
+        if (mv[i]) MRS_CHECK(cudaMemcpy(dv[i], mv[i], r->np * 4, cudaMemcpyHostToDevice));
+        else MRS_CHECK(cudaMemset(dv[i], 0, r->np * 4));
+    }
+    r->step = step;
+    r->bf_stale = true;
+    return MRS_OK;
 }
 
 extern "C" mrs_status mrs_rdn_check(mrs_rdn r)

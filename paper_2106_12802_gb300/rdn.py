@@ -10,7 +10,7 @@ import numpy as np
 import torch
 
 from ._lib import call, load
-from .fusion import _prec
+from .fusion import LOSSES, _prec
 from .render import _dev, _ptr, _stream
 
 
@@ -104,3 +104,44 @@ class RDN:
     def check(self):
         """Raises if a tensor-core wait of an earlier fuse gave up."""
         call("mrs_rdn_check", self.handle)
+
+    @property
+    def nparams(self):
+        return nparams(self.scale, self.hr_channels)
+
+    def train_step(self, lrhs, hrls, albedo, normal, target, lr=1e-4, loss="robust", beta=0.1,
+                   extra=None, out=None, sync_loss=True, precision="fp32", stream=None):
+        """One Adam step on a batch (CUDA float32 NHWC tensors as in fuse plus
+        target [N,H,W,3]); returns the mean loss, or None when sync_loss is
+        False (no host synchronisation).  out [N,H,W,3] receives I_SR."""
+        for t in (lrhs, hrls, albedo, normal, target) + ((extra,) if extra is not None else ()):
+            _dev(t, torch.float32)
+        if out is not None:
+            _dev(out, torch.float32)
+        N, H, W, _ = hrls.shape
+        v = ctypes.c_double()
+        call("mrs_rdn_train_step", self.handle, _ptr(lrhs), _ptr(hrls), _ptr(albedo), _ptr(normal),
+             _ptr(extra), _ptr(target), N, H, W, LOSSES[loss] if isinstance(loss, str) else int(loss),
+             float(beta), float(lr), _prec(precision), _ptr(out),
+             ctypes.byref(v) if sync_loss else None, _stream(stream))
+        return float(v.value) if sync_loss else None
+
+    def get_grads(self):
+        g = np.zeros(self.nparams, np.float32)
+        call("mrs_rdn_get_grads", self.handle, ctypes.c_void_p(g.ctypes.data), g.size)
+        return g
+
+    def get_state(self):
+        p, m, v = (np.zeros(self.nparams, np.float32) for _ in range(3))
+        step = ctypes.c_int64()
+        call("mrs_rdn_get_state", self.handle, *(ctypes.c_void_p(a.ctypes.data) for a in (p, m, v)),
+             p.size, ctypes.byref(step))
+        return {"params": p, "adam_m": m, "adam_v": v, "step": int(step.value)}
+
+    def get_params(self):
+        return self.get_state()["params"]
+
+    def set_state(self, st):
+        p, m, v = (np.ascontiguousarray(st[k], np.float32) for k in ("params", "adam_m", "adam_v"))
+        call("mrs_rdn_set_state", self.handle, *(ctypes.c_void_p(a.ctypes.data) for a in (p, m, v)),
+             p.size, int(st["step"]))

@@ -270,3 +270,27 @@ def test_loss_and_grad_robust_loss_by_finite_differences():
         vm, _ = rdn.loss_and_grad(p - e, lr, hr, alb, nrm, target, s, loss="robust", beta=0.1)
         fd = (vp - vm) / 2e-6
         assert abs(g[j] - fd) <= 1e-5 * max(1e-3, abs(fd)), (j, g[j], fd)
+
+
+@pytest.mark.parametrize("s", [2, 4])
+def test_backward_abs_terms(s):
+    # the |terms| sums that scale the training tolerances: the gradient is
+    # unchanged by asking for them; every element obeys |g| <= terms (the
+    # triangle inequality over its terms); where every term is non-negative
+    # they are the gradient itself: H_Rec's input is a shuffle of ReLU
+    # outputs (>= 0), so with dL/dI_SR = G >= 0 its weight and bias rows equal
+    # the gradient
+    p, lr, hr, alb, nrm, ex, rng = _small_case(s, 11)
+    y, tape = rdn.forward_tape(p, lr, hr, alb, nrm, s, ex)
+    G = rng.normal(size=y.shape)
+    g0 = rdn.backward(p, tape, G)
+    g, t = rdn.backward(p, tape, G, abs_terms=True)
+    assert np.array_equal(g, g0) and t.shape == g.shape
+    assert (np.abs(g) <= t * (1 + 1e-12) + 1e-300).all()
+    nz = t > 0
+    assert nz.mean() > 0.3
+    assert (np.abs(g[nz]) < t[nz] * (1 - 1e-9)).mean() > 0.25    # mixed-sign terms
+    Gp = np.abs(G)
+    g, t = rdn.backward(p, tape, Gp, abs_terms=True)
+    _, wo, bo, k, ci, co = rdn.layer_offsets(s)[-1]
+    assert np.allclose(g[wo:bo + co], t[wo:bo + co], rtol=1e-12, atol=0)
