@@ -599,6 +599,7 @@ def paper_network(mrs, flush, s=S, reps=10):
         torch.cuda.synchronize()
         tb.append(e0.elapsed_time(e1) / nb)
     del lrb, hrb, outb
+    train = rdn_train_timing(mrs, flush, s)
     ms = float(np.median(ts))
     flop = rdn.flops_per_lr_pixel(s) * LR * LR
     peaks = _peaks()
@@ -612,9 +613,59 @@ def paper_network(mrs, flush, s=S, reps=10):
            "tensor_frac_of_measured_sustained": tf / peaks["bf16_tflops_sustained"],
            "conv_tc_ms_events": conv_ms, "conv_tc_launches": prof["conv_tc"][1] // reps_prof,
            "conv_tc_tflops": flop / (conv_ms * 1e-3) / 1e12 if conv_ms else None,
-           "l2": "flushed before every rep (512 MiB write)"}
+           "l2": "flushed before every rep (512 MiB write)", "train_step_fp32": train}
     net.close()
     return res
+
+
+def rdn_train_flop_per_lr_pixel(s):
+    """Multiply-adds x 2 of one training step per LR pixel: the forward, every
+    layer's weight gradient (as much again) and every layer's input gradient
+    except the two encoders' (their inputs are images)."""
+    from paper_2106_12802_gb300 import rdn
+    fwd = rdn.flops_per_lr_pixel(s)
+    enc = 2 * 9 * 3 * 64 + 2 * 9 * 9 * 64 * s * s
+    return 3 * fwd - enc
+
+
+def rdn_train_timing(mrs, flush, s=S, N=16, crop=192, reps=3, warmup=2):
+    """Device time of one FP32 training step of the method's own network at
+    the paper's training batch (Sec. 4 "Implement details": mini-batch 16,
+    192 x 192 HR patches at x4): forward with its activations kept, the
+    robust loss, the backward of every step, Adam.  Random radiance-like
+    inputs on the device, L2 flushed before every step."""
+    import torch
+
+    from paper_2106_12802_gb300 import rdn
+    net = mrs.RDN(rdn.kaiming_params(s), s)
+    g = torch.Generator(device="cuda").manual_seed(12)
+    h = crop // s
+    lr = torch.rand((N, h, h, 3), device="cuda", generator=g) * 2
+    hr = torch.rand((N, crop, crop, 3), device="cuda", generator=g) * 2
+    alb = torch.rand((N, crop, crop, 3), device="cuda", generator=g)
+    nrm = torch.rand((N, crop, crop, 3), device="cuda", generator=g) * 2 - 1
+    tgt = torch.rand((N, crop, crop, 3), device="cuda", generator=g) * 2
+    for _ in range(warmup):
+        net.train_step(lr, hr, alb, nrm, tgt, lr=1e-4, loss="robust", beta=0.1, sync_loss=False)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        net.train_step(lr, hr, alb, nrm, tgt, lr=1e-4, loss="robust", beta=0.1, sync_loss=False)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    net.close()
+    ms = float(np.median(ts))
+    flop = rdn_train_flop_per_lr_pixel(s) * N * h * h
+    tf = flop / (ms * 1e-3) / 1e12
+    sm = torch.cuda.get_device_properties(0).multi_processor_count
+    fp32_peak = sm * 128 * 2 * 2.07e9 / 1e12   # TFLOP/s: FP32 lanes x FMA x max SM clock
+    return {"batch": [N, crop, crop], "scale": s, "precision": "fp32 (SIMT)", "loss": "robust, beta 0.1",
+            "optimizer": "Adam, lr 1e-4", "ms": ms, "tflop_per_step": flop / 1e12, "tflops": tf,
+            "fp32_frac": tf / fp32_peak, "fp32_peak_tflops": fp32_peak}
 
 
 def fp8_gemm_tflops(n=8192, reps=10):
@@ -916,8 +967,20 @@ def run_gpu(args, rank, world):
         torch.cuda.synchronize()
         pms = e0.elapsed_time(e1)
         rays = int(plain["counts"].sum().item() + plain["shadow_counts"].sum().item())
+        # the same render over the clustering tree (a static scene built once;
+        # the frame above rebuilds its LBVH every step)
+        scene.set_tree("cluster")
+        plain = mrs.render(scene, HR, HR, 64, DEPTH, RR, 8, out=plain)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        plain = mrs.render(scene, HR, HR, 64, DEPTH, RR, 8, out=plain)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        cms = e0.elapsed_time(e1)
+        scene.set_tree("lbvh")
         extra["plain_path_trace_1024_64spp"] = {
-            "ms": pms, "msamples_per_s": HR * HR * 64 / pms / 1e3, "mrays_per_s": rays / pms / 1e3}
+            "ms": pms, "msamples_per_s": HR * HR * 64 / pms / 1e3, "mrays_per_s": rays / pms / 1e3,
+            "cluster_tree_ms": cms, "cluster_tree_msamples_per_s": HR * HR * 64 / cms / 1e3}
 
     peaks = _peaks()
     conv_ms = prof["conv_tc"][0] / prof_steps

@@ -26,6 +26,9 @@ SIGS = {
     "mrs_build_scene": [P, I32, P, P, P, I32, P, I32, P, P, P, P],
     "mrs_build_scene_seeded": [U64, I32, P, P, P],
     "mrs_scene_rebuild": [P, P],
+    "mrs_scene_set_tree": [P, I32, P],
+    "mrs_scene_get_tree": [P, P],
+    "mrs_scene_export_nodes": [P, P, I64, P, P],
     "mrs_scene_update_vertices": [P, P, I32, P],
     "mrs_free_scene": [P],
     "mrs_scene_export_bvh": [P, P, P, P, P, P, P],

@@ -127,6 +127,13 @@ struct mrs_scene_s {
     float4* tris = nullptr;      // [n][3]: (v0, prim bits), (e1, 0), (e2, 0) in sorted order
     int2* tri_ml = nullptr;      // [n]: material, light in sorted order
     mrs::Buf sort_tmp;           // radix-sort scratch
+    mrs::Buf ploc_tmp;           // clustering-build scratch
+    cudaGraphExec_t ploc_exec = nullptr;   // the clustering build as a graph (see build_ploc)
+    int ploc_ns = -1;                      // ... for this tree size
+    void* ploc_buf = nullptr;              // ... and this scratch buffer
+    cudaStream_t ploc_cap = nullptr;       // stream the graph is captured on
+    int32_t tree = MRS_TREE_LBVH;          // render tree to build (MRS_TREE_*)
+    int32_t tree_built = MRS_TREE_LBVH;    // the one built (the LBVH if clustering gave up)
     mrs::Buf class_tmp;          // large / small classification scratch
     int* class_host = nullptr;   // pinned [2]: small and large triangle counts
     mrs::Buf export_tmp;         // full-scene LBVH built on export

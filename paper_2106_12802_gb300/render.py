@@ -109,6 +109,34 @@ class Scene:
         """First bounce of the tail kernel (-1: automatic; > max_depth: none)."""
         call("mrs_scene_set_tail", self.handle, int(bounce))
 
+    TREES = {"lbvh": 0, "cluster": 1}
+
+    def set_tree(self, kind: str = "cluster", stream=None):
+        """Render tree: "lbvh" (the radix tree, the default: cheapest build) or
+        "cluster" (locally-ordered clustering: faster renders, slower build);
+        rebuilds it."""
+        call("mrs_scene_set_tree", self.handle, self.TREES[kind], _stream(stream))
+
+    def tree(self) -> str:
+        """The render tree in use ("lbvh" also when clustering gave up)."""
+        k = ctypes.c_int32()
+        call("mrs_scene_get_tree", self.handle, ctypes.byref(k))
+        return {v: n for n, v in self.TREES.items()}[k.value]
+
+    def export_nodes(self):
+        """The render tree: dict(ns, box [ns-1, 2, 6] child boxes, child
+        [ns-1, 2] ids (< ns - 1 internal, else leaf ns - 1 + k), order [ns])."""
+        ns = ctypes.c_int32()
+        call("mrs_scene_export_nodes", self.handle, None, 0, None, ctypes.byref(ns))
+        ns = int(ns.value)
+        raw = np.zeros((max(ns - 1, 1), 16), np.float32)
+        order = np.zeros(max(ns, 1), np.int32)
+        call("mrs_scene_export_nodes", self.handle, ctypes.c_void_p(raw.ctypes.data), raw.size,
+             ctypes.c_void_p(order.ctypes.data), ctypes.byref(ctypes.c_int32()))
+        raw = raw[: max(ns - 1, 0)]
+        return {"ns": ns, "box": raw[:, :12].reshape(-1, 2, 6).copy(),
+                "child": raw[:, 12:14].copy().view(np.int32), "order": order[:ns]}
+
     def export_bvh(self, stream=None):
         n = self.n
         dev = torch.device("cuda")

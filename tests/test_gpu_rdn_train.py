@@ -19,14 +19,16 @@ Tolerances (the GPU step runs in FP32, the oracle in float64):
   the two sides, moving single pixels' terms, and the change spreads
   through the transposed convolutions below it (the 64-element bias arrays
   show it first).  Bars: median 1e-5 and 99th percentile 1e-3 per weight /
-  bias array, r > 1e-3 for at most 0.1% of all elements.  (2) End to end, against the float64 step: the robust loss's
-  slope beta / (beta + |e|)^2 turns the forward's rounding (|dy| up to
+  bias array, r > 1e-3 for at most 0.1% of all elements.
+  (2) End to end, against the float64 step: the robust loss's slope
+  beta / (beta + |e|)^2 turns the forward's rounding (|dy| up to
   1e-5 max |y|) into a relative change of dL/dI_SR of up to
   2 |dy| / (beta + |e|): 1e-4 to 6e-3 at beta = 0.1 for outputs of 1 to 30.
   Bars: median 1e-4 per array; over all elements 99th percentile 2e-3 and
   r > 1e-2 for at most 0.1% (a 64-element bias array's 99th percentile is
-  its maximum, where a single ill-conditioned element decides).  A wrong tap, channel, part,
-  mask or skip gives r of order 1e-2 to 1 over whole arrays.
+  its maximum, where a single ill-conditioned element decides).
+  A wrong tap, channel, part, mask or skip gives r of order 1e-2 to 1 over
+  whole arrays.
 * Adam update: within 1% of lr plus the FP32 spacing of the stored weight
   wherever the oracle gradient is well conditioned (|g| > 1e-6 and
   |g| > 1e-3 sum |terms|: the first step is lr * g / (|g| + eps), whose sign

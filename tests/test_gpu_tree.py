@@ -1,0 +1,134 @@
+"""The render tree: the radix tree (the default) and locally-ordered
+clustering.  The exported clustering tree is checked on the host (every node but
+the root a child exactly once, leaf boxes the triangles' boxes, every
+internal box the exact union of its children's); closest hits and renders
+are the same with both trees, bit for bit, and equal the oracle's; the
+clustering tree's surface-area cost and traversal work are below the radix
+tree's on the procedural scene.  Sizes span the single-block finish (2048
+clusters), several grid-wide rounds, ties (identical triangles) and
+degenerate (zero-area) triangles."""
+import numpy as np
+import pytest
+
+from synth import scenes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mrs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2106_12802_gb300 as m
+    m.load()
+    return m
+
+
+def _half_area(lo, hi):
+    e = np.maximum(hi - lo, 0.0)
+    return e[..., 0] * e[..., 1] + e[..., 1] * e[..., 2] + e[..., 2] * e[..., 0]
+
+
+def check_tree(t, V):
+    """Validates the exported tree; returns its surface-area cost (internal
+    node areas + leaf areas, over the root's)."""
+    ns, child, box, order = t["ns"], t["child"], t["box"], t["order"]
+    assert len(np.unique(order)) == ns
+    if ns <= 1:
+        return 0.0
+    ids = child.ravel()
+    assert np.array_equal(np.sort(ids), np.arange(1, 2 * ns - 1))   # root 0 is nobody's child
+    bx = box.reshape(-1, 6)
+    tri = np.asarray(V, np.float32).reshape(-1, 3, 3)[order]
+    leaf = ids >= ns - 1
+    k = ids[leaf] - (ns - 1)
+    assert np.array_equal(bx[leaf, :3], tri[k].min(axis=1))
+    assert np.array_equal(bx[leaf, 3:], tri[k].max(axis=1))
+    c = ids[~leaf]
+    assert np.array_equal(bx[~leaf, :3], box[c, :, :3].min(axis=1))
+    assert np.array_equal(bx[~leaf, 3:], box[c, :, 3:].max(axis=1))
+    node_lo, node_hi = box[:, :, :3].min(axis=1), box[:, :, 3:].max(axis=1)
+    root = _half_area(node_lo[0], node_hi[0])
+    return float((_half_area(node_lo, node_hi).sum() + _half_area(bx[leaf, :3], bx[leaf, 3:]).sum())
+                 / root)
+
+
+def _soup(seed, n, identical=False, degenerate=False):
+    desc = scenes.random_triangles(seed, n)
+    V = desc["V"].reshape(n, 3, 3)
+    if identical:
+        V[:] = V[0]
+    if degenerate:
+        V[::3, 2] = V[::3, 0]                 # every third triangle has zero area
+        V[1::7, 1] = V[1::7, 0]
+        V[1::7, 2] = V[1::7, 0]               # and some are points
+    desc["V"] = V.reshape(desc["V"].shape)
+    return desc
+
+
+@pytest.mark.parametrize("n,kw", [(2, {}), (3, {}), (100, {}), (2047, {}), (2048, {}), (2049, {}),
+                                  (5000, {}), (70000, {}), (3000, {"identical": True}),
+                                  (4000, {"degenerate": True})])
+def test_cluster_tree_is_valid(mrs, n, kw):
+    desc = _soup(n, n, **kw)
+    sc = mrs.Scene(desc)
+    assert sc.tree() == "lbvh"
+    check_tree(sc.export_nodes(), desc["V"])
+    sc.set_tree("cluster")
+    assert sc.tree() == "cluster"
+    check_tree(sc.export_nodes(), desc["V"])
+    sc.rebuild()                        # the choice stays with the scene
+    assert sc.tree() == "cluster"
+
+
+@pytest.mark.parametrize("seed,n,kw", [(0, 8, {}), (2, 3000, {}), (3, 50000, {}),
+                                       (4, 3000, {"identical": True}),
+                                       (5, 4000, {"degenerate": True})])
+def test_cast_same_with_both_trees_and_brute_force(mrs, orc, seed, n, kw):
+    desc = _soup(seed, n, **kw)
+    o, d = scenes.random_rays(seed, 40000)
+    sc = mrs.Scene(desc)
+    sc.set_tree("cluster")
+    to, td = torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda()
+    pc, tc = sc.cast(to, td)
+    sc.set_tree("lbvh")
+    assert sc.tree() == "lbvh"
+    pl, tl = sc.cast(to, td)
+    assert torch.equal(pc, pl) and torch.equal(tc, tl)
+    pb, tb = orc.cast(desc["V"], o, d, brute=n <= 64)
+    assert np.array_equal(pc.cpu().numpy(), pb)
+    assert np.array_equal(tc.cpu().numpy(), tb)
+
+
+def test_procedural_scene_trees(mrs, orc):
+    # 200,968-triangle lit procedural scene: both trees valid, the clustering
+    # one with a lower surface-area cost and fewer node visits, renders
+    # identical bit for bit and equal to the oracle's on a small image
+    desc = scenes.procedural(0)
+    sc = mrs.Scene(desc)
+    sc.set_tree("cluster")
+    cost_c = check_tree(sc.export_nodes(), desc["V"])
+    st_c = mrs.render_stats(sc, 96, 96, 2, 8, 3, 7)
+    rc = mrs.render(sc, 96, 96, 2, 8, rr_start=3, seed=7)
+    sc.set_tree("lbvh")
+    cost_l = check_tree(sc.export_nodes(), desc["V"])
+    st_l = mrs.render_stats(sc, 96, 96, 2, 8, 3, 7)
+    rl = mrs.render(sc, 96, 96, 2, 8, rr_start=3, seed=7)
+    for k in rc:
+        assert torch.equal(rc[k], rl[k]), k
+    assert cost_c < 0.9 * cost_l, (cost_c, cost_l)
+    assert st_c["visits"] < st_l["visits"], (st_c, st_l)
+    r = orc.render(desc, 96, 96, 2, 8, rr_start=3, seed=7)
+    assert np.array_equal(rc["counts"].cpu().numpy().astype(np.uint64), r["counts"])
+    assert np.array_equal(rc["shadow_counts"].cpu().numpy().astype(np.uint64), r["shadow_counts"])
+    print(f"\nSAH cost: cluster {cost_c:.2f}, radix tree {cost_l:.2f}; closest-hit node visits "
+          f"{st_c['visits']} vs {st_l['visits']}, shadow {st_c['shadow_visits']} vs {st_l['shadow_visits']}")
+
+
+def test_set_tree_rejects_unknown_kind(mrs):
+    from paper_2106_12802_gb300._lib import call
+    sc = mrs.Scene(_soup(1, 10))
+    with pytest.raises(mrs.MrsError):
+        call("mrs_scene_set_tree", sc.handle, 7, None)
+    assert sc.tree() == "lbvh"
