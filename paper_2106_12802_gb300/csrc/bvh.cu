@@ -703,36 +703,37 @@ __global__ void __launch_bounds__(1024) k_ploc_finish(const int* __restrict__ id
     if (tid == 0 && (N != 1 || next != -1 || idA[0] != 0)) *err = 1;
 }
 
-// the render tree by clustering: returns MRS_ERR_CAPACITY (the caller builds
-// the LBVH instead) if it did not reduce to one root within the iteration bound.
-// The usual build -- init, kPlocBatch grid-wide rounds, the single-block
-// finish and the read-back of its error word -- is one CUDA graph per scene
-// (captured again when the tree size or the scratch buffer changes): the
-// rounds are short kernels whose host-side launch cost would dominate.  When
-// kPlocBatch rounds leave more than kPlocCap clusters, further rounds follow
-// by direct launches, kPlocBatch at a time, each batch ending with a read-back
-// of the cluster count.
-mrs_status build_ploc(mrs_scene_s* S, cudaStream_t st)
+// Scratch of the clustering build, carved from S->ploc_tmp
+struct PlocBufs {
+    float4* cb[2];       // cluster boxes (2 float4 each), ping-pong
+    int* ids[2];         // cluster node ids, ping-pong
+    int* nn;             // nearest neighbour of each position
+    int2* blk;           // per-block (kept, merges) totals, then their prefix sums
+    int* cnt;            // clusters at the start of round it
+    int* nxt;            // next internal node id at the start of round it
+    int* err;            // set by the finish unless it ends with the root as node 0
+    int nb;              // 256-position blocks of the first round
+};
+
+mrs_status ploc_bufs(mrs_scene_s* S, PlocBufs& b)
 {
     const int ns = S->ns;
-    const int nb = (ns + 255) / 256;
+    b.nb = (ns + 255) / 256;
     const size_t need = (size_t)ns * (2 * sizeof(int) + 4 * sizeof(float4) + sizeof(int)) +
-                        (size_t)nb * sizeof(int2) + 2 * (kPlocIters + kPlocBatch + 2) * sizeof(int) +
+                        (size_t)b.nb * sizeof(int2) + 2 * (kPlocIters + kPlocBatch + 2) * sizeof(int) +
                         sizeof(int) + 1024;
     mrs_status rc = S->ploc_tmp.ensure(need);
     if (rc != MRS_OK) return rc;
     char* p = S->ploc_tmp.as<char>();
-    float4* cb[2];
-    cb[0] = (float4*)p; p += (size_t)ns * 2 * sizeof(float4);
-    cb[1] = (float4*)p; p += (size_t)ns * 2 * sizeof(float4);
-    int* ids[2];
-    ids[0] = (int*)p; p += (size_t)ns * sizeof(int);
-    ids[1] = (int*)p; p += (size_t)ns * sizeof(int);
-    int* nn = (int*)p; p += (size_t)ns * sizeof(int);
-    int2* blk = (int2*)(((uintptr_t)p + 7) & ~(uintptr_t)7); p = (char*)(blk + nb);
-    int* cnt = (int*)p; p += (kPlocIters + kPlocBatch + 2) * sizeof(int);
-    int* nxt = (int*)p; p += (kPlocIters + kPlocBatch + 2) * sizeof(int);
-    int* err = (int*)p;
+    b.cb[0] = (float4*)p; p += (size_t)ns * 2 * sizeof(float4);
+    b.cb[1] = (float4*)p; p += (size_t)ns * 2 * sizeof(float4);
+    b.ids[0] = (int*)p; p += (size_t)ns * sizeof(int);
+    b.ids[1] = (int*)p; p += (size_t)ns * sizeof(int);
+    b.nn = (int*)p; p += (size_t)ns * sizeof(int);
+    b.blk = (int2*)(((uintptr_t)p + 7) & ~(uintptr_t)7); p = (char*)(b.blk + b.nb);
+    b.cnt = (int*)p; p += (kPlocIters + kPlocBatch + 2) * sizeof(int);
+    b.nxt = (int*)p; p += (kPlocIters + kPlocBatch + 2) * sizeof(int);
+    b.err = (int*)p;
     static bool attr_set[64] = {false};
     int dev = 0;
     MRS_CHECK(cudaGetDevice(&dev));
@@ -742,65 +743,68 @@ mrs_status build_ploc(mrs_scene_s* S, cudaStream_t st)
                                        (int)kPlocFinishSmem));
         attr_set[dev] = true;
     }
-    auto rounds = [&](int it0) {
-        for (int it = it0; it < it0 + kPlocBatch; ++it) {
-            const int a = it & 1;
-            k_ploc_nn<<<nb, 256, 0, st>>>(cb[a], cnt, it, nn);
-            k_ploc_count<<<nb, 256, 0, st>>>(nn, cnt, it, blk);
-            k_ploc_scan<<<1, 1024, 0, st>>>(blk, cnt, nxt, it);
-            k_ploc_compact<<<nb, 256, 0, st>>>(ids[a], cb[a], nn, blk, cnt, nxt, it, ids[a ^ 1],
-                                               cb[a ^ 1], S->nodes, S->box);
-        }
-    };
-    auto finish = [&](int it) {
-        k_ploc_finish<<<1, 1024, kPlocFinishSmem, st>>>(ids[it & 1], cb[it & 1], cnt, nxt, it,
-                                                        S->nodes, S->box, err);
-    };
-    const int it_g = ns > kPlocCap ? kPlocBatch : 0;     // rounds in the graph
-    if (!S->ploc_exec || S->ploc_ns != ns || S->ploc_buf != S->ploc_tmp.p) {
-        if (S->ploc_exec) { cudaGraphExecDestroy(S->ploc_exec); S->ploc_exec = nullptr; }
-        // captured on a private stream (the caller's may be the legacy default
-        // stream, which cannot be captured), launched on the caller's
-        if (!S->ploc_cap) MRS_CHECK(cudaStreamCreateWithFlags(&S->ploc_cap, cudaStreamNonBlocking));
-        cudaStream_t caller = st;
-        st = S->ploc_cap;
-        cudaGraph_t g = nullptr;
-        MRS_CHECK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-        k_ploc_init<<<blocks_for(ns, kBlock), kBlock, 0, st>>>(ns, S->box, ids[0], cb[0], cnt, nxt, err);
-        if (it_g) rounds(0);
-        finish(it_g);
-        cudaMemcpyAsync(S->class_host, err, sizeof(int), cudaMemcpyDeviceToHost, st);
-        cudaError_t e = cudaStreamEndCapture(st, &g);
-        st = caller;
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&S->ploc_exec, g, 0);
-        if (g) cudaGraphDestroy(g);
-        if (e != cudaSuccess) { S->ploc_exec = nullptr; return cuda_status(e, "clustering graph"); }
-        S->ploc_ns = ns;
-        S->ploc_buf = S->ploc_tmp.p;
+    return MRS_OK;
+}
+
+// rounds it0 .. it0 + kPlocBatch - 1 (4 kernels each)
+void ploc_rounds(mrs_scene_s* S, const PlocBufs& b, int it0, cudaStream_t st)
+{
+    for (int it = it0; it < it0 + kPlocBatch; ++it) {
+        const int a = it & 1;
+        k_ploc_nn<<<b.nb, 256, 0, st>>>(b.cb[a], b.cnt, it, b.nn);
+        k_ploc_count<<<b.nb, 256, 0, st>>>(b.nn, b.cnt, it, b.blk);
+        k_ploc_scan<<<1, 1024, 0, st>>>(b.blk, b.cnt, b.nxt, it);
+        k_ploc_compact<<<b.nb, 256, 0, st>>>(b.ids[a], b.cb[a], b.nn, b.blk, b.cnt, b.nxt, it,
+                                             b.ids[a ^ 1], b.cb[a ^ 1], S->nodes, S->box);
     }
-    MRS_CHECK(cudaGraphLaunch(S->ploc_exec, st));
-    MRS_LAUNCHED(2 + 4 * it_g);
-    MRS_CHECK(cudaStreamSynchronize(st));
-    if (!S->class_host[0]) return MRS_OK;
-    // more clusters than the finish takes (or a finish that did not converge)
-    MRS_CHECK(cudaMemcpyAsync(S->class_host, cnt + it_g, sizeof(int), cudaMemcpyDeviceToHost, st));
+}
+
+void ploc_finish(mrs_scene_s* S, const PlocBufs& b, int it, cudaStream_t st)
+{
+    k_ploc_finish<<<1, 1024, kPlocFinishSmem, st>>>(b.ids[it & 1], b.cb[it & 1], b.cnt, b.nxt, it,
+                                                    S->nodes, S->box, b.err);
+}
+
+// the usual clustering build (after k_leaves): init, kPlocBatch rounds when
+// the tree has more than kPlocCap leaves, the finish, the error word to the
+// host (S->class_host[0]); returns the kernels enqueued
+int ploc_enqueue(mrs_scene_s* S, const PlocBufs& b, cudaStream_t st)
+{
+    const int ns = S->ns;
+    k_ploc_init<<<blocks_for(ns, kBlock), kBlock, 0, st>>>(ns, S->box, b.ids[0], b.cb[0], b.cnt, b.nxt,
+                                                           b.err);
+    const int it_g = ns > kPlocCap ? kPlocBatch : 0;
+    if (it_g) ploc_rounds(S, b, 0, st);
+    ploc_finish(S, b, it_g, st);
+    cudaMemcpyAsync(S->class_host, b.err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    return 2 + 4 * it_g;
+}
+
+// after ploc_enqueue reported an error: more rounds if more than kPlocCap
+// clusters were left, kPlocBatch at a time with a count read-back after each
+// batch, then the finish again.  MRS_ERR_CAPACITY: no root within the bound
+// (the caller builds the radix tree instead).
+mrs_status ploc_continue(mrs_scene_s* S, const PlocBufs& b, cudaStream_t st)
+{
+    const int it_g = S->ns > kPlocCap ? kPlocBatch : 0;
+    MRS_CHECK(cudaMemcpyAsync(S->class_host, b.cnt + it_g, sizeof(int), cudaMemcpyDeviceToHost, st));
     MRS_CHECK(cudaStreamSynchronize(st));
     int n_now = S->class_host[0];
     if (n_now <= kPlocCap) return MRS_ERR_CAPACITY;
     int it = it_g;
     while (n_now > kPlocCap) {
         if (it >= kPlocIters) return MRS_ERR_CAPACITY;
-        rounds(it);
+        ploc_rounds(S, b, it, st);
         MRS_LAUNCHED(4 * kPlocBatch);
         it += kPlocBatch;
-        MRS_CHECK(cudaMemcpyAsync(S->class_host, cnt + it, sizeof(int), cudaMemcpyDeviceToHost, st));
+        MRS_CHECK(cudaMemcpyAsync(S->class_host, b.cnt + it, sizeof(int), cudaMemcpyDeviceToHost, st));
         MRS_CHECK(cudaStreamSynchronize(st));
         n_now = S->class_host[0];
     }
-    MRS_CHECK(cudaMemsetAsync(err, 0, sizeof(int), st));
-    finish(it);
+    MRS_CHECK(cudaMemsetAsync(b.err, 0, sizeof(int), st));
+    ploc_finish(S, b, it, st);
     MRS_LAUNCHED(1);
-    MRS_CHECK(cudaMemcpyAsync(S->class_host, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MRS_CHECK(cudaMemcpyAsync(S->class_host, b.err, sizeof(int), cudaMemcpyDeviceToHost, st));
     MRS_CHECK(cudaStreamSynchronize(st));
     return S->class_host[0] ? MRS_ERR_CAPACITY : MRS_OK;
 }
@@ -810,6 +814,24 @@ mrs_status build_ploc(mrs_scene_s* S, cudaStream_t st)
 // tests exhaustively first -- large triangles (a ground plane, walls) would
 // otherwise inflate the boxes of the tree's upper levels.  The closest hit is
 // the same either way (smallest t, ties to the smaller triangle index).
+// The radix tree over the sorted leaves (after k_leaves): topology, then the
+// bottom-up refit that writes the traversal nodes; returns the kernels enqueued
+int karras_enqueue(mrs_scene_s* S, cudaStream_t st)
+{
+    const int ns = S->ns;
+    k_karras<<<blocks_for(ns - 1, kBlock), kBlock, 0, st>>>(S->skeys, S->order, ns, S->left, S->right,
+                                                           S->parent);
+    k_refit<<<blocks_for(ns, kBlock), kBlock, 0, st>>>(ns, S->left, S->right, S->parent, S->box,
+                                                       S->visit, S->nodes);
+    return 2;
+}
+
+// The whole build is one CUDA graph per scene (captured again when the tree
+// size, the tree kind or a scratch buffer changes): some 20 short kernels for
+// the LBVH, a hundred for the clustering tree, whose host-side launch cost
+// would otherwise be most of the build.  The clustering build then reads its
+// error word back (one synchronisation) and, past kPlocBatch rounds or if
+// clustering gave up, goes on by direct launches.
 mrs_status build_lbvh(mrs_scene_s* S, cudaStream_t st)
 {
     const int n = S->n, ns = S->ns, nb = n - ns;
@@ -821,6 +843,9 @@ mrs_status build_lbvh(mrs_scene_s* S, cudaStream_t st)
                   (sizeof(uint32_t) + sizeof(int)) * 2 * (size_t)(ns > 0 ? ns : 1) + 256;
     mrs_status s = S->sort_tmp.ensure(need);
     if (s != MRS_OK) return s;
+    const bool cluster = ns > 1 && S->tree == MRS_TREE_CLUSTER;
+    PlocBufs pb;
+    if (cluster && (s = ploc_bufs(S, pb)) != MRS_OK) return s;
     char* p = S->sort_tmp.as<char>();
     float* part = (float*)p; p += sizeof(float) * 6 * nparts;
     uint32_t* counts = (uint32_t*)p; p += sizeof(uint32_t) * 256 * (size_t)ntiles;
@@ -829,52 +854,84 @@ mrs_status build_lbvh(mrs_scene_s* S, cudaStream_t st)
     int* va = (int*)p; p += sizeof(int) * (size_t)ns;
     int* vb = (int*)p;
 
-    cudaEvent_t lbvh_a = prof_on() ? prof_record(st) : nullptr;
-    if (ns > 0) {
-        k_bounds_partial<<<nparts, kBlock, 0, st>>>(S->V, ns, part, S->small_idx);
-        MRS_LAUNCHED(1);
-        k_morton<<<min(blocks_for(ns, kBlock), 8 * sm_count()), kBlock, 0, st>>>(
-            S->V, ns, part, nparts, nullptr, ka, va, S->small_idx);
-        MRS_LAUNCHED(1);
-        // 30-bit codes: digits at bits 0, 8, 16, 24 (4 passes, ends back in ka/va)
-        for (int pass = 0; pass < 4; ++pass) {
-            int shift = pass * 8;
-            uint32_t* kin = (pass & 1) ? kb : ka;
-            uint32_t* kout = (pass & 1) ? ka : kb;
-            int* vin = (pass & 1) ? vb : va;
-            int* vout = (pass & 1) ? va : vb;
-            k_sort_hist<<<ntiles, kBlock, 0, st>>>(kin, ns, shift, counts, ntiles);
-            MRS_LAUNCHED(1);
-            k_sort_scan<<<1, 1024, 0, st>>>(counts, 256 * ntiles);
-            MRS_LAUNCHED(1);
-            k_sort_scatter<<<ntiles, kBlock, 0, st>>>(kin, vin, kout, vout, ns, shift, counts, ntiles);
-            MRS_LAUNCHED(1);
+    // every kernel of the build on stream c; returns how many
+    auto enqueue = [&](cudaStream_t c, bool with_cluster) -> int {
+        int kernels = 0;
+        if (ns > 0) {
+            k_bounds_partial<<<nparts, kBlock, 0, c>>>(S->V, ns, part, S->small_idx);
+            k_morton<<<min(blocks_for(ns, kBlock), 8 * sm_count()), kBlock, 0, c>>>(
+                S->V, ns, part, nparts, nullptr, ka, va, S->small_idx);
+            kernels += 2;
+            // 30-bit codes: digits at bits 0, 8, 16, 24 (4 passes, ends back in ka/va)
+            for (int pass = 0; pass < 4; ++pass) {
+                int shift = pass * 8;
+                uint32_t* kin = (pass & 1) ? kb : ka;
+                uint32_t* kout = (pass & 1) ? ka : kb;
+                int* vin = (pass & 1) ? vb : va;
+                int* vout = (pass & 1) ? va : vb;
+                k_sort_hist<<<ntiles, kBlock, 0, c>>>(kin, ns, shift, counts, ntiles);
+                k_sort_scan<<<1, 1024, 0, c>>>(counts, 256 * ntiles);
+                k_sort_scatter<<<ntiles, kBlock, 0, c>>>(kin, vin, kout, vout, ns, shift, counts, ntiles);
+                kernels += 3;
+            }
+            cudaMemcpyAsync(S->skeys, ka, sizeof(uint32_t) * ns, cudaMemcpyDeviceToDevice, c);
+            cudaMemcpyAsync(S->order, va, sizeof(int) * ns, cudaMemcpyDeviceToDevice, c);
+            k_leaves<<<blocks_for(ns, kBlock), kBlock, 0, c>>>(S->V, S->tri_mat, S->tri_light, S->order,
+                                                               ns, S->tris, S->tri_ml, S->box, S->visit);
+            kernels += 1;
+            if (with_cluster) kernels += ploc_enqueue(S, pb, c);
+            else if (ns > 1) kernels += karras_enqueue(S, c);
         }
-        MRS_CHECK(cudaMemcpyAsync(S->skeys, ka, sizeof(uint32_t) * ns, cudaMemcpyDeviceToDevice, st));
-        MRS_CHECK(cudaMemcpyAsync(S->order, va, sizeof(int) * ns, cudaMemcpyDeviceToDevice, st));
-        k_leaves<<<blocks_for(ns, kBlock), kBlock, 0, st>>>(S->V, S->tri_mat, S->tri_light, S->order,
-                                                            ns, S->tris, S->tri_ml, S->box, S->visit);
-        MRS_LAUNCHED(1);
+        if (nb > 0) {
+            k_big_leaves<<<blocks_for(nb, kBlock), kBlock, 0, c>>>(S->V, S->tri_mat, S->tri_light,
+                                                                   S->big_idx, ns, nb, S->order,
+                                                                   S->tris, S->tri_ml);
+            kernels += 1;
+        }
+        return kernels;
+    };
+
+    // inside the caller's own stream capture (a captured frame) the kernels go
+    // straight into it; the clustering tree, which reads a word back, is not
+    // available there and the radix tree is built
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    MRS_CHECK(cudaStreamIsCapturing(st, &cs));
+    if (cs != cudaStreamCaptureStatusNone) {
+        MRS_LAUNCHED(enqueue(st, false));
         if (ns > 1) S->tree_built = MRS_TREE_LBVH;
-        if (ns > 1 && S->tree == MRS_TREE_CLUSTER) {
-            mrs_status pc = build_ploc(S, st);
-            if (pc == MRS_OK) S->tree_built = MRS_TREE_CLUSTER;
-            else if (pc != MRS_ERR_CAPACITY) return pc;
-        }
-        if (ns > 1 && S->tree_built == MRS_TREE_LBVH) {
-            k_karras<<<blocks_for(ns - 1, kBlock), kBlock, 0, st>>>(S->skeys, S->order, ns, S->left,
-                                                                   S->right, S->parent);
-            MRS_LAUNCHED(1);
-            k_refit<<<blocks_for(ns, kBlock), kBlock, 0, st>>>(ns, S->left, S->right, S->parent,
-                                                               S->box, S->visit, S->nodes);
-            MRS_LAUNCHED(1);
-        }
+        return cuda_status(cudaGetLastError(), "lbvh launch");
     }
-    if (nb > 0) {
-        k_big_leaves<<<blocks_for(nb, kBlock), kBlock, 0, st>>>(S->V, S->tri_mat, S->tri_light,
-                                                                S->big_idx, ns, nb, S->order,
-                                                                S->tris, S->tri_ml);
-        MRS_LAUNCHED(1);
+
+    const BuildKey key{n, ns, cluster ? 1 : 0, S->sort_tmp.p, cluster ? S->ploc_tmp.p : nullptr};
+    if (!S->build_exec || !(key == S->build_key)) {
+        if (S->build_exec) { cudaGraphExecDestroy(S->build_exec); S->build_exec = nullptr; }
+        // captured on a private stream (the caller's may be the legacy
+        // default stream, which cannot be captured), launched on the caller's
+        if (!S->cap_stream) MRS_CHECK(cudaStreamCreateWithFlags(&S->cap_stream, cudaStreamNonBlocking));
+        MRS_CHECK(cudaStreamBeginCapture(S->cap_stream, cudaStreamCaptureModeThreadLocal));
+        const int kernels = enqueue(S->cap_stream, cluster);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(S->cap_stream, &g);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&S->build_exec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) { S->build_exec = nullptr; return cuda_status(e, "build graph"); }
+        S->build_key = key;
+        S->build_kernels = kernels;
+    }
+    cudaEvent_t lbvh_a = prof_on() ? prof_record(st) : nullptr;
+    MRS_CHECK(cudaGraphLaunch(S->build_exec, st));
+    MRS_LAUNCHED(S->build_kernels);
+    if (cluster) {
+        MRS_CHECK(cudaStreamSynchronize(st));
+        mrs_status pc = S->class_host[0] ? ploc_continue(S, pb, st) : MRS_OK;
+        if (pc == MRS_ERR_CAPACITY) {
+            S->tree_built = MRS_TREE_LBVH;
+            MRS_LAUNCHED(karras_enqueue(S, st));
+        } else if (pc != MRS_OK) {
+            return pc;
+        }
+    } else if (ns > 1) {
+        S->tree_built = MRS_TREE_LBVH;
     }
     if (lbvh_a) prof_push(PK_LBVH, lbvh_a, prof_record(st));
     return cuda_status(cudaGetLastError(), "lbvh launch");
@@ -1000,8 +1057,8 @@ void free_scene(mrs_scene_s* S)
     for (void* q : ptrs)
         if (q) cudaFree(q);
     S->sort_tmp.release();
-    if (S->ploc_exec) cudaGraphExecDestroy(S->ploc_exec);
-    if (S->ploc_cap) cudaStreamDestroy(S->ploc_cap);
+    if (S->build_exec) cudaGraphExecDestroy(S->build_exec);
+    if (S->cap_stream) cudaStreamDestroy(S->cap_stream);
     S->ploc_tmp.release();
     S->export_tmp.release();
     S->class_tmp.release();

@@ -99,6 +99,20 @@ inline int sm_count()
 
 }  // namespace mrs
 
+namespace mrs {
+// what a captured tree-build graph depends on besides the scene's own arrays
+struct BuildKey {
+    int n = -1, ns = -1, cluster = -1;
+    void* sort_buf = nullptr;
+    void* ploc_buf = nullptr;
+    bool operator==(const BuildKey& o) const
+    {
+        return n == o.n && ns == o.ns && cluster == o.cluster && sort_buf == o.sort_buf &&
+               ploc_buf == o.ploc_buf;
+    }
+};
+}  // namespace mrs
+
 // Scene handle: triangle soup, materials, lights, camera and the LBVH, all
 // resident on the device, plus the render arena.
 struct mrs_scene_s {
@@ -128,10 +142,10 @@ struct mrs_scene_s {
     int2* tri_ml = nullptr;      // [n]: material, light in sorted order
     mrs::Buf sort_tmp;           // radix-sort scratch
     mrs::Buf ploc_tmp;           // clustering-build scratch
-    cudaGraphExec_t ploc_exec = nullptr;   // the clustering build as a graph (see build_ploc)
-    int ploc_ns = -1;                      // ... for this tree size
-    void* ploc_buf = nullptr;              // ... and this scratch buffer
-    cudaStream_t ploc_cap = nullptr;       // stream the graph is captured on
+    cudaGraphExec_t build_exec = nullptr;  // the tree build as one graph (see build_lbvh)
+    mrs::BuildKey build_key;               // ... for these sizes, tree kind and buffers
+    int build_kernels = 0;                 // ... holding this many kernels
+    cudaStream_t cap_stream = nullptr;     // stream the graph is captured on
     int32_t tree = MRS_TREE_LBVH;          // render tree to build (MRS_TREE_*)
     int32_t tree_built = MRS_TREE_LBVH;    // the one built (the LBVH if clustering gave up)
     mrs::Buf class_tmp;          // large / small classification scratch
