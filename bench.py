@@ -599,7 +599,8 @@ def paper_network(mrs, flush, s=S, reps=10):
         torch.cuda.synchronize()
         tb.append(e0.elapsed_time(e1) / nb)
     del lrb, hrb, outb
-    train = rdn_train_timing(mrs, flush, s)
+    train = rdn_train_timing(mrs, flush, s, precision="fp32")
+    train_bf16 = rdn_train_timing(mrs, flush, s, precision="bf16", reps=10, warmup=3)
     ms = float(np.median(ts))
     flop = rdn.flops_per_lr_pixel(s) * LR * LR
     peaks = _peaks()
@@ -613,7 +614,8 @@ def paper_network(mrs, flush, s=S, reps=10):
            "tensor_frac_of_measured_sustained": tf / peaks["bf16_tflops_sustained"],
            "conv_tc_ms_events": conv_ms, "conv_tc_launches": prof["conv_tc"][1] // reps_prof,
            "conv_tc_tflops": flop / (conv_ms * 1e-3) / 1e12 if conv_ms else None,
-           "l2": "flushed before every rep (512 MiB write)", "train_step_fp32": train}
+           "l2": "flushed before every rep (512 MiB write)", "train_step_fp32": train,
+           "train_step_bf16": train_bf16}
     net.close()
     return res
 
@@ -628,12 +630,13 @@ def rdn_train_flop_per_lr_pixel(s):
     return 3 * fwd - enc
 
 
-def rdn_train_timing(mrs, flush, s=S, N=16, crop=192, reps=3, warmup=2):
-    """Device time of one FP32 training step of the method's own network at
-    the paper's training batch (Sec. 4 "Implement details": mini-batch 16,
+def rdn_train_timing(mrs, flush, s=S, N=16, crop=192, reps=3, warmup=2, precision="fp32"):
+    """Device time of one training step of the method's own network at the
+    paper's training batch (Sec. 4 "Implement details": mini-batch 16,
     192 x 192 HR patches at x4): forward with its activations kept, the
-    robust loss, the backward of every step, Adam.  Random radiance-like
-    inputs on the device, L2 flushed before every step."""
+    robust loss, the backward of every step, Adam; FP32 on the SIMT cores or
+    BF16 on the tensor cores.  Random radiance-like inputs on the device, L2
+    flushed before every step."""
     import torch
 
     from paper_2106_12802_gb300 import rdn
@@ -646,14 +649,16 @@ def rdn_train_timing(mrs, flush, s=S, N=16, crop=192, reps=3, warmup=2):
     nrm = torch.rand((N, crop, crop, 3), device="cuda", generator=g) * 2 - 1
     tgt = torch.rand((N, crop, crop, 3), device="cuda", generator=g) * 2
     for _ in range(warmup):
-        net.train_step(lr, hr, alb, nrm, tgt, lr=1e-4, loss="robust", beta=0.1, sync_loss=False)
+        net.train_step(lr, hr, alb, nrm, tgt, lr=1e-4, loss="robust", beta=0.1, sync_loss=False,
+                       precision=precision)
     torch.cuda.synchronize()
     ts = []
     for _ in range(reps):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        net.train_step(lr, hr, alb, nrm, tgt, lr=1e-4, loss="robust", beta=0.1, sync_loss=False)
+        net.train_step(lr, hr, alb, nrm, tgt, lr=1e-4, loss="robust", beta=0.1, sync_loss=False,
+                       precision=precision)
         e1.record()
         torch.cuda.synchronize()
         ts.append(e0.elapsed_time(e1))
@@ -661,11 +666,16 @@ def rdn_train_timing(mrs, flush, s=S, N=16, crop=192, reps=3, warmup=2):
     ms = float(np.median(ts))
     flop = rdn_train_flop_per_lr_pixel(s) * N * h * h
     tf = flop / (ms * 1e-3) / 1e12
-    sm = torch.cuda.get_device_properties(0).multi_processor_count
-    fp32_peak = sm * 128 * 2 * 2.07e9 / 1e12   # TFLOP/s: FP32 lanes x FMA x max SM clock
-    return {"batch": [N, crop, crop], "scale": s, "precision": "fp32 (SIMT)", "loss": "robust, beta 0.1",
-            "optimizer": "Adam, lr 1e-4", "ms": ms, "tflop_per_step": flop / 1e12, "tflops": tf,
-            "fp32_frac": tf / fp32_peak, "fp32_peak_tflops": fp32_peak}
+    res = {"batch": [N, crop, crop], "scale": s, "loss": "robust, beta 0.1", "optimizer": "Adam, lr 1e-4",
+           "ms": ms, "tflop_per_step": flop / 1e12, "tflops": tf}
+    if precision == "fp32":
+        sm = torch.cuda.get_device_properties(0).multi_processor_count
+        fp32_peak = sm * 128 * 2 * 2.07e9 / 1e12   # TFLOP/s: FP32 lanes x FMA x max SM clock
+        res.update({"precision": "fp32 (SIMT)", "fp32_frac": tf / fp32_peak, "fp32_peak_tflops": fp32_peak})
+    else:
+        res.update({"precision": "bf16 (tensor cores: forward, input and weight gradients)",
+                    "tensor_frac_of_measured_sustained": tf / _peaks()["bf16_tflops_sustained"]})
+    return res
 
 
 def fp8_gemm_tflops(n=8192, reps=10):

@@ -665,26 +665,34 @@ mrs_status mrs_rdn_check(mrs_rdn rdn);
 
 /* One training step of the network (Sec. 4 "Implement details": trained
  * with Adam; the loss l_r of Sec. 3 "Loss function", or the L1-log loss):
- * the FP32 forward of mrs_rdn_fuse (the same arithmetic in the same order,
- * so `out` equals mrs_rdn_fuse's FP32 result bit for bit) keeping every
- * block's concatenation and every ReLU output, the loss of I_SR against
- * min(target, 100) (firefly clipping of the training target, Sec. 3.2; the
- * inputs are used as given) over N*H*W*3 values reduced in float64, the
- * backward of every step in reverse (transposed convolutions with flipped
- * taps, ReLU masks from the stored outputs, deshuffle / shuffle exchanged,
- * the dense concatenations' gradients summed per part, the block, group and
- * Eq. F_DF skips adding theirs; dW / db reduced in a fixed order), and one
- * bias-corrected Adam update (beta1 0.9, beta2 0.999, eps 1e-8) of the FP32
- * weights at learning rate lr (>= 0).
+ * the forward of mrs_rdn_fuse keeping every block's concatenation and every
+ * ReLU output, the loss of I_SR against min(target, 100) (firefly clipping of
+ * the training target, Sec. 3.2; the inputs are used as given) over N*H*W*3
+ * values reduced in float64, the backward of every step in reverse
+ * (transposed convolutions with flipped taps, ReLU masks from the stored
+ * outputs, deshuffle / shuffle exchanged, the dense concatenations' gradients
+ * summed per part, the block, group and Eq. F_DF skips adding theirs; dW / db
+ * reduced in a fixed order), and one bias-corrected Adam update (beta1 0.9,
+ * beta2 0.999, eps 1e-8) of the FP32 weights at learning rate lr (>= 0).
+ * precision:
+ *   MRS_PREC_FP32  SIMT, the same forward arithmetic in the same order as
+ *                  mrs_rdn_fuse's FP32 path (`out` equals it bit for bit)
+ *   MRS_PREC_BF16  tensor cores: the BF16 forward (a block's output is its
+ *                  input plus its local-fusion ReLU output summed in FP32 and
+ *                  rounded once, so not bit-equal to mrs_rdn_fuse's BF16
+ *                  output), input gradients as convolutions with the
+ *                  transposed, tap-flipped BF16 weights, weight gradients per
+ *                  64 x 64 tile reduced in FP32, BF16 activation gradients
  * Images as in mrs_rdn_fuse plus target device [N][H][W][3].  loss one of
- * MRS_LOSS_L1LOG / MRS_LOSS_ROBUST (beta > 0 for the latter).  precision:
- * MRS_PREC_FP32 (SIMT; the only one accepted).  out (device [N][H][W][3],
- * may be NULL) receives I_SR of the forward; loss_out (HOST, may be NULL)
- * the mean loss, which synchronises `stream`.  The first step allocates the
- * gradient and Adam moments (3 x n_params floats, moments zero); the
- * workspace (about 20 KB per LR pixel plus 1.3 KB per HR pixel) lives in the
- * handle.  A later MRS_PREC_BF16 mrs_rdn_fuse repacks its BF16 weights from
- * the updated FP32 ones.  Limit: N*H*W <= 2^24. */
+ * MRS_LOSS_L1LOG / MRS_LOSS_ROBUST (beta > 0 for the latter).  out (device
+ * [N][H][W][3], may be NULL) receives I_SR of the forward; loss_out (HOST,
+ * may be NULL) the mean loss, which synchronises `stream` (and then
+ * MRS_ERR_TIMEOUT if a BF16 step's tensor-core wait gave up).  The first step
+ * allocates the gradient and Adam moments (3 x n_params floats, moments
+ * zero); the workspace (FP32: about 20 KB per LR pixel plus 1.3 KB per HR
+ * pixel; BF16: about 11 KB per LR pixel plus 0.8 KB per HR pixel) lives in
+ * the handle.  A later MRS_PREC_BF16 mrs_rdn_fuse repacks its BF16 weights
+ * from the updated FP32 ones.  Limit: N*H*W <= 2^24. */
 mrs_status mrs_rdn_train_step(mrs_rdn rdn, const float* lrhs, const float* hrls,
                               const float* albedo, const float* normal, const float* extra,
                               const float* target, int32_t N, int32_t H, int32_t W, int32_t loss,

@@ -25,6 +25,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <array>
 #include <vector>
 
 #include "conv_tc.cuh"
@@ -345,6 +346,94 @@ __global__ void k_dw_reduce_tiles(const float* __restrict__ part, const float* _
     }
 }
 
+// packed[i] = bf16(src[idx[i]]) (0 where idx[i] < 0): weights re-packed from
+// the FP32 parameters through a layout's index table
+__global__ void k_gather_bf16(const float* __restrict__ src, const int* __restrict__ idx, size_t n,
+                              __nv_bfloat16* __restrict__ packed)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int k = idx[i];
+        packed[i] = __float2bfloat16_rn(k >= 0 ? src[k] : 0.0f);
+    }
+}
+__global__ void k_gather_f32(const float* __restrict__ src, const int* __restrict__ idx, size_t n,
+                             float* __restrict__ out)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int k = idx[i];
+        out[i] = k >= 0 ? src[k] : 0.0f;
+    }
+}
+
+// ---- training (BF16): elementwise steps ------------------------------------
+// out[i] = act[i] > 0 ? d[i] : 0 (out may be d)
+__global__ void k_mask_copy_bf16(const __nv_bfloat16* d, const __nv_bfloat16* __restrict__ act,
+                                 size_t n, __nv_bfloat16* out)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        out[i] = __bfloat162float(act[i]) > 0.0f ? d[i] : __float2bfloat16_rn(0.0f);
+}
+
+// out = a + b (+ c) (+ e), summed in FP32 and rounded once; when act is given,
+// out = act > 0 ? that : 0
+__global__ void k_sum_bf16(__nv_bfloat16* out, const __nv_bfloat16* a, const __nv_bfloat16* b,
+                           const __nv_bfloat16* c, const __nv_bfloat16* e,
+                           const __nv_bfloat16* __restrict__ act, size_t n)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        float v = __bfloat162float(a[i]) + __bfloat162float(b[i]);
+        if (c) v += __bfloat162float(c[i]);
+        if (e) v += __bfloat162float(e[i]);
+        if (act && !(__bfloat162float(act[i]) > 0.0f)) v = 0.0f;
+        out[i] = __float2bfloat16_rn(v);
+    }
+}
+
+// bf16 [P][64] rows from FP32 [P][cin] (channels past cin zero)
+__global__ void k_f32_to_bf16_rows(const float* __restrict__ x, size_t P, int cin,
+                                   __nv_bfloat16* __restrict__ o)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < P * 64;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const size_t p = i / 64;
+        const int c = (int)(i % 64);
+        o[i] = __float2bfloat16_rn(c < cin ? x[p * cin + c] : 0.0f);
+    }
+}
+
+// One tensor-core weight-gradient tile (part [G][9][cout_t][cin_t], dbpart
+// [G][cout_t]) summed over its G partials in order into a layer's gradient
+// [cout][KK][cin] (KK = 9, or 1 for a 1x1 layer: tap 4 of the tile):
+// tile output o' is layer output o_mul o' + o_add, tile input c' is layer input
+// c0 + c', or, for chunk q >= 1 of the fuse conv, 64 + dsf_channel(c', oy, ox, D)
+// with q - 1 = oy s + ox.  The bias is written when with_bias.
+__global__ void k_wg_reduce(const float* __restrict__ part, const float* __restrict__ dbpart, int G,
+                            int cin_t, int cout_t, int KK, int CIN, int o_mul, int o_add, int c0,
+                            int q, int s, int D, int with_bias, float* __restrict__ gw,
+                            float* __restrict__ gb)
+{
+    const size_t nw = (size_t)cout_t * KK * cin_t;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nw + cout_t;
+         i += (size_t)gridDim.x * blockDim.x) {
+        float acc = 0.0f;
+        if (i < nw) {
+            const int c = (int)(i % cin_t), tl = (int)((i / cin_t) % KK), o = (int)(i / ((size_t)cin_t * KK));
+            const int t = KK == 9 ? tl : 4;
+            for (int g = 0; g < G; ++g) acc += part[(((size_t)g * 9 + t) * cout_t + o) * cin_t + c];
+            const int ci = q > 0 ? 64 + dsf_channel(c, (q - 1) / s, (q - 1) % s, D) : c0 + c;
+            gw[((size_t)(o_mul * o + o_add) * KK + tl) * CIN + ci] = acc;
+        } else if (with_bias) {
+            const int o = (int)(i - nw);
+            for (int g = 0; g < G; ++g) acc += dbpart[(size_t)g * cout_t + o];
+            gb[o_mul * o + o_add] = acc;
+        }
+    }
+}
+
 inline int grid_for(size_t n)
 {
     size_t g = (n + 255) / 256;
@@ -372,6 +461,17 @@ struct mrs_rdn_s {
     float* bch = nullptr;          // chunk biases [nchunks][64]
     std::vector<WChunk> ch;
     std::vector<int> first;        // first chunk of each layer
+    std::vector<int> widx, bidx;   // packing index tables (parameter of each packed value, -1: 0)
+    int* d_widx = nullptr;         // ... on the device (uploaded by the first BF16 training step)
+    int* d_bidx = nullptr;
+    // transposed chunks of the BF16 training step's input gradients: layer li's
+    // chunk j at rows tfirst[li] + 9 * 64 * j of wmapT_all (-1: none)
+    std::vector<int> tidx, tfirst;
+    int* d_tidx = nullptr;
+    __nv_bfloat16* wbfT = nullptr;
+    CUtensorMap wmapT_all;
+    Buf trb;                       // BF16 training workspace
+    Buf tdmaps;                    // its multi-chunk A-operand maps on the device
     CUtensorMap wmap_all;          // every chunk's weights as one [rows][64] tensor
     std::vector<CUtensorMap> hmaps;  // A-operand maps of the multi-chunk convs of a call
     Buf dmaps;                     // their device copy
@@ -389,58 +489,73 @@ struct mrs_rdn_s {
 namespace mrs {
 namespace {
 
-// BF16 chunks of every layer, packed on the host as [tap][o][c] (o < nout,
-// c < 64) for conv_tc, with per-chunk biases (the layer bias on the chunk that
-// starts a chain, zero elsewhere)
-mrs_status pack_chunks(mrs_rdn_s* r, const float* P)
+// BF16 chunks of every layer, [tap][o][c] (o < nout, c < 64) for conv_tc,
+// with per-chunk biases (the layer bias on the chunk that starts a chain, zero
+// elsewhere).  The layout is an index table built once on the host: for each
+// packed weight and bias, the parameter it holds (or -1: zero).  mrs_rdn_create
+// packs through it on the host; a training step re-packs the updated FP32
+// weights through the same table on the device (k_gather_bf16), into the same
+// buffers, so the tensor maps stay valid.
+void build_pack_index(mrs_rdn_s* r)
 {
-    std::vector<__nv_bfloat16> wb;
-    std::vector<float> bb;
+    std::vector<int>& wi = r->widx;
+    std::vector<int>& bi = r->bidx;
+    wi.clear();
+    bi.clear();
     r->ch.clear();
     r->first.clear();
     auto chunk = [&](int nout, auto wfun, auto bfun) {
         WChunk c;
-        c.off = wb.size();
+        c.off = wi.size();
         c.nout = nout;
         for (int t = 0; t < 9; ++t)
             for (int o = 0; o < nout; ++o)
-                for (int k = 0; k < 64; ++k) wb.push_back(__float2bfloat16_rn(wfun(t, o, k)));
-        for (int o = 0; o < 64; ++o) bb.push_back(o < nout ? bfun(o) : 0.0f);
+                for (int k = 0; k < 64; ++k) wi.push_back(wfun(t, o, k));
+        for (int o = 0; o < 64; ++o) bi.push_back(o < nout ? bfun(o) : -1);
         r->ch.push_back(c);
     };
     const int D = r->D, s = r->s;
     for (size_t li = 0; li < r->L.size(); ++li) {
         const RLayer& l = r->L[li];
         r->first.push_back((int)r->ch.size());
-        const float* w = P + l.woff;
-        const float* b = P + l.boff;
+        const int w = (int)l.woff, b = (int)l.boff;
         const bool is_up = li + 1 < r->L.size() && l.cout == 4 * kF;
         if (li == 2) {
             // fuse: chunk 0 = F_LRHS channels, chunk 1 + oy s + ox = HR sub-pixel (oy, ox)
             for (int q = 0; q <= s * s; ++q) {
                 int oy = q ? (q - 1) / s : 0, ox = q ? (q - 1) % s : 0;
-                chunk(64, [&](int t, int o, int k) -> float {
-                    if (t != 4) return 0.0f;
+                chunk(64, [&](int t, int o, int k) -> int {
+                    if (t != 4) return -1;
                     int ci = q == 0 ? k : 64 + dsf_channel(k, oy, ox, D);
-                    return w[(size_t)o * l.cin + ci];
-                }, [&](int o) -> float { return q == 0 ? b[o] : 0.0f; });
+                    return w + o * l.cin + ci;
+                }, [&](int o) -> int { return q == 0 ? b + o : -1; });
             }
         } else if (is_up) {
             // upsampling conv: chunk q = 2 dy + dx computes output channels 4c + q
             for (int q = 0; q < 4; ++q)
-                chunk(64, [&](int t, int o, int k) -> float {
-                    return w[((size_t)(4 * o + q) * 9 + t) * l.cin + k];
-                }, [&](int o) -> float { return b[4 * o + q]; });
+                chunk(64, [&](int t, int o, int k) -> int {
+                    return w + ((4 * o + q) * 9 + t) * l.cin + k;
+                }, [&](int o) -> int { return b + 4 * o + q; });
         } else {
             const int nout = l.cout > 16 ? 64 : 16;
             const int nch = (l.cin + 63) / 64;
             for (int j = 0; j < nch; ++j)
-                chunk(nout, [&](int t, int o, int k) -> float {
+                chunk(nout, [&](int t, int o, int k) -> int {
                     int ci = 64 * j + k;
-                    return (o < l.cout && ci < l.cin) ? w[((size_t)o * 9 + t) * l.cin + ci] : 0.0f;
-                }, [&](int o) -> float { return (j == 0 && o < l.cout) ? b[o] : 0.0f; });
+                    return (o < l.cout && ci < l.cin) ? w + (o * 9 + t) * l.cin + ci : -1;
+                }, [&](int o) -> int { return (j == 0 && o < l.cout) ? b + o : -1; });
         }
     }
+}
+
+mrs_status pack_chunks(mrs_rdn_s* r, const float* P)
+{
+    build_pack_index(r);
+    std::vector<__nv_bfloat16> wb(r->widx.size());
+    std::vector<float> bb(r->bidx.size());
+    for (size_t i = 0; i < wb.size(); ++i)
+        wb[i] = __float2bfloat16_rn(r->widx[i] >= 0 ? P[r->widx[i]] : 0.0f);
+    for (size_t i = 0; i < bb.size(); ++i) bb[i] = r->bidx[i] >= 0 ? P[r->bidx[i]] : 0.0f;
     if (r->wbf) cudaFree(r->wbf);
     if (r->bch) cudaFree(r->bch);
     r->wbf = nullptr;
@@ -985,16 +1100,406 @@ mrs_status ensure_train_state(mrs_rdn_s* r)
     return MRS_OK;
 }
 
-// the BF16 chunks from the current FP32 weights (after training steps)
+// Transposed, tap-flipped chunks for the input gradients (dx = conv(dz, w^T)):
+// [tap][c][o] = w[o][8 - tap][c] for a dgrad output channel c (a forward input
+// channel) and a dgrad input channel o (a forward output channel), in 64 x 64
+// chunks: one per 64 forward input channels (a dense conv's concatenation
+// parts, the fuse conv's F_LRHS part and deshuffle views, centre tap only),
+// one per sub-pixel view q for an upsampling conv (its dgrad sums the four
+// views in one multi-chunk launch), one for H_Rec (forward outputs 3, the rest
+// zero).  The encoders need none (their inputs are images).
+void build_tpack_index(mrs_rdn_s* r)
+{
+    std::vector<int>& ti = r->tidx;
+    ti.clear();
+    r->tfirst.assign(r->L.size(), -1);
+    auto tchunk = [&](auto f) {
+        for (int t = 0; t < 9; ++t)
+            for (int c = 0; c < 64; ++c)
+                for (int o = 0; o < 64; ++o) ti.push_back(f(t, c, o));
+    };
+    const int D = r->D, s = r->s, nl = (int)r->L.size();
+    for (int li = 2; li < nl; ++li) {
+        const RLayer& l = r->L[li];
+        const int w = (int)l.woff;
+        r->tfirst[li] = (int)(ti.size() / 64);
+        if (li == 2) {
+            for (int q = 0; q <= s * s; ++q) {
+                const int oy = q ? (q - 1) / s : 0, ox = q ? (q - 1) % s : 0;
+                tchunk([&](int t, int c, int o) -> int {
+                    if (t != 4) return -1;
+                    const int ci = q == 0 ? c : 64 + dsf_channel(c, oy, ox, D);
+                    return w + o * l.cin + ci;
+                });
+            }
+        } else if (li == nl - 1) {
+            tchunk([&](int t, int c, int o) -> int { return o < l.cout ? w + (o * 9 + (8 - t)) * l.cin + c : -1; });
+        } else if (l.cout == 4 * kF) {
+            for (int q = 0; q < 4; ++q)
+                tchunk([&](int t, int c, int o) -> int { return w + ((4 * o + q) * 9 + (8 - t)) * l.cin + c; });
+        } else {
+            for (int j = 0; j < l.cin / 64; ++j)
+                tchunk([&](int t, int c, int o) -> int { return w + (o * 9 + (8 - t)) * l.cin + 64 * j + c; });
+        }
+    }
+}
+
+// the BF16 chunks from the current FP32 weights (after training steps), on
+// the device through the packing index tables (uploaded on first use)
+mrs_status upload_index(const std::vector<int>& h, int** d)
+{
+    if (*d) return MRS_OK;
+    MRS_CHECK(cudaMalloc(d, h.size() * sizeof(int) + 4));
+    MRS_CHECK(cudaMemcpy(*d, h.data(), h.size() * sizeof(int), cudaMemcpyHostToDevice));
+    return MRS_OK;
+}
+
+mrs_status repack_bf16(mrs_rdn_s* r, cudaStream_t st)
+{
+    mrs_status rc = upload_index(r->widx, &r->d_widx);
+    if (rc == MRS_OK) rc = upload_index(r->bidx, &r->d_bidx);
+    if (rc != MRS_OK) return rc;
+    k_gather_bf16<<<grid_for(r->widx.size()), 256, 0, st>>>(r->master, r->d_widx, r->widx.size(), r->wbf);
+    k_gather_f32<<<grid_for(r->bidx.size()), 256, 0, st>>>(r->master, r->d_bidx, r->bidx.size(), r->bch);
+    MRS_LAUNCHED(2);
+    r->bf_stale = false;
+    return cuda_status(cudaGetLastError(), "rdn repack");
+}
+
 mrs_status repack_if_stale(mrs_rdn_s* r, cudaStream_t st)
 {
-    if (!r->bf_stale) return MRS_OK;
-    std::vector<float> host(r->np);
-    MRS_CHECK(cudaStreamSynchronize(st));
-    MRS_CHECK(cudaMemcpy(host.data(), r->master, r->np * 4, cudaMemcpyDeviceToHost));
-    mrs_status rc = pack_chunks(r, host.data());
-    if (rc == MRS_OK) r->bf_stale = false;
-    return rc;
+    return r->bf_stale ? repack_bf16(r, st) : MRS_OK;
+}
+
+// ---- training step (BF16 tensor cores) ---------------------------------------
+// The forward of rdn_bf16 with every tensor the backward reads kept apart
+// (each block's input, F_1..F_3 and ReLU(local fusion); a block's output is
+// its input + that ReLU output, summed in FP32 and rounded once, plus the
+// group and Eq. F_DF skips), the loss on the FP32 I_SR, then the backward:
+// input gradients as tensor-core convs with the transposed, tap-flipped chunk
+// weights (ReLU masks as epilogues or elementwise passes, the dense parts'
+// gradients accumulated in place by residual epilogues, the shuffle and
+// deshuffle exchanged through strided views), weight gradients on k_wgrad_tc
+// per 64 x 64 tile with a fixed-order reduction into the FP32 gradient, Adam
+// on the FP32 weights.  Activations and their gradients are BF16.
+mrs_status rdn_train_bf16(mrs_rdn_s* r, const float* lrhs, const float* hrls, const float* alb,
+                          const float* nrm, const float* extra, const float* tgt, int N, int H, int W,
+                          int kind, float beta, float lr, float* yout, double* loss_out,
+                          cudaStream_t st)
+{
+    const int s = r->s, D = r->D, h = H / s, w = W / s, SS = s * s;
+    const int nblk = kRDG * kRDB, nl = (int)r->L.size();
+    const size_t Pl = (size_t)N * h * w, Ph = (size_t)N * H * W;
+    size_t Pd[4];
+    int hd[4], wd[4];
+    Pd[0] = Pl; hd[0] = h; wd[0] = w;
+    size_t nUrows = 0;
+    for (int d = 0; d < D; ++d) {
+        Pd[d + 1] = 4 * Pd[d]; hd[d + 1] = 2 * hd[d]; wd[d + 1] = 2 * wd[d];
+        nUrows += Pd[d + 1];
+    }
+    mrs_status rc = MRS_OK;
+    // weights: forward chunks and transposed chunks from the FP32 parameters
+    if (r->tidx.empty()) {
+        build_tpack_index(r);
+        if ((rc = upload_index(r->tidx, &r->d_tidx)) != MRS_OK) return rc;
+        MRS_CHECK(cudaMalloc(&r->wbfT, r->tidx.size() * sizeof(__nv_bfloat16)));
+        if ((rc = tc_make_w_map(&r->wmapT_all, r->wbfT, (int)(r->tidx.size() / 64), 64, TC_BF16)) != MRS_OK)
+            return rc;
+    }
+    if ((rc = repack_bf16(r, st)) != MRS_OK) return rc;
+    k_gather_bf16<<<grid_for(r->tidx.size()), 256, 0, st>>>(r->master, r->d_tidx, r->tidx.size(), r->wbfT);
+    MRS_LAUNCHED(1);
+
+    // workspace: BF16 [P][64] tensors, then FP32
+    const size_t rows = Pl * (3 + 15 + 4 * nblk + 10) + Ph * 6 + nUrows;
+    const int maxp = tc_wgrad_max_parts();
+    const size_t nf = Ph * 6 + (size_t)maxp * 9 * 4096 + (size_t)maxp * 64 + 64;
+    if ((rc = r->trb.ensure(rows * 128 + nf * 4 + (kLossParts + 2) * 8 + 4096)) != MRS_OK) return rc;
+    __nv_bfloat16* bp = r->trb.as<__nv_bfloat16>();
+    auto take = [&](size_t P) { __nv_bfloat16* q = bp; bp += P * 64; return q; };
+    __nv_bfloat16* inL = take(Pl);
+    __nv_bfloat16* inH = take(Ph);
+    __nv_bfloat16* Flr = take(Pl);
+    __nv_bfloat16* Fh0 = take(Ph);
+    __nv_bfloat16* F0 = take(Pl);
+    __nv_bfloat16* X[kRDG * kRDB + 1];       // block inputs; X[nblk] = F_DF
+    X[0] = F0;
+    for (int k = 1; k <= nblk; ++k) X[k] = take(Pl);
+    __nv_bfloat16* Fk[kRDG * kRDB][4];       // F_1, F_2, F_3, ReLU(local fusion) of each block
+    for (int k = 0; k < nblk; ++k)
+        for (int j = 0; j < 4; ++j) Fk[k][j] = take(Pl);
+    __nv_bfloat16* U[4];                      // U[0] = F_DF, U[d + 1] the output of upsampling stage d
+    U[0] = X[nblk];
+    for (int d = 1; d <= D; ++d) U[d] = take(Pd[d]);
+    __nv_bfloat16* dyb = take(Ph);
+    __nv_bfloat16* dU[2] = {take(Ph), take(Ph)};
+    __nv_bfloat16* G = take(Pl);              // gradient of the current block's output / input
+    __nv_bfloat16* dp[4];                     // dp[0] = G; dp[1..3]: the block's F_1..F_3 gradients
+    dp[0] = G;
+    for (int j = 1; j < 4; ++j) dp[j] = take(Pl);
+    __nv_bfloat16* dz4 = take(Pl);
+    __nv_bfloat16* dSkip = take(Pl);
+    __nv_bfloat16* dzf = take(Pl);
+    __nv_bfloat16* dzlr = take(Pl);
+    __nv_bfloat16* dz1 = take(Ph);
+    float* y = (float*)bp;
+    float* dy = y + Ph * 3;
+    float* part = dy + Ph * 3;
+    float* dbpart = part + (size_t)maxp * 9 * 4096;
+    float* zero = dbpart + (size_t)maxp * 64;   // zero biases of the input-gradient convs
+    double* lparts = (double*)(((uintptr_t)(zero + 64) + 7) & ~(uintptr_t)7);
+    double* lsum = lparts + kLossParts;
+
+    // tensor maps
+    auto amap = [&](CUtensorMap* m, const void* q, int hh, int ww) { return tc_make_act_map(m, q, N, hh, ww, TC_BF16, kABox); };
+    auto omap = [&](CUtensorMap* m, const void* q, int hh, int ww) { return tc_make_act_map(m, q, N, hh, ww, TC_BF16, kOutBox); };
+    auto xmap = [&](CUtensorMap* m, const void* q, int hh, int ww) { return tc_make_act_map(m, q, N, hh, ww, TC_BF16, kWgKB + 2); };
+    auto ymap = [&](CUtensorMap* m, const void* q, int hh, int ww) { return tc_make_act_map(m, q, N, hh, ww, TC_BF16, kWgKB); };
+    // sub-pixel (oy, ox) of every sub x sub block of a [N][HH][WW][64] tensor
+    auto view = [&](CUtensorMap* m, const __nv_bfloat16* base, int sub, int oy, int ox, int HH, int WW, int box) {
+        return tc_make_view_map(m, base + ((size_t)oy * WW + ox) * 64, N, HH / sub, WW / sub,
+                                (long long)sub * 128, (long long)sub * WW * 128, (long long)HH * WW * 128, box);
+    };
+    struct M4 { CUtensorMap a, o, x, y; };   // the four box kinds of one tensor
+    auto all4 = [&](M4& m, const void* q, int hh, int ww) {
+        mrs_status e = amap(&m.a, q, hh, ww);
+        if (e == MRS_OK) e = omap(&m.o, q, hh, ww);
+        if (e == MRS_OK) e = xmap(&m.x, q, hh, ww);
+        if (e == MRS_OK) e = ymap(&m.y, q, hh, ww);
+        return e;
+    };
+    M4 mInL, mInH, mFlr, mFh0, mX[kRDG * kRDB + 1], mF[kRDG * kRDB][4], mU[4], mDyb, mDU[2], mDp[4], mDz4,
+        mDzf, mDzlr, mDz1;
+    if (rc == MRS_OK) rc = all4(mInL, inL, h, w);
+    if (rc == MRS_OK) rc = all4(mInH, inH, H, W);
+    if (rc == MRS_OK) rc = all4(mFlr, Flr, h, w);
+    if (rc == MRS_OK) rc = all4(mFh0, Fh0, H, W);
+    for (int k = 0; k <= nblk && rc == MRS_OK; ++k) rc = all4(mX[k], X[k], h, w);
+    for (int k = 0; k < nblk; ++k)
+        for (int j = 0; j < 4 && rc == MRS_OK; ++j) rc = all4(mF[k][j], Fk[k][j], h, w);
+    for (int d = 0; d <= D && rc == MRS_OK; ++d) rc = all4(mU[d], U[d], hd[d], wd[d]);
+    if (rc == MRS_OK) rc = all4(mDyb, dyb, H, W);
+    for (int j = 0; j < 4 && rc == MRS_OK; ++j) rc = all4(mDp[j], dp[j], h, w);
+    if (rc == MRS_OK) rc = all4(mDz4, dz4, h, w);
+    if (rc == MRS_OK) rc = all4(mDzf, dzf, h, w);
+    if (rc == MRS_OK) rc = all4(mDzlr, dzlr, h, w);
+    if (rc == MRS_OK) rc = all4(mDz1, dz1, H, W);
+    if (rc != MRS_OK) return rc;
+    // the level-(d + 1) gradient of the upsampling path sits in dU[(D - 1 - d) & 1]
+    // ([P_{d+1}][64]); its plain maps per level, and the deshuffle views
+    std::vector<M4> mDUl(D + 1);
+    for (int d = 0; d <= D && rc == MRS_OK; ++d) rc = all4(mDUl[d], dU[(D - d) & 1], hd[d], wd[d]);
+    std::vector<CUtensorMap> dsfA(SS), dsfO(SS), dsfX(SS), dz1O(SS);
+    for (int q = 0; q < SS && rc == MRS_OK; ++q) {
+        const int oy = q / s, ox = q % s;
+        rc = view(&dsfA[q], Fh0, s, oy, ox, H, W, kABox);
+        if (rc == MRS_OK) rc = view(&dsfO[q], Fh0, s, oy, ox, H, W, kOutBox);
+        if (rc == MRS_OK) rc = view(&dsfX[q], Fh0, s, oy, ox, H, W, kWgKB + 2);
+        if (rc == MRS_OK) rc = view(&dz1O[q], dz1, s, oy, ox, H, W, kOutBox);
+    }
+    // upsampling stage d: output views of U[d + 1] (forward) and views of the
+    // level-(d + 1) gradient (A operands and weight-gradient dy)
+    std::vector<std::array<CUtensorMap, 4>> upO(D), dupA(D), dupY(D);
+    for (int d = 0; d < D && rc == MRS_OK; ++d)
+        for (int q = 0; q < 4 && rc == MRS_OK; ++q) {
+            const int dy_ = q >> 1, dx_ = q & 1;
+            const __nv_bfloat16* g = dU[(D - 1 - d) & 1];
+            rc = view(&upO[d][q], U[d + 1], 2, dy_, dx_, hd[d + 1], wd[d + 1], kOutBox);
+            if (rc == MRS_OK) rc = view(&dupA[d][q], g, 2, dy_, dx_, hd[d + 1], wd[d + 1], kABox);
+            if (rc == MRS_OK) rc = view(&dupY[d][q], g, 2, dy_, dx_, hd[d + 1], wd[d + 1], kWgKB);
+        }
+    if (rc != MRS_OK) return rc;
+    // multi-chunk A-operand arrays: the fuse conv's 17 inputs, each block's 4
+    // concatenation parts, each upsampling stage's 4 gradient views
+    std::vector<CUtensorMap> mc;
+    const size_t mc_fuse = mc.size();
+    mc.push_back(mFlr.a);
+    for (int q = 0; q < SS; ++q) mc.push_back(dsfA[q]);
+    std::vector<size_t> mc_blk(nblk), mc_up(D);
+    for (int k = 0; k < nblk; ++k) {
+        mc_blk[k] = mc.size();
+        mc.push_back(mX[k].a);
+        for (int j = 0; j < 3; ++j) mc.push_back(mF[k][j].a);
+    }
+    for (int d = 0; d < D; ++d) {
+        mc_up[d] = mc.size();
+        for (int q = 0; q < 4; ++q) mc.push_back(dupA[d][q]);
+    }
+    if ((rc = r->tdmaps.ensure(mc.size() * sizeof(CUtensorMap) + 64)) != MRS_OK) return rc;
+    const CUtensorMap* dmc = r->tdmaps.as<CUtensorMap>();
+    MRS_CHECK(cudaMemcpyAsync(r->tdmaps.p, mc.data(), mc.size() * sizeof(CUtensorMap),
+                              cudaMemcpyHostToDevice, st));
+
+    TcConvArgs a;
+    memset(&a, 0, sizeof(a));
+    a.N = N; a.scale = 1; a.operand = TC_BF16; a.err = r->err;
+    // one tensor-core conv: mc_off >= 0 = a kc-chunk launch over dmc[mc_off ..]
+    auto conv = [&](int hh, int ww, const CUtensorMap* A, long mc_off, int kc, const CUtensorMap* wm,
+                    int w_row0, const float* bias, int nout, int mode, const CUtensorMap* res,
+                    const CUtensorMap* out, float* outf = nullptr, int cout = 64) -> mrs_status {
+        a.H = hh; a.W = ww; a.tmap_x = A;
+        a.amaps = mc_off >= 0 ? dmc + mc_off : nullptr;
+        a.kc = mc_off >= 0 ? kc : 0;
+        a.tmap_w = wm; a.w_row0 = w_row0; a.bias = bias; a.nout = nout; a.mode = mode;
+        a.tmap_res = res; a.tmap_out = out; a.out = outf; a.cout = cout; a.relu = 0;
+        return tc_conv3x3(a, st);
+    };
+    const WChunk* CH = r->ch.data();
+    auto fmap = [&](int li, int j) { return &CH[r->first[li] + j].map; };       // single forward chunk
+    auto frow = [&](int li) { return (int)(CH[r->first[li]].off / 64); };       // a layer's chunks in wmap_all
+    auto fbias = [&](int li, int j) { return r->bch + (size_t)(r->first[li] + j) * 64; };
+    auto trow = [&](int li, int j) { return r->tfirst[li] + 9 * 64 * j; };      // transposed chunk j
+    MRS_CHECK(cudaMemsetAsync(zero, 0, 64 * sizeof(float), st));
+
+    // ---- forward
+    k_lr_input_bf16<<<grid_for(Pl), 256, 0, st>>>(lrhs, Pl, inL);
+    k_hr_input_bf16<<<grid_for(Ph), 256, 0, st>>>(hrls, alb, nrm, extra, Ph, inH);
+    MRS_LAUNCHED(2);
+    if ((rc = conv(h, w, &mInL.a, -1, 1, fmap(0, 0), 0, fbias(0, 0), 64, TC_RELU_BF16, nullptr, &mFlr.o)) != MRS_OK) return rc;
+    if ((rc = conv(H, W, &mInH.a, -1, 1, fmap(1, 0), 0, fbias(1, 0), 64, TC_RELU_BF16, nullptr, &mFh0.o)) != MRS_OK) return rc;
+    if ((rc = conv(h, w, &mFlr.a, (long)mc_fuse, 1 + SS, &r->wmap_all, frow(2), fbias(2, 0), 64, TC_RELU_BF16,
+                   nullptr, &mX[0].o)) != MRS_OK) return rc;
+    int li = 3;
+    for (int g = 0; g < kRDG; ++g) {
+        for (int b = 0; b < kRDB; ++b) {
+            const int k = kRDB * g + b;
+            for (int c = 1; c <= kConv; ++c, ++li) {
+                const CUtensorMap* out = &mF[k][c - 1].o;        // F_1, F_2, F_3, ReLU(local fusion)
+                rc = c == 1 ? conv(h, w, &mX[k].a, -1, 1, fmap(li, 0), 0, fbias(li, 0), 64, TC_RELU_BF16, nullptr, out)
+                            : conv(h, w, &mX[k].a, (long)mc_blk[k], c, &r->wmap_all, frow(li), fbias(li, 0), 64,
+                                   TC_RELU_BF16, nullptr, out);
+                if (rc != MRS_OK) return rc;
+            }
+            // block output; + F_{g-1} after a group's last block; + F_0 at the end (Eq. F_DF)
+            const bool last = b == kRDB - 1;
+            k_sum_bf16<<<grid_for(Pl * 64), 256, 0, st>>>(X[k + 1], X[k], Fk[k][3], last ? X[kRDB * g] : nullptr,
+                                                          k + 1 == nblk ? F0 : nullptr, nullptr, Pl * 64);
+            MRS_LAUNCHED(1);
+        }
+    }
+    for (int d = 0; d < D; ++d, ++li)
+        for (int q = 0; q < 4; ++q)
+            if ((rc = conv(hd[d], wd[d], &mU[d].a, -1, 1, fmap(li, q), 0, fbias(li, q), 64, TC_RELU_BF16,
+                           nullptr, &upO[d][q])) != MRS_OK) return rc;
+    const int li_rec = li;
+    if ((rc = conv(H, W, &mU[D].a, -1, 1, fmap(li_rec, 0), 0, fbias(li_rec, 0), CH[r->first[li_rec]].nout,
+                   TC_PLAIN_F32, nullptr, nullptr, y, 3)) != MRS_OK) return rc;
+    if (yout) MRS_CHECK(cudaMemcpyAsync(yout, y, Ph * 3 * 4, cudaMemcpyDeviceToDevice, st));
+
+    // ---- loss and dL/dI_SR
+    if ((rc = loss_grad_f32(y, tgt, Ph * 3, kTrainClip, kind, beta, dy, lparts, lsum, st)) != MRS_OK) return rc;
+    k_f32_to_bf16_rows<<<grid_for(Ph * 64), 256, 0, st>>>(dy, Ph, 3, dyb);
+    MRS_LAUNCHED(1);
+
+    // ---- backward
+    // weight gradient of one 64 x 64 tile (see k_wg_reduce for the mappings)
+    auto wgrad = [&](int hh, int ww, const CUtensorMap* xm, const CUtensorMap* ym, int cin_t, int cout_t,
+                     int lidx, int o_mul, int o_add, int c0, int q, bool with_bias) -> mrs_status {
+        TcWgradArgs wa;
+        wa.tmap_x = xm; wa.tmap_dy = ym; wa.part = part; wa.dbpart = dbpart;
+        wa.N = N; wa.H = hh; wa.W = ww; wa.cin = cin_t; wa.cout = cout_t; wa.err = r->err;
+        int np = 0;
+        mrs_status e = tc_conv3x3_wgrad(wa, &np, st);
+        if (e != MRS_OK) return e;
+        const RLayer& l = r->L[lidx];
+        const int KK = l.k * l.k;
+        const size_t n = (size_t)cout_t * KK * cin_t + cout_t;
+        k_wg_reduce<<<grid_for(n), 256, 0, st>>>(part, dbpart, np, cin_t, cout_t, KK, l.cin, o_mul, o_add, c0,
+                                                 q, s, D, with_bias ? 1 : 0, r->grad + l.woff,
+                                                 r->grad + l.boff);
+        MRS_LAUNCHED(1);
+        return cuda_status(cudaGetLastError(), "rdn wgrad");
+    };
+    auto mask = [&](const __nv_bfloat16* d, const __nv_bfloat16* act, size_t P, __nv_bfloat16* out) {
+        k_mask_copy_bf16<<<grid_for(P * 64), 256, 0, st>>>(d, act, P * 64, out);
+        MRS_LAUNCHED(1);
+    };
+    const CUtensorMap* WT = &r->wmapT_all;
+    // H_Rec
+    if ((rc = wgrad(H, W, &mU[D].x, &mDyb.y, 64, 3, li_rec, 1, 0, 0, 0, true)) != MRS_OK) return rc;
+    if ((rc = conv(H, W, &mDyb.a, -1, 1, WT, trow(li_rec, 0), zero, 64, TC_LIN_BF16, nullptr, &mDUl[D].o)) != MRS_OK)
+        return rc;
+    // upsampling stages in reverse: the level-(d + 1) gradient masked by U[d + 1] > 0
+    for (int d = D - 1; d >= 0; --d) {
+        const int lu = 3 + kConv * nblk + d;
+        __nv_bfloat16* gd = dU[(D - 1 - d) & 1];
+        mask(gd, U[d + 1], Pd[d + 1], gd);
+        for (int q = 0; q < 4; ++q)
+            if ((rc = wgrad(hd[d], wd[d], &mU[d].x, &dupY[d][q], 64, 64, lu, 4, q, 0, 0, true)) != MRS_OK) return rc;
+        if ((rc = conv(hd[d], wd[d], &dupA[d][0], (long)mc_up[d], 4, WT, trow(lu, 0), zero, 64, TC_LIN_BF16,
+                       nullptr, &mDUl[d].o)) != MRS_OK) return rc;
+    }
+    __nv_bfloat16* gdf = dU[D & 1];               // dL/dF_DF: to F_G (the chain) and to F_0
+    MRS_CHECK(cudaMemcpyAsync(G, gdf, Pl * 128, cudaMemcpyDeviceToDevice, st));
+    for (int g = kRDG - 1; g >= 0; --g) {
+        MRS_CHECK(cudaMemcpyAsync(dSkip, G, Pl * 128, cudaMemcpyDeviceToDevice, st));
+        for (int b = kRDB - 1; b >= 0; --b) {
+            const int k = kRDB * g + b, lb = 3 + kConv * k;
+            // local fusion: dz4 = G masked by its ReLU output; one weight tile per
+            // concatenation part; part 0's gradient = G + conv^T, parts 1..3 start here
+            mask(G, Fk[k][3], Pl, dz4);
+            for (int j = 0; j < 4; ++j)
+                if ((rc = wgrad(h, w, j ? &mF[k][j - 1].x : &mX[k].x, &mDz4.y, 64, 64, lb + 3, 1, 0, 64 * j, 0,
+                                j == 0)) != MRS_OK) return rc;
+            if ((rc = conv(h, w, &mDz4.a, -1, 1, WT, trow(lb + 3, 0), zero, 64, TC_RESID_BF16, &mDp[0].o,
+                           &mDp[0].o)) != MRS_OK) return rc;
+            for (int j = 1; j < 4; ++j)
+                if ((rc = conv(h, w, &mDz4.a, -1, 1, WT, trow(lb + 3, j), zero, 64, TC_LIN_BF16, nullptr,
+                               &mDp[j].o)) != MRS_OK) return rc;
+            // dense convs 3, 2, 1: the gradient of F_c is complete once the later
+            // convs have added theirs; masked by F_c, then its weight tiles and
+            // its input gradients added into parts 0 .. c - 1
+            for (int c = kConv - 1; c >= 1; --c) {
+                const int lc = lb + c - 1;
+                mask(dp[c], Fk[k][c - 1], Pl, dp[c]);
+                for (int j = 0; j < c; ++j)
+                    if ((rc = wgrad(h, w, j ? &mF[k][j - 1].x : &mX[k].x, &mDp[c].y, 64, 64, lc, 1, 0, 64 * j, 0,
+                                    j == 0)) != MRS_OK) return rc;
+                for (int j = 0; j < c; ++j)
+                    if ((rc = conv(h, w, &mDp[c].a, -1, 1, WT, trow(lc, j), zero, 64, TC_RESID_BF16, &mDp[j].o,
+                                   &mDp[j].o)) != MRS_OK) return rc;
+            }
+        }
+        // F_g = chain(F_{g-1}) + F_{g-1}
+        k_sum_bf16<<<grid_for(Pl * 64), 256, 0, st>>>(G, G, dSkip, nullptr, nullptr, nullptr, Pl * 64);
+        MRS_LAUNCHED(1);
+    }
+    // fuse: dz = (dL/dF_DF + the chain's gradient) masked by F_0
+    k_sum_bf16<<<grid_for(Pl * 64), 256, 0, st>>>(dzf, gdf, G, nullptr, nullptr, F0, Pl * 64);
+    MRS_LAUNCHED(1);
+    for (int q = 0; q <= SS; ++q)
+        if ((rc = wgrad(h, w, q ? &dsfX[q - 1] : &mFlr.x, &mDzf.y, 64, 64, 2, 1, 0, 0, q, q == 0)) != MRS_OK)
+            return rc;
+    // its input gradients, masked by the encoders' ReLU outputs: chunk 0 into
+    // F_LRHS's gradient, chunk q into deshuffle view q of F0_HRLS's
+    if ((rc = conv(h, w, &mDzf.a, -1, 1, WT, trow(2, 0), zero, 64, TC_MASK_BF16, &mFlr.o, &mDzlr.o)) != MRS_OK)
+        return rc;
+    for (int q = 1; q <= SS; ++q)
+        if ((rc = conv(h, w, &mDzf.a, -1, 1, WT, trow(2, q), zero, 64, TC_MASK_BF16, &dsfO[q - 1],
+                       &dz1O[q - 1])) != MRS_OK) return rc;
+    // encoders
+    if ((rc = wgrad(h, w, &mInL.x, &mDzlr.y, 3, 64, 0, 1, 0, 0, 0, true)) != MRS_OK) return rc;
+    if ((rc = wgrad(H, W, &mInH.x, &mDz1.y, r->c_hr, 64, 1, 1, 0, 0, 0, true)) != MRS_OK) return rc;
+
+    // ---- Adam on the FP32 weights
+    r->step += 1;
+    if ((rc = adam_f32(r->master, r->grad, r->adam_m, r->adam_v, r->np, lr, r->step, st)) != MRS_OK) return rc;
+    r->bf_stale = true;
+    if (loss_out) {
+        double hsum = 0;
+        int herr = 0;
+        MRS_CHECK(cudaMemcpyAsync(&hsum, lsum, sizeof(double), cudaMemcpyDeviceToHost, st));
+        MRS_CHECK(cudaMemcpyAsync(&herr, r->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        MRS_CHECK(cudaStreamSynchronize(st));
+        if (herr) {
+            cudaMemset(r->err, 0, 4);
+            set_error("tensor-core wait timed out in the training step");
+            return MRS_ERR_TIMEOUT;
+        }
+        *loss_out = hsum / (double)(Ph * 3);
+    }
+    return cuda_status(cudaGetLastError(), "rdn train step bf16");
 }
 
 }  // namespace
@@ -1013,12 +1518,14 @@ extern "C" mrs_status mrs_rdn_free(mrs_rdn r)
 {
     if (!r) return MRS_OK;
     cudaDeviceSynchronize();
-    void* ptrs[] = {r->master, r->w_fuse3, r->wbf, r->bch, r->err, r->grad, r->adam_m, r->adam_v};
+    void* ptrs[] = {r->master, r->w_fuse3, r->wbf, r->bch, r->err, r->grad, r->adam_m, r->adam_v,
+                    r->d_widx, r->d_bidx, r->d_tidx, r->wbfT};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     r->f32.release();
     r->bf.release();
     r->tr.release();
+    r->trb.release();
     r->dmaps.release();
     delete r;
     return MRS_OK;
@@ -1091,9 +1598,13 @@ extern "C" mrs_status mrs_rdn_train_step(mrs_rdn r, const float* lrhs, const flo
     MRS_ARG(loss == MRS_LOSS_L1LOG || loss == MRS_LOSS_ROBUST, "loss must be MRS_LOSS_L1LOG or MRS_LOSS_ROBUST");
     MRS_ARG(loss != MRS_LOSS_ROBUST || beta > 0.0f, "beta must be > 0");
     MRS_ARG(lr >= 0.0f, "lr must be >= 0");
-    MRS_ARG(precision == MRS_PREC_FP32, "precision must be MRS_PREC_FP32");
+    MRS_ARG(precision == MRS_PREC_FP32 || precision == MRS_PREC_BF16,
+            "precision must be MRS_PREC_FP32 or MRS_PREC_BF16");
     mrs_status rc = ensure_train_state(r);
     if (rc != MRS_OK) return rc;
+    if (precision == MRS_PREC_BF16)
+        return rdn_train_bf16(r, lrhs, hrls, albedo, normal, extra, target, N, H, W, loss, beta, lr, out,
+                              loss_out, (cudaStream_t)stream);
     return rdn_train_f32(r, lrhs, hrls, albedo, normal, extra, target, N, H, W, loss, beta, lr, out,
                          loss_out, (cudaStream_t)stream);
 }
