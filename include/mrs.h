@@ -692,7 +692,11 @@ mrs_status mrs_rdn_check(mrs_rdn rdn);
  * zero); the workspace (FP32: about 20 KB per LR pixel plus 1.3 KB per HR
  * pixel; BF16: about 11 KB per LR pixel plus 0.8 KB per HR pixel) lives in
  * the handle.  A later MRS_PREC_BF16 mrs_rdn_fuse repacks its BF16 weights
- * from the updated FP32 ones.  Limit: N*H*W <= 2^24. */
+ * from the updated FP32 ones.  A BF16 step copies the batch into the
+ * handle's staging buffers; the first step of a shape (N, H, W, loss, beta)
+ * runs its launches directly and records them as a CUDA graph that later
+ * steps of that shape replay (bit-identical; not while mrs_profile_enable is
+ * on).  Limit: N*H*W <= 2^24. */
 mrs_status mrs_rdn_train_step(mrs_rdn rdn, const float* lrhs, const float* hrls,
                               const float* albedo, const float* normal, const float* extra,
                               const float* target, int32_t N, int32_t H, int32_t W, int32_t loss,

@@ -446,6 +446,17 @@ struct WChunk {
     CUtensorMap map;
 };
 
+// what a recorded BF16 training step depends on besides the handle's weights
+struct TrainKey {
+    int N = -1, H = -1, W = -1, kind = -1;
+    float beta = 0.0f;
+    void* buf = nullptr;
+    bool operator==(const TrainKey& o) const
+    {
+        return N == o.N && H == o.H && W == o.W && kind == o.kind && beta == o.beta && buf == o.buf;
+    }
+};
+
 }  // namespace
 }  // namespace mrs
 
@@ -471,6 +482,10 @@ struct mrs_rdn_s {
     __nv_bfloat16* wbfT = nullptr;
     CUtensorMap wmapT_all;
     Buf trb;                       // BF16 training workspace
+    cudaGraphExec_t tgraph = nullptr;   // its launches for one shape (see rdn_train_bf16)
+    mrs::TrainKey tkey;
+    uint64_t tgraph_kernels = 0;
+    cudaStream_t tcap = nullptr;        // stream they are recorded on
     Buf tdmaps;                    // its multi-chunk A-operand maps on the device
     CUtensorMap wmap_all;          // every chunk's weights as one [rows][64] tensor
     std::vector<CUtensorMap> hmaps;  // A-operand maps of the multi-chunk convs of a call
@@ -1207,14 +1222,10 @@ mrs_status rdn_train_bf16(mrs_rdn_s* r, const float* lrhs, const float* hrls, co
         if ((rc = tc_make_w_map(&r->wmapT_all, r->wbfT, (int)(r->tidx.size() / 64), 64, TC_BF16)) != MRS_OK)
             return rc;
     }
-    if ((rc = repack_bf16(r, st)) != MRS_OK) return rc;
-    k_gather_bf16<<<grid_for(r->tidx.size()), 256, 0, st>>>(r->master, r->d_tidx, r->tidx.size(), r->wbfT);
-    MRS_LAUNCHED(1);
-
     // workspace: BF16 [P][64] tensors, then FP32
     const size_t rows = Pl * (3 + 15 + 4 * nblk + 10) + Ph * 6 + nUrows;
     const int maxp = tc_wgrad_max_parts();
-    const size_t nf = Ph * 6 + (size_t)maxp * 9 * 4096 + (size_t)maxp * 64 + 64;
+    const size_t nf = Ph * 6 + (size_t)maxp * 9 * 4096 + (size_t)maxp * 64 + 64 + Pl * 3 + Ph * 21;
     if ((rc = r->trb.ensure(rows * 128 + nf * 4 + (kLossParts + 2) * 8 + 4096)) != MRS_OK) return rc;
     __nv_bfloat16* bp = r->trb.as<__nv_bfloat16>();
     auto take = [&](size_t P) { __nv_bfloat16* q = bp; bp += P * 64; return q; };
@@ -1248,8 +1259,34 @@ mrs_status rdn_train_bf16(mrs_rdn_s* r, const float* lrhs, const float* hrls, co
     float* part = dy + Ph * 3;
     float* dbpart = part + (size_t)maxp * 9 * 4096;
     float* zero = dbpart + (size_t)maxp * 64;   // zero biases of the input-gradient convs
-    double* lparts = (double*)(((uintptr_t)(zero + 64) + 7) & ~(uintptr_t)7);
+    // staging: the caller's batch, copied here every step (the recorded launches read these)
+    float* sLr = zero + 64;
+    float* sHr = sLr + Pl * 3;
+    float* sAlb = sHr + Ph * 3;
+    float* sNrm = sAlb + Ph * 3;
+    float* sEx = sNrm + Ph * 3;
+    float* sTgt = sEx + Ph * 9;
+    double* lparts = (double*)(((uintptr_t)(sTgt + Ph * 3) + 7) & ~(uintptr_t)7);
     double* lsum = lparts + kLossParts;
+    MRS_CHECK(cudaMemcpyAsync(sLr, lrhs, Pl * 3 * 4, cudaMemcpyDeviceToDevice, st));
+    MRS_CHECK(cudaMemcpyAsync(sHr, hrls, Ph * 3 * 4, cudaMemcpyDeviceToDevice, st));
+    MRS_CHECK(cudaMemcpyAsync(sAlb, alb, Ph * 3 * 4, cudaMemcpyDeviceToDevice, st));
+    MRS_CHECK(cudaMemcpyAsync(sNrm, nrm, Ph * 3 * 4, cudaMemcpyDeviceToDevice, st));
+    if (extra) MRS_CHECK(cudaMemcpyAsync(sEx, extra, Ph * 9 * 4, cudaMemcpyDeviceToDevice, st));
+    MRS_CHECK(cudaMemcpyAsync(sTgt, tgt, Ph * 3 * 4, cudaMemcpyDeviceToDevice, st));
+
+    // The launches of a step depend only on the shapes, the loss and the
+    // workspace: the first step of a shape runs them directly and records
+    // them as a CUDA graph (on a private stream), later steps replay it.
+    // (with per-launch event timing on, steps run directly and nothing is
+    // recorded: the timing events must be real ones)
+    const TrainKey key{N, H, W, kind, beta, r->trb.p};
+    const bool timing = prof_on();
+    if (r->tgraph && key == r->tkey && !timing) {
+        MRS_CHECK(cudaGraphLaunch(r->tgraph, st));
+        launch_counter() += r->tgraph_kernels;
+    } else {
+    if (r->tgraph) { cudaGraphExecDestroy(r->tgraph); r->tgraph = nullptr; }
 
     // tensor maps
     auto amap = [&](CUtensorMap* m, const void* q, int hh, int ww) { return tc_make_act_map(m, q, N, hh, ww, TC_BF16, kABox); };
@@ -1331,6 +1368,11 @@ mrs_status rdn_train_bf16(mrs_rdn_s* r, const float* lrhs, const float* hrls, co
     MRS_CHECK(cudaMemcpyAsync(r->tdmaps.p, mc.data(), mc.size() * sizeof(CUtensorMap),
                               cudaMemcpyHostToDevice, st));
 
+    auto body = [&](cudaStream_t st) -> mrs_status {
+    mrs_status rc = repack_bf16(r, st);
+    if (rc != MRS_OK) return rc;
+    k_gather_bf16<<<grid_for(r->tidx.size()), 256, 0, st>>>(r->master, r->d_tidx, r->tidx.size(), r->wbfT);
+    MRS_LAUNCHED(1);
     TcConvArgs a;
     memset(&a, 0, sizeof(a));
     a.N = N; a.scale = 1; a.operand = TC_BF16; a.err = r->err;
@@ -1353,8 +1395,8 @@ mrs_status rdn_train_bf16(mrs_rdn_s* r, const float* lrhs, const float* hrls, co
     MRS_CHECK(cudaMemsetAsync(zero, 0, 64 * sizeof(float), st));
 
     // ---- forward
-    k_lr_input_bf16<<<grid_for(Pl), 256, 0, st>>>(lrhs, Pl, inL);
-    k_hr_input_bf16<<<grid_for(Ph), 256, 0, st>>>(hrls, alb, nrm, extra, Ph, inH);
+    k_lr_input_bf16<<<grid_for(Pl), 256, 0, st>>>(sLr, Pl, inL);
+    k_hr_input_bf16<<<grid_for(Ph), 256, 0, st>>>(sHr, sAlb, sNrm, extra ? sEx : nullptr, Ph, inH);
     MRS_LAUNCHED(2);
     if ((rc = conv(h, w, &mInL.a, -1, 1, fmap(0, 0), 0, fbias(0, 0), 64, TC_RELU_BF16, nullptr, &mFlr.o)) != MRS_OK) return rc;
     if ((rc = conv(H, W, &mInH.a, -1, 1, fmap(1, 0), 0, fbias(1, 0), 64, TC_RELU_BF16, nullptr, &mFh0.o)) != MRS_OK) return rc;
@@ -1385,10 +1427,9 @@ mrs_status rdn_train_bf16(mrs_rdn_s* r, const float* lrhs, const float* hrls, co
     const int li_rec = li;
     if ((rc = conv(H, W, &mU[D].a, -1, 1, fmap(li_rec, 0), 0, fbias(li_rec, 0), CH[r->first[li_rec]].nout,
                    TC_PLAIN_F32, nullptr, nullptr, y, 3)) != MRS_OK) return rc;
-    if (yout) MRS_CHECK(cudaMemcpyAsync(yout, y, Ph * 3 * 4, cudaMemcpyDeviceToDevice, st));
 
     // ---- loss and dL/dI_SR
-    if ((rc = loss_grad_f32(y, tgt, Ph * 3, kTrainClip, kind, beta, dy, lparts, lsum, st)) != MRS_OK) return rc;
+    if ((rc = loss_grad_f32(y, sTgt, Ph * 3, kTrainClip, kind, beta, dy, lparts, lsum, st)) != MRS_OK) return rc;
     k_f32_to_bf16_rows<<<grid_for(Ph * 64), 256, 0, st>>>(dy, Ph, 3, dyb);
     MRS_LAUNCHED(1);
 
@@ -1482,6 +1523,33 @@ mrs_status rdn_train_bf16(mrs_rdn_s* r, const float* lrhs, const float* hrls, co
     if ((rc = wgrad(h, w, &mInL.x, &mDzlr.y, 3, 64, 0, 1, 0, 0, 0, true)) != MRS_OK) return rc;
     if ((rc = wgrad(H, W, &mInH.x, &mDz1.y, r->c_hr, 64, 1, 1, 0, 0, 0, true)) != MRS_OK) return rc;
 
+    return MRS_OK;
+    };
+    // this step, directly
+    if ((rc = body(st)) != MRS_OK) return rc;
+    // recorded for the next steps of this shape
+    if (!timing) {
+    if (!r->tcap) MRS_CHECK(cudaStreamCreateWithFlags(&r->tcap, cudaStreamNonBlocking));
+    const uint64_t before = launch_counter().load();
+    MRS_CHECK(cudaStreamBeginCapture(r->tcap, cudaStreamCaptureModeThreadLocal));
+    mrs_status cr = body(r->tcap);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(r->tcap, &g);
+    const uint64_t recorded = launch_counter().load() - before;
+    launch_counter() -= recorded;              // recorded, not run
+    if (cr == MRS_OK && e == cudaSuccess) e = cudaGraphInstantiate(&r->tgraph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (cr != MRS_OK || e != cudaSuccess) {
+        r->tgraph = nullptr;
+        cudaGetLastError();
+    } else {
+        r->tkey = key;
+        r->tgraph_kernels = recorded;
+    }
+    }
+    }
+    if (yout) MRS_CHECK(cudaMemcpyAsync(yout, y, Ph * 3 * 4, cudaMemcpyDeviceToDevice, st));
+
     // ---- Adam on the FP32 weights
     r->step += 1;
     if ((rc = adam_f32(r->master, r->grad, r->adam_m, r->adam_v, r->np, lr, r->step, st)) != MRS_OK) return rc;
@@ -1522,6 +1590,8 @@ extern "C" mrs_status mrs_rdn_free(mrs_rdn r)
                     r->d_widx, r->d_bidx, r->d_tidx, r->wbfT};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    if (r->tgraph) cudaGraphExecDestroy(r->tgraph);
+    if (r->tcap) cudaStreamDestroy(r->tcap);
     r->f32.release();
     r->bf.release();
     r->tr.release();

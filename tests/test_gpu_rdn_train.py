@@ -265,3 +265,26 @@ def test_rdn_bf16_training_reduces_loss(mrs):
     # the BF16 weights used by inference follow the trained FP32 weights
     c = mrs.RDN(net.get_params(), 4)
     assert torch.equal(net.fuse(*dev[:4], precision="bf16"), c.fuse(*dev[:4], precision="bf16"))
+
+
+def test_rdn_bf16_recorded_steps_equal_direct_steps(mrs):
+    # the first BF16 step of a shape runs its launches directly and records
+    # them; later steps replay the recording on the staged batch.  Three steps
+    # on one handle (two replayed, each on a different batch) equal three
+    # steps that are each the first of a fresh handle, bit for bit
+    batches = [_cuda(*_batch(40 + i, 2, 6, 6, 4)[:4], _batch(40 + i, 2, 6, 6, 4)[5]) for i in range(3)]
+    p = _params(4, 4)
+    a = mrs.RDN(p, 4)
+    la = [a.train_step(*b, lr=1e-3, loss="robust", precision="bf16") for b in batches]
+    st = {"params": p, "adam_m": np.zeros_like(p), "adam_v": np.zeros_like(p), "step": 0}
+    lb = []
+    for b in batches:
+        c = mrs.RDN(st["params"], 4)
+        c.set_state(st)
+        lb.append(c.train_step(*b, lr=1e-3, loss="robust", precision="bf16"))
+        st = c.get_state()
+        c.close()
+    assert la == lb
+    sa = a.get_state()
+    for k in ("params", "adam_m", "adam_v"):
+        assert np.array_equal(sa[k], st[k]), k
