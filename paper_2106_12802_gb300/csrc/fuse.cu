@@ -524,21 +524,38 @@ __global__ void __launch_bounds__(256)
 }
 
 // grad[o][t][c] (params layout) = sum_g part[g][t][o][c]; grad_b[o] = sum_g dbpart[g][o]
-__global__ void k_dw_reduce(const float* __restrict__ part, const float* __restrict__ dbpart,
-                            int G, int cin, int cout, float* __restrict__ gw, float* __restrict__ gb)
+// A block takes 32 consecutive values; warp w sums partials w, w + 8, ... (one
+// coalesced 128-byte row per partial) and the eight sums are added in warp
+// order: a fixed order, so the result is deterministic.
+__global__ void __launch_bounds__(256) k_dw_reduce(const float* __restrict__ part,
+                                                   const float* __restrict__ dbpart, int G, int cin,
+                                                   int cout, float* __restrict__ gw,
+                                                   float* __restrict__ gb)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    int nw = cout * 9 * cin;
-    if (i < nw) {
-        int c = i % cin, t = (i / cin) % 9, o = i / (cin * 9);
+    __shared__ float red[8][32];
+    const int nw = cout * 9 * cin, ntot = nw + cout;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const size_t gstride = (size_t)9 * cout * cin;
+    for (int e0 = blockIdx.x * 32; e0 < ntot; e0 += gridDim.x * 32) {
+        const int e = e0 + lane;
         float acc = 0.0f;
-        for (int g = 0; g < G; ++g) acc += part[(((size_t)g * 9 + t) * cout + o) * cin + c];
-        gw[i] = acc;
-    } else if (i < nw + cout) {
-        int o = i - nw;
-        float acc = 0.0f;
-        for (int g = 0; g < G; ++g) acc += dbpart[(size_t)g * cout + o];
-        gb[o] = acc;
+        if (e < nw) {
+            const int c = e % cin, t = (e / cin) % 9, o = e / (cin * 9);
+            const float* src = part + ((size_t)t * cout + o) * cin + c;
+            for (int g = wp; g < G; g += 8) acc += src[(size_t)g * gstride];
+        } else if (e < ntot) {
+            const int o = e - nw;
+            for (int g = wp; g < G; g += 8) acc += dbpart[(size_t)g * cout + o];
+        }
+        red[wp][lane] = acc;
+        __syncthreads();
+        if (wp == 0 && e < ntot) {
+            float v = red[0][lane];
+            for (int k = 1; k < 8; ++k) v += red[k][lane];
+            if (e < nw) gw[e] = v;
+            else gb[e - nw] = v;
+        }
+        __syncthreads();
     }
 }
 
@@ -1273,7 +1290,7 @@ mrs_status layer_dw(mrs_net_s* net, int l, const float* x, const float* dy, int 
     MRS_TIMED(PK_TRAIN, st, (k_dw_partial<float, float><<<grid, 256, 0, st>>>(x, L.cin, L.cin, dy, L.cout, L.cout, N, H, W, part, dbpart, 0, 1)));
     MRS_LAUNCHED(1);
     int nw = L.cout * 9 * L.cin + L.cout;
-    MRS_TIMED(PK_TRAIN, st, k_dw_reduce<<<(nw + 255) / 256, 256, 0, st>>>(part, dbpart, kDwSplits, L.cin, L.cout,
+    MRS_TIMED(PK_TRAIN, st, k_dw_reduce<<<(nw + 31) / 32, 256, 0, st>>>(part, dbpart, kDwSplits, L.cin, L.cout,
                                                          net->grad + L.woff, net->grad + L.boff));
     MRS_LAUNCHED(1);
     return cuda_status(cudaGetLastError(), "dw");
@@ -1513,7 +1530,7 @@ mrs_status train_step_bf16(mrs_net_s* net, const float* lrhs, const float* hrls,
         mrs_status r = tc_conv3x3_wgrad(wa, &np, st);
         if (r != MRS_OK) return r;
         int nw = S_.cout * 9 * S_.cin + S_.cout;
-        MRS_TIMED(PK_TRAIN, st, k_dw_reduce<<<(nw + 255) / 256, 256, 0, st>>>(part, dbpart, np, S_.cin, S_.cout,
+        MRS_TIMED(PK_TRAIN, st, k_dw_reduce<<<(nw + 31) / 32, 256, 0, st>>>(part, dbpart, np, S_.cin, S_.cout,
                                                        net->grad + S_.woff, net->grad + S_.boff));
         MRS_LAUNCHED(1);
         return cuda_status(cudaGetLastError(), "dw");
@@ -1856,7 +1873,7 @@ extern "C" mrs_status mrs_conv3x3_wgrad(const float* x, const float* dy, int32_t
         wa.N = N; wa.H = H; wa.W = W; wa.cin = cin; wa.cout = cout; wa.err = err;
         if ((rc = tc_conv3x3_wgrad(wa, &np, st)) != MRS_OK) return rc;
     }
-    k_dw_reduce<<<(int)((nw + cout + 255) / 256), 256, 0, st>>>(part, dbpart, np, cin, cout, gw, gb);
+    k_dw_reduce<<<(int)((nw + cout + 31) / 32), 256, 0, st>>>(part, dbpart, np, cin, cout, gw, gb);
     MRS_LAUNCHED(1);
     MRS_CHECK(cudaMemcpyAsync(dw, gw, nw * 4, cudaMemcpyDeviceToHost, st));
     MRS_CHECK(cudaMemcpyAsync(db, gb, cout * 4, cudaMemcpyDeviceToHost, st));

@@ -406,31 +406,49 @@ __global__ void k_f32_to_bf16_rows(const float* __restrict__ x, size_t P, int ci
 }
 
 // One tensor-core weight-gradient tile (part [G][9][cout_t][cin_t], dbpart
-// [G][cout_t]) summed over its G partials in order into a layer's gradient
+// [G][cout_t]) summed over its G partials into a layer's gradient
 // [cout][KK][cin] (KK = 9, or 1 for a 1x1 layer: tap 4 of the tile):
 // tile output o' is layer output o_mul o' + o_add, tile input c' is layer input
 // c0 + c', or, for chunk q >= 1 of the fuse conv, 64 + dsf_channel(c', oy, ox, D)
-// with q - 1 = oy s + ox.  The bias is written when with_bias.
-__global__ void k_wg_reduce(const float* __restrict__ part, const float* __restrict__ dbpart, int G,
-                            int cin_t, int cout_t, int KK, int CIN, int o_mul, int o_add, int c0,
-                            int q, int s, int D, int with_bias, float* __restrict__ gw,
-                            float* __restrict__ gb)
+// with q - 1 = oy s + ox.  The bias is written when with_bias.  A block takes
+// 32 consecutive values; warp w sums partials w, w + 8, ... (one coalesced
+// 128-byte row per partial), the eight sums are added in warp order: a fixed
+// order, so the result is deterministic.
+__global__ void __launch_bounds__(256) k_wg_reduce(const float* __restrict__ part,
+                                                   const float* __restrict__ dbpart, int G, int cin_t,
+                                                   int cout_t, int KK, int CIN, int o_mul, int o_add,
+                                                   int c0, int q, int s, int D, int with_bias,
+                                                   float* __restrict__ gw, float* __restrict__ gb)
 {
-    const size_t nw = (size_t)cout_t * KK * cin_t;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nw + cout_t;
-         i += (size_t)gridDim.x * blockDim.x) {
+    __shared__ float red[8][32];
+    const size_t nw = (size_t)cout_t * KK * cin_t, ntot = nw + (with_bias ? cout_t : 0);
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const size_t gstride = (size_t)9 * cout_t * cin_t;
+    for (size_t e0 = (size_t)blockIdx.x * 32; e0 < ntot; e0 += (size_t)gridDim.x * 32) {
+        const size_t e = e0 + lane;
         float acc = 0.0f;
-        if (i < nw) {
-            const int c = (int)(i % cin_t), tl = (int)((i / cin_t) % KK), o = (int)(i / ((size_t)cin_t * KK));
-            const int t = KK == 9 ? tl : 4;
-            for (int g = 0; g < G; ++g) acc += part[(((size_t)g * 9 + t) * cout_t + o) * cin_t + c];
-            const int ci = q > 0 ? 64 + dsf_channel(c, (q - 1) / s, (q - 1) % s, D) : c0 + c;
-            gw[((size_t)(o_mul * o + o_add) * KK + tl) * CIN + ci] = acc;
-        } else if (with_bias) {
-            const int o = (int)(i - nw);
-            for (int g = 0; g < G; ++g) acc += dbpart[(size_t)g * cout_t + o];
-            gb[o_mul * o + o_add] = acc;
+        if (e < nw) {
+            const int c = (int)(e % cin_t), tl = (int)((e / cin_t) % KK), o = (int)(e / ((size_t)cin_t * KK));
+            const float* src = part + ((size_t)(KK == 9 ? tl : 4) * cout_t + o) * cin_t + c;
+            for (int g = wp; g < G; g += 8) acc += src[(size_t)g * gstride];
+        } else if (e < ntot) {
+            const int o = (int)(e - nw);
+            for (int g = wp; g < G; g += 8) acc += dbpart[(size_t)g * cout_t + o];
         }
+        red[wp][lane] = acc;
+        __syncthreads();
+        if (wp == 0 && e < ntot) {
+            float v = red[0][lane];
+            for (int k = 1; k < 8; ++k) v += red[k][lane];
+            if (e < nw) {
+                const int c = (int)(e % cin_t), tl = (int)((e / cin_t) % KK), o = (int)(e / ((size_t)cin_t * KK));
+                const int ci = q > 0 ? 64 + dsf_channel(c, (q - 1) / s, (q - 1) % s, D) : c0 + c;
+                gw[((size_t)(o_mul * o + o_add) * KK + tl) * CIN + ci] = v;
+            } else {
+                gb[o_mul * (int)(e - nw) + o_add] = v;
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -1446,7 +1464,7 @@ mrs_status rdn_train_bf16(mrs_rdn_s* r, const float* lrhs, const float* hrls, co
         const RLayer& l = r->L[lidx];
         const int KK = l.k * l.k;
         const size_t n = (size_t)cout_t * KK * cin_t + cout_t;
-        k_wg_reduce<<<grid_for(n), 256, 0, st>>>(part, dbpart, np, cin_t, cout_t, KK, l.cin, o_mul, o_add, c0,
+        k_wg_reduce<<<(int)((n + 31) / 32), 256, 0, st>>>(part, dbpart, np, cin_t, cout_t, KK, l.cin, o_mul, o_add, c0,
                                                  q, s, D, with_bias ? 1 : 0, r->grad + l.woff,
                                                  r->grad + l.boff);
         MRS_LAUNCHED(1);

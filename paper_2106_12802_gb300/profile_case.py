@@ -7,6 +7,8 @@ profiles/ runs one of these cases.
   python -m paper_2106_12802_gb300.profile_case render --size 512 --spp 4
   python -m paper_2106_12802_gb300.profile_case rdn    --size 1024 --prec bf16
   python -m paper_2106_12802_gb300.profile_case train  --batch 16 --crop 128
+  python -m paper_2106_12802_gb300.profile_case rdn_train --batch 16 --crop 192 --prec bf16
+  python -m paper_2106_12802_gb300.profile_case tree   --kind cluster
 
 `fuse` runs the x4 fusion network at size x size output (inputs random,
 Kaiming weights); `rdn` the method's own x4 two-encoder network (the same);
@@ -14,9 +16,12 @@ Kaiming weights); `rdn` the method's own x4 two-encoder network (the same);
 from bounce 3) and prints its per-bounce ray counts, whose bounce >= 1 part is
 the number of closest-hit segments the tail kernel traces (the unit that a
 traffic capture of one tail launch is divided by); `train` runs BF16 training
-steps of the fusion network on a random batch.  Each case runs one warm-up
-call first, so the second call's launches are steady-state (ncu: skip the
-first call's launches with -s).
+steps of the fusion network on a random batch; `rdn_train` training steps of
+the method's own x4 network (the paper's batch: 16 crops of 192^2; a BF16
+step after the first replays its recorded graph); `tree` rebuilds the
+procedural scene's render tree (--kind lbvh or cluster).  Each case runs one
+warm-up call first, so the second call's launches are steady-state (ncu: skip
+the first call's launches with -s).
 """
 from __future__ import annotations
 
@@ -30,7 +35,8 @@ import numpy as np
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["fuse", "render", "rdn", "train"])
+    ap.add_argument("case", choices=["fuse", "render", "rdn", "train", "rdn_train", "tree"])
+    ap.add_argument("--kind", default="cluster")
     ap.add_argument("--size", type=int, default=1024)
     ap.add_argument("--prec", default="bf16")
     ap.add_argument("--spp", type=int, default=4)
@@ -81,6 +87,24 @@ def main(argv=None):
         for _ in range(2):
             loss = mrs.train_step(net, *t, s, lr=1e-4, precision=a.prec)
         print("train ok", loss)
+    elif a.case == "rdn_train":
+        from paper_2106_12802_gb300 import rdn
+        s = 4
+        N, c = a.batch, a.crop
+        net = mrs.RDN(rdn.kaiming_params(s), s)
+        g = torch.Generator(device="cuda").manual_seed(12)
+        t = [torch.rand((N, c // s, c // s, 3), device="cuda", generator=g) * 2] + \
+            [torch.rand((N, c, c, 3), device="cuda", generator=g) for _ in range(4)]
+        for _ in range(2):
+            loss = net.train_step(*t, lr=1e-4, loss="robust", beta=0.1, precision=a.prec)
+        print("rdn_train ok", loss)
+    elif a.case == "tree":
+        sc = mrs.Scene(scenes.procedural(0))
+        sc.set_tree(a.kind)
+        for _ in range(2):
+            sc.rebuild()
+        torch.cuda.synchronize()
+        print("tree ok", sc.tree())
     else:
         sc = mrs.Scene(scenes.procedural(0))
         for _ in range(2):
