@@ -1084,7 +1084,8 @@ mrs_status tc_conv3x3_wgrad(const TcWgradArgs& a, int* nparts, cudaStream_t st)
         attr = true;
     }
     long long njobs = (long long)a.N * a.H * ((a.W + kWgKB - 1) / kWgKB);
-    int grid = njobs < sm_count() ? (int)njobs : sm_count();
+    const int cap = a.max_ctas > 0 && a.max_ctas < sm_count() ? a.max_ctas : sm_count();
+    int grid = njobs < cap ? (int)njobs : cap;
     *nparts = grid;
     if (grid < 1) return MRS_OK;
     MRS_TIMED(PK_WGRAD_TC, st, (k_wgrad_tc<<<grid, kWgThreads, smem, st>>>(*a.tmap_x, *a.tmap_dy, a, stages)));

@@ -98,6 +98,10 @@ struct TcWgradArgs {
     float* dbpart;
     int N, H, W, cin, cout;
     int* err;
+    // at most this many CTAs (= partials), 0: one per SM.  Several small
+    // gradients launched side by side on different streams, each on a share
+    // of the SMs, write that many fewer partials each.
+    int max_ctas = 0;
 };
 int tc_wgrad_max_parts();
 mrs_status tc_conv3x3_wgrad(const TcWgradArgs& a, int* nparts, cudaStream_t st);

@@ -504,6 +504,8 @@ struct mrs_rdn_s {
     mrs::TrainKey tkey;
     uint64_t tgraph_kernels = 0;
     cudaStream_t tcap = nullptr;        // stream they are recorded on
+    cudaStream_t side[3] = {nullptr, nullptr, nullptr};   // weight-gradient tiles side by side
+    cudaEvent_t ev_fork = nullptr, ev_join[3] = {nullptr, nullptr, nullptr};
     Buf tdmaps;                    // its multi-chunk A-operand maps on the device
     CUtensorMap wmap_all;          // every chunk's weights as one [rows][64] tensor
     std::vector<CUtensorMap> hmaps;  // A-operand maps of the multi-chunk convs of a call
@@ -1452,22 +1454,57 @@ mrs_status rdn_train_bf16(mrs_rdn_s* r, const float* lrhs, const float* hrls, co
     MRS_LAUNCHED(1);
 
     // ---- backward
-    // weight gradient of one 64 x 64 tile (see k_wg_reduce for the mappings)
-    auto wgrad = [&](int hh, int ww, const CUtensorMap* xm, const CUtensorMap* ym, int cin_t, int cout_t,
-                     int lidx, int o_mul, int o_add, int c0, int q, bool with_bias) -> mrs_status {
-        TcWgradArgs wa;
-        wa.tmap_x = xm; wa.tmap_dy = ym; wa.part = part; wa.dbpart = dbpart;
-        wa.N = N; wa.H = hh; wa.W = ww; wa.cin = cin_t; wa.cout = cout_t; wa.err = r->err;
-        int np = 0;
-        mrs_status e = tc_conv3x3_wgrad(wa, &np, st);
-        if (e != MRS_OK) return e;
-        const RLayer& l = r->L[lidx];
-        const int KK = l.k * l.k;
-        const size_t n = (size_t)cout_t * KK * cin_t + cout_t;
-        k_wg_reduce<<<(int)((n + 31) / 32), 256, 0, st>>>(part, dbpart, np, cin_t, cout_t, KK, l.cin, o_mul, o_add, c0,
-                                                 q, s, D, with_bias ? 1 : 0, r->grad + l.woff,
-                                                 r->grad + l.boff);
-        MRS_LAUNCHED(1);
+    // Weight gradients, one 64 x 64 tile per launch (see k_wg_reduce for the
+    // mappings into the layer gradient).  A group of tiles (a conv's input
+    // parts, an upsampling conv's four views, the fuse conv's 17 chunks) runs
+    // side by side on up to kWgStreams streams, each tile on its stream's
+    // share of the SMs: at the LR grid a tile is little work, and a tile on
+    // fewer CTAs writes (and its reduction reads) that many fewer partials.
+    struct WgTile {
+        const CUtensorMap* xm;
+        const CUtensorMap* ym;
+        int hh, ww, cin_t, cout_t, lidx, o_mul, o_add, c0, q;
+        bool with_bias;
+    };
+    constexpr int kWgStreams = 4;
+    auto wgrad_group = [&](int ntile, auto tile) -> mrs_status {
+        const int S = ntile < kWgStreams ? ntile : kWgStreams;
+        const int cap = maxp / S;
+        cudaStream_t ss[kWgStreams] = {st, nullptr, nullptr, nullptr};
+        for (int i = 1; i < S; ++i) {
+            if (!r->side[i - 1]) MRS_CHECK(cudaStreamCreateWithFlags(&r->side[i - 1], cudaStreamNonBlocking));
+            if (!r->ev_join[i - 1]) MRS_CHECK(cudaEventCreateWithFlags(&r->ev_join[i - 1], cudaEventDisableTiming));
+            ss[i] = r->side[i - 1];
+        }
+        if (S > 1) {
+            if (!r->ev_fork) MRS_CHECK(cudaEventCreateWithFlags(&r->ev_fork, cudaEventDisableTiming));
+            MRS_CHECK(cudaEventRecord(r->ev_fork, st));
+            for (int i = 1; i < S; ++i) MRS_CHECK(cudaStreamWaitEvent(ss[i], r->ev_fork, 0));
+        }
+        for (int i = 0; i < ntile; ++i) {
+            const WgTile t = tile(i);
+            cudaStream_t sq = ss[i % S];
+            float* pt = part + (size_t)(i % S) * cap * 9 * 4096;
+            float* pb = dbpart + (size_t)(i % S) * cap * 64;
+            TcWgradArgs wa;
+            wa.tmap_x = t.xm; wa.tmap_dy = t.ym; wa.part = pt; wa.dbpart = pb;
+            wa.N = N; wa.H = t.hh; wa.W = t.ww; wa.cin = t.cin_t; wa.cout = t.cout_t; wa.err = r->err;
+            wa.max_ctas = cap;
+            int np = 0;
+            mrs_status e = tc_conv3x3_wgrad(wa, &np, sq);
+            if (e != MRS_OK) return e;
+            const RLayer& l = r->L[t.lidx];
+            const int KK = l.k * l.k;
+            const size_t n = (size_t)t.cout_t * KK * t.cin_t + t.cout_t;
+            k_wg_reduce<<<(int)((n + 31) / 32), 256, 0, sq>>>(pt, pb, np, t.cin_t, t.cout_t, KK, l.cin, t.o_mul,
+                                                              t.o_add, t.c0, t.q, s, D, t.with_bias ? 1 : 0,
+                                                              r->grad + l.woff, r->grad + l.boff);
+            MRS_LAUNCHED(1);
+        }
+        for (int i = 1; i < S; ++i) {
+            MRS_CHECK(cudaEventRecord(r->ev_join[i - 1], ss[i]));
+            MRS_CHECK(cudaStreamWaitEvent(st, r->ev_join[i - 1], 0));
+        }
         return cuda_status(cudaGetLastError(), "rdn wgrad");
     };
     auto mask = [&](const __nv_bfloat16* d, const __nv_bfloat16* act, size_t P, __nv_bfloat16* out) {
@@ -1476,7 +1513,8 @@ mrs_status rdn_train_bf16(mrs_rdn_s* r, const float* lrhs, const float* hrls, co
     };
     const CUtensorMap* WT = &r->wmapT_all;
     // H_Rec
-    if ((rc = wgrad(H, W, &mU[D].x, &mDyb.y, 64, 3, li_rec, 1, 0, 0, 0, true)) != MRS_OK) return rc;
+    if ((rc = wgrad_group(1, [&](int) { return WgTile{&mU[D].x, &mDyb.y, H, W, 64, 3, li_rec, 1, 0, 0, 0, true}; }))
+        != MRS_OK) return rc;
     if ((rc = conv(H, W, &mDyb.a, -1, 1, WT, trow(li_rec, 0), zero, 64, TC_LIN_BF16, nullptr, &mDUl[D].o)) != MRS_OK)
         return rc;
     // upsampling stages in reverse: the level-(d + 1) gradient masked by U[d + 1] > 0
@@ -1484,8 +1522,9 @@ mrs_status rdn_train_bf16(mrs_rdn_s* r, const float* lrhs, const float* hrls, co
         const int lu = 3 + kConv * nblk + d;
         __nv_bfloat16* gd = dU[(D - 1 - d) & 1];
         mask(gd, U[d + 1], Pd[d + 1], gd);
-        for (int q = 0; q < 4; ++q)
-            if ((rc = wgrad(hd[d], wd[d], &mU[d].x, &dupY[d][q], 64, 64, lu, 4, q, 0, 0, true)) != MRS_OK) return rc;
+        if ((rc = wgrad_group(4, [&](int q) {
+                 return WgTile{&mU[d].x, &dupY[d][q], hd[d], wd[d], 64, 64, lu, 4, q, 0, 0, true}; })) != MRS_OK)
+            return rc;
         if ((rc = conv(hd[d], wd[d], &dupA[d][0], (long)mc_up[d], 4, WT, trow(lu, 0), zero, 64, TC_LIN_BF16,
                        nullptr, &mDUl[d].o)) != MRS_OK) return rc;
     }
@@ -1498,9 +1537,9 @@ mrs_status rdn_train_bf16(mrs_rdn_s* r, const float* lrhs, const float* hrls, co
             // local fusion: dz4 = G masked by its ReLU output; one weight tile per
             // concatenation part; part 0's gradient = G + conv^T, parts 1..3 start here
             mask(G, Fk[k][3], Pl, dz4);
-            for (int j = 0; j < 4; ++j)
-                if ((rc = wgrad(h, w, j ? &mF[k][j - 1].x : &mX[k].x, &mDz4.y, 64, 64, lb + 3, 1, 0, 64 * j, 0,
-                                j == 0)) != MRS_OK) return rc;
+            if ((rc = wgrad_group(4, [&](int j) {
+                     return WgTile{j ? &mF[k][j - 1].x : &mX[k].x, &mDz4.y, h, w, 64, 64, lb + 3, 1, 0, 64 * j, 0,
+                                   j == 0}; })) != MRS_OK) return rc;
             if ((rc = conv(h, w, &mDz4.a, -1, 1, WT, trow(lb + 3, 0), zero, 64, TC_RESID_BF16, &mDp[0].o,
                            &mDp[0].o)) != MRS_OK) return rc;
             for (int j = 1; j < 4; ++j)
@@ -1512,9 +1551,9 @@ mrs_status rdn_train_bf16(mrs_rdn_s* r, const float* lrhs, const float* hrls, co
             for (int c = kConv - 1; c >= 1; --c) {
                 const int lc = lb + c - 1;
                 mask(dp[c], Fk[k][c - 1], Pl, dp[c]);
-                for (int j = 0; j < c; ++j)
-                    if ((rc = wgrad(h, w, j ? &mF[k][j - 1].x : &mX[k].x, &mDp[c].y, 64, 64, lc, 1, 0, 64 * j, 0,
-                                    j == 0)) != MRS_OK) return rc;
+                if ((rc = wgrad_group(c, [&](int j) {
+                         return WgTile{j ? &mF[k][j - 1].x : &mX[k].x, &mDp[c].y, h, w, 64, 64, lc, 1, 0, 64 * j, 0,
+                                       j == 0}; })) != MRS_OK) return rc;
                 for (int j = 0; j < c; ++j)
                     if ((rc = conv(h, w, &mDp[c].a, -1, 1, WT, trow(lc, j), zero, 64, TC_RESID_BF16, &mDp[j].o,
                                    &mDp[j].o)) != MRS_OK) return rc;
@@ -1527,9 +1566,9 @@ mrs_status rdn_train_bf16(mrs_rdn_s* r, const float* lrhs, const float* hrls, co
     // fuse: dz = (dL/dF_DF + the chain's gradient) masked by F_0
     k_sum_bf16<<<grid_for(Pl * 64), 256, 0, st>>>(dzf, gdf, G, nullptr, nullptr, F0, Pl * 64);
     MRS_LAUNCHED(1);
-    for (int q = 0; q <= SS; ++q)
-        if ((rc = wgrad(h, w, q ? &dsfX[q - 1] : &mFlr.x, &mDzf.y, 64, 64, 2, 1, 0, 0, q, q == 0)) != MRS_OK)
-            return rc;
+    if ((rc = wgrad_group(SS + 1, [&](int q) {
+             return WgTile{q ? &dsfX[q - 1] : &mFlr.x, &mDzf.y, h, w, 64, 64, 2, 1, 0, 0, q, q == 0}; })) != MRS_OK)
+        return rc;
     // its input gradients, masked by the encoders' ReLU outputs: chunk 0 into
     // F_LRHS's gradient, chunk q into deshuffle view q of F0_HRLS's
     if ((rc = conv(h, w, &mDzf.a, -1, 1, WT, trow(2, 0), zero, 64, TC_MASK_BF16, &mFlr.o, &mDzlr.o)) != MRS_OK)
@@ -1538,8 +1577,10 @@ mrs_status rdn_train_bf16(mrs_rdn_s* r, const float* lrhs, const float* hrls, co
         if ((rc = conv(h, w, &mDzf.a, -1, 1, WT, trow(2, q), zero, 64, TC_MASK_BF16, &dsfO[q - 1],
                        &dz1O[q - 1])) != MRS_OK) return rc;
     // encoders
-    if ((rc = wgrad(h, w, &mInL.x, &mDzlr.y, 3, 64, 0, 1, 0, 0, 0, true)) != MRS_OK) return rc;
-    if ((rc = wgrad(H, W, &mInH.x, &mDz1.y, r->c_hr, 64, 1, 1, 0, 0, 0, true)) != MRS_OK) return rc;
+    if ((rc = wgrad_group(2, [&](int e) {
+             return e == 0 ? WgTile{&mInL.x, &mDzlr.y, h, w, 3, 64, 0, 1, 0, 0, 0, true}
+                           : WgTile{&mInH.x, &mDz1.y, H, W, r->c_hr, 64, 1, 1, 0, 0, 0, true}; })) != MRS_OK)
+        return rc;
 
     return MRS_OK;
     };
@@ -1610,6 +1651,11 @@ extern "C" mrs_status mrs_rdn_free(mrs_rdn r)
         if (p) cudaFree(p);
     if (r->tgraph) cudaGraphExecDestroy(r->tgraph);
     if (r->tcap) cudaStreamDestroy(r->tcap);
+    for (int i = 0; i < 3; ++i) {
+        if (r->side[i]) cudaStreamDestroy(r->side[i]);
+        if (r->ev_join[i]) cudaEventDestroy(r->ev_join[i]);
+    }
+    if (r->ev_fork) cudaEventDestroy(r->ev_fork);
     r->f32.release();
     r->bf.release();
     r->tr.release();
