@@ -158,83 +158,145 @@ __global__ void k_input_q(const float* lrhs, const float* hrls, const float* alb
 }
 
 // ---- FP32 SIMT direct convolution -------------------------------------------
-// block = 16 x 8 output pixels, 16 output channels (grid.z over channel groups);
-// input channels staged through shared memory 4 at a time with a 1-pixel halo
-constexpr int kTX = 16, kTY = 8, kCT = 16, kCC = 4;
+// block = (8 SP) x 16 output pixels and 16 output channels (grid.z over images
+// x channel groups), 128 threads; a thread computes SP consecutive pixels of
+// one row x 16 channels (16 SP accumulators).  Input channels go through
+// shared memory in stages (8 channels for SP = 2, 4 for SP = 4, whose 64
+// accumulators leave registers for 4 blocks per SM), with a 1-pixel halo, in
+// two buffers: the asynchronous copies (cp.async, zero-filled outside the
+// image and past cin) of the next stage are in flight while the current one
+// is used.  Per (channel, kernel row) a thread reads SP + 2 inputs and, per
+// column tap, 16 weights (broadcast) for 16 SP FMAs.  The input rows are
+// padded so that a warp's reads (8 threads along x, 4 rows) fall in distinct
+// banks (SP = 4) or at most two to a bank (SP = 2).
+constexpr int kSY = 16, kSO = 16;
+constexpr int simt_pitch(int sp) { return sp == 4 ? 37 : 19; }
+constexpr int simt_stage(int sp) { return sp == 4 ? 4 : 8; }
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool ok)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(ok ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int kPending>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(kPending) : "memory");
+}
 // x [P][xs] (first cin channels read), out / res [P][os] / [P][rs] (first
 // cout written / read): strides let a layer read a prefix of a concatenation
 // buffer and write into a channel slice of another
-__global__ void __launch_bounds__(kTX * kTY)
+template <int kSP>
+__global__ void __launch_bounds__(128, kSP == 4 ? 4 : 5)
     k_conv_simt(const float* __restrict__ x, int cin, int xs, const float* __restrict__ w,
                 const float* __restrict__ b, int cout, int mode, int relu,
                 const float* __restrict__ res, int rs, float* __restrict__ out, int os,
                 const float* __restrict__ lrhs, int H, int W, int s)
 {
-    __shared__ float sin_[kTY + 2][kTX + 2][kCC];
-    __shared__ __align__(16) float sw[9][kCC][kCT];
-    const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
-    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
-    const int n = blockIdx.z / ((cout + kCT - 1) / kCT);
-    const int o0 = (blockIdx.z % ((cout + kCT - 1) / kCT)) * kCT;
+    constexpr int kSX = 8 * kSP, kSPitch = simt_pitch(kSP), kSC = simt_stage(kSP);
+    __shared__ float sin_[2][kSC][kSY + 2][kSPitch];
+    __shared__ __align__(16) float sw[2][9][kSC][kSO];
+    const int tx = threadIdx.x % (kSX / kSP), ty = threadIdx.x / (kSX / kSP);
+    const int x0 = blockIdx.x * kSX, y0 = blockIdx.y * kSY;
+    const int ngrp = (cout + kSO - 1) / kSO;
+    const int n = blockIdx.z / ngrp;
+    const int o0 = (blockIdx.z % ngrp) * kSO;
     const float* xin = x + (size_t)n * H * W * xs;
-    float acc[kCT];
-#pragma unroll
-    for (int o = 0; o < kCT; ++o) acc[o] = 0.0f;
-    for (int c0 = 0; c0 < cin; c0 += kCC) {
-        for (int i = threadIdx.x; i < (kTY + 2) * (kTX + 2) * kCC; i += kTX * kTY) {
-            int c = i % kCC, px = (i / kCC) % (kTX + 2), py = i / (kCC * (kTX + 2));
-            int gx = x0 + px - 1, gy = y0 + py - 1;
-            float v = 0.0f;
-            if (gx >= 0 && gx < W && gy >= 0 && gy < H && c0 + c < cin)
-                v = __ldg(xin + ((size_t)gy * W + gx) * xs + c0 + c);
-            sin_[py][px][c] = v;
+    // channels c0 .. c0 + 7 of the input tile and of the weights into buffer q
+    auto stage = [&](int c0, int q) {
+        for (int i = threadIdx.x; i < (kSY + 2) * (kSX + 2) * kSC; i += 128) {
+            const int c = i % kSC, px = (i / kSC) % (kSX + 2), py = i / (kSC * (kSX + 2));
+            const int gx = x0 + px - 1, gy = y0 + py - 1;
+            const bool ok = gx >= 0 && gx < W && gy >= 0 && gy < H && c0 + c < cin;
+            cp_async4(&sin_[q][c][py][px], ok ? xin + ((size_t)gy * W + gx) * xs + c0 + c : x, ok);
         }
-        for (int i = threadIdx.x; i < 9 * kCC * kCT; i += kTX * kTY) {
-            int o = i % kCT, c = (i / kCT) % kCC, t = i / (kCT * kCC);
-            float v = 0.0f;
-            if (o0 + o < cout && c0 + c < cin) v = __ldg(w + ((size_t)(o0 + o) * 9 + t) * cin + c0 + c);
-            sw[t][c][o] = v;
+        for (int i = threadIdx.x; i < 9 * kSC * kSO; i += 128) {
+            const int c = i % kSC, t = (i / kSC) % 9, o = i / (kSC * 9);
+            const bool ok = o0 + o < cout && c0 + c < cin;
+            cp_async4(&sw[q][t][c][o], ok ? w + ((size_t)(o0 + o) * 9 + t) * cin + c0 + c : w, ok);
+        }
+        cp_async_commit();
+    };
+    float acc[kSP][kSO];
+#pragma unroll
+    for (int p = 0; p < kSP; ++p)
+#pragma unroll
+        for (int o = 0; o < kSO; ++o) acc[p][o] = 0.0f;
+    const int nk = (cin + kSC - 1) / kSC;
+    stage(0, 0);
+    for (int k = 0; k < nk; ++k) {
+        if (k + 1 < nk) {
+            stage((k + 1) * kSC, (k + 1) & 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
         }
         __syncthreads();
+        const int q = k & 1;
+#pragma unroll 2
+        for (int c = 0; c < kSC; ++c) {
 #pragma unroll
-        for (int t = 0; t < 9; ++t) {
+            for (int dy = 0; dy < 3; ++dy) {
+                const float* row = &sin_[q][c][ty + dy][tx * kSP];
+                float in[kSP + 2];
 #pragma unroll
-            for (int c = 0; c < kCC; ++c) {
-                float v = sin_[ty + t / 3][tx + t % 3][c];
-                const float4* w4 = (const float4*)sw[t][c];
+                for (int k2 = 0; k2 < kSP + 2; ++k2) in[k2] = row[k2];
 #pragma unroll
-                for (int o4 = 0; o4 < kCT / 4; ++o4) {
-                    float4 ww = w4[o4];
-                    acc[4 * o4] += v * ww.x;
-                    acc[4 * o4 + 1] += v * ww.y;
-                    acc[4 * o4 + 2] += v * ww.z;
-                    acc[4 * o4 + 3] += v * ww.w;
+                for (int dx = 0; dx < 3; ++dx) {
+                    const float4* w4 = (const float4*)sw[q][dy * 3 + dx][c];
+                    float wv[kSO];
+#pragma unroll
+                    for (int j = 0; j < kSO / 4; ++j) {
+                        const float4 t4 = w4[j];
+                        wv[4 * j] = t4.x; wv[4 * j + 1] = t4.y; wv[4 * j + 2] = t4.z; wv[4 * j + 3] = t4.w;
+                    }
+#pragma unroll
+                    for (int p = 0; p < kSP; ++p)
+#pragma unroll
+                        for (int o = 0; o < kSO; ++o) acc[p][o] += in[p + dx] * wv[o];
                 }
             }
         }
+        // the next iteration's copies overwrite the buffer read here
         __syncthreads();
     }
-    int gx = x0 + tx, gy = y0 + ty;
-    if (gx >= W || gy >= H) return;
-    size_t p = ((size_t)n * H + gy) * W + gx;
-    if (mode == SIMT_FINAL) {
-        float up[3];
-        int h = H / s, wl = W / s;
-        up_pixel(lrhs + (size_t)n * h * wl * 3, h, wl, s, gx, gy, up);
-        for (int o = 0; o < kCT; ++o)
-            if (o0 + o < 3) out[p * 3 + o0 + o] = (acc[o] + __ldg(b + o0 + o)) + up[o0 + o];
-        return;
-    }
+    const int gy = y0 + ty;
+    if (gy >= H) return;
 #pragma unroll
-    for (int o = 0; o < kCT; ++o) {
-        if (o0 + o >= cout) break;
-        float v = acc[o] + __ldg(b + o0 + o);
-        if (mode == SIMT_RESID) v = res[p * rs + o0 + o] + v;
-        else if (mode == SIMT_MASK) v = res[p * rs + o0 + o] > 0.0f ? v : 0.0f;
-        else if (mode == SIMT_RESRELU) v = res[p * rs + o0 + o] + fmaxf(v, 0.0f);
-        else if (relu) v = fmaxf(v, 0.0f);
-        out[p * os + o0 + o] = v;
+    for (int p = 0; p < kSP; ++p) {
+        const int gx = x0 + tx * kSP + p;
+        if (gx >= W) break;
+        const size_t pp = ((size_t)n * H + gy) * W + gx;
+        if (mode == SIMT_FINAL) {
+            float up[3];
+            const int h = H / s, wl = W / s;
+            up_pixel(lrhs + (size_t)n * h * wl * 3, h, wl, s, gx, gy, up);
+            for (int o = 0; o < kSO; ++o)
+                if (o0 + o < 3) out[pp * 3 + o0 + o] = (acc[p][o] + __ldg(b + o0 + o)) + up[o0 + o];
+            continue;
+        }
+#pragma unroll
+        for (int o = 0; o < kSO; ++o) {
+            if (o0 + o >= cout) break;
+            float v = acc[p][o] + __ldg(b + o0 + o);
+            if (mode == SIMT_RESID) v = res[pp * rs + o0 + o] + v;
+            else if (mode == SIMT_MASK) v = res[pp * rs + o0 + o] > 0.0f ? v : 0.0f;
+            else if (mode == SIMT_RESRELU) v = res[pp * rs + o0 + o] + fmaxf(v, 0.0f);
+            else if (relu) v = fmaxf(v, 0.0f);
+            out[pp * os + o0 + o] = v;
+        }
     }
+}
+
+// Four pixels per thread (4 blocks per SM) pays on large grids, two (5 blocks
+// per SM, more warps to hide latency) below about four waves of the former
+int simt_sp(int N, int H, int W, int cout)
+{
+    const long long blocks4 = (long long)((W + 31) / 32) * ((H + kSY - 1) / kSY) * N *
+                              ((cout + kSO - 1) / kSO);
+    return blocks4 >= 16LL * sm_count() ? 4 : 2;
 }
 
 }  // namespace
@@ -243,8 +305,12 @@ mrs_status simt_conv3x3(const float* x, int cin, int xs, const float* w, const f
                         int mode, int relu, const float* res, int rs, float* out, int os,
                         const float* lrhs, int N, int H, int W, int s, cudaStream_t st)
 {
-    dim3 grid((W + kTX - 1) / kTX, (H + kTY - 1) / kTY, N * ((cout + kCT - 1) / kCT));
-    MRS_TIMED(PK_CONV_SIMT, st, k_conv_simt<<<grid, kTX * kTY, 0, st>>>(x, cin, xs, w, b, cout, mode, relu, res, rs, out, os, lrhs, H, W, s));
+    const int sp = simt_sp(N, H, W, cout);
+    dim3 grid((W + 8 * sp - 1) / (8 * sp), (H + kSY - 1) / kSY, N * ((cout + kSO - 1) / kSO));
+    if (sp == 4)
+        MRS_TIMED(PK_CONV_SIMT, st, k_conv_simt<4><<<grid, 128, 0, st>>>(x, cin, xs, w, b, cout, mode, relu, res, rs, out, os, lrhs, H, W, s));
+    else
+        MRS_TIMED(PK_CONV_SIMT, st, k_conv_simt<2><<<grid, 128, 0, st>>>(x, cin, xs, w, b, cout, mode, relu, res, rs, out, os, lrhs, H, W, s));
     MRS_LAUNCHED(1);
     return cuda_status(cudaGetLastError(), "conv_simt launch");
 }
