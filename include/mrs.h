@@ -137,6 +137,15 @@ mrs_status mrs_scene_rebuild(mrs_scene scene, void* stream);
  *                     surface area (ties by a hash of the position pair),
  *                     mutual pairs merge, the list is compacted (for scenes
  *                     built once and rendered many times)
+ *   MRS_TREE_HCLUSTER the same clustering inside the subtrees of the radix
+ *                     tree, bottom-up in one launch (Benthin et al., HPG 2024,
+ *                     on the agglomerative walk of Apetrei, 2014): a subtree
+ *                     keeps at most 16 clusters; where two children meet with
+ *                     more, one warp merges mutual nearest pairs among all of
+ *                     them until 16 are left (one at the root).  Nearly the
+ *                     global rounds' surface-area cost, no read-back, also
+ *                     inside a caller's stream capture.  Node ids (not the
+ *                     tree) depend on the order in which warps merge.
  * set_tree records the choice and rebuilds the tree on `stream` (synchronised).
  * get_tree returns the kind in use: MRS_TREE_LBVH also when clustering was
  * asked for but did not finish within its bound of 72 grid-wide rounds plus
@@ -144,6 +153,7 @@ mrs_status mrs_scene_rebuild(mrs_scene scene, void* stream);
  * choice stays with the scene for later rebuilds. */
 #define MRS_TREE_LBVH 0
 #define MRS_TREE_CLUSTER 1
+#define MRS_TREE_HCLUSTER 2
 mrs_status mrs_scene_set_tree(mrs_scene scene, int32_t kind, void* stream);
 mrs_status mrs_scene_get_tree(mrs_scene scene, int32_t* kind);
 /* The render tree's nodes: n_tree (HOST) receives ns, the triangles in the

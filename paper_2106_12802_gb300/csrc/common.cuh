@@ -102,12 +102,12 @@ inline int sm_count()
 namespace mrs {
 // what a captured tree-build graph depends on besides the scene's own arrays
 struct BuildKey {
-    int n = -1, ns = -1, cluster = -1;
+    int n = -1, ns = -1, tree = -1;
     void* sort_buf = nullptr;
     void* ploc_buf = nullptr;
     bool operator==(const BuildKey& o) const
     {
-        return n == o.n && ns == o.ns && cluster == o.cluster && sort_buf == o.sort_buf &&
+        return n == o.n && ns == o.ns && tree == o.tree && sort_buf == o.sort_buf &&
                ploc_buf == o.ploc_buf;
     }
 };

@@ -109,12 +109,13 @@ class Scene:
         """First bounce of the tail kernel (-1: automatic; > max_depth: none)."""
         call("mrs_scene_set_tail", self.handle, int(bounce))
 
-    TREES = {"lbvh": 0, "cluster": 1}
+    TREES = {"lbvh": 0, "cluster": 1, "hcluster": 2}
 
     def set_tree(self, kind: str = "cluster", stream=None):
-        """Render tree: "lbvh" (the radix tree, the default: cheapest build) or
-        "cluster" (locally-ordered clustering: faster renders, slower build);
-        rebuilds it."""
+        """Render tree: "lbvh" (the radix tree, the default: cheapest build),
+        "cluster" (locally-ordered clustering in grid-wide rounds: faster
+        renders, slower build) or "hcluster" (the same clustering inside the
+        radix tree's subtrees, one launch); rebuilds it."""
         call("mrs_scene_set_tree", self.handle, self.TREES[kind], _stream(stream))
 
     def tree(self) -> str:

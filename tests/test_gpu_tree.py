@@ -1,11 +1,13 @@
 """The render tree: the radix tree (the default) and locally-ordered
-clustering.  The exported clustering tree is checked on the host (every node but
-the root a child exactly once, leaf boxes the triangles' boxes, every
-internal box the exact union of its children's); closest hits and renders
-are the same with both trees, bit for bit, and equal the oracle's; the
-clustering tree's surface-area cost and traversal work are below the radix
-tree's on the procedural scene.  Sizes span the single-block finish (2048
-clusters), several grid-wide rounds, ties (identical triangles) and
+clustering, in grid-wide rounds ("cluster") or inside the radix tree's
+subtrees in one launch ("hcluster").  The exported trees are checked on the
+host (every node but the root a child exactly once, leaf boxes the
+triangles' boxes, every internal box the exact union of its children's);
+closest hits and renders are the same with every tree, bit for bit, and
+equal the oracle's; the clustering trees' surface-area cost and traversal
+work are below the radix tree's on the procedural scene.  Sizes span the
+single-block finish (2048 clusters), several grid-wide rounds, a subtree's
+16 kept clusters (16, 17, 33 leaves), ties (identical triangles) and
 degenerate (zero-area) triangles."""
 import numpy as np
 import pytest
@@ -67,63 +69,106 @@ def _soup(seed, n, identical=False, degenerate=False):
     return desc
 
 
-@pytest.mark.parametrize("n,kw", [(2, {}), (3, {}), (100, {}), (2047, {}), (2048, {}), (2049, {}),
-                                  (5000, {}), (70000, {}), (3000, {"identical": True}),
-                                  (4000, {"degenerate": True})])
-def test_cluster_tree_is_valid(mrs, n, kw):
+@pytest.mark.parametrize("kind", ["cluster", "hcluster"])
+@pytest.mark.parametrize("n,kw", [(2, {}), (3, {}), (16, {}), (17, {}), (33, {}), (100, {}),
+                                  (2047, {}), (2048, {}), (2049, {}), (5000, {}), (70000, {}),
+                                  (3000, {"identical": True}), (4000, {"degenerate": True})])
+def test_cluster_tree_is_valid(mrs, n, kw, kind):
     desc = _soup(n, n, **kw)
     sc = mrs.Scene(desc)
     assert sc.tree() == "lbvh"
     check_tree(sc.export_nodes(), desc["V"])
-    sc.set_tree("cluster")
-    assert sc.tree() == "cluster"
+    sc.set_tree(kind)
+    assert sc.tree() == kind
     check_tree(sc.export_nodes(), desc["V"])
     sc.rebuild()                        # the choice stays with the scene
-    assert sc.tree() == "cluster"
+    assert sc.tree() == kind
+    check_tree(sc.export_nodes(), desc["V"])
 
 
 @pytest.mark.parametrize("seed,n,kw", [(0, 8, {}), (2, 3000, {}), (3, 50000, {}),
                                        (4, 3000, {"identical": True}),
                                        (5, 4000, {"degenerate": True})])
-def test_cast_same_with_both_trees_and_brute_force(mrs, orc, seed, n, kw):
+def test_cast_same_with_every_tree_and_brute_force(mrs, orc, seed, n, kw):
     desc = _soup(seed, n, **kw)
     o, d = scenes.random_rays(seed, 40000)
     sc = mrs.Scene(desc)
-    sc.set_tree("cluster")
     to, td = torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda()
+    sc.set_tree("cluster")
     pc, tc = sc.cast(to, td)
+    sc.set_tree("hcluster")
+    ph, th = sc.cast(to, td)
     sc.set_tree("lbvh")
     assert sc.tree() == "lbvh"
     pl, tl = sc.cast(to, td)
     assert torch.equal(pc, pl) and torch.equal(tc, tl)
+    assert torch.equal(ph, pl) and torch.equal(th, tl)
     pb, tb = orc.cast(desc["V"], o, d, brute=n <= 64)
     assert np.array_equal(pc.cpu().numpy(), pb)
     assert np.array_equal(tc.cpu().numpy(), tb)
 
 
 def test_procedural_scene_trees(mrs, orc):
-    # 200,968-triangle lit procedural scene: both trees valid, the clustering
-    # one with a lower surface-area cost and fewer node visits, renders
+    # 200,968-triangle lit procedural scene: every tree valid, the clustering
+    # ones with a lower surface-area cost and fewer node visits, renders
     # identical bit for bit and equal to the oracle's on a small image
     desc = scenes.procedural(0)
     sc = mrs.Scene(desc)
-    sc.set_tree("cluster")
-    cost_c = check_tree(sc.export_nodes(), desc["V"])
-    st_c = mrs.render_stats(sc, 96, 96, 2, 8, 3, 7)
-    rc = mrs.render(sc, 96, 96, 2, 8, rr_start=3, seed=7)
-    sc.set_tree("lbvh")
-    cost_l = check_tree(sc.export_nodes(), desc["V"])
-    st_l = mrs.render_stats(sc, 96, 96, 2, 8, 3, 7)
-    rl = mrs.render(sc, 96, 96, 2, 8, rr_start=3, seed=7)
-    for k in rc:
-        assert torch.equal(rc[k], rl[k]), k
-    assert cost_c < 0.9 * cost_l, (cost_c, cost_l)
-    assert st_c["visits"] < st_l["visits"], (st_c, st_l)
+    cost, st, img = {}, {}, {}
+    for kind in ("cluster", "hcluster", "lbvh"):
+        sc.set_tree(kind)
+        assert sc.tree() == kind
+        cost[kind] = check_tree(sc.export_nodes(), desc["V"])
+        st[kind] = mrs.render_stats(sc, 96, 96, 2, 8, 3, 7)
+        img[kind] = mrs.render(sc, 96, 96, 2, 8, rr_start=3, seed=7)
+    for kind in ("cluster", "hcluster"):
+        for k in img["lbvh"]:
+            assert torch.equal(img[kind][k], img["lbvh"][k]), (kind, k)
+        assert cost[kind] < 0.9 * cost["lbvh"], cost
+        assert st[kind]["visits"] < st["lbvh"]["visits"], st
+    # the one-launch build keeps nearly the global rounds' quality
+    assert cost["hcluster"] < 1.03 * cost["cluster"], cost
     r = orc.render(desc, 96, 96, 2, 8, rr_start=3, seed=7)
+    rc = img["hcluster"]
     assert np.array_equal(rc["counts"].cpu().numpy().astype(np.uint64), r["counts"])
     assert np.array_equal(rc["shadow_counts"].cpu().numpy().astype(np.uint64), r["shadow_counts"])
-    print(f"\nSAH cost: cluster {cost_c:.2f}, radix tree {cost_l:.2f}; closest-hit node visits "
-          f"{st_c['visits']} vs {st_l['visits']}, shadow {st_c['shadow_visits']} vs {st_l['shadow_visits']}")
+    print("\nSAH cost:", {k: round(v, 2) for k, v in cost.items()}, "closest-hit node visits:",
+          {k: v["visits"] for k, v in st.items()}, "shadow:", {k: v["shadow_visits"] for k, v in st.items()})
+
+
+def test_hcluster_node_ids_are_a_function_of_the_tree(mrs):
+    # node ids come from the split positions, not from the order in which
+    # warps merge: rebuilding gives the same node array bit for bit
+    desc = _soup(8, 60000)
+    sc = mrs.Scene(desc)
+    sc.set_tree("hcluster")
+    t0 = sc.export_nodes()
+    for _ in range(3):
+        sc.rebuild()
+        t1 = sc.export_nodes()
+        assert np.array_equal(t0["child"], t1["child"])
+        assert np.array_equal(t0["box"], t1["box"])
+
+
+def test_hcluster_tree_inside_a_capture(mrs):
+    # the one-launch build reads nothing back, so a caller's stream capture
+    # records it; replaying the capture rebuilds the same tree
+    desc = _soup(9, 30000)
+    sc = mrs.Scene(desc)
+    sc.set_tree("hcluster")
+    o, d = scenes.random_rays(9, 20000)
+    to, td = torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda()
+    p0, t0 = sc.cast(to, td)
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        sc.rebuild(stream=s)
+    assert sc.tree() == "hcluster"
+    g.replay()
+    torch.cuda.synchronize()
+    check_tree(sc.export_nodes(), desc["V"])
+    p1, t1 = sc.cast(to, td)
+    assert torch.equal(p0, p1) and torch.equal(t0, t1)
 
 
 def test_set_tree_rejects_unknown_kind(mrs):
