@@ -874,6 +874,8 @@ struct HClusterArgs {
 // Per-warp scratch of a merge: the union areas of the warp's cluster pairs
 struct HWarpScratch {
     float D[32][33];        // half surface area of cluster i's and j's union (+inf: none)
+    float4 kb[64];          // a round's merged boxes, by lane
+    int kp[32];             // and each lane's nearest neighbour
 };
 
 // One warp merges the clusters of range [L, R] (split after p); see above.
@@ -945,18 +947,24 @@ __device__ void hcluster_merge(const HClusterArgs& a, int L, int R, int p, HWarp
         __syncwarp();
     }
     for (int round = 0; c > target && round < 2 * kHKeep; ++round) {
-        // nearest neighbour: smallest area, then pair hash, then position
+        // nearest neighbour: smallest area, then pair hash, then position (the
+        // hashes only where a row has a tie for its smallest area)
         float best = INFINITY;
         int bj = -1;
+        bool tie = false;
         if (mine) {
+#pragma unroll
             for (int j = 0; j < 32; ++j) {
                 const float v = sc.D[lane][j];
-                if (v < best) {
-                    best = v;
-                    bj = j;
-                } else if (v == best && bj >= 0 && pair_key(lane, j) < pair_key(lane, bj)) {
-                    bj = j;
-                }
+                tie = v == best ? true : (v < best ? false : tie);
+                bj = v < best ? j : bj;
+                best = fminf(best, v);
+            }
+        }
+        if (__any_sync(0xffffffffu, tie && best != INFINITY)) {
+            if (tie && best != INFINITY) {
+                for (int j = bj + 1; j < 32; ++j)
+                    if (sc.D[lane][j] == best && pair_key(lane, j) < pair_key(lane, bj)) bj = j;
             }
         }
         const int back = __shfl_sync(0xffffffffu, bj, bj >= 0 ? bj : lane);
@@ -982,17 +990,19 @@ __device__ void hcluster_merge(const HClusterArgs& a, int L, int R, int p, HWarp
         mine = (alive >> lane) & 1u;
         __syncwarp();
         // merged clusters: new row and column; the partners' columns closed
+        if (lead) {
+            sc.kb[2 * lane] = b0;
+            sc.kb[2 * lane + 1] = b1;
+        }
+        sc.kp[lane] = bj;
+        __syncwarp();
         for (unsigned mm = lm; mm; mm &= mm - 1) {
             const int k = __ffs(mm) - 1;
-            const int kp = __shfl_sync(0xffffffffu, bj, k);
-            const float4 k0 = shfl4(b0, k);
-            const float k1x = __shfl_sync(0xffffffffu, b1.x, k), k1y = __shfl_sync(0xffffffffu, b1.y, k);
-            const float u = mine && lane != k
-                                ? union_half_area(k0, make_float4(k1x, k1y, 0.0f, 0.0f), b0, b1)
-                                : INFINITY;
+            const float u = mine && lane != k ? union_half_area(sc.kb[2 * k], sc.kb[2 * k + 1], b0, b1)
+                                              : INFINITY;
             sc.D[k][lane] = u;
             sc.D[lane][k] = u;
-            sc.D[lane][kp] = INFINITY;
+            sc.D[lane][sc.kp[k]] = INFINITY;
         }
         __syncwarp();
     }
