@@ -106,15 +106,26 @@ __global__ void k_morton(const float* __restrict__ V, int n, const float* __rest
                          int* __restrict__ vals, const int* __restrict__ idx = nullptr)
 {
     __shared__ float lo[3], sc[3];
-    if (threadIdx.x < 3) {
-        float l = INFINITY, h = -INFINITY;
-        for (int b = 0; b < nparts; ++b) {
-            l = fminf(l, part[b * 6 + threadIdx.x]);
-            h = fmaxf(h, part[b * 6 + 3 + threadIdx.x]);
-        }
-        float ext = h - l;
-        lo[threadIdx.x] = l;
-        sc[threadIdx.x] = ext > 0.0f ? 1024.0f / ext : 0.0f;
+    if (threadIdx.x < 32) {
+        // the first warp: partials strided over its lanes, then a butterfly
+        // (min and max are exact, so the order does not matter)
+        float l[3] = {INFINITY, INFINITY, INFINITY}, h[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (int b = threadIdx.x; b < nparts; b += 32)
+            for (int a = 0; a < 3; ++a) {
+                l[a] = fminf(l[a], part[b * 6 + a]);
+                h[a] = fmaxf(h[a], part[b * 6 + 3 + a]);
+            }
+        for (int off = 16; off > 0; off >>= 1)
+            for (int a = 0; a < 3; ++a) {
+                l[a] = fminf(l[a], __shfl_xor_sync(0xffffffffu, l[a], off));
+                h[a] = fmaxf(h[a], __shfl_xor_sync(0xffffffffu, h[a], off));
+            }
+        if (threadIdx.x == 0)
+            for (int a = 0; a < 3; ++a) {
+                const float ext = h[a] - l[a];
+                lo[a] = l[a];
+                sc[a] = ext > 0.0f ? 1024.0f / ext : 0.0f;
+            }
     }
     __syncthreads();
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
@@ -156,10 +167,11 @@ __global__ void k_sort_hist(const uint32_t* __restrict__ keys, int n, int shift,
 // thread sums a contiguous run of ceil(m / 1024) counts, one block-wide scan
 // of the 1024 run totals gives each run's offset, and each thread writes its
 // run's exclusive prefix (integer sums: the order does not change the result).
-// A run is read in groups of 8 independent loads, so that a thread waits for
-// the memory once per group rather than once per count.
-constexpr int kScanGroup = 8;
-__global__ void k_sort_scan(uint32_t* __restrict__ counts, int m)
+// A run is read in groups of kScanGroup independent loads, so that a thread
+// waits for the memory once per group rather than once per count (a 200k-key
+// sort has runs of 25 counts: one wait per pass).
+constexpr int kScanGroup = 32;
+__global__ void __launch_bounds__(1024) k_sort_scan(uint32_t* __restrict__ counts, int m)
 {
     __shared__ uint32_t s[32];
     const int per = (m + 1023) / 1024;
