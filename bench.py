@@ -977,20 +977,53 @@ def run_gpu(args, rank, world):
         torch.cuda.synchronize()
         pms = e0.elapsed_time(e1)
         rays = int(plain["counts"].sum().item() + plain["shadow_counts"].sum().item())
-        # the same render over the clustering tree (a static scene built once;
-        # the frame above rebuilds its LBVH every step)
-        scene.set_tree("cluster")
-        plain = mrs.render(scene, HR, HR, 64, DEPTH, RR, 8, out=plain)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        plain = mrs.render(scene, HR, HR, 64, DEPTH, RR, 8, out=plain)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        cms = e0.elapsed_time(e1)
+        # the same render over the clustering trees (grid-wide rounds, and
+        # the one-launch hierarchical build)
+        tree_ms = {}
+        for kind in ("cluster", "hcluster"):
+            scene.set_tree(kind)
+            plain = mrs.render(scene, HR, HR, 64, DEPTH, RR, 8, out=plain)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            plain = mrs.render(scene, HR, HR, 64, DEPTH, RR, 8, out=plain)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tree_ms[kind] = e0.elapsed_time(e1)
         scene.set_tree("lbvh")
         extra["plain_path_trace_1024_64spp"] = {
             "ms": pms, "msamples_per_s": HR * HR * 64 / pms / 1e3, "mrays_per_s": rays / pms / 1e3,
-            "cluster_tree_ms": cms, "cluster_tree_msamples_per_s": HR * HR * 64 / cms / 1e3}
+            "cluster_tree_ms": tree_ms["cluster"],
+            "cluster_tree_msamples_per_s": HR * HR * 64 / tree_ms["cluster"] / 1e3,
+            "hcluster_tree_ms": tree_ms["hcluster"],
+            "hcluster_tree_msamples_per_s": HR * HR * 64 / tree_ms["hcluster"] / 1e3}
+        # the timed frame again with its tree rebuilt by the one-launch
+        # hierarchical clustering instead of the radix tree (same steps, same
+        # L2 flush; the images are the same bit for bit), and both builds alone
+        scene.set_tree("hcluster")
+        for k in range(3):
+            frame(2000 + k)
+        hev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.zero_()
+            hev[k][0].record(stream)
+            frame(k)
+            hev[k][1].record(stream)
+        torch.cuda.synchronize()
+        build_ms = {}
+        for kind in ("hcluster", "lbvh"):
+            scene.set_tree(kind)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(10):
+                scene.rebuild()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            build_ms[kind] = e0.elapsed_time(e1) / 10
+        extra["frame_hcluster_tree"] = {
+            "ms_per_step": float(np.mean([a.elapsed_time(b) for a, b in hev])),
+            "tree_build_ms": build_ms}
 
     peaks = _peaks()
     conv_ms = prof["conv_tc"][0] / prof_steps
