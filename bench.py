@@ -272,7 +272,7 @@ def run_reference(args, rank, world):
 # ----------------------------------------------------------------------------
 # equal-PSNR comparison: hybrid frame vs plain high-resolution path tracing
 # ----------------------------------------------------------------------------
-def train_net(mrs, s, n_scenes=160, steps=6000):
+def train_net(mrs, s, n_scenes=800, steps=20000):
     """Trains the fusion network by the training recipe (seeded 200k-triangle
     scenes, seeds 1.. -- never the bench scene -- one 256^2 window of the
     1024^2 frame per scene with LRHS 64 spp, HRLS 4 spp and a 1024-spp
