@@ -2,9 +2,11 @@
 """Benchmark of the multi-resolution sampling hot path on GB300.
 
 One step = one hybrid frame of the 200k-triangle procedural scene:
-  LBVH rebuild -> LRHS render 256x256 @ 64 spp -> HRLS render 1024x1024 @ 4 spp
+  render-tree rebuild (Morton codes, radix sort, hierarchical clustering in one
+  launch) -> LRHS render 256x256 @ 64 spp -> HRLS render 1024x1024 @ 4 spp
   (+ albedo / normal / depth) -> x4 fusion CNN in BF16 on tcgen05 -> fallback
-  gate (box-downsampled fused vs LRHS, RelMSE threshold 0.01).
+  gate (box-downsampled fused vs LRHS, RelMSE threshold 0.01).  The same frame
+  over the Karras LBVH (radix tree + refit) is reported beside it.
 Max depth 8 with Russian roulette from bounce 3 for both renders.
 
 Prints one JSON line.  `value` is device-timed ms per frame (inputs resident in
@@ -30,10 +32,13 @@ sys.path.insert(0, ROOT)
 
 METRIC = "ms/frame at equal PSNR, hybrid vs plain HR path trace; Msamples/s; conv TFLOP/s"
 WORKLOAD = {
-    "workload": "hybrid frame: procedural 200,968-triangle scene (seed 0); LRHS 256x256 @ 64 spp + "
+    "workload": "hybrid frame: procedural 200,968-triangle scene (seed 0), render tree rebuilt "
+                "every step; LRHS 256x256 @ 64 spp + "
                 "HRLS 1024x1024 @ 4 spp (albedo/normal/depth), max depth 8, roulette from bounce 3; "
                 "x4 fusion CNN (12->64, 8 residual blocks, 64->3) in BF16 on tcgen05; fallback gate; "
                 "the two renders run concurrently on two streams",
+    "tree": "hierarchical clustering in one launch over the Morton-sorted triangles (the images "
+            "are those of the LBVH bit for bit)",
     "scene_seed": 0, "lrhs": [256, 256, 64], "hrls": [1024, 1024, 4], "scale": 4,
     "max_depth": 8, "rr_start": 3, "precision": "bf16",
     "net_init": "trained before the timed region by the training recipe (reduced: see "
@@ -41,6 +46,7 @@ WORKLOAD = {
     "l2": "flushed between steps (512 MiB write)",
 }
 LR, HR, S = 256, 1024, 4
+TREE = "hcluster"       # the frame's render tree (mrs_scene_set_tree)
 SPP_LR, SPP_HR, DEPTH, RR = 64, 4, 8, 3
 CONV_FLOP_PER_PX = 2 * 9 * (12 * 64 + 16 * 64 * 64 + 64 * 3)      # 1,196,928
 # algorithmic HBM bytes per HR pixel of the 18 BF16 conv layers: input layer
@@ -813,6 +819,7 @@ def run_gpu(args, rank, world):
     stream = torch.cuda.current_stream()
     desc = scenes.procedural(0)
     scene = mrs.Scene(desc)
+    scene.set_tree(TREE)
     # the network: trained on held-out scenes before anything is timed (the
     # timed frame and the equal-PSNR comparison use the same weights);
     # --quick keeps the Kaiming initialisation (timing does not depend on the
@@ -977,10 +984,10 @@ def run_gpu(args, rank, world):
         torch.cuda.synchronize()
         pms = e0.elapsed_time(e1)
         rays = int(plain["counts"].sum().item() + plain["shadow_counts"].sum().item())
-        # the same render over the clustering trees (grid-wide rounds, and
-        # the one-launch hierarchical build)
+        # the same render over the other trees (the radix tree, and clustering
+        # in grid-wide rounds)
         tree_ms = {}
-        for kind in ("cluster", "hcluster"):
+        for kind in ("lbvh", "cluster"):
             scene.set_tree(kind)
             plain = mrs.render(scene, HR, HR, 64, DEPTH, RR, 8, out=plain)
             torch.cuda.synchronize()
@@ -989,17 +996,18 @@ def run_gpu(args, rank, world):
             e1.record(stream)
             torch.cuda.synchronize()
             tree_ms[kind] = e0.elapsed_time(e1)
-        scene.set_tree("lbvh")
+        scene.set_tree(TREE)
         extra["plain_path_trace_1024_64spp"] = {
-            "ms": pms, "msamples_per_s": HR * HR * 64 / pms / 1e3, "mrays_per_s": rays / pms / 1e3,
+            "tree": TREE, "ms": pms, "msamples_per_s": HR * HR * 64 / pms / 1e3,
+            "mrays_per_s": rays / pms / 1e3,
+            "lbvh_tree_ms": tree_ms["lbvh"],
+            "lbvh_tree_msamples_per_s": HR * HR * 64 / tree_ms["lbvh"] / 1e3,
             "cluster_tree_ms": tree_ms["cluster"],
-            "cluster_tree_msamples_per_s": HR * HR * 64 / tree_ms["cluster"] / 1e3,
-            "hcluster_tree_ms": tree_ms["hcluster"],
-            "hcluster_tree_msamples_per_s": HR * HR * 64 / tree_ms["hcluster"] / 1e3}
-        # the timed frame again with its tree rebuilt by the one-launch
-        # hierarchical clustering instead of the radix tree (same steps, same
-        # L2 flush; the images are the same bit for bit), and both builds alone
-        scene.set_tree("hcluster")
+            "cluster_tree_msamples_per_s": HR * HR * 64 / tree_ms["cluster"] / 1e3}
+        # the timed frame again with its tree rebuilt as the Karras LBVH (radix
+        # tree and refit) instead (same steps, same L2 flush; the images are the
+        # same bit for bit), and both builds alone
+        scene.set_tree("lbvh")
         for k in range(3):
             frame(2000 + k)
         hev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -1012,7 +1020,7 @@ def run_gpu(args, rank, world):
             hev[k][1].record(stream)
         torch.cuda.synchronize()
         build_ms = {}
-        for kind in ("hcluster", "lbvh"):
+        for kind in ("lbvh", TREE):
             scene.set_tree(kind)
             torch.cuda.synchronize()
             e0.record(stream)
@@ -1021,7 +1029,7 @@ def run_gpu(args, rank, world):
             e1.record(stream)
             torch.cuda.synchronize()
             build_ms[kind] = e0.elapsed_time(e1) / 10
-        extra["frame_hcluster_tree"] = {
+        extra["frame_lbvh_tree"] = {
             "ms_per_step": float(np.mean([a.elapsed_time(b) for a, b in hev])),
             "tree_build_ms": build_ms}
 

@@ -264,7 +264,7 @@ mrs_status mrs_render_stats(mrs_scene scene, int32_t W, int32_t H, int32_t spp, 
  * mrs_profile_read (which synchronises on those events) returns and clears
  * the total milliseconds and launch count of one kernel family:
  * 0 closest-hit traversal, 1 shade, 2 shadow traversal, 3 ray generation,
- * 4 accumulation, 5 LBVH build (whole), 6 tensor-core conv, 7 SIMT conv,
+ * 4 accumulation, 5 render-tree build (whole, any kind), 6 tensor-core conv, 7 SIMT conv,
  * 8 fusion input, 9 metrics, 10 training kernels (other than 11),
  * 11 tensor-core weight gradient, 12 the render's tail kernel (the late
  * bounces' traversal, shading and shadow rays in one launch).

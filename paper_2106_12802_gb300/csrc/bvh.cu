@@ -163,40 +163,27 @@ __global__ void k_sort_hist(const uint32_t* __restrict__ keys, int n, int shift,
     counts[threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
 }
 
-// exclusive scan of counts[0..m) in place, one block of 1024 threads: each
-// thread sums a contiguous run of ceil(m / 1024) counts, one block-wide scan
-// of the 1024 run totals gives each run's offset, and each thread writes its
-// run's exclusive prefix (integer sums: the order does not change the result).
-// A run is read in groups of kScanGroup independent loads, so that a thread
-// waits for the memory once per group rather than once per count (a 200k-key
-// sort has runs of 25 counts: one wait per pass).
-constexpr int kScanGroup = 32;
+// exclusive scan of counts[0..m) in place, one block of 1024 threads: warp w
+// owns a contiguous chunk, which it reads 32 consecutive counts at a time
+// (coalesced); a first pass sums each chunk, one warp scans the 32 chunk
+// totals, and a second pass scans each chunk group by group by shuffles,
+// carrying the running offset (integer sums: the order does not change the
+// result)
 __global__ void __launch_bounds__(1024) k_sort_scan(uint32_t* __restrict__ counts, int m)
 {
     __shared__ uint32_t s[32];
-    const int per = (m + 1023) / 1024;
-    const int b0 = threadIdx.x * per;
-    uint32_t sum = 0;
-    for (int k0 = 0; k0 < per; k0 += kScanGroup) {
-        uint32_t v[kScanGroup];
-#pragma unroll
-        for (int j = 0; j < kScanGroup; ++j) {
-            const int i = b0 + k0 + j;
-            v[j] = (k0 + j < per && i < m) ? counts[i] : 0u;
-        }
-#pragma unroll
-        for (int j = 0; j < kScanGroup; ++j) sum += v[j];
-    }
-    // block-wide inclusive scan of the run totals: within each warp by
-    // shuffles, then over the 32 warp totals
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t incl = sum;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, off);
-        if (lane >= off) incl += t;
+    const int chunk = ((m + 31) / 32 + 31) & ~31;
+    const int b0 = warp * chunk;
+    uint32_t sum = 0;
+#pragma unroll 8
+    for (int k = lane; k < chunk; k += 32) {
+        const int i = b0 + k;
+        if (i < m) sum += counts[i];
     }
-    if (lane == 31) s[warp] = incl;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+    if (lane == 0) s[warp] = sum;
     __syncthreads();
     if (warp == 0) {
         uint32_t w = s[lane];
@@ -208,21 +195,19 @@ __global__ void __launch_bounds__(1024) k_sort_scan(uint32_t* __restrict__ count
         s[lane] = w;
     }
     __syncthreads();
-    incl += warp > 0 ? s[warp - 1] : 0u;
-    uint32_t run = incl - sum;
-    for (int k0 = 0; k0 < per; k0 += kScanGroup) {
-        uint32_t v[kScanGroup];
+    uint32_t carry = warp > 0 ? s[warp - 1] : 0u;
+#pragma unroll 4
+    for (int k = lane; k < chunk; k += 32) {
+        const int i = b0 + k;
+        const uint32_t v = i < m ? counts[i] : 0u;
+        uint32_t x = v;
 #pragma unroll
-        for (int j = 0; j < kScanGroup; ++j) {
-            const int i = b0 + k0 + j;
-            v[j] = (k0 + j < per && i < m) ? counts[i] : 0u;
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, x, off);
+            if (lane >= off) x += t;
         }
-#pragma unroll
-        for (int j = 0; j < kScanGroup; ++j) {
-            const int i = b0 + k0 + j;
-            if (k0 + j < per && i < m) counts[i] = run;
-            run += v[j];
-        }
+        if (i < m) counts[i] = carry + x - v;
+        carry += __shfl_sync(0xffffffffu, x, 31);
     }
 }
 
@@ -351,6 +336,21 @@ __global__ void k_big_leaves(const float* __restrict__ V, const int* __restrict_
     tri_ml[k] = make_int2(tri_mat[prim], tri_light[prim]);
 }
 
+// atomic add at GPU scope: acquire-release (publishes the box this thread
+// wrote before it), or acquire only (a leaf's box comes from an earlier kernel)
+__device__ __forceinline__ int add_acq_rel(int* p, int v)
+{
+    int old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ int add_acquire(int* p, int v)
+{
+    int old;
+    asm volatile("atom.acquire.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
 // bottom-up refit: the second child to arrive at a parent computes its box
 // and writes the 64-byte traversal node (both child boxes + child ids)
 __global__ void k_refit(int n, const int* __restrict__ left, const int* __restrict__ right,
@@ -360,10 +360,12 @@ __global__ void k_refit(int n, const int* __restrict__ left, const int* __restri
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     int node = parent[(n - 1) + k];
+    bool wrote = false;
     while (node >= 0) {
-        __threadfence();
-        if (atomicAdd(&visit[node], 1) == 0) return;   // first arrival: the sibling finishes
-        __threadfence();
+        // first arrival: the sibling finishes (the exchange releases the box
+        // written below, and acquires the sibling's)
+        if ((wrote ? add_acq_rel(&visit[node], 1) : add_acquire(&visit[node], 1)) == 0) return;
+        wrote = true;
         int l = left[node], r = right[node];
         const volatile float* bl = box + (size_t)l * 6;
         const volatile float* br = box + (size_t)r * 6;
@@ -1034,11 +1036,18 @@ __device__ void hcluster_merge(const HClusterArgs& a, int L, int R, int p, HWarp
     __syncwarp();
 }
 
-// atomic exchange with acquire-release semantics at GPU scope
+// atomic exchange at GPU scope: acquire-release (publishes what the warp
+// stored before it), or acquire only (nothing new to publish)
 __device__ __forceinline__ int exch_acq_rel(int* p, int v)
 {
     int old;
     asm volatile("atom.acq_rel.gpu.global.exch.b32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ int exch_acquire(int* p, int v)
+{
+    int old;
+    asm volatile("atom.acquire.gpu.global.exch.b32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
     return old;
 }
 
@@ -1049,6 +1058,7 @@ __global__ void __launch_bounds__(128) k_hcluster(const HClusterArgs a)
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     int L = k, R = k;
     bool active = k < ns;
+    bool fresh = false;   // this lane's range merged since its last exchange
     for (int level = 0; level < kHLevels; ++level) {
         if (!__any_sync(0xffffffffu, active)) return;
         int p = 0;
@@ -1057,8 +1067,11 @@ __global__ void __launch_bounds__(128) k_hcluster(const HClusterArgs a)
             const bool is_left = L == 0 ||
                                  (R != ns - 1 && key_xor(a.code, a.order, R) < key_xor(a.code, a.order, L - 1));
             p = is_left ? R : L - 1;
-            // releases what this warp stored for the range, acquires the sibling's
-            const int prev = exch_acq_rel(a.other + p, (is_left ? L : R) + 1);
+            // releases what this warp stored for the range (if it merged: a
+            // range of leaves only has the previous kernel's data), acquires
+            // the sibling's
+            const int v = (is_left ? L : R) + 1;
+            const int prev = fresh ? exch_acq_rel(a.other + p, v) : exch_acquire(a.other + p, v);
             if (prev == 0) {
                 active = false;
             } else {
@@ -1069,6 +1082,7 @@ __global__ void __launch_bounds__(128) k_hcluster(const HClusterArgs a)
         }
         const bool root = up && L == 0 && R == ns - 1;
         unsigned need = __ballot_sync(0xffffffffu, up && (R - L + 1 > kHKeep || root));
+        fresh = (need >> (threadIdx.x & 31)) & 1u;
         while (need) {
             const int q = __ffs(need) - 1;
             need &= need - 1;
@@ -1424,10 +1438,10 @@ __global__ void k_static_refit(int n, const int* __restrict__ left, const int* _
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     int node = parent[(n - 1) + k];
+    bool wrote = false;
     while (node >= 0) {
-        __threadfence();
-        if (atomicAdd(&visit[node], 1) == 0) return;
-        __threadfence();
+        if ((wrote ? add_acq_rel(&visit[node], 1) : add_acquire(&visit[node], 1)) == 0) return;
+        wrote = true;
         const volatile float* bl = box + (size_t)left[node] * 6;
         const volatile float* br = box + (size_t)right[node] * 6;
         float* b = box + (size_t)node * 6;

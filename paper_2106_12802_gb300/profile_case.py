@@ -4,7 +4,7 @@ This is the package's profiling entry point: every command recorded under
 profiles/ runs one of these cases.
 
   python -m paper_2106_12802_gb300.profile_case fuse   --size 1024 --prec bf16
-  python -m paper_2106_12802_gb300.profile_case render --size 512 --spp 4
+  python -m paper_2106_12802_gb300.profile_case render --size 512 --spp 4 [--tree hcluster]
   python -m paper_2106_12802_gb300.profile_case rdn    --size 1024 --prec bf16
   python -m paper_2106_12802_gb300.profile_case train  --batch 16 --crop 128
   python -m paper_2106_12802_gb300.profile_case rdn_train --batch 16 --crop 192 --prec bf16
@@ -13,7 +13,7 @@ profiles/ runs one of these cases.
 `fuse` runs the x4 fusion network at size x size output (inputs random,
 Kaiming weights); `rdn` the method's own x4 two-encoder network (the same);
 `render` renders the 200k-triangle procedural scene (seed 0, depth 8, roulette
-from bounce 3) and prints its per-bounce ray counts, whose bounce >= 1 part is
+from bounce 3; over the radix tree, or --tree cluster / hcluster) and prints its per-bounce ray counts, whose bounce >= 1 part is
 the number of closest-hit segments the tail kernel traces (the unit that a
 traffic capture of one tail launch is divided by); `train` runs BF16 training
 steps of the fusion network on a random batch; `rdn_train` training steps of
@@ -37,6 +37,7 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("case", choices=["fuse", "render", "rdn", "train", "rdn_train", "tree"])
     ap.add_argument("--kind", default="cluster")
+    ap.add_argument("--tree", default="lbvh")
     ap.add_argument("--size", type=int, default=1024)
     ap.add_argument("--prec", default="bf16")
     ap.add_argument("--spp", type=int, default=4)
@@ -107,6 +108,7 @@ def main(argv=None):
         print("tree ok", sc.tree())
     else:
         sc = mrs.Scene(scenes.procedural(0))
+        sc.set_tree(a.tree)
         for _ in range(2):
             r = mrs.render(sc, a.size, a.size, a.spp, a.depth, rr_start=3, seed=0)
         torch.cuda.synchronize()

@@ -314,7 +314,7 @@ def render_stats(scene: Scene, W, H, spp, max_depth, rr_start=None, seed=0, stre
     return out
 
 
-PROFILE_KERNELS = ["trace", "shade", "shadow", "raygen", "accumulate", "lbvh", "conv_tc",
+PROFILE_KERNELS = ["trace", "shade", "shadow", "raygen", "accumulate", "tree", "conv_tc",
                    "conv_simt", "input", "metrics", "train", "wgrad_tc", "tail"]
 
 
