@@ -129,7 +129,7 @@ mrs_status mrs_scene_rebuild(mrs_scene scene, void* stream);
 
 /* The render tree (the nodes mrs_render, mrs_cast and the path tracer walk):
  *   MRS_TREE_LBVH     the Karras radix tree with refitted boxes (the default:
- *                     the cheapest build, for scenes rebuilt every frame)
+ *                     the cheapest build)
  *   MRS_TREE_CLUSTER  locally-ordered agglomerative clustering (Meister and
  *                     Bittner, TVCG 2018) over the Morton-sorted leaves, search
  *                     radius 16: each round, every cluster picks the neighbour
@@ -144,8 +144,10 @@ mrs_status mrs_scene_rebuild(mrs_scene scene, void* stream);
  *                     more, one warp merges mutual nearest pairs among all of
  *                     them until 16 are left (one at the root).  Nearly the
  *                     global rounds' surface-area cost, no read-back, also
- *                     inside a caller's stream capture.  Node ids (not the
- *                     tree) depend on the order in which warps merge.
+ *                     inside a caller's stream capture.  Node ids are a
+ *                     function of the tree (the radix tree's split
+ *                     positions), the same on every rebuild.  A frame that
+ *                     rebuilds its tree every step runs fastest over it.
  * set_tree records the choice and rebuilds the tree on `stream` (synchronised).
  * get_tree returns the kind in use: MRS_TREE_LBVH also when clustering was
  * asked for but did not finish within its bound of 72 grid-wide rounds plus

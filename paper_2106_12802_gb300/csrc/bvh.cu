@@ -840,7 +840,7 @@ mrs_status ploc_continue(mrs_scene_s* S, const PlocBufs& b, cudaStream_t st)
 //    children's clusters (at most kHKeep each, so at most one per lane) and
 //    runs clustering rounds on them -- every cluster's nearest neighbour
 //    among all others by union surface area (ties as in the global rounds,
-//    by the pair hash of list positions), mutual pairs merge -- until at most
+//    by the pair hash of the clusters' lanes), mutual pairs merge -- until at most
 //    kHKeep are left (one at the root).  They are stored at the range's first
 //    positions with their count, for the next level.
 // Node ids come from the split positions: a subtree of the radix tree over
