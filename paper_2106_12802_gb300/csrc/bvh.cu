@@ -1,10 +1,13 @@
-// LBVH construction on the GPU: centroid bounds, 30-bit Morton codes, a
-// stable LSD radix sort of (code, triangle index), the binary radix tree of
-// Karras (HPG 2012) and a bottom-up box refit that also writes the traversal
+// Render-tree construction on the GPU: centroid bounds, 30-bit Morton codes,
+// a stable LSD radix sort of (code, triangle index), then the binary radix
+// tree of Karras (HPG 2012) with a bottom-up box refit, or locally-ordered
+// clustering over the sorted leaves (in grid-wide rounds, or inside the radix
+// tree's subtrees in one launch); every tree is written in the same traversal
 // node layout (both child boxes + child ids in one 64-byte node).
 //
 // Compiled with --fmad=false: the Morton quantisation must round exactly like
 // the oracle's ((v0 + v1) + v2) * (1/3), (c - lo) * (1024 / extent).
+#include <float.h>
 #include <stdarg.h>
 #include <string.h>
 
@@ -885,6 +888,14 @@ struct HClusterArgs {
     int ns;
 };
 
+// a pair's entry in the matrix: its union's half area, at most FLT_MAX (+inf
+// marks "no pair": an overflowing or NaN area -- huge or non-finite
+// coordinates -- must still order the pair, so that every round merges)
+__device__ __forceinline__ float pair_area(float4 a0, float4 a1, float4 b0, float4 b1)
+{
+    return fminf(union_half_area(a0, a1, b0, b1), FLT_MAX);
+}
+
 // Per-warp scratch of a merge: the union areas of the warp's cluster pairs
 struct HWarpScratch {
     float D[32][33];        // half surface area of cluster i's and j's union (+inf: none)
@@ -953,7 +964,7 @@ __device__ void hcluster_merge(const HClusterArgs& a, int L, int R, int p, HWarp
             const float4 o0 = shfl4(b0, j);
             const float o1x = __shfl_sync(0xffffffffu, b1.x, j), o1y = __shfl_sync(0xffffffffu, b1.y, j);
             const float u = mine && ((alive >> j) & 1u)
-                                ? union_half_area(b0, b1, o0, make_float4(o1x, o1y, 0.0f, 0.0f))
+                                ? pair_area(b0, b1, o0, make_float4(o1x, o1y, 0.0f, 0.0f))
                                 : INFINITY;
             sc.D[lane][j] = u;
             sc.D[j][lane] = u;
@@ -1012,7 +1023,7 @@ __device__ void hcluster_merge(const HClusterArgs& a, int L, int R, int p, HWarp
         __syncwarp();
         for (unsigned mm = lm; mm; mm &= mm - 1) {
             const int k = __ffs(mm) - 1;
-            const float u = mine && lane != k ? union_half_area(sc.kb[2 * k], sc.kb[2 * k + 1], b0, b1)
+            const float u = mine && lane != k ? pair_area(sc.kb[2 * k], sc.kb[2 * k + 1], b0, b1)
                                               : INFINITY;
             sc.D[k][lane] = u;
             sc.D[lane][k] = u;

@@ -136,6 +136,31 @@ def test_procedural_scene_trees(mrs, orc):
           {k: v["visits"] for k, v in st.items()}, "shadow:", {k: v["shadow_visits"] for k, v in st.items()})
 
 
+def test_hcluster_tree_with_overflowing_and_nan_boxes(mrs):
+    # triangles a 1e20 apart make union areas overflow single precision and
+    # a NaN vertex makes a NaN box: the one-launch build must still merge
+    # every cluster (its pair areas are capped at FLT_MAX) into one valid
+    # tree, whose closest hits equal the radix tree's (NaN triangles are
+    # never hit)
+    desc = _soup(11, 3000)
+    V = desc["V"].reshape(3000, 3, 3)
+    V[::40] *= np.float32(1e20)       # 75 of them: more than the 64 large triangles
+                                      # tested outside the tree, so all are in it
+    V[7::97, 1, 0] = np.nan
+    desc["V"] = V.reshape(desc["V"].shape)
+    o, d = scenes.random_rays(11, 20000)
+    sc = mrs.Scene(desc)
+    to, td = torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda()
+    pl, tl = sc.cast(to, td)
+    sc.set_tree("hcluster")
+    assert sc.tree() == "hcluster"
+    t = sc.export_nodes()
+    ids = t["child"].ravel()
+    assert np.array_equal(np.sort(ids), np.arange(1, 2 * t["ns"] - 1))
+    ph, th = sc.cast(to, td)
+    assert torch.equal(ph, pl) and torch.equal(th, tl)
+
+
 def test_hcluster_node_ids_are_a_function_of_the_tree(mrs):
     # node ids come from the split positions, not from the order in which
     # warps merge: rebuilding gives the same node array bit for bit
