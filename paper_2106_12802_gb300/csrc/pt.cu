@@ -24,7 +24,9 @@ constexpr float RAY_EPS = 1e-4f;
 constexpr float SHADOW_FRAC = 0.999f;
 constexpr float T_INF = 1e30f;
 constexpr int kThreads = 256;
-constexpr int kStack = 64;   // LBVH depth <= 62 (one key bit per level)
+// traversal stack: the radix tree over 64-bit keys is at most 63 deep; the
+// clustering trees have no bound by construction (measured at most 63 deep)
+constexpr int kStack = 128;
 
 // ---- Philox4x32-10 (Salmon et al., SC'11) ----------------------------------
 __device__ __forceinline__ uint4 philox(uint4 c, uint2 k)

@@ -50,7 +50,8 @@ def check_tree(t, V):
     c = ids[~leaf]
     assert np.array_equal(bx[~leaf, :3], box[c, :, :3].min(axis=1))
     assert np.array_equal(bx[~leaf, 3:], box[c, :, 3:].max(axis=1))
-    # depth within the traversal's 64-entry stack (a far child per level)
+    # depth within the traversal's 128-entry stack (a far child per level);
+    # every tree here is in fact at most 63 deep
     depth = np.zeros(ns - 1, np.int64)
     order_ = [0]
     for v in order_:
@@ -58,7 +59,7 @@ def check_tree(t, V):
             if c_ < ns - 1:
                 depth[c_] = depth[v] + 1
                 order_.append(c_)
-    assert depth.max() + 1 <= 64, depth.max()
+    assert depth.max() + 1 <= 64, depth.max()       # the stack holds 128
     node_lo, node_hi = box[:, :, :3].min(axis=1), box[:, :, 3:].max(axis=1)
     root = _half_area(node_lo[0], node_hi[0])
     return float((_half_area(node_lo, node_hi).sum() + _half_area(bx[leaf, :3], bx[leaf, 3:]).sum())
