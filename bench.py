@@ -371,7 +371,8 @@ def equal_psnr(mrs, scene, s, net, training, ref_spp=4096):
 # ----------------------------------------------------------------------------
 # batched serving: many frames of uneven size, scale and spp in one CUDA graph
 # ----------------------------------------------------------------------------
-def batched_serving(mrs, params, n_jobs=32, seed=5, psnr_window=256, ref_spp=4096, reps=3):
+def batched_serving(mrs, params, n_jobs=32, seed=5, psnr_window=256, ref_spp=4096, reps=3,
+                    tree="cluster"):
     """32 hybrid frames of 32 different seeded 200k-triangle scenes: HR in
     {512, 1024, 2048}^2, scale in {2, 4}, HRLS spp in {1, 2, 4, 8}, LRHS
     64 spp.  All 64 renders are one batched render (mrs_render_batch: the
@@ -384,7 +385,9 @@ def batched_serving(mrs, params, n_jobs=32, seed=5, psnr_window=256, ref_spp=409
     over its central psnr_window^2 window (a window render is bit-identical
     to those pixels of the whole render).  For comparison the same frames
     are also timed with one render call per frame (the batch as 64 separate
-    renders in one graph)."""
+    renders in one graph).  The scenes are built once, before anything is
+    timed, with the `tree` render tree (default: clustering in grid-wide
+    rounds, the fastest to render over)."""
     import torch
 
     from paper_2106_12802_gb300 import autotune
@@ -394,6 +397,8 @@ def batched_serving(mrs, params, n_jobs=32, seed=5, psnr_window=256, ref_spp=409
         frames.append({"scene": mrs.Scene.seeded(200 + j), "hr": int(rng.choice([512, 1024, 2048])),
                        "s": int(rng.choice([2, 4])), "spp_h": int(rng.choice([1, 2, 4, 8])),
                        "seed": 1000 + j})
+    for f in frames:
+        f["scene"].set_tree(tree)
     net = mrs.Net(params)
     dev = torch.device("cuda")
     groups = {}
@@ -443,7 +448,7 @@ def batched_serving(mrs, params, n_jobs=32, seed=5, psnr_window=256, ref_spp=409
     tuned["ring"], t_ring = autotune.tune("batch:ring", [{"ring": r} for r in autotune.RING_CANDIDATES],
                                           lambda c: mrs.conv_set_ring(c["ring"]),
                                           lambda: fuse_all("bf16"), reps=2, cache=None)
-    result = {"jobs": n_jobs, "distinct_scenes": n_jobs,
+    result = {"jobs": n_jobs, "distinct_scenes": n_jobs, "tree": tree,
               "hr_mix": {str(r): sum(1 for f in frames if f["hr"] == r) for r in (512, 1024, 2048)},
               "groups": {f"{H}x{H}/s{s}": len(fs) for (H, s), fs in groups.items()},
               "paths_per_batch": int(sum((f["hr"] // f["s"]) ** 2 * SPP_LR + f["hr"] ** 2 * f["spp_h"]
